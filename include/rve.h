@@ -1,0 +1,203 @@
+/*
+ * rve.h -- C ABI of the GB300 ADMM solver for periodic micromechanics cells.
+ *
+ * Method: Zhou & Bhattacharya, "Accelerated computational micromechanics",
+ * Section 2.1 (augmented Lagrangian, eq. al; ADMM Steps 1-4, eqs. eq, helm,
+ * update, check; penalty update eq. rho-update) on the periodic unit cell of
+ * Section 2.3 (strain control <F> = Fbar, central-difference symbols).
+ *
+ * Conventions shared by every call
+ *   - The cell is the unit cube [0,1)^d, d = 2 (plane strain) or 3, on an
+ *     N^d grid, h = 1/N.  N is even, of the form 2^a 3^b, 4 <= N <= 512.
+ *   - A scalar field is N^d values, x fastest: index (z*N + y)*N + x.
+ *   - A tensor field (F, Lambda) is d*d scalar fields, component-major,
+ *     component (i, j) at offset (i*d + j) * N^d.  A vector field (u~, n) is
+ *     d (or 3 for n) scalar fields.
+ *   - 3x3 host matrices (Fbar, stress) are row-major double[9]; in 2D only the
+ *     upper-left 2x2 block is read or written (the rest of stress is zero).
+ *   - The multiplier Lambda has the paper's sign: the Lagrangian term is
+ *     Lambda : (grad u - F), so Lambda converges to the first Piola-Kirchhoff
+ *     stress (Section 2.1, "Connection to physics").
+ *   - All calls return an int status: RVE_OK (0) or a negative RVE_E_* code.
+ *     No exception crosses the ABI and device code never traps; device-side
+ *     failures come back as status codes.  rve_strerror() names a code.
+ *   - A handle is used by one host thread at a time.
+ *   - Host pointers passed in are read during the call only; the caller keeps
+ *     ownership.  Device memory is owned by the handle (or by the caller when a
+ *     workspace is supplied to rve_create_in).
+ */
+#ifndef RVE_H
+#define RVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define RVE_OK 0
+#define RVE_E_INVALID_ARG (-1)   /* bad size, pointer, enum or value          */
+#define RVE_E_OOM (-2)           /* device allocation or workspace too small */
+#define RVE_E_NOT_CONVERGED (-3) /* max_iter reached; state valid, info set  */
+#define RVE_E_NUMERICAL (-4)     /* NaN/Inf residual or J <= 0 in the state  */
+#define RVE_E_CUDA (-5)          /* a CUDA runtime call failed               */
+#define RVE_E_BUSY (-6)          /* server: no slot / queue full             */
+#define RVE_E_STATE (-7)         /* call out of order (e.g. no material set) */
+#define RVE_E_NOT_FOUND (-8)     /* server: unknown or finished ticket       */
+
+/* ------------------------------------------------------------------ enums */
+enum rve_model {
+    RVE_NEOHOOKE = 0, /* W = mu/2(|F|^2 - d - 2 ln J) + lam/2 (J-1)^2, Section 4.1
+                         params per phase: {mu, lam}                           */
+    RVE_LINEAR = 1,   /* W = mu|sym(F-I)|^2 + lam/2 tr(F-I)^2, params {mu, lam} */
+    RVE_LCE = 2       /* liquid crystal elastomer, Section 5.1 (3D only); params
+                         per phase {mu, lam, r, alpha, kappa_F}; needs n0      */
+};
+enum rve_precision {
+    RVE_FP64 = 0,  /* every field, FFT and local solve in double                 */
+    RVE_MIXED = 1, /* float bulk (fields, FFT, Newton) with double residuals and
+                      stress; promoted to double for the final iterations        */
+    RVE_FP32 = 2   /* float bulk only, double residuals (stops at its floor)     */
+};
+enum rve_rho_policy { RVE_RHO_FIXED = 0, RVE_RHO_ADAPTIVE = 1 };
+enum rve_lambda0 { RVE_LAMBDA0_STRESS = 0, RVE_LAMBDA0_ZERO = 1 };
+enum rve_field { RVE_FIELD_F = 0, RVE_FIELD_LAMBDA = 1, RVE_FIELD_U = 2, RVE_FIELD_N = 3 };
+
+/* ------------------------------------------------------------------ options */
+typedef struct rve_options {
+    int precision;      /* enum rve_precision, default RVE_FP64                    */
+    int rho_policy;     /* enum rve_rho_policy, default fixed                      */
+    int lambda0;        /* initial multiplier of a fresh state: W_F(Fbar) or 0     */
+    int max_iter;       /* ADMM iteration cap per solve, default 1000              */
+    int newton_max;     /* per-voxel Newton iteration cap, default 30              */
+    double newton_tol;  /* Newton stops after a full step with max|dF| <= this;
+                           0 selects 1e-10 (double) / 1e-5 (float)                 */
+    double rho_kappa;   /* adaptive rho factor (eq. rho-update), default 1.3       */
+    double rho_tau;     /* adaptive rho balance threshold, default 10              */
+    double rho_min;     /* adaptive rho lower bound; 0 selects mu_ref              */
+    double mu_ref;      /* modulus in r_d (eq. check); 0 selects the volume average
+                           of the per-voxel shear modulus                          */
+    double mixed_switch;/* RVE_MIXED: promote to double once max(r_p, r_d) <= this
+                           or float stagnates; default 1e-6                        */
+    int check_every;    /* host reads the device status every this many iterations */
+    int use_graph;      /* 1: replay iteration chunks as a CUDA graph (default 1)  */
+} rve_options;
+
+/* Fill *opt with the defaults listed above. */
+void rve_default_options(rve_options* opt);
+
+/* ------------------------------------------------------------------ solve info */
+typedef struct rve_solve_info {
+    int iterations;        /* ADMM iterations done by this solve (all precisions) */
+    int fp64_iterations;   /* of which in double (RVE_MIXED polish)               */
+    int converged;         /* 1 if r_p <= tol and r_d <= tol                      */
+    int status;            /* same code the call returned                         */
+    double r_p, r_d;       /* residuals of the last iteration (eq. check)         */
+    double rho;            /* penalty used in the last iteration                  */
+    double mu_ref;         /* modulus used in r_d                                 */
+    int newton_max_iters;  /* largest per-voxel Newton count in the last pass     */
+    long long newton_fail; /* voxels that hit newton_max in the last pass         */
+    double time_ms;        /* device time of the iteration loop (CUDA events)    */
+    long long launches;    /* kernel launches this solve issued (graph nodes too) */
+} rve_solve_info;
+
+typedef struct rve* rve_t;
+
+/* ------------------------------------------------------------------ lifetime */
+/* Create a solver for a d-dimensional N^d cell (d = 2 or 3).  All device state
+ * is allocated here with cudaMalloc and stays resident until rve_destroy.
+ * opt may be NULL (defaults).  cuda_stream is a cudaStream_t (NULL = legacy
+ * default stream); all device work of the handle is ordered after prior work
+ * on that stream and each call returns with its work finished.
+ * Errors: RVE_E_INVALID_ARG (bad d, N, options), RVE_E_OOM, RVE_E_CUDA. */
+int rve_create(rve_t* out, int dim, int n, int model, const rve_options* opt, void* cuda_stream);
+
+/* Same as rve_create but carves all device state out of a caller-owned device
+ * buffer of `bytes` bytes (>= rve_workspace_bytes(...), 256-byte aligned), which
+ * must outlive the handle.  Nothing is allocated on the device. */
+int rve_create_in(rve_t* out, int dim, int n, int model, const rve_options* opt, void* cuda_stream,
+                  void* device_workspace, size_t bytes);
+
+/* Device bytes a handle of this shape and these options needs (fields, tables,
+ * control block, residual history); opt may be NULL (defaults).  0 if invalid. */
+size_t rve_workspace_bytes(int dim, int n, int model, const rve_options* opt);
+
+/* Release the handle and, unless the workspace was supplied, its device memory. */
+void rve_destroy(rve_t h);
+
+/* ------------------------------------------------------------------ material */
+/* Set the microstructure: phase[N^d] (host, values < nphase), params[nphase *
+ * nparam] per-phase constants of the model (see enum rve_model), n0[3 * N^d]
+ * (host, unit vectors, component-major) for RVE_LCE, else NULL.  Marks the
+ * state fresh: the next solve starts from F = Fbar, u~ = 0, Lambda_0.
+ * Errors: RVE_E_INVALID_ARG (phase id out of range, non-positive modulus,
+ * nparam too small, missing n0), RVE_E_CUDA. */
+int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* params, int nparam,
+                     const double* n0);
+
+/* ------------------------------------------------------------------ solve */
+/* Run ADMM iterations (Section 2.1, Steps 1-4) at macroscopic gradient Fbar
+ * until r_p <= tol and r_d <= tol or opt.max_iter iterations.  A fresh state is
+ * initialised from Fbar; otherwise the resident state (F, Lambda, u~) of the
+ * previous solve is the warm start (the previous load step, Algorithm 1).  rho
+ * is the penalty (the starting value under the adaptive policy).  tol < 0 runs
+ * exactly max_iter iterations.  info may be NULL.
+ * Returns RVE_OK, RVE_E_NOT_CONVERGED (state valid), RVE_E_NUMERICAL,
+ * RVE_E_STATE (no material), RVE_E_INVALID_ARG (rho <= 0, det Fbar <= 0),
+ * RVE_E_CUDA. */
+int rve_solve(rve_t h, const double Fbar[9], double rho, double tol, rve_solve_info* info);
+
+/* Homogenised first Piola-Kirchhoff stress <W_F(F)> of the current state,
+ * summed in double on the device (Section 2.3: <S> is the macroscopic stress). */
+int rve_stress(rve_t h, double S[9]);
+
+/* Mean of the multiplier field <Lambda> (equals <W_F(F)> at an exact local solve). */
+int rve_mean_lambda(rve_t h, double L[9]);
+
+/* Copy a field of the current state to/from host doubles in the layout above:
+ * F, LAMBDA: d*d*N^d; U: d*N^d (the periodic part u~); N: 3*N^d (RVE_LCE).
+ * rve_set_field makes the state non-fresh (it is the warm start of the next solve). */
+int rve_get_field(rve_t h, int which, double* host_out);
+int rve_set_field(rve_t h, int which, const double* host_in);
+
+/* Mark the state fresh (the next solve starts from F = Fbar, u~ = 0). */
+int rve_reset(rve_t h);
+
+/* Residual history of the last solve: r_p, r_d and the rho used, per iteration
+ * (up to cap entries).  Returns the number of entries written (>= 0) or an error. */
+int rve_history(rve_t h, double* r_p, double* r_d, double* rho, int cap);
+
+/* ------------------------------------------------------------------ profiling */
+/* Kernel classes of the iteration (index into rve_kernel_times' arrays). */
+enum rve_kernel_class {
+    RVE_KCLASS_LOCAL = 0,       /* fused Step 3 + Step 4 partials + Step 1 (per iteration)   */
+    RVE_KCLASS_LOCAL_FIRST = 1, /* Step 1 alone (start of a solve / precision phase)         */
+    RVE_KCLASS_XFWD = 2,        /* divergence of F - Lambda/rho + forward x FFT (Step 2)     */
+    RVE_KCLASS_FWD_Y = 3,       /* forward y FFT (3D)                                        */
+    RVE_KCLASS_SOLVE = 4,       /* last-axis forward FFT, multiply by 1/|k|^2, inverse       */
+    RVE_KCLASS_INV_Y = 5,       /* inverse y FFT (3D)                                        */
+    RVE_KCLASS_XINV = 6,        /* inverse x FFT -> u~ (Step 2 result)                       */
+    RVE_KCLASS_COUNT = 7
+};
+
+/* on != 0: every kernel launch of later solves is bracketed by CUDA events on
+ * the handle's stream (CUDA graphs are not used meanwhile) and its device time is
+ * added to per-class totals, for iterations that ran before the stop flag.
+ * Switching it (on or off) clears the totals. */
+int rve_set_profiling(rve_t h, int on);
+
+/* Copy the per-class totals for the double (fp64 != 0) or float kernels:
+ * ms[c] summed milliseconds, launches[c] launch count, for c < RVE_KCLASS_COUNT.
+ * cap is the length of both arrays (>= RVE_KCLASS_COUNT).  Returns the number
+ * of classes written or RVE_E_INVALID_ARG. */
+int rve_kernel_times(rve_t h, int fp64, double* ms, long long* launches, int cap);
+
+/* Human-readable name of a status code (static string). */
+const char* rve_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RVE_H */

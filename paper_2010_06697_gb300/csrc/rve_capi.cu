@@ -1,0 +1,738 @@
+// Host side of the C ABI declared in include/rve.h: handle lifetime, device
+// workspace layout, FFT plans and tables, and the ADMM driver loop
+// (Zhou & Bhattacharya, Algorithm 1: initialise, iterate Steps 1-4 on the
+// device until both residuals pass, keep the state resident between solves).
+//
+// The iteration loop never waits on the host per iteration: chunks of
+// `check_every` iterations are replayed as one CUDA graph, every kernel exits
+// at once when the device-side stop flag is set, and the host reads the control
+// block once per chunk.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/rve.h"
+#include "rve_internal.cuh"
+
+using admm::Ctrl;
+using admm::Launch;
+
+struct rve {
+    int dim = 0, n = 0, model = 0;
+    long long V = 0;
+    rve_options opt{};
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev0 = nullptr, ev1 = nullptr;
+    unsigned char* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+    Launch L{};
+    Ctrl* hctrl = nullptr;  // pinned host mirror of the control block
+    bool material_set = false;
+    bool fresh = true;
+    int state_fp64 = 1;     // which set holds the current state
+    double mu_ref = 1.0;
+    int nphase = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [fp64]
+    long long k = 0;        // host copy of Ctrl::k
+    int last_iters = 0;
+    long long launches = 0; // kernel launches issued by the running solve
+    // profiling: every launch bracketed by events, per kernel class and precision
+    bool prof = false;
+    std::vector<cudaEvent_t> pev;
+    double prof_ms[2][RVE_KCLASS_COUNT] = {};
+    long long prof_n[2][RVE_KCLASS_COUNT] = {};
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool valid_n(int n) {
+    if (n < 4 || n > 512 || (n & 1)) return false;
+    int m = n;
+    while (m % 2 == 0) m /= 2;
+    while (m % 3 == 0) m /= 3;
+    return m == 1;
+}
+
+int factor(int L, int* rad) {
+    int np = 0;
+    while (L % 8 == 0) { rad[np++] = 8; L /= 8; }
+    if (L % 4 == 0) { rad[np++] = 4; L /= 4; }
+    if (L % 2 == 0) { rad[np++] = 2; L /= 2; }
+    while (L % 3 == 0) { rad[np++] = 3; L /= 3; }
+    return L == 1 ? np : -1;
+}
+
+int local_blocks_for(long long V) {
+    const long long want = (V + admm::kLocalThreads - 1) / admm::kLocalThreads;
+    const long long cap = 152 * 12;  // whole waves at 2, 3, 4 or 6 resident blocks per SM
+    return (int)(want < cap ? want : cap);
+}
+
+struct Layout {
+    size_t ctrl, hist, partials, phase, mat, n0;
+    size_t F64[2], L64, U64[2], tw64, ksq64;
+    size_t F32[2], L32, U32[2], tw32, ksq32;
+    size_t total;
+};
+
+Layout layout(int dim, int n, int model, int precision, int max_iter) {
+    Layout o{};
+    const long long V = dim == 3 ? (long long)n * n * n : (long long)n * n;
+    const size_t nF = (size_t)dim * dim * V, nU = (size_t)dim * V;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    o.ctrl = take(sizeof(Ctrl));
+    o.hist = take(sizeof(double) * 3 * (size_t)(max_iter + 1));
+    o.partials = take(sizeof(double) * admm::kPartialStride * (size_t)local_blocks_for(V));
+    o.phase = take((size_t)V);
+    o.mat = take(sizeof(double) * 256 * admm::kMaxParam);
+    o.n0 = model == admm::kLce ? take(sizeof(double) * 3 * (size_t)V) : 0;
+    const bool need64 = precision != RVE_FP32;
+    const bool need32 = precision != RVE_FP64;
+    if (need64) {
+        o.F64[0] = take(8 * nF);
+        o.F64[1] = take(8 * nF);
+        o.L64 = take(8 * nF);
+        o.U64[0] = take(8 * nU);
+        o.U64[1] = take(8 * nU);
+        o.tw64 = take(16 * (size_t)n);
+        o.ksq64 = take(8 * (size_t)n);
+    }
+    if (need32) {
+        o.F32[0] = take(4 * nF);
+        o.F32[1] = take(4 * nF);
+        o.L32 = take(4 * nF);
+        o.U32[0] = take(4 * nU);
+        o.U32[1] = take(4 * nU);
+        o.tw32 = take(8 * (size_t)n);
+        o.ksq32 = take(4 * (size_t)n);
+    }
+    o.total = off;
+    return o;
+}
+
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return RVE_E_CUDA; \
+    } while (0)
+
+int read_ctrl(rve* h) {
+    CK(cudaMemcpyAsync(h->hctrl, h->L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->k = h->hctrl->k;
+    return RVE_OK;
+}
+
+int write_ctrl(rve* h) {
+    CK(cudaMemcpyAsync(h->L.ctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+    return RVE_OK;
+}
+
+// Order the handle's stream after everything already queued on the caller's stream.
+int enter(rve* h) {
+    CK(cudaEventRecord(h->ev_in, h->user_stream));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+    return RVE_OK;
+}
+
+// kernel class of FFT stage s (see rve_kernel_times)
+int fft_class(int dim, int s) {
+    if (dim == 3) return RVE_KCLASS_XFWD + s;
+    return s == 0 ? RVE_KCLASS_XFWD : (s == 1 ? RVE_KCLASS_SOLVE : RVE_KCLASS_XINV);
+}
+
+int launches_per_iteration(const rve* h) {
+    return admm::fft_stages(h->dim) + 1 + (h->opt.rho_policy == RVE_RHO_ADAPTIVE ? 1 : 0);
+}
+
+int ensure_prof_events(rve* h) {
+    const size_t need = (size_t)h->opt.check_every * (admm::fft_stages(h->dim) + 3) + 2;
+    while (h->pev.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        h->pev.push_back(e);
+    }
+    return RVE_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+// Profiled variant of one chunk: direct launches with an event after each kernel;
+// only iterations that ran (before the stop flag) are accumulated.
+int run_chunk_profiled(rve* h, bool fp64) {
+    const int S = admm::fft_stages(h->dim);
+    const int per = S + 2 + 1;  // start event, S fft, local, redo
+    const long long k_before = h->hctrl->k;
+    const int f = fp64 ? 1 : 0;
+    for (int i = 0; i < h->opt.check_every; ++i) {
+        cudaEvent_t* e = &h->pev[(size_t)i * per];
+        CK(cudaEventRecord(e[0], h->stream));
+        for (int st = 0; st < S; ++st) {
+            if (admm::launch_fft(h->L, fp64, st) != cudaSuccess) return RVE_E_CUDA;
+            CK(cudaEventRecord(e[1 + st], h->stream));
+        }
+        if (admm::launch_local(h->L, fp64, false, false) != cudaSuccess) return RVE_E_CUDA;
+        CK(cudaEventRecord(e[1 + S], h->stream));
+        if (h->opt.rho_policy == RVE_RHO_ADAPTIVE) {
+            if (admm::launch_local(h->L, fp64, true, true) != cudaSuccess) return RVE_E_CUDA;
+            CK(cudaEventRecord(e[2 + S], h->stream));
+        }
+    }
+    const int rc = read_ctrl(h);
+    if (rc) return rc;
+    const long long ran = h->hctrl->k - k_before;
+    for (long long i = 0; i < ran && i < h->opt.check_every; ++i) {
+        cudaEvent_t* e = &h->pev[(size_t)i * per];
+        for (int st = 0; st < S; ++st) {
+            h->prof_ms[f][fft_class(h->dim, st)] += elapsed(e[st], e[st + 1]);
+            h->prof_n[f][fft_class(h->dim, st)] += 1;
+        }
+        h->prof_ms[f][RVE_KCLASS_LOCAL] += elapsed(e[S], e[S + 1]);
+        h->prof_n[f][RVE_KCLASS_LOCAL] += 1;
+    }
+    return RVE_OK;
+}
+
+int capture_chunk(rve* h, bool fp64) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < h->opt.check_every && e == cudaSuccess; ++i) {
+        e = admm::launch_fft(h->L, fp64);
+        if (e == cudaSuccess) e = admm::launch_local(h->L, fp64, false, false);
+        if (e == cudaSuccess && h->opt.rho_policy == RVE_RHO_ADAPTIVE) e = admm::launch_local(h->L, fp64, true, true);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return RVE_E_CUDA;
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&h->graph[fp64 ? 1 : 0], g, 0);
+    cudaGraphDestroy(g);
+    return e3 == cudaSuccess ? RVE_OK : RVE_E_CUDA;
+}
+
+// Run iterations in one precision until the device sets the stop flag.
+int run_phase(rve* h, bool fp64) {
+    if (h->prof) {
+        if (ensure_prof_events(h)) return RVE_E_CUDA;
+        const size_t last = h->pev.size() - 2;
+        CK(cudaEventRecord(h->pev[last], h->stream));
+        if (admm::launch_local(h->L, fp64, true, false) != cudaSuccess) return RVE_E_CUDA;
+        CK(cudaEventRecord(h->pev[last + 1], h->stream));
+        CK(cudaEventSynchronize(h->pev[last + 1]));
+        h->prof_ms[fp64 ? 1 : 0][RVE_KCLASS_LOCAL_FIRST] += elapsed(h->pev[last], h->pev[last + 1]);
+        h->prof_n[fp64 ? 1 : 0][RVE_KCLASS_LOCAL_FIRST] += 1;
+    } else if (admm::launch_local(h->L, fp64, true, false) != cudaSuccess) {
+        return RVE_E_CUDA;
+    }
+    h->launches += 1;
+    for (;;) {
+        h->launches += (long long)h->opt.check_every * launches_per_iteration(h);
+        if (h->prof) {
+            const int rc = run_chunk_profiled(h, fp64);
+            if (rc) return rc;
+            if (h->hctrl->done != admm::kRunning) return RVE_OK;
+            continue;
+        }
+        if (h->opt.use_graph) {
+            if (!h->graph[fp64 ? 1 : 0]) {
+                const int rc = capture_chunk(h, fp64);
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(h->graph[fp64 ? 1 : 0], h->stream));
+        } else {
+            for (int i = 0; i < h->opt.check_every; ++i) {
+                if (admm::launch_fft(h->L, fp64) != cudaSuccess) return RVE_E_CUDA;
+                if (admm::launch_local(h->L, fp64, false, false) != cudaSuccess) return RVE_E_CUDA;
+                if (h->opt.rho_policy == RVE_RHO_ADAPTIVE &&
+                    admm::launch_local(h->L, fp64, true, true) != cudaSuccess)
+                    return RVE_E_CUDA;
+            }
+        }
+        const int rc = read_ctrl(h);
+        if (rc) return rc;
+        if (h->hctrl->done != admm::kRunning) return RVE_OK;
+    }
+}
+
+int upload_tables(rve* h) {
+    const int n = h->n;
+    std::vector<double> tw(2 * (size_t)n), ksq(n);
+    std::vector<float> tw32(2 * (size_t)n), ksq32(n);
+    const double pi = 3.14159265358979323846;
+    for (int m = 0; m < n; ++m) {
+        const double a = -2.0 * pi * (double)m / (double)n;
+        tw[2 * m] = cos(a);
+        tw[2 * m + 1] = sin(a);
+        const double s = (m == 0 || 2 * m == n) ? 0.0 : (double)n * sin(2.0 * pi * (double)m / (double)n);
+        ksq[m] = s * s;
+        tw32[2 * m] = (float)tw[2 * m];
+        tw32[2 * m + 1] = (float)tw[2 * m + 1];
+        ksq32[m] = (float)ksq[m];
+    }
+    if (h->L.tw64) {
+        CK(cudaMemcpyAsync((void*)h->L.tw64, tw.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync((void*)h->L.ksq64, ksq.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+    }
+    if (h->L.tw32) {
+        CK(cudaMemcpyAsync((void*)h->L.tw32, tw32.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync((void*)h->L.ksq32, ksq32.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return RVE_OK;
+}
+
+int check_options(const rve_options& o) {
+    if (o.precision < RVE_FP64 || o.precision > RVE_FP32) return RVE_E_INVALID_ARG;
+    if (o.rho_policy != RVE_RHO_FIXED && o.rho_policy != RVE_RHO_ADAPTIVE) return RVE_E_INVALID_ARG;
+    if (o.lambda0 != RVE_LAMBDA0_STRESS && o.lambda0 != RVE_LAMBDA0_ZERO) return RVE_E_INVALID_ARG;
+    if (o.max_iter < 0 || o.max_iter > 10000000) return RVE_E_INVALID_ARG;
+    if (o.newton_max < 1 || o.newton_max > 1000) return RVE_E_INVALID_ARG;
+    if (!(o.newton_tol >= 0) || !(o.rho_kappa > 1) || !(o.rho_tau > 1) || !(o.rho_min >= 0)) return RVE_E_INVALID_ARG;
+    if (!(o.mu_ref >= 0) || !(o.mixed_switch >= 0)) return RVE_E_INVALID_ARG;
+    if (o.check_every < 1 || o.check_every > 4096) return RVE_E_INVALID_ARG;
+    return RVE_OK;
+}
+
+int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt, void* stream, void* ws,
+                  size_t bytes) {
+    if (!out) return RVE_E_INVALID_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || !valid_n(n)) return RVE_E_INVALID_ARG;
+    if (model != RVE_NEOHOOKE && model != RVE_LINEAR) return RVE_E_INVALID_ARG;
+    rve_options o;
+    rve_default_options(&o);
+    if (opt) o = *opt;
+    if (check_options(o)) return RVE_E_INVALID_ARG;
+    const Layout lay = layout(dim, n, model, o.precision, o.max_iter);
+    if (ws && (bytes < lay.total || ((uintptr_t)ws % kAlign) != 0)) return RVE_E_OOM;
+
+    rve* h = new (std::nothrow) rve();
+    if (!h) return RVE_E_OOM;
+    h->dim = dim;
+    h->n = n;
+    h->model = model;
+    h->V = dim == 3 ? (long long)n * n * n : (long long)n * n;
+    h->opt = o;
+    h->user_stream = (cudaStream_t)stream;
+    auto fail = [&](int code) {
+        rve_destroy(h);
+        return code;
+    };
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(RVE_E_CUDA);
+    if (cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess) return fail(RVE_E_CUDA);
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) return fail(RVE_E_CUDA);
+    if (cudaMallocHost((void**)&h->hctrl, sizeof(Ctrl)) != cudaSuccess) return fail(RVE_E_CUDA);
+    memset(h->hctrl, 0, sizeof(Ctrl));
+    if (ws) {
+        h->ws = (unsigned char*)ws;
+        h->ws_bytes = bytes;
+    } else {
+        if (cudaMalloc((void**)&h->ws, lay.total) != cudaSuccess) return fail(RVE_E_OOM);
+        h->own_ws = true;
+        h->ws_bytes = lay.total;
+    }
+    if (enter(h)) return fail(RVE_E_CUDA);
+    if (cudaMemsetAsync(h->ws, 0, lay.total, h->stream) != cudaSuccess) return fail(RVE_E_CUDA);
+
+    Launch& L = h->L;
+    unsigned char* b = h->ws;
+    L.stream = h->stream;
+    L.dim = dim;
+    L.n = n;
+    L.model = model;
+    L.V = h->V;
+    L.local_blocks = local_blocks_for(h->V);
+    L.ctrl = (Ctrl*)(b + lay.ctrl);
+    L.hist = (double*)(b + lay.hist);
+    L.partials = (double*)(b + lay.partials);
+    L.phase = (const uint8_t*)(b + lay.phase);
+    L.mat = (const double*)(b + lay.mat);
+    L.nparam = 2;
+    L.n0 = model == admm::kLce ? (const double*)(b + lay.n0) : nullptr;
+    if (o.precision != RVE_FP32) {
+        L.F64[0] = (double*)(b + lay.F64[0]);
+        L.F64[1] = (double*)(b + lay.F64[1]);
+        L.L64 = (double*)(b + lay.L64);
+        L.U64[0] = (double*)(b + lay.U64[0]);
+        L.U64[1] = (double*)(b + lay.U64[1]);
+        L.tw64 = (const double2*)(b + lay.tw64);
+        L.ksq64 = (const double*)(b + lay.ksq64);
+    }
+    if (o.precision != RVE_FP64) {
+        L.F32[0] = (float*)(b + lay.F32[0]);
+        L.F32[1] = (float*)(b + lay.F32[1]);
+        L.L32 = (float*)(b + lay.L32);
+        L.U32[0] = (float*)(b + lay.U32[0]);
+        L.U32[1] = (float*)(b + lay.U32[1]);
+        L.tw32 = (const float2*)(b + lay.tw32);
+        L.ksq32 = (const float*)(b + lay.ksq32);
+    }
+    const int H = n / 2;
+    L.plan.n = n;
+    L.plan.np_half = factor(H, L.plan.rad_half);
+    L.plan.np_full = factor(n, L.plan.rad_full);
+    if (L.plan.np_half < 0 || L.plan.np_full < 0) return fail(RVE_E_INVALID_ARG);
+    if (admm::prepare_fft_kernels(n) != cudaSuccess) return fail(RVE_E_CUDA);
+    h->state_fp64 = o.precision == RVE_FP64 ? 1 : 0;
+    h->hctrl->hist_cap = o.max_iter + 1;
+    if (write_ctrl(h)) return fail(RVE_E_CUDA);
+    if (upload_tables(h)) return fail(RVE_E_CUDA);
+    *out = h;
+    return RVE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rve_default_options(rve_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = RVE_FP64;
+    o->rho_policy = RVE_RHO_FIXED;
+    o->lambda0 = RVE_LAMBDA0_STRESS;
+    o->max_iter = 1000;
+    o->newton_max = 30;
+    o->newton_tol = 0.0;
+    o->rho_kappa = 1.3;
+    o->rho_tau = 10.0;
+    o->rho_min = 0.0;
+    o->mu_ref = 0.0;
+    o->mixed_switch = 1e-6;
+    o->check_every = 16;
+    o->use_graph = 1;
+}
+
+size_t rve_workspace_bytes(int dim, int n, int model, const rve_options* opt) {
+    if ((dim != 2 && dim != 3) || !valid_n(n)) return 0;
+    rve_options o;
+    rve_default_options(&o);
+    if (opt) o = *opt;
+    if (check_options(o)) return 0;
+    return layout(dim, n, model, o.precision, o.max_iter).total;
+}
+
+int rve_create(rve_t* out, int dim, int n, int model, const rve_options* opt, void* cuda_stream) {
+    return create_common(out, dim, n, model, opt, cuda_stream, nullptr, 0);
+}
+
+int rve_create_in(rve_t* out, int dim, int n, int model, const rve_options* opt, void* cuda_stream,
+                  void* device_workspace, size_t bytes) {
+    if (!device_workspace) return RVE_E_INVALID_ARG;
+    return create_common(out, dim, n, model, opt, cuda_stream, device_workspace, bytes);
+}
+
+void rve_destroy(rve_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int i = 0; i < 2; ++i)
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+    if (h->own_ws && h->ws) cudaFree(h->ws);
+    if (h->hctrl) cudaFreeHost(h->hctrl);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* params, int nparam,
+                     const double* n0) {
+    if (!h || !phase || !params || nphase < 1 || nphase > 256 || nparam < 2 || nparam > admm::kMaxParam)
+        return RVE_E_INVALID_ARG;
+    (void)n0;
+    std::vector<long long> count(256, 0);
+    for (long long v = 0; v < h->V; ++v) {
+        if (phase[v] >= nphase) return RVE_E_INVALID_ARG;
+        count[phase[v]]++;
+    }
+    std::vector<double> tab(256 * (size_t)admm::kMaxParam, 0.0);
+    double musum = 0.0;
+    for (int p = 0; p < nphase; ++p) {
+        const double mu = params[p * nparam + 0], lam = params[p * nparam + 1];
+        if (!(mu > 0) || !(lam >= 0) || !isfinite(mu) || !isfinite(lam)) return RVE_E_INVALID_ARG;
+        for (int q = 0; q < nparam; ++q) tab[p * admm::kMaxParam + q] = params[p * nparam + q];
+        musum += mu * (double)count[p];
+    }
+    if (enter(h)) return RVE_E_CUDA;
+    CK(cudaMemcpyAsync((void*)h->L.phase, phase, (size_t)h->V, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync((void*)h->L.mat, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->L.nparam = admm::kMaxParam;
+    h->nphase = nphase;
+    h->mu_ref = musum / (double)h->V;
+    h->material_set = true;
+    h->fresh = true;
+    return RVE_OK;
+}
+
+int rve_reset(rve_t h) {
+    if (!h) return RVE_E_INVALID_ARG;
+    h->fresh = true;
+    return RVE_OK;
+}
+
+int rve_solve(rve_t h, const double Fbar[9], double rho, double tol, rve_solve_info* info) {
+    if (!h || !Fbar) return RVE_E_INVALID_ARG;
+    if (!h->material_set) return RVE_E_STATE;
+    if (!(rho > 0) || !isfinite(rho) || isnan(tol)) return RVE_E_INVALID_ARG;
+    for (int i = 0; i < 9; ++i)
+        if (!isfinite(Fbar[i])) return RVE_E_INVALID_ARG;
+    const double det2 = Fbar[0] * Fbar[4] - Fbar[1] * Fbar[3];
+    const double det3 = Fbar[0] * (Fbar[4] * Fbar[8] - Fbar[5] * Fbar[7]) -
+                        Fbar[1] * (Fbar[3] * Fbar[8] - Fbar[5] * Fbar[6]) +
+                        Fbar[2] * (Fbar[3] * Fbar[7] - Fbar[4] * Fbar[6]);
+    if (!((h->dim == 2 ? det2 : det3) > 0)) return RVE_E_INVALID_ARG;
+    const rve_options& o = h->opt;
+    if (enter(h)) return RVE_E_CUDA;
+    int rc = read_ctrl(h);
+    if (rc) return rc;
+    Ctrl& c = *h->hctrl;
+    for (int i = 0; i < 9; ++i) c.Fbar[i] = Fbar[i];
+    c.rho = rho;
+    c.inv_rho = 1.0 / rho;
+    c.mu_ref = o.mu_ref > 0 ? o.mu_ref : h->mu_ref;
+    c.tol = tol;
+    c.rho_kappa = o.rho_kappa;
+    c.rho_tau = o.rho_tau;
+    c.rho_min = o.rho_min > 0 ? o.rho_min : c.mu_ref;
+    c.switch_tol = o.mixed_switch;
+    c.best = INFINITY;
+    c.stall = 0;
+    c.k_start = c.k;
+    c.k_cap = c.k + o.max_iter;
+    c.done = o.max_iter > 0 ? admm::kRunning : admm::kCapped;
+    c.adaptive = o.rho_policy == RVE_RHO_ADAPTIVE;
+    c.rho_changed = 0;
+    c.newton_cap = o.newton_max;
+    c.hist_cap = o.max_iter + 1;
+    c.counter = 0;
+    c.counter2 = 0;
+    c.newton_max = 0;
+    c.newton_fail = 0;
+    const bool fp32_first = o.precision != RVE_FP64;
+    c.phase_fp32 = fp32_first ? 1 : 0;
+    c.newton_tol = o.newton_tol > 0 ? o.newton_tol : (fp32_first ? 1e-5 : 1e-10);
+    if (write_ctrl(h)) return RVE_E_CUDA;
+    CK(cudaEventRecord(h->ev0, h->stream));
+    h->launches = 0;
+    if (h->fresh) {
+        h->launches += 1;
+        if (admm::launch_init(h->L, !fp32_first, o.lambda0 == RVE_LAMBDA0_ZERO) != cudaSuccess) return RVE_E_CUDA;
+        h->fresh = false;
+        h->state_fp64 = fp32_first ? 0 : 1;
+    } else if (fp32_first && h->state_fp64) {
+        h->launches += 1;
+        if (admm::launch_convert(h->L, false) != cudaSuccess) return RVE_E_CUDA;
+        h->state_fp64 = 0;
+    }
+    const long long k0 = c.k;
+    int fp64_iters = 0;
+    if (c.done == admm::kRunning) {
+        rc = run_phase(h, !fp32_first);
+        if (rc) return rc;
+        if (o.precision == RVE_MIXED && h->hctrl->done == admm::kSwitch) {
+            const long long ksw = h->hctrl->k;
+            h->launches += 1;
+            if (admm::launch_convert(h->L, true) != cudaSuccess) return RVE_E_CUDA;
+            h->state_fp64 = 1;
+            h->hctrl->done = admm::kRunning;
+            h->hctrl->phase_fp32 = 0;
+            h->hctrl->counter = 0;
+            h->hctrl->newton_tol = o.newton_tol > 0 ? o.newton_tol : 1e-10;
+            if (write_ctrl(h)) return RVE_E_CUDA;
+            rc = run_phase(h, true);
+            if (rc) return rc;
+            fp64_iters = (int)(h->hctrl->k - ksw);
+        } else if (o.precision == RVE_FP64) {
+            fp64_iters = (int)(h->hctrl->k - k0);
+        }
+    }
+    CK(cudaEventRecord(h->ev1, h->stream));
+    CK(cudaEventSynchronize(h->ev1));
+    if (read_ctrl(h)) return RVE_E_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    const Ctrl& e = *h->hctrl;
+    int status;
+    switch (e.done) {
+        case admm::kConverged: status = RVE_OK; break;
+        case admm::kNumerical: status = RVE_E_NUMERICAL; break;
+        default: status = RVE_E_NOT_CONVERGED; break;
+    }
+    h->last_iters = (int)(e.k - k0);
+    if (info) {
+        info->iterations = h->last_iters;
+        info->fp64_iterations = fp64_iters;
+        info->converged = e.done == admm::kConverged;
+        info->status = status;
+        info->r_p = e.r_p;
+        info->r_d = e.r_d;
+        info->rho = e.rho;
+        info->mu_ref = e.mu_ref;
+        info->newton_max_iters = e.newton_max;
+        info->newton_fail = (long long)e.newton_fail;
+        info->time_ms = ms;
+        info->launches = h->launches;
+    }
+    return status;
+}
+
+int rve_stress(rve_t h, double S[9]) {
+    if (!h || !S) return RVE_E_INVALID_ARG;
+    if (!h->material_set) return RVE_E_STATE;
+    if (enter(h)) return RVE_E_CUDA;
+    if (admm::launch_stress(h->L, h->state_fp64 != 0) != cudaSuccess) return RVE_E_CUDA;
+    if (read_ctrl(h)) return RVE_E_CUDA;
+    for (int i = 0; i < 9; ++i) S[i] = h->hctrl->stress[i];
+    return RVE_OK;
+}
+
+int rve_mean_lambda(rve_t h, double Lm[9]) {
+    if (!h || !Lm) return RVE_E_INVALID_ARG;
+    if (!h->material_set) return RVE_E_STATE;
+    if (enter(h)) return RVE_E_CUDA;
+    if (admm::launch_stress(h->L, h->state_fp64 != 0) != cudaSuccess) return RVE_E_CUDA;
+    if (read_ctrl(h)) return RVE_E_CUDA;
+    for (int i = 0; i < 9; ++i) Lm[i] = h->hctrl->lam_mean[i];
+    return RVE_OK;
+}
+
+static int field_ptr(rve_t h, int which, void** ptr, size_t* count) {
+    const long long V = h->V;
+    const int par = (int)(h->k & 1);
+    const bool f64 = h->state_fp64 != 0;
+    switch (which) {
+        case RVE_FIELD_F:
+            *ptr = f64 ? (void*)h->L.F64[par] : (void*)h->L.F32[par];
+            *count = (size_t)h->dim * h->dim * V;
+            return RVE_OK;
+        case RVE_FIELD_LAMBDA:
+            *ptr = f64 ? (void*)h->L.L64 : (void*)h->L.L32;
+            *count = (size_t)h->dim * h->dim * V;
+            return RVE_OK;
+        case RVE_FIELD_U:
+            *ptr = f64 ? (void*)h->L.U64[par] : (void*)h->L.U32[par];
+            *count = (size_t)h->dim * V;
+            return RVE_OK;
+        default: return RVE_E_INVALID_ARG;
+    }
+}
+
+int rve_get_field(rve_t h, int which, double* out) {
+    if (!h || !out) return RVE_E_INVALID_ARG;
+    void* p;
+    size_t cnt;
+    int rc = field_ptr(h, which, &p, &cnt);
+    if (rc) return rc;
+    if (enter(h)) return RVE_E_CUDA;
+    if (h->state_fp64) {
+        CK(cudaMemcpyAsync(out, p, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    } else {
+        std::vector<float> tmp(cnt);
+        CK(cudaMemcpyAsync(tmp.data(), p, cnt * 4, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (size_t i = 0; i < cnt; ++i) out[i] = tmp[i];
+    }
+    return RVE_OK;
+}
+
+int rve_set_field(rve_t h, int which, const double* in) {
+    if (!h || !in) return RVE_E_INVALID_ARG;
+    void* p;
+    size_t cnt;
+    int rc = field_ptr(h, which, &p, &cnt);
+    if (rc) return rc;
+    for (size_t i = 0; i < cnt; ++i)
+        if (!isfinite(in[i])) return RVE_E_INVALID_ARG;
+    if (enter(h)) return RVE_E_CUDA;
+    if (h->state_fp64) {
+        CK(cudaMemcpyAsync(p, in, cnt * 8, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    } else {
+        std::vector<float> tmp(cnt);
+        for (size_t i = 0; i < cnt; ++i) tmp[i] = (float)in[i];
+        CK(cudaMemcpyAsync(p, tmp.data(), cnt * 4, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    h->fresh = false;
+    return RVE_OK;
+}
+
+int rve_history(rve_t h, double* rp, double* rd, double* rho, int cap) {
+    if (!h || cap < 0) return RVE_E_INVALID_ARG;
+    int cnt = h->last_iters < cap ? h->last_iters : cap;
+    if (cnt > h->opt.max_iter + 1) cnt = h->opt.max_iter + 1;
+    if (cnt <= 0) return 0;
+    std::vector<double> tmp(3 * (size_t)cnt);
+    if (enter(h)) return RVE_E_CUDA;
+    CK(cudaMemcpyAsync(tmp.data(), h->L.hist, tmp.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < cnt; ++i) {
+        if (rp) rp[i] = tmp[3 * i];
+        if (rd) rd[i] = tmp[3 * i + 1];
+        if (rho) rho[i] = tmp[3 * i + 2];
+    }
+    return cnt;
+}
+
+int rve_set_profiling(rve_t h, int on) {
+    if (!h) return RVE_E_INVALID_ARG;
+    h->prof = on != 0;
+    for (int f = 0; f < 2; ++f)
+        for (int c = 0; c < RVE_KCLASS_COUNT; ++c) {
+            h->prof_ms[f][c] = 0.0;
+            h->prof_n[f][c] = 0;
+        }
+    return RVE_OK;
+}
+
+int rve_kernel_times(rve_t h, int fp64, double* ms, long long* launches, int cap) {
+    if (!h || !ms || !launches || cap < RVE_KCLASS_COUNT) return RVE_E_INVALID_ARG;
+    const int f = fp64 ? 1 : 0;
+    for (int c = 0; c < RVE_KCLASS_COUNT; ++c) {
+        ms[c] = h->prof_ms[f][c];
+        launches[c] = h->prof_n[f][c];
+    }
+    return RVE_KCLASS_COUNT;
+}
+
+const char* rve_strerror(int code) {
+    switch (code) {
+        case RVE_OK: return "ok";
+        case RVE_E_INVALID_ARG: return "invalid argument";
+        case RVE_E_OOM: return "out of device memory or workspace too small";
+        case RVE_E_NOT_CONVERGED: return "not converged within max_iter";
+        case RVE_E_NUMERICAL: return "numerical failure (non-finite residual)";
+        case RVE_E_CUDA: return "CUDA runtime error";
+        case RVE_E_BUSY: return "busy: no free slot";
+        case RVE_E_STATE: return "call out of order (material not set)";
+        case RVE_E_NOT_FOUND: return "unknown ticket";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,504 @@
+// Spectral Helmholtz projection, Zhou & Bhattacharya Section 2.1 Step 2 (eq. helm)
+// solved in Fourier space (eq. helmf) on the periodic cell of Section 2.3:
+//
+//   D^T D u~_{i+1} = D^T (F_{i+1} - Lambda_i / rho),
+//
+// D the central-difference gradient (symbol i k_j, k_j = sin(h xi_j)/h), so the
+// Laplacian symbol is |k|^2 = sum_j k_j^2 and u^ = (D^T Q)^ / |k|^2, u^ = 0 where
+// |k|^2 = 0.  The divergence D^T Q is taken in real space inside the first FFT
+// pass; per component the rest is a scalar periodic Poisson solve.
+//
+// Pass structure per iteration (3D; 2D drops the y pass pair):
+//   k_xfwd   divergence stencil of Q = F - Lambda/rho, real-to-complex FFT along x
+//   k_faxis  forward FFT along y
+//   k_faxis  forward FFT along z, multiply by 2/(N^d |k|^2), inverse FFT along z
+//   k_faxis  inverse FFT along y
+//   k_xinv   complex-to-real inverse FFT along x -> u~_{i+1}
+// The spectrum of u~_{i+1} is built in the buffer that held u~_{i-1} (dead once
+// the fused local kernel of iteration i has run), so no extra field is stored.
+//
+// Real-to-complex along x: a real line of N points is read as N/2 complex
+// points z_m = r_{2m} + i r_{2m+1}, transformed at length N/2 and split into the
+// N/2+1 bins of the real transform.  Bins 0 and N/2 are real and their symbol
+// k_x vanishes at both, so they are stored together as one complex value
+// (X_0 + i X_{N/2}); every x-line then holds exactly N/2 complex bins and the
+// spectrum occupies the same bytes as the real field.
+//
+// Each 1D transform is a self-sorting Stockham FFT (radix 8/4/3/2) staged in
+// shared memory; x-lines are read and written as contiguous rows, y/z lines as
+// tiles of TK adjacent columns so that every global access is a coalesced row
+// segment.  Twiddles come from a per-grid table exp(-2 pi i m / N) computed on
+// the host in double.
+#include <stdint.h>
+
+#include "rve_internal.cuh"
+
+namespace admm {
+namespace {
+
+template <typename T>
+struct Cx;
+template <>
+struct Cx<double> { using t = double2; };
+template <>
+struct Cx<float> { using t = float2; };
+
+template <typename V>
+__device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
+template <typename V>
+__device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
+template <typename V>
+__device__ __forceinline__ V cmul(V a, V b) { return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+template <typename V>
+__device__ __forceinline__ V cconj(V a) { return V{a.x, -a.y}; }
+template <typename V>
+__device__ __forceinline__ V mul_i(V a) { return V{-a.y, a.x}; }   // i a
+template <typename V>
+__device__ __forceinline__ V mul_mi(V a) { return V{a.y, -a.x}; }  // -i a
+template <typename V, typename S>
+__device__ __forceinline__ V cscale(V a, S s) { return V{a.x * s, a.y * s}; }
+
+// Small DFTs, sign -1 (forward) or +1 (INV), unnormalised.
+template <bool INV, typename V>
+__device__ __forceinline__ void dft2(V* v) {
+    const V a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+}
+template <bool INV, typename V>
+__device__ __forceinline__ void dft3(V* v) {
+    using S = decltype(v[0].x);
+    const S c = S(0.86602540378443864676);  // sin(2 pi / 3)
+    const V s12 = cadd(v[1], v[2]);
+    const V d12 = cscale(csub(v[1], v[2]), c);
+    const V t = csub(v[0], cscale(s12, S(0.5)));
+    v[0] = cadd(v[0], s12);
+    const V jd = INV ? mul_i(d12) : mul_mi(d12);
+    v[1] = cadd(t, jd);
+    v[2] = csub(t, jd);
+}
+template <bool INV, typename V>
+__device__ __forceinline__ void dft4(V& a0, V& a1, V& a2, V& a3) {
+    const V s02 = cadd(a0, a2), d02 = csub(a0, a2);
+    const V s13 = cadd(a1, a3), d13 = csub(a1, a3);
+    const V jd = INV ? mul_i(d13) : mul_mi(d13);
+    a0 = cadd(s02, s13);
+    a2 = csub(s02, s13);
+    a1 = cadd(d02, jd);
+    a3 = csub(d02, jd);
+}
+template <bool INV, typename V>
+__device__ __forceinline__ void dft4(V* v) {
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+}
+template <bool INV, typename V>
+__device__ __forceinline__ void dft8(V* v) {
+    using S = decltype(v[0].x);
+    const S r = S(0.70710678118654752440);  // 1/sqrt(2)
+    V e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    V o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    // twiddles W8^1, W8^2, W8^3 with W8 = exp(-+ i pi/4)
+    if (INV) {
+        o1 = V{(o1.x - o1.y) * r, (o1.x + o1.y) * r};
+        o2 = mul_i(o2);
+        o3 = V{(-o3.x - o3.y) * r, (o3.x - o3.y) * r};
+    } else {
+        o1 = V{(o1.x + o1.y) * r, (o1.y - o1.x) * r};
+        o2 = mul_mi(o2);
+        o3 = V{(o3.y - o3.x) * r, -(o3.x + o3.y) * r};
+    }
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+}
+
+template <int R, bool INV, typename V>
+__device__ __forceinline__ void dft(V* v) {
+    if constexpr (R == 2) dft2<INV>(v);
+    else if constexpr (R == 3) dft3<INV>(v);
+    else if constexpr (R == 4) dft4<INV>(v);
+    else dft8<INV>(v);
+}
+
+// One Stockham pass of radix R over `nl` independent transforms of length Lx
+// held in shared memory.  Element e of transform l sits at l*ls + e*es.  Ns is
+// the product of the radices already applied.  Output is in natural order
+// after the last pass.  COLS: consecutive threads take consecutive transforms
+// (tiles of columns); otherwise consecutive butterflies of one transform.
+template <int R, bool INV, bool COLS, typename V>
+__device__ __forceinline__ void stockham_pass(const V* __restrict__ src, V* __restrict__ dst,
+                                              const V* __restrict__ tw, int Lx, int Ns, int twmul, int nl,
+                                              int ls, int es) {
+    const int nb = Lx / R;
+    const int total = nb * nl;
+    const int tstep = (Lx / (Ns * R)) * twmul;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        int l, j;
+        if (COLS) {
+            l = t % nl;
+            j = t / nl;
+        } else {
+            j = t % nb;
+            l = t / nb;
+        }
+        const int base = l * ls;
+        V v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[base + (j + r * nb) * es];
+        const int kk = j % Ns;
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                V w = tw[r * kk * tstep];
+                if (INV) w = cconj(w);
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dft<R, INV>(v);
+        const int d0 = (j - kk) * R + kk;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[base + (d0 + r * Ns) * es] = v[r];
+    }
+}
+
+// All passes of one transform length; returns the buffer holding the result.
+template <bool INV, bool COLS, typename V>
+__device__ V* stockham(V* a, V* b, const V* tw, int Lx, const int* rad, int np, int twmul, int nl, int ls,
+                       int es) {
+    int Ns = 1;
+    V* src = a;
+    V* dst = b;
+    for (int p = 0; p < np; ++p) {
+        const int R = rad[p];
+        switch (R) {
+            case 2: stockham_pass<2, INV, COLS>(src, dst, tw, Lx, Ns, twmul, nl, ls, es); break;
+            case 3: stockham_pass<3, INV, COLS>(src, dst, tw, Lx, Ns, twmul, nl, ls, es); break;
+            case 4: stockham_pass<4, INV, COLS>(src, dst, tw, Lx, Ns, twmul, nl, ls, es); break;
+            default: stockham_pass<8, INV, COLS>(src, dst, tw, Lx, Ns, twmul, nl, ls, es); break;
+        }
+        __syncthreads();
+        Ns *= R;
+        V* t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
+template <typename V>
+__device__ __forceinline__ void load_twiddles(V* s_tw, const V* __restrict__ g_tw, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s_tw[i] = g_tw[i];
+}
+
+// ------------------------------------------------------------------ x passes
+
+// Divergence of Q = F_{k+1} - Lambda_k / rho (D^T Q = minus the central
+// divergence) and real-to-complex FFT along x, for `lpb` consecutive x-lines.
+template <typename T, int D>
+__global__ void __launch_bounds__(kFftThreads)
+k_xfwd(const Ctrl* __restrict__ ctrl, const T* F0, const T* F1, const T* __restrict__ Lam, T* U0, T* U1,
+       const typename Cx<T>::t* __restrict__ g_tw, FftPlan plan, int lpb) {
+    using V = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (ctrl->done) return;
+    const int n = plan.n, H = n / 2;
+    const long long Vn = (D == 3) ? (long long)n * n * n : (long long)n * n;
+    const int nlines = (D == 3) ? n * n : n;
+    const int par = (int)(ctrl->k & 1);
+    const T* __restrict__ F = par ? F0 : F1;  // F_{k+1}
+    V* __restrict__ S = reinterpret_cast<V*>(par ? U0 : U1);
+    const T inv_rho = (T)ctrl->inv_rho;
+    const T half_n = (T)(0.5 * n);
+
+    V* s_tw = reinterpret_cast<V*>(smem_raw);
+    V* A = s_tw + n;
+    V* B = A + lpb * H;
+    T* Ar = reinterpret_cast<T*>(A);
+    load_twiddles(s_tw, g_tw, n);
+    const int line0 = blockIdx.x * lpb;
+    const long long sn = n, s2 = sn * sn;
+
+    for (int c = 0; c < D; ++c) {
+        const T* F_c0 = F + (long long)(c * D + 0) * Vn;
+        const T* F_c1 = F + (long long)(c * D + 1) * Vn;
+        const T* L_c0 = Lam + (long long)(c * D + 0) * Vn;
+        const T* L_c1 = Lam + (long long)(c * D + 1) * Vn;
+        for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) {
+            const int l = idx / n;
+            const int x = idx - l * n;
+            const int line = line0 + l;
+            T r = T(0);
+            if (line < nlines) {
+                const int y = line % n;
+                const long long v = (long long)line * n + x;
+                const long long xp = v + (x + 1 == n ? 1 - n : 1), xm = v + (x == 0 ? n - 1 : -1);
+                const long long yp = v + (y + 1 == n ? (1 - n) * sn : sn), ym = v + (y == 0 ? (n - 1) * sn : -sn);
+                T q = (F_c0[xp] - F_c0[xm]) - (L_c0[xp] - L_c0[xm]) * inv_rho;
+                q += (F_c1[yp] - F_c1[ym]) - (L_c1[yp] - L_c1[ym]) * inv_rho;
+                if constexpr (D == 3) {
+                    const int z = line / n;
+                    const T* F_c2 = F + (long long)(c * D + 2) * Vn;
+                    const T* L_c2 = Lam + (long long)(c * D + 2) * Vn;
+                    const long long zp = v + (z + 1 == n ? (1 - n) * s2 : s2);
+                    const long long zm = v + (z == 0 ? (n - 1) * s2 : -s2);
+                    q += (F_c2[zp] - F_c2[zm]) - (L_c2[zp] - L_c2[zm]) * inv_rho;
+                }
+                r = -q * half_n;
+            }
+            Ar[idx] = r;
+        }
+        __syncthreads();
+        V* X = stockham<false, false>(A, B, s_tw, H, plan.rad_half, plan.np_half, 2, lpb, H, 1);
+        V* S_c = S + (long long)c * (Vn / 2);
+        for (int idx = threadIdx.x; idx < lpb * H; idx += blockDim.x) {
+            const int l = idx / H;
+            const int kk = idx - l * H;
+            const int line = line0 + l;
+            if (line >= nlines) continue;
+            const V Zk = X[l * H + kk];
+            V out;
+            if (kk == 0) {
+                out = V{Zk.x + Zk.y, Zk.x - Zk.y};  // (X_0, X_{N/2}) packed
+            } else {
+                const V Zc = cconj(X[l * H + (H - kk)]);
+                const V E = cscale(cadd(Zk, Zc), T(0.5));
+                const V O = cscale(mul_mi(csub(Zk, Zc)), T(0.5));
+                out = cadd(E, cmul(s_tw[kk], O));
+            }
+            S_c[(long long)line * H + kk] = out;
+        }
+        __syncthreads();
+    }
+}
+
+// Complex-to-real inverse FFT along x, in place: spectrum lines -> u~_{k+1}.
+template <typename T, int D>
+__global__ void __launch_bounds__(kFftThreads)
+k_xinv(const Ctrl* __restrict__ ctrl, T* U0, T* U1, const typename Cx<T>::t* __restrict__ g_tw, FftPlan plan,
+       int lpb) {
+    using V = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (ctrl->done) return;
+    const int n = plan.n, H = n / 2;
+    const long long Vn = (D == 3) ? (long long)n * n * n : (long long)n * n;
+    const int nlines = (D == 3) ? n * n : n;
+    const int par = (int)(ctrl->k & 1);
+    T* Ur = par ? U0 : U1;
+    V* S = reinterpret_cast<V*>(Ur);
+    V* s_tw = reinterpret_cast<V*>(smem_raw);
+    V* A = s_tw + n;
+    V* B = A + lpb * H;
+    load_twiddles(s_tw, g_tw, n);
+    __syncthreads();
+    const int line0 = blockIdx.x * lpb;
+    for (int c = 0; c < D; ++c) {
+        V* S_c = S + (long long)c * (Vn / 2);
+        for (int idx = threadIdx.x; idx < lpb * H; idx += blockDim.x) {
+            const int l = idx / H;
+            const int kk = idx - l * H;
+            const int line = line0 + l;
+            V Z = V{T(0), T(0)};
+            if (line < nlines) {
+                const V Xk = S_c[(long long)line * H + kk];
+                if (kk == 0) {
+                    Z = V{T(0.5) * (Xk.x + Xk.y), T(0.5) * (Xk.x - Xk.y)};
+                } else {
+                    const V Xc = cconj(S_c[(long long)line * H + (H - kk)]);
+                    const V E = cscale(cadd(Xk, Xc), T(0.5));
+                    const V O = cmul(cscale(csub(Xk, Xc), T(0.5)), cconj(s_tw[kk]));
+                    Z = cadd(E, mul_i(O));
+                }
+            }
+            A[idx] = Z;
+        }
+        __syncthreads();
+        V* X = stockham<true, false>(A, B, s_tw, H, plan.rad_half, plan.np_half, 2, lpb, H, 1);
+        const T* Xr = reinterpret_cast<const T*>(X);
+        T* U_c = Ur + (long long)c * Vn;
+        for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) {
+            const int l = idx / n;
+            const int line = line0 + l;
+            if (line < nlines) U_c[(long long)line * n + (idx - l * n)] = Xr[idx];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ y / z passes
+
+// FFT along AXIS (1 = y, 2 = z) of tiles of `tk` adjacent x-frequency columns.
+// MODE 0: forward; 1: inverse; 2: forward, multiply by scale/|k|^2, inverse.
+template <typename T, int D, int AXIS, int MODE>
+__global__ void __launch_bounds__(kFftThreads)
+k_faxis(const Ctrl* __restrict__ ctrl, T* U0, T* U1, const typename Cx<T>::t* __restrict__ g_tw,
+        const T* __restrict__ ksq, FftPlan plan, int tk, T scale) {
+    using V = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (ctrl->done) return;
+    const int n = plan.n, H = n / 2;
+    const long long Vn = (D == 3) ? (long long)n * n * n : (long long)n * n;
+    const int par = (int)(ctrl->k & 1);
+    V* S = reinterpret_cast<V*>(par ? U0 : U1);
+    V* s_tw = reinterpret_cast<V*>(smem_raw);
+    V* X = s_tw + n;
+    V* Y = X + n * tk;
+    load_twiddles(s_tw, g_tw, n);
+
+    const int col0 = blockIdx.x * tk;
+    const int outer = blockIdx.y;
+    const int c = blockIdx.z;
+    long long base, es_g;
+    if (D == 3 && AXIS == 1) {
+        base = (long long)c * (Vn / 2) + (long long)outer * n * H + col0;
+        es_g = H;
+    } else if (D == 3 && AXIS == 2) {
+        base = (long long)c * (Vn / 2) + (long long)outer * H + col0;
+        es_g = (long long)n * H;
+    } else {
+        base = (long long)c * (Vn / 2) + col0;
+        es_g = H;
+    }
+    for (int idx = threadIdx.x; idx < n * tk; idx += blockDim.x) {
+        const int e = idx / tk;
+        const int cl = idx - e * tk;
+        X[idx] = (col0 + cl < H) ? S[base + e * es_g + cl] : V{T(0), T(0)};
+    }
+    __syncthreads();
+    V* R;
+    if (MODE == 1) {
+        R = stockham<true, true>(X, Y, s_tw, n, plan.rad_full, plan.np_full, 1, tk, 1, tk);
+    } else {
+        R = stockham<false, true>(X, Y, s_tw, n, plan.rad_full, plan.np_full, 1, tk, 1, tk);
+        if (MODE == 2) {
+            const T kout = (D == 3) ? __ldg(ksq + outer) : T(0);
+            for (int idx = threadIdx.x; idx < n * tk; idx += blockDim.x) {
+                const int e = idx / tk;
+                const int col = col0 + idx - e * tk;
+                const T den = __ldg(ksq + e) + __ldg(ksq + min(col, H - 1)) + kout;
+                const T m = den > T(0) ? scale / den : T(0);
+                R[idx] = cscale(R[idx], m);
+            }
+            __syncthreads();
+            V* other = (R == X) ? Y : X;
+            R = stockham<true, true>(R, other, s_tw, n, plan.rad_full, plan.np_full, 1, tk, 1, tk);
+        }
+    }
+    for (int idx = threadIdx.x; idx < n * tk; idx += blockDim.x) {
+        const int e = idx / tk;
+        const int cl = idx - e * tk;
+        if (col0 + cl < H) S[base + e * es_g + cl] = R[idx];
+    }
+}
+
+// ------------------------------------------------------------------ launch
+
+template <typename T>
+struct FftArgs;
+template <>
+struct FftArgs<double> {
+    static double* U(const Launch& L, int i) { return L.U64[i]; }
+    static const double* F(const Launch& L, int i) { return L.F64[i]; }
+    static const double* Lm(const Launch& L) { return L.L64; }
+    static const double2* tw(const Launch& L) { return L.tw64; }
+    static const double* ksq(const Launch& L) { return L.ksq64; }
+    static constexpr int tk = 8;
+};
+template <>
+struct FftArgs<float> {
+    static float* U(const Launch& L, int i) { return L.U32[i]; }
+    static const float* F(const Launch& L, int i) { return L.F32[i]; }
+    static const float* Lm(const Launch& L) { return L.L32; }
+    static const float2* tw(const Launch& L) { return L.tw32; }
+    static const float* ksq(const Launch& L) { return L.ksq32; }
+    static constexpr int tk = 16;
+};
+
+inline int lines_per_block(int n, int nlines) {
+    int lpb = 2048 / n;
+    if (lpb < 1) lpb = 1;
+    if (lpb > nlines) lpb = nlines;
+    return lpb;
+}
+
+// stage < 0: all passes of one iteration; otherwise only pass `stage`
+// (3D: 0 x-forward, 1 y-forward, 2 z solve, 3 y-inverse, 4 x-inverse;
+//  2D: 0 x-forward, 1 y solve, 2 x-inverse).
+template <typename T, int D>
+cudaError_t run_fft(const Launch& L, int stage) {
+    using V = typename Cx<T>::t;
+    using A = FftArgs<T>;
+    const int n = L.n, H = n / 2;
+    const int nlines = (D == 3) ? n * n : n;
+    const int lpb = lines_per_block(n, nlines);
+    const int gx = (nlines + lpb - 1) / lpb;
+    const size_t smx = (size_t)n * sizeof(V) + 2 * (size_t)lpb * H * sizeof(V);
+    const int tk = A::tk < H ? A::tk : H;
+    const size_t sma = (size_t)n * sizeof(V) + 2 * (size_t)n * tk * sizeof(V);
+    const dim3 ga((H + tk - 1) / tk, D == 3 ? n : 1, D);
+    const T scale = (T)(2.0 / (double)L.V);
+    const int last = D == 3 ? 4 : 2;
+    auto want = [&](int s) { return stage < 0 || stage == s; };
+    if (want(0))
+        k_xfwd<T, D><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, A::F(L, 0), A::F(L, 1), A::Lm(L), A::U(L, 0),
+                                                         A::U(L, 1), A::tw(L), L.plan, lpb);
+    if (D == 3) {
+        if (want(1))
+            k_faxis<T, D, 1, 0><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::tw(L),
+                                                                    A::ksq(L), L.plan, tk, scale);
+        if (want(2))
+            k_faxis<T, D, 2, 2><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::tw(L),
+                                                                    A::ksq(L), L.plan, tk, scale);
+        if (want(3))
+            k_faxis<T, D, 1, 1><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::tw(L),
+                                                                    A::ksq(L), L.plan, tk, scale);
+    } else if (want(1)) {
+        k_faxis<T, D, 1, 2><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::tw(L),
+                                                                A::ksq(L), L.plan, tk, scale);
+    }
+    if (want(last))
+        k_xinv<T, D><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::tw(L), L.plan, lpb);
+    return cudaGetLastError();
+}
+
+template <typename T, int D>
+cudaError_t set_smem_attrs(int bytes) {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (r != cudaSuccess) e = r;
+    };
+    set((const void*)k_xfwd<T, D>);
+    set((const void*)k_xinv<T, D>);
+    set((const void*)k_faxis<T, D, 1, 0>);
+    set((const void*)k_faxis<T, D, 1, 1>);
+    set((const void*)k_faxis<T, D, 1, 2>);
+    set((const void*)k_faxis<T, D, 2, 2>);
+    return e;
+}
+
+}  // namespace
+
+cudaError_t launch_fft(const Launch& L, bool fp64, int stage) {
+    if (fp64) return L.dim == 3 ? run_fft<double, 3>(L, stage) : run_fft<double, 2>(L, stage);
+    return L.dim == 3 ? run_fft<float, 3>(L, stage) : run_fft<float, 2>(L, stage);
+}
+
+// Allow the FFT kernels the dynamic shared memory the largest grid needs.
+cudaError_t prepare_fft_kernels(int n) {
+    (void)n;
+    const int bytes = 200 * 1024;
+    cudaError_t e;
+    if ((e = set_smem_attrs<double, 2>(bytes)) != cudaSuccess) return e;
+    if ((e = set_smem_attrs<double, 3>(bytes)) != cudaSuccess) return e;
+    if ((e = set_smem_attrs<float, 2>(bytes)) != cudaSuccess) return e;
+    return set_smem_attrs<float, 3>(bytes);
+}
+
+}  // namespace admm

@@ -1,0 +1,98 @@
+// Internal definitions shared by the solver's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace admm {
+
+constexpr int kMaxPasses = 16;
+constexpr int kLocalThreads = 128;    // threads per block of the local-step kernels
+constexpr int kFftThreads = 256;      // threads per block of the FFT kernels
+constexpr int kMaxParam = 8;          // per-phase material constants
+constexpr int kPartialStride = 20;    // doubles per block in the partial-sum buffer
+
+enum Done : int { kRunning = 0, kConverged = 1, kCapped = 2, kNumerical = 3, kSwitch = 4 };
+enum Model : int { kNeoHooke = 0, kLinear = 1, kLce = 2 };
+
+// Per-RVE control block in device memory.  Every kernel reads it at entry (the
+// ping-pong parity, the penalty, the stop flag); only the last block of the
+// fused local kernel and the host write it.  Field order is part of the
+// host/device contract within this library only.
+struct Ctrl {
+    double Fbar[9];      // macroscopic gradient (row-major, 3x3; d x d block used)
+    double rho;          // penalty of the current iteration
+    double inv_rho;
+    double mu_ref;       // modulus in r_d
+    double tol;
+    double rho_kappa, rho_tau, rho_min;
+    double switch_tol;   // float phase of mixed mode: promote once max(r_p, r_d) <= this
+    double best;         // best max(r_p, r_d) of the float phase (stagnation test)
+    double r_p, r_d;     // residuals of the last completed iteration
+    double stress[9];    // <W_F(F)> of the current state (written by the stress kernel)
+    double lam_mean[9];  // <Lambda>
+    long long k;         // iterations completed over the handle's life: F_k, u~_k live in buffer k & 1
+    long long k_start;   // value of k when the running solve began
+    long long k_cap;     // solve stops when k reaches this
+    int done;            // enum Done
+    int adaptive;        // eq. rho-update on
+    int phase_fp32;      // 1 while a float phase of RVE_MIXED runs (switch rules on)
+    int stall;           // float-phase iterations without a 10 % improvement of best
+    int rho_changed;     // last iteration changed rho: the speculative local step is redone
+    int newton_cap;
+    double newton_tol;
+    int newton_max;      // largest per-voxel Newton count of the last fused pass
+    int hist_cap;        // capacity of the residual history (entries)
+    unsigned long long newton_fail;
+    unsigned int counter; // last-block counter of the fused local kernel
+    unsigned int counter2;// last-block counter of the stress kernel
+};
+
+// Stockham plan for one grid size: radix sequences for the half-length x
+// transform (N/2) and the full-length y/z transforms (N).
+struct FftPlan {
+    int n;
+    int np_half, np_full;
+    int rad_half[kMaxPasses];
+    int rad_full[kMaxPasses];
+};
+
+// Everything a launch needs.  Pointers of the precision not in use may be null.
+struct Launch {
+    cudaStream_t stream;
+    int dim, n, model;
+    long long V;
+    int local_blocks;
+    Ctrl* ctrl;
+    double* hist;          // 3 doubles per iteration: r_p, r_d, rho
+    double* partials;      // kPartialStride doubles per local block
+    const uint8_t* phase;
+    const double* mat;     // per-phase constants, nparam each
+    int nparam;
+    const double* n0;      // LCE reference directors (3 x V) or null
+    // double precision state
+    double* F64[2];
+    double* L64;
+    double* U64[2];
+    const double2* tw64;   // exp(-2 pi i m / N), m < N
+    const double* ksq64;   // (N sin(2 pi m / N))^2, exact 0 at m = 0, N/2
+    // single precision state
+    float* F32[2];
+    float* L32;
+    float* U32[2];
+    const float2* tw32;
+    const float* ksq32;
+    FftPlan plan;
+};
+
+// rve_local.cu
+cudaError_t launch_init(const Launch& L, bool fp64, bool lambda_zero);
+cudaError_t launch_local(const Launch& L, bool fp64, bool first, bool only_if_rho_changed);
+cudaError_t launch_stress(const Launch& L, bool fp64);
+cudaError_t launch_convert(const Launch& L, bool to_fp64);
+// rve_fft.cu
+cudaError_t launch_fft(const Launch& L, bool fp64, int stage = -1);
+inline int fft_stages(int dim) { return dim == 3 ? 5 : 3; }
+cudaError_t prepare_fft_kernels(int n);
+
+}  // namespace admm

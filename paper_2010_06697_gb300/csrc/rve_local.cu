@@ -1,0 +1,780 @@
+// Local (pointwise) kernels of the ADMM iteration, Zhou & Bhattacharya Section 2.1:
+//   Step 1 (eq. eq)      F_{i+1} = argmin_F W(F;x) - Lambda_i : F + rho/2 |F - G_i|^2
+//   Step 3 (eq. update)  Lambda_{i+1} = Lambda_i + rho (G_{i+1} - F_{i+1})
+//   Step 4 (eq. check)   r_p = ||G_{i+1} - F_{i+1}||,  r_d = rho/mu ||G_{i+1} - G_i||
+// with G = Fbar + D u~ and D the central-difference gradient of Section 2.3.
+//
+// One fused kernel per iteration finishes Steps 3-4 of iteration i and runs Step 1
+// of iteration i+1 at each voxel, so F, Lambda and u~ are read once and F, Lambda
+// written once per iteration.  One thread owns one voxel; the 3x3 (2x2) algebra,
+// the 9x9 (4x4) Newton Hessian and its Cholesky factor live in registers.
+// Residual sums are accumulated in double whatever the field precision, reduced
+// per block with warp shuffles and finished by the last block in a fixed order,
+// so the result does not depend on block scheduling.
+#include <math.h>
+#include <stdint.h>
+
+#include "rve_internal.cuh"
+
+namespace admm {
+namespace {
+
+// ------------------------------------------------------------------ small dense algebra
+
+template <typename T, int D>
+__device__ __forceinline__ T det_cof(const T* F, T* K) {
+    if constexpr (D == 2) {
+        K[0] = F[3];
+        K[1] = -F[2];
+        K[2] = -F[1];
+        K[3] = F[0];
+        return F[0] * F[3] - F[1] * F[2];
+    } else {
+        K[0] = F[4] * F[8] - F[5] * F[7];
+        K[1] = F[5] * F[6] - F[3] * F[8];
+        K[2] = F[3] * F[7] - F[4] * F[6];
+        K[3] = F[2] * F[7] - F[1] * F[8];
+        K[4] = F[0] * F[8] - F[2] * F[6];
+        K[5] = F[1] * F[6] - F[0] * F[7];
+        K[6] = F[1] * F[5] - F[2] * F[4];
+        K[7] = F[2] * F[3] - F[0] * F[5];
+        K[8] = F[0] * F[4] - F[1] * F[3];
+        return F[0] * K[0] + F[1] * K[1] + F[2] * K[2];
+    }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ T det(const T* F) {
+    if constexpr (D == 2) {
+        return F[0] * F[3] - F[1] * F[2];
+    } else {
+        return F[0] * (F[4] * F[8] - F[5] * F[7]) + F[1] * (F[5] * F[6] - F[3] * F[8]) +
+               F[2] * (F[3] * F[7] - F[4] * F[6]);
+    }
+}
+
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float log_t(float x) { return logf(x); }
+__device__ __forceinline__ double log_t(double x) { return log(x); }
+
+// Solve H x = -g for symmetric positive definite H given in packed lower storage
+// (row p, column q <= p at p(p+1)/2 + q).  H is overwritten by its Cholesky
+// factor.  Returns false when a pivot is not positive.
+template <typename T, int N>
+__device__ __forceinline__ bool chol_solve(T* H, const T* g, T* x) {
+    T inv[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+#pragma unroll
+        for (int q = 0; q <= p; ++q) {
+            T s = H[p * (p + 1) / 2 + q];
+#pragma unroll
+            for (int r = 0; r < q; ++r) s -= H[p * (p + 1) / 2 + r] * H[q * (q + 1) / 2 + r];
+            if (p == q) {
+                if (!(s > T(0))) return false;
+                const T is = rsqrt_t(s);
+                inv[p] = is;
+                H[p * (p + 1) / 2 + p] = s * is;
+            } else {
+                H[p * (p + 1) / 2 + q] = s * inv[q];
+            }
+        }
+    }
+    T y[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        T s = -g[p];
+#pragma unroll
+        for (int r = 0; r < p; ++r) s -= H[p * (p + 1) / 2 + r] * y[r];
+        y[p] = s * inv[p];
+    }
+#pragma unroll
+    for (int p = N - 1; p >= 0; --p) {
+        T s = y[p];
+#pragma unroll
+        for (int r = p + 1; r < N; ++r) s -= H[r * (r + 1) / 2 + p] * x[r];
+        x[p] = s * inv[p];
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------ constitutive laws
+// Each law gives, for the local objective phi(F) = W(F) + rho/2 |F|^2 - B : F
+// (B = Lambda + rho G; the constant rho/2 |G|^2 is dropped):
+//   grad_hess: g = W_F(F) + rho F - B and the packed Hessian W_FF + rho I
+//   phi:       the objective (line search)
+//   stress:    W_F(F)
+
+// Compressible neo-Hookean, Section 4.1: W = mu/2 (|F|^2 - d - 2 ln J) + lam/2 (J-1)^2.
+// W_F = mu F + c F^{-T}, c = lam J (J-1) - mu;
+// W_FF[ij,kl] = mu d_ik d_jl + lam (2J-1) J A_ij A_kl - c A_il A_kj, A = F^{-T}.
+template <typename T, int D>
+struct NeoHooke {
+    T mu, lam;
+    __device__ __forceinline__ bool grad_hess(const T* F, const T* B, T rho, T* g, T* H) const {
+        constexpr int NN = D * D;
+        T A[NN];
+        const T J = det_cof<T, D>(F, A);
+        if (!(J > T(0))) return false;
+        const T iJ = T(1) / J;
+#pragma unroll
+        for (int p = 0; p < NN; ++p) A[p] *= iJ;
+        const T c = lam * J * (J - T(1)) - mu;
+        const T b = lam * (T(2) * J - T(1)) * J;
+        const T a = mu + rho;
+#pragma unroll
+        for (int p = 0; p < NN; ++p) g[p] = a * F[p] + c * A[p] - B[p];
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            const int i = p / D, j = p % D;
+#pragma unroll
+            for (int q = 0; q <= p; ++q) {
+                const int k = q / D, l = q % D;
+                T h = b * A[p] * A[q] - c * A[i * D + l] * A[k * D + j];
+                if (p == q) h += a;
+                H[p * (p + 1) / 2 + q] = h;
+            }
+        }
+        return true;
+    }
+    __device__ __forceinline__ T phi(const T* F, const T* B, T rho, T J) const {
+        T ff = 0, bf = 0;
+#pragma unroll
+        for (int p = 0; p < D * D; ++p) {
+            ff += F[p] * F[p];
+            bf += B[p] * F[p];
+        }
+        return T(0.5) * mu * (ff - T(2) * log_t(J)) + T(0.5) * lam * (J - T(1)) * (J - T(1)) +
+               T(0.5) * rho * ff - bf;
+    }
+    __device__ __forceinline__ void stress(const T* F, T* P) const {
+        T A[D * D];
+        const T J = det_cof<T, D>(F, A);
+        const T c = (lam * J * (J - T(1)) - mu) / J;
+#pragma unroll
+        for (int p = 0; p < D * D; ++p) P[p] = mu * F[p] + c * A[p];
+    }
+    __device__ __forceinline__ T modulus() const { return mu; }
+};
+
+// Isotropic linear elasticity in H = F - I: W = mu |sym H|^2 + lam/2 (tr H)^2.
+template <typename T, int D>
+struct Linear {
+    T mu, lam;
+    __device__ __forceinline__ bool grad_hess(const T* F, const T* B, T rho, T* g, T* H) const {
+        T tr = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) tr += F[i * D + i] - T(1);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const T hij = F[i * D + j] - (i == j ? T(1) : T(0));
+                const T hji = F[j * D + i] - (i == j ? T(1) : T(0));
+                g[i * D + j] = mu * (hij + hji) + (i == j ? lam * tr : T(0)) + rho * F[i * D + j] - B[i * D + j];
+            }
+#pragma unroll
+        for (int p = 0; p < D * D; ++p) {
+            const int i = p / D, j = p % D;
+#pragma unroll
+            for (int q = 0; q <= p; ++q) {
+                const int k = q / D, l = q % D;
+                T h = mu * (T(i == k && j == l) + T(i == l && j == k)) + lam * T(i == j && k == l);
+                if (p == q) h += rho;
+                H[p * (p + 1) / 2 + q] = h;
+            }
+        }
+        return true;
+    }
+    __device__ __forceinline__ T phi(const T* F, const T* B, T rho, T /*J*/) const {
+        T e2 = 0, tr = 0, ff = 0, bf = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            tr += F[i * D + i] - T(1);
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const T e = T(0.5) * (F[i * D + j] + F[j * D + i]) - (i == j ? T(1) : T(0));
+                e2 += e * e;
+                ff += F[i * D + j] * F[i * D + j];
+                bf += B[i * D + j] * F[i * D + j];
+            }
+        }
+        return mu * e2 + T(0.5) * lam * tr * tr + T(0.5) * rho * ff - bf;
+    }
+    __device__ __forceinline__ void stress(const T* F, T* P) const {
+        T tr = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) tr += F[i * D + i] - T(1);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+                P[i * D + j] = mu * (F[i * D + j] + F[j * D + i] - T(2) * T(i == j)) + (i == j ? lam * tr : T(0));
+    }
+    __device__ __forceinline__ T modulus() const { return mu; }
+};
+
+template <typename T, int D, int MODEL>
+struct LawOf;
+template <typename T, int D>
+struct LawOf<T, D, kNeoHooke> { using type = NeoHooke<T, D>; };
+template <typename T, int D>
+struct LawOf<T, D, kLinear> { using type = Linear<T, D>; };
+
+template <typename Law, typename T>
+__device__ __forceinline__ Law load_law(const uint8_t* phase, const double* mat, int nparam, long long v) {
+    const int ph = phase[v];
+    Law m;
+    m.mu = (T)__ldg(mat + ph * nparam + 0);
+    m.lam = (T)__ldg(mat + ph * nparam + 1);
+    return m;
+}
+
+template <typename T>
+struct NewtonConst;
+template <>
+struct NewtonConst<double> { static constexpr double big = 1e-2; };
+template <>
+struct NewtonConst<float> { static constexpr float big = 1e-2f; };
+
+// Damped Newton for phi at one voxel, starting from F (overwritten).  Steps
+// larger than NewtonConst::big take an Armijo backtracking line search on phi;
+// every step keeps J = det F > 0.  Stops after a full step with max|dF| <= tol.
+// Returns the number of Newton steps; conv tells whether the test was met.
+template <typename T, int D, typename Law>
+__device__ __forceinline__ int newton(const Law& m, T* F, const T* B, T rho, int cap, T tol, bool& conv) {
+    constexpr int NN = D * D;
+    constexpr int NP = NN * (NN + 1) / 2;
+    conv = false;
+    int it = 0;
+    while (it < cap) {
+        T g[NN], H[NP], dx[NN];
+        if (!m.grad_hess(F, B, rho, g, H)) break;
+        if (!chol_solve<T, NN>(H, g, dx)) {
+            const T s = T(1) / (m.modulus() + rho);
+#pragma unroll
+            for (int p = 0; p < NN; ++p) dx[p] = -g[p] * s;
+        }
+        T slope = 0, size = 0;
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            slope += g[p] * dx[p];
+            size = fmax(size, fabs(dx[p]));
+        }
+        if (!(slope < T(0))) {  // not a descent direction: steepest descent (Section 2.1's local method)
+            const T s = T(1) / (m.modulus() + rho);
+            slope = 0;
+            size = 0;
+#pragma unroll
+            for (int p = 0; p < NN; ++p) {
+                dx[p] = -g[p] * s;
+                slope += g[p] * dx[p];
+                size = fmax(size, fabs(dx[p]));
+            }
+        }
+        if (!(size < T(1e30))) break;  // NaN or overflow
+        T t = T(1);
+        T Ft[NN];
+        if (size > NewtonConst<T>::big) {
+            const T phi0 = m.phi(F, B, rho, det<T, D>(F));
+            int ls = 0;
+            for (; ls < 40; ++ls) {
+#pragma unroll
+                for (int p = 0; p < NN; ++p) Ft[p] = F[p] + t * dx[p];
+                const T Jt = det<T, D>(Ft);
+                if (Jt > T(0) && m.phi(Ft, B, rho, Jt) <= phi0 + T(1e-4) * t * slope) break;
+                t *= T(0.5);
+            }
+            if (ls == 40) t = T(0);
+        } else {
+            int ls = 0;
+            for (; ls < 40; ++ls) {
+#pragma unroll
+                for (int p = 0; p < NN; ++p) Ft[p] = F[p] + t * dx[p];
+                if (det<T, D>(Ft) > T(0)) break;
+                t *= T(0.5);
+            }
+            if (ls == 40) t = T(0);
+        }
+#pragma unroll
+        for (int p = 0; p < NN; ++p) F[p] += t * dx[p];
+        ++it;
+        if (t == T(1) && size <= tol) {
+            conv = true;
+            break;
+        }
+        if (t == T(0)) break;
+    }
+    return it;
+}
+
+// ------------------------------------------------------------------ grid helpers
+
+template <int D>
+struct Nbr {
+    long long xp, xm, yp, ym, zp, zm;
+};
+
+template <int D>
+__device__ __forceinline__ Nbr<D> neighbours(long long v, int n) {
+    Nbr<D> o;
+    const int x = (int)(v % n);
+    const long long r = v / n;
+    const int y = (int)(r % n);
+    o.xp = v + (x + 1 == n ? 1 - n : 1);
+    o.xm = v + (x == 0 ? n - 1 : -1);
+    const long long sn = n;
+    o.yp = v + (y + 1 == n ? (1 - n) * sn : sn);
+    o.ym = v + (y == 0 ? (n - 1) * sn : -sn);
+    if constexpr (D == 3) {
+        const int z = (int)(r / n);
+        const long long s2 = sn * sn;
+        o.zp = v + (z + 1 == n ? (1 - n) * s2 : s2);
+        o.zm = v + (z == 0 ? (n - 1) * s2 : -s2);
+    } else {
+        o.zp = o.zm = v;
+    }
+    return o;
+}
+
+// G_ij = Fbar_ij + (u_i(x + h e_j) - u_i(x - h e_j)) / (2h), h = 1/n.
+template <typename T, int D>
+__device__ __forceinline__ void grad_u(const T* __restrict__ U, long long V, const Nbr<D>& nb, const T* Fb,
+                                       T half_n, T* G) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const T* u = U + i * V;
+        G[i * D + 0] = Fb[i * D + 0] + (__ldg(u + nb.xp) - __ldg(u + nb.xm)) * half_n;
+        G[i * D + 1] = Fb[i * D + 1] + (__ldg(u + nb.yp) - __ldg(u + nb.ym)) * half_n;
+        if constexpr (D == 3) G[i * D + 2] = Fb[i * D + 2] + (__ldg(u + nb.zp) - __ldg(u + nb.zm)) * half_n;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// ------------------------------------------------------------------ kernels
+
+// Fresh state: F_k = Fbar, u~_k = 0, Lambda = W_F(Fbar; x) (or 0).
+template <typename T, int D, int MODEL>
+__global__ void __launch_bounds__(kLocalThreads)
+k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const uint8_t* __restrict__ phase,
+       const double* __restrict__ mat, int nparam, long long V, int lambda_zero) {
+    using Law = typename LawOf<T, D, MODEL>::type;
+    const int par = (int)(ctrl->k & 1);
+    T* F = par ? F1 : F0;
+    T* U = par ? U1 : U0;
+    T Fb[D * D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) Fb[i * D + j] = (T)ctrl->Fbar[i * 3 + j];
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        T P[D * D];
+        if (lambda_zero) {
+#pragma unroll
+            for (int p = 0; p < D * D; ++p) P[p] = T(0);
+        } else {
+            const Law m = load_law<Law, T>(phase, mat, nparam, v);
+            m.stress(Fb, P);
+        }
+#pragma unroll
+        for (int p = 0; p < D * D; ++p) {
+            F[p * V + v] = Fb[p];
+            Lam[p * V + v] = P[p];
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) U[i * V + v] = T(0);
+    }
+}
+
+// The fused per-iteration kernel.  With FIRST = false, at iteration index k
+// (k iterations done): reads u~_{k+1}, u~_k, F_{k+1}, Lambda_k; writes
+// Lambda_{k+1} (Step 3), accumulates r_p, r_d of iteration k (Step 4) and runs
+// Step 1 of iteration k+1 into F_{k+2}; the last block finishes the residuals,
+// advances k and sets the stop flag.  With FIRST = true only Step 1 runs
+// (F_{k+1} from F_k, Lambda_k, u~_k): at the start of a solve, after a precision
+// switch, and (only_if_rho_changed) to redo the speculative step when the
+// adaptive rule changed rho.
+template <typename T, int D, int MODEL, bool FIRST>
+__global__ void __launch_bounds__(kLocalThreads)
+k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__ partials, T* F0, T* F1, T* Lam,
+        const T* U0, const T* U1, const uint8_t* __restrict__ phase, const double* __restrict__ mat, int nparam,
+        int n, long long V, int only_if_rho_changed) {
+    using Law = typename LawOf<T, D, MODEL>::type;
+    constexpr int NN = D * D;
+    __shared__ double s_sum[kLocalThreads / 32][2];
+    __shared__ int s_int[kLocalThreads / 32][2];
+    __shared__ int s_last;
+
+    if (ctrl->done) return;
+    if (FIRST && only_if_rho_changed && !ctrl->rho_changed) return;
+    const long long k = ctrl->k;
+    const int par = (int)(k & 1);
+    T *Fcur, *Fnext;
+    const T *Unew, *Uold;
+    if (FIRST) {
+        Fcur = par ? F1 : F0;
+        Fnext = par ? F0 : F1;
+        Unew = par ? U1 : U0;
+        Uold = nullptr;
+    } else {
+        Fcur = par ? F0 : F1;
+        Fnext = par ? F1 : F0;
+        Unew = par ? U0 : U1;
+        Uold = par ? U1 : U0;
+    }
+    const T rho = (T)ctrl->rho;
+    const T half_n = (T)(0.5 * n);
+    const int cap = ctrl->newton_cap;
+    const T ntol = (T)ctrl->newton_tol;
+    T Fb[NN];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) Fb[i * D + j] = (T)ctrl->Fbar[i * 3 + j];
+
+    double rp2 = 0.0, rd2 = 0.0;
+    int nmax = 0, nfail = 0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        const Nbr<D> nb = neighbours<D>(v, n);
+        T G[NN], L[NN], F[NN];
+        grad_u<T, D>(Unew, V, nb, Fb, half_n, G);
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            L[p] = Lam[p * V + v];
+            F[p] = Fcur[p * V + v];
+        }
+        if (!FIRST) {
+            T Go[NN];
+            grad_u<T, D>(Uold, V, nb, Fb, half_n, Go);
+#pragma unroll
+            for (int p = 0; p < NN; ++p) {
+                const T df = G[p] - F[p];
+                const T dg = G[p] - Go[p];
+                L[p] += rho * df;
+                rp2 += (double)df * (double)df;
+                rd2 += (double)dg * (double)dg;
+                Lam[p * V + v] = L[p];
+            }
+        }
+        const Law m = load_law<Law, T>(phase, mat, nparam, v);
+        T B[NN];
+#pragma unroll
+        for (int p = 0; p < NN; ++p) B[p] = L[p] + rho * G[p];
+        bool conv;
+        const int it = newton<T, D>(m, F, B, rho, cap, ntol, conv);
+        nmax = max(nmax, it);
+        nfail += conv ? 0 : 1;
+#pragma unroll
+        for (int p = 0; p < NN; ++p) Fnext[p * V + v] = F[p];
+    }
+    if (FIRST) return;
+
+    // block partials: r_p^2, r_d^2 sums (double), Newton max / failures
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    rp2 = warp_sum(rp2);
+    rd2 = warp_sum(rd2);
+    nmax = warp_max(nmax);
+    for (int o = 16; o > 0; o >>= 1) nfail += __shfl_down_sync(0xffffffffu, nfail, o);
+    if (lane == 0) {
+        s_sum[warp][0] = rp2;
+        s_sum[warp][1] = rd2;
+        s_int[warp][0] = nmax;
+        s_int[warp][1] = nfail;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        int mx = 0, nf = 0;
+        for (int w = 0; w < kLocalThreads / 32; ++w) {
+            a += s_sum[w][0];
+            b += s_sum[w][1];
+            mx = max(mx, s_int[w][0]);
+            nf += s_int[w][1];
+        }
+        double* pp = partials + (size_t)blockIdx.x * kPartialStride;
+        pp[0] = a;
+        pp[1] = b;
+        pp[2] = (double)mx;
+        pp[3] = (double)nf;
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctrl->counter, 1u);
+        s_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+
+    // last block: fixed-order sum over all block partials
+    double a = 0, b = 0;
+    int mx = 0;
+    double nf = 0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        const double* pp = partials + (size_t)i * kPartialStride;
+        a += __ldcg(pp + 0);
+        b += __ldcg(pp + 1);
+        mx = max(mx, (int)__ldcg(pp + 2));
+        nf += __ldcg(pp + 3);
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    nf = warp_sum(nf);
+    mx = warp_max(mx);
+    if (lane == 0) {
+        s_sum[warp][0] = a;
+        s_sum[warp][1] = b;
+        s_int[warp][0] = mx;
+        s_int[warp][1] = (int)nf;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    a = 0;
+    b = 0;
+    mx = 0;
+    long long nft = 0;
+    for (int w = 0; w < kLocalThreads / 32; ++w) {
+        a += s_sum[w][0];
+        b += s_sum[w][1];
+        mx = max(mx, s_int[w][0]);
+        nft += s_int[w][1];
+    }
+    Ctrl* c = ctrl;
+    const double rhod = c->rho;
+    const double r_p = sqrt(a / (double)V);
+    const double r_d = rhod / c->mu_ref * sqrt(b / (double)V);
+    const long long idx = k - c->k_start;
+    if (idx >= 0 && idx < c->hist_cap) {
+        hist[3 * idx + 0] = r_p;
+        hist[3 * idx + 1] = r_d;
+        hist[3 * idx + 2] = rhod;
+    }
+    c->r_p = r_p;
+    c->r_d = r_d;
+    c->k = k + 1;
+    c->newton_max = mx;
+    c->newton_fail = (unsigned long long)nft;
+    int done = kRunning;
+    if (!(isfinite(r_p) && isfinite(r_d))) {
+        done = kNumerical;
+    } else if (r_p <= c->tol && r_d <= c->tol) {
+        done = kConverged;
+    } else if (k + 1 >= c->k_cap) {
+        done = kCapped;
+    } else if (c->phase_fp32) {
+        const double mres = fmax(r_p, r_d);
+        if (mres <= c->switch_tol) {
+            done = kSwitch;
+        } else if (mres < 0.9 * c->best) {
+            c->best = mres;
+            c->stall = 0;
+        } else if (++c->stall >= 10) {
+            done = kSwitch;
+        }
+    }
+    c->rho_changed = 0;
+    if (done == kRunning && c->adaptive) {  // eq. rho-update (He, Yang & Wang)
+        double nr = rhod;
+        if (r_d > 0.0 && r_p / r_d > c->rho_tau)
+            nr = c->rho_kappa * rhod;
+        else if (r_p > 0.0 && r_d / r_p > c->rho_tau)
+            nr = fmax(rhod / c->rho_kappa, c->rho_min);
+        if (nr != rhod) {
+            c->rho = nr;
+            c->inv_rho = 1.0 / nr;
+            c->rho_changed = 1;
+        }
+    }
+    c->done = done;
+    c->counter = 0u;
+}
+
+// <W_F(F_k)> and <Lambda_k>, summed in double with the same fixed-order scheme.
+template <typename T, int D, int MODEL>
+__global__ void __launch_bounds__(kLocalThreads)
+k_stress(Ctrl* __restrict__ ctrl, double* __restrict__ partials, const T* F0, const T* F1, const T* Lam,
+         const uint8_t* __restrict__ phase, const double* __restrict__ mat, int nparam, long long V) {
+    using Law = typename LawOf<T, D, MODEL>::type;
+    constexpr int NN = D * D;
+    __shared__ double s_sum[kLocalThreads / 32][2 * NN];
+    __shared__ int s_last;
+    const T* F = (ctrl->k & 1) ? F1 : F0;
+    double acc[2 * NN];
+#pragma unroll
+    for (int p = 0; p < 2 * NN; ++p) acc[p] = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        T Fv[NN], P[NN];
+#pragma unroll
+        for (int p = 0; p < NN; ++p) Fv[p] = F[p * V + v];
+        const Law m = load_law<Law, T>(phase, mat, nparam, v);
+        m.stress(Fv, P);
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            acc[p] += (double)P[p];
+            acc[NN + p] += (double)Lam[p * V + v];
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int p = 0; p < 2 * NN; ++p) {
+        const double s = warp_sum(acc[p]);
+        if (lane == 0) s_sum[warp][p] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double* pp = partials + (size_t)blockIdx.x * kPartialStride;
+        for (int p = 0; p < 2 * NN; ++p) {
+            double s = 0;
+            for (int w = 0; w < kLocalThreads / 32; ++w) s += s_sum[w][p];
+            pp[p] = s;
+        }
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctrl->counter2, 1u);
+        s_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int p = 0; p < 2 * NN; ++p) acc[p] = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        const double* pp = partials + (size_t)i * kPartialStride;
+#pragma unroll
+        for (int p = 0; p < 2 * NN; ++p) acc[p] += __ldcg(pp + p);
+    }
+#pragma unroll
+    for (int p = 0; p < 2 * NN; ++p) {
+        const double s = warp_sum(acc[p]);
+        if (lane == 0) s_sum[warp][p] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int i = 0; i < 9; ++i) {
+        ctrl->stress[i] = 0.0;
+        ctrl->lam_mean[i] = 0.0;
+    }
+    for (int p = 0; p < NN; ++p) {
+        double s = 0, l = 0;
+        for (int w = 0; w < kLocalThreads / 32; ++w) {
+            s += s_sum[w][p];
+            l += s_sum[w][NN + p];
+        }
+        const int i = p / D, j = p % D;
+        ctrl->stress[i * 3 + j] = s / (double)V;
+        ctrl->lam_mean[i * 3 + j] = l / (double)V;
+    }
+    ctrl->counter2 = 0u;
+}
+
+// Copy the current state (F_k, Lambda_k, u~_k) between the float and double sets.
+template <typename S, typename Dd>
+__global__ void k_convert(const Ctrl* __restrict__ ctrl, const S* Fs0, const S* Fs1, const S* Ls, const S* Us0,
+                          const S* Us1, Dd* Fd0, Dd* Fd1, Dd* Ld, Dd* Ud0, Dd* Ud1, long long nF, long long nU) {
+    const int par = (int)(ctrl->k & 1);
+    const S* Fs = par ? Fs1 : Fs0;
+    const S* Us = par ? Us1 : Us0;
+    Dd* Fd = par ? Fd1 : Fd0;
+    Dd* Ud = par ? Ud1 : Ud0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nF; i += (long long)gridDim.x * blockDim.x) {
+        Fd[i] = (Dd)Fs[i];
+        Ld[i] = (Dd)Ls[i];
+        if (i < nU) Ud[i] = (Dd)Us[i];
+    }
+}
+
+// ------------------------------------------------------------------ dispatch
+
+template <typename T>
+struct Set;
+template <>
+struct Set<double> {
+    static double* F(const Launch& L, int i) { return L.F64[i]; }
+    static double* Lm(const Launch& L) { return L.L64; }
+    static double* U(const Launch& L, int i) { return L.U64[i]; }
+};
+template <>
+struct Set<float> {
+    static float* F(const Launch& L, int i) { return L.F32[i]; }
+    static float* Lm(const Launch& L) { return L.L32; }
+    static float* U(const Launch& L, int i) { return L.U32[i]; }
+};
+
+template <typename T, int D, int MODEL>
+cudaError_t run_init(const Launch& L, bool lambda_zero) {
+    k_init<T, D, MODEL><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
+        L.ctrl, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0), Set<T>::U(L, 1), L.phase, L.mat,
+        L.nparam, L.V, lambda_zero ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <typename T, int D, int MODEL>
+cudaError_t run_local(const Launch& L, bool first, bool only_if) {
+    if (first)
+        k_local<T, D, MODEL, true><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
+            L.ctrl, L.hist, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0),
+            Set<T>::U(L, 1), L.phase, L.mat, L.nparam, L.n, L.V, only_if ? 1 : 0);
+    else
+        k_local<T, D, MODEL, false><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
+            L.ctrl, L.hist, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0),
+            Set<T>::U(L, 1), L.phase, L.mat, L.nparam, L.n, L.V, 0);
+    return cudaGetLastError();
+}
+
+template <typename T, int D, int MODEL>
+cudaError_t run_stress(const Launch& L) {
+    k_stress<T, D, MODEL><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
+        L.ctrl, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), L.phase, L.mat, L.nparam, L.V);
+    return cudaGetLastError();
+}
+
+#define RVE_DISPATCH(FN, T, ...)                                                            \
+    do {                                                                                    \
+        if (L.dim == 2 && L.model == kNeoHooke) return FN<T, 2, kNeoHooke>(__VA_ARGS__);    \
+        if (L.dim == 3 && L.model == kNeoHooke) return FN<T, 3, kNeoHooke>(__VA_ARGS__);    \
+        if (L.dim == 2 && L.model == kLinear) return FN<T, 2, kLinear>(__VA_ARGS__);        \
+        if (L.dim == 3 && L.model == kLinear) return FN<T, 3, kLinear>(__VA_ARGS__);        \
+        return cudaErrorInvalidValue;                                                       \
+    } while (0)
+
+}  // namespace
+
+cudaError_t launch_init(const Launch& L, bool fp64, bool lambda_zero) {
+    if (fp64) RVE_DISPATCH(run_init, double, L, lambda_zero);
+    RVE_DISPATCH(run_init, float, L, lambda_zero);
+}
+
+cudaError_t launch_local(const Launch& L, bool fp64, bool first, bool only_if_rho_changed) {
+    if (fp64) RVE_DISPATCH(run_local, double, L, first, only_if_rho_changed);
+    RVE_DISPATCH(run_local, float, L, first, only_if_rho_changed);
+}
+
+cudaError_t launch_stress(const Launch& L, bool fp64) {
+    if (fp64) RVE_DISPATCH(run_stress, double, L);
+    RVE_DISPATCH(run_stress, float, L);
+}
+
+cudaError_t launch_convert(const Launch& L, bool to_fp64) {
+    const long long nF = (long long)L.dim * L.dim * L.V;
+    const long long nU = (long long)L.dim * L.V;
+    const int blocks = 152 * 8;
+    if (to_fp64)
+        k_convert<float, double><<<blocks, 256, 0, L.stream>>>(L.ctrl, L.F32[0], L.F32[1], L.L32, L.U32[0],
+                                                               L.U32[1], L.F64[0], L.F64[1], L.L64, L.U64[0],
+                                                               L.U64[1], nF, nU);
+    else
+        k_convert<double, float><<<blocks, 256, 0, L.stream>>>(L.ctrl, L.F64[0], L.F64[1], L.L64, L.U64[0],
+                                                               L.U64[1], L.F32[0], L.F32[1], L.L32, L.U32[0],
+                                                               L.U32[1], nF, nU);
+    return cudaGetLastError();
+}
+
+}  // namespace admm

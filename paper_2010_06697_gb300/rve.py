@@ -1,0 +1,364 @@
+"""ctypes binding of the C ABI in include/rve.h (same names, argument marshalling only).
+
+Every step of the ADMM iteration runs in ``lib/librve.so``; this module only
+converts numpy / torch arguments to pointers and status codes to exceptions.
+It raises ImportError-like RuntimeError when the library has not been built:
+there is no fallback path.
+
+``Rve`` is a small owner object around one handle.  By default it takes its
+device workspace from a torch CUDA tensor (``rve_create_in``), so PyTorch's
+caching allocator provides the memory; pass ``use_torch=False`` to let the
+library call cudaMalloc itself (``rve_create``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "librve.so")
+
+RVE_OK = 0
+RVE_E_INVALID_ARG = -1
+RVE_E_OOM = -2
+RVE_E_NOT_CONVERGED = -3
+RVE_E_NUMERICAL = -4
+RVE_E_CUDA = -5
+RVE_E_BUSY = -6
+RVE_E_STATE = -7
+RVE_E_NOT_FOUND = -8
+
+RVE_NEOHOOKE, RVE_LINEAR, RVE_LCE = 0, 1, 2
+RVE_FP64, RVE_MIXED, RVE_FP32 = 0, 1, 2
+RVE_RHO_FIXED, RVE_RHO_ADAPTIVE = 0, 1
+RVE_LAMBDA0_STRESS, RVE_LAMBDA0_ZERO = 0, 1
+RVE_FIELD_F, RVE_FIELD_LAMBDA, RVE_FIELD_U, RVE_FIELD_N = 0, 1, 2, 3
+
+MODELS = {"neohookean": RVE_NEOHOOKE, "linear": RVE_LINEAR, "lce": RVE_LCE}
+PRECISIONS = {"fp64": RVE_FP64, "mixed": RVE_MIXED, "fp32": RVE_FP32}
+
+
+class rve_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("rho_policy", ctypes.c_int),
+        ("lambda0", ctypes.c_int),
+        ("max_iter", ctypes.c_int),
+        ("newton_max", ctypes.c_int),
+        ("newton_tol", ctypes.c_double),
+        ("rho_kappa", ctypes.c_double),
+        ("rho_tau", ctypes.c_double),
+        ("rho_min", ctypes.c_double),
+        ("mu_ref", ctypes.c_double),
+        ("mixed_switch", ctypes.c_double),
+        ("check_every", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+    ]
+
+
+class rve_solve_info(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int),
+        ("fp64_iterations", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("status", ctypes.c_int),
+        ("r_p", ctypes.c_double),
+        ("r_d", ctypes.c_double),
+        ("rho", ctypes.c_double),
+        ("mu_ref", ctypes.c_double),
+        ("newton_max_iters", ctypes.c_int),
+        ("newton_fail", ctypes.c_longlong),
+        ("time_ms", ctypes.c_double),
+        ("launches", ctypes.c_longlong),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+_PD = ctypes.POINTER(ctypes.c_double)
+
+SIGNATURES = {
+    "rve_default_options": (None, [ctypes.POINTER(rve_options)]),
+    "rve_workspace_bytes": (_SZ, [_I, _I, _I, ctypes.POINTER(rve_options)]),
+    "rve_create": (_I, [ctypes.POINTER(_VP), _I, _I, _I, ctypes.POINTER(rve_options), _VP]),
+    "rve_create_in": (_I, [ctypes.POINTER(_VP), _I, _I, _I, ctypes.POINTER(rve_options), _VP, _VP, _SZ]),
+    "rve_destroy": (None, [_VP]),
+    "rve_set_material": (_I, [_VP, ctypes.POINTER(ctypes.c_uint8), _I, _PD, _I, _PD]),
+    "rve_solve": (_I, [_VP, _PD, _D, _D, ctypes.POINTER(rve_solve_info)]),
+    "rve_stress": (_I, [_VP, _PD]),
+    "rve_mean_lambda": (_I, [_VP, _PD]),
+    "rve_get_field": (_I, [_VP, _I, _PD]),
+    "rve_set_field": (_I, [_VP, _I, _PD]),
+    "rve_reset": (_I, [_VP]),
+    "rve_history": (_I, [_VP, _PD, _PD, _PD, _I]),
+    "rve_strerror": (ctypes.c_char_p, [_I]),
+    "rve_set_profiling": (_I, [_VP, _I]),
+    "rve_kernel_times": (_I, [_VP, _I, _PD, ctypes.POINTER(ctypes.c_longlong), _I]),
+}
+
+KCLASS_NAMES = ["local", "local_first", "xfwd", "fwd_y", "solve", "inv_y", "xinv"]
+
+_lib = None
+
+
+def lib():
+    """Load librve.so (once).  Raises RuntimeError if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class RveError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = lib().rve_strerror(code).decode()
+        super().__init__(f"{where}: {msg} ({code})" if where else f"{msg} ({code})")
+
+
+def _check(code, where):
+    if code != RVE_OK:
+        raise RveError(code, where)
+    return code
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_PD)
+
+
+# ------------------------------------------------------------------ ABI-named thin wrappers
+
+def rve_default_options():
+    o = rve_options()
+    lib().rve_default_options(ctypes.byref(o))
+    return o
+
+
+def rve_workspace_bytes(dim, n, model, opt=None):
+    return int(lib().rve_workspace_bytes(dim, n, model, ctypes.byref(opt) if opt is not None else None))
+
+
+def rve_strerror(code):
+    return lib().rve_strerror(code).decode()
+
+
+def rve_create(dim, n, model, opt=None, stream=None):
+    h = _VP()
+    rc = lib().rve_create(ctypes.byref(h), dim, n, model, ctypes.byref(opt) if opt is not None else None,
+                          _VP(stream or 0))
+    return rc, h
+
+
+def rve_create_in(dim, n, model, opt, stream, workspace_ptr, nbytes):
+    h = _VP()
+    rc = lib().rve_create_in(ctypes.byref(h), dim, n, model, ctypes.byref(opt) if opt is not None else None,
+                             _VP(stream or 0), _VP(workspace_ptr), nbytes)
+    return rc, h
+
+
+def rve_destroy(h):
+    lib().rve_destroy(h)
+
+
+def rve_set_material(h, phase, params, n0=None):
+    ph = np.ascontiguousarray(phase, dtype=np.uint8)
+    par = np.ascontiguousarray(params, dtype=np.float64)
+    nphase, nparam = par.shape
+    n0p = None
+    if n0 is not None:
+        n0a = np.ascontiguousarray(n0, dtype=np.float64)
+        n0p = _dptr(n0a)
+    return lib().rve_set_material(h, ph.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nphase, _dptr(par),
+                                  nparam, n0p)
+
+
+def rve_solve(h, Fbar, rho, tol):
+    fb = np.ascontiguousarray(np.asarray(Fbar, dtype=np.float64).reshape(3, 3))
+    info = rve_solve_info()
+    rc = lib().rve_solve(h, _dptr(fb), float(rho), float(tol), ctypes.byref(info))
+    return rc, info
+
+
+def rve_stress(h):
+    S = np.zeros(9)
+    rc = lib().rve_stress(h, _dptr(S))
+    return rc, S.reshape(3, 3)
+
+
+def rve_mean_lambda(h):
+    S = np.zeros(9)
+    rc = lib().rve_mean_lambda(h, _dptr(S))
+    return rc, S.reshape(3, 3)
+
+
+def rve_get_field(h, which, out):
+    return lib().rve_get_field(h, which, _dptr(out))
+
+
+def rve_set_field(h, which, arr):
+    a = np.ascontiguousarray(arr, dtype=np.float64)
+    return lib().rve_set_field(h, which, _dptr(a))
+
+
+def rve_reset(h):
+    return lib().rve_reset(h)
+
+
+def rve_history(h, cap):
+    rp, rd, rho = np.zeros(cap), np.zeros(cap), np.zeros(cap)
+    cnt = lib().rve_history(h, _dptr(rp), _dptr(rd), _dptr(rho), cap)
+    if cnt < 0:
+        return cnt, None
+    return cnt, np.stack([rp[:cnt], rd[:cnt], rho[:cnt]], axis=1)
+
+
+def rve_set_profiling(h, on):
+    return lib().rve_set_profiling(h, 1 if on else 0)
+
+
+def rve_kernel_times(h, fp64):
+    ms = np.zeros(len(KCLASS_NAMES))
+    n = np.zeros(len(KCLASS_NAMES), dtype=np.int64)
+    rc = lib().rve_kernel_times(h, 1 if fp64 else 0, _dptr(ms), n.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                len(KCLASS_NAMES))
+    return rc, ms, n
+
+
+# ------------------------------------------------------------------ owner object
+
+class Rve:
+    """One solver handle: ``Rve(dim, n, model="neohookean", precision="fp64", **options)``."""
+
+    def __init__(self, dim, n, model="neohookean", precision="fp64", stream=None, use_torch=True, **options):
+        self.dim, self.n = int(dim), int(n)
+        self.model = MODELS[model] if isinstance(model, str) else int(model)
+        opt = rve_default_options()
+        opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        for k, v in options.items():
+            if k == "rho_policy" and isinstance(v, str):
+                v = {"fixed": RVE_RHO_FIXED, "adaptive": RVE_RHO_ADAPTIVE}[v]
+            if k == "lambda0" and isinstance(v, str):
+                v = {"stress": RVE_LAMBDA0_STRESS, "zero": RVE_LAMBDA0_ZERO}[v]
+            setattr(opt, k, v)
+        self.opt = opt
+        self._ws = None
+        self.h = None
+        if stream is None and use_torch:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        if use_torch:
+            import torch
+            nbytes = self.workspace_bytes()
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._ws.data_ptr()
+            aligned = (base + 255) // 256 * 256
+            rc, h = rve_create_in(self.dim, self.n, self.model, opt, stream, aligned, nbytes)
+        else:
+            rc, h = rve_create(self.dim, self.n, self.model, opt, stream)
+        _check(rc, "rve_create")
+        self.h = h
+
+    def workspace_bytes(self):
+        return rve_workspace_bytes(self.dim, self.n, self.model, self.opt)
+
+    @property
+    def grid(self):
+        return (self.n,) * self.dim
+
+    def set_material(self, phase, params, n0=None):
+        ph = np.asarray(phase)
+        if ph.shape != self.grid:
+            raise ValueError(f"phase shape {ph.shape} != {self.grid}")
+        _check(rve_set_material(self.h, ph, params, n0), "rve_set_material")
+
+    def solve(self, Fbar, rho, tol, check=False):
+        rc, info = rve_solve(self.h, Fbar, rho, tol)
+        if rc not in (RVE_OK, RVE_E_NOT_CONVERGED) or (check and rc != RVE_OK):
+            raise RveError(rc, "rve_solve")
+        return info
+
+    def stress(self):
+        rc, S = rve_stress(self.h)
+        _check(rc, "rve_stress")
+        return S[: self.dim, : self.dim].copy()
+
+    def mean_lambda(self):
+        rc, S = rve_mean_lambda(self.h)
+        _check(rc, "rve_mean_lambda")
+        return S[: self.dim, : self.dim].copy()
+
+    def _shape(self, which):
+        d = self.dim
+        if which in (RVE_FIELD_F, RVE_FIELD_LAMBDA):
+            return (d, d) + self.grid
+        if which == RVE_FIELD_U:
+            return (d,) + self.grid
+        return (3,) + self.grid
+
+    def get_field(self, which):
+        out = np.empty(self._shape(which))
+        _check(rve_get_field(self.h, which, out), "rve_get_field")
+        return out
+
+    def set_field(self, which, arr):
+        a = np.asarray(arr, dtype=np.float64)
+        if a.shape != self._shape(which):
+            raise ValueError(f"field shape {a.shape} != {self._shape(which)}")
+        _check(rve_set_field(self.h, which, a), "rve_set_field")
+
+    def state(self):
+        return {"F": self.get_field(RVE_FIELD_F), "Lam": self.get_field(RVE_FIELD_LAMBDA),
+                "u": self.get_field(RVE_FIELD_U)}
+
+    def set_state(self, st):
+        self.set_field(RVE_FIELD_F, st["F"])
+        self.set_field(RVE_FIELD_LAMBDA, st["Lam"])
+        self.set_field(RVE_FIELD_U, st["u"])
+
+    def reset(self):
+        _check(rve_reset(self.h), "rve_reset")
+
+    def history(self, cap=None):
+        cnt, hst = rve_history(self.h, cap or (self.opt.max_iter + 1))
+        if cnt < 0:
+            raise RveError(cnt, "rve_history")
+        return hst
+
+    def set_profiling(self, on):
+        _check(rve_set_profiling(self.h, on), "rve_set_profiling")
+
+    def kernel_times(self):
+        """{precision: {class: (total_ms, launches)}} for classes with launches."""
+        out = {}
+        for name, f in (("fp64", True), ("fp32", False)):
+            rc, ms, n = rve_kernel_times(self.h, f)
+            if rc < 0:
+                raise RveError(rc, "rve_kernel_times")
+            out[name] = {KCLASS_NAMES[c]: (float(ms[c]), int(n[c])) for c in range(len(KCLASS_NAMES)) if n[c]}
+        return out
+
+    def close(self):
+        if self.h is not None:
+            rve_destroy(self.h)
+            self.h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,84 @@
+"""The C-ABI library builds, loads on a machine without a GPU and exports every
+entry point include/*.h declares; host-side argument checks need no device."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2010_06697_gb300 import build, rve
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(rve_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return rve.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"rve_create", "rve_set_material", "rve_solve", "rve_stress", "rve_destroy"} <= names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert set(rve.SIGNATURES) >= names
+
+
+def test_default_options(lib):
+    o = rve.rve_default_options()
+    assert o.precision == rve.RVE_FP64 and o.rho_policy == rve.RVE_RHO_FIXED
+    assert o.max_iter == 1000 and o.rho_kappa == 1.3 and o.rho_tau == 10.0
+    assert o.check_every >= 1 and o.use_graph == 1
+
+
+def test_workspace_bytes(lib):
+    o = rve.rve_default_options()
+    b64 = rve.rve_workspace_bytes(3, 128, rve.RVE_NEOHOOKE, o)
+    # 2 F + Lambda (9 comps each) + 2 u (3 comps): 33 doubles per voxel at least
+    assert b64 >= 33 * 8 * 128 ** 3
+    o.precision = rve.RVE_MIXED
+    bm = rve.rve_workspace_bytes(3, 128, rve.RVE_NEOHOOKE, o)
+    assert bm >= b64 + 33 * 4 * 128 ** 3
+    for bad in [(1, 16), (3, 7), (3, 10), (3, 1024), (2, 2)]:
+        assert rve.rve_workspace_bytes(bad[0], bad[1], 0, None) == 0
+
+
+@pytest.mark.parametrize("dim,n,model", [(4, 16, 0), (3, 7, 0), (3, 20, 0), (2, 16, 9)])
+def test_create_rejects_bad_shapes_without_device(lib, dim, n, model):
+    rc, h = rve.rve_create(dim, n, model)
+    assert rc == rve.RVE_E_INVALID_ARG and not h.value
+
+
+def test_create_rejects_bad_options(lib):
+    o = rve.rve_default_options()
+    o.newton_max = 0
+    rc, _ = rve.rve_create(3, 16, 0, o)
+    assert rc == rve.RVE_E_INVALID_ARG
+    o = rve.rve_default_options()
+    o.check_every = 0
+    rc, _ = rve.rve_create(3, 16, 0, o)
+    assert rc == rve.RVE_E_INVALID_ARG
+
+
+def test_null_handle_is_rejected(lib):
+    assert lib.rve_solve(None, None, ctypes.c_double(1.0), ctypes.c_double(1.0), None) == rve.RVE_E_INVALID_ARG
+    assert lib.rve_stress(None, None) == rve.RVE_E_INVALID_ARG
+    assert lib.rve_reset(None) == rve.RVE_E_INVALID_ARG
+    lib.rve_destroy(None)
+
+
+def test_strerror(lib):
+    for c in range(-8, 1):
+        assert len(rve.rve_strerror(c)) > 0
