@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Benchmark of the ADMM hot path (Zhou & Bhattacharya, Section 2.1, Steps 1-4).
+
+Workload: 3D 128^3 compressible neo-Hookean matrix (mu = 1) with periodic
+spherical inclusions (mu = 10, radius 6 voxels, seeded centres, 20 % volume
+fraction), nu = 0.3, Fbar = diag(0.9, 1, 1), rho = 10, solved to r_p, r_d <=
+1e-8.  One step is one complete RVE solve from the fresh state (initialise,
+iterate to tolerance, homogenised stress), i.e. every kernel of the path.
+
+Prints ONE JSON line.  ``value`` is voxel-iterations/s of the default precision
+mode (RVE_MIXED: float bulk, double residuals and stress, double polish) over
+the timed steps; ``fp64`` repeats the measurement in plain double.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ADMM voxel-iterations/s and fraction of HBM roofline; p50/p99 RVE solve latency"
+UNIT = "voxel-iterations/s"
+N, DIM, SEED = 128, 3, 0
+FBAR = np.diag([0.9, 1.0, 1.0])
+RHO, TOL = 10.0, 1e-8
+MU = (1.0, 10.0)
+NU = 0.3
+L2_BYTES = 129e6
+
+# algorithmic bytes per voxel and launch, per kernel class (s = bytes per scalar)
+#   local: read u~_{k+1}, u~_k (d each), F, Lambda (d^2 each); write F, Lambda; phase id (1 B)
+#   xfwd: read F, Lambda; write the spectrum (d scalars);  fwd_y / solve / inv_y / xinv: read + write d scalars
+#   local_r: local in double + write the float increment R (d^2 floats)
+#   xfwd_incr: read R (d^2 floats), write the float spectrum;  xinv_incr: read the float spectrum and
+#   u~_k (double), write u~_{k+1} (double)
+def bytes_per_voxel(cls: str, s: int, d: int = 3) -> float:
+    return {"local": (2 * d + 4 * d * d) * s + 1, "local_first": (d + 3 * d * d) * s + 1,
+            "xfwd": (2 * d * d + d) * s, "fwd_y": 2 * d * s, "solve": 2 * d * s, "inv_y": 2 * d * s,
+            "xinv": 2 * d * s, "local_r": (2 * d + 4 * d * d) * 8 + 1 + d * d * 4,
+            "xfwd_incr": (d * d + d) * 4, "xinv_incr": d * 4 + 2 * d * 8}[cls]
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "source": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        p = {"hbm_gbs": float(m["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        pass
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_inputs(n=N):
+    from paper_2010_06697_gb300 import synth
+    ph = synth.inclusion_phase(n, DIM, SEED)
+    par = synth.two_phase_params(MU[0], MU[1], NU)
+    return ph, par
+
+
+def oracle_child(n: int, iters: int) -> dict:
+    """Time the FP64 oracle in a fresh single-threaded child process (no CUDA)."""
+    code = (
+        "import json,sys,time;sys.path.insert(0,%r);import numpy as np;import oracle;"
+        "from paper_2010_06697_gb300 import synth;"
+        "ph=synth.inclusion_phase(%d,3,%d);par=synth.two_phase_params(%r,%r,%r);"
+        "t=time.perf_counter();r=oracle.admm_solve(ph,par,np.diag([0.9,1.0,1.0]),%r,-1.0,%d);"
+        "dt=time.perf_counter()-t;print(json.dumps({'seconds':dt,'iters':r['iters'],'voxels':ph.size}))"
+    ) % (ROOT, n, SEED, MU[0], MU[1], NU, RHO, iters)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=3600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline():
+    r = oracle_child(N, 1)
+    v = r["voxels"] * r["iters"] / r["seconds"]
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 ADMM iteration of the {N}^3 inclusion cell from the fresh state "
+                      f"({r['seconds']:.1f} s, FP64 numpy oracle, 1 thread)"}
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # size each step so the whole run stays within a few minutes on the host cores
+    budget_s = 200.0
+    est = {128: 36.0, 96: 15.0, 64: 4.5, 48: 1.9, 32: 0.6}
+    n = next(m for m in (128, 96, 64, 48, 32) if est[m] * (args.steps + args.warmup) <= budget_s or m == 32)
+    for _ in range(args.warmup):
+        oracle_child(n, 1)
+    secs, vox = 0.0, 0
+    for _ in range(args.steps):
+        r = oracle_child(n, 1)
+        secs += r["seconds"]
+        vox += r["voxels"] * r["iters"]
+    v = vox / secs
+    sample = (f"each step: 1 ADMM iteration of the inclusion cell recipe at {n}^3 "
+              f"(FP64 numpy oracle, 1 thread); {N}^3 is the GPU arm's size")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"inclusions{n}", "n": n, "dim": 3},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def timed_solves(s, steps, torch, phase=None, params=None, pinned_phase=None):
+    """K full solves; returns (elapsed_ms by CUDA events on the caller's stream, infos, stresses)."""
+    infos, stresses = [], []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(steps):
+        if pinned_phase is not None:
+            s.set_material(pinned_phase, params)     # host -> device copy of the inputs
+        else:
+            s.reset()
+        infos.append(s.solve(FBAR, RHO, TOL))
+        stresses.append(s.stress())                    # device -> host read of the result
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), infos, stresses
+
+
+def run_ours(args):
+    import torch
+    from paper_2010_06697_gb300 import build, rve
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    rve.lib()
+    ph, par = make_inputs()
+    V = ph.size
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    for prec in ([args.precision] + (["fp64"] if args.precision != "fp64" and not args.quick else [])):
+        s = rve.Rve(DIM, N, "neohookean", prec, max_iter=2000)
+        s.set_material(ph, par)
+        for _ in range(args.warmup):
+            s.reset()
+            s.solve(FBAR, RHO, TOL)
+            s.stress()
+        barrier()
+        clocks = ClockSampler(local_rank) if prec == args.precision else None
+        if clocks:
+            clocks.start()
+        ms, infos, stresses = timed_solves(s, args.steps, torch)
+        if clocks:
+            clk = clocks.stop()
+        ms = max_over_ranks(ms)
+        iters = sum(i.iterations for i in infos)
+        res = {"ms": ms, "iters_per_step": iters / args.steps, "value": world * V * iters / (ms / 1e3),
+               "converged": all(i.converged for i in infos),
+               "fp64_iters_per_step": sum(i.fp64_iterations for i in infos) / args.steps,
+               "launches": sum(i.launches for i in infos) + args.steps, "stress": stresses[-1].tolist()}
+        if clocks:
+            res["clocks"] = clk
+        # e2e: the same steps through the public API from pinned host memory
+        if prec == args.precision:
+            pinned = torch.empty(ph.shape, dtype=torch.uint8, pin_memory=True)
+            pinned.copy_(torch.from_numpy(ph))
+            barrier()
+            ems, einfos, _ = timed_solves(s, args.steps, torch, params=par, pinned_phase=pinned.numpy())
+            ems = max_over_ranks(ems)
+            eiters = sum(i.iterations for i in einfos)
+            res["e2e"] = {"value": world * V * eiters / (ems / 1e3), "unit": UNIT,
+                          "h2d_bytes_per_step": int(V + par.size * 8 + 72), "d2h_bytes_per_step": 72}
+            # per-kernel device times (events around every launch, no graphs) for the roofline
+            s.set_profiling(True)
+            for _ in range(2):
+                s.reset()
+                s.solve(FBAR, RHO, TOL)
+            res["kernels"] = s.kernel_times()
+            s.set_profiling(False)
+        s.close()
+        results[prec] = res
+        barrier()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    main = results[args.precision]
+    pk = peaks()
+    # roofline of the dominant kernel class
+    kern = []
+    for pname, table in main["kernels"].items():
+        sz = 8 if pname == "fp64" else 4
+        for cls, (tot, cnt) in table.items():
+            if cls in ("local_r", "xfwd_incr", "xinv_incr"):
+                sz = 0  # fixed mixed-width byte counts
+            per_launch_ms = tot / cnt
+            byts = bytes_per_voxel(cls, sz) * V
+            kern.append({"kernel": cls, "precision": pname, "total_ms": tot, "launches": cnt,
+                         "ms_per_launch": per_launch_ms, "alg_bytes_per_launch": byts,
+                         "gbs": byts / (per_launch_ms / 1e3) / 1e9})
+    kern.sort(key=lambda k: -k["total_ms"])
+    top = kern[0]
+    roof = {"bound": "hbm", "achieved": top["gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": top["gbs"] / pk["hbm_gbs"], "traffic": None,
+            "kernel": f"{top['kernel']} ({top['precision']})", "peak_source": pk["source"],
+            "share_of_profiled_time": top["total_ms"] / sum(k["total_ms"] for k in kern)}
+    line = {
+        "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else ("f64" if args.precision == "fp64" else "f32"),
+        "data": "synthetic",
+        "config": {"workload": "inclusions128", "n": N, "dim": DIM, "model": "neohookean", "seed": SEED,
+                   "Fbar": "diag(0.9,1,1)", "rho": RHO, "tol": TOL, "precision": args.precision,
+                   "step": "one full RVE solve from the fresh state", "l2": "inputs larger than L2 "
+                   f"(resident state {33 * 4 * V / 1e6:.0f} MB float / {33 * 8 * V / 1e6:.0f} MB double > 129 MB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "iters_per_step": main["iters_per_step"], "fp64_iters_per_step": main["fp64_iters_per_step"],
+        "converged": main["converged"], "stress_xx": main["stress"][0][0],
+        "gpu_launches": main["launches"],
+        "clocks": main.get("clocks"),
+        "e2e": main["e2e"],
+        "roofline": roof,
+        "kernels": [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in kk.items()} for kk in kern],
+    }
+    if "fp64" in results and args.precision != "fp64":
+        f = results["fp64"]
+        line["fp64"] = {"value": f["value"], "ms_per_step": f["ms"] / args.steps,
+                        "iters_per_step": f["iters_per_step"], "converged": f["converged"],
+                        "stress_xx": f["stress"][0][0]}
+        line["mixed_over_fp64"] = main["value"] / f["value"]
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_single(args):
+    import torch
+    from paper_2010_06697_gb300 import build, rve
+    torch.cuda.set_device(0)
+    build.build()
+    ph, par = make_inputs()
+    s = rve.Rve(DIM, N, "neohookean", args.precision, max_iter=2000)
+    s.set_material(ph, par)
+    info = s.solve(FBAR, RHO, TOL)
+    S = s.stress()
+    s.close()
+    print(json.dumps({"single": True, "precision": args.precision, "iterations": info.iterations,
+                      "fp64_iterations": info.fp64_iterations, "converged": bool(info.converged),
+                      "time_ms": info.time_ms, "launches": info.launches, "stress_xx": float(S[0, 0])}))
+    return 0 if info.converged else 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the fp64 comparison run")
+    ap.add_argument("--single", action="store_true",
+                    help="one solve of the workload (for profiler captures), prints a short summary")
+    args = ap.parse_args()
+    if args.single:
+        return run_single(args)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -179,7 +179,10 @@ enum rve_kernel_class {
     RVE_KCLASS_SOLVE = 4,       /* last-axis forward FFT, multiply by 1/|k|^2, inverse       */
     RVE_KCLASS_INV_Y = 5,       /* inverse y FFT (3D)                                        */
     RVE_KCLASS_XINV = 6,        /* inverse x FFT -> u~ (Step 2 result)                       */
-    RVE_KCLASS_COUNT = 7
+    RVE_KCLASS_LOCAL_R = 7,     /* double polish (RVE_MIXED): fused local + float increment R */
+    RVE_KCLASS_XFWD_INCR = 8,   /* divergence of R + forward x FFT (float)                   */
+    RVE_KCLASS_XINV_INCR = 9,   /* inverse x FFT, u~_{k+1} = u~_k + P(R) in double           */
+    RVE_KCLASS_COUNT = 10
 };
 
 /* on != 0: every kernel launch of later solves is bracketed by CUDA events on

@@ -39,7 +39,7 @@ struct rve {
     int state_fp64 = 1;     // which set holds the current state
     double mu_ref = 1.0;
     int nphase = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [fp64]
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // float, double, double polish
     long long k = 0;        // host copy of Ctrl::k
     int last_iters = 0;
     long long launches = 0; // kernel launches issued by the running solve
@@ -178,8 +178,9 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 }
 
 // Profiled variant of one chunk: direct launches with an event after each kernel;
-// only iterations that ran (before the stop flag) are accumulated.
-int run_chunk_profiled(rve* h, bool fp64) {
+// only iterations that ran (before the stop flag) are accumulated.  incr: the
+// double polish of RVE_MIXED (float increment projection + local with R).
+int run_chunk_profiled(rve* h, bool fp64, bool incr) {
     const int S = admm::fft_stages(h->dim);
     const int per = S + 2 + 1;  // start event, S fft, local, redo
     const long long k_before = h->hctrl->k;
@@ -188,10 +189,11 @@ int run_chunk_profiled(rve* h, bool fp64) {
         cudaEvent_t* e = &h->pev[(size_t)i * per];
         CK(cudaEventRecord(e[0], h->stream));
         for (int st = 0; st < S; ++st) {
-            if (admm::launch_fft(h->L, fp64, st) != cudaSuccess) return RVE_E_CUDA;
+            const cudaError_t le = incr ? admm::launch_fft_incr(h->L, st) : admm::launch_fft(h->L, fp64, st);
+            if (le != cudaSuccess) return RVE_E_CUDA;
             CK(cudaEventRecord(e[1 + st], h->stream));
         }
-        if (admm::launch_local(h->L, fp64, false, false) != cudaSuccess) return RVE_E_CUDA;
+        if (admm::launch_local(h->L, fp64, false, false, incr) != cudaSuccess) return RVE_E_CUDA;
         CK(cudaEventRecord(e[1 + S], h->stream));
         if (h->opt.rho_policy == RVE_RHO_ADAPTIVE) {
             if (admm::launch_local(h->L, fp64, true, true) != cudaSuccess) return RVE_E_CUDA;
@@ -204,22 +206,29 @@ int run_chunk_profiled(rve* h, bool fp64) {
     for (long long i = 0; i < ran && i < h->opt.check_every; ++i) {
         cudaEvent_t* e = &h->pev[(size_t)i * per];
         for (int st = 0; st < S; ++st) {
-            h->prof_ms[f][fft_class(h->dim, st)] += elapsed(e[st], e[st + 1]);
-            h->prof_n[f][fft_class(h->dim, st)] += 1;
+            int cls = fft_class(h->dim, st), fb = f;
+            if (incr) {
+                fb = 0;
+                if (st == 0) cls = RVE_KCLASS_XFWD_INCR;
+                if (st == S - 1) cls = RVE_KCLASS_XINV_INCR;
+            }
+            h->prof_ms[fb][cls] += elapsed(e[st], e[st + 1]);
+            h->prof_n[fb][cls] += 1;
         }
-        h->prof_ms[f][RVE_KCLASS_LOCAL] += elapsed(e[S], e[S + 1]);
-        h->prof_n[f][RVE_KCLASS_LOCAL] += 1;
+        const int lc = incr ? RVE_KCLASS_LOCAL_R : RVE_KCLASS_LOCAL;
+        h->prof_ms[f][lc] += elapsed(e[S], e[S + 1]);
+        h->prof_n[f][lc] += 1;
     }
     return RVE_OK;
 }
 
-int capture_chunk(rve* h, bool fp64) {
+int capture_chunk(rve* h, bool fp64, bool incr, int slot) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < h->opt.check_every && e == cudaSuccess; ++i) {
-        e = admm::launch_fft(h->L, fp64);
-        if (e == cudaSuccess) e = admm::launch_local(h->L, fp64, false, false);
+        e = incr ? admm::launch_fft_incr(h->L) : admm::launch_fft(h->L, fp64);
+        if (e == cudaSuccess) e = admm::launch_local(h->L, fp64, false, false, incr);
         if (e == cudaSuccess && h->opt.rho_policy == RVE_RHO_ADAPTIVE) e = admm::launch_local(h->L, fp64, true, true);
     }
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
@@ -227,13 +236,15 @@ int capture_chunk(rve* h, bool fp64) {
         if (g) cudaGraphDestroy(g);
         return RVE_E_CUDA;
     }
-    cudaError_t e3 = cudaGraphInstantiate(&h->graph[fp64 ? 1 : 0], g, 0);
+    cudaError_t e3 = cudaGraphInstantiate(&h->graph[slot], g, 0);
     cudaGraphDestroy(g);
     return e3 == cudaSuccess ? RVE_OK : RVE_E_CUDA;
 }
 
-// Run iterations in one precision until the device sets the stop flag.
-int run_phase(rve* h, bool fp64) {
+// Run iterations in one precision until the device sets the stop flag.  polish
+// (RVE_MIXED, fixed rho): after the first step, one full double projection,
+// then increment projections in float (see admm::launch_fft_incr).
+int run_phase(rve* h, bool fp64, bool polish = false) {
     if (h->prof) {
         if (ensure_prof_events(h)) return RVE_E_CUDA;
         const size_t last = h->pev.size() - 2;
@@ -247,24 +258,34 @@ int run_phase(rve* h, bool fp64) {
         return RVE_E_CUDA;
     }
     h->launches += 1;
+    if (polish) {
+        if (admm::launch_fft(h->L, true) != cudaSuccess) return RVE_E_CUDA;
+        if (admm::launch_local(h->L, true, false, false, true) != cudaSuccess) return RVE_E_CUDA;
+        h->launches += admm::fft_stages(h->dim) + 1;
+        const int rc = read_ctrl(h);
+        if (rc) return rc;
+        if (h->hctrl->done != admm::kRunning) return RVE_OK;
+    }
+    const int slot = polish ? 2 : (fp64 ? 1 : 0);
     for (;;) {
         h->launches += (long long)h->opt.check_every * launches_per_iteration(h);
         if (h->prof) {
-            const int rc = run_chunk_profiled(h, fp64);
+            const int rc = run_chunk_profiled(h, fp64, polish);
             if (rc) return rc;
             if (h->hctrl->done != admm::kRunning) return RVE_OK;
             continue;
         }
         if (h->opt.use_graph) {
-            if (!h->graph[fp64 ? 1 : 0]) {
-                const int rc = capture_chunk(h, fp64);
+            if (!h->graph[slot]) {
+                const int rc = capture_chunk(h, fp64, polish, slot);
                 if (rc) return rc;
             }
-            CK(cudaGraphLaunch(h->graph[fp64 ? 1 : 0], h->stream));
+            CK(cudaGraphLaunch(h->graph[slot], h->stream));
         } else {
             for (int i = 0; i < h->opt.check_every; ++i) {
-                if (admm::launch_fft(h->L, fp64) != cudaSuccess) return RVE_E_CUDA;
-                if (admm::launch_local(h->L, fp64, false, false) != cudaSuccess) return RVE_E_CUDA;
+                const cudaError_t fe = polish ? admm::launch_fft_incr(h->L) : admm::launch_fft(h->L, fp64);
+                if (fe != cudaSuccess) return RVE_E_CUDA;
+                if (admm::launch_local(h->L, fp64, false, false, polish) != cudaSuccess) return RVE_E_CUDA;
                 if (h->opt.rho_policy == RVE_RHO_ADAPTIVE &&
                     admm::launch_local(h->L, fp64, true, true) != cudaSuccess)
                     return RVE_E_CUDA;
@@ -389,6 +410,10 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
         L.tw32 = (const float2*)(b + lay.tw32);
         L.ksq32 = (const float*)(b + lay.ksq32);
     }
+    if (o.precision == RVE_MIXED) {
+        L.R32 = L.F32[0];
+        L.S32 = L.U32[0];
+    }
     const int H = n / 2;
     L.plan.n = n;
     L.plan.np_half = factor(H, L.plan.rad_half);
@@ -447,7 +472,7 @@ int rve_create_in(rve_t* out, int dim, int n, int model, const rve_options* opt,
 void rve_destroy(rve_t h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 3; ++i)
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
     if (h->own_ws && h->ws) cudaFree(h->ws);
     if (h->hctrl) cudaFreeHost(h->hctrl);
@@ -563,7 +588,7 @@ int rve_solve(rve_t h, const double Fbar[9], double rho, double tol, rve_solve_i
             h->hctrl->counter = 0;
             h->hctrl->newton_tol = o.newton_tol > 0 ? o.newton_tol : 1e-10;
             if (write_ctrl(h)) return RVE_E_CUDA;
-            rc = run_phase(h, true);
+            rc = run_phase(h, true, o.rho_policy == RVE_RHO_FIXED);
             if (rc) return rc;
             fp64_iters = (int)(h->hctrl->k - ksw);
         } else if (o.precision == RVE_FP64) {

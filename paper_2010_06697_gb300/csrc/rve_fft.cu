@@ -31,6 +31,8 @@
 // the host in double.
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "rve_internal.cuh"
 
 namespace admm {
@@ -201,7 +203,9 @@ __device__ __forceinline__ void load_twiddles(V* s_tw, const V* __restrict__ g_t
 
 // Divergence of Q = F_{k+1} - Lambda_k / rho (D^T Q = minus the central
 // divergence) and real-to-complex FFT along x, for `lpb` consecutive x-lines.
-template <typename T, int D>
+// INCR: Q is the increment R given in F0 (= F1), Lambda is not read, and the
+// spectrum goes to U0 (= U1).
+template <typename T, int D, bool INCR>
 __global__ void __launch_bounds__(kFftThreads)
 k_xfwd(const Ctrl* __restrict__ ctrl, const T* F0, const T* F1, const T* __restrict__ Lam, T* U0, T* U1,
        const typename Cx<T>::t* __restrict__ g_tw, FftPlan plan, int lpb) {
@@ -228,8 +232,8 @@ k_xfwd(const Ctrl* __restrict__ ctrl, const T* F0, const T* F1, const T* __restr
     for (int c = 0; c < D; ++c) {
         const T* F_c0 = F + (long long)(c * D + 0) * Vn;
         const T* F_c1 = F + (long long)(c * D + 1) * Vn;
-        const T* L_c0 = Lam + (long long)(c * D + 0) * Vn;
-        const T* L_c1 = Lam + (long long)(c * D + 1) * Vn;
+        const T* L_c0 = INCR ? nullptr : Lam + (long long)(c * D + 0) * Vn;
+        const T* L_c1 = INCR ? nullptr : Lam + (long long)(c * D + 1) * Vn;
         for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) {
             const int l = idx / n;
             const int x = idx - l * n;
@@ -240,15 +244,18 @@ k_xfwd(const Ctrl* __restrict__ ctrl, const T* F0, const T* F1, const T* __restr
                 const long long v = (long long)line * n + x;
                 const long long xp = v + (x + 1 == n ? 1 - n : 1), xm = v + (x == 0 ? n - 1 : -1);
                 const long long yp = v + (y + 1 == n ? (1 - n) * sn : sn), ym = v + (y == 0 ? (n - 1) * sn : -sn);
-                T q = (F_c0[xp] - F_c0[xm]) - (L_c0[xp] - L_c0[xm]) * inv_rho;
-                q += (F_c1[yp] - F_c1[ym]) - (L_c1[yp] - L_c1[ym]) * inv_rho;
+                T q = (F_c0[xp] - F_c0[xm]) + (F_c1[yp] - F_c1[ym]);
+                if (!INCR) q -= ((L_c0[xp] - L_c0[xm]) + (L_c1[yp] - L_c1[ym])) * inv_rho;
                 if constexpr (D == 3) {
                     const int z = line / n;
                     const T* F_c2 = F + (long long)(c * D + 2) * Vn;
-                    const T* L_c2 = Lam + (long long)(c * D + 2) * Vn;
                     const long long zp = v + (z + 1 == n ? (1 - n) * s2 : s2);
                     const long long zm = v + (z == 0 ? (n - 1) * s2 : -s2);
-                    q += (F_c2[zp] - F_c2[zm]) - (L_c2[zp] - L_c2[zm]) * inv_rho;
+                    q += F_c2[zp] - F_c2[zm];
+                    if (!INCR) {
+                        const T* L_c2 = Lam + (long long)(c * D + 2) * Vn;
+                        q -= (L_c2[zp] - L_c2[zm]) * inv_rho;
+                    }
                 }
                 r = -q * half_n;
             }
@@ -278,11 +285,14 @@ k_xfwd(const Ctrl* __restrict__ ctrl, const T* F0, const T* F1, const T* __restr
     }
 }
 
-// Complex-to-real inverse FFT along x, in place: spectrum lines -> u~_{k+1}.
-template <typename T, int D>
+// Complex-to-real inverse FFT along x.  Plain: in place, spectrum lines in the
+// buffer of u~_{k+1} (S0/S1 by parity) become u~_{k+1} (TO = T, O = S).
+// INCR: the spectrum of P(R) sits in S0; u~_{k+1} = u~_k + P(R) is written in
+// the precision TO of the state buffers O0/O1.
+template <typename T, typename TO, int D, bool INCR>
 __global__ void __launch_bounds__(kFftThreads)
-k_xinv(const Ctrl* __restrict__ ctrl, T* U0, T* U1, const typename Cx<T>::t* __restrict__ g_tw, FftPlan plan,
-       int lpb) {
+k_xinv(const Ctrl* __restrict__ ctrl, T* S0, T* S1, TO* O0, TO* O1, const typename Cx<T>::t* __restrict__ g_tw,
+       FftPlan plan, int lpb) {
     using V = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (ctrl->done) return;
@@ -290,8 +300,9 @@ k_xinv(const Ctrl* __restrict__ ctrl, T* U0, T* U1, const typename Cx<T>::t* __r
     const long long Vn = (D == 3) ? (long long)n * n * n : (long long)n * n;
     const int nlines = (D == 3) ? n * n : n;
     const int par = (int)(ctrl->k & 1);
-    T* Ur = par ? U0 : U1;
-    V* S = reinterpret_cast<V*>(Ur);
+    V* S = reinterpret_cast<V*>(INCR ? S0 : (par ? S0 : S1));
+    TO* Out = par ? O0 : O1;
+    const TO* In = par ? O1 : O0;
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* A = s_tw + n;
     V* B = A + lpb * H;
@@ -321,11 +332,18 @@ k_xinv(const Ctrl* __restrict__ ctrl, T* U0, T* U1, const typename Cx<T>::t* __r
         __syncthreads();
         V* X = stockham<true, false>(A, B, s_tw, H, plan.rad_half, plan.np_half, 2, lpb, H, 1);
         const T* Xr = reinterpret_cast<const T*>(X);
-        T* U_c = Ur + (long long)c * Vn;
+        TO* O_c = Out + (long long)c * Vn;
+        const TO* I_c = In + (long long)c * Vn;
         for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) {
             const int l = idx / n;
             const int line = line0 + l;
-            if (line < nlines) U_c[(long long)line * n + (idx - l * n)] = Xr[idx];
+            if (line < nlines) {
+                const long long o = (long long)line * n + (idx - l * n);
+                if (INCR)
+                    O_c[o] = I_c[o] + (TO)Xr[idx];
+                else
+                    O_c[o] = (TO)Xr[idx];
+            }
         }
         __syncthreads();
     }
@@ -446,8 +464,8 @@ cudaError_t run_fft(const Launch& L, int stage) {
     const int last = D == 3 ? 4 : 2;
     auto want = [&](int s) { return stage < 0 || stage == s; };
     if (want(0))
-        k_xfwd<T, D><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, A::F(L, 0), A::F(L, 1), A::Lm(L), A::U(L, 0),
-                                                         A::U(L, 1), A::tw(L), L.plan, lpb);
+        k_xfwd<T, D, false><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, A::F(L, 0), A::F(L, 1), A::Lm(L),
+                                                                A::U(L, 0), A::U(L, 1), A::tw(L), L.plan, lpb);
     if (D == 3) {
         if (want(1))
             k_faxis<T, D, 1, 0><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::tw(L),
@@ -463,7 +481,47 @@ cudaError_t run_fft(const Launch& L, int stage) {
                                                                 A::ksq(L), L.plan, tk, scale);
     }
     if (want(last))
-        k_xinv<T, D><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::tw(L), L.plan, lpb);
+        k_xinv<T, T, D, false><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::U(L, 0),
+                                                                   A::U(L, 1), A::tw(L), L.plan, lpb);
+    return cudaGetLastError();
+}
+
+// Float projection of the increment R (L.R32) added to the double u~ (double
+// polish of RVE_MIXED); same stage numbering as run_fft.
+template <int D>
+cudaError_t run_fft_incr(const Launch& L, int stage) {
+    using V = float2;
+    const int n = L.n, H = n / 2;
+    const int nlines = (D == 3) ? n * n : n;
+    const int lpb = lines_per_block(n, nlines);
+    const int gx = (nlines + lpb - 1) / lpb;
+    const size_t smx = (size_t)n * sizeof(V) + 2 * (size_t)lpb * H * sizeof(V);
+    const int tk = FftArgs<float>::tk < H ? FftArgs<float>::tk : H;
+    const size_t sma = (size_t)n * sizeof(V) + 2 * (size_t)n * tk * sizeof(V);
+    const dim3 ga((H + tk - 1) / tk, D == 3 ? n : 1, D);
+    const float scale = (float)(2.0 / (double)L.V);
+    const int last = D == 3 ? 4 : 2;
+    auto want = [&](int s) { return stage < 0 || stage == s; };
+    float* S = L.S32;
+    if (want(0))
+        k_xfwd<float, D, true><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, L.R32, L.R32, nullptr, S, S, L.tw32,
+                                                                   L.plan, lpb);
+    if (D == 3) {
+        if (want(1))
+            k_faxis<float, D, 1, 0><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, S, S, L.tw32, L.ksq32, L.plan, tk,
+                                                                        scale);
+        if (want(2))
+            k_faxis<float, D, 2, 2><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, S, S, L.tw32, L.ksq32, L.plan, tk,
+                                                                        scale);
+        if (want(3))
+            k_faxis<float, D, 1, 1><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, S, S, L.tw32, L.ksq32, L.plan, tk,
+                                                                        scale);
+    } else if (want(1)) {
+        k_faxis<float, D, 1, 2><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, S, S, L.tw32, L.ksq32, L.plan, tk, scale);
+    }
+    if (want(last))
+        k_xinv<float, double, D, true><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, S, S, L.U64[0], L.U64[1], L.tw32,
+                                                                           L.plan, lpb);
     return cudaGetLastError();
 }
 
@@ -474,8 +532,10 @@ cudaError_t set_smem_attrs(int bytes) {
         cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (r != cudaSuccess) e = r;
     };
-    set((const void*)k_xfwd<T, D>);
-    set((const void*)k_xinv<T, D>);
+    set((const void*)k_xfwd<T, D, false>);
+    set((const void*)k_xfwd<T, D, true>);
+    set((const void*)k_xinv<T, T, D, false>);
+    if (std::is_same<T, float>::value) set((const void*)k_xinv<float, double, D, true>);
     set((const void*)k_faxis<T, D, 1, 0>);
     set((const void*)k_faxis<T, D, 1, 1>);
     set((const void*)k_faxis<T, D, 1, 2>);
@@ -488,6 +548,10 @@ cudaError_t set_smem_attrs(int bytes) {
 cudaError_t launch_fft(const Launch& L, bool fp64, int stage) {
     if (fp64) return L.dim == 3 ? run_fft<double, 3>(L, stage) : run_fft<double, 2>(L, stage);
     return L.dim == 3 ? run_fft<float, 3>(L, stage) : run_fft<float, 2>(L, stage);
+}
+
+cudaError_t launch_fft_incr(const Launch& L, int stage) {
+    return L.dim == 3 ? run_fft_incr<3>(L, stage) : run_fft_incr<2>(L, stage);
 }
 
 // Allow the FFT kernels the dynamic shared memory the largest grid needs.

@@ -82,16 +82,22 @@ struct Launch {
     float* U32[2];
     const float2* tw32;
     const float* ksq32;
+    // double polish of RVE_MIXED: float increment R = F_{k+1} - G_k (d*d*V) and
+    // its float spectrum (d*V); both alias float state buffers idle in that phase
+    float* R32;
+    float* S32;
     FftPlan plan;
 };
 
 // rve_local.cu
 cudaError_t launch_init(const Launch& L, bool fp64, bool lambda_zero);
-cudaError_t launch_local(const Launch& L, bool fp64, bool first, bool only_if_rho_changed);
+cudaError_t launch_local(const Launch& L, bool fp64, bool first, bool only_if_rho_changed, bool write_r = false);
 cudaError_t launch_stress(const Launch& L, bool fp64);
 cudaError_t launch_convert(const Launch& L, bool to_fp64);
 // rve_fft.cu
 cudaError_t launch_fft(const Launch& L, bool fp64, int stage = -1);
+// Projection of the float increment R into the double u~: u~_{k+1} = u~_k + P(R).
+cudaError_t launch_fft_incr(const Launch& L, int stage = -1);
 inline int fft_stages(int dim) { return dim == 3 ? 5 : 3; }
 cudaError_t prepare_fft_kernels(int n);
 

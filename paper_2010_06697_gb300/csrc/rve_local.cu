@@ -14,6 +14,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "rve_internal.cuh"
 
 namespace admm {
@@ -102,9 +104,10 @@ __device__ __forceinline__ bool chol_solve(T* H, const T* g, T* x) {
 // ------------------------------------------------------------------ constitutive laws
 // Each law gives, for the local objective phi(F) = W(F) + rho/2 |F|^2 - B : F
 // (B = Lambda + rho G; the constant rho/2 |G|^2 is dropped):
-//   grad_hess: g = W_F(F) + rho F - B and the packed Hessian W_FF + rho I
-//   phi:       the objective (line search)
-//   stress:    W_F(F)
+//   grad:   g = W_F(F) + rho F - B in the field precision T, plus the auxiliary
+//           values (A = F^{-T}, J) the Hessian needs
+//   hess:   the packed Hessian W_FF + rho I, always in float (see newton())
+//   phi:    the objective (line search);  stress: W_F(F)
 
 // Compressible neo-Hookean, Section 4.1: W = mu/2 (|F|^2 - d - 2 ln J) + lam/2 (J-1)^2.
 // W_F = mu F + c F^{-T}, c = lam J (J-1) - mu;
@@ -112,31 +115,41 @@ __device__ __forceinline__ bool chol_solve(T* H, const T* g, T* x) {
 template <typename T, int D>
 struct NeoHooke {
     T mu, lam;
-    __device__ __forceinline__ bool grad_hess(const T* F, const T* B, T rho, T* g, T* H) const {
+    static constexpr int NAUX = D * D + 1;
+    __device__ __forceinline__ bool grad(const T* F, const T* B, T rho, T* g, T* aux) const {
         constexpr int NN = D * D;
-        T A[NN];
+        T* A = aux;
         const T J = det_cof<T, D>(F, A);
+        aux[NN] = J;
         if (!(J > T(0))) return false;
         const T iJ = T(1) / J;
 #pragma unroll
         for (int p = 0; p < NN; ++p) A[p] *= iJ;
         const T c = lam * J * (J - T(1)) - mu;
-        const T b = lam * (T(2) * J - T(1)) * J;
         const T a = mu + rho;
 #pragma unroll
         for (int p = 0; p < NN; ++p) g[p] = a * F[p] + c * A[p] - B[p];
+        return true;
+    }
+    __device__ __forceinline__ void hess(const float* aux, float rho, float* H) const {
+        constexpr int NN = D * D;
+        const float* A = aux;
+        const float J = aux[NN];
+        const float fm = (float)mu, fl = (float)lam;
+        const float c = fl * J * (J - 1.f) - fm;
+        const float b = fl * (2.f * J - 1.f) * J;
+        const float a = fm + rho;
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
             const int i = p / D, j = p % D;
 #pragma unroll
             for (int q = 0; q <= p; ++q) {
                 const int k = q / D, l = q % D;
-                T h = b * A[p] * A[q] - c * A[i * D + l] * A[k * D + j];
+                float h = b * A[p] * A[q] - c * A[i * D + l] * A[k * D + j];
                 if (p == q) h += a;
                 H[p * (p + 1) / 2 + q] = h;
             }
         }
-        return true;
     }
     __device__ __forceinline__ T phi(const T* F, const T* B, T rho, T J) const {
         T ff = 0, bf = 0;
@@ -162,7 +175,9 @@ struct NeoHooke {
 template <typename T, int D>
 struct Linear {
     T mu, lam;
-    __device__ __forceinline__ bool grad_hess(const T* F, const T* B, T rho, T* g, T* H) const {
+    static constexpr int NAUX = 1;
+    __device__ __forceinline__ bool grad(const T* F, const T* B, T rho, T* g, T* aux) const {
+        aux[0] = T(1);
         T tr = 0;
 #pragma unroll
         for (int i = 0; i < D; ++i) tr += F[i * D + i] - T(1);
@@ -174,18 +189,21 @@ struct Linear {
                 const T hji = F[j * D + i] - (i == j ? T(1) : T(0));
                 g[i * D + j] = mu * (hij + hji) + (i == j ? lam * tr : T(0)) + rho * F[i * D + j] - B[i * D + j];
             }
+        return true;
+    }
+    __device__ __forceinline__ void hess(const float* /*aux*/, float rho, float* H) const {
+        const float fm = (float)mu, fl = (float)lam;
 #pragma unroll
         for (int p = 0; p < D * D; ++p) {
             const int i = p / D, j = p % D;
 #pragma unroll
             for (int q = 0; q <= p; ++q) {
                 const int k = q / D, l = q % D;
-                T h = mu * (T(i == k && j == l) + T(i == l && j == k)) + lam * T(i == j && k == l);
+                float h = fm * (float(i == k && j == l) + float(i == l && j == k)) + fl * float(i == j && k == l);
                 if (p == q) h += rho;
                 H[p * (p + 1) / 2 + q] = h;
             }
         }
-        return true;
     }
     __device__ __forceinline__ T phi(const T* F, const T* B, T rho, T /*J*/) const {
         T e2 = 0, tr = 0, ff = 0, bf = 0;
@@ -238,23 +256,46 @@ struct NewtonConst<double> { static constexpr double big = 1e-2; };
 template <>
 struct NewtonConst<float> { static constexpr float big = 1e-2f; };
 
-// Damped Newton for phi at one voxel, starting from F (overwritten).  Steps
-// larger than NewtonConst::big take an Armijo backtracking line search on phi;
-// every step keeps J = det F > 0.  Stops after a full step with max|dF| <= tol.
-// Returns the number of Newton steps; conv tells whether the test was met.
+// Damped Newton for phi at one voxel, starting from F (overwritten).
+//
+// The gradient, the objective and the update are evaluated in the field
+// precision T; the Hessian is assembled and factored in float.  For T = float
+// this is plain Newton.  For T = double it is Newton with mixed-precision
+// iterative refinement: each step solves H_f dx = -g with the float factor of
+// the Hessian and the double gradient, so the iteration still converges to the
+// double-precision stationary point g = 0 (the float factor only slows the
+// quadratic rate to a linear rate of about eps_float * cond(H) per step, which
+// the tolerance test absorbs), at a fraction of the double arithmetic.
+//
+// Steps larger than NewtonConst::big take an Armijo backtracking line search on
+// phi; every step keeps J = det F > 0.  Stops after a full step with
+// max|dF| <= tol.  Returns the number of Newton steps; conv tells whether the
+// test was met.
 template <typename T, int D, typename Law>
 __device__ __forceinline__ int newton(const Law& m, T* F, const T* B, T rho, int cap, T tol, bool& conv) {
     constexpr int NN = D * D;
     constexpr int NP = NN * (NN + 1) / 2;
+    constexpr int NAUX = Law::NAUX;
     conv = false;
     int it = 0;
     while (it < cap) {
-        T g[NN], H[NP], dx[NN];
-        if (!m.grad_hess(F, B, rho, g, H)) break;
-        if (!chol_solve<T, NN>(H, g, dx)) {
-            const T s = T(1) / (m.modulus() + rho);
+        T g[NN], aux[NAUX], dx[NN];
+        if (!m.grad(F, B, rho, g, aux)) break;
+        {
+            float Hf[NP], gf[NN], af[NAUX], df[NN];
 #pragma unroll
-            for (int p = 0; p < NN; ++p) dx[p] = -g[p] * s;
+            for (int p = 0; p < NAUX; ++p) af[p] = (float)aux[p];
+#pragma unroll
+            for (int p = 0; p < NN; ++p) gf[p] = (float)g[p];
+            m.hess(af, (float)rho, Hf);
+            if (chol_solve<float, NN>(Hf, gf, df)) {
+#pragma unroll
+                for (int p = 0; p < NN; ++p) dx[p] = (T)df[p];
+            } else {
+                const T s = T(1) / (m.modulus() + rho);
+#pragma unroll
+                for (int p = 0; p < NN; ++p) dx[p] = -g[p] * s;
+            }
         }
         T slope = 0, size = 0;
 #pragma unroll
@@ -405,11 +446,15 @@ k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const 
 // (F_{k+1} from F_k, Lambda_k, u~_k): at the start of a solve, after a precision
 // switch, and (only_if_rho_changed) to redo the speculative step when the
 // adaptive rule changed rho.
-template <typename T, int D, int MODEL, bool FIRST>
+//
+// WRITE_R (double polish of RVE_MIXED): also store R = F_{k+2} - G_{k+1} in
+// float.  With rho fixed, Q_{k+2} - Q_{k+1} = R for Q = F - Lambda/rho, so the
+// next projection only has to transform this small increment (see rve_fft.cu).
+template <typename T, int D, int MODEL, bool FIRST, bool WRITE_R>
 __global__ void __launch_bounds__(kLocalThreads)
 k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__ partials, T* F0, T* F1, T* Lam,
         const T* U0, const T* U1, const uint8_t* __restrict__ phase, const double* __restrict__ mat, int nparam,
-        int n, long long V, int only_if_rho_changed) {
+        int n, long long V, int only_if_rho_changed, float* __restrict__ Rout) {
     using Law = typename LawOf<T, D, MODEL>::type;
     constexpr int NN = D * D;
     __shared__ double s_sum[kLocalThreads / 32][2];
@@ -477,6 +522,10 @@ k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__
         nfail += conv ? 0 : 1;
 #pragma unroll
         for (int p = 0; p < NN; ++p) Fnext[p * V + v] = F[p];
+        if constexpr (WRITE_R) {
+#pragma unroll
+            for (int p = 0; p < NN; ++p) Rout[p * V + v] = (float)(F[p] - G[p]);
+        }
     }
     if (FIRST) return;
 
@@ -717,15 +766,19 @@ cudaError_t run_init(const Launch& L, bool lambda_zero) {
 }
 
 template <typename T, int D, int MODEL>
-cudaError_t run_local(const Launch& L, bool first, bool only_if) {
+cudaError_t run_local(const Launch& L, bool first, bool only_if, bool write_r) {
     if (first)
-        k_local<T, D, MODEL, true><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
+        k_local<T, D, MODEL, true, false><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
             L.ctrl, L.hist, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0),
-            Set<T>::U(L, 1), L.phase, L.mat, L.nparam, L.n, L.V, only_if ? 1 : 0);
+            Set<T>::U(L, 1), L.phase, L.mat, L.nparam, L.n, L.V, only_if ? 1 : 0, nullptr);
+    else if (write_r && std::is_same<T, double>::value)
+        k_local<T, D, MODEL, false, true><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
+            L.ctrl, L.hist, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0),
+            Set<T>::U(L, 1), L.phase, L.mat, L.nparam, L.n, L.V, 0, L.R32);
     else
-        k_local<T, D, MODEL, false><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
+        k_local<T, D, MODEL, false, false><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
             L.ctrl, L.hist, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0),
-            Set<T>::U(L, 1), L.phase, L.mat, L.nparam, L.n, L.V, 0);
+            Set<T>::U(L, 1), L.phase, L.mat, L.nparam, L.n, L.V, 0, nullptr);
     return cudaGetLastError();
 }
 
@@ -752,9 +805,9 @@ cudaError_t launch_init(const Launch& L, bool fp64, bool lambda_zero) {
     RVE_DISPATCH(run_init, float, L, lambda_zero);
 }
 
-cudaError_t launch_local(const Launch& L, bool fp64, bool first, bool only_if_rho_changed) {
-    if (fp64) RVE_DISPATCH(run_local, double, L, first, only_if_rho_changed);
-    RVE_DISPATCH(run_local, float, L, first, only_if_rho_changed);
+cudaError_t launch_local(const Launch& L, bool fp64, bool first, bool only_if_rho_changed, bool write_r) {
+    if (fp64) RVE_DISPATCH(run_local, double, L, first, only_if_rho_changed, write_r);
+    RVE_DISPATCH(run_local, float, L, first, only_if_rho_changed, false);
 }
 
 cudaError_t launch_stress(const Launch& L, bool fp64) {

@@ -103,7 +103,8 @@ SIGNATURES = {
     "rve_kernel_times": (_I, [_VP, _I, _PD, ctypes.POINTER(ctypes.c_longlong), _I]),
 }
 
-KCLASS_NAMES = ["local", "local_first", "xfwd", "fwd_y", "solve", "inv_y", "xinv"]
+KCLASS_NAMES = ["local", "local_first", "xfwd", "fwd_y", "solve", "inv_y", "xinv", "local_r", "xfwd_incr",
+                "xinv_incr"]
 
 _lib = None
 
