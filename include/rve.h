@@ -197,6 +197,28 @@ int rve_set_profiling(rve_t h, int on);
  * of classes written or RVE_E_INVALID_ARG. */
 int rve_kernel_times(rve_t h, int fp64, double* ms, long long* launches, int cap);
 
+/* ------------------------------------------------------------------ no-allocation variant */
+/* <W_F(F)> (first Piola-Kirchhoff, row-major 3x3, zero outside the d x d block)
+ * for callers that cannot allocate device memory: an application that owns all
+ * device memory through its own pool and forbids further allocations, or a
+ * latency-critical loop that must not call cudaMalloc/cudaFree because they may
+ * synchronise the device.  The paper has no counterpart; this is a systems entry
+ * point, with the same result as rve_stress on the same F.
+ * Inputs, all DEVICE pointers owned by the caller: F_dev (d*d*N^d doubles, the
+ * field layout above), phase_dev (N^d bytes, values < nphase), params_dev
+ * (nphase * nparam doubles, {mu, lam} first).  Output: S_dev (9 doubles, device).
+ * model is RVE_NEOHOOKE or RVE_LINEAR.  Work is queued on cuda_stream (NULL =
+ * legacy default stream); the call returns without waiting for it.
+ * Nothing is allocated: block partial sums go to a static device array of 2 MiB
+ * (+256 B) that every GPU loading this library holds until exit, which limits
+ * N^d to 16,777,216 voxels (256^3); larger sizes return RVE_E_INVALID_ARG.  The
+ * first call on each device looks up that array's address (call it once before
+ * any stream capture).  All calls share the array and clear its header on
+ * entry: calls whose work overlaps on the GPU race, so serialise them (e.g. one
+ * stream).  A phase id >= nphase makes the result NaN. */
+int rve_stress_noalloc(int dim, int n, int model, const double* F_dev, const uint8_t* phase_dev,
+                       const double* params_dev, int nphase, int nparam, double* S_dev, void* cuda_stream);
+
 /* Human-readable name of a status code (static string). */
 const char* rve_strerror(int code);
 

@@ -100,6 +100,7 @@ SIGNATURES = {
     "rve_history": (_I, [_VP, _PD, _PD, _PD, _I]),
     "rve_strerror": (ctypes.c_char_p, [_I]),
     "rve_set_profiling": (_I, [_VP, _I]),
+    "rve_stress_noalloc": (_I, [_I, _I, _I, _VP, _VP, _VP, _I, _I, _VP, _VP]),
     "rve_kernel_times": (_I, [_VP, _I, _PD, ctypes.POINTER(ctypes.c_longlong), _I]),
 }
 
@@ -225,6 +226,12 @@ def rve_history(h, cap):
     if cnt < 0:
         return cnt, None
     return cnt, np.stack([rp[:cnt], rd[:cnt], rho[:cnt]], axis=1)
+
+
+def rve_stress_noalloc(dim, n, model, F_ptr, phase_ptr, params_ptr, nphase, nparam, S_ptr, stream=None):
+    """Device pointers in, device pointer out; see include/rve.h (no device allocation)."""
+    return lib().rve_stress_noalloc(dim, n, model, _VP(F_ptr), _VP(phase_ptr), _VP(params_ptr), nphase, nparam,
+                                    _VP(S_ptr), _VP(stream or 0))
 
 
 def rve_set_profiling(h, on):
