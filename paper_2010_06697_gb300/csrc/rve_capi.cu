@@ -193,7 +193,7 @@ int run_chunk_profiled(rve* h, bool fp64, bool incr) {
             if (le != cudaSuccess) return RVE_E_CUDA;
             CK(cudaEventRecord(e[1 + st], h->stream));
         }
-        if (admm::launch_local(h->L, fp64, false, false, incr) != cudaSuccess) return RVE_E_CUDA;
+        if (admm::launch_local(h->L, fp64, false, false, incr ? 2 : 0) != cudaSuccess) return RVE_E_CUDA;
         CK(cudaEventRecord(e[1 + S], h->stream));
         if (h->opt.rho_policy == RVE_RHO_ADAPTIVE) {
             if (admm::launch_local(h->L, fp64, true, true) != cudaSuccess) return RVE_E_CUDA;
@@ -228,7 +228,7 @@ int capture_chunk(rve* h, bool fp64, bool incr, int slot) {
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < h->opt.check_every && e == cudaSuccess; ++i) {
         e = incr ? admm::launch_fft_incr(h->L) : admm::launch_fft(h->L, fp64);
-        if (e == cudaSuccess) e = admm::launch_local(h->L, fp64, false, false, incr);
+        if (e == cudaSuccess) e = admm::launch_local(h->L, fp64, false, false, incr ? 2 : 0);
         if (e == cudaSuccess && h->opt.rho_policy == RVE_RHO_ADAPTIVE) e = admm::launch_local(h->L, fp64, true, true);
     }
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
@@ -260,7 +260,7 @@ int run_phase(rve* h, bool fp64, bool polish = false) {
     h->launches += 1;
     if (polish) {
         if (admm::launch_fft(h->L, true) != cudaSuccess) return RVE_E_CUDA;
-        if (admm::launch_local(h->L, true, false, false, true) != cudaSuccess) return RVE_E_CUDA;
+        if (admm::launch_local(h->L, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
         h->launches += admm::fft_stages(h->dim) + 1;
         const int rc = read_ctrl(h);
         if (rc) return rc;
@@ -285,7 +285,7 @@ int run_phase(rve* h, bool fp64, bool polish = false) {
             for (int i = 0; i < h->opt.check_every; ++i) {
                 const cudaError_t fe = polish ? admm::launch_fft_incr(h->L) : admm::launch_fft(h->L, fp64);
                 if (fe != cudaSuccess) return RVE_E_CUDA;
-                if (admm::launch_local(h->L, fp64, false, false, polish) != cudaSuccess) return RVE_E_CUDA;
+                if (admm::launch_local(h->L, fp64, false, false, polish ? 2 : 0) != cudaSuccess) return RVE_E_CUDA;
                 if (h->opt.rho_policy == RVE_RHO_ADAPTIVE &&
                     admm::launch_local(h->L, fp64, true, true) != cudaSuccess)
                     return RVE_E_CUDA;
@@ -413,6 +413,7 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
     if (o.precision == RVE_MIXED) {
         L.R32 = L.F32[0];
         L.S32 = L.U32[0];
+        L.D32 = L.U32[1];
     }
     const int H = n / 2;
     L.plan.n = n;
@@ -586,7 +587,9 @@ int rve_solve(rve_t h, const double Fbar[9], double rho, double tol, rve_solve_i
             h->hctrl->done = admm::kRunning;
             h->hctrl->phase_fp32 = 0;
             h->hctrl->counter = 0;
-            h->hctrl->newton_tol = o.newton_tol > 0 ? o.newton_tol : 1e-10;
+            // polish: a step of max|dF| <= 1e-7 leaves an error of about 1e-6 * 1e-7 (float
+            // Hessian) + |dF|^2, i.e. ~1e-13, far below the double residual tolerance
+            h->hctrl->newton_tol = o.newton_tol > 0 ? o.newton_tol : 1e-7;
             if (write_ctrl(h)) return RVE_E_CUDA;
             rc = run_phase(h, true, o.rho_policy == RVE_RHO_FIXED);
             if (rc) return rc;

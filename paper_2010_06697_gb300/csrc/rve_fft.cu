@@ -289,10 +289,11 @@ k_xfwd(const Ctrl* __restrict__ ctrl, const T* F0, const T* F1, const T* __restr
 // buffer of u~_{k+1} (S0/S1 by parity) become u~_{k+1} (TO = T, O = S).
 // INCR: the spectrum of P(R) sits in S0; u~_{k+1} = u~_k + P(R) is written in
 // the precision TO of the state buffers O0/O1.
+// INCR also stores the float increment itself in DUout (read by the next local step for r_d).
 template <typename T, typename TO, int D, bool INCR>
 __global__ void __launch_bounds__(kFftThreads)
 k_xinv(const Ctrl* __restrict__ ctrl, T* S0, T* S1, TO* O0, TO* O1, const typename Cx<T>::t* __restrict__ g_tw,
-       FftPlan plan, int lpb) {
+       FftPlan plan, int lpb, T* __restrict__ DUout) {
     using V = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (ctrl->done) return;
@@ -339,9 +340,10 @@ k_xinv(const Ctrl* __restrict__ ctrl, T* S0, T* S1, TO* O0, TO* O1, const typena
             const int line = line0 + l;
             if (line < nlines) {
                 const long long o = (long long)line * n + (idx - l * n);
-                if (INCR)
+                if (INCR) {
                     O_c[o] = I_c[o] + (TO)Xr[idx];
-                else
+                    DUout[(long long)c * Vn + o] = Xr[idx];
+                } else
                     O_c[o] = (TO)Xr[idx];
             }
         }
@@ -482,7 +484,7 @@ cudaError_t run_fft(const Launch& L, int stage) {
     }
     if (want(last))
         k_xinv<T, T, D, false><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::U(L, 0),
-                                                                   A::U(L, 1), A::tw(L), L.plan, lpb);
+                                                                   A::U(L, 1), A::tw(L), L.plan, lpb, nullptr);
     return cudaGetLastError();
 }
 
@@ -521,7 +523,7 @@ cudaError_t run_fft_incr(const Launch& L, int stage) {
     }
     if (want(last))
         k_xinv<float, double, D, true><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, S, S, L.U64[0], L.U64[1], L.tw32,
-                                                                           L.plan, lpb);
+                                                                           L.plan, lpb, L.D32);
     return cudaGetLastError();
 }
 

@@ -86,12 +86,15 @@ struct Launch {
     // its float spectrum (d*V); both alias float state buffers idle in that phase
     float* R32;
     float* S32;
+    float* D32;  // float u~ increment of the last increment projection (d*V)
     FftPlan plan;
 };
 
 // rve_local.cu
 cudaError_t launch_init(const Launch& L, bool fp64, bool lambda_zero);
-cudaError_t launch_local(const Launch& L, bool fp64, bool first, bool only_if_rho_changed, bool write_r = false);
+// polish_mode (double only): 0 plain; 1 also write R; 2 also write R and take
+// r_d from the float u~ increment D32 (see k_local).
+cudaError_t launch_local(const Launch& L, bool fp64, bool first, bool only_if_rho_changed, int polish_mode = 0);
 cudaError_t launch_stress(const Launch& L, bool fp64);
 cudaError_t launch_convert(const Launch& L, bool to_fp64);
 // rve_fft.cu

@@ -169,6 +169,13 @@ struct NeoHooke {
         for (int p = 0; p < D * D; ++p) P[p] = mu * F[p] + c * A[p];
     }
     __device__ __forceinline__ T modulus() const { return mu; }
+    // det(F + dF) > 0 is certain when |F^{-1} dF| < 1/2: |F^{-1} dF|_2 <= |A|_F * d * max|dF|
+    __device__ __forceinline__ bool small_step_safe(const float* aux, float size) const {
+        float a2 = 0.f;
+#pragma unroll
+        for (int p = 0; p < D * D; ++p) a2 += aux[p] * aux[p];
+        return (float)D * size * sqrtf(a2) < 0.5f;
+    }
 };
 
 // Isotropic linear elasticity in H = F - I: W = mu |sym H|^2 + lam/2 (tr H)^2.
@@ -231,6 +238,9 @@ struct Linear {
                 P[i * D + j] = mu * (F[i * D + j] + F[j * D + i] - T(2) * T(i == j)) + (i == j ? lam * tr : T(0));
     }
     __device__ __forceinline__ T modulus() const { return mu; }
+    // no positivity requirement on J for linear elasticity, but J > 0 is kept like
+    // for the other laws: small steps from a state with J > 0 are accepted directly
+    __device__ __forceinline__ bool small_step_safe(const float*, float size) const { return size < 1e-2f; }
 };
 
 template <typename T, int D, int MODEL>
@@ -279,69 +289,69 @@ __device__ __forceinline__ int newton(const Law& m, T* F, const T* B, T rho, int
     conv = false;
     int it = 0;
     while (it < cap) {
-        T g[NN], aux[NAUX], dx[NN];
+        T g[NN], aux[NAUX];
         if (!m.grad(F, B, rho, g, aux)) break;
+        float df[NN], gf[NN], af[NAUX];
         {
-            float Hf[NP], gf[NN], af[NAUX], df[NN];
+            float Hf[NP];
 #pragma unroll
             for (int p = 0; p < NAUX; ++p) af[p] = (float)aux[p];
 #pragma unroll
             for (int p = 0; p < NN; ++p) gf[p] = (float)g[p];
             m.hess(af, (float)rho, Hf);
-            if (chol_solve<float, NN>(Hf, gf, df)) {
+            if (!chol_solve<float, NN>(Hf, gf, df)) {
+                const float s = 1.f / (float)(m.modulus() + rho);
 #pragma unroll
-                for (int p = 0; p < NN; ++p) dx[p] = (T)df[p];
-            } else {
-                const T s = T(1) / (m.modulus() + rho);
-#pragma unroll
-                for (int p = 0; p < NN; ++p) dx[p] = -g[p] * s;
+                for (int p = 0; p < NN; ++p) df[p] = -gf[p] * s;
             }
         }
-        T slope = 0, size = 0;
+        // slope and step size only steer the line search and the stopping test: float suffices
+        float slope = 0.f, size = 0.f;
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
-            slope += g[p] * dx[p];
-            size = fmax(size, fabs(dx[p]));
+            slope += gf[p] * df[p];
+            size = fmaxf(size, fabsf(df[p]));
         }
-        if (!(slope < T(0))) {  // not a descent direction: steepest descent (Section 2.1's local method)
-            const T s = T(1) / (m.modulus() + rho);
-            slope = 0;
-            size = 0;
+        if (!(slope < 0.f)) {  // not a descent direction: steepest descent (Section 2.1's local method)
+            const float s = 1.f / (float)(m.modulus() + rho);
+            slope = 0.f;
+            size = 0.f;
 #pragma unroll
             for (int p = 0; p < NN; ++p) {
-                dx[p] = -g[p] * s;
-                slope += g[p] * dx[p];
-                size = fmax(size, fabs(dx[p]));
+                df[p] = -gf[p] * s;
+                slope += gf[p] * df[p];
+                size = fmaxf(size, fabsf(df[p]));
             }
         }
-        if (!(size < T(1e30))) break;  // NaN or overflow
+        if (!(size < 1e30f)) break;  // NaN or overflow
         T t = T(1);
-        T Ft[NN];
-        if (size > NewtonConst<T>::big) {
+        if (size > (float)NewtonConst<T>::big) {
+            T Ft[NN];
             const T phi0 = m.phi(F, B, rho, det<T, D>(F));
             int ls = 0;
             for (; ls < 40; ++ls) {
 #pragma unroll
-                for (int p = 0; p < NN; ++p) Ft[p] = F[p] + t * dx[p];
+                for (int p = 0; p < NN; ++p) Ft[p] = F[p] + t * (T)df[p];
                 const T Jt = det<T, D>(Ft);
-                if (Jt > T(0) && m.phi(Ft, B, rho, Jt) <= phi0 + T(1e-4) * t * slope) break;
+                if (Jt > T(0) && m.phi(Ft, B, rho, Jt) <= phi0 + T(1e-4) * t * (T)slope) break;
                 t *= T(0.5);
             }
             if (ls == 40) t = T(0);
-        } else {
+        } else if (!m.small_step_safe(af, size)) {
+            T Ft[NN];
             int ls = 0;
             for (; ls < 40; ++ls) {
 #pragma unroll
-                for (int p = 0; p < NN; ++p) Ft[p] = F[p] + t * dx[p];
+                for (int p = 0; p < NN; ++p) Ft[p] = F[p] + t * (T)df[p];
                 if (det<T, D>(Ft) > T(0)) break;
                 t *= T(0.5);
             }
             if (ls == 40) t = T(0);
         }
 #pragma unroll
-        for (int p = 0; p < NN; ++p) F[p] += t * dx[p];
+        for (int p = 0; p < NN; ++p) F[p] += t * (T)df[p];
         ++it;
-        if (t == T(1) && size <= tol) {
+        if (t == T(1) && size <= (float)tol) {
             conv = true;
             break;
         }
@@ -450,11 +460,15 @@ k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const 
 // WRITE_R (double polish of RVE_MIXED): also store R = F_{k+2} - G_{k+1} in
 // float.  With rho fixed, Q_{k+2} - Q_{k+1} = R for Q = F - Lambda/rho, so the
 // next projection only has to transform this small increment (see rve_fft.cu).
-template <typename T, int D, int MODEL, bool FIRST, bool WRITE_R>
+//
+// DU (same polish, after its first iteration): the float increment
+// u~_{k+1} - u~_k written by the increment projection is read instead of u~_k,
+// and G_{k+1} - G_k = D(u~_{k+1} - u~_k) for r_d is formed in float.
+template <typename T, int D, int MODEL, bool FIRST, bool WRITE_R, bool DU>
 __global__ void __launch_bounds__(kLocalThreads)
 k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__ partials, T* F0, T* F1, T* Lam,
         const T* U0, const T* U1, const uint8_t* __restrict__ phase, const double* __restrict__ mat, int nparam,
-        int n, long long V, int only_if_rho_changed, float* __restrict__ Rout) {
+        int n, long long V, int only_if_rho_changed, float* __restrict__ Rout, const float* __restrict__ DUin) {
     using Law = typename LawOf<T, D, MODEL>::type;
     constexpr int NN = D * D;
     __shared__ double s_sum[kLocalThreads / 32][2];
@@ -500,17 +514,34 @@ k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__
             F[p] = Fcur[p * V + v];
         }
         if (!FIRST) {
-            T Go[NN];
-            grad_u<T, D>(Uold, V, nb, Fb, half_n, Go);
+            // squares are summed per voxel in T (9 terms) and the voxel sums in double
+            T sp = T(0), sd = T(0);
 #pragma unroll
             for (int p = 0; p < NN; ++p) {
                 const T df = G[p] - F[p];
-                const T dg = G[p] - Go[p];
                 L[p] += rho * df;
-                rp2 += (double)df * (double)df;
-                rd2 += (double)dg * (double)dg;
+                sp += df * df;
                 Lam[p * V + v] = L[p];
             }
+            if constexpr (DU) {
+                const float zero[NN] = {};
+                float dG[NN];
+                grad_u<float, D>(DUin, V, nb, zero, 0.5f * (float)n, dG);
+                float sdf = 0.f;
+#pragma unroll
+                for (int p = 0; p < NN; ++p) sdf += dG[p] * dG[p];
+                sd = (T)sdf;
+            } else {
+                T Go[NN];
+                grad_u<T, D>(Uold, V, nb, Fb, half_n, Go);
+#pragma unroll
+                for (int p = 0; p < NN; ++p) {
+                    const T dg = G[p] - Go[p];
+                    sd += dg * dg;
+                }
+            }
+            rp2 += (double)sp;
+            rd2 += (double)sd;
         }
         const Law m = load_law<Law, T>(phase, mat, nparam, v);
         T B[NN];
@@ -765,20 +796,25 @@ cudaError_t run_init(const Launch& L, bool lambda_zero) {
     return cudaGetLastError();
 }
 
+// mode: 0 plain, 1 write R (first polish iteration), 2 write R and read the float u~ increment
 template <typename T, int D, int MODEL>
-cudaError_t run_local(const Launch& L, bool first, bool only_if, bool write_r) {
+cudaError_t run_local(const Launch& L, bool first, bool only_if, int mode) {
+#define RVE_LOCAL_ARGS                                                                                          \
+    L.ctrl, L.hist, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0), Set<T>::U(L, 1), \
+        L.phase, L.mat, L.nparam, L.n, L.V
     if (first)
-        k_local<T, D, MODEL, true, false><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
-            L.ctrl, L.hist, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0),
-            Set<T>::U(L, 1), L.phase, L.mat, L.nparam, L.n, L.V, only_if ? 1 : 0, nullptr);
-    else if (write_r && std::is_same<T, double>::value)
-        k_local<T, D, MODEL, false, true><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
-            L.ctrl, L.hist, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0),
-            Set<T>::U(L, 1), L.phase, L.mat, L.nparam, L.n, L.V, 0, L.R32);
+        k_local<T, D, MODEL, true, false, false>
+            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, only_if ? 1 : 0, nullptr, nullptr);
+    else if (mode == 1 && std::is_same<T, double>::value)
+        k_local<T, D, MODEL, false, true, false>
+            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, 0, L.R32, nullptr);
+    else if (mode == 2 && std::is_same<T, double>::value)
+        k_local<T, D, MODEL, false, true, true>
+            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, 0, L.R32, L.D32);
     else
-        k_local<T, D, MODEL, false, false><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
-            L.ctrl, L.hist, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0),
-            Set<T>::U(L, 1), L.phase, L.mat, L.nparam, L.n, L.V, 0, nullptr);
+        k_local<T, D, MODEL, false, false, false>
+            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, 0, nullptr, nullptr);
+#undef RVE_LOCAL_ARGS
     return cudaGetLastError();
 }
 
@@ -805,9 +841,9 @@ cudaError_t launch_init(const Launch& L, bool fp64, bool lambda_zero) {
     RVE_DISPATCH(run_init, float, L, lambda_zero);
 }
 
-cudaError_t launch_local(const Launch& L, bool fp64, bool first, bool only_if_rho_changed, bool write_r) {
-    if (fp64) RVE_DISPATCH(run_local, double, L, first, only_if_rho_changed, write_r);
-    RVE_DISPATCH(run_local, float, L, first, only_if_rho_changed, false);
+cudaError_t launch_local(const Launch& L, bool fp64, bool first, bool only_if_rho_changed, int polish_mode) {
+    if (fp64) RVE_DISPATCH(run_local, double, L, first, only_if_rho_changed, polish_mode);
+    RVE_DISPATCH(run_local, float, L, first, only_if_rho_changed, 0);
 }
 
 cudaError_t launch_stress(const Launch& L, bool fp64) {
