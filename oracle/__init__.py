@@ -6,5 +6,6 @@ the CPU-baseline leg of ``bench.py`` may import it.  It shares no code with the
 CUDA library and never imports the solver package.
 """
 from .admm import (admm_solve, u_step, grad_u, grad_from_spectrum, local_newton, wavenumbers,
-                   rms, initial_state, homogenised_stress)
-from .materials import NeoHookean, LinearElastic, make_material
+                   rms, initial_state, homogenised_stress, local_newton_lce, frank_force,
+                   tangent_basis, retract)
+from .materials import NeoHookean, LinearElastic, LCE, make_material, make_lce

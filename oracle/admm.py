@@ -43,7 +43,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .materials import make_material
+from .materials import make_lce, make_material
 
 # --------------------------------------------------------------------------- discrete symbols
 
@@ -186,6 +186,122 @@ def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, smal
     return F, iters
 
 
+# --------------------------------------------------------------------------- Step 1 for the LCE (F and director n)
+
+
+def frank_force(n_field: np.ndarray, kappa: np.ndarray) -> np.ndarray:
+    """Explicit Frank force at every voxel from the director field of iterate i
+    (eq. kin2: the gradient of the internal variable is taken from the previous
+    iterate).  The discrete Frank energy kappa sum_edges |n(x + h e_j) - n(x)|^2 / h^2
+    restricted to |n(x)| = 1 with the neighbours frozen is const - f . n(x) with
+
+        f(x) = 2 kappa / h^2 * sum of the 2d neighbours' directors,
+
+    which equals 2 kappa Delta_h n_i up to a multiple of n_i (the same tangential
+    force, hence the same fixed points).  n_field (3, *grid); returns (V, 3)."""
+    d = n_field.ndim - 1
+    N = n_field.shape[-1]
+    s = np.zeros_like(n_field)
+    for ax in range(1, d + 1):
+        s = s + np.roll(n_field, 1, axis=ax) + np.roll(n_field, -1, axis=ax)
+    return (2.0 * N * N) * np.asarray(kappa)[:, None] * s.reshape(3, -1).T
+
+
+def tangent_basis(n: np.ndarray):
+    """Orthonormal (a, b) spanning the plane normal to each unit vector n (V, 3):
+    Gram-Schmidt of the coordinate axis least aligned with n, b = n x a."""
+    k = np.argmin(np.abs(n), axis=1)
+    e = np.zeros_like(n)
+    e[np.arange(n.shape[0]), k] = 1.0
+    a = e - np.sum(e * n, axis=1)[:, None] * n
+    a = a / np.linalg.norm(a, axis=1)[:, None]
+    b = np.cross(n, a)
+    return a, b
+
+
+def retract(n, a, b, t1, t2):
+    """Move on the unit sphere: normalise(n + t1 a + t2 b)."""
+    v = n + t1[:, None] * a + t2[:, None] * b
+    return v / np.linalg.norm(v, axis=1)[:, None]
+
+
+def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60, armijo=1e-4, small_step=1e-7):
+    """Step 1 (eqs. eq and kin with the Frank gradient treated explicitly, eq. kin2) for
+    the LCE at every voxel: minimise over F and the unit director n
+
+        phi(F, n) = W(F, n) - force . n - Lam : F + rho/2 |F - G|^2,
+
+    force: the explicit Frank force from the previous director field (frank_force).  Newton on the 11 unknowns (F, t) with n = normalise(n + t1 a + t2 b),
+    (a, b) a basis of the tangent plane at the current n: the reduced Hessian adds the
+    sphere's curvature term -(n . phi_n) I, plus a shift 1e-6 mu I on that block.  Backtracking keeps J > 0 and the Armijo
+    decrease; steepest descent when Newton's direction does not descend.
+    F0, Lam, G (V,3,3); n_init, force (V,3).  Returns (F, n, iters)."""
+    V = F0.shape[0]
+    F = F0.copy()
+    n = n_init.copy()
+    iters = np.zeros(V, dtype=np.int64)
+    active = np.ones(V, dtype=bool)
+
+    def phi(sub, Fs, ns, Lam_s, G_s, f_s):
+        return (sub.W(Fs, ns) - np.sum(f_s * ns, axis=1) - np.einsum("vij,vij->v", Lam_s, Fs)
+                + 0.5 * rho * np.einsum("vij,vij->v", Fs - G_s, Fs - G_s))
+
+    for _ in range(cap):
+        idx = np.nonzero(active)[0]
+        if idx.size == 0:
+            break
+        sub = mat.subset(idx)
+        Fa, na = F[idx], n[idx]
+        Lam_s, G_s, f_s = Lam[idx], G[idx], force[idx]
+        P, Wn, WFF, WFn, Wnn = sub.derivatives(Fa, na)
+        gF = P - Lam_s + rho * (Fa - G_s)
+        gn = Wn - f_s
+        a, b = tangent_basis(na)
+        E = np.stack([a, b], axis=2)                                   # (v, 3, 2)
+        gt = np.einsum("vk,vka->va", gn, E)
+        Htt = np.einsum("vka,vkp,vpb->vab", E, Wnn, E) - np.sum(na * gn, axis=1)[:, None, None] * np.eye(2)[None]
+        HFt = np.einsum("vklp,vpb->vklb", WFn, E).reshape(-1, 9, 2)
+        H = np.zeros((idx.size, 11, 11))
+        H[:, :9, :9] = WFF.reshape(-1, 9, 9) + rho * np.eye(9)[None]
+        H[:, :9, 9:] = HFt
+        H[:, 9:, :9] = HFt.transpose(0, 2, 1)
+        # Levenberg shift on the two director unknowns: keeps the step defined where W does
+        # not depend on n (r = 1, alpha = 0); the converged point (gradient zero) is unchanged
+        H[:, 9:, 9:] = Htt + 1e-6 * sub.mu[:, None, None] * np.eye(2)[None]
+        g = np.concatenate([gF.reshape(-1, 9), gt], axis=1)
+        delta = -np.linalg.solve(H, g[..., None])[..., 0]
+        slope = np.sum(g * delta, axis=1)
+        bad = ~(slope < 0.0) | ~np.all(np.isfinite(delta), axis=1)
+        if np.any(bad):
+            delta[bad] = -g[bad]
+            slope[bad] = -np.sum(g[bad] * g[bad], axis=1)
+        phi0 = phi(sub, Fa, na, Lam_s, G_s, f_s)
+        size = np.max(np.abs(delta), axis=1)
+        t = np.ones(idx.size)
+        accepted = np.zeros(idx.size, dtype=bool)
+        for _ls in range(60):
+            pend = ~accepted
+            if not np.any(pend):
+                break
+            Ft = Fa + t[:, None, None] * delta[:, :9].reshape(-1, 3, 3)
+            nt = retract(na, a, b, t * delta[:, 9], t * delta[:, 10])
+            J = np.linalg.det(Ft)
+            ok = J > 0.0
+            with np.errstate(invalid="ignore", divide="ignore"):
+                ph = phi(sub, Ft, nt, Lam_s, G_s, f_s)
+            dec = ph <= phi0 + armijo * t * slope
+            acc = pend & ok & (dec | (t * size <= small_step))
+            accepted |= acc
+            t = np.where(pend & ~acc, 0.5 * t, t)
+        t = np.where(accepted, t, 0.0)
+        F[idx] = Fa + t[:, None, None] * delta[:, :9].reshape(-1, 3, 3)
+        n[idx] = retract(na, a, b, t * delta[:, 9], t * delta[:, 10])
+        iters[idx] += 1
+        done = accepted & (t == 1.0) & (size <= step_tol)
+        active[idx[done]] = False
+    return F, n, iters
+
+
 # --------------------------------------------------------------------------- Steps 3 and 4
 
 
@@ -203,24 +319,27 @@ def rms(T: np.ndarray) -> float:
     return float(np.sqrt(np.sum(T * T) / T[0, 0].size))
 
 
-def initial_state(mat, Fbar_d: np.ndarray, grid_shape, lambda0: str = "stress"):
+def initial_state(mat, Fbar_d: np.ndarray, grid_shape, lambda0: str = "stress", n0=None):
     d = Fbar_d.shape[0]
     V = int(np.prod(grid_shape))
     Fv = np.broadcast_to(Fbar_d, (V, d, d)).copy()
     F = _to_field(Fv, grid_shape)
     if lambda0 == "stress":
-        Lam = _to_field(mat.P(Fv), grid_shape)
+        Lam = _to_field(mat.P(Fv) if n0 is None else mat.P(Fv, np.asarray(n0).reshape(3, -1).T), grid_shape)
     elif lambda0 == "zero":
         Lam = np.zeros_like(F)
     else:
         raise ValueError(lambda0)
     u = np.zeros((d,) + tuple(grid_shape))
-    return {"F": F, "Lam": Lam, "u": u}
+    st = {"F": F, "Lam": Lam, "u": u}
+    if n0 is not None:
+        st["n"] = np.array(n0, dtype=np.float64).reshape((3,) + tuple(grid_shape))
+    return st
 
 
 def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_ref=None,
                lambda0="stress", state=None, rho_policy="fixed", kappa=1.3, tau=10.0,
-               rho_min=None, local_cap=50, step_tol=1e-10):
+               rho_min=None, local_cap=50, step_tol=1e-10, n0=None):
     """Run the ADMM iteration (Steps 1-4) until r_p <= tol and r_d <= tol, or max_iter.
 
     phase: uint8 grid (N,)*d; params: per-phase (mu, lam); Fbar: 3x3 (the upper-left
@@ -231,23 +350,33 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
     phase = np.asarray(phase)
     d = phase.ndim
     grid = phase.shape
-    mat = make_material(model, phase, params)
+    lce = model == "lce"
+    mat = make_lce(phase, params, n0) if lce else make_material(model, phase, params)
     Fbar_d = np.asarray(Fbar, dtype=np.float64)[:d, :d]
     if mu_ref is None:
         mu_ref = float(np.mean(mat.mu))
     if rho_min is None:
         rho_min = mu_ref
-    st = initial_state(mat, Fbar_d, grid, lambda0) if state is None else {
-        k: np.array(v, dtype=np.float64, copy=True) for k, v in state.items()}
+    if state is None:
+        st = initial_state(mat, Fbar_d, grid, lambda0, n0=n0 if lce else None)
+    else:
+        st = {k: np.array(v, dtype=np.float64, copy=True) for k, v in state.items()}
     F, Lam, u = st["F"], st["Lam"], st["u"]
+    nd = st.get("n")
     G = Fbar_d.reshape((d, d) + (1,) * d) + grad_u(u)
     history = []
     converged = False
     it = 0
     for it in range(1, max_iter + 1):
         # Step 1
-        Fv, _ = local_newton(mat, _to_voxels(F), _to_voxels(Lam), _to_voxels(G), rho,
-                             step_tol=step_tol, cap=local_cap)
+        if lce:
+            force = frank_force(nd, mat.kappa)
+            Fv, nv, _ = local_newton_lce(mat, _to_voxels(F), nd.reshape(3, -1).T, _to_voxels(Lam),
+                                         _to_voxels(G), force, rho, step_tol=step_tol, cap=local_cap)
+            nd = nv.T.reshape((3,) + tuple(grid))
+        else:
+            Fv, _ = local_newton(mat, _to_voxels(F), _to_voxels(Lam), _to_voxels(G), rho,
+                                 step_tol=step_tol, cap=local_cap)
         F = _to_field(Fv, grid)
         # Step 2
         uh, u = u_step(F, Lam, rho)
@@ -269,10 +398,16 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
                 rho = kappa * rho
             elif r_p > 0.0 and r_d / r_p > tau:
                 rho = max(rho / kappa, rho_min)
-    stress = np.mean(mat.P(_to_voxels(F)), axis=0)
-    return {"F": F, "Lam": Lam, "u": u, "iters": it if max_iter > 0 else 0,
-            "converged": converged, "history": history, "rho": rho,
-            "stress": stress, "mu_ref": mu_ref}
+    if lce:
+        stress = np.mean(mat.P(_to_voxels(F), nd.reshape(3, -1).T), axis=0)
+    else:
+        stress = np.mean(mat.P(_to_voxels(F)), axis=0)
+    out = {"F": F, "Lam": Lam, "u": u, "iters": it if max_iter > 0 else 0,
+           "converged": converged, "history": history, "rho": rho,
+           "stress": stress, "mu_ref": mu_ref}
+    if lce:
+        out["n"] = nd
+    return out
 
 
 def homogenised_stress(phase, params, F, model="neohookean"):

@@ -116,3 +116,89 @@ def make_material(model: str, phase: np.ndarray, params: np.ndarray):
     ph = np.asarray(phase).reshape(-1).astype(np.int64)
     tab = np.asarray(params, dtype=np.float64)
     return MODELS[model](tab[ph, 0], tab[ph, 1])
+
+
+class LCE:
+    """Liquid crystal elastomer of Section 5.1 (3D), compressible network:
+
+        W(F, n; x) = mu/2 (tr(F^T l^{-1} F) - 3 - 2 ln J) + lam/2 (J - 1)^2        (network)
+                     + mu alpha/2 tr((I - n0 (x) n0) F^T (n (x) n) F)                 (non-ideality)
+
+    with the step-length tensor l = r^{-1/3} (I + (r - 1) n (x) n) (the sign that makes
+    l positive definite and elongates the material along n by r^{1/3}), so
+    l^{-1} = r^{1/3} (I - (1 - 1/r) n (x) n).  The Frank energy is not part of W here;
+    the iteration adds its explicit force (see admm.local_newton_lce).
+
+    In terms of m = F^T n:  W = mu r^{1/3}/2 |F|^2 + 1/2 m.M m - mu ln J + lam/2 (J-1)^2
+    - 3 mu/2 with M = mu (alpha - r^{1/3}(1 - 1/r)) I - mu alpha n0 (x) n0; the
+    derivatives below are taken from that form.  Arrays: F (V,3,3), n (V,3).
+    """
+
+    nparam = 5
+
+    def __init__(self, mu, lam, r, alpha, kappa, n0):
+        self.mu = np.asarray(mu, dtype=np.float64)
+        self.lam = np.asarray(lam, dtype=np.float64)
+        self.r = np.asarray(r, dtype=np.float64)
+        self.alpha = np.asarray(alpha, dtype=np.float64)
+        self.kappa = np.asarray(kappa, dtype=np.float64)
+        self.n0 = np.asarray(n0, dtype=np.float64)
+
+    def subset(self, idx):
+        return LCE(self.mu[idx], self.lam[idx], self.r[idx], self.alpha[idx], self.kappa[idx], self.n0[idx])
+
+    def ell_inv(self, n):
+        r13 = np.cbrt(self.r)
+        s = 1.0 - 1.0 / self.r
+        return r13[:, None, None] * (np.eye(3)[None] - s[:, None, None] * np.einsum("vi,vj->vij", n, n))
+
+    def W(self, F, n):
+        J = np.linalg.det(F)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            lnJ = np.log(J)
+        tr_el = np.einsum("vji,vjk,vki->v", F, self.ell_inv(n), F)
+        P0 = np.eye(3)[None] - np.einsum("vi,vj->vij", self.n0, self.n0)
+        FtnnF = np.einsum("vji,vj,vk,vkl->vil", F, n, n, F)
+        tr_ni = np.einsum("vij,vji->v", P0, FtnnF)
+        return (0.5 * self.mu * (tr_el - 3.0 - 2.0 * lnJ) + 0.5 * self.lam * (J - 1.0) ** 2
+                + 0.5 * self.mu * self.alpha * tr_ni)
+
+    def _M(self):
+        r13 = np.cbrt(self.r)
+        c1 = self.mu * (self.alpha - r13 * (1.0 - 1.0 / self.r))
+        c2 = self.mu * self.alpha
+        return c1[:, None, None] * np.eye(3)[None] - c2[:, None, None] * np.einsum("vi,vj->vij", self.n0, self.n0)
+
+    def derivatives(self, F, n):
+        """Gradients and Hessian blocks of W: (P = W_F, W_n, W_FF (V,3,3,3,3), W_Fn (V,3,3,3), W_nn (V,3,3))."""
+        A = np.linalg.inv(F).transpose(0, 2, 1)
+        J = np.linalg.det(F)
+        r13 = np.cbrt(self.r)
+        M = self._M()
+        m = np.einsum("vij,vi->vj", F, n)
+        Mm = np.einsum("vjl,vl->vj", M, m)
+        c = self.lam * J * (J - 1.0) - self.mu
+        b = self.lam * (2.0 * J - 1.0) * J
+        P = (self.mu * r13)[:, None, None] * F + np.einsum("vk,vl->vkl", n, Mm) + c[:, None, None] * A
+        Wn = np.einsum("vkj,vj->vk", F, Mm)
+        I = np.eye(3)
+        WFF = ((self.mu * r13)[:, None, None, None, None] * np.einsum("ik,jl->ijkl", I, I)[None]
+               + np.einsum("vk,vp,vlq->vklpq", n, n, M)
+               + b[:, None, None, None, None] * np.einsum("vij,vkl->vijkl", A, A)
+               - c[:, None, None, None, None] * np.einsum("vil,vkj->vijkl", A, A))
+        MFt = np.einsum("vlj,vpj->vlp", M, F)
+        WFn = np.einsum("kp,vl->vklp", I, Mm) + np.einsum("vk,vlp->vklp", n, MFt)
+        Wnn = np.einsum("vkj,vjl,vpl->vkp", F, M, F)
+        return P, Wn, WFF, WFn, Wnn
+
+    def P(self, F, n):
+        return self.derivatives(F, n)[0]
+
+
+def make_lce(phase: np.ndarray, params: np.ndarray, n0: np.ndarray):
+    """Per-voxel LCE material: params[p] = (mu, lam, r, alpha, kappa_F); n0 of shape
+    (3, *grid) (component-major, like the fields)."""
+    ph = np.asarray(phase).reshape(-1).astype(np.int64)
+    tab = np.asarray(params, dtype=np.float64)
+    n0v = np.asarray(n0, dtype=np.float64).reshape(3, -1).T
+    return LCE(tab[ph, 0], tab[ph, 1], tab[ph, 2], tab[ph, 3], tab[ph, 4], n0v)

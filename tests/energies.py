@@ -98,3 +98,46 @@ def div_stencil(T):
             ax = d - 1 - j
             out[i] += (np.roll(T[i, j], -1, axis=ax) - np.roll(T[i, j], 1, axis=ax)) * (n / 2.0)
     return out
+
+
+# ----------------------------------------------------------------- liquid crystal elastomer (Section 5.1)
+
+def w_lce(F, n, mu, lam, r, alpha, n0):
+    """Compressible network + non-ideality, literally from Section 5.1's formulas with
+    l = r^{-1/3}(I + (r-1) n n^T) (positive-definite sign):
+    mu/2 (tr(F^T l^{-1} F) - 3 - ln det C) + lam/2 (sqrt(det C) - 1)^2
+    + mu alpha/2 tr((I - n0 n0^T) F^T (n n^T) F).  n is used as given (not normalised)."""
+    ell = r ** (-1.0 / 3.0) * (np.eye(3) + (r - 1.0) * np.outer(n, n))
+    ell_inv = np.linalg.inv(ell) if not np.iscomplexobj(n) else _inv3(ell)
+    C = F.T @ F
+    I3 = _det(C)
+    W_el = 0.5 * mu * (np.trace(F.T @ ell_inv @ F) - 3.0 - np.log(I3)) + 0.5 * lam * (np.sqrt(I3) - 1.0) ** 2
+    W_ni = 0.5 * mu * alpha * np.trace((np.eye(3) - np.outer(n0, n0)) @ F.T @ np.outer(n, n) @ F)
+    return W_el + W_ni
+
+
+def _inv3(M):
+    c = np.array([[M[1, 1] * M[2, 2] - M[1, 2] * M[2, 1], M[0, 2] * M[2, 1] - M[0, 1] * M[2, 2],
+                   M[0, 1] * M[1, 2] - M[0, 2] * M[1, 1]],
+                  [M[1, 2] * M[2, 0] - M[1, 0] * M[2, 2], M[0, 0] * M[2, 2] - M[0, 2] * M[2, 0],
+                   M[0, 2] * M[1, 0] - M[0, 0] * M[1, 2]],
+                  [M[1, 0] * M[2, 1] - M[1, 1] * M[2, 0], M[0, 1] * M[2, 0] - M[0, 0] * M[2, 1],
+                   M[0, 0] * M[1, 1] - M[0, 1] * M[1, 0]]], dtype=M.dtype)
+    return c / _det(M)
+
+
+def lce_grad_cs(F, n, args, h=1e-30):
+    """(W_F, W_n) of w_lce by complex steps in each component of F and of n."""
+    gF = np.zeros((3, 3))
+    gn = np.zeros(3)
+    Fc = F.astype(np.complex128)
+    nc = n.astype(np.complex128)
+    for k in range(3):
+        for l in range(3):
+            E = np.zeros((3, 3), dtype=np.complex128)
+            E[k, l] = 1j * h
+            gF[k, l] = np.imag(w_lce(Fc + E, nc, *args)) / h
+        e = np.zeros(3, dtype=np.complex128)
+        e[k] = 1j * h
+        gn[k] = np.imag(w_lce(Fc, nc + e, *args)) / h
+    return gF, gn

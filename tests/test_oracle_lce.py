@@ -1,0 +1,170 @@
+"""Pins of the oracle's liquid crystal elastomer model (Section 5.1) and its local
+solve, against facts independent of the oracle's derivative code."""
+import numpy as np
+import pytest
+from scipy import optimize
+
+import oracle
+from oracle import admm as oadmm
+from oracle.materials import LCE
+from paper_2010_06697_gb300 import synth
+from tests import energies as E
+
+RNG = np.random.default_rng(99)
+MU, LAM, R, ALPHA = 1.0, 20.0, 7.71, 0.06
+
+
+def _unit(v):
+    return v / np.linalg.norm(v)
+
+
+def _mat(n0, r=R, alpha=ALPHA, kappa=0.0, V=1):
+    return LCE(np.full(V, MU), np.full(V, LAM), np.full(V, r), np.full(V, alpha), np.full(V, kappa),
+               np.broadcast_to(n0, (V, 3)).copy())
+
+
+def test_lce_derivatives_match_complex_step():
+    """W_F, and the derivatives in n along the unit sphere (the only ones the local
+    solve uses: tangential gradient, Riemannian Hessian E^T W_nn E - (n.W_n) I, mixed
+    block W_Fn E), equal complex-step / finite-difference derivatives of Section 5.1's
+    energy typed separately (whose extension off |n| = 1 differs)."""
+    for _ in range(5):
+        F = np.eye(3) + 0.2 * RNG.uniform(-1, 1, (3, 3))
+        n = _unit(RNG.standard_normal(3))
+        n0 = _unit(RNG.standard_normal(3))
+        m = _mat(n0)
+        args = (MU, LAM, R, ALPHA, n0)
+        assert abs(m.W(F[None], n[None])[0] - np.real(E.w_lce(F, n, *args))) < 1e-12
+        P, Wn, WFF, WFn, Wnn = m.derivatives(F[None], n[None])
+        gF, gn = E.lce_grad_cs(F, n, args)
+        np.testing.assert_allclose(P[0], gF, atol=1e-11)
+        a, b = oadmm.tangent_basis(n[None])
+        Et = np.stack([a[0], b[0]], axis=1)                      # (3, 2)
+        np.testing.assert_allclose(Et.T @ Wn[0], Et.T @ gn, atol=1e-11)
+        eps = 1e-6
+        for k in range(3):
+            for l in range(3):
+                dF = np.zeros((3, 3))
+                dF[k, l] = eps
+                gp, gnp = E.lce_grad_cs(F + dF, n, args)
+                gm, gnm = E.lce_grad_cs(F - dF, n, args)
+                np.testing.assert_allclose(WFF[0][:, :, k, l], (gp - gm) / (2 * eps), atol=1e-6)
+                np.testing.assert_allclose(Et.T @ WFn[0][k, l, :], Et.T @ (gnp - gnm) / (2 * eps), atol=1e-6)
+        # Riemannian Hessian in the tangent plane from second differences of W along the sphere
+        def w_on_sphere(t):
+            return np.real(E.w_lce(F, oadmm.retract(n[None], a, b, np.array([t[0]]), np.array([t[1]]))[0], *args))
+        H_fd = np.zeros((2, 2))
+        h = 1e-4
+        for i in range(2):
+            for j in range(2):
+                ei, ej = np.eye(2)[i] * h, np.eye(2)[j] * h
+                H_fd[i, j] = (w_on_sphere(ei + ej) - w_on_sphere(ei - ej) - w_on_sphere(-ei + ej)
+                              + w_on_sphere(-ei - ej)) / (4 * h * h)
+        H_or = Et.T @ Wnn[0] @ Et - np.dot(n, Wn[0]) * np.eye(2)
+        np.testing.assert_allclose(H_or, H_fd, atol=1e-5)
+
+
+def test_lce_ground_state_is_stress_free():
+    """Section 5.1: F = R l0^{1/2} Q, n = R e gives W_el = 0; with n0 = e also W_ni = 0,
+    and the homogeneous cell at that Fbar is an exact fixed point with zero stress."""
+    e = _unit(np.array([0.6, 0.8, 0.0]))
+    ell = R ** (-1 / 3) * (np.eye(3) + (R - 1) * np.outer(e, e))
+    w, Q = np.linalg.eigh(ell)
+    Fg = Q @ np.diag(np.sqrt(w)) @ Q.T
+    th = 0.3
+    Rot = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+    m = _mat(e)
+    assert abs(np.real(E.w_lce(Fg, e, MU, LAM, R, ALPHA, e))) < 1e-13
+    assert abs(np.real(E.w_lce(Rot @ Fg, Rot @ e, MU, LAM, R, 0.0, e))) < 1e-13
+    assert np.max(np.abs(m.P(Fg[None], e[None]))) < 1e-13
+    n = 8
+    ph = np.zeros((n,) * 3, np.uint8)
+    n0 = np.broadcast_to(e[:, None, None, None], (3, n, n, n)).copy()
+    par = np.array([[MU, LAM, R, ALPHA, 4.0 / n ** 2]])
+    r = oracle.admm_solve(ph, par, Fg, 10.0, 1e-12, 5, model="lce", n0=n0)
+    assert r["converged"] and r["iters"] == 1
+    assert np.max(np.abs(r["stress"])) < 1e-12
+    assert np.max(np.abs(r["n"] - n0)) < 1e-12
+
+
+def test_lce_reduces_to_neohookean():
+    """r = 1, alpha = 0, kappa_F = 0: W no longer depends on n (Section 5.1) and the
+    LCE iteration equals the neo-Hookean one."""
+    n = 8
+    ph = synth.inclusion_phase(n, 3, 2, radius=2)
+    par_nh = synth.two_phase_params(1.0, 10.0)
+    par = np.column_stack([par_nh, np.ones(2), np.zeros(2), np.zeros(2)])
+    n0 = synth.director_grf(n, 3, corr=2.0)
+    Fbar = np.diag([0.95, 1.02, 1.0])
+    a = oracle.admm_solve(ph, par_nh, Fbar, 10.0, -1.0, 6)
+    b = oracle.admm_solve(ph, par, Fbar, 10.0, -1.0, 6, model="lce", n0=n0)
+    np.testing.assert_allclose(b["F"], a["F"], atol=1e-12)
+    np.testing.assert_allclose(b["stress"], a["stress"], atol=1e-12)
+
+
+def test_uniform_director_has_no_frank_torque():
+    """A uniform director field: the Frank force is parallel to n (no tangential part)."""
+    n = 6
+    e = _unit(np.array([0.2, -0.5, 0.8]))
+    field = np.broadcast_to(e[:, None, None, None], (3, n, n, n)).copy()
+    f = oadmm.frank_force(field, np.full(n ** 3, 0.3))
+    tang = f - np.sum(f * e[None], axis=1)[:, None] * e[None]
+    assert np.max(np.abs(tang)) < 1e-12
+
+
+def test_frank_force_is_tangentially_the_laplacian():
+    """The neighbour-sum force equals 2 kappa Delta_h n (compact Laplacian, Section 2.3
+    symbol, here by FFT) up to a multiple of n: same tangential component."""
+    n = 8
+    field = synth.director_grf(n, 5, corr=2.0)
+    kap = 0.07
+    f = oadmm.frank_force(field, np.full(n ** 3, kap))
+    m = np.fft.fftfreq(n) * n
+    s = -4.0 * n * n * np.sin(np.pi * m / n) ** 2
+    sym = s[:, None, None] + s[None, :, None] + s[None, None, :]
+    lap = np.fft.ifftn(np.fft.fftn(field, axes=(1, 2, 3)) * sym, axes=(1, 2, 3)).real
+    g = 2 * kap * lap.reshape(3, -1).T
+    nv = field.reshape(3, -1).T
+    proj = lambda x: x - np.sum(x * nv, axis=1)[:, None] * nv
+    np.testing.assert_allclose(proj(f), proj(g), atol=1e-9)
+
+
+@pytest.mark.parametrize("trial", range(3))
+def test_lce_local_solve_matches_brute_force(trial):
+    """Step 1 for the LCE at one voxel: the oracle's (F, n) minimiser agrees with a
+    derivative-free minimisation over F and the two spherical angles of n."""
+    rng = np.random.default_rng(100 + trial)
+    n0 = _unit(rng.standard_normal(3))
+    n_init = _unit(n0 + 0.3 * rng.standard_normal(3))
+    G = np.eye(3) + 0.08 * rng.uniform(-1, 1, (3, 3))
+    Lam = 0.3 * rng.uniform(-1, 1, (3, 3))
+    f = 0.5 * rng.standard_normal(3)
+    rho = 10.0
+    r_ = 2.5
+
+    def phi(x):
+        F = x[:9].reshape(3, 3)
+        th, ps = x[9], x[10]
+        nn = np.array([np.sin(th) * np.cos(ps), np.sin(th) * np.sin(ps), np.cos(th)])
+        if np.linalg.det(F) <= 0:
+            return np.inf
+        return (float(np.real(E.w_lce(F, nn, MU, LAM, r_, ALPHA, n0))) - f @ nn - np.sum(Lam * F)
+                + 0.5 * rho * np.sum((F - G) ** 2))
+
+    m = _mat(n0, r=r_)
+    Fn, nn, _ = oadmm.local_newton_lce(m, G[None].copy(), n_init[None], Lam[None], G[None], f[None], rho)
+    th0 = np.arccos(np.clip(nn[0, 2], -1, 1))
+    ps0 = np.arctan2(nn[0, 1], nn[0, 0])
+    x_newton = np.concatenate([Fn[0].ravel(), [th0, ps0]])
+    best = None
+    for s in range(3):
+        x0 = x_newton + 0.02 * rng.standard_normal(11)
+        res = optimize.minimize(phi, x0, method="Nelder-Mead",
+                                options={"xatol": 1e-10, "fatol": 1e-14, "maxiter": 60000, "maxfev": 120000})
+        res = optimize.minimize(phi, res.x, method="Powell", options={"xtol": 1e-11, "ftol": 1e-15})
+        if best is None or res.fun < best.fun:
+            best = res
+    assert phi(x_newton) <= best.fun + 1e-11
+    np.testing.assert_allclose(Fn[0].ravel(), best.x[:9], atol=1e-5)
+    nb = np.array([np.sin(best.x[9]) * np.cos(best.x[10]), np.sin(best.x[9]) * np.sin(best.x[10]), np.cos(best.x[9])])
+    assert min(np.max(np.abs(nb - nn[0])), np.max(np.abs(nb + nn[0]))) < 1e-5
