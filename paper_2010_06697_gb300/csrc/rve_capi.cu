@@ -80,9 +80,9 @@ int local_blocks_for(long long V) {
 }
 
 struct Layout {
-    size_t ctrl, hist, partials, phase, mat, n0;
-    size_t F64[2], L64, U64[2], tw64, ksq64;
-    size_t F32[2], L32, U32[2], tw32, ksq32;
+    size_t ctrl, hist, partials, phase, mat;
+    size_t F64[2], L64, U64[2], tw64, ksq64, N64[2], n064;
+    size_t F32[2], L32, U32[2], tw32, ksq32, N32[2], n032;
     size_t total;
 };
 
@@ -101,9 +101,9 @@ Layout layout(int dim, int n, int model, int precision, int max_iter) {
     o.partials = take(sizeof(double) * admm::kPartialStride * (size_t)local_blocks_for(V));
     o.phase = take((size_t)V);
     o.mat = take(sizeof(double) * 256 * admm::kMaxParam);
-    o.n0 = model == admm::kLce ? take(sizeof(double) * 3 * (size_t)V) : 0;
     const bool need64 = precision != RVE_FP32;
     const bool need32 = precision != RVE_FP64;
+    const bool lce = model == admm::kLce;
     if (need64) {
         o.F64[0] = take(8 * nF);
         o.F64[1] = take(8 * nF);
@@ -112,6 +112,11 @@ Layout layout(int dim, int n, int model, int precision, int max_iter) {
         o.U64[1] = take(8 * nU);
         o.tw64 = take(16 * (size_t)n);
         o.ksq64 = take(8 * (size_t)n);
+        if (lce) {
+            o.N64[0] = take(8 * 3 * (size_t)V);
+            o.N64[1] = take(8 * 3 * (size_t)V);
+            o.n064 = take(8 * 3 * (size_t)V);
+        }
     }
     if (need32) {
         o.F32[0] = take(4 * nF);
@@ -121,6 +126,11 @@ Layout layout(int dim, int n, int model, int precision, int max_iter) {
         o.U32[1] = take(4 * nU);
         o.tw32 = take(8 * (size_t)n);
         o.ksq32 = take(4 * (size_t)n);
+        if (lce) {
+            o.N32[0] = take(4 * 3 * (size_t)V);
+            o.N32[1] = take(4 * 3 * (size_t)V);
+            o.n032 = take(4 * 3 * (size_t)V);
+        }
     }
     o.total = off;
     return o;
@@ -341,7 +351,8 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
     if (!out) return RVE_E_INVALID_ARG;
     *out = nullptr;
     if ((dim != 2 && dim != 3) || !valid_n(n)) return RVE_E_INVALID_ARG;
-    if (model != RVE_NEOHOOKE && model != RVE_LINEAR) return RVE_E_INVALID_ARG;
+    if (model != RVE_NEOHOOKE && model != RVE_LINEAR && model != RVE_LCE) return RVE_E_INVALID_ARG;
+    if (model == RVE_LCE && dim != 3) return RVE_E_INVALID_ARG;
     rve_options o;
     rve_default_options(&o);
     if (opt) o = *opt;
@@ -391,7 +402,7 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
     L.phase = (const uint8_t*)(b + lay.phase);
     L.mat = (const double*)(b + lay.mat);
     L.nparam = 2;
-    L.n0 = model == admm::kLce ? (const double*)(b + lay.n0) : nullptr;
+    const bool lce = model == admm::kLce;
     if (o.precision != RVE_FP32) {
         L.F64[0] = (double*)(b + lay.F64[0]);
         L.F64[1] = (double*)(b + lay.F64[1]);
@@ -400,6 +411,11 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
         L.U64[1] = (double*)(b + lay.U64[1]);
         L.tw64 = (const double2*)(b + lay.tw64);
         L.ksq64 = (const double*)(b + lay.ksq64);
+        if (lce) {
+            L.N64[0] = (double*)(b + lay.N64[0]);
+            L.N64[1] = (double*)(b + lay.N64[1]);
+            L.n0_64 = (const double*)(b + lay.n064);
+        }
     }
     if (o.precision != RVE_FP64) {
         L.F32[0] = (float*)(b + lay.F32[0]);
@@ -409,6 +425,11 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
         L.U32[1] = (float*)(b + lay.U32[1]);
         L.tw32 = (const float2*)(b + lay.tw32);
         L.ksq32 = (const float*)(b + lay.ksq32);
+        if (lce) {
+            L.N32[0] = (float*)(b + lay.N32[0]);
+            L.N32[1] = (float*)(b + lay.N32[1]);
+            L.n0_32 = (const float*)(b + lay.n032);
+        }
     }
     if (o.precision == RVE_MIXED) {
         L.R32 = L.F32[0];
@@ -488,7 +509,8 @@ int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* pa
                      const double* n0) {
     if (!h || !phase || !params || nphase < 1 || nphase > 256 || nparam < 2 || nparam > admm::kMaxParam)
         return RVE_E_INVALID_ARG;
-    (void)n0;
+    const bool lce = h->model == RVE_LCE;
+    if (lce && (nparam < 5 || !n0)) return RVE_E_INVALID_ARG;
     std::vector<long long> count(256, 0);
     for (long long v = 0; v < h->V; ++v) {
         if (phase[v] >= nphase) return RVE_E_INVALID_ARG;
@@ -499,12 +521,40 @@ int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* pa
     for (int p = 0; p < nphase; ++p) {
         const double mu = params[p * nparam + 0], lam = params[p * nparam + 1];
         if (!(mu > 0) || !(lam >= 0) || !isfinite(mu) || !isfinite(lam)) return RVE_E_INVALID_ARG;
-        for (int q = 0; q < nparam; ++q) tab[p * admm::kMaxParam + q] = params[p * nparam + q];
+        double* row = &tab[p * admm::kMaxParam];
+        for (int q = 0; q < (lce ? 5 : nparam); ++q) row[q] = params[p * nparam + q];
+        if (lce) {
+            // {mu, lam, r, alpha, kappa_F}; derived a = mu r^{1/3}, c1, c2 of the m = F^T n form
+            const double r = row[2], alpha = row[3], kap = row[4];
+            if (!(r > 0) || !(alpha >= 0) || !(kap >= 0) || !isfinite(r) || !isfinite(alpha) || !isfinite(kap))
+                return RVE_E_INVALID_ARG;
+            const double r13 = cbrt(r);
+            row[5] = mu * r13;
+            row[6] = mu * (alpha - r13 * (1.0 - 1.0 / r));
+            row[7] = mu * alpha;
+        }
         musum += mu * (double)count[p];
+    }
+    std::vector<float> n0f;
+    if (lce) {
+        const long long V = h->V;
+        for (long long v = 0; v < V; ++v) {
+            const double a = n0[v], b = n0[V + v], c = n0[2 * V + v];
+            const double nn = a * a + b * b + c * c;
+            if (!isfinite(nn) || fabs(nn - 1.0) > 1e-6) return RVE_E_INVALID_ARG;
+        }
+        if (h->L.n0_32) {
+            n0f.resize(3 * (size_t)V);
+            for (size_t i = 0; i < n0f.size(); ++i) n0f[i] = (float)n0[i];
+        }
     }
     if (enter(h)) return RVE_E_CUDA;
     CK(cudaMemcpyAsync((void*)h->L.phase, phase, (size_t)h->V, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync((void*)h->L.mat, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (lce && h->L.n0_64)
+        CK(cudaMemcpyAsync((void*)h->L.n0_64, n0, 3 * (size_t)h->V * 8, cudaMemcpyHostToDevice, h->stream));
+    if (lce && h->L.n0_32)
+        CK(cudaMemcpyAsync((void*)h->L.n0_32, n0f.data(), n0f.size() * 4, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->L.nparam = admm::kMaxParam;
     h->nphase = nphase;
@@ -664,6 +714,11 @@ static int field_ptr(rve_t h, int which, void** ptr, size_t* count) {
         case RVE_FIELD_U:
             *ptr = f64 ? (void*)h->L.U64[par] : (void*)h->L.U32[par];
             *count = (size_t)h->dim * V;
+            return RVE_OK;
+        case RVE_FIELD_N:
+            if (h->model != RVE_LCE) return RVE_E_INVALID_ARG;
+            *ptr = f64 ? (void*)h->L.N64[par] : (void*)h->L.N32[par];
+            *count = 3 * (size_t)V;
             return RVE_OK;
         default: return RVE_E_INVALID_ARG;
     }

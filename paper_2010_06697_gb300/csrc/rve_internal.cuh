@@ -69,7 +69,12 @@ struct Launch {
     const uint8_t* phase;
     const double* mat;     // per-phase constants, nparam each
     int nparam;
-    const double* n0;      // LCE reference directors (3 x V) or null
+    // LCE directors (3 x V each, null for the other laws): ping-pong fields and the
+    // reference directors n0, in both precisions
+    double* N64[2];
+    const double* n0_64;
+    float* N32[2];
+    const float* n0_32;
     // double precision state
     double* F64[2];
     double* L64;

@@ -360,6 +360,257 @@ __device__ __forceinline__ int newton(const Law& m, T* F, const T* B, T rho, int
     return it;
 }
 
+// ------------------------------------------------------------------ liquid crystal elastomer
+// Section 5.1 with the readings of the oracle: compressible network with the
+// positive-definite step-length tensor l = r^{-1/3}(I + (r-1) n n), non-ideality,
+// Frank gradient from the previous iterate.  With m = F^T n and
+// M = c1 I - c2 n0 n0 (c1 = mu(alpha - r^{1/3}(1 - 1/r)), c2 = mu alpha):
+//   W = a/2 |F|^2 + 1/2 m.M m - mu ln J + lam/2 (J-1)^2 + const,   a = mu r^{1/3}.
+// Local objective: phi(F, n) = W - f.n - Lambda:F + rho/2 |F - G|^2 on |n| = 1,
+// f = 2 kappa_F / h^2 * (sum of the neighbours' directors of the previous iterate).
+template <typename T>
+struct Lce {
+    T mu, lam, a, c1, c2;
+    T n0[3];
+    __device__ __forceinline__ void Mv(const T* v, T* o) const {
+        const T d = n0[0] * v[0] + n0[1] * v[1] + n0[2] * v[2];
+        for (int i = 0; i < 3; ++i) o[i] = c1 * v[i] - c2 * d * n0[i];
+    }
+    __device__ __forceinline__ T phi(const T* F, const T* n, const T* B, const T* f, T rho, T J) const {
+        T ff = 0, bf = 0, mm[3], Mm[3];
+#pragma unroll
+        for (int p = 0; p < 9; ++p) {
+            ff += F[p] * F[p];
+            bf += B[p] * F[p];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) mm[j] = n[0] * F[j] + n[1] * F[3 + j] + n[2] * F[6 + j];
+        Mv(mm, Mm);
+        const T q = mm[0] * Mm[0] + mm[1] * Mm[1] + mm[2] * Mm[2];
+        return T(0.5) * (a + rho) * ff + T(0.5) * q - mu * log_t(J) + T(0.5) * lam * (J - T(1)) * (J - T(1)) -
+               (f[0] * n[0] + f[1] * n[1] + f[2] * n[2]) - bf;
+    }
+    // W_F = a F + n (x) M m + (lam J (J-1) - mu) F^{-T}
+    __device__ __forceinline__ void stress(const T* F, const T* n, T* P) const {
+        T K[9], mm[3], Mm[3];
+        const T J = det_cof<T, 3>(F, K);
+        const T c = (lam * J * (J - T(1)) - mu) / J;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) mm[j] = n[0] * F[j] + n[1] * F[3 + j] + n[2] * F[6 + j];
+        Mv(mm, Mm);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) P[k * 3 + l] = a * F[k * 3 + l] + n[k] * Mm[l] + c * K[k * 3 + l];
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ Lce<T> load_lce(const uint8_t* phase, const double* mat, int nparam, long long v,
+                                          const T* __restrict__ n0, long long V) {
+    const int ph = phase[v];
+    const double* q = mat + ph * nparam;
+    Lce<T> m;
+    m.mu = (T)__ldg(q + 0);
+    m.lam = (T)__ldg(q + 1);
+    m.a = (T)__ldg(q + 5);
+    m.c1 = (T)__ldg(q + 6);
+    m.c2 = (T)__ldg(q + 7);
+    m.n0[0] = n0[v];
+    m.n0[1] = n0[V + v];
+    m.n0[2] = n0[2 * V + v];
+    return m;
+}
+
+// Orthonormal (ta, tb) spanning the tangent plane at the unit vector n.
+template <typename T>
+__device__ __forceinline__ void tangent_basis(const T* n, T* ta, T* tb) {
+    const T ax = fabs(n[0]), ay = fabs(n[1]), az = fabs(n[2]);
+    T e[3] = {T(0), T(0), T(0)};
+    if (ax <= ay && ax <= az) e[0] = T(1);
+    else if (ay <= az) e[1] = T(1);
+    else e[2] = T(1);
+    const T d = e[0] * n[0] + e[1] * n[1] + e[2] * n[2];
+    T nrm = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        ta[i] = e[i] - d * n[i];
+        nrm += ta[i] * ta[i];
+    }
+    const T inv = T(1) / sqrt(nrm);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ta[i] *= inv;
+    tb[0] = n[1] * ta[2] - n[2] * ta[1];
+    tb[1] = n[2] * ta[0] - n[0] * ta[2];
+    tb[2] = n[0] * ta[1] - n[1] * ta[0];
+}
+
+template <typename T>
+__device__ __forceinline__ void retract(const T* n, const T* ta, const T* tb, T t1, T t2, T* out) {
+    T nrm = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        out[i] = n[i] + t1 * ta[i] + t2 * tb[i];
+        nrm += out[i] * out[i];
+    }
+    const T inv = T(1) / sqrt(nrm);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[i] *= inv;
+}
+
+// Newton on (F, t1, t2) with n <- normalise(n + t1 ta + t2 tb) (tangent plane at the
+// current n): gradient and objective in T, Hessian (11x11) assembled and factored
+// in float; the director block gets the curvature term -(n . phi_n) I and a shift
+// 1e-6 mu I (a Levenberg term that keeps the step defined where W does not depend
+// on n; the converged point is unchanged).  Same line search and stopping rule as
+// newton().
+template <typename T>
+__device__ __forceinline__ int newton_lce(const Lce<T>& m, T* F, T* n, const T* B, const T* f, T rho, int cap, T tol,
+                                          bool& conv) {
+    constexpr int NU = 11;
+    constexpr int NP = NU * (NU + 1) / 2;
+    conv = false;
+    int it = 0;
+    while (it < cap) {
+        T A[9], mm[3], Mm[3], g[NU], ta[3], tb[3];
+        const T J = det_cof<T, 3>(F, A);
+        if (!(J > T(0))) break;
+        const T iJ = T(1) / J;
+#pragma unroll
+        for (int p = 0; p < 9; ++p) A[p] *= iJ;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) mm[j] = n[0] * F[j] + n[1] * F[3 + j] + n[2] * F[6 + j];
+        m.Mv(mm, Mm);
+        const T c = m.lam * J * (J - T(1)) - m.mu;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int l = 0; l < 3; ++l)
+                g[k * 3 + l] = (m.a + rho) * F[k * 3 + l] + n[k] * Mm[l] + c * A[k * 3 + l] - B[k * 3 + l];
+        T gn[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gn[k] = F[k * 3 + 0] * Mm[0] + F[k * 3 + 1] * Mm[1] + F[k * 3 + 2] * Mm[2] - f[k];
+        tangent_basis(n, ta, tb);
+        g[9] = ta[0] * gn[0] + ta[1] * gn[1] + ta[2] * gn[2];
+        g[10] = tb[0] * gn[0] + tb[1] * gn[1] + tb[2] * gn[2];
+        const T ngn = n[0] * gn[0] + n[1] * gn[1] + n[2] * gn[2];
+
+        float d[NU], gf[NU];
+#pragma unroll
+        for (int p = 0; p < NU; ++p) gf[p] = (float)g[p];
+        {
+            float H[NP];
+            float Af[9], nf[3], n0f[3], Mmf[3], Ftaf[3], Ftbf[3], MFta[3], MFtb[3];
+            const float c1 = (float)m.c1, c2 = (float)m.c2;
+#pragma unroll
+            for (int p = 0; p < 9; ++p) Af[p] = (float)A[p];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                nf[i] = (float)n[i];
+                n0f[i] = (float)m.n0[i];
+                Mmf[i] = (float)Mm[i];
+            }
+            // F^T ta, F^T tb and M applied to them
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                Ftaf[j] = (float)(F[j] * ta[0] + F[3 + j] * ta[1] + F[6 + j] * ta[2]);
+                Ftbf[j] = (float)(F[j] * tb[0] + F[3 + j] * tb[1] + F[6 + j] * tb[2]);
+            }
+            {
+                const float da = n0f[0] * Ftaf[0] + n0f[1] * Ftaf[1] + n0f[2] * Ftaf[2];
+                const float db = n0f[0] * Ftbf[0] + n0f[1] * Ftbf[1] + n0f[2] * Ftbf[2];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    MFta[i] = c1 * Ftaf[i] - c2 * da * n0f[i];
+                    MFtb[i] = c1 * Ftbf[i] - c2 * db * n0f[i];
+                }
+            }
+            const float Jf = (float)J, cf = (float)c;
+            const float bf = (float)m.lam * (2.f * Jf - 1.f) * Jf;
+            const float diag = (float)(m.a + rho);
+            // F-F block: (a+rho) d d + n_k n_r M_ls + b A_kl A_rs - c A_ks A_rl
+#pragma unroll
+            for (int p = 0; p < 9; ++p) {
+                const int k = p / 3, l = p % 3;
+#pragma unroll
+                for (int q = 0; q <= p; ++q) {
+                    const int r = q / 3, s2 = q % 3;
+                    const float Mls = (l == s2 ? c1 : 0.f) - c2 * n0f[l] * n0f[s2];
+                    float h = nf[k] * nf[r] * Mls + bf * Af[p] * Af[q] - cf * Af[k * 3 + s2] * Af[r * 3 + l];
+                    if (p == q) h += diag;
+                    H[p * (p + 1) / 2 + q] = h;
+                }
+            }
+            // director rows: d2/dF_rs dt_beta = e_r (M m)_s + n_r (M F^T e)_s
+            const float taf[3] = {(float)ta[0], (float)ta[1], (float)ta[2]};
+            const float tbf[3] = {(float)tb[0], (float)tb[1], (float)tb[2]};
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const int r = q / 3, s2 = q % 3;
+                H[9 * 10 / 2 + q] = taf[r] * Mmf[s2] + nf[r] * MFta[s2];
+                H[10 * 11 / 2 + q] = tbf[r] * Mmf[s2] + nf[r] * MFtb[s2];
+            }
+            const float shift = 1e-6f * (float)m.mu - (float)ngn;
+            H[9 * 10 / 2 + 9] = Ftaf[0] * MFta[0] + Ftaf[1] * MFta[1] + Ftaf[2] * MFta[2] + shift;
+            H[10 * 11 / 2 + 9] = Ftbf[0] * MFta[0] + Ftbf[1] * MFta[1] + Ftbf[2] * MFta[2];
+            H[10 * 11 / 2 + 10] = Ftbf[0] * MFtb[0] + Ftbf[1] * MFtb[1] + Ftbf[2] * MFtb[2] + shift;
+            if (!chol_solve<float, NU>(H, gf, d)) {
+                const float sc = 1.f / (float)(m.mu + rho);
+#pragma unroll
+                for (int p = 0; p < NU; ++p) d[p] = -gf[p] * sc;
+            }
+        }
+        float slope = 0.f, size = 0.f;
+#pragma unroll
+        for (int p = 0; p < NU; ++p) {
+            slope += gf[p] * d[p];
+            size = fmaxf(size, fabsf(d[p]));
+        }
+        if (!(slope < 0.f)) {
+            const float sc = 1.f / (float)(m.mu + rho);
+            slope = 0.f;
+            size = 0.f;
+#pragma unroll
+            for (int p = 0; p < NU; ++p) {
+                d[p] = -gf[p] * sc;
+                slope += gf[p] * d[p];
+                size = fmaxf(size, fabsf(d[p]));
+            }
+        }
+        if (!(size < 1e30f)) break;
+        T t = T(1);
+        T Ft[9], nt[3];
+        {
+            const T phi0 = (size > (float)NewtonConst<T>::big) ? m.phi(F, n, B, f, rho, J) : T(0);
+            int ls = 0;
+            for (; ls < 40; ++ls) {
+#pragma unroll
+                for (int p = 0; p < 9; ++p) Ft[p] = F[p] + t * (T)d[p];
+                const T Jt = det<T, 3>(Ft);
+                if (Jt > T(0)) {
+                    if (!(size > (float)NewtonConst<T>::big)) break;
+                    retract(n, ta, tb, t * (T)d[9], t * (T)d[10], nt);
+                    if (m.phi(Ft, nt, B, f, rho, Jt) <= phi0 + T(1e-4) * t * (T)slope) break;
+                }
+                t *= T(0.5);
+            }
+            if (ls == 40) t = T(0);
+        }
+#pragma unroll
+        for (int p = 0; p < 9; ++p) F[p] += t * (T)d[p];
+        retract(n, ta, tb, t * (T)d[9], t * (T)d[10], nt);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) n[i] = nt[i];
+        ++it;
+        if (t == T(1) && size <= (float)tol) {
+            conv = true;
+            break;
+        }
+        if (t == T(0)) break;
+    }
+    return it;
+}
+
 // ------------------------------------------------------------------ grid helpers
 
 template <int D>
@@ -415,12 +666,20 @@ __device__ __forceinline__ int warp_max(int v) {
 
 // ------------------------------------------------------------------ kernels
 
+// Director fields of the LCE (null for the other laws): ping-pong N0/N1 by the
+// same parity as F, and the reference directors n0 (read only).
+template <typename T>
+struct Dirs {
+    T* N0;
+    T* N1;
+    const T* ref;
+};
+
 // Fresh state: F_k = Fbar, u~_k = 0, Lambda = W_F(Fbar; x) (or 0).
 template <typename T, int D, int MODEL>
 __global__ void __launch_bounds__(kLocalThreads)
 k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const uint8_t* __restrict__ phase,
-       const double* __restrict__ mat, int nparam, long long V, int lambda_zero) {
-    using Law = typename LawOf<T, D, MODEL>::type;
+       const double* __restrict__ mat, int nparam, long long V, int lambda_zero, Dirs<T> dir) {
     const int par = (int)(ctrl->k & 1);
     T* F = par ? F1 : F0;
     T* U = par ? U1 : U0;
@@ -431,10 +690,25 @@ k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const 
         for (int j = 0; j < D; ++j) Fb[i * D + j] = (T)ctrl->Fbar[i * 3 + j];
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
         T P[D * D];
-        if (lambda_zero) {
+        if constexpr (MODEL == kLce) {
+            T* Nk = par ? dir.N1 : dir.N0;
+            T nv[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                nv[i] = dir.ref[i * V + v];
+                Nk[i * V + v] = nv[i];
+            }
+            if (lambda_zero) {
+#pragma unroll
+                for (int p = 0; p < 9; ++p) P[p] = T(0);
+            } else {
+                load_lce<T>(phase, mat, nparam, v, dir.ref, V).stress(Fb, nv, P);
+            }
+        } else if (lambda_zero) {
 #pragma unroll
             for (int p = 0; p < D * D; ++p) P[p] = T(0);
         } else {
+            using Law = typename LawOf<T, D, MODEL>::type;
             const Law m = load_law<Law, T>(phase, mat, nparam, v);
             m.stress(Fb, P);
         }
@@ -468,8 +742,8 @@ template <typename T, int D, int MODEL, bool FIRST, bool WRITE_R, bool DU>
 __global__ void __launch_bounds__(kLocalThreads)
 k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__ partials, T* F0, T* F1, T* Lam,
         const T* U0, const T* U1, const uint8_t* __restrict__ phase, const double* __restrict__ mat, int nparam,
-        int n, long long V, int only_if_rho_changed, float* __restrict__ Rout, const float* __restrict__ DUin) {
-    using Law = typename LawOf<T, D, MODEL>::type;
+        int n, long long V, int only_if_rho_changed, float* __restrict__ Rout, const float* __restrict__ DUin,
+        Dirs<T> dir) {
     constexpr int NN = D * D;
     __shared__ double s_sum[kLocalThreads / 32][2];
     __shared__ int s_int[kLocalThreads / 32][2];
@@ -543,12 +817,32 @@ k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__
             rp2 += (double)sp;
             rd2 += (double)sd;
         }
-        const Law m = load_law<Law, T>(phase, mat, nparam, v);
         T B[NN];
 #pragma unroll
         for (int p = 0; p < NN; ++p) B[p] = L[p] + rho * G[p];
         bool conv;
-        const int it = newton<T, D>(m, F, B, rho, cap, ntol, conv);
+        int it;
+        if constexpr (MODEL == kLce) {
+            // director of the current iterate (same parity as F) and the explicit Frank force
+            const T* nCur = FIRST ? (par ? dir.N1 : dir.N0) : (par ? dir.N0 : dir.N1);
+            T* nNext = FIRST ? (par ? dir.N0 : dir.N1) : (par ? dir.N1 : dir.N0);
+            const T kf = (T)(2.0 * __ldg(mat + phase[v] * nparam + 4) * (double)n * (double)n);
+            T nv[3], fr[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T* c = nCur + i * V;
+                nv[i] = c[v];
+                fr[i] = kf * (c[nb.xp] + c[nb.xm] + c[nb.yp] + c[nb.ym] + c[nb.zp] + c[nb.zm]);
+            }
+            const Lce<T> m = load_lce<T>(phase, mat, nparam, v, dir.ref, V);
+            it = newton_lce<T>(m, F, nv, B, fr, rho, cap, ntol, conv);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) nNext[i * V + v] = nv[i];
+        } else {
+            using Law = typename LawOf<T, D, MODEL>::type;
+            const Law m = load_law<Law, T>(phase, mat, nparam, v);
+            it = newton<T, D>(m, F, B, rho, cap, ntol, conv);
+        }
         nmax = max(nmax, it);
         nfail += conv ? 0 : 1;
 #pragma unroll
@@ -682,8 +976,7 @@ k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__
 template <typename T, int D, int MODEL>
 __global__ void __launch_bounds__(kLocalThreads)
 k_stress(Ctrl* __restrict__ ctrl, double* __restrict__ partials, const T* F0, const T* F1, const T* Lam,
-         const uint8_t* __restrict__ phase, const double* __restrict__ mat, int nparam, long long V) {
-    using Law = typename LawOf<T, D, MODEL>::type;
+         const uint8_t* __restrict__ phase, const double* __restrict__ mat, int nparam, long long V, Dirs<T> dir) {
     constexpr int NN = D * D;
     __shared__ double s_sum[kLocalThreads / 32][2 * NN];
     __shared__ int s_last;
@@ -695,8 +988,15 @@ k_stress(Ctrl* __restrict__ ctrl, double* __restrict__ partials, const T* F0, co
         T Fv[NN], P[NN];
 #pragma unroll
         for (int p = 0; p < NN; ++p) Fv[p] = F[p * V + v];
-        const Law m = load_law<Law, T>(phase, mat, nparam, v);
-        m.stress(Fv, P);
+        if constexpr (MODEL == kLce) {
+            const T* Nk = (ctrl->k & 1) ? dir.N1 : dir.N0;
+            const T nv[3] = {Nk[v], Nk[V + v], Nk[2 * V + v]};
+            load_lce<T>(phase, mat, nparam, v, dir.ref, V).stress(Fv, nv, P);
+        } else {
+            using Law = typename LawOf<T, D, MODEL>::type;
+            const Law m = load_law<Law, T>(phase, mat, nparam, v);
+            m.stress(Fv, P);
+        }
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
             acc[p] += (double)P[p];
@@ -758,16 +1058,20 @@ k_stress(Ctrl* __restrict__ ctrl, double* __restrict__ partials, const T* F0, co
 // Copy the current state (F_k, Lambda_k, u~_k) between the float and double sets.
 template <typename S, typename Dd>
 __global__ void k_convert(const Ctrl* __restrict__ ctrl, const S* Fs0, const S* Fs1, const S* Ls, const S* Us0,
-                          const S* Us1, Dd* Fd0, Dd* Fd1, Dd* Ld, Dd* Ud0, Dd* Ud1, long long nF, long long nU) {
+                          const S* Us1, Dd* Fd0, Dd* Fd1, Dd* Ld, Dd* Ud0, Dd* Ud1, long long nF, long long nU,
+                          const S* Ns0, const S* Ns1, Dd* Nd0, Dd* Nd1, long long nN) {
     const int par = (int)(ctrl->k & 1);
     const S* Fs = par ? Fs1 : Fs0;
     const S* Us = par ? Us1 : Us0;
+    const S* Ns = par ? Ns1 : Ns0;
     Dd* Fd = par ? Fd1 : Fd0;
     Dd* Ud = par ? Ud1 : Ud0;
+    Dd* Nd = par ? Nd1 : Nd0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nF; i += (long long)gridDim.x * blockDim.x) {
         Fd[i] = (Dd)Fs[i];
         Ld[i] = (Dd)Ls[i];
         if (i < nU) Ud[i] = (Dd)Us[i];
+        if (i < nN) Nd[i] = (Dd)Ns[i];
     }
 }
 
@@ -780,19 +1084,21 @@ struct Set<double> {
     static double* F(const Launch& L, int i) { return L.F64[i]; }
     static double* Lm(const Launch& L) { return L.L64; }
     static double* U(const Launch& L, int i) { return L.U64[i]; }
+    static Dirs<double> dirs(const Launch& L) { return Dirs<double>{L.N64[0], L.N64[1], L.n0_64}; }
 };
 template <>
 struct Set<float> {
     static float* F(const Launch& L, int i) { return L.F32[i]; }
     static float* Lm(const Launch& L) { return L.L32; }
     static float* U(const Launch& L, int i) { return L.U32[i]; }
+    static Dirs<float> dirs(const Launch& L) { return Dirs<float>{L.N32[0], L.N32[1], L.n0_32}; }
 };
 
 template <typename T, int D, int MODEL>
 cudaError_t run_init(const Launch& L, bool lambda_zero) {
     k_init<T, D, MODEL><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
         L.ctrl, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0), Set<T>::U(L, 1), L.phase, L.mat,
-        L.nparam, L.V, lambda_zero ? 1 : 0);
+        L.nparam, L.V, lambda_zero ? 1 : 0, Set<T>::dirs(L));
     return cudaGetLastError();
 }
 
@@ -804,16 +1110,16 @@ cudaError_t run_local(const Launch& L, bool first, bool only_if, int mode) {
         L.phase, L.mat, L.nparam, L.n, L.V
     if (first)
         k_local<T, D, MODEL, true, false, false>
-            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, only_if ? 1 : 0, nullptr, nullptr);
+            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, only_if ? 1 : 0, nullptr, nullptr, Set<T>::dirs(L));
     else if (mode == 1 && std::is_same<T, double>::value)
         k_local<T, D, MODEL, false, true, false>
-            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, 0, L.R32, nullptr);
+            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, 0, L.R32, nullptr, Set<T>::dirs(L));
     else if (mode == 2 && std::is_same<T, double>::value)
         k_local<T, D, MODEL, false, true, true>
-            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, 0, L.R32, L.D32);
+            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, 0, L.R32, L.D32, Set<T>::dirs(L));
     else
         k_local<T, D, MODEL, false, false, false>
-            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, 0, nullptr, nullptr);
+            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, 0, nullptr, nullptr, Set<T>::dirs(L));
 #undef RVE_LOCAL_ARGS
     return cudaGetLastError();
 }
@@ -821,7 +1127,8 @@ cudaError_t run_local(const Launch& L, bool first, bool only_if, int mode) {
 template <typename T, int D, int MODEL>
 cudaError_t run_stress(const Launch& L) {
     k_stress<T, D, MODEL><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
-        L.ctrl, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), L.phase, L.mat, L.nparam, L.V);
+        L.ctrl, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), L.phase, L.mat, L.nparam, L.V,
+        Set<T>::dirs(L));
     return cudaGetLastError();
 }
 
@@ -831,6 +1138,7 @@ cudaError_t run_stress(const Launch& L) {
         if (L.dim == 3 && L.model == kNeoHooke) return FN<T, 3, kNeoHooke>(__VA_ARGS__);    \
         if (L.dim == 2 && L.model == kLinear) return FN<T, 2, kLinear>(__VA_ARGS__);        \
         if (L.dim == 3 && L.model == kLinear) return FN<T, 3, kLinear>(__VA_ARGS__);        \
+        if (L.dim == 3 && L.model == kLce) return FN<T, 3, kLce>(__VA_ARGS__);              \
         return cudaErrorInvalidValue;                                                       \
     } while (0)
 
@@ -854,15 +1162,18 @@ cudaError_t launch_stress(const Launch& L, bool fp64) {
 cudaError_t launch_convert(const Launch& L, bool to_fp64) {
     const long long nF = (long long)L.dim * L.dim * L.V;
     const long long nU = (long long)L.dim * L.V;
+    const long long nN = L.model == kLce ? 3 * L.V : 0;
     const int blocks = 152 * 8;
     if (to_fp64)
         k_convert<float, double><<<blocks, 256, 0, L.stream>>>(L.ctrl, L.F32[0], L.F32[1], L.L32, L.U32[0],
                                                                L.U32[1], L.F64[0], L.F64[1], L.L64, L.U64[0],
-                                                               L.U64[1], nF, nU);
+                                                               L.U64[1], nF, nU, L.N32[0], L.N32[1], L.N64[0],
+                                                               L.N64[1], nN);
     else
         k_convert<double, float><<<blocks, 256, 0, L.stream>>>(L.ctrl, L.F64[0], L.F64[1], L.L64, L.U64[0],
                                                                L.U64[1], L.F32[0], L.F32[1], L.L32, L.U32[0],
-                                                               L.U32[1], nF, nU);
+                                                               L.U32[1], nF, nU, L.N64[0], L.N64[1], L.N32[0],
+                                                               L.N32[1], nN);
     return cudaGetLastError();
 }
 

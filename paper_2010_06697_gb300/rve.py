@@ -329,13 +329,18 @@ class Rve:
         _check(rve_set_field(self.h, which, a), "rve_set_field")
 
     def state(self):
-        return {"F": self.get_field(RVE_FIELD_F), "Lam": self.get_field(RVE_FIELD_LAMBDA),
-                "u": self.get_field(RVE_FIELD_U)}
+        st = {"F": self.get_field(RVE_FIELD_F), "Lam": self.get_field(RVE_FIELD_LAMBDA),
+              "u": self.get_field(RVE_FIELD_U)}
+        if self.model == RVE_LCE:
+            st["n"] = self.get_field(RVE_FIELD_N)
+        return st
 
     def set_state(self, st):
         self.set_field(RVE_FIELD_F, st["F"])
         self.set_field(RVE_FIELD_LAMBDA, st["Lam"])
         self.set_field(RVE_FIELD_U, st["u"])
+        if self.model == RVE_LCE:
+            self.set_field(RVE_FIELD_N, st["n"])
 
     def reset(self):
         _check(rve_reset(self.h), "rve_reset")
