@@ -169,6 +169,35 @@ int rve_reset(rve_t h);
  * (up to cap entries).  Returns the number of entries written (>= 0) or an error. */
 int rve_history(rve_t h, double* r_p, double* r_d, double* rho, int cap);
 
+/* ------------------------------------------------------------------ batches */
+typedef struct rve_batch* rve_batch_t;
+
+/* Group existing handles (each with its material set) for batched solves of
+ * uneven RVEs.  Every per-iteration pass of all members runs as ONE persistent
+ * kernel launch over a tile table spanning the members (per group of members
+ * with the same model and dimension), and chunks of iterations are replayed as
+ * CUDA graphs.  Members keep their own state, options and sizes; they must share
+ * the precision mode and the rho policy.  A member's result is bitwise the same
+ * as solving it alone with rve_solve (its blocks, partial sums and reductions
+ * depend on its own size only).  The handles must outlive the batch and must not
+ * be used by other calls during rve_batch_solve.  cuda_stream as in rve_create.
+ * Allocates descriptors and tile tables with cudaMalloc.
+ * Errors: RVE_E_INVALID_ARG (count < 1, null handle, duplicate handle, mixed
+ * precision or rho policy), RVE_E_STATE (a member without material), RVE_E_OOM,
+ * RVE_E_CUDA. */
+int rve_batch_create(rve_batch_t* out, rve_t* handles, int count, void* cuda_stream);
+
+/* Solve every member at its own Fbars[9*i .. 9*i+8] (row-major) and rhos[i] to
+ * tol, as rve_solve does for one handle (same initialisation, warm start, stop
+ * rule and precision phases).  Members finish independently; a finished member
+ * leaves the tile tables.  infos (count entries, may be NULL) gets each member's
+ * result.  Returns RVE_OK if every member converged, else the status of the first
+ * member (in handle order) that did not. */
+int rve_batch_solve(rve_batch_t b, const double* Fbars, const double* rhos, double tol, rve_solve_info* infos);
+
+/* Release the batch (not its handles). */
+void rve_batch_destroy(rve_batch_t b);
+
 /* ------------------------------------------------------------------ profiling */
 /* Kernel classes of the iteration (index into rve_kernel_times' arrays). */
 enum rve_kernel_class {

@@ -13,6 +13,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -33,6 +35,8 @@ struct rve {
     size_t ws_bytes = 0;
     bool own_ws = false;
     Launch L{};
+    admm::Exec E{};         // tile-table execution of this RVE alone
+    Launch* d_L = nullptr;  // device copy of L (the descriptor the tile kernels read)
     Ctrl* hctrl = nullptr;  // pinned host mirror of the control block
     bool material_set = false;
     bool fresh = true;
@@ -73,22 +77,26 @@ int factor(int L, int* rad) {
     return L == 1 ? np : -1;
 }
 
-int local_blocks_for(long long V) {
-    const long long want = (V + admm::kLocalThreads - 1) / admm::kLocalThreads;
-    const long long cap = 152 * 12;  // whole waves at 2, 3, 4 or 6 resident blocks per SM
-    return (int)(want < cap ? want : cap);
-}
-
 struct Layout {
-    size_t ctrl, hist, partials, phase, mat;
+    size_t ctrl, hist, partials, phase, mat, desc, tiles[admm::kTileClasses];
     size_t F64[2], L64, U64[2], tw64, ksq64, N64[2], n064;
     size_t F32[2], L32, U32[2], tw32, ksq32, N32[2], n032;
     size_t total;
 };
 
+Launch geometry(int dim, int n) {
+    Launch g{};
+    g.dim = dim;
+    g.n = n;
+    g.V = dim == 3 ? (long long)n * n * n : (long long)n * n;
+    admm::set_geometry(g);
+    return g;
+}
+
 Layout layout(int dim, int n, int model, int precision, int max_iter) {
     Layout o{};
-    const long long V = dim == 3 ? (long long)n * n * n : (long long)n * n;
+    const Launch g = geometry(dim, n);
+    const long long V = g.V;
     const size_t nF = (size_t)dim * dim * V, nU = (size_t)dim * V;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -98,7 +106,12 @@ Layout layout(int dim, int n, int model, int precision, int max_iter) {
     };
     o.ctrl = take(sizeof(Ctrl));
     o.hist = take(sizeof(double) * 3 * (size_t)(max_iter + 1));
-    o.partials = take(sizeof(double) * admm::kPartialStride * (size_t)local_blocks_for(V));
+    o.partials = take(sizeof(double) * admm::kPartialStride * (size_t)g.local_blocks);
+    o.desc = take(sizeof(Launch));
+    o.tiles[admm::kTilesLocal] = take(sizeof(int2) * (size_t)admm::tiles_local(g));
+    o.tiles[admm::kTilesX] = take(sizeof(int2) * (size_t)admm::tiles_x(g));
+    o.tiles[admm::kTilesAx64] = take(sizeof(int2) * (size_t)admm::tiles_ax(g, true));
+    o.tiles[admm::kTilesAx32] = take(sizeof(int2) * (size_t)admm::tiles_ax(g, false));
     o.phase = take((size_t)V);
     o.mat = take(sizeof(double) * 256 * admm::kMaxParam);
     const bool need64 = precision != RVE_FP32;
@@ -142,16 +155,132 @@ Layout layout(int dim, int n, int model, int precision, int max_iter) {
         if (e_ != cudaSuccess) return RVE_E_CUDA; \
     } while (0)
 
-int read_ctrl(rve* h) {
-    CK(cudaMemcpyAsync(h->hctrl, h->L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+int read_ctrl_on(rve* h, cudaStream_t st) {
+    CK(cudaMemcpyAsync(h->hctrl, h->L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     h->k = h->hctrl->k;
     return RVE_OK;
 }
+int read_ctrl(rve* h) { return read_ctrl_on(h, h->stream); }
 
-int write_ctrl(rve* h) {
-    CK(cudaMemcpyAsync(h->L.ctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+int write_ctrl_on(rve* h, cudaStream_t st) {
+    CK(cudaMemcpyAsync(h->L.ctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
     return RVE_OK;
+}
+int write_ctrl(rve* h) { return write_ctrl_on(h, h->stream); }
+
+// Copy the host descriptor to the device copy the tile kernels read.
+int write_desc(rve* h) {
+    CK(cudaMemcpyAsync(h->d_L, &h->L, sizeof(Launch), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return RVE_OK;
+}
+
+int check_solve_args(const rve* h, const double Fbar[9], double rho, double tol) {
+    if (!h || !Fbar) return RVE_E_INVALID_ARG;
+    if (!h->material_set) return RVE_E_STATE;
+    if (!(rho > 0) || !isfinite(rho) || isnan(tol)) return RVE_E_INVALID_ARG;
+    for (int i = 0; i < 9; ++i)
+        if (!isfinite(Fbar[i])) return RVE_E_INVALID_ARG;
+    const double det2 = Fbar[0] * Fbar[4] - Fbar[1] * Fbar[3];
+    const double det3 = Fbar[0] * (Fbar[4] * Fbar[8] - Fbar[5] * Fbar[7]) -
+                        Fbar[1] * (Fbar[3] * Fbar[8] - Fbar[5] * Fbar[6]) +
+                        Fbar[2] * (Fbar[3] * Fbar[7] - Fbar[4] * Fbar[6]);
+    if (!((h->dim == 2 ? det2 : det3) > 0)) return RVE_E_INVALID_ARG;
+    return RVE_OK;
+}
+
+// Prepare the control block of a solve (Algorithm 1's initialisation) and, for a
+// fresh state, the initial fields; everything on stream st.  Leaves the first
+// precision phase ready to start (its FIRST local step not yet launched).
+int begin_solve(rve* h, const double Fbar[9], double rho, double tol, cudaStream_t st) {
+    const rve_options& o = h->opt;
+    int rc = read_ctrl_on(h, st);
+    if (rc) return rc;
+    Ctrl& c = *h->hctrl;
+    for (int i = 0; i < 9; ++i) c.Fbar[i] = Fbar[i];
+    c.rho = rho;
+    c.inv_rho = 1.0 / rho;
+    c.mu_ref = o.mu_ref > 0 ? o.mu_ref : h->mu_ref;
+    c.tol = tol;
+    c.rho_kappa = o.rho_kappa;
+    c.rho_tau = o.rho_tau;
+    c.rho_min = o.rho_min > 0 ? o.rho_min : c.mu_ref;
+    c.switch_tol = o.mixed_switch;
+    c.best = INFINITY;
+    c.stall = 0;
+    c.k_start = c.k;
+    c.k_cap = c.k + o.max_iter;
+    c.done = o.max_iter > 0 ? admm::kRunning : admm::kCapped;
+    c.adaptive = o.rho_policy == RVE_RHO_ADAPTIVE;
+    c.rho_changed = 0;
+    c.newton_cap = o.newton_max;
+    c.hist_cap = o.max_iter + 1;
+    c.counter = 0;
+    c.counter2 = 0;
+    c.newton_max = 0;
+    c.newton_fail = 0;
+    const bool fp32_first = o.precision != RVE_FP64;
+    c.phase_fp32 = fp32_first ? 1 : 0;
+    c.newton_tol = o.newton_tol > 0 ? o.newton_tol : (fp32_first ? 1e-5 : 1e-10);
+    if (write_ctrl_on(h, st)) return RVE_E_CUDA;
+    CK(cudaMemcpyAsync(h->d_L, &h->L, sizeof(Launch), cudaMemcpyHostToDevice, st));
+    Launch Ls = h->L;
+    Ls.stream = st;
+    if (h->fresh) {
+        h->launches += 1;
+        if (admm::launch_init(Ls, !fp32_first, o.lambda0 == RVE_LAMBDA0_ZERO) != cudaSuccess) return RVE_E_CUDA;
+        h->fresh = false;
+        h->state_fp64 = fp32_first ? 0 : 1;
+    } else if (fp32_first && h->state_fp64) {
+        h->launches += 1;
+        if (admm::launch_convert(Ls, false) != cudaSuccess) return RVE_E_CUDA;
+        h->state_fp64 = 0;
+    }
+    return RVE_OK;
+}
+
+// The switch of RVE_MIXED from the float phase to the double polish, on stream st.
+int switch_to_double(rve* h, cudaStream_t st) {
+    Launch Ls = h->L;
+    Ls.stream = st;
+    h->launches += 1;
+    if (admm::launch_convert(Ls, true) != cudaSuccess) return RVE_E_CUDA;
+    h->state_fp64 = 1;
+    h->hctrl->done = admm::kRunning;
+    h->hctrl->phase_fp32 = 0;
+    h->hctrl->counter = 0;
+    // polish: a step of max|dF| <= 1e-7 leaves an error of about 1e-6 * 1e-7 (float
+    // Hessian) + |dF|^2, i.e. ~1e-13, far below the double residual tolerance
+    h->hctrl->newton_tol = h->opt.newton_tol > 0 ? h->opt.newton_tol : 1e-7;
+    return write_ctrl_on(h, st);
+}
+
+int status_of(int done) {
+    switch (done) {
+        case admm::kConverged: return RVE_OK;
+        case admm::kNumerical: return RVE_E_NUMERICAL;
+        default: return RVE_E_NOT_CONVERGED;
+    }
+}
+
+void fill_info(rve* h, long long k0, int fp64_iters, double ms, rve_solve_info* info) {
+    const Ctrl& e = *h->hctrl;
+    const int status = status_of(e.done);
+    h->last_iters = (int)(e.k - k0);
+    if (!info) return;
+    info->iterations = h->last_iters;
+    info->fp64_iterations = fp64_iters;
+    info->converged = e.done == admm::kConverged;
+    info->status = status;
+    info->r_p = e.r_p;
+    info->r_d = e.r_d;
+    info->rho = e.rho;
+    info->mu_ref = e.mu_ref;
+    info->newton_max_iters = e.newton_max;
+    info->newton_fail = (long long)e.newton_fail;
+    info->time_ms = ms;
+    info->launches = h->launches;
 }
 
 // Order the handle's stream after everything already queued on the caller's stream.
@@ -199,14 +328,14 @@ int run_chunk_profiled(rve* h, bool fp64, bool incr) {
         cudaEvent_t* e = &h->pev[(size_t)i * per];
         CK(cudaEventRecord(e[0], h->stream));
         for (int st = 0; st < S; ++st) {
-            const cudaError_t le = incr ? admm::launch_fft_incr(h->L, st) : admm::launch_fft(h->L, fp64, st);
+            const cudaError_t le = incr ? admm::launch_fft_incr(h->E, st) : admm::launch_fft(h->E, fp64, st);
             if (le != cudaSuccess) return RVE_E_CUDA;
             CK(cudaEventRecord(e[1 + st], h->stream));
         }
-        if (admm::launch_local(h->L, fp64, false, false, incr ? 2 : 0) != cudaSuccess) return RVE_E_CUDA;
+        if (admm::launch_local(h->E, fp64, false, false, incr ? 2 : 0) != cudaSuccess) return RVE_E_CUDA;
         CK(cudaEventRecord(e[1 + S], h->stream));
         if (h->opt.rho_policy == RVE_RHO_ADAPTIVE) {
-            if (admm::launch_local(h->L, fp64, true, true) != cudaSuccess) return RVE_E_CUDA;
+            if (admm::launch_local(h->E, fp64, true, true) != cudaSuccess) return RVE_E_CUDA;
             CK(cudaEventRecord(e[2 + S], h->stream));
         }
     }
@@ -237,9 +366,9 @@ int capture_chunk(rve* h, bool fp64, bool incr, int slot) {
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < h->opt.check_every && e == cudaSuccess; ++i) {
-        e = incr ? admm::launch_fft_incr(h->L) : admm::launch_fft(h->L, fp64);
-        if (e == cudaSuccess) e = admm::launch_local(h->L, fp64, false, false, incr ? 2 : 0);
-        if (e == cudaSuccess && h->opt.rho_policy == RVE_RHO_ADAPTIVE) e = admm::launch_local(h->L, fp64, true, true);
+        e = incr ? admm::launch_fft_incr(h->E) : admm::launch_fft(h->E, fp64);
+        if (e == cudaSuccess) e = admm::launch_local(h->E, fp64, false, false, incr ? 2 : 0);
+        if (e == cudaSuccess && h->opt.rho_policy == RVE_RHO_ADAPTIVE) e = admm::launch_local(h->E, fp64, true, true);
     }
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -259,18 +388,18 @@ int run_phase(rve* h, bool fp64, bool polish = false) {
         if (ensure_prof_events(h)) return RVE_E_CUDA;
         const size_t last = h->pev.size() - 2;
         CK(cudaEventRecord(h->pev[last], h->stream));
-        if (admm::launch_local(h->L, fp64, true, false) != cudaSuccess) return RVE_E_CUDA;
+        if (admm::launch_local(h->E, fp64, true, false) != cudaSuccess) return RVE_E_CUDA;
         CK(cudaEventRecord(h->pev[last + 1], h->stream));
         CK(cudaEventSynchronize(h->pev[last + 1]));
         h->prof_ms[fp64 ? 1 : 0][RVE_KCLASS_LOCAL_FIRST] += elapsed(h->pev[last], h->pev[last + 1]);
         h->prof_n[fp64 ? 1 : 0][RVE_KCLASS_LOCAL_FIRST] += 1;
-    } else if (admm::launch_local(h->L, fp64, true, false) != cudaSuccess) {
+    } else if (admm::launch_local(h->E, fp64, true, false) != cudaSuccess) {
         return RVE_E_CUDA;
     }
     h->launches += 1;
     if (polish) {
-        if (admm::launch_fft(h->L, true) != cudaSuccess) return RVE_E_CUDA;
-        if (admm::launch_local(h->L, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
+        if (admm::launch_fft(h->E, true) != cudaSuccess) return RVE_E_CUDA;
+        if (admm::launch_local(h->E, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
         h->launches += admm::fft_stages(h->dim) + 1;
         const int rc = read_ctrl(h);
         if (rc) return rc;
@@ -293,11 +422,11 @@ int run_phase(rve* h, bool fp64, bool polish = false) {
             CK(cudaGraphLaunch(h->graph[slot], h->stream));
         } else {
             for (int i = 0; i < h->opt.check_every; ++i) {
-                const cudaError_t fe = polish ? admm::launch_fft_incr(h->L) : admm::launch_fft(h->L, fp64);
+                const cudaError_t fe = polish ? admm::launch_fft_incr(h->E) : admm::launch_fft(h->E, fp64);
                 if (fe != cudaSuccess) return RVE_E_CUDA;
-                if (admm::launch_local(h->L, fp64, false, false, polish ? 2 : 0) != cudaSuccess) return RVE_E_CUDA;
+                if (admm::launch_local(h->E, fp64, false, false, polish ? 2 : 0) != cudaSuccess) return RVE_E_CUDA;
                 if (h->opt.rho_policy == RVE_RHO_ADAPTIVE &&
-                    admm::launch_local(h->L, fp64, true, true) != cudaSuccess)
+                    admm::launch_local(h->E, fp64, true, true) != cudaSuccess)
                     return RVE_E_CUDA;
             }
         }
@@ -395,7 +524,7 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
     L.n = n;
     L.model = model;
     L.V = h->V;
-    L.local_blocks = local_blocks_for(h->V);
+    admm::set_geometry(L);
     L.ctrl = (Ctrl*)(b + lay.ctrl);
     L.hist = (double*)(b + lay.hist);
     L.partials = (double*)(b + lay.partials);
@@ -442,6 +571,32 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
     L.plan.np_full = factor(n, L.plan.rad_full);
     if (L.plan.np_half < 0 || L.plan.np_full < 0) return fail(RVE_E_INVALID_ARG);
     if (admm::prepare_fft_kernels(n) != cudaSuccess) return fail(RVE_E_CUDA);
+    // single-RVE execution: descriptor and tile tables (RVE index 0) in the workspace
+    h->d_L = (Launch*)(b + lay.desc);
+    {
+        std::vector<int2> t;
+        admm::Exec& E = h->E;
+        E.stream = h->stream;
+        E.rep = &h->L;
+        E.rds = h->d_L;
+        const int counts[admm::kTileClasses] = {admm::tiles_local(L), admm::tiles_x(L), admm::tiles_ax(L, true),
+                                                admm::tiles_ax(L, false)};
+        for (int c = 0; c < admm::kTileClasses; ++c) {
+            t.resize(counts[c]);
+            for (int i = 0; i < counts[c]; ++i) t[i] = make_int2(0, i);
+            int2* dst = (int2*)(b + lay.tiles[c]);
+            if (cudaMemcpyAsync(dst, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(h->stream) != cudaSuccess)
+                return fail(RVE_E_CUDA);
+            E.tiles[c] = dst;
+            E.ntiles[c] = counts[c];
+        }
+        for (int f = 0; f < 2; ++f) {
+            E.smem_x[f] = admm::smem_x_bytes(L, f == 1);
+            E.smem_a[f] = admm::smem_a_bytes(L, f == 1);
+        }
+    }
     h->state_fp64 = o.precision == RVE_FP64 ? 1 : 0;
     h->hctrl->hist_cap = o.max_iter + 1;
     if (write_ctrl(h)) return fail(RVE_E_CUDA);
@@ -571,76 +726,23 @@ int rve_reset(rve_t h) {
 }
 
 int rve_solve(rve_t h, const double Fbar[9], double rho, double tol, rve_solve_info* info) {
-    if (!h || !Fbar) return RVE_E_INVALID_ARG;
-    if (!h->material_set) return RVE_E_STATE;
-    if (!(rho > 0) || !isfinite(rho) || isnan(tol)) return RVE_E_INVALID_ARG;
-    for (int i = 0; i < 9; ++i)
-        if (!isfinite(Fbar[i])) return RVE_E_INVALID_ARG;
-    const double det2 = Fbar[0] * Fbar[4] - Fbar[1] * Fbar[3];
-    const double det3 = Fbar[0] * (Fbar[4] * Fbar[8] - Fbar[5] * Fbar[7]) -
-                        Fbar[1] * (Fbar[3] * Fbar[8] - Fbar[5] * Fbar[6]) +
-                        Fbar[2] * (Fbar[3] * Fbar[7] - Fbar[4] * Fbar[6]);
-    if (!((h->dim == 2 ? det2 : det3) > 0)) return RVE_E_INVALID_ARG;
+    int rc = check_solve_args(h, Fbar, rho, tol);
+    if (rc) return rc;
     const rve_options& o = h->opt;
     if (enter(h)) return RVE_E_CUDA;
-    int rc = read_ctrl(h);
-    if (rc) return rc;
-    Ctrl& c = *h->hctrl;
-    for (int i = 0; i < 9; ++i) c.Fbar[i] = Fbar[i];
-    c.rho = rho;
-    c.inv_rho = 1.0 / rho;
-    c.mu_ref = o.mu_ref > 0 ? o.mu_ref : h->mu_ref;
-    c.tol = tol;
-    c.rho_kappa = o.rho_kappa;
-    c.rho_tau = o.rho_tau;
-    c.rho_min = o.rho_min > 0 ? o.rho_min : c.mu_ref;
-    c.switch_tol = o.mixed_switch;
-    c.best = INFINITY;
-    c.stall = 0;
-    c.k_start = c.k;
-    c.k_cap = c.k + o.max_iter;
-    c.done = o.max_iter > 0 ? admm::kRunning : admm::kCapped;
-    c.adaptive = o.rho_policy == RVE_RHO_ADAPTIVE;
-    c.rho_changed = 0;
-    c.newton_cap = o.newton_max;
-    c.hist_cap = o.max_iter + 1;
-    c.counter = 0;
-    c.counter2 = 0;
-    c.newton_max = 0;
-    c.newton_fail = 0;
-    const bool fp32_first = o.precision != RVE_FP64;
-    c.phase_fp32 = fp32_first ? 1 : 0;
-    c.newton_tol = o.newton_tol > 0 ? o.newton_tol : (fp32_first ? 1e-5 : 1e-10);
-    if (write_ctrl(h)) return RVE_E_CUDA;
-    CK(cudaEventRecord(h->ev0, h->stream));
     h->launches = 0;
-    if (h->fresh) {
-        h->launches += 1;
-        if (admm::launch_init(h->L, !fp32_first, o.lambda0 == RVE_LAMBDA0_ZERO) != cudaSuccess) return RVE_E_CUDA;
-        h->fresh = false;
-        h->state_fp64 = fp32_first ? 0 : 1;
-    } else if (fp32_first && h->state_fp64) {
-        h->launches += 1;
-        if (admm::launch_convert(h->L, false) != cudaSuccess) return RVE_E_CUDA;
-        h->state_fp64 = 0;
-    }
-    const long long k0 = c.k;
+    CK(cudaEventRecord(h->ev0, h->stream));
+    rc = begin_solve(h, Fbar, rho, tol, h->stream);
+    if (rc) return rc;
+    const bool fp32_first = o.precision != RVE_FP64;
+    const long long k0 = h->hctrl->k;
     int fp64_iters = 0;
-    if (c.done == admm::kRunning) {
+    if (h->hctrl->done == admm::kRunning) {
         rc = run_phase(h, !fp32_first);
         if (rc) return rc;
         if (o.precision == RVE_MIXED && h->hctrl->done == admm::kSwitch) {
             const long long ksw = h->hctrl->k;
-            h->launches += 1;
-            if (admm::launch_convert(h->L, true) != cudaSuccess) return RVE_E_CUDA;
-            h->state_fp64 = 1;
-            h->hctrl->done = admm::kRunning;
-            h->hctrl->phase_fp32 = 0;
-            h->hctrl->counter = 0;
-            // polish: a step of max|dF| <= 1e-7 leaves an error of about 1e-6 * 1e-7 (float
-            // Hessian) + |dF|^2, i.e. ~1e-13, far below the double residual tolerance
-            h->hctrl->newton_tol = o.newton_tol > 0 ? o.newton_tol : 1e-7;
-            if (write_ctrl(h)) return RVE_E_CUDA;
+            if (switch_to_double(h, h->stream)) return RVE_E_CUDA;
             rc = run_phase(h, true, o.rho_policy == RVE_RHO_FIXED);
             if (rc) return rc;
             fp64_iters = (int)(h->hctrl->k - ksw);
@@ -653,29 +755,8 @@ int rve_solve(rve_t h, const double Fbar[9], double rho, double tol, rve_solve_i
     if (read_ctrl(h)) return RVE_E_CUDA;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-    const Ctrl& e = *h->hctrl;
-    int status;
-    switch (e.done) {
-        case admm::kConverged: status = RVE_OK; break;
-        case admm::kNumerical: status = RVE_E_NUMERICAL; break;
-        default: status = RVE_E_NOT_CONVERGED; break;
-    }
-    h->last_iters = (int)(e.k - k0);
-    if (info) {
-        info->iterations = h->last_iters;
-        info->fp64_iterations = fp64_iters;
-        info->converged = e.done == admm::kConverged;
-        info->status = status;
-        info->r_p = e.r_p;
-        info->r_d = e.r_d;
-        info->rho = e.rho;
-        info->mu_ref = e.mu_ref;
-        info->newton_max_iters = e.newton_max;
-        info->newton_fail = (long long)e.newton_fail;
-        info->time_ms = ms;
-        info->launches = h->launches;
-    }
-    return status;
+    fill_info(h, k0, fp64_iters, ms, info);
+    return status_of(h->hctrl->done);
 }
 
 int rve_stress(rve_t h, double S[9]) {
@@ -816,6 +897,302 @@ const char* rve_strerror(int code) {
         case RVE_E_NOT_FOUND: return "unknown ticket";
         default: return "unknown status";
     }
+}
+
+}  // extern "C"
+
+// ================================================================== batches
+
+namespace {
+
+// (done, k) of every member's control block, for the host's per-chunk check.
+__global__ void k_gather_status(const Launch* __restrict__ rds, int count, long long* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const Ctrl* c = rds[i].ctrl;
+        out[2 * i] = c->done;
+        out[2 * i + 1] = c->k;
+    }
+}
+
+enum Stage : int { kStageF32 = 0, kStageF64 = 1, kStagePolish = 2, kStages = 3 };
+
+struct BatchRun {  // the members of one (group, stage) that are still iterating
+    std::vector<int> active;
+    admm::Exec E{};
+    int2* d_tiles[admm::kTileClasses] = {};
+    int cap[admm::kTileClasses] = {};
+    cudaGraphExec_t graph = nullptr;
+    bool dirty = true;
+};
+
+}  // namespace
+
+struct rve_batch {
+    std::vector<rve*> m;
+    std::vector<int> group_of;  // member -> group
+    int ngroups = 0;
+    cudaStream_t user_stream = nullptr, stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev0 = nullptr, ev1 = nullptr;
+    Launch* d_rds = nullptr;
+    long long* d_status = nullptr;
+    long long* h_status = nullptr;
+    std::vector<BatchRun> runs;  // [group * kStages + stage]
+};
+
+namespace {
+
+int batch_upload_tiles(rve_batch* b, BatchRun& r) {
+    std::vector<int2> t;
+    for (int c = 0; c < admm::kTileClasses; ++c) {
+        t.clear();
+        for (int i : r.active) {
+            const Launch& L = b->m[i]->L;
+            const int cnt = c == admm::kTilesLocal ? admm::tiles_local(L)
+                          : c == admm::kTilesX     ? admm::tiles_x(L)
+                                                   : admm::tiles_ax(L, c == admm::kTilesAx64);
+            for (int j = 0; j < cnt; ++j) t.push_back(make_int2(i, j));
+        }
+        if ((int)t.size() > r.cap[c]) {
+            if (r.d_tiles[c]) cudaFree(r.d_tiles[c]);
+            r.d_tiles[c] = nullptr;
+            r.cap[c] = 0;
+            if (cudaMalloc((void**)&r.d_tiles[c], std::max<size_t>(t.size(), 1) * sizeof(int2)) != cudaSuccess)
+                return RVE_E_OOM;
+            r.cap[c] = (int)t.size();
+        }
+        if (!t.empty())
+            CK(cudaMemcpyAsync(r.d_tiles[c], t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        r.E.tiles[c] = r.d_tiles[c];
+        r.E.ntiles[c] = (int)t.size();
+    }
+    r.E.stream = b->stream;
+    r.E.rds = b->d_rds;
+    r.E.rep = &b->m[r.active.front()]->L;
+    for (int f = 0; f < 2; ++f) {
+        r.E.smem_x[f] = 0;
+        r.E.smem_a[f] = 0;
+        for (int i : r.active) {
+            r.E.smem_x[f] = std::max(r.E.smem_x[f], admm::smem_x_bytes(b->m[i]->L, f == 1));
+            r.E.smem_a[f] = std::max(r.E.smem_a[f], admm::smem_a_bytes(b->m[i]->L, f == 1));
+        }
+    }
+    if (r.graph) {
+        cudaGraphExecDestroy(r.graph);
+        r.graph = nullptr;
+    }
+    r.dirty = false;
+    return RVE_OK;
+}
+
+// one chunk of iterations for the members of run r (captured once per membership)
+int batch_chunk(rve_batch* b, BatchRun& r, int stage) {
+    const rve_options& o = b->m[r.active.front()]->opt;
+    const bool fp64 = stage != kStageF32;
+    const bool polish = stage == kStagePolish;
+    auto body = [&]() -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < o.check_every && e == cudaSuccess; ++i) {
+            e = polish ? admm::launch_fft_incr(r.E) : admm::launch_fft(r.E, fp64);
+            if (e == cudaSuccess) e = admm::launch_local(r.E, fp64, false, false, polish ? 2 : 0);
+            if (e == cudaSuccess && o.rho_policy == RVE_RHO_ADAPTIVE) e = admm::launch_local(r.E, fp64, true, true);
+        }
+        return e;
+    };
+    if (!o.use_graph) return body() == cudaSuccess ? RVE_OK : RVE_E_CUDA;
+    if (!r.graph) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t e = body();
+        const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return RVE_E_CUDA;
+        }
+        const cudaError_t e3 = cudaGraphInstantiate(&r.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e3 != cudaSuccess) return RVE_E_CUDA;
+    }
+    CK(cudaGraphLaunch(r.graph, b->stream));
+    return RVE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rve_batch_create(rve_batch_t* out, rve_t* handles, int count, void* cuda_stream) {
+    if (!out || !handles || count < 1) return RVE_E_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        if (!handles[i]) return RVE_E_INVALID_ARG;
+        if (!handles[i]->material_set) return RVE_E_STATE;
+        if (handles[i]->opt.precision != handles[0]->opt.precision ||
+            handles[i]->opt.rho_policy != handles[0]->opt.rho_policy)
+            return RVE_E_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (handles[j] == handles[i]) return RVE_E_INVALID_ARG;
+    }
+    rve_batch* b = new (std::nothrow) rve_batch();
+    if (!b) return RVE_E_OOM;
+    auto fail = [&](int code) {
+        rve_batch_destroy(b);
+        return code;
+    };
+    b->m.assign(handles, handles + count);
+    std::vector<std::pair<int, int>> keys;
+    for (rve* h : b->m) {
+        const std::pair<int, int> key(h->dim, h->model);
+        auto it = std::find(keys.begin(), keys.end(), key);
+        if (it == keys.end()) {
+            keys.push_back(key);
+            b->group_of.push_back((int)keys.size() - 1);
+        } else {
+            b->group_of.push_back((int)(it - keys.begin()));
+        }
+    }
+    b->ngroups = (int)keys.size();
+    b->runs.resize((size_t)b->ngroups * kStages);
+    b->user_stream = (cudaStream_t)cuda_stream;
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(RVE_E_CUDA);
+    if (cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess) return fail(RVE_E_CUDA);
+    if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) return fail(RVE_E_CUDA);
+    if (cudaMalloc((void**)&b->d_rds, sizeof(Launch) * count) != cudaSuccess) return fail(RVE_E_OOM);
+    if (cudaMalloc((void**)&b->d_status, sizeof(long long) * 2 * count) != cudaSuccess) return fail(RVE_E_OOM);
+    if (cudaMallocHost((void**)&b->h_status, sizeof(long long) * 2 * count) != cudaSuccess) return fail(RVE_E_OOM);
+    *out = b;
+    return RVE_OK;
+}
+
+void rve_batch_destroy(rve_batch_t b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (BatchRun& r : b->runs) {
+        if (r.graph) cudaGraphExecDestroy(r.graph);
+        for (int c = 0; c < admm::kTileClasses; ++c)
+            if (r.d_tiles[c]) cudaFree(r.d_tiles[c]);
+    }
+    if (b->d_rds) cudaFree(b->d_rds);
+    if (b->d_status) cudaFree(b->d_status);
+    if (b->h_status) cudaFreeHost(b->h_status);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int rve_batch_solve(rve_batch_t b, const double* Fbars, const double* rhos, double tol, rve_solve_info* infos) {
+    if (!b || !Fbars || !rhos) return RVE_E_INVALID_ARG;
+    const int count = (int)b->m.size();
+    for (int i = 0; i < count; ++i) {
+        const int rc = check_solve_args(b->m[i], Fbars + 9 * i, rhos[i], tol);
+        if (rc) return rc;
+    }
+    const int precision = b->m[0]->opt.precision;
+    const bool fixed_rho = b->m[0]->opt.rho_policy == RVE_RHO_FIXED;
+    CK(cudaEventRecord(b->ev_in, b->user_stream));
+    CK(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+    CK(cudaEventRecord(b->ev0, b->stream));
+    std::vector<int> stage(count), running(count, 0), fp64_iters(count, 0);
+    std::vector<long long> k0(count), ksw(count, -1);
+    for (BatchRun& r : b->runs) {
+        r.active.clear();
+        r.dirty = true;
+    }
+    for (int i = 0; i < count; ++i) {
+        rve* h = b->m[i];
+        h->launches = 0;
+        const int rc = begin_solve(h, Fbars + 9 * i, rhos[i], tol, b->stream);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(b->d_rds + i, &h->L, sizeof(Launch), cudaMemcpyHostToDevice, b->stream));
+        k0[i] = h->hctrl->k;
+        stage[i] = precision == RVE_FP64 ? kStageF64 : kStageF32;
+        running[i] = h->hctrl->done == admm::kRunning;
+        if (running[i]) b->runs[b->group_of[i] * kStages + stage[i]].active.push_back(i);
+    }
+    CK(cudaStreamSynchronize(b->stream));
+    // first local step of every running member, one launch per (group, stage)
+    for (int g = 0; g < b->ngroups; ++g)
+        for (int st = 0; st < kStages; ++st) {
+            BatchRun& r = b->runs[g * kStages + st];
+            if (r.active.empty()) continue;
+            int rc = batch_upload_tiles(b, r);
+            if (rc) return rc;
+            if (admm::launch_local(r.E, st != kStageF32, true, false) != cudaSuccess) return RVE_E_CUDA;
+            for (int i : r.active) b->m[i]->launches += 1;
+        }
+    for (;;) {
+        bool any = false;
+        for (int g = 0; g < b->ngroups; ++g)
+            for (int st = 0; st < kStages; ++st) {
+                BatchRun& r = b->runs[g * kStages + st];
+                if (r.active.empty()) continue;
+                any = true;
+                if (r.dirty) {
+                    const int rc = batch_upload_tiles(b, r);
+                    if (rc) return rc;
+                }
+                const int rc = batch_chunk(b, r, st);
+                if (rc) return rc;
+                const int per = admm::fft_stages(b->m[r.active.front()]->dim) + 1 + (fixed_rho ? 0 : 1);
+                for (int i : r.active) b->m[i]->launches += (long long)b->m[i]->opt.check_every * per;
+            }
+        if (!any) break;
+        k_gather_status<<<(count + 127) / 128, 128, 0, b->stream>>>(b->d_rds, count, b->d_status);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(long long) * 2 * count, cudaMemcpyDeviceToHost,
+                           b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        for (int i = 0; i < count; ++i) {
+            if (!running[i] || b->h_status[2 * i] == admm::kRunning) continue;
+            rve* h = b->m[i];
+            BatchRun& from = b->runs[b->group_of[i] * kStages + stage[i]];
+            from.active.erase(std::find(from.active.begin(), from.active.end(), i));
+            from.dirty = true;
+            if (read_ctrl_on(h, b->stream)) return RVE_E_CUDA;
+            if (precision == RVE_MIXED && stage[i] == kStageF32 && h->hctrl->done == admm::kSwitch) {
+                ksw[i] = h->hctrl->k;
+                if (switch_to_double(h, b->stream)) return RVE_E_CUDA;
+                // the member's first double iterations (local step, one full double projection,
+                // local step writing R) run on its own tile tables
+                admm::Exec Ei = h->E;
+                Ei.stream = b->stream;
+                if (admm::launch_local(Ei, true, true, false) != cudaSuccess) return RVE_E_CUDA;
+                if (fixed_rho) {
+                    if (admm::launch_fft(Ei, true) != cudaSuccess) return RVE_E_CUDA;
+                    if (admm::launch_local(Ei, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
+                    h->launches += admm::fft_stages(h->dim) + 2;
+                } else {
+                    h->launches += 1;
+                }
+                stage[i] = fixed_rho ? kStagePolish : kStageF64;
+                BatchRun& to = b->runs[b->group_of[i] * kStages + stage[i]];
+                to.active.push_back(i);
+                std::sort(to.active.begin(), to.active.end());
+                to.dirty = true;
+            } else {
+                running[i] = 0;
+            }
+        }
+    }
+    CK(cudaEventRecord(b->ev1, b->stream));
+    CK(cudaEventSynchronize(b->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+    int status = RVE_OK;
+    for (int i = 0; i < count; ++i) {
+        rve* h = b->m[i];
+        if (read_ctrl_on(h, b->stream)) return RVE_E_CUDA;
+        if (precision == RVE_FP64)
+            fp64_iters[i] = (int)(h->hctrl->k - k0[i]);
+        else if (ksw[i] >= 0)
+            fp64_iters[i] = (int)(h->hctrl->k - ksw[i]);
+        fill_info(h, k0[i], fp64_iters[i], ms, infos ? infos + i : nullptr);
+        const int st = status_of(h->hctrl->done);
+        if (status == RVE_OK && st != RVE_OK) status = st;
+    }
+    return status;
 }
 
 }  // extern "C"

@@ -31,7 +31,10 @@
 // the host in double.
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "rve_internal.cuh"
 
@@ -199,6 +202,29 @@ __device__ __forceinline__ void load_twiddles(V* s_tw, const V* __restrict__ g_t
     for (int i = threadIdx.x; i < n; i += blockDim.x) s_tw[i] = g_tw[i];
 }
 
+template <typename T>
+struct FftArgs;
+template <>
+struct FftArgs<double> {
+    __host__ __device__ static double* U(const Launch& L, int i) { return L.U64[i]; }
+    __host__ __device__ static const double* F(const Launch& L, int i) { return L.F64[i]; }
+    __host__ __device__ static const double* Lm(const Launch& L) { return L.L64; }
+    __host__ __device__ static const double2* tw(const Launch& L) { return L.tw64; }
+    __host__ __device__ static const double* ksq(const Launch& L) { return L.ksq64; }
+    __host__ __device__ static int tile(const Launch& L) { return L.tk64; }
+    static constexpr int tk = 8;
+};
+template <>
+struct FftArgs<float> {
+    __host__ __device__ static float* U(const Launch& L, int i) { return L.U32[i]; }
+    __host__ __device__ static const float* F(const Launch& L, int i) { return L.F32[i]; }
+    __host__ __device__ static const float* Lm(const Launch& L) { return L.L32; }
+    __host__ __device__ static const float2* tw(const Launch& L) { return L.tw32; }
+    __host__ __device__ static const float* ksq(const Launch& L) { return L.ksq32; }
+    __host__ __device__ static int tile(const Launch& L) { return L.tk32; }
+    static constexpr int tk = 16;
+};
+
 // ------------------------------------------------------------------ x passes
 
 // Divergence of Q = F_{k+1} - Lambda_k / rho (D^T Q = minus the central
@@ -206,11 +232,19 @@ __device__ __forceinline__ void load_twiddles(V* s_tw, const V* __restrict__ g_t
 // INCR: Q is the increment R given in F0 (= F1), Lambda is not read, and the
 // spectrum goes to U0 (= U1).
 template <typename T, int D, bool INCR>
-__global__ void __launch_bounds__(kFftThreads)
-k_xfwd(const Ctrl* __restrict__ ctrl, const T* F0, const T* F1, const T* __restrict__ Lam, T* U0, T* U1,
-       const typename Cx<T>::t* __restrict__ g_tw, FftPlan plan, int lpb) {
+__device__ __forceinline__ void xfwd_tile(const Launch& L, int bid) {
     using V = typename Cx<T>::t;
+    using Args = FftArgs<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Ctrl* __restrict__ ctrl = L.ctrl;
+    const T* F0 = INCR ? (const T*)L.R32 : Args::F(L, 0);
+    const T* F1 = INCR ? (const T*)L.R32 : Args::F(L, 1);
+    const T* __restrict__ Lam = Args::Lm(L);
+    T* U0 = INCR ? (T*)L.S32 : Args::U(L, 0);
+    T* U1 = INCR ? (T*)L.S32 : Args::U(L, 1);
+    const V* __restrict__ g_tw = Args::tw(L);
+    const FftPlan& plan = L.plan;
+    const int lpb = L.lpb;
     if (ctrl->done) return;
     const int n = plan.n, H = n / 2;
     const long long Vn = (D == 3) ? (long long)n * n * n : (long long)n * n;
@@ -226,7 +260,7 @@ k_xfwd(const Ctrl* __restrict__ ctrl, const T* F0, const T* F1, const T* __restr
     V* B = A + lpb * H;
     T* Ar = reinterpret_cast<T*>(A);
     load_twiddles(s_tw, g_tw, n);
-    const int line0 = blockIdx.x * lpb;
+    const int line0 = bid * lpb;
     const long long sn = n, s2 = sn * sn;
 
     for (int c = 0; c < D; ++c) {
@@ -291,11 +325,19 @@ k_xfwd(const Ctrl* __restrict__ ctrl, const T* F0, const T* F1, const T* __restr
 // the precision TO of the state buffers O0/O1.
 // INCR also stores the float increment itself in DUout (read by the next local step for r_d).
 template <typename T, typename TO, int D, bool INCR>
-__global__ void __launch_bounds__(kFftThreads)
-k_xinv(const Ctrl* __restrict__ ctrl, T* S0, T* S1, TO* O0, TO* O1, const typename Cx<T>::t* __restrict__ g_tw,
-       FftPlan plan, int lpb, T* __restrict__ DUout) {
+__device__ __forceinline__ void xinv_tile(const Launch& L, int bid) {
     using V = typename Cx<T>::t;
+    using Args = FftArgs<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Ctrl* __restrict__ ctrl = L.ctrl;
+    T* S0 = INCR ? (T*)L.S32 : Args::U(L, 0);
+    T* S1 = INCR ? (T*)L.S32 : Args::U(L, 1);
+    TO* O0 = INCR ? (TO*)L.U64[0] : (TO*)Args::U(L, 0);
+    TO* O1 = INCR ? (TO*)L.U64[1] : (TO*)Args::U(L, 1);
+    T* __restrict__ DUout = (T*)L.D32;
+    const V* __restrict__ g_tw = Args::tw(L);
+    const FftPlan& plan = L.plan;
+    const int lpb = L.lpb;
     if (ctrl->done) return;
     const int n = plan.n, H = n / 2;
     const long long Vn = (D == 3) ? (long long)n * n * n : (long long)n * n;
@@ -309,7 +351,7 @@ k_xinv(const Ctrl* __restrict__ ctrl, T* S0, T* S1, TO* O0, TO* O1, const typena
     V* B = A + lpb * H;
     load_twiddles(s_tw, g_tw, n);
     __syncthreads();
-    const int line0 = blockIdx.x * lpb;
+    const int line0 = bid * lpb;
     for (int c = 0; c < D; ++c) {
         V* S_c = S + (long long)c * (Vn / 2);
         for (int idx = threadIdx.x; idx < lpb * H; idx += blockDim.x) {
@@ -355,12 +397,19 @@ k_xinv(const Ctrl* __restrict__ ctrl, T* S0, T* S1, TO* O0, TO* O1, const typena
 
 // FFT along AXIS (1 = y, 2 = z) of tiles of `tk` adjacent x-frequency columns.
 // MODE 0: forward; 1: inverse; 2: forward, multiply by scale/|k|^2, inverse.
-template <typename T, int D, int AXIS, int MODE>
-__global__ void __launch_bounds__(kFftThreads)
-k_faxis(const Ctrl* __restrict__ ctrl, T* U0, T* U1, const typename Cx<T>::t* __restrict__ g_tw,
-        const T* __restrict__ ksq, FftPlan plan, int tk, T scale) {
+template <typename T, int D, int AXIS, int MODE, bool INCR>
+__device__ __forceinline__ void faxis_tile(const Launch& L, int bid) {
     using V = typename Cx<T>::t;
+    using Args = FftArgs<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Ctrl* __restrict__ ctrl = L.ctrl;
+    T* U0 = INCR ? (T*)L.S32 : Args::U(L, 0);
+    T* U1 = INCR ? (T*)L.S32 : Args::U(L, 1);
+    const V* __restrict__ g_tw = Args::tw(L);
+    const T* __restrict__ ksq = Args::ksq(L);
+    const FftPlan& plan = L.plan;
+    const int tk = Args::tile(L);
+    const T scale = (T)(2.0 / (double)L.V);
     if (ctrl->done) return;
     const int n = plan.n, H = n / 2;
     const long long Vn = (D == 3) ? (long long)n * n * n : (long long)n * n;
@@ -371,9 +420,11 @@ k_faxis(const Ctrl* __restrict__ ctrl, T* U0, T* U1, const typename Cx<T>::t* __
     V* Y = X + n * tk;
     load_twiddles(s_tw, g_tw, n);
 
-    const int col0 = blockIdx.x * tk;
-    const int outer = blockIdx.y;
-    const int c = blockIdx.z;
+    const int gxa = (H + tk - 1) / tk;
+    const int gya = (D == 3) ? n : 1;
+    const int col0 = (bid % gxa) * tk;
+    const int outer = (bid / gxa) % gya;
+    const int c = bid / (gxa * gya);
     long long base, es_g;
     if (D == 3 && AXIS == 1) {
         base = (long long)c * (Vn / 2) + (long long)outer * n * H + col0;
@@ -419,27 +470,6 @@ k_faxis(const Ctrl* __restrict__ ctrl, T* U0, T* U1, const typename Cx<T>::t* __
 
 // ------------------------------------------------------------------ launch
 
-template <typename T>
-struct FftArgs;
-template <>
-struct FftArgs<double> {
-    static double* U(const Launch& L, int i) { return L.U64[i]; }
-    static const double* F(const Launch& L, int i) { return L.F64[i]; }
-    static const double* Lm(const Launch& L) { return L.L64; }
-    static const double2* tw(const Launch& L) { return L.tw64; }
-    static const double* ksq(const Launch& L) { return L.ksq64; }
-    static constexpr int tk = 8;
-};
-template <>
-struct FftArgs<float> {
-    static float* U(const Launch& L, int i) { return L.U32[i]; }
-    static const float* F(const Launch& L, int i) { return L.F32[i]; }
-    static const float* Lm(const Launch& L) { return L.L32; }
-    static const float2* tw(const Launch& L) { return L.tw32; }
-    static const float* ksq(const Launch& L) { return L.ksq32; }
-    static constexpr int tk = 16;
-};
-
 inline int lines_per_block(int n, int nlines) {
     int lpb = 2048 / n;
     if (lpb < 1) lpb = 1;
@@ -447,83 +477,69 @@ inline int lines_per_block(int n, int nlines) {
     return lpb;
 }
 
-// stage < 0: all passes of one iteration; otherwise only pass `stage`
-// (3D: 0 x-forward, 1 y-forward, 2 z solve, 3 y-inverse, 4 x-inverse;
-//  2D: 0 x-forward, 1 y solve, 2 x-inverse).
-template <typename T, int D>
-cudaError_t run_fft(const Launch& L, int stage) {
-    using V = typename Cx<T>::t;
-    using A = FftArgs<T>;
-    const int n = L.n, H = n / 2;
-    const int nlines = (D == 3) ? n * n : n;
-    const int lpb = lines_per_block(n, nlines);
-    const int gx = (nlines + lpb - 1) / lpb;
-    const size_t smx = (size_t)n * sizeof(V) + 2 * (size_t)lpb * H * sizeof(V);
-    const int tk = A::tk < H ? A::tk : H;
-    const size_t sma = (size_t)n * sizeof(V) + 2 * (size_t)n * tk * sizeof(V);
-    const dim3 ga((H + tk - 1) / tk, D == 3 ? n : 1, D);
-    const T scale = (T)(2.0 / (double)L.V);
-    const int last = D == 3 ? 4 : 2;
-    auto want = [&](int s) { return stage < 0 || stage == s; };
-    if (want(0))
-        k_xfwd<T, D, false><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, A::F(L, 0), A::F(L, 1), A::Lm(L),
-                                                                A::U(L, 0), A::U(L, 1), A::tw(L), L.plan, lpb);
-    if (D == 3) {
-        if (want(1))
-            k_faxis<T, D, 1, 0><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::tw(L),
-                                                                    A::ksq(L), L.plan, tk, scale);
-        if (want(2))
-            k_faxis<T, D, 2, 2><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::tw(L),
-                                                                    A::ksq(L), L.plan, tk, scale);
-        if (want(3))
-            k_faxis<T, D, 1, 1><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::tw(L),
-                                                                    A::ksq(L), L.plan, tk, scale);
-    } else if (want(1)) {
-        k_faxis<T, D, 1, 2><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::tw(L),
-                                                                A::ksq(L), L.plan, tk, scale);
+template <typename T, int D, bool INCR>
+__global__ void __launch_bounds__(kFftThreads)
+k_xfwd(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        xfwd_tile<T, D, INCR>(rds[tl.x], tl.y);
+        __syncthreads();
     }
-    if (want(last))
-        k_xinv<T, T, D, false><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, A::U(L, 0), A::U(L, 1), A::U(L, 0),
-                                                                   A::U(L, 1), A::tw(L), L.plan, lpb, nullptr);
-    return cudaGetLastError();
 }
 
-// Float projection of the increment R (L.R32) added to the double u~ (double
-// polish of RVE_MIXED); same stage numbering as run_fft.
-template <int D>
-cudaError_t run_fft_incr(const Launch& L, int stage) {
-    using V = float2;
-    const int n = L.n, H = n / 2;
-    const int nlines = (D == 3) ? n * n : n;
-    const int lpb = lines_per_block(n, nlines);
-    const int gx = (nlines + lpb - 1) / lpb;
-    const size_t smx = (size_t)n * sizeof(V) + 2 * (size_t)lpb * H * sizeof(V);
-    const int tk = FftArgs<float>::tk < H ? FftArgs<float>::tk : H;
-    const size_t sma = (size_t)n * sizeof(V) + 2 * (size_t)n * tk * sizeof(V);
-    const dim3 ga((H + tk - 1) / tk, D == 3 ? n : 1, D);
-    const float scale = (float)(2.0 / (double)L.V);
+template <typename T, typename TO, int D, bool INCR>
+__global__ void __launch_bounds__(kFftThreads)
+k_xinv(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        xinv_tile<T, TO, D, INCR>(rds[tl.x], tl.y);
+        __syncthreads();
+    }
+}
+
+template <typename T, int D, int AXIS, int MODE, bool INCR>
+__global__ void __launch_bounds__(kFftThreads)
+k_faxis(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        faxis_tile<T, D, AXIS, MODE, INCR>(rds[tl.x], tl.y);
+        __syncthreads();
+    }
+}
+
+template <typename K>
+void go(K kern, const Exec& E, int cls, size_t smem) {
+    const int nt = E.ntiles[cls];
+    const int grid = persistent_grid((const void*)kern, kFftThreads, smem, nt);
+    kern<<<grid, kFftThreads, smem, E.stream>>>(E.rds, E.tiles[cls], nt);
+}
+
+// stage < 0: all passes of one iteration; otherwise only pass `stage`
+// (3D: 0 x-forward, 1 y-forward, 2 z solve, 3 y-inverse, 4 x-inverse;
+//  2D: 0 x-forward, 1 y solve, 2 x-inverse).  INCR: the float increment
+// projection of the double polish (see launch_fft_incr).
+template <typename T, int D, bool INCR>
+cudaError_t run_fft(const Exec& E, int stage) {
+    const int f = std::is_same<T, double>::value ? 1 : 0;
+    const int ax = f ? kTilesAx64 : kTilesAx32;
+    const size_t smx = E.smem_x[f], sma = E.smem_a[f];
     const int last = D == 3 ? 4 : 2;
     auto want = [&](int s) { return stage < 0 || stage == s; };
-    float* S = L.S32;
-    if (want(0))
-        k_xfwd<float, D, true><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, L.R32, L.R32, nullptr, S, S, L.tw32,
-                                                                   L.plan, lpb);
+    static_assert(!INCR || std::is_same<T, float>::value, "increment projection runs in float");
+    if (want(0)) go(k_xfwd<T, D, INCR>, E, kTilesX, smx);
     if (D == 3) {
-        if (want(1))
-            k_faxis<float, D, 1, 0><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, S, S, L.tw32, L.ksq32, L.plan, tk,
-                                                                        scale);
-        if (want(2))
-            k_faxis<float, D, 2, 2><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, S, S, L.tw32, L.ksq32, L.plan, tk,
-                                                                        scale);
-        if (want(3))
-            k_faxis<float, D, 1, 1><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, S, S, L.tw32, L.ksq32, L.plan, tk,
-                                                                        scale);
+        if (want(1)) go(k_faxis<T, D, 1, 0, INCR>, E, ax, sma);
+        if (want(2)) go(k_faxis<T, D, 2, 2, INCR>, E, ax, sma);
+        if (want(3)) go(k_faxis<T, D, 1, 1, INCR>, E, ax, sma);
     } else if (want(1)) {
-        k_faxis<float, D, 1, 2><<<ga, kFftThreads, sma, L.stream>>>(L.ctrl, S, S, L.tw32, L.ksq32, L.plan, tk, scale);
+        go(k_faxis<T, D, 1, 2, INCR>, E, ax, sma);
     }
-    if (want(last))
-        k_xinv<float, double, D, true><<<gx, kFftThreads, smx, L.stream>>>(L.ctrl, S, S, L.U64[0], L.U64[1], L.tw32,
-                                                                           L.plan, lpb, L.D32);
+    if (want(last)) {
+        if constexpr (INCR)
+            go(k_xinv<float, double, D, true>, E, kTilesX, smx);
+        else
+            go(k_xinv<T, T, D, false>, E, kTilesX, smx);
+    }
     return cudaGetLastError();
 }
 
@@ -535,25 +551,88 @@ cudaError_t set_smem_attrs(int bytes) {
         if (r != cudaSuccess) e = r;
     };
     set((const void*)k_xfwd<T, D, false>);
-    set((const void*)k_xfwd<T, D, true>);
     set((const void*)k_xinv<T, T, D, false>);
-    if (std::is_same<T, float>::value) set((const void*)k_xinv<float, double, D, true>);
-    set((const void*)k_faxis<T, D, 1, 0>);
-    set((const void*)k_faxis<T, D, 1, 1>);
-    set((const void*)k_faxis<T, D, 1, 2>);
-    set((const void*)k_faxis<T, D, 2, 2>);
+    set((const void*)k_faxis<T, D, 1, 0, false>);
+    set((const void*)k_faxis<T, D, 1, 1, false>);
+    set((const void*)k_faxis<T, D, 1, 2, false>);
+    set((const void*)k_faxis<T, D, 2, 2, false>);
+    if constexpr (std::is_same<T, float>::value) {
+        set((const void*)k_xfwd<float, D, true>);
+        set((const void*)k_xinv<float, double, D, true>);
+        set((const void*)k_faxis<float, D, 1, 0, true>);
+        set((const void*)k_faxis<float, D, 1, 1, true>);
+        set((const void*)k_faxis<float, D, 1, 2, true>);
+        set((const void*)k_faxis<float, D, 2, 2, true>);
+    }
     return e;
 }
 
 }  // namespace
 
-cudaError_t launch_fft(const Launch& L, bool fp64, int stage) {
-    if (fp64) return L.dim == 3 ? run_fft<double, 3>(L, stage) : run_fft<double, 2>(L, stage);
-    return L.dim == 3 ? run_fft<float, 3>(L, stage) : run_fft<float, 2>(L, stage);
+cudaError_t launch_fft(const Exec& E, bool fp64, int stage) {
+    const int dim = E.rep->dim;
+    if (fp64) return dim == 3 ? run_fft<double, 3, false>(E, stage) : run_fft<double, 2, false>(E, stage);
+    return dim == 3 ? run_fft<float, 3, false>(E, stage) : run_fft<float, 2, false>(E, stage);
 }
 
-cudaError_t launch_fft_incr(const Launch& L, int stage) {
-    return L.dim == 3 ? run_fft_incr<3>(L, stage) : run_fft_incr<2>(L, stage);
+cudaError_t launch_fft_incr(const Exec& E, int stage) {
+    return E.rep->dim == 3 ? run_fft<float, 3, true>(E, stage) : run_fft<float, 2, true>(E, stage);
+}
+
+void set_geometry(Launch& L) {
+    const int n = L.n, H = n / 2;
+    const int nlines = L.dim == 3 ? n * n : n;
+    const long long want = (L.V + kLocalThreads - 1) / kLocalThreads;
+    const long long cap = 152 * 12;  // whole waves at 2, 3, 4 or 6 resident blocks per SM
+    L.local_blocks = (int)(want < cap ? want : cap);
+    L.lpb = lines_per_block(n, nlines);
+    L.xblocks = (nlines + L.lpb - 1) / L.lpb;
+    L.tk64 = FftArgs<double>::tk < H ? FftArgs<double>::tk : H;
+    L.tk32 = FftArgs<float>::tk < H ? FftArgs<float>::tk : H;
+}
+
+int tiles_local(const Launch& L) { return L.local_blocks; }
+int tiles_x(const Launch& L) { return L.xblocks; }
+int tiles_ax(const Launch& L, bool fp64) {
+    const int H = L.n / 2;
+    const int tk = fp64 ? L.tk64 : L.tk32;
+    return ((H + tk - 1) / tk) * (L.dim == 3 ? L.n : 1) * L.dim;
+}
+
+size_t smem_x_bytes(const Launch& L, bool fp64) {
+    const size_t v = fp64 ? sizeof(double2) : sizeof(float2);
+    return (size_t)L.n * v + 2 * (size_t)L.lpb * (L.n / 2) * v;
+}
+size_t smem_a_bytes(const Launch& L, bool fp64) {
+    const size_t v = fp64 ? sizeof(double2) : sizeof(float2);
+    return (size_t)L.n * v + 2 * (size_t)L.n * (fp64 ? L.tk64 : L.tk32) * v;
+}
+
+int persistent_grid(const void* kernel, int threads, size_t smem, int ntiles) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, size_t>, int> cache;
+    static int sms = 0;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (sms == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+        }
+        auto it = cache.find({kernel, smem});
+        if (it != cache.end()) {
+            per_sm = it->second;
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+                per_sm <= 0)
+                per_sm = 1;
+            cache[{kernel, smem}] = per_sm;
+        }
+    }
+    const long long cap = (long long)per_sm * sms;
+    if (ntiles < 1) return 1;
+    return (int)(ntiles < cap ? ntiles : cap);
 }
 
 // Allow the FFT kernels the dynamic shared memory the largest grid needs.

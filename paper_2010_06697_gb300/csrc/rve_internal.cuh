@@ -57,12 +57,16 @@ struct FftPlan {
     int rad_full[kMaxPasses];
 };
 
-// Everything a launch needs.  Pointers of the precision not in use may be null.
+// Everything the kernels need about one RVE.  A copy lives in device memory (the
+// per-RVE descriptor read by the tile-loop kernels); pointers of the precision not
+// in use may be null.
 struct Launch {
     cudaStream_t stream;
     int dim, n, model;
     long long V;
-    int local_blocks;
+    int local_blocks;      // blocks (tiles) of the local kernel for this RVE
+    int lpb, xblocks;      // x passes: lines per block, blocks
+    int tk64, tk32;        // y/z passes: columns per tile (double / float)
     Ctrl* ctrl;
     double* hist;          // 3 doubles per iteration: r_p, r_d, rho
     double* partials;      // kPartialStride doubles per local block
@@ -95,17 +99,45 @@ struct Launch {
     FftPlan plan;
 };
 
+// Per-iteration kernels run as persistent loops over a tile table: entry t is
+// (RVE index into the descriptor array, block index within that RVE's grid for
+// the pass).  An RVE's blocks, partial sums and reductions depend on its own size
+// only, so its results are the same alone or in any batch.
+enum TileClass : int { kTilesLocal = 0, kTilesX = 1, kTilesAx64 = 2, kTilesAx32 = 3, kTileClasses = 4 };
+
+struct Exec {
+    cudaStream_t stream;
+    const Launch* rep;            // host copy of one member (dim, model, precision set)
+    const Launch* rds;            // device array of member descriptors
+    const int2* tiles[kTileClasses];
+    int ntiles[kTileClasses];
+    size_t smem_x[2];             // dynamic shared memory of the x passes [fp64], max over members
+    size_t smem_a[2];             // and of the y/z passes
+};
+
+// per-RVE launch geometry (local_blocks, lpb, xblocks, tk) from dim and n
+void set_geometry(Launch& L);
+// tiles of one RVE for each class
+int tiles_local(const Launch& L);
+int tiles_x(const Launch& L);
+int tiles_ax(const Launch& L, bool fp64);
+// dynamic shared memory of the x passes and of the y/z passes for one RVE
+size_t smem_x_bytes(const Launch& L, bool fp64);
+size_t smem_a_bytes(const Launch& L, bool fp64);
+// grid size of a persistent launch: min(tiles, resident blocks on the device)
+int persistent_grid(const void* kernel, int threads, size_t smem, int ntiles);
+
 // rve_local.cu
 cudaError_t launch_init(const Launch& L, bool fp64, bool lambda_zero);
 // polish_mode (double only): 0 plain; 1 also write R; 2 also write R and take
-// r_d from the float u~ increment D32 (see k_local).
-cudaError_t launch_local(const Launch& L, bool fp64, bool first, bool only_if_rho_changed, int polish_mode = 0);
+// r_d from the float u~ increment D32 (see local_tile).
+cudaError_t launch_local(const Exec& E, bool fp64, bool first, bool only_if_rho_changed, int polish_mode = 0);
 cudaError_t launch_stress(const Launch& L, bool fp64);
 cudaError_t launch_convert(const Launch& L, bool to_fp64);
 // rve_fft.cu
-cudaError_t launch_fft(const Launch& L, bool fp64, int stage = -1);
+cudaError_t launch_fft(const Exec& E, bool fp64, int stage = -1);
 // Projection of the float increment R into the double u~: u~_{k+1} = u~_k + P(R).
-cudaError_t launch_fft_incr(const Launch& L, int stage = -1);
+cudaError_t launch_fft_incr(const Exec& E, int stage = -1);
 inline int fft_stages(int dim) { return dim == 3 ? 5 : 3; }
 cudaError_t prepare_fft_kernels(int n);
 

@@ -675,6 +675,23 @@ struct Dirs {
     const T* ref;
 };
 
+template <typename T>
+struct Set;
+template <>
+struct Set<double> {
+    __host__ __device__ static double* F(const Launch& L, int i) { return L.F64[i]; }
+    __host__ __device__ static double* Lm(const Launch& L) { return L.L64; }
+    __host__ __device__ static double* U(const Launch& L, int i) { return L.U64[i]; }
+    __host__ __device__ static Dirs<double> dirs(const Launch& L) { return Dirs<double>{L.N64[0], L.N64[1], L.n0_64}; }
+};
+template <>
+struct Set<float> {
+    __host__ __device__ static float* F(const Launch& L, int i) { return L.F32[i]; }
+    __host__ __device__ static float* Lm(const Launch& L) { return L.L32; }
+    __host__ __device__ static float* U(const Launch& L, int i) { return L.U32[i]; }
+    __host__ __device__ static Dirs<float> dirs(const Launch& L) { return Dirs<float>{L.N32[0], L.N32[1], L.n0_32}; }
+};
+
 // Fresh state: F_k = Fbar, u~_k = 0, Lambda = W_F(Fbar; x) (or 0).
 template <typename T, int D, int MODEL>
 __global__ void __launch_bounds__(kLocalThreads)
@@ -738,13 +755,30 @@ k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const 
 // DU (same polish, after its first iteration): the float increment
 // u~_{k+1} - u~_k written by the increment projection is read instead of u~_k,
 // and G_{k+1} - G_k = D(u~_{k+1} - u~_k) for r_d is formed in float.
-template <typename T, int D, int MODEL, bool FIRST, bool WRITE_R, bool DU>
-__global__ void __launch_bounds__(kLocalThreads)
-k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__ partials, T* F0, T* F1, T* Lam,
-        const T* U0, const T* U1, const uint8_t* __restrict__ phase, const double* __restrict__ mat, int nparam,
-        int n, long long V, int only_if_rho_changed, float* __restrict__ Rout, const float* __restrict__ DUin,
-        Dirs<T> dir) {
+// One tile = block `bid` of the RVE's local grid (L.local_blocks blocks).  FIRST
+// is a run-time flag (not a template parameter) so that the local step compiles
+// to one instruction sequence for both entry paths: a solve resumed from a saved
+// state then reproduces the uninterrupted run bit for bit.
+template <typename T, int D, int MODEL, bool WRITE_R, bool DU>
+__device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool FIRST, int only_if_rho_changed) {
     constexpr int NN = D * D;
+    Ctrl* __restrict__ ctrl = L.ctrl;
+    double* __restrict__ hist = L.hist;
+    double* __restrict__ partials = L.partials;
+    T* F0 = Set<T>::F(L, 0);
+    T* F1 = Set<T>::F(L, 1);
+    T* Lam = Set<T>::Lm(L);
+    const T* U0 = Set<T>::U(L, 0);
+    const T* U1 = Set<T>::U(L, 1);
+    const uint8_t* __restrict__ phase = L.phase;
+    const double* __restrict__ mat = L.mat;
+    const int nparam = L.nparam;
+    const int n = L.n;
+    const long long V = L.V;
+    float* __restrict__ Rout = L.R32;
+    const float* __restrict__ DUin = L.D32;
+    const Dirs<T> dir = Set<T>::dirs(L);
+    const int nblk = L.local_blocks;
     __shared__ double s_sum[kLocalThreads / 32][2];
     __shared__ int s_int[kLocalThreads / 32][2];
     __shared__ int s_last;
@@ -778,7 +812,7 @@ k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__
 
     double rp2 = 0.0, rd2 = 0.0;
     int nmax = 0, nfail = 0;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    for (long long v = bid * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)nblk * blockDim.x) {
         const Nbr<D> nb = neighbours<D>(v, n);
         T G[NN], L[NN], F[NN];
         grad_u<T, D>(Unew, V, nb, Fb, half_n, G);
@@ -876,14 +910,14 @@ k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__
             mx = max(mx, s_int[w][0]);
             nf += s_int[w][1];
         }
-        double* pp = partials + (size_t)blockIdx.x * kPartialStride;
+        double* pp = partials + (size_t)bid * kPartialStride;
         pp[0] = a;
         pp[1] = b;
         pp[2] = (double)mx;
         pp[3] = (double)nf;
         __threadfence();
         const unsigned prev = atomicAdd(&ctrl->counter, 1u);
-        s_last = (prev == gridDim.x - 1);
+        s_last = (prev == nblk - 1);
     }
     __syncthreads();
     if (!s_last) return;
@@ -893,7 +927,7 @@ k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__
     double a = 0, b = 0;
     int mx = 0;
     double nf = 0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    for (int i = threadIdx.x; i < (int)nblk; i += blockDim.x) {
         const double* pp = partials + (size_t)i * kPartialStride;
         a += __ldcg(pp + 0);
         b += __ldcg(pp + 1);
@@ -970,6 +1004,18 @@ k_local(Ctrl* __restrict__ ctrl, double* __restrict__ hist, double* __restrict__
     }
     c->done = done;
     c->counter = 0u;
+}
+
+
+template <typename T, int D, int MODEL, bool WRITE_R, bool DU>
+__global__ void __launch_bounds__(kLocalThreads)
+k_local(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles, int first,
+        int only_if_rho_changed) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        local_tile<T, D, MODEL, WRITE_R, DU>(rds[tl.x], tl.y, first != 0, only_if_rho_changed);
+        __syncthreads();
+    }
 }
 
 // <W_F(F_k)> and <Lambda_k>, summed in double with the same fixed-order scheme.
@@ -1077,23 +1123,6 @@ __global__ void k_convert(const Ctrl* __restrict__ ctrl, const S* Fs0, const S* 
 
 // ------------------------------------------------------------------ dispatch
 
-template <typename T>
-struct Set;
-template <>
-struct Set<double> {
-    static double* F(const Launch& L, int i) { return L.F64[i]; }
-    static double* Lm(const Launch& L) { return L.L64; }
-    static double* U(const Launch& L, int i) { return L.U64[i]; }
-    static Dirs<double> dirs(const Launch& L) { return Dirs<double>{L.N64[0], L.N64[1], L.n0_64}; }
-};
-template <>
-struct Set<float> {
-    static float* F(const Launch& L, int i) { return L.F32[i]; }
-    static float* Lm(const Launch& L) { return L.L32; }
-    static float* U(const Launch& L, int i) { return L.U32[i]; }
-    static Dirs<float> dirs(const Launch& L) { return Dirs<float>{L.N32[0], L.N32[1], L.n0_32}; }
-};
-
 template <typename T, int D, int MODEL>
 cudaError_t run_init(const Launch& L, bool lambda_zero) {
     k_init<T, D, MODEL><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
@@ -1104,23 +1133,21 @@ cudaError_t run_init(const Launch& L, bool lambda_zero) {
 
 // mode: 0 plain, 1 write R (first polish iteration), 2 write R and read the float u~ increment
 template <typename T, int D, int MODEL>
-cudaError_t run_local(const Launch& L, bool first, bool only_if, int mode) {
-#define RVE_LOCAL_ARGS                                                                                          \
-    L.ctrl, L.hist, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0), Set<T>::U(L, 1), \
-        L.phase, L.mat, L.nparam, L.n, L.V
+cudaError_t run_local(const Exec& E, bool first, bool only_if, int mode) {
+    const int nt = E.ntiles[kTilesLocal];
+    const int2* tl = E.tiles[kTilesLocal];
+    auto go = [&](auto kern, int is_first, int flag) {
+        const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, nt);
+        kern<<<grid, kLocalThreads, 0, E.stream>>>(E.rds, tl, nt, is_first, flag);
+    };
     if (first)
-        k_local<T, D, MODEL, true, false, false>
-            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, only_if ? 1 : 0, nullptr, nullptr, Set<T>::dirs(L));
+        go(k_local<T, D, MODEL, false, false>, 1, only_if ? 1 : 0);
     else if (mode == 1 && std::is_same<T, double>::value)
-        k_local<T, D, MODEL, false, true, false>
-            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, 0, L.R32, nullptr, Set<T>::dirs(L));
+        go(k_local<T, D, MODEL, true, false>, 0, 0);
     else if (mode == 2 && std::is_same<T, double>::value)
-        k_local<T, D, MODEL, false, true, true>
-            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, 0, L.R32, L.D32, Set<T>::dirs(L));
+        go(k_local<T, D, MODEL, true, true>, 0, 0);
     else
-        k_local<T, D, MODEL, false, false, false>
-            <<<L.local_blocks, kLocalThreads, 0, L.stream>>>(RVE_LOCAL_ARGS, 0, nullptr, nullptr, Set<T>::dirs(L));
-#undef RVE_LOCAL_ARGS
+        go(k_local<T, D, MODEL, false, false>, 0, 0);
     return cudaGetLastError();
 }
 
@@ -1149,9 +1176,10 @@ cudaError_t launch_init(const Launch& L, bool fp64, bool lambda_zero) {
     RVE_DISPATCH(run_init, float, L, lambda_zero);
 }
 
-cudaError_t launch_local(const Launch& L, bool fp64, bool first, bool only_if_rho_changed, int polish_mode) {
-    if (fp64) RVE_DISPATCH(run_local, double, L, first, only_if_rho_changed, polish_mode);
-    RVE_DISPATCH(run_local, float, L, first, only_if_rho_changed, 0);
+cudaError_t launch_local(const Exec& E, bool fp64, bool first, bool only_if_rho_changed, int polish_mode) {
+    const Launch& L = *E.rep;
+    if (fp64) RVE_DISPATCH(run_local, double, E, first, only_if_rho_changed, polish_mode);
+    RVE_DISPATCH(run_local, float, E, first, only_if_rho_changed, 0);
 }
 
 cudaError_t launch_stress(const Launch& L, bool fp64) {

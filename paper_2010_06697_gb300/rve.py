@@ -101,6 +101,9 @@ SIGNATURES = {
     "rve_strerror": (ctypes.c_char_p, [_I]),
     "rve_set_profiling": (_I, [_VP, _I]),
     "rve_stress_noalloc": (_I, [_I, _I, _I, _VP, _VP, _VP, _I, _I, _VP, _VP]),
+    "rve_batch_create": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP]),
+    "rve_batch_solve": (_I, [_VP, _PD, _PD, _D, ctypes.POINTER(rve_solve_info)]),
+    "rve_batch_destroy": (None, [_VP]),
     "rve_kernel_times": (_I, [_VP, _I, _PD, ctypes.POINTER(ctypes.c_longlong), _I]),
 }
 
@@ -244,6 +247,55 @@ def rve_kernel_times(h, fp64):
     rc = lib().rve_kernel_times(h, 1 if fp64 else 0, _dptr(ms), n.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
                                 len(KCLASS_NAMES))
     return rc, ms, n
+
+
+def rve_batch_create(handles, stream=None):
+    arr = (_VP * len(handles))(*[h.value if isinstance(h, _VP) else h for h in handles])
+    b = _VP()
+    rc = lib().rve_batch_create(ctypes.byref(b), arr, len(handles), _VP(stream or 0))
+    return rc, b
+
+
+def rve_batch_solve(b, Fbars, rhos, tol):
+    fb = np.ascontiguousarray(np.asarray(Fbars, dtype=np.float64).reshape(-1, 9))
+    rh = np.ascontiguousarray(np.asarray(rhos, dtype=np.float64).reshape(-1))
+    infos = (rve_solve_info * fb.shape[0])()
+    rc = lib().rve_batch_solve(b, _dptr(fb), _dptr(rh), float(tol), infos)
+    return rc, list(infos)
+
+
+def rve_batch_destroy(b):
+    lib().rve_batch_destroy(b)
+
+
+class Batch:
+    """Batched solves over existing Rve objects (kept alive by this object)."""
+
+    def __init__(self, members, stream=None):
+        self.members = list(members)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        rc, b = rve_batch_create([m.h for m in self.members], stream)
+        _check(rc, "rve_batch_create")
+        self.b = b
+
+    def solve(self, Fbars, rhos, tol):
+        rc, infos = rve_batch_solve(self.b, Fbars, rhos, tol)
+        if rc not in (RVE_OK, RVE_E_NOT_CONVERGED):
+            raise RveError(rc, "rve_batch_solve")
+        return infos
+
+    def close(self):
+        if self.b is not None:
+            rve_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ owner object
