@@ -198,6 +198,49 @@ int rve_batch_solve(rve_batch_t b, const double* Fbars, const double* rhos, doub
 /* Release the batch (not its handles). */
 void rve_batch_destroy(rve_batch_t b);
 
+/* ------------------------------------------------------------------ serving */
+typedef struct rve_server* rve_server_t;
+
+/* A continuous-batching server for RVE solve requests of any size and model.
+ * Requests are admitted, in arrival order, whenever the device workspaces of the
+ * admitted requests fit mem_budget_bytes (rve_workspace_bytes with opt); idle
+ * workspaces are kept by shape for reuse and released when memory is needed.
+ * Admitted requests iterate together: each rve_server_step runs one chunk of
+ * opt->check_every iterations of every admitted request as batched launches
+ * (see rve_batch_create), retires the finished ones (homogenised stress and info
+ * kept for rve_server_poll) and admits waiting requests into the freed memory,
+ * so requests that arrive while others run join the running set.  A request's
+ * result is bitwise the same as rve_solve of the same input on a fresh handle.
+ * opt applies to every request (NULL = defaults).  The server is driven by one
+ * host thread. */
+int rve_server_create(rve_server_t* out, size_t mem_budget_bytes, const rve_options* opt, void* cuda_stream);
+
+/* Queue a solve: a fresh state on an N^d cell (inputs as rve_create /
+ * rve_set_material / rve_solve; host arrays are copied).  *ticket identifies it.
+ * Errors: RVE_E_INVALID_ARG, RVE_E_OOM (its workspace exceeds the budget). */
+int rve_server_submit(rve_server_t s, int dim, int n, int model, const uint8_t* phase, int nphase,
+                      const double* params, int nparam, const double* n0, const double Fbar[9], double rho,
+                      double tol, long long* ticket);
+
+/* One scheduler tick (admit, iterate one chunk, retire); active/queued counts out. */
+int rve_server_step(rve_server_t s, int* active_out, int* queued_out);
+
+/* Result of a finished request: RVE_OK (or its non-OK solve status) with S (3x3,
+ * row-major), info (info.time_ms = admission to completion), latency (submit to
+ * completion) and queue wait in milliseconds; the result is then forgotten.
+ * RVE_E_BUSY while queued or running, RVE_E_NOT_FOUND for unknown tickets. */
+int rve_server_poll(rve_server_t s, long long ticket, double S[9], rve_solve_info* info, double* latency_ms,
+                    double* queue_ms);
+
+/* Drop a queued or running request (its workspace returns to the pool). */
+int rve_server_cancel(rve_server_t s, long long ticket);
+
+/* Queue length, running requests, completed requests, workspace bytes held. */
+int rve_server_stats(rve_server_t s, long long* queued, long long* active, long long* completed, size_t* bytes_used);
+
+/* Release the server, its pooled and running workspaces. */
+void rve_server_destroy(rve_server_t s);
+
 /* ------------------------------------------------------------------ profiling */
 /* Kernel classes of the iteration (index into rve_kernel_times' arrays). */
 enum rve_kernel_class {

@@ -14,8 +14,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <deque>
 #include <map>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "../../include/rve.h"
@@ -901,23 +904,33 @@ const char* rve_strerror(int code) {
 
 }  // extern "C"
 
-// ================================================================== batches
+// ================================================================== batches and serving
+//
+// Engine: RVE solves in flight on one stream.  Members sit in descriptor slots;
+// members with the same (dimension, model, precision stage) form a run whose
+// per-iteration passes are single persistent launches over the run's tile
+// table, replayed as CUDA graphs of check_every iterations.  add() starts a
+// member (its first local step on its own tiles); tick() runs one chunk of every
+// run, reads every running member's stop flag, moves members of RVE_MIXED to the
+// double polish and reports finished members.  Membership changes rebuild the
+// affected tile tables (and graphs).  Used by rve_batch_solve (add all, tick
+// until empty) and by the server (admit whenever memory frees up).
 
 namespace {
 
-// (done, k) of every member's control block, for the host's per-chunk check.
-__global__ void k_gather_status(const Launch* __restrict__ rds, int count, long long* __restrict__ out) {
+__global__ void k_gather_status(const Launch* __restrict__ rds, const int* __restrict__ slots, int count,
+                                long long* __restrict__ out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-        const Ctrl* c = rds[i].ctrl;
+        const Ctrl* c = rds[slots[i]].ctrl;
         out[2 * i] = c->done;
         out[2 * i + 1] = c->k;
     }
 }
 
-enum Stage : int { kStageF32 = 0, kStageF64 = 1, kStagePolish = 2, kStages = 3 };
+enum Stage : int { kStageF32 = 0, kStageF64 = 1, kStagePolish = 2 };
 
-struct BatchRun {  // the members of one (group, stage) that are still iterating
-    std::vector<int> active;
+struct BatchRun {  // members of one (dim, model, stage) still iterating
+    std::vector<int> active;  // slots
     admm::Exec E{};
     int2* d_tiles[admm::kTileClasses] = {};
     int cap[admm::kTileClasses] = {};
@@ -925,32 +938,97 @@ struct BatchRun {  // the members of one (group, stage) that are still iterating
     bool dirty = true;
 };
 
-}  // namespace
-
-struct rve_batch {
-    std::vector<rve*> m;
-    std::vector<int> group_of;  // member -> group
-    int ngroups = 0;
-    cudaStream_t user_stream = nullptr, stream = nullptr;
-    cudaEvent_t ev_in = nullptr, ev0 = nullptr, ev1 = nullptr;
-    Launch* d_rds = nullptr;
-    long long* d_status = nullptr;
-    long long* h_status = nullptr;
-    std::vector<BatchRun> runs;  // [group * kStages + stage]
+struct Member {
+    rve* h = nullptr;
+    int stage = 0;
+    long long k0 = 0, ksw = -1;
+    bool running = false;
 };
 
-namespace {
+using RunKey = std::tuple<int, int, int>;
 
-int batch_upload_tiles(rve_batch* b, BatchRun& r) {
+struct Engine {
+    cudaStream_t stream = nullptr;
+    Launch* d_rds = nullptr;
+    int cap = 0;
+    int* d_slots = nullptr;
+    long long* d_status = nullptr;
+    long long* h_status = nullptr;
+    int* h_slots = nullptr;
+    std::vector<Member> mem;  // by slot
+    std::vector<int> free_slots;
+    std::map<RunKey, BatchRun> runs;
+};
+
+void engine_free(Engine& E) {
+    if (E.stream) cudaStreamSynchronize(E.stream);
+    for (auto& kv : E.runs) {
+        if (kv.second.graph) cudaGraphExecDestroy(kv.second.graph);
+        for (int c = 0; c < admm::kTileClasses; ++c)
+            if (kv.second.d_tiles[c]) cudaFree(kv.second.d_tiles[c]);
+    }
+    E.runs.clear();
+    if (E.d_rds) cudaFree(E.d_rds);
+    if (E.d_slots) cudaFree(E.d_slots);
+    if (E.d_status) cudaFree(E.d_status);
+    if (E.h_status) cudaFreeHost(E.h_status);
+    if (E.h_slots) cudaFreeHost(E.h_slots);
+    E.d_rds = nullptr;
+    E.d_slots = nullptr;
+    E.d_status = nullptr;
+    E.h_status = nullptr;
+    E.h_slots = nullptr;
+    E.cap = 0;
+}
+
+int engine_reserve(Engine& E, int need) {
+    if (need <= E.cap) return RVE_OK;
+    int cap = std::max(need, std::max(16, 2 * E.cap));
+    Launch* rds = nullptr;
+    int* dsl = nullptr;
+    long long *dst = nullptr, *hst = nullptr;
+    int* hsl = nullptr;
+    if (cudaMalloc((void**)&rds, sizeof(Launch) * cap) != cudaSuccess) return RVE_E_OOM;
+    if (cudaMalloc((void**)&dsl, sizeof(int) * cap) != cudaSuccess || cudaMalloc((void**)&dst, 16 * (size_t)cap) != cudaSuccess ||
+        cudaMallocHost((void**)&hst, 16 * (size_t)cap) != cudaSuccess || cudaMallocHost((void**)&hsl, sizeof(int) * cap) != cudaSuccess) {
+        cudaFree(rds);
+        if (dsl) cudaFree(dsl);
+        if (dst) cudaFree(dst);
+        if (hst) cudaFreeHost(hst);
+        return RVE_E_OOM;
+    }
+    if (E.d_rds) {
+        CK(cudaMemcpyAsync(rds, E.d_rds, sizeof(Launch) * E.cap, cudaMemcpyDeviceToDevice, E.stream));
+        CK(cudaStreamSynchronize(E.stream));
+        cudaFree(E.d_rds);
+        cudaFree(E.d_slots);
+        cudaFree(E.d_status);
+        cudaFreeHost(E.h_status);
+        cudaFreeHost(E.h_slots);
+    }
+    E.d_rds = rds;
+    E.d_slots = dsl;
+    E.d_status = dst;
+    E.h_status = hst;
+    E.h_slots = hsl;
+    for (int s = E.cap; s < cap; ++s) E.free_slots.push_back(s);
+    std::sort(E.free_slots.rbegin(), E.free_slots.rend());  // hand out low slots first
+    E.mem.resize(cap);
+    E.cap = cap;
+    for (auto& kv : E.runs) kv.second.dirty = true;  // descriptor array moved
+    return RVE_OK;
+}
+
+int run_upload(Engine& E, BatchRun& r) {
     std::vector<int2> t;
     for (int c = 0; c < admm::kTileClasses; ++c) {
         t.clear();
-        for (int i : r.active) {
-            const Launch& L = b->m[i]->L;
+        for (int slot : r.active) {
+            const Launch& L = E.mem[slot].h->L;
             const int cnt = c == admm::kTilesLocal ? admm::tiles_local(L)
                           : c == admm::kTilesX     ? admm::tiles_x(L)
                                                    : admm::tiles_ax(L, c == admm::kTilesAx64);
-            for (int j = 0; j < cnt; ++j) t.push_back(make_int2(i, j));
+            for (int j = 0; j < cnt; ++j) t.push_back(make_int2(slot, j));
         }
         if ((int)t.size() > r.cap[c]) {
             if (r.d_tiles[c]) cudaFree(r.d_tiles[c]);
@@ -961,20 +1039,20 @@ int batch_upload_tiles(rve_batch* b, BatchRun& r) {
             r.cap[c] = (int)t.size();
         }
         if (!t.empty())
-            CK(cudaMemcpyAsync(r.d_tiles[c], t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
-        CK(cudaStreamSynchronize(b->stream));
+            CK(cudaMemcpyAsync(r.d_tiles[c], t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice, E.stream));
+        CK(cudaStreamSynchronize(E.stream));
         r.E.tiles[c] = r.d_tiles[c];
         r.E.ntiles[c] = (int)t.size();
     }
-    r.E.stream = b->stream;
-    r.E.rds = b->d_rds;
-    r.E.rep = &b->m[r.active.front()]->L;
+    r.E.stream = E.stream;
+    r.E.rds = E.d_rds;
+    r.E.rep = &E.mem[r.active.front()].h->L;
     for (int f = 0; f < 2; ++f) {
         r.E.smem_x[f] = 0;
         r.E.smem_a[f] = 0;
-        for (int i : r.active) {
-            r.E.smem_x[f] = std::max(r.E.smem_x[f], admm::smem_x_bytes(b->m[i]->L, f == 1));
-            r.E.smem_a[f] = std::max(r.E.smem_a[f], admm::smem_a_bytes(b->m[i]->L, f == 1));
+        for (int slot : r.active) {
+            r.E.smem_x[f] = std::max(r.E.smem_x[f], admm::smem_x_bytes(E.mem[slot].h->L, f == 1));
+            r.E.smem_a[f] = std::max(r.E.smem_a[f], admm::smem_a_bytes(E.mem[slot].h->L, f == 1));
         }
     }
     if (r.graph) {
@@ -985,9 +1063,8 @@ int batch_upload_tiles(rve_batch* b, BatchRun& r) {
     return RVE_OK;
 }
 
-// one chunk of iterations for the members of run r (captured once per membership)
-int batch_chunk(rve_batch* b, BatchRun& r, int stage) {
-    const rve_options& o = b->m[r.active.front()]->opt;
+int run_chunk(Engine& E, BatchRun& r, int stage) {
+    const rve_options& o = E.mem[r.active.front()].h->opt;
     const bool fp64 = stage != kStageF32;
     const bool polish = stage == kStagePolish;
     auto body = [&]() -> cudaError_t {
@@ -1002,9 +1079,9 @@ int batch_chunk(rve_batch* b, BatchRun& r, int stage) {
     if (!o.use_graph) return body() == cudaSuccess ? RVE_OK : RVE_E_CUDA;
     if (!r.graph) {
         cudaGraph_t g = nullptr;
-        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        CK(cudaStreamBeginCapture(E.stream, cudaStreamCaptureModeThreadLocal));
         const cudaError_t e = body();
-        const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        const cudaError_t e2 = cudaStreamEndCapture(E.stream, &g);
         if (e != cudaSuccess || e2 != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             return RVE_E_CUDA;
@@ -1013,11 +1090,149 @@ int batch_chunk(rve_batch* b, BatchRun& r, int stage) {
         cudaGraphDestroy(g);
         if (e3 != cudaSuccess) return RVE_E_CUDA;
     }
-    CK(cudaGraphLaunch(r.graph, b->stream));
+    CK(cudaGraphLaunch(r.graph, E.stream));
     return RVE_OK;
 }
 
+void run_insert(Engine& E, int slot) {
+    const Member& m = E.mem[slot];
+    BatchRun& r = E.runs[RunKey(m.h->dim, m.h->model, m.stage)];
+    r.active.insert(std::lower_bound(r.active.begin(), r.active.end(), slot), slot);
+    r.dirty = true;
+}
+
+void run_remove(Engine& E, int slot) {
+    const Member& m = E.mem[slot];
+    auto it = E.runs.find(RunKey(m.h->dim, m.h->model, m.stage));
+    if (it == E.runs.end()) return;
+    auto pos = std::find(it->second.active.begin(), it->second.active.end(), slot);
+    if (pos != it->second.active.end()) {
+        it->second.active.erase(pos);
+        it->second.dirty = true;
+    }
+}
+
+// Start a solve of h in the engine; returns the slot (>= 0) or an error.
+int engine_add(Engine& E, rve* h, const double Fbar[9], double rho, double tol) {
+    int rc = check_solve_args(h, Fbar, rho, tol);
+    if (rc) return rc;
+    if (E.free_slots.empty() && (rc = engine_reserve(E, E.cap + 1))) return rc;
+    const int slot = E.free_slots.back();
+    E.free_slots.pop_back();
+    h->launches = 0;
+    rc = begin_solve(h, Fbar, rho, tol, E.stream);
+    if (rc) {
+        E.free_slots.push_back(slot);
+        return rc;
+    }
+    CK(cudaMemcpyAsync(E.d_rds + slot, &h->L, sizeof(Launch), cudaMemcpyHostToDevice, E.stream));
+    Member& m = E.mem[slot];
+    m.h = h;
+    m.k0 = h->hctrl->k;
+    m.ksw = -1;
+    m.stage = h->opt.precision == RVE_FP64 ? kStageF64 : kStageF32;
+    m.running = h->hctrl->done == admm::kRunning;
+    if (m.running) {
+        admm::Exec Ei = h->E;  // the member's own tile tables for its first local step
+        Ei.stream = E.stream;
+        if (admm::launch_local(Ei, m.stage != kStageF32, true, false) != cudaSuccess) return RVE_E_CUDA;
+        h->launches += 1;
+        run_insert(E, slot);
+    }
+    return slot;
+}
+
+int engine_running(const Engine& E) {
+    int n = 0;
+    for (int s = 0; s < E.cap; ++s) n += (E.mem[s].h && E.mem[s].running) ? 1 : 0;
+    return n;
+}
+
+// One chunk of every run; returns the slots that finished in this tick.
+int engine_tick(Engine& E, std::vector<int>& finished) {
+    finished.clear();
+    int nrun = 0;
+    for (auto& kv : E.runs) {
+        BatchRun& r = kv.second;
+        if (r.active.empty()) continue;
+        if (r.dirty) {
+            const int rc = run_upload(E, r);
+            if (rc) return rc;
+        }
+        const int rc = run_chunk(E, r, std::get<2>(kv.first));
+        if (rc) return rc;
+        const rve* h0 = E.mem[r.active.front()].h;
+        const int per = admm::fft_stages(h0->dim) + 1 + (h0->opt.rho_policy == RVE_RHO_ADAPTIVE ? 1 : 0);
+        for (int slot : r.active) E.mem[slot].h->launches += (long long)h0->opt.check_every * per;
+        nrun += (int)r.active.size();
+    }
+    if (nrun == 0) return RVE_OK;
+    int cnt = 0;
+    for (int s = 0; s < E.cap; ++s)
+        if (E.mem[s].h && E.mem[s].running) E.h_slots[cnt++] = s;
+    CK(cudaMemcpyAsync(E.d_slots, E.h_slots, sizeof(int) * cnt, cudaMemcpyHostToDevice, E.stream));
+    k_gather_status<<<(cnt + 127) / 128, 128, 0, E.stream>>>(E.d_rds, E.d_slots, cnt, E.d_status);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(E.h_status, E.d_status, 16 * (size_t)cnt, cudaMemcpyDeviceToHost, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
+    std::vector<int> slots(E.h_slots, E.h_slots + cnt);
+    std::vector<long long> st(E.h_status, E.h_status + 2 * cnt);
+    for (int i = 0; i < cnt; ++i) {
+        if (st[2 * i] == admm::kRunning) continue;
+        const int slot = slots[i];
+        Member& m = E.mem[slot];
+        rve* h = m.h;
+        run_remove(E, slot);
+        if (read_ctrl_on(h, E.stream)) return RVE_E_CUDA;
+        const bool fixed_rho = h->opt.rho_policy == RVE_RHO_FIXED;
+        if (h->opt.precision == RVE_MIXED && m.stage == kStageF32 && h->hctrl->done == admm::kSwitch) {
+            m.ksw = h->hctrl->k;
+            if (switch_to_double(h, E.stream)) return RVE_E_CUDA;
+            // the member's first double iterations (local step, one full double projection,
+            // local step writing R) run on its own tile tables
+            admm::Exec Ei = h->E;
+            Ei.stream = E.stream;
+            if (admm::launch_local(Ei, true, true, false) != cudaSuccess) return RVE_E_CUDA;
+            if (fixed_rho) {
+                if (admm::launch_fft(Ei, true) != cudaSuccess) return RVE_E_CUDA;
+                if (admm::launch_local(Ei, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
+                h->launches += admm::fft_stages(h->dim) + 2;
+            } else {
+                h->launches += 1;
+            }
+            m.stage = fixed_rho ? kStagePolish : kStageF64;
+            run_insert(E, slot);
+        } else {
+            m.running = false;
+            finished.push_back(slot);
+        }
+    }
+    return RVE_OK;
+}
+
+// Info of a finished member and release of its slot.
+void engine_release(Engine& E, int slot, double ms, rve_solve_info* info) {
+    Member& m = E.mem[slot];
+    rve* h = m.h;
+    int fp64_iters = 0;
+    if (h->opt.precision == RVE_FP64)
+        fp64_iters = (int)(h->hctrl->k - m.k0);
+    else if (m.ksw >= 0)
+        fp64_iters = (int)(h->hctrl->k - m.ksw);
+    fill_info(h, m.k0, fp64_iters, ms, info);
+    if (m.running) run_remove(E, slot);
+    m = Member();
+    E.free_slots.push_back(slot);
+}
+
 }  // namespace
+
+struct rve_batch {
+    std::vector<rve*> m;
+    cudaStream_t user_stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev0 = nullptr, ev1 = nullptr;
+    Engine E;
+};
 
 extern "C" {
 
@@ -1040,45 +1255,23 @@ int rve_batch_create(rve_batch_t* out, rve_t* handles, int count, void* cuda_str
         return code;
     };
     b->m.assign(handles, handles + count);
-    std::vector<std::pair<int, int>> keys;
-    for (rve* h : b->m) {
-        const std::pair<int, int> key(h->dim, h->model);
-        auto it = std::find(keys.begin(), keys.end(), key);
-        if (it == keys.end()) {
-            keys.push_back(key);
-            b->group_of.push_back((int)keys.size() - 1);
-        } else {
-            b->group_of.push_back((int)(it - keys.begin()));
-        }
-    }
-    b->ngroups = (int)keys.size();
-    b->runs.resize((size_t)b->ngroups * kStages);
     b->user_stream = (cudaStream_t)cuda_stream;
-    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(RVE_E_CUDA);
+    if (cudaStreamCreateWithFlags(&b->E.stream, cudaStreamNonBlocking) != cudaSuccess) return fail(RVE_E_CUDA);
     if (cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess) return fail(RVE_E_CUDA);
     if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) return fail(RVE_E_CUDA);
-    if (cudaMalloc((void**)&b->d_rds, sizeof(Launch) * count) != cudaSuccess) return fail(RVE_E_OOM);
-    if (cudaMalloc((void**)&b->d_status, sizeof(long long) * 2 * count) != cudaSuccess) return fail(RVE_E_OOM);
-    if (cudaMallocHost((void**)&b->h_status, sizeof(long long) * 2 * count) != cudaSuccess) return fail(RVE_E_OOM);
+    const int rc = engine_reserve(b->E, count);
+    if (rc) return fail(rc);
     *out = b;
     return RVE_OK;
 }
 
 void rve_batch_destroy(rve_batch_t b) {
     if (!b) return;
-    if (b->stream) cudaStreamSynchronize(b->stream);
-    for (BatchRun& r : b->runs) {
-        if (r.graph) cudaGraphExecDestroy(r.graph);
-        for (int c = 0; c < admm::kTileClasses; ++c)
-            if (r.d_tiles[c]) cudaFree(r.d_tiles[c]);
-    }
-    if (b->d_rds) cudaFree(b->d_rds);
-    if (b->d_status) cudaFree(b->d_status);
-    if (b->h_status) cudaFreeHost(b->h_status);
+    engine_free(b->E);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
-    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->E.stream) cudaStreamDestroy(b->E.stream);
     delete b;
 }
 
@@ -1089,110 +1282,304 @@ int rve_batch_solve(rve_batch_t b, const double* Fbars, const double* rhos, doub
         const int rc = check_solve_args(b->m[i], Fbars + 9 * i, rhos[i], tol);
         if (rc) return rc;
     }
-    const int precision = b->m[0]->opt.precision;
-    const bool fixed_rho = b->m[0]->opt.rho_policy == RVE_RHO_FIXED;
+    Engine& E = b->E;
     CK(cudaEventRecord(b->ev_in, b->user_stream));
-    CK(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
-    CK(cudaEventRecord(b->ev0, b->stream));
-    std::vector<int> stage(count), running(count, 0), fp64_iters(count, 0);
-    std::vector<long long> k0(count), ksw(count, -1);
-    for (BatchRun& r : b->runs) {
-        r.active.clear();
-        r.dirty = true;
-    }
+    CK(cudaStreamWaitEvent(E.stream, b->ev_in, 0));
+    CK(cudaEventRecord(b->ev0, E.stream));
+    std::vector<int> slot(count);
     for (int i = 0; i < count; ++i) {
-        rve* h = b->m[i];
-        h->launches = 0;
-        const int rc = begin_solve(h, Fbars + 9 * i, rhos[i], tol, b->stream);
+        slot[i] = engine_add(E, b->m[i], Fbars + 9 * i, rhos[i], tol);
+        if (slot[i] < 0) return slot[i];
+    }
+    std::vector<int> finished;
+    while (engine_running(E) > 0) {
+        const int rc = engine_tick(E, finished);
         if (rc) return rc;
-        CK(cudaMemcpyAsync(b->d_rds + i, &h->L, sizeof(Launch), cudaMemcpyHostToDevice, b->stream));
-        k0[i] = h->hctrl->k;
-        stage[i] = precision == RVE_FP64 ? kStageF64 : kStageF32;
-        running[i] = h->hctrl->done == admm::kRunning;
-        if (running[i]) b->runs[b->group_of[i] * kStages + stage[i]].active.push_back(i);
     }
-    CK(cudaStreamSynchronize(b->stream));
-    // first local step of every running member, one launch per (group, stage)
-    for (int g = 0; g < b->ngroups; ++g)
-        for (int st = 0; st < kStages; ++st) {
-            BatchRun& r = b->runs[g * kStages + st];
-            if (r.active.empty()) continue;
-            int rc = batch_upload_tiles(b, r);
-            if (rc) return rc;
-            if (admm::launch_local(r.E, st != kStageF32, true, false) != cudaSuccess) return RVE_E_CUDA;
-            for (int i : r.active) b->m[i]->launches += 1;
-        }
-    for (;;) {
-        bool any = false;
-        for (int g = 0; g < b->ngroups; ++g)
-            for (int st = 0; st < kStages; ++st) {
-                BatchRun& r = b->runs[g * kStages + st];
-                if (r.active.empty()) continue;
-                any = true;
-                if (r.dirty) {
-                    const int rc = batch_upload_tiles(b, r);
-                    if (rc) return rc;
-                }
-                const int rc = batch_chunk(b, r, st);
-                if (rc) return rc;
-                const int per = admm::fft_stages(b->m[r.active.front()]->dim) + 1 + (fixed_rho ? 0 : 1);
-                for (int i : r.active) b->m[i]->launches += (long long)b->m[i]->opt.check_every * per;
-            }
-        if (!any) break;
-        k_gather_status<<<(count + 127) / 128, 128, 0, b->stream>>>(b->d_rds, count, b->d_status);
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(long long) * 2 * count, cudaMemcpyDeviceToHost,
-                           b->stream));
-        CK(cudaStreamSynchronize(b->stream));
-        for (int i = 0; i < count; ++i) {
-            if (!running[i] || b->h_status[2 * i] == admm::kRunning) continue;
-            rve* h = b->m[i];
-            BatchRun& from = b->runs[b->group_of[i] * kStages + stage[i]];
-            from.active.erase(std::find(from.active.begin(), from.active.end(), i));
-            from.dirty = true;
-            if (read_ctrl_on(h, b->stream)) return RVE_E_CUDA;
-            if (precision == RVE_MIXED && stage[i] == kStageF32 && h->hctrl->done == admm::kSwitch) {
-                ksw[i] = h->hctrl->k;
-                if (switch_to_double(h, b->stream)) return RVE_E_CUDA;
-                // the member's first double iterations (local step, one full double projection,
-                // local step writing R) run on its own tile tables
-                admm::Exec Ei = h->E;
-                Ei.stream = b->stream;
-                if (admm::launch_local(Ei, true, true, false) != cudaSuccess) return RVE_E_CUDA;
-                if (fixed_rho) {
-                    if (admm::launch_fft(Ei, true) != cudaSuccess) return RVE_E_CUDA;
-                    if (admm::launch_local(Ei, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
-                    h->launches += admm::fft_stages(h->dim) + 2;
-                } else {
-                    h->launches += 1;
-                }
-                stage[i] = fixed_rho ? kStagePolish : kStageF64;
-                BatchRun& to = b->runs[b->group_of[i] * kStages + stage[i]];
-                to.active.push_back(i);
-                std::sort(to.active.begin(), to.active.end());
-                to.dirty = true;
-            } else {
-                running[i] = 0;
-            }
-        }
-    }
-    CK(cudaEventRecord(b->ev1, b->stream));
+    CK(cudaEventRecord(b->ev1, E.stream));
     CK(cudaEventSynchronize(b->ev1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, b->ev0, b->ev1);
     int status = RVE_OK;
     for (int i = 0; i < count; ++i) {
         rve* h = b->m[i];
-        if (read_ctrl_on(h, b->stream)) return RVE_E_CUDA;
-        if (precision == RVE_FP64)
-            fp64_iters[i] = (int)(h->hctrl->k - k0[i]);
-        else if (ksw[i] >= 0)
-            fp64_iters[i] = (int)(h->hctrl->k - ksw[i]);
-        fill_info(h, k0[i], fp64_iters[i], ms, infos ? infos + i : nullptr);
+        if (read_ctrl_on(h, E.stream)) return RVE_E_CUDA;
+        engine_release(E, slot[i], ms, infos ? infos + i : nullptr);
         const int st = status_of(h->hctrl->done);
         if (status == RVE_OK && st != RVE_OK) status = st;
     }
     return status;
+}
+
+}  // extern "C"
+
+// ================================================================== server (continuous batching)
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    long long ticket = 0;
+    int dim = 3, n = 0, model = 0, nphase = 0, nparam = 0;
+    std::vector<uint8_t> phase;
+    std::vector<double> params, n0;
+    double Fbar[9] = {};
+    double rho = 10.0, tol = 1e-8;
+    size_t bytes = 0;
+    double t_submit = 0.0, t_admit = 0.0;
+};
+
+struct Finished {
+    int status = RVE_OK;
+    double S[9] = {};
+    rve_solve_info info{};
+    double queue_ms = 0.0, latency_ms = 0.0;
+};
+
+using ShapeKey = std::tuple<int, int, int>;
+
+}  // namespace
+
+struct rve_server {
+    rve_options opt{};
+    size_t budget = 0, used = 0;  // bytes of workspaces held (active + pooled)
+    cudaStream_t user_stream = nullptr;
+    Engine E;
+    std::deque<Request> queue;
+    std::map<int, Request> active;  // slot -> request (inputs dropped)
+    std::map<int, rve*> active_h;
+    std::map<long long, Finished> done;
+    std::multimap<ShapeKey, rve*> pool;  // idle handles by (dim, n, model)
+    long long next_ticket = 1;
+    long long completed = 0;
+};
+
+namespace {
+
+size_t server_bytes(const rve_server* s, int dim, int n, int model) {
+    return layout(dim, n, model, s->opt.precision, s->opt.max_iter).total;
+}
+
+void server_drop_pool(rve_server* s, size_t need) {
+    while (s->used + need > s->budget && !s->pool.empty()) {
+        auto it = s->pool.begin();
+        rve* h = it->second;
+        s->used -= server_bytes(s, h->dim, h->n, h->model);
+        rve_destroy(h);
+        s->pool.erase(it);
+    }
+}
+
+// Admit queued requests in arrival order while their workspaces fit the budget.
+int server_admit(rve_server* s) {
+    for (auto it = s->queue.begin(); it != s->queue.end();) {
+        Request& r = *it;
+        const ShapeKey key(r.dim, r.n, r.model);
+        rve* h = nullptr;
+        auto pit = s->pool.find(key);
+        if (pit != s->pool.end()) {
+            h = pit->second;
+            s->pool.erase(pit);
+        } else {
+            server_drop_pool(s, r.bytes);
+            if (s->used + r.bytes > s->budget) {
+                ++it;
+                continue;
+            }
+            const int rc = rve_create(&h, r.dim, r.n, r.model, &s->opt, s->user_stream);
+            if (rc == RVE_E_OOM) {
+                ++it;
+                continue;
+            }
+            if (rc) return rc;
+            s->used += r.bytes;
+        }
+        int rc = rve_set_material(h, r.phase.data(), r.nphase, r.params.data(), r.nparam,
+                                  r.model == RVE_LCE ? r.n0.data() : nullptr);
+        if (rc) {
+            rve_destroy(h);
+            s->used -= r.bytes;
+            return rc;
+        }
+        const int slot = engine_add(s->E, h, r.Fbar, r.rho, r.tol);
+        if (slot < 0) {
+            rve_destroy(h);
+            s->used -= r.bytes;
+            return slot;
+        }
+        r.t_admit = now_ms();
+        r.phase.clear();
+        r.phase.shrink_to_fit();
+        r.params.clear();
+        r.n0.clear();
+        r.n0.shrink_to_fit();
+        s->active[slot] = std::move(r);
+        s->active_h[slot] = h;
+        it = s->queue.erase(it);
+    }
+    return RVE_OK;
+}
+
+int server_retire(rve_server* s, int slot) {
+    rve* h = s->active_h[slot];
+    Request& r = s->active[slot];
+    Finished f;
+    if (read_ctrl_on(h, s->E.stream)) return RVE_E_CUDA;
+    f.status = status_of(h->hctrl->done);
+    engine_release(s->E, slot, 0.0, &f.info);
+    const int rc = rve_stress(h, f.S);
+    if (rc) return rc;
+    const double t = now_ms();
+    f.queue_ms = r.t_admit - r.t_submit;
+    f.latency_ms = t - r.t_submit;
+    f.info.time_ms = t - r.t_admit;
+    s->done[r.ticket] = f;
+    s->pool.insert({ShapeKey(h->dim, h->n, h->model), h});
+    s->active.erase(slot);
+    s->active_h.erase(slot);
+    s->completed += 1;
+    return RVE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rve_server_create(rve_server_t* out, size_t mem_budget_bytes, const rve_options* opt, void* cuda_stream) {
+    if (!out || mem_budget_bytes == 0) return RVE_E_INVALID_ARG;
+    *out = nullptr;
+    rve_options o;
+    rve_default_options(&o);
+    if (opt) o = *opt;
+    if (check_options(o)) return RVE_E_INVALID_ARG;
+    rve_server* s = new (std::nothrow) rve_server();
+    if (!s) return RVE_E_OOM;
+    s->opt = o;
+    s->budget = mem_budget_bytes;
+    s->user_stream = (cudaStream_t)cuda_stream;
+    if (cudaStreamCreateWithFlags(&s->E.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return RVE_E_CUDA;
+    }
+    *out = s;
+    return RVE_OK;
+}
+
+void rve_server_destroy(rve_server_t s) {
+    if (!s) return;
+    engine_free(s->E);
+    for (auto& kv : s->active_h) rve_destroy(kv.second);
+    for (auto& kv : s->pool) rve_destroy(kv.second);
+    if (s->E.stream) cudaStreamDestroy(s->E.stream);
+    delete s;
+}
+
+int rve_server_submit(rve_server_t s, int dim, int n, int model, const uint8_t* phase, int nphase,
+                      const double* params, int nparam, const double* n0, const double Fbar[9], double rho,
+                      double tol, long long* ticket) {
+    if (!s || !phase || !params || !Fbar || !ticket) return RVE_E_INVALID_ARG;
+    if ((dim != 2 && dim != 3) || !valid_n(n)) return RVE_E_INVALID_ARG;
+    if (model != RVE_NEOHOOKE && model != RVE_LINEAR && model != RVE_LCE) return RVE_E_INVALID_ARG;
+    if (model == RVE_LCE && (dim != 3 || !n0 || nparam < 5)) return RVE_E_INVALID_ARG;
+    if (nphase < 1 || nphase > 256 || nparam < 2 || nparam > admm::kMaxParam) return RVE_E_INVALID_ARG;
+    if (!(rho > 0) || !isfinite(rho) || isnan(tol)) return RVE_E_INVALID_ARG;
+    const long long V = dim == 3 ? (long long)n * n * n : (long long)n * n;
+    for (long long v = 0; v < V; ++v)
+        if (phase[v] >= nphase) return RVE_E_INVALID_ARG;
+    const size_t bytes = server_bytes(s, dim, n, model);
+    if (bytes > s->budget) return RVE_E_OOM;  // can never be admitted
+    Request r;
+    r.ticket = s->next_ticket++;
+    r.dim = dim;
+    r.n = n;
+    r.model = model;
+    r.nphase = nphase;
+    r.nparam = nparam;
+    r.phase.assign(phase, phase + V);
+    r.params.assign(params, params + (size_t)nphase * nparam);
+    if (model == RVE_LCE) r.n0.assign(n0, n0 + 3 * V);
+    for (int i = 0; i < 9; ++i) r.Fbar[i] = Fbar[i];
+    r.rho = rho;
+    r.tol = tol;
+    r.bytes = bytes;
+    r.t_submit = now_ms();
+    *ticket = r.ticket;
+    s->queue.push_back(std::move(r));
+    return RVE_OK;
+}
+
+int rve_server_step(rve_server_t s, int* active_out, int* queued_out) {
+    if (!s) return RVE_E_INVALID_ARG;
+    int rc = server_admit(s);
+    if (rc) return rc;
+    if (engine_running(s->E) > 0) {
+        std::vector<int> finished;
+        rc = engine_tick(s->E, finished);
+        if (rc) return rc;
+        for (int slot : finished) {
+            rc = server_retire(s, slot);
+            if (rc) return rc;
+        }
+    }
+    if (active_out) *active_out = (int)s->active.size();
+    if (queued_out) *queued_out = (int)s->queue.size();
+    return RVE_OK;
+}
+
+int rve_server_poll(rve_server_t s, long long ticket, double S[9], rve_solve_info* info, double* latency_ms,
+                    double* queue_ms) {
+    if (!s) return RVE_E_INVALID_ARG;
+    auto it = s->done.find(ticket);
+    if (it == s->done.end()) {
+        for (const Request& r : s->queue)
+            if (r.ticket == ticket) return RVE_E_BUSY;
+        for (const auto& kv : s->active)
+            if (kv.second.ticket == ticket) return RVE_E_BUSY;
+        return RVE_E_NOT_FOUND;
+    }
+    const Finished& f = it->second;
+    if (S)
+        for (int i = 0; i < 9; ++i) S[i] = f.S[i];
+    if (info) *info = f.info;
+    if (latency_ms) *latency_ms = f.latency_ms;
+    if (queue_ms) *queue_ms = f.queue_ms;
+    const int st = f.status;
+    s->done.erase(it);
+    return st == RVE_OK ? RVE_OK : st;
+}
+
+int rve_server_cancel(rve_server_t s, long long ticket) {
+    if (!s) return RVE_E_INVALID_ARG;
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+        if (it->ticket == ticket) {
+            s->queue.erase(it);
+            return RVE_OK;
+        }
+    for (auto& kv : s->active)
+        if (kv.second.ticket == ticket) {
+            const int slot = kv.first;
+            rve* h = s->active_h[slot];
+            CK(cudaStreamSynchronize(s->E.stream));
+            engine_release(s->E, slot, 0.0, nullptr);
+            s->pool.insert({ShapeKey(h->dim, h->n, h->model), h});
+            s->active.erase(slot);
+            s->active_h.erase(slot);
+            return RVE_OK;
+        }
+    return RVE_E_NOT_FOUND;
+}
+
+int rve_server_stats(rve_server_t s, long long* queued, long long* active, long long* completed, size_t* bytes_used) {
+    if (!s) return RVE_E_INVALID_ARG;
+    if (queued) *queued = (long long)s->queue.size();
+    if (active) *active = (long long)s->active.size();
+    if (completed) *completed = s->completed;
+    if (bytes_used) *bytes_used = s->used;
+    return RVE_OK;
 }
 
 }  // extern "C"

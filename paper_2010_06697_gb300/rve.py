@@ -104,6 +104,15 @@ SIGNATURES = {
     "rve_batch_create": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP]),
     "rve_batch_solve": (_I, [_VP, _PD, _PD, _D, ctypes.POINTER(rve_solve_info)]),
     "rve_batch_destroy": (None, [_VP]),
+    "rve_server_create": (_I, [ctypes.POINTER(_VP), _SZ, ctypes.POINTER(rve_options), _VP]),
+    "rve_server_submit": (_I, [_VP, _I, _I, _I, ctypes.POINTER(ctypes.c_uint8), _I, _PD, _I, _PD, _PD, _D, _D,
+                               ctypes.POINTER(ctypes.c_longlong)]),
+    "rve_server_step": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "rve_server_poll": (_I, [_VP, ctypes.c_longlong, _PD, ctypes.POINTER(rve_solve_info), _PD, _PD]),
+    "rve_server_cancel": (_I, [_VP, ctypes.c_longlong]),
+    "rve_server_stats": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                              ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_SZ)]),
+    "rve_server_destroy": (None, [_VP]),
     "rve_kernel_times": (_I, [_VP, _I, _PD, ctypes.POINTER(ctypes.c_longlong), _I]),
 }
 
@@ -290,6 +299,78 @@ class Batch:
         if self.b is not None:
             rve_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server (rve_server_*): submit requests, step, poll results."""
+
+    def __init__(self, mem_budget_bytes, precision="mixed", stream=None, **options):
+        opt = rve_default_options()
+        opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        for k, v in options.items():
+            setattr(opt, k, v)
+        self.opt = opt
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = _VP()
+        _check(lib().rve_server_create(ctypes.byref(h), int(mem_budget_bytes), ctypes.byref(opt), _VP(stream or 0)),
+               "rve_server_create")
+        self.s = h
+
+    def submit(self, phase, params, Fbar, rho, tol, model="neohookean", n0=None):
+        ph = np.ascontiguousarray(phase, dtype=np.uint8)
+        par = np.ascontiguousarray(params, dtype=np.float64)
+        fb = np.ascontiguousarray(np.asarray(Fbar, dtype=np.float64).reshape(3, 3))
+        n0p = None
+        if n0 is not None:
+            n0a = np.ascontiguousarray(n0, dtype=np.float64)
+            n0p = _dptr(n0a)
+        t = ctypes.c_longlong()
+        m = MODELS[model] if isinstance(model, str) else int(model)
+        rc = lib().rve_server_submit(self.s, ph.ndim, ph.shape[0], m, ph.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                     par.shape[0], _dptr(par), par.shape[1], n0p, _dptr(fb), float(rho), float(tol),
+                                     ctypes.byref(t))
+        _check(rc, "rve_server_submit")
+        return t.value
+
+    def step(self):
+        a, q = _I(), _I()
+        _check(lib().rve_server_step(self.s, ctypes.byref(a), ctypes.byref(q)), "rve_server_step")
+        return a.value, q.value
+
+    def poll(self, ticket):
+        """None while pending; else (status, S 3x3, info, latency_ms, queue_ms)."""
+        S = np.zeros(9)
+        info = rve_solve_info()
+        lat, qw = ctypes.c_double(), ctypes.c_double()
+        rc = lib().rve_server_poll(self.s, ticket, _dptr(S), ctypes.byref(info), ctypes.byref(lat), ctypes.byref(qw))
+        if rc == RVE_E_BUSY:
+            return None
+        if rc == RVE_E_NOT_FOUND or rc in (RVE_E_INVALID_ARG, RVE_E_CUDA):
+            raise RveError(rc, "rve_server_poll")
+        return rc, S.reshape(3, 3), info, lat.value, qw.value
+
+    def cancel(self, ticket):
+        return lib().rve_server_cancel(self.s, ticket)
+
+    def stats(self):
+        q, a, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        b = _SZ()
+        _check(lib().rve_server_stats(self.s, ctypes.byref(q), ctypes.byref(a), ctypes.byref(c), ctypes.byref(b)),
+               "rve_server_stats")
+        return {"queued": q.value, "active": a.value, "completed": c.value, "bytes": b.value}
+
+    def close(self):
+        if self.s is not None:
+            lib().rve_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:
