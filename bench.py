@@ -322,6 +322,15 @@ def run_ours(args):
                         "iters_per_step": f["iters_per_step"], "converged": f["converged"],
                         "stress_xx": f["stress"][0][0]}
         line["mixed_over_fp64"] = main["value"] / f["value"]
+    if world == 1 and not args.no_extra:
+        from paper_2010_06697_gb300 import synth
+        extra = {}
+        for name, fn in (("lce256", bench_lce256), ("batch64", bench_batch64), ("serving", bench_serving)):
+            try:
+                extra[name] = fn(torch, rve, synth)
+            except Exception as e:  # report, do not lose the main line
+                extra[name] = {"error": repr(e)[:300]}
+        line["other_workloads"] = extra
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))
@@ -347,6 +356,139 @@ def run_single(args):
     return 0 if info.converged else 1
 
 
+# ------------------------------------------------------------------ the other workloads (extra JSON objects)
+
+def bench_lce256(torch, rve, synth, iters=40):
+    """3D 256^3 LCE polydomain (Section 5.1 readings): one phase mu = 1, lam = 20, r = 7.71,
+    alpha = 0.06, wall length 2h; directors from a Gaussian random field (correlation 8
+    voxels); Fbar = diag(1.2, 0.91, 0.91); mixed precision; fixed iteration count (the
+    relaxation plateaus instead of reaching a tolerance)."""
+    n = 256
+    n0 = synth.director_grf(n, 0, corr=8.0)
+    ph = np.zeros((n,) * 3, np.uint8)
+    par = np.array([[1.0, 20.0, 7.71, 0.06, (2.0 / n) ** 2]])
+    Fb = np.diag([1.2, 0.91, 0.91])
+    s = rve.Rve(3, n, "lce", "mixed", max_iter=iters)
+    s.set_material(ph, par, n0)
+    s.solve(Fb, RHO, -1.0)
+    s.reset()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    info = s.solve(Fb, RHO, -1.0)
+    S = s.stress()
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    s.close()
+    return {"workload": "lce256", "value": ph.size * info.iterations / (ms / 1e3), "unit": UNIT,
+            "ms": ms, "iterations": info.iterations, "fp64_iterations": info.fp64_iterations,
+            "r_p": info.r_p, "r_d": info.r_d, "stress_xx": float(S[0, 0]), "precision": "mixed"}
+
+
+def bench_batch64(torch, rve, synth, count=64):
+    """64 RVEs, N uniform over {32, 48, 64, 96, 128}^3, laminate / inclusion by seed parity,
+    Fbar = I + sym(E) with |E_ij| <= 0.1, tol 1e-8, mixed precision, FFT geometry tuned per
+    N; one batched solve (one persistent launch per pass) against the members solved alone."""
+    spec = synth.batch_spec(count, 0)
+    par = synth.two_phase_params(MU[0], MU[1], NU)
+    tuned = {}
+    for n in sorted({m["n"] for m in spec}):
+        tuned[n] = rve.rve_autotune(3, n, "mixed")
+
+    def make():
+        out = []
+        for m in spec:
+            ph = synth.laminate_phase(m["n"], 3) if m["kind"] == "laminate" else synth.inclusion_phase(m["n"], 3, m["seed"])
+            h = rve.Rve(3, m["n"], "neohookean", "mixed", max_iter=1000)
+            h.set_material(ph, par)
+            out.append(h)
+        return out
+
+    Fb = np.stack([m["Fbar"] for m in spec])
+    rhos = np.full(count, RHO)
+    hs = make()
+    b = rve.Batch(hs)
+    b.solve(Fb, rhos, TOL)                  # warm-up: graphs, tile tables
+    for h in hs:
+        h.reset()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    infos = b.solve(Fb, rhos, TOL)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    vox_it = sum(h.n ** 3 * i.iterations for h, i in zip(hs, infos))
+    # the same members one after the other
+    for h in hs:
+        h.reset()
+    torch.cuda.synchronize()
+    ev0.record()
+    for h, F in zip(hs, Fb):
+        h.solve(F, RHO, TOL)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_seq = ev0.elapsed_time(ev1)
+    b.close()
+    for h in hs:
+        h.close()
+    return {"workload": "batch64", "value": vox_it / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "sequential_ms": ms_seq, "batch_speedup": ms_seq / ms, "voxels": int(sum(m["n"] ** 3 for m in spec)),
+            "converged": int(sum(i.converged for i in infos)), "count": count,
+            "mean_iterations": float(np.mean([i.iterations for i in infos])), "fft_tuned_ms": tuned,
+            "precision": "mixed"}
+
+
+def bench_serving(torch, rve, synth, count=32, rate=200.0):
+    """Poisson arrivals (mean 200/s) of RVE solve requests: N log-uniform over even 2^a 3^b in
+    [32, 256], laminate / inclusion / LCE 40/40/20, Fbar = I + sym(E) with |E_ij| <= 0.1,
+    tol 1e-6, max 150 iterations, mixed precision, admission by a 120 GB device budget."""
+    par = synth.two_phase_params(MU[0], MU[1], NU)
+    stream = synth.serving_stream(count, 0, rate_hz=rate)
+    inputs = []
+    for r in stream:
+        n = r["n"]
+        if r["kind"] == "lce":
+            inputs.append(dict(phase=np.zeros((n,) * 3, np.uint8), n0=synth.director_grf(n, r["seed"], corr=8.0),
+                               params=np.array([[1.0, 20.0, 7.71, 0.06, (2.0 / n) ** 2]]), model="lce"))
+        else:
+            ph = synth.laminate_phase(n, 3) if r["kind"] == "laminate" else synth.inclusion_phase(n, 3, r["seed"])
+            inputs.append(dict(phase=ph, n0=None, params=par, model="neohookean"))
+    srv = rve.Server(120 << 30, "mixed", max_iter=150, check_every=8)
+    for i in range(2):                           # warm-up requests (graphs, modules)
+        t = srv.submit(inputs[i]["phase"], inputs[i]["params"], stream[i]["Fbar"], RHO, 1e-6, inputs[i]["model"],
+                       inputs[i]["n0"])
+        while srv.poll(t) is None:
+            srv.step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets, results, nxt = {}, {}, 0
+    while len(results) < count:
+        now = time.perf_counter() - t0
+        while nxt < count and stream[nxt]["t"] <= now:
+            inp = inputs[nxt]
+            tickets[nxt] = srv.submit(inp["phase"], inp["params"], stream[nxt]["Fbar"], RHO, 1e-6, inp["model"],
+                                      inp["n0"])
+            nxt += 1
+        srv.step()
+        for i, t in list(tickets.items()):
+            if i not in results:
+                out = srv.poll(t)
+                if out is not None:
+                    results[i] = out
+    wall = time.perf_counter() - t0
+    lat = np.array([results[i][3] for i in range(count)])
+    vox_it = sum(stream[i]["n"] ** 3 * results[i][2].iterations for i in range(count))
+    srv.close()
+    return {"workload": "serving", "value": vox_it / wall, "unit": UNIT, "requests": count, "rate_hz": rate,
+            "wall_s": wall, "p50_latency_ms": float(np.percentile(lat, 50)),
+            "p99_latency_ms": float(np.percentile(lat, 99)),
+            "converged": int(sum(results[i][2].converged for i in range(count))),
+            "sizes": sorted(int(r["n"]) for r in stream), "precision": "mixed",
+            "note": "all requests arrive within ~0.2 s: latency includes queueing behind a saturated GPU"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -356,6 +498,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the fp64 comparison run")
+    ap.add_argument("--no-extra", action="store_true", help="skip the LCE, batch and serving workloads")
     ap.add_argument("--single", action="store_true",
                     help="one solve of the workload (for profiler captures), prints a short summary")
     args = ap.parse_args()

@@ -241,6 +241,22 @@ int rve_server_stats(rve_server_t s, long long* queued, long long* active, long 
 /* Release the server, its pooled and running workspaces. */
 void rve_server_destroy(rve_server_t s);
 
+/* ------------------------------------------------------------------ FFT autotuner */
+/* Time candidate FFT geometries for N^d grids on the current device -- x-pass
+ * lines per block with the order of the half-length radices, y/z tile width with
+ * the order of the full-length radices -- in the arithmetic of the given precision
+ * mode (double for RVE_FP64, float otherwise), and keep the fastest: every later
+ * rve_create of that shape in this process uses it (handles created before keep
+ * theirs).  If cache_path is not NULL, one text line
+ * "rve-fft-geometry dim n precision lpb tk64 tk32 nh r... nf r... ms" is appended.
+ * *best_ms (may be NULL) gets the tuned FFT time of one iteration.  Allocates a
+ * scratch handle.  Returns RVE_OK or an error. */
+int rve_autotune(int dim, int n, int precision, const char* cache_path, double* best_ms);
+
+/* Register the geometries stored in a cache file written by rve_autotune (later
+ * lines win).  Returns the number of lines loaded, or RVE_E_NOT_FOUND. */
+int rve_autotune_load(const char* cache_path);
+
 /* ------------------------------------------------------------------ profiling */
 /* Kernel classes of the iteration (index into rve_kernel_times' arrays). */
 enum rve_kernel_class {

@@ -13,6 +13,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <stdio.h>
+
 #include <algorithm>
 #include <chrono>
 #include <deque>
@@ -69,15 +71,6 @@ bool valid_n(int n) {
     while (m % 2 == 0) m /= 2;
     while (m % 3 == 0) m /= 3;
     return m == 1;
-}
-
-int factor(int L, int* rad) {
-    int np = 0;
-    while (L % 8 == 0) { rad[np++] = 8; L /= 8; }
-    if (L % 4 == 0) { rad[np++] = 4; L /= 4; }
-    if (L % 2 == 0) { rad[np++] = 2; L /= 2; }
-    while (L % 3 == 0) { rad[np++] = 3; L /= 3; }
-    return L == 1 ? np : -1;
 }
 
 struct Layout {
@@ -568,10 +561,6 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
         L.S32 = L.U32[0];
         L.D32 = L.U32[1];
     }
-    const int H = n / 2;
-    L.plan.n = n;
-    L.plan.np_half = factor(H, L.plan.rad_half);
-    L.plan.np_full = factor(n, L.plan.rad_full);
     if (L.plan.np_half < 0 || L.plan.np_full < 0) return fail(RVE_E_INVALID_ARG);
     if (admm::prepare_fft_kernels(n) != cudaSuccess) return fail(RVE_E_CUDA);
     // single-RVE execution: descriptor and tile tables (RVE index 0) in the workspace
@@ -1580,6 +1569,217 @@ int rve_server_stats(rve_server_t s, long long* queued, long long* active, long 
     if (completed) *completed = s->completed;
     if (bytes_used) *bytes_used = s->used;
     return RVE_OK;
+}
+
+}  // extern "C"
+
+// ================================================================== FFT autotuner
+
+namespace {
+
+// distinct orderings of a radix multiset
+std::vector<std::vector<int>> radix_orders(int L) {
+    int rad[admm::kMaxPasses];
+    const int np = admm::factor_radices(L, rad);
+    std::vector<int> v(rad, rad + np);
+    std::sort(v.begin(), v.end());
+    std::vector<std::vector<int>> out;
+    do out.push_back(v);
+    while (std::next_permutation(v.begin(), v.end()) && out.size() < 12);
+    return out;
+}
+
+int upload_tiles_tmp(rve* h, const Launch& L, int2** buf, int* cap, int cls, admm::Exec& E) {
+    const int cnt = cls == admm::kTilesX ? admm::tiles_x(L) : admm::tiles_ax(L, cls == admm::kTilesAx64);
+    if (cnt > *cap) {
+        if (*buf) cudaFree(*buf);
+        *buf = nullptr;
+        if (cudaMalloc((void**)buf, sizeof(int2) * cnt) != cudaSuccess) return RVE_E_OOM;
+        *cap = cnt;
+    }
+    std::vector<int2> t(cnt);
+    for (int i = 0; i < cnt; ++i) t[i] = make_int2(0, i);
+    CK(cudaMemcpyAsync(*buf, t.data(), sizeof(int2) * cnt, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    E.tiles[cls] = *buf;
+    E.ntiles[cls] = cnt;
+    return RVE_OK;
+}
+
+// min over reps of the summed device time of the chosen FFT stages
+int time_stages(rve* h, admm::Exec& E, bool fp64, const std::vector<int>& stages, double* best) {
+    const int S = admm::fft_stages(h->dim);
+    std::vector<cudaEvent_t> ev(S + 1);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    *best = 1e30;
+    for (int rep = 0; rep < 4; ++rep) {
+        CK(cudaEventRecord(ev[0], h->stream));
+        for (int st = 0; st < S; ++st) {
+            if (admm::launch_fft(E, fp64, st) != cudaSuccess) return RVE_E_CUDA;
+            CK(cudaEventRecord(ev[st + 1], h->stream));
+        }
+        CK(cudaEventSynchronize(ev[S]));
+        double t = 0.0;
+        for (int st : stages) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[st], ev[st + 1]);
+            t += ms;
+        }
+        if (rep > 0) *best = std::min(*best, t);  // first repetition warms up
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return RVE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rve_autotune(int dim, int n, int precision, const char* cache_path, double* best_ms) {
+    if ((dim != 2 && dim != 3) || !valid_n(n) || precision < RVE_FP64 || precision > RVE_FP32)
+        return RVE_E_INVALID_ARG;
+    const bool fp64 = precision == RVE_FP64;
+    rve_options o;
+    rve_default_options(&o);
+    o.precision = fp64 ? RVE_FP64 : RVE_FP32;
+    o.max_iter = 1;
+    rve* h = nullptr;
+    int rc = rve_create(&h, dim, n, RVE_NEOHOOKE, &o, nullptr);
+    if (rc) return rc;
+    const long long V = h->V;
+    std::vector<uint8_t> ph((size_t)V, 0);
+    const double par[2] = {1.0, 1.5};
+    const double I[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    int2 *tx = nullptr, *ta = nullptr;
+    int capx = 0, capa = 0;
+    admm::Geometry best_g = admm::default_geometry(dim, n);
+    double best_x = 1e30, best_a = 1e30;
+    auto cleanup = [&](int code) {
+        if (tx) cudaFree(tx);
+        if (ta) cudaFree(ta);
+        rve_destroy(h);
+        return code;
+    };
+    if ((rc = rve_set_material(h, ph.data(), 1, par, 2, nullptr))) return cleanup(rc);
+    if ((rc = begin_solve(h, I, 10.0, -1.0, h->stream))) return cleanup(rc);
+    const int H = n / 2, nlines = dim == 3 ? n * n : n;
+    const int S = admm::fft_stages(dim);
+    const std::vector<int> xstages = {0, S - 1};
+    std::vector<int> astages;
+    for (int st = 1; st < S - 1; ++st) astages.push_back(st);
+    const auto half_orders = radix_orders(H);
+    const auto full_orders = radix_orders(n);
+    std::vector<int> lpbs;
+    for (int t : {1024, 2048, 4096, 8192}) {
+        const int l = std::max(1, std::min(nlines, t / n));
+        if (std::find(lpbs.begin(), lpbs.end(), l) == lpbs.end()) lpbs.push_back(l);
+    }
+    std::vector<int> tks;
+    for (int t : {4, 8, 16, 32})
+        if (t <= H) tks.push_back(t);
+    if (tks.empty()) tks.push_back(H);
+    admm::Exec E = h->E;
+    const int acls = fp64 ? admm::kTilesAx64 : admm::kTilesAx32;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool xpass = pass == 0;
+        const size_t nc = xpass ? lpbs.size() * half_orders.size() : tks.size() * full_orders.size();
+        for (size_t c = 0; c < nc; ++c) {
+            admm::Geometry g = best_g;
+            if (xpass) {
+                g.lpb = lpbs[c / half_orders.size()];
+                const auto& ord = half_orders[c % half_orders.size()];
+                g.np_half = (int)ord.size();
+                for (size_t i = 0; i < ord.size(); ++i) g.rad_half[i] = ord[i];
+            } else {
+                (fp64 ? g.tk64 : g.tk32) = tks[c / full_orders.size()];
+                const auto& ord = full_orders[c % full_orders.size()];
+                g.np_full = (int)ord.size();
+                for (size_t i = 0; i < ord.size(); ++i) g.rad_full[i] = ord[i];
+            }
+            admm::apply_geometry(h->L, g);
+            if ((rc = write_desc(h))) return cleanup(rc);
+            if ((rc = upload_tiles_tmp(h, h->L, &tx, &capx, admm::kTilesX, E))) return cleanup(rc);
+            if ((rc = upload_tiles_tmp(h, h->L, &ta, &capa, acls, E))) return cleanup(rc);
+            for (int f = 0; f < 2; ++f) {
+                E.smem_x[f] = admm::smem_x_bytes(h->L, f == 1);
+                E.smem_a[f] = admm::smem_a_bytes(h->L, f == 1);
+            }
+            if (E.smem_x[fp64] > 200 * 1024 || E.smem_a[fp64] > 200 * 1024) continue;
+            double t = 0.0;
+            if ((rc = time_stages(h, E, fp64, xpass ? xstages : astages, &t))) return cleanup(rc);
+            if (xpass && t < best_x) {
+                best_x = t;
+                best_g.lpb = g.lpb;
+                best_g.np_half = g.np_half;
+                for (int i = 0; i < admm::kMaxPasses; ++i) best_g.rad_half[i] = g.rad_half[i];
+            } else if (!xpass && t < best_a) {
+                best_a = t;
+                (fp64 ? best_g.tk64 : best_g.tk32) = fp64 ? g.tk64 : g.tk32;
+                best_g.np_full = g.np_full;
+                for (int i = 0; i < admm::kMaxPasses; ++i) best_g.rad_full[i] = g.rad_full[i];
+            }
+        }
+        (void)nlines;
+    }
+    admm::register_geometry(dim, n, best_g);
+    if (best_ms) *best_ms = best_x + best_a;
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "rve-fft-geometry %d %d %d %d %d %d %d", dim, n, precision, best_g.lpb, best_g.tk64,
+                    best_g.tk32, best_g.np_half);
+            for (int i = 0; i < best_g.np_half; ++i) fprintf(f, " %d", best_g.rad_half[i]);
+            fprintf(f, " %d", best_g.np_full);
+            for (int i = 0; i < best_g.np_full; ++i) fprintf(f, " %d", best_g.rad_full[i]);
+            fprintf(f, " %.6f\n", best_x + best_a);
+            fclose(f);
+        }
+    }
+    return cleanup(RVE_OK);
+}
+
+int rve_autotune_load(const char* cache_path) {
+    if (!cache_path) return RVE_E_INVALID_ARG;
+    FILE* f = fopen(cache_path, "r");
+    if (!f) return RVE_E_NOT_FOUND;
+    char line[512];
+    int loaded = 0;
+    while (fgets(line, sizeof line, f)) {
+        admm::Geometry g{};
+        int dim, n, prec, pos = 0;
+        if (sscanf(line, "rve-fft-geometry %d %d %d %d %d %d %d%n", &dim, &n, &prec, &g.lpb, &g.tk64, &g.tk32,
+                   &g.np_half, &pos) != 7)
+            continue;
+        const char* p = line + pos;
+        bool ok = (dim == 2 || dim == 3) && valid_n(n) && g.np_half > 0 && g.np_half <= admm::kMaxPasses;
+        int prod = 1;
+        for (int i = 0; ok && i < g.np_half; ++i) {
+            int r = 0, k = 0;
+            ok = sscanf(p, " %d%n", &r, &k) == 1 && (r == 2 || r == 3 || r == 4 || r == 8);
+            g.rad_half[i] = r;
+            prod *= r;
+            p += k;
+        }
+        ok = ok && prod == n / 2;
+        int k = 0;
+        ok = ok && sscanf(p, " %d%n", &g.np_full, &k) == 1 && g.np_full > 0 && g.np_full <= admm::kMaxPasses;
+        p += k;
+        prod = 1;
+        for (int i = 0; ok && i < g.np_full; ++i) {
+            int r = 0;
+            ok = sscanf(p, " %d%n", &r, &k) == 1 && (r == 2 || r == 3 || r == 4 || r == 8);
+            g.rad_full[i] = r;
+            prod *= r;
+            p += k;
+        }
+        ok = ok && prod == n && g.lpb >= 1 && g.tk64 >= 1 && g.tk64 <= n / 2 && g.tk32 >= 1 && g.tk32 <= n / 2;
+        if (ok) {
+            admm::register_geometry(dim, n, g);
+            ++loaded;
+        }
+    }
+    fclose(f);
+    return loaded;
 }
 
 }  // extern "C"

@@ -579,16 +579,69 @@ cudaError_t launch_fft_incr(const Exec& E, int stage) {
     return E.rep->dim == 3 ? run_fft<float, 3, true>(E, stage) : run_fft<float, 2, true>(E, stage);
 }
 
-void set_geometry(Launch& L) {
-    const int n = L.n, H = n / 2;
+// Radix sequence for a transform length L = 2^a 3^b: radix 8 first, then 4, 2, 3.
+int factor_radices(int L, int* rad) {
+    int np = 0;
+    while (L % 8 == 0) { rad[np++] = 8; L /= 8; }
+    if (L % 4 == 0) { rad[np++] = 4; L /= 4; }
+    if (L % 2 == 0) { rad[np++] = 2; L /= 2; }
+    while (L % 3 == 0) { rad[np++] = 3; L /= 3; }
+    return L == 1 ? np : -1;
+}
+
+namespace {
+std::mutex g_geo_mu;
+std::map<std::pair<int, int>, Geometry> g_geo;  // (dim, n) -> tuned geometry
+}  // namespace
+
+void register_geometry(int dim, int n, const Geometry& g) {
+    std::lock_guard<std::mutex> lock(g_geo_mu);
+    g_geo[{dim, n}] = g;
+}
+
+bool lookup_geometry(int dim, int n, Geometry* g) {
+    std::lock_guard<std::mutex> lock(g_geo_mu);
+    auto it = g_geo.find({dim, n});
+    if (it == g_geo.end()) return false;
+    *g = it->second;
+    return true;
+}
+
+Geometry default_geometry(int dim, int n) {
+    Geometry g{};
+    const int H = n / 2;
+    const int nlines = dim == 3 ? n * n : n;
+    g.lpb = lines_per_block(n, nlines);
+    g.tk64 = FftArgs<double>::tk < H ? FftArgs<double>::tk : H;
+    g.tk32 = FftArgs<float>::tk < H ? FftArgs<float>::tk : H;
+    g.np_half = factor_radices(H, g.rad_half);
+    g.np_full = factor_radices(n, g.rad_full);
+    return g;
+}
+
+void apply_geometry(Launch& L, const Geometry& g) {
+    const int n = L.n;
     const int nlines = L.dim == 3 ? n * n : n;
+    L.lpb = g.lpb < nlines ? g.lpb : nlines;
+    L.xblocks = (nlines + L.lpb - 1) / L.lpb;
+    L.tk64 = g.tk64;
+    L.tk32 = g.tk32;
+    L.plan.n = n;
+    L.plan.np_half = g.np_half;
+    L.plan.np_full = g.np_full;
+    for (int i = 0; i < kMaxPasses; ++i) {
+        L.plan.rad_half[i] = i < g.np_half ? g.rad_half[i] : 0;
+        L.plan.rad_full[i] = i < g.np_full ? g.rad_full[i] : 0;
+    }
+}
+
+void set_geometry(Launch& L) {
     const long long want = (L.V + kLocalThreads - 1) / kLocalThreads;
     const long long cap = 152 * 12;  // whole waves at 2, 3, 4 or 6 resident blocks per SM
     L.local_blocks = (int)(want < cap ? want : cap);
-    L.lpb = lines_per_block(n, nlines);
-    L.xblocks = (nlines + L.lpb - 1) / L.lpb;
-    L.tk64 = FftArgs<double>::tk < H ? FftArgs<double>::tk : H;
-    L.tk32 = FftArgs<float>::tk < H ? FftArgs<float>::tk : H;
+    Geometry g;
+    if (!lookup_geometry(L.dim, L.n, &g)) g = default_geometry(L.dim, L.n);
+    apply_geometry(L, g);
 }
 
 int tiles_local(const Launch& L) { return L.local_blocks; }

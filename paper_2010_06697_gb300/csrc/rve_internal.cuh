@@ -115,7 +115,21 @@ struct Exec {
     size_t smem_a[2];             // and of the y/z passes
 };
 
-// per-RVE launch geometry (local_blocks, lpb, xblocks, tk) from dim and n
+// FFT geometry of one grid shape: x-pass lines per block and half-length radices,
+// y/z tile widths and full-length radices (default rule or picked by the autotuner)
+struct Geometry {
+    int lpb, tk64, tk32;
+    int np_half, np_full;
+    int rad_half[kMaxPasses];
+    int rad_full[kMaxPasses];
+};
+int factor_radices(int L, int* rad);
+Geometry default_geometry(int dim, int n);
+void register_geometry(int dim, int n, const Geometry& g);
+bool lookup_geometry(int dim, int n, Geometry* g);
+void apply_geometry(Launch& L, const Geometry& g);
+// per-RVE launch geometry (local_blocks, lpb, xblocks, tk, radices) from dim and n
+// (the registered tuned geometry of the shape if any, else the default rule)
 void set_geometry(Launch& L);
 // tiles of one RVE for each class
 int tiles_local(const Launch& L);

@@ -113,6 +113,8 @@ SIGNATURES = {
     "rve_server_stats": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                               ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_SZ)]),
     "rve_server_destroy": (None, [_VP]),
+    "rve_autotune": (_I, [_I, _I, _I, ctypes.c_char_p, _PD]),
+    "rve_autotune_load": (_I, [ctypes.c_char_p]),
     "rve_kernel_times": (_I, [_VP, _I, _PD, ctypes.POINTER(ctypes.c_longlong), _I]),
 }
 
@@ -244,6 +246,19 @@ def rve_stress_noalloc(dim, n, model, F_ptr, phase_ptr, params_ptr, nphase, npar
     """Device pointers in, device pointer out; see include/rve.h (no device allocation)."""
     return lib().rve_stress_noalloc(dim, n, model, _VP(F_ptr), _VP(phase_ptr), _VP(params_ptr), nphase, nparam,
                                     _VP(S_ptr), _VP(stream or 0))
+
+
+def rve_autotune(dim, n, precision="mixed", cache_path=None):
+    """Tune the FFT geometry of N^d grids; returns the tuned FFT milliseconds per iteration."""
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    ms = ctypes.c_double()
+    rc = lib().rve_autotune(dim, n, p, cache_path.encode() if cache_path else None, ctypes.byref(ms))
+    _check(rc, "rve_autotune")
+    return ms.value
+
+
+def rve_autotune_load(cache_path):
+    return lib().rve_autotune_load(cache_path.encode())
 
 
 def rve_set_profiling(h, on):
