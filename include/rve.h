@@ -80,7 +80,8 @@ typedef struct rve_options {
     double mu_ref;      /* modulus in r_d (eq. check); 0 selects the volume average
                            of the per-voxel shear modulus                          */
     double mixed_switch;/* RVE_MIXED: promote to double once max(r_p, r_d) <= this
-                           or float stagnates; default 1e-6                        */
+                           or float stagnates; default 3e-7 (float state reaches
+                           about 2e-7 on O(1) deformation gradients)               */
     int check_every;    /* host reads the device status every this many iterations */
     int use_graph;      /* 1: replay iteration chunks as a CUDA graph (default 1)  */
 } rve_options;

@@ -613,28 +613,35 @@ __device__ __forceinline__ int newton_lce(const Lce<T>& m, T* F, T* n, const T* 
 
 // ------------------------------------------------------------------ grid helpers
 
+// Periodic neighbour indices of voxel v (x fastest).  32-bit arithmetic: one
+// RVE has at most 512^3 < 2^31 voxels, and 64-bit division would run as a long
+// software sequence on every voxel.
 template <int D>
 struct Nbr {
-    long long xp, xm, yp, ym, zp, zm;
+    int xp, xm, yp, ym, zp, zm;
 };
 
 template <int D>
-__device__ __forceinline__ Nbr<D> neighbours(long long v, int n) {
+__device__ __forceinline__ Nbr<D> neighbours(int v, int n) {
     Nbr<D> o;
-    const int x = (int)(v % n);
-    const long long r = v / n;
-    const int y = (int)(r % n);
+    const unsigned un = (unsigned)n;
+    const unsigned r = (unsigned)v / un;
+    const int x = v - (int)(r * un);
     o.xp = v + (x + 1 == n ? 1 - n : 1);
     o.xm = v + (x == 0 ? n - 1 : -1);
-    const long long sn = n;
-    o.yp = v + (y + 1 == n ? (1 - n) * sn : sn);
-    o.ym = v + (y == 0 ? (n - 1) * sn : -sn);
     if constexpr (D == 3) {
-        const int z = (int)(r / n);
-        const long long s2 = sn * sn;
+        const unsigned zq = r / un;
+        const int y = (int)(r - zq * un);
+        const int z = (int)zq;
+        o.yp = v + (y + 1 == n ? (1 - n) * n : n);
+        o.ym = v + (y == 0 ? (n - 1) * n : -n);
+        const int s2 = n * n;
         o.zp = v + (z + 1 == n ? (1 - n) * s2 : s2);
         o.zm = v + (z == 0 ? (n - 1) * s2 : -s2);
     } else {
+        const int y = (int)r;
+        o.yp = v + (y + 1 == n ? (1 - n) * n : n);
+        o.ym = v + (y == 0 ? (n - 1) * n : -n);
         o.zp = o.zm = v;
     }
     return o;
@@ -813,7 +820,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     double rp2 = 0.0, rd2 = 0.0;
     int nmax = 0, nfail = 0;
     for (long long v = bid * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)nblk * blockDim.x) {
-        const Nbr<D> nb = neighbours<D>(v, n);
+        const Nbr<D> nb = neighbours<D>((int)v, n);
         T G[NN], L[NN], F[NN];
         grad_u<T, D>(Unew, V, nb, Fb, half_n, G);
 #pragma unroll
@@ -1008,7 +1015,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
 
 
 template <typename T, int D, int MODEL, bool WRITE_R, bool DU>
-__global__ void __launch_bounds__(kLocalThreads)
+__global__ void __launch_bounds__(kLocalThreads, (sizeof(T) == 4 && MODEL != kLce) ? 4 : 1)
 k_local(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles, int first,
         int only_if_rho_changed) {
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
