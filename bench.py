@@ -350,7 +350,8 @@ def run_ours(args):
     if world == 1 and not args.no_extra:
         from paper_2010_06697_gb300 import synth
         extra = {}
-        for name, fn in (("lce256", bench_lce256), ("batch64", bench_batch64), ("serving", bench_serving)):
+        for name, fn in (("laminate32_2d", bench_laminate32), ("lce256", bench_lce256), ("batch64", bench_batch64),
+                         ("serving", bench_serving)):
             try:
                 extra[name] = fn(torch, rve, synth)
             except Exception as e:  # report, do not lose the main line
@@ -382,6 +383,34 @@ def run_single(args):
 
 
 # ------------------------------------------------------------------ the other workloads (extra JSON objects)
+
+def bench_laminate32(torch, rve, synth, iters=300, reps=5):
+    """2D 32x32 plane-strain neo-Hookean laminate (mu = 1 | 10, nu = 0.3), Fbar = diag(1.05, 1),
+    rho = 10, exactly 300 FP64 iterations: a latency-bound cell (1024 voxels); reports the device
+    time per iteration of the whole solve."""
+    n = 32
+    ph = synth.laminate_phase(n, 2)
+    par = synth.two_phase_params(MU[0], MU[1], NU)
+    s = rve.Rve(2, n, "neohookean", "fp64", max_iter=iters)
+    s.set_material(ph, par)
+    Fb = np.diag([1.05, 1.0, 1.0])
+    s.solve(Fb, RHO, -1.0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 1e30
+    for _ in range(reps):
+        s.reset()
+        torch.cuda.synchronize()
+        ev0.record()
+        info = s.solve(Fb, RHO, -1.0)
+        S = s.stress()
+        ev1.record()
+        torch.cuda.synchronize()
+        best = min(best, ev0.elapsed_time(ev1))
+    s.close()
+    return {"workload": "laminate32_2d", "value": ph.size * iters / (best / 1e3), "unit": UNIT,
+            "us_per_iteration": 1e3 * best / iters, "ms": best, "iterations": info.iterations,
+            "stress_xx": float(S[0, 0]), "precision": "fp64"}
+
 
 def bench_lce256(torch, rve, synth, iters=40):
     """3D 256^3 LCE polydomain (Section 5.1 readings): one phase mu = 1, lam = 20, r = 7.71,

@@ -1670,12 +1670,12 @@ int rve_autotune(int dim, int n, int precision, const char* cache_path, double* 
     const auto half_orders = radix_orders(H);
     const auto full_orders = radix_orders(n);
     std::vector<int> lpbs;
-    for (int t : {1024, 2048, 4096, 8192}) {
+    for (int t : {32, 128, 512, 1024, 2048, 4096, 8192}) {
         const int l = std::max(1, std::min(nlines, t / n));
         if (std::find(lpbs.begin(), lpbs.end(), l) == lpbs.end()) lpbs.push_back(l);
     }
     std::vector<int> tks;
-    for (int t : {4, 8, 16, 32})
+    for (int t : {1, 2, 4, 8, 16, 32})
         if (t <= H) tks.push_back(t);
     if (tks.empty()) tks.push_back(H);
     admm::Exec E = h->E;

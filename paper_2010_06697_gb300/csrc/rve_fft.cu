@@ -611,9 +611,15 @@ Geometry default_geometry(int dim, int n) {
     Geometry g{};
     const int H = n / 2;
     const int nlines = dim == 3 ? n * n : n;
+    // small grids: fewer lines / columns per block until a pass has ~2 blocks per SM
+    const int want_blocks = 2 * 152;
     g.lpb = lines_per_block(n, nlines);
+    while (g.lpb > 1 && (nlines + g.lpb - 1) / g.lpb < want_blocks) g.lpb /= 2;
+    auto ax_blocks = [&](int tk) { return ((H + tk - 1) / tk) * (dim == 3 ? n : 1) * dim; };
     g.tk64 = FftArgs<double>::tk < H ? FftArgs<double>::tk : H;
     g.tk32 = FftArgs<float>::tk < H ? FftArgs<float>::tk : H;
+    while (g.tk64 > 1 && ax_blocks(g.tk64) < want_blocks) g.tk64 /= 2;
+    while (g.tk32 > 1 && ax_blocks(g.tk32) < want_blocks) g.tk32 /= 2;
     g.np_half = factor_radices(H, g.rad_half);
     g.np_full = factor_radices(n, g.rad_full);
     return g;
@@ -636,7 +642,13 @@ void apply_geometry(Launch& L, const Geometry& g) {
 }
 
 void set_geometry(Launch& L) {
-    const long long want = (L.V + kLocalThreads - 1) / kLocalThreads;
+    // voxels a local tile covers per sweep: a whole block of threads, or fewer for small
+    // cells so that the local step still spreads over ~2 blocks per SM (a function of the
+    // RVE's size only, so results do not depend on what else runs in the launch)
+    int chunk = kLocalThreads;
+    while (chunk > 32 && (L.V + chunk - 1) / chunk < 2 * 152) chunk /= 2;
+    L.local_chunk = chunk;
+    const long long want = (L.V + chunk - 1) / chunk;
     const long long cap = 152 * 12;  // whole waves at 2, 3, 4 or 6 resident blocks per SM
     L.local_blocks = (int)(want < cap ? want : cap);
     Geometry g;

@@ -65,6 +65,7 @@ struct Launch {
     int dim, n, model;
     long long V;
     int local_blocks;      // blocks (tiles) of the local kernel for this RVE
+    int local_chunk;       // voxels one local tile covers per sweep (<= kLocalThreads)
     int lpb, xblocks;      // x passes: lines per block, blocks
     int tk64, tk32;        // y/z passes: columns per tile (double / float)
     Ctrl* ctrl;

@@ -819,7 +819,8 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
 
     double rp2 = 0.0, rd2 = 0.0;
     int nmax = 0, nfail = 0;
-    for (long long v = bid * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)nblk * blockDim.x) {
+    const int chunk = L.local_chunk;
+    for (long long v = bid * (long long)chunk + threadIdx.x; threadIdx.x < chunk && v < V; v += (long long)nblk * chunk) {
         const Nbr<D> nb = neighbours<D>((int)v, n);
         T G[NN], L[NN], F[NN];
         grad_u<T, D>(Unew, V, nb, Fb, half_n, G);
