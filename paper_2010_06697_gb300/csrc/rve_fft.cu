@@ -132,64 +132,63 @@ __device__ __forceinline__ void dft(V* v) {
     else dft8<INV>(v);
 }
 
-// One Stockham pass of radix R over `nl` independent transforms of length Lx
-// held in shared memory.  Element e of transform l sits at l*ls + e*es.  Ns is
-// the product of the radices already applied.  Output is in natural order
-// after the last pass.  COLS: consecutive threads take consecutive transforms
-// (tiles of columns); otherwise consecutive butterflies of one transform.
+// One Stockham pass of radix R over `nl` independent transforms of length L
+// held in shared memory.  Element e of transform l sits at l*ls + e*es.  P holds
+// nb = L/R, Ns (the product of the radices already applied) and the twiddle
+// stride.  Output is in natural order after the last pass.  COLS: consecutive
+// threads take consecutive transforms (tiles of columns); otherwise consecutive
+// butterflies of one transform.
 template <int R, bool INV, bool COLS, typename V>
 __device__ __forceinline__ void stockham_pass(const V* __restrict__ src, V* __restrict__ dst,
-                                              const V* __restrict__ tw, int Lx, int Ns, int twmul, int nl,
+                                              const V* __restrict__ tw, const FftPass& P, const FastDiv& nl,
                                               int ls, int es) {
-    const int nb = Lx / R;
-    const int total = nb * nl;
-    const int tstep = (Lx / (Ns * R)) * twmul;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        int l, j;
+    const unsigned nb = P.nb.d, Ns = P.ns.d;
+    const unsigned total = nb * nl.d;
+    const int tstep = P.tstep;
+    for (unsigned t = threadIdx.x; t < total; t += blockDim.x) {
+        unsigned l, j;
         if (COLS) {
-            l = t % nl;
-            j = t / nl;
+            j = fdiv(t, nl);
+            l = t - j * nl.d;
         } else {
-            j = t % nb;
-            l = t / nb;
+            l = fdiv(t, P.nb);
+            j = t - l * nb;
         }
-        const int base = l * ls;
+        const int base = (int)l * ls;
         V v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[base + (j + r * nb) * es];
-        const int kk = j % Ns;
+        for (int r = 0; r < R; ++r) v[r] = src[base + (int)(j + r * nb) * es];
+        const unsigned kk = j - fdiv(j, P.ns) * Ns;
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                V w = tw[r * kk * tstep];
+                V w = tw[r * (int)kk * tstep];
                 if (INV) w = cconj(w);
                 v[r] = cmul(v[r], w);
             }
         }
         dft<R, INV>(v);
-        const int d0 = (j - kk) * R + kk;
+        const int d0 = (int)((j - kk) * R + kk);
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[base + (d0 + r * Ns) * es] = v[r];
+        for (int r = 0; r < R; ++r) dst[base + (d0 + r * (int)Ns) * es] = v[r];
     }
 }
 
-// All passes of one transform length; returns the buffer holding the result.
+// All passes of one transform; returns the buffer holding the result.
 template <bool INV, bool COLS, typename V>
-__device__ V* stockham(V* a, V* b, const V* tw, int Lx, const int* rad, int np, int twmul, int nl, int ls,
-                       int es) {
-    int Ns = 1;
+__device__ V* stockham(V* a, V* b, const V* tw, const int* rad, const FftPass* passes, int np, const FastDiv& nl,
+                       int ls, int es) {
     V* src = a;
     V* dst = b;
     for (int p = 0; p < np; ++p) {
-        const int R = rad[p];
-        switch (R) {
-            case 2: stockham_pass<2, INV, COLS>(src, dst, tw, Lx, Ns, twmul, nl, ls, es); break;
-            case 3: stockham_pass<3, INV, COLS>(src, dst, tw, Lx, Ns, twmul, nl, ls, es); break;
-            case 4: stockham_pass<4, INV, COLS>(src, dst, tw, Lx, Ns, twmul, nl, ls, es); break;
-            default: stockham_pass<8, INV, COLS>(src, dst, tw, Lx, Ns, twmul, nl, ls, es); break;
+        const FftPass& P = passes[p];
+        switch (rad[p]) {
+            case 2: stockham_pass<2, INV, COLS>(src, dst, tw, P, nl, ls, es); break;
+            case 3: stockham_pass<3, INV, COLS>(src, dst, tw, P, nl, ls, es); break;
+            case 4: stockham_pass<4, INV, COLS>(src, dst, tw, P, nl, ls, es); break;
+            default: stockham_pass<8, INV, COLS>(src, dst, tw, P, nl, ls, es); break;
         }
         __syncthreads();
-        Ns *= R;
         V* t = src;
         src = dst;
         dst = t;
@@ -212,6 +211,7 @@ struct FftArgs<double> {
     __host__ __device__ static const double2* tw(const Launch& L) { return L.tw64; }
     __host__ __device__ static const double* ksq(const Launch& L) { return L.ksq64; }
     __host__ __device__ static int tile(const Launch& L) { return L.tk64; }
+    __host__ __device__ static const FastDiv& tile_div(const Launch& L) { return L.plan.div_tk64; }
     static constexpr int tk = 8;
 };
 template <>
@@ -222,6 +222,7 @@ struct FftArgs<float> {
     __host__ __device__ static const float2* tw(const Launch& L) { return L.tw32; }
     __host__ __device__ static const float* ksq(const Launch& L) { return L.ksq32; }
     __host__ __device__ static int tile(const Launch& L) { return L.tk32; }
+    __host__ __device__ static const FastDiv& tile_div(const Launch& L) { return L.plan.div_tk32; }
     static constexpr int tk = 16;
 };
 
@@ -261,6 +262,7 @@ __device__ __forceinline__ void xfwd_tile(const Launch& L, int bid) {
     T* Ar = reinterpret_cast<T*>(A);
     load_twiddles(s_tw, g_tw, n);
     const int line0 = bid * lpb;
+    const FastDiv nl{(unsigned)lpb, 0u, 0u};  // transforms per block (only the count is used)
     const long long sn = n, s2 = sn * sn;
 
     for (int c = 0; c < D; ++c) {
@@ -269,19 +271,20 @@ __device__ __forceinline__ void xfwd_tile(const Launch& L, int bid) {
         const T* L_c0 = INCR ? nullptr : Lam + (long long)(c * D + 0) * Vn;
         const T* L_c1 = INCR ? nullptr : Lam + (long long)(c * D + 1) * Vn;
         for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) {
-            const int l = idx / n;
+            const int l = (int)fdiv(idx, plan.div_n);
             const int x = idx - l * n;
             const int line = line0 + l;
             T r = T(0);
             if (line < nlines) {
-                const int y = line % n;
+                const int zq = (int)fdiv(line, plan.div_n);
+                const int y = line - zq * n;
                 const long long v = (long long)line * n + x;
                 const long long xp = v + (x + 1 == n ? 1 - n : 1), xm = v + (x == 0 ? n - 1 : -1);
                 const long long yp = v + (y + 1 == n ? (1 - n) * sn : sn), ym = v + (y == 0 ? (n - 1) * sn : -sn);
                 T q = (F_c0[xp] - F_c0[xm]) + (F_c1[yp] - F_c1[ym]);
                 if (!INCR) q -= ((L_c0[xp] - L_c0[xm]) + (L_c1[yp] - L_c1[ym])) * inv_rho;
                 if constexpr (D == 3) {
-                    const int z = line / n;
+                    const int z = zq;
                     const T* F_c2 = F + (long long)(c * D + 2) * Vn;
                     const long long zp = v + (z + 1 == n ? (1 - n) * s2 : s2);
                     const long long zm = v + (z == 0 ? (n - 1) * s2 : -s2);
@@ -296,10 +299,10 @@ __device__ __forceinline__ void xfwd_tile(const Launch& L, int bid) {
             Ar[idx] = r;
         }
         __syncthreads();
-        V* X = stockham<false, false>(A, B, s_tw, H, plan.rad_half, plan.np_half, 2, lpb, H, 1);
+        V* X = stockham<false, false>(A, B, s_tw, plan.rad_half, plan.pass_half, plan.np_half, nl, H, 1);
         V* S_c = S + (long long)c * (Vn / 2);
         for (int idx = threadIdx.x; idx < lpb * H; idx += blockDim.x) {
-            const int l = idx / H;
+            const int l = (int)fdiv(idx, plan.div_h);
             const int kk = idx - l * H;
             const int line = line0 + l;
             if (line >= nlines) continue;
@@ -352,10 +355,11 @@ __device__ __forceinline__ void xinv_tile(const Launch& L, int bid) {
     load_twiddles(s_tw, g_tw, n);
     __syncthreads();
     const int line0 = bid * lpb;
+    const FastDiv nl{(unsigned)lpb, 0u, 0u};  // transforms per block (only the count is used)
     for (int c = 0; c < D; ++c) {
         V* S_c = S + (long long)c * (Vn / 2);
         for (int idx = threadIdx.x; idx < lpb * H; idx += blockDim.x) {
-            const int l = idx / H;
+            const int l = (int)fdiv(idx, plan.div_h);
             const int kk = idx - l * H;
             const int line = line0 + l;
             V Z = V{T(0), T(0)};
@@ -373,12 +377,12 @@ __device__ __forceinline__ void xinv_tile(const Launch& L, int bid) {
             A[idx] = Z;
         }
         __syncthreads();
-        V* X = stockham<true, false>(A, B, s_tw, H, plan.rad_half, plan.np_half, 2, lpb, H, 1);
+        V* X = stockham<true, false>(A, B, s_tw, plan.rad_half, plan.pass_half, plan.np_half, nl, H, 1);
         const T* Xr = reinterpret_cast<const T*>(X);
         TO* O_c = Out + (long long)c * Vn;
         const TO* I_c = In + (long long)c * Vn;
         for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) {
-            const int l = idx / n;
+            const int l = (int)fdiv(idx, plan.div_n);
             const int line = line0 + l;
             if (line < nlines) {
                 const long long o = (long long)line * n + (idx - l * n);
@@ -409,6 +413,7 @@ __device__ __forceinline__ void faxis_tile(const Launch& L, int bid) {
     const T* __restrict__ ksq = Args::ksq(L);
     const FftPlan& plan = L.plan;
     const int tk = Args::tile(L);
+    const FastDiv& dtk = Args::tile_div(L);
     const T scale = (T)(2.0 / (double)L.V);
     if (ctrl->done) return;
     const int n = plan.n, H = n / 2;
@@ -437,20 +442,20 @@ __device__ __forceinline__ void faxis_tile(const Launch& L, int bid) {
         es_g = H;
     }
     for (int idx = threadIdx.x; idx < n * tk; idx += blockDim.x) {
-        const int e = idx / tk;
+        const int e = (int)fdiv(idx, dtk);
         const int cl = idx - e * tk;
         X[idx] = (col0 + cl < H) ? S[base + e * es_g + cl] : V{T(0), T(0)};
     }
     __syncthreads();
     V* R;
     if (MODE == 1) {
-        R = stockham<true, true>(X, Y, s_tw, n, plan.rad_full, plan.np_full, 1, tk, 1, tk);
+        R = stockham<true, true>(X, Y, s_tw, plan.rad_full, plan.pass_full, plan.np_full, dtk, 1, tk);
     } else {
-        R = stockham<false, true>(X, Y, s_tw, n, plan.rad_full, plan.np_full, 1, tk, 1, tk);
+        R = stockham<false, true>(X, Y, s_tw, plan.rad_full, plan.pass_full, plan.np_full, dtk, 1, tk);
         if (MODE == 2) {
             const T kout = (D == 3) ? __ldg(ksq + outer) : T(0);
             for (int idx = threadIdx.x; idx < n * tk; idx += blockDim.x) {
-                const int e = idx / tk;
+                const int e = (int)fdiv(idx, dtk);
                 const int col = col0 + idx - e * tk;
                 const T den = __ldg(ksq + e) + __ldg(ksq + min(col, H - 1)) + kout;
                 const T m = den > T(0) ? scale / den : T(0);
@@ -458,11 +463,11 @@ __device__ __forceinline__ void faxis_tile(const Launch& L, int bid) {
             }
             __syncthreads();
             V* other = (R == X) ? Y : X;
-            R = stockham<true, true>(R, other, s_tw, n, plan.rad_full, plan.np_full, 1, tk, 1, tk);
+            R = stockham<true, true>(R, other, s_tw, plan.rad_full, plan.pass_full, plan.np_full, dtk, 1, tk);
         }
     }
     for (int idx = threadIdx.x; idx < n * tk; idx += blockDim.x) {
-        const int e = idx / tk;
+        const int e = (int)fdiv(idx, dtk);
         const int cl = idx - e * tk;
         if (col0 + cl < H) S[base + e * es_g + cl] = R[idx];
     }
@@ -639,6 +644,24 @@ void apply_geometry(Launch& L, const Geometry& g) {
         L.plan.rad_half[i] = i < g.np_half ? g.rad_half[i] : 0;
         L.plan.rad_full[i] = i < g.np_full ? g.rad_full[i] : 0;
     }
+    // per-pass divisors; the twiddle table has N entries, so a transform of
+    // length Lt = N / twmul steps through it with stride twmul Lt / (Ns R) = N / (Ns R)
+    auto passes = [n](int Lt, const int* rad, int np, FftPass* out) {
+        int Ns = 1;
+        for (int p = 0; p < kMaxPasses; ++p) {
+            const int R = p < np ? rad[p] : 1;
+            out[p].nb = make_fastdiv((unsigned)(Lt / R));
+            out[p].ns = make_fastdiv((unsigned)Ns);
+            out[p].tstep = n / (Ns * R);
+            if (p < np) Ns *= R;
+        }
+    };
+    passes(n / 2, L.plan.rad_half, g.np_half, L.plan.pass_half);
+    passes(n, L.plan.rad_full, g.np_full, L.plan.pass_full);
+    L.plan.div_n = make_fastdiv((unsigned)n);
+    L.plan.div_h = make_fastdiv((unsigned)(n / 2));
+    L.plan.div_tk64 = make_fastdiv((unsigned)L.tk64);
+    L.plan.div_tk32 = make_fastdiv((unsigned)L.tk32);
 }
 
 void set_geometry(Launch& L) {

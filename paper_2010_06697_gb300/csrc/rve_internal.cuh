@@ -48,13 +48,45 @@ struct Ctrl {
     unsigned int counter2;// last-block counter of the stress kernel
 };
 
+// Division by a divisor d >= 1 fixed at plan time, for dividends below 2^31:
+// floor(q / d) = (2q * m) >> (32 + l) with l = ceil(log2 d) and the rounded-up
+// reciprocal m = ceil(2^(31+l) / d) < 2^32 (Granlund & Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994).  With m d = 2^(31+l) + e,
+// 0 <= e < d <= 2^l, the product overshoots q / d by q e / (d 2^(31+l)) < 1 / d,
+// which never reaches the next integer.  One multiply-high and two shifts
+// instead of the integer divide sequence.
+struct FastDiv {
+    unsigned d, m, l;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+    unsigned l = 0;
+    while ((1ull << l) < d) ++l;
+    const unsigned long long num = 1ull << (31 + l);
+    return FastDiv{d, (unsigned)((num + d - 1) / d), l};
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned fdiv(unsigned q, const FastDiv& f) { return __umulhi(q << 1, f.m) >> f.l; }
+#endif
+
+// One Stockham pass: butterflies per transform nb = L / R, span Ns of the radices
+// already applied, and the twiddle stride N / (Ns R) into the table exp(-2 pi i m / N).
+struct FftPass {
+    FastDiv nb, ns;
+    int tstep;
+};
+
 // Stockham plan for one grid size: radix sequences for the half-length x
-// transform (N/2) and the full-length y/z transforms (N).
+// transform (N/2) and the full-length y/z transforms (N), with the divisors the
+// kernels' index arithmetic needs.
 struct FftPlan {
     int n;
     int np_half, np_full;
     int rad_half[kMaxPasses];
     int rad_full[kMaxPasses];
+    FftPass pass_half[kMaxPasses];
+    FftPass pass_full[kMaxPasses];
+    FastDiv div_n, div_h;      // N, N/2
+    FastDiv div_tk64, div_tk32; // y/z tile widths
 };
 
 // Everything the kernels need about one RVE.  A copy lives in device memory (the

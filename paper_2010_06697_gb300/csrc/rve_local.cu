@@ -622,15 +622,16 @@ struct Nbr {
 };
 
 template <int D>
-__device__ __forceinline__ Nbr<D> neighbours(int v, int n) {
+__device__ __forceinline__ Nbr<D> neighbours(int v, const FastDiv& dn) {
     Nbr<D> o;
-    const unsigned un = (unsigned)n;
-    const unsigned r = (unsigned)v / un;
+    const int n = (int)dn.d;
+    const unsigned un = dn.d;
+    const unsigned r = fdiv((unsigned)v, dn);
     const int x = v - (int)(r * un);
     o.xp = v + (x + 1 == n ? 1 - n : 1);
     o.xm = v + (x == 0 ? n - 1 : -1);
     if constexpr (D == 3) {
-        const unsigned zq = r / un;
+        const unsigned zq = fdiv(r, dn);
         const int y = (int)(r - zq * un);
         const int z = (int)zq;
         o.yp = v + (y + 1 == n ? (1 - n) * n : n);
@@ -820,8 +821,9 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     double rp2 = 0.0, rd2 = 0.0;
     int nmax = 0, nfail = 0;
     const int chunk = L.local_chunk;
+    const FastDiv dn = L.plan.div_n;
     for (long long v = bid * (long long)chunk + threadIdx.x; threadIdx.x < chunk && v < V; v += (long long)nblk * chunk) {
-        const Nbr<D> nb = neighbours<D>((int)v, n);
+        const Nbr<D> nb = neighbours<D>((int)v, dn);
         T G[NN], L[NN], F[NN];
         grad_u<T, D>(Unew, V, nb, Fb, half_n, G);
 #pragma unroll
