@@ -60,12 +60,11 @@ __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float log_t(float x) { return logf(x); }
 __device__ __forceinline__ double log_t(double x) { return log(x); }
 
-// Solve H x = -g for symmetric positive definite H given in packed lower storage
-// (row p, column q <= p at p(p+1)/2 + q).  H is overwritten by its Cholesky
-// factor.  Returns false when a pivot is not positive.
+// Cholesky factor of a symmetric positive definite H in packed lower storage
+// (row p, column q <= p at p(p+1)/2 + q), in place, with the reciprocal pivots in
+// inv.  Returns false when a pivot is not positive.
 template <typename T, int N>
-__device__ __forceinline__ bool chol_solve(T* H, const T* g, T* x) {
-    T inv[N];
+__device__ __forceinline__ bool chol_factor(T* H, T* inv) {
 #pragma unroll
     for (int p = 0; p < N; ++p) {
 #pragma unroll
@@ -83,6 +82,12 @@ __device__ __forceinline__ bool chol_solve(T* H, const T* g, T* x) {
             }
         }
     }
+    return true;
+}
+
+// x = -H^{-1} g from the factor of chol_factor (forward, then back substitution).
+template <typename T, int N>
+__device__ __forceinline__ void chol_subst(const T* H, const T* inv, const T* g, T* x) {
     T y[N];
 #pragma unroll
     for (int p = 0; p < N; ++p) {
@@ -98,6 +103,14 @@ __device__ __forceinline__ bool chol_solve(T* H, const T* g, T* x) {
         for (int r = p + 1; r < N; ++r) s -= H[r * (r + 1) / 2 + p] * x[r];
         x[p] = s * inv[p];
     }
+}
+
+// Solve H x = -g; H is overwritten by its Cholesky factor.
+template <typename T, int N>
+__device__ __forceinline__ bool chol_solve(T* H, const T* g, T* x) {
+    T inv[N];
+    if (!chol_factor<T, N>(H, inv)) return false;
+    chol_subst<T, N>(H, inv, g, x);
     return true;
 }
 
@@ -105,36 +118,38 @@ __device__ __forceinline__ bool chol_solve(T* H, const T* g, T* x) {
 // Each law gives, for the local objective phi(F) = W(F) + rho/2 |F|^2 - B : F
 // (B = Lambda + rho G; the constant rho/2 |G|^2 is dropped):
 //   grad:   g = W_F(F) + rho F - B in the field precision T, plus the auxiliary
-//           values (A = F^{-T}, J) the Hessian needs
+//           values the Hessian needs (law-specific)
 //   hess:   the packed Hessian W_FF + rho I, always in float (see newton())
 //   phi:    the objective (line search);  stress: W_F(F)
 
 // Compressible neo-Hookean, Section 4.1: W = mu/2 (|F|^2 - d - 2 ln J) + lam/2 (J-1)^2.
 // W_F = mu F + c F^{-T}, c = lam J (J-1) - mu;
 // W_FF[ij,kl] = mu d_ik d_jl + lam (2J-1) J A_ij A_kl - c A_il A_kj, A = F^{-T}.
+// The auxiliary values are the cofactor matrix K = J F^{-T} and J; the gradient
+// uses c / J times K, and the float side forms A = K / J itself.
 template <typename T, int D>
 struct NeoHooke {
     T mu, lam;
     static constexpr int NAUX = D * D + 1;
     __device__ __forceinline__ bool grad(const T* F, const T* B, T rho, T* g, T* aux) const {
         constexpr int NN = D * D;
-        T* A = aux;
-        const T J = det_cof<T, D>(F, A);
+        T* K = aux;
+        const T J = det_cof<T, D>(F, K);
         aux[NN] = J;
         if (!(J > T(0))) return false;
-        const T iJ = T(1) / J;
-#pragma unroll
-        for (int p = 0; p < NN; ++p) A[p] *= iJ;
-        const T c = lam * J * (J - T(1)) - mu;
+        const T cJ = (lam * J * (J - T(1)) - mu) / J;
         const T a = mu + rho;
 #pragma unroll
-        for (int p = 0; p < NN; ++p) g[p] = a * F[p] + c * A[p] - B[p];
+        for (int p = 0; p < NN; ++p) g[p] = a * F[p] + cJ * K[p] - B[p];
         return true;
     }
     __device__ __forceinline__ void hess(const float* aux, float rho, float* H) const {
         constexpr int NN = D * D;
-        const float* A = aux;
         const float J = aux[NN];
+        const float iJ = 1.f / J;
+        float A[NN];
+#pragma unroll
+        for (int p = 0; p < NN; ++p) A[p] = aux[p] * iJ;
         const float fm = (float)mu, fl = (float)lam;
         const float c = fl * J * (J - 1.f) - fm;
         const float b = fl * (2.f * J - 1.f) * J;
@@ -169,12 +184,16 @@ struct NeoHooke {
         for (int p = 0; p < D * D; ++p) P[p] = mu * F[p] + c * A[p];
     }
     __device__ __forceinline__ T modulus() const { return mu; }
-    // det(F + dF) > 0 is certain when |F^{-1} dF| < 1/2: |F^{-1} dF|_2 <= |A|_F * d * max|dF|
-    __device__ __forceinline__ bool small_step_safe(const float* aux, float size) const {
+    // det(F + dF) > 0 is certain when |F^{-1} dF| < 1/2: |F^{-1} dF|_2 <= |A|_F * d * max|dF|;
+    // safety_scale is |A|_F = |K|_F / J, and a step is safe when d * size * scale < 1/2
+    __device__ __forceinline__ float safety_scale(const float* aux) const {
         float a2 = 0.f;
 #pragma unroll
         for (int p = 0; p < D * D; ++p) a2 += aux[p] * aux[p];
-        return (float)D * size * sqrtf(a2) < 0.5f;
+        return sqrtf(a2) / aux[D * D];
+    }
+    __device__ __forceinline__ bool small_step_safe(const float* aux, float size) const {
+        return (float)D * size * safety_scale(aux) < 0.5f;
     }
 };
 
@@ -240,6 +259,7 @@ struct Linear {
     __device__ __forceinline__ T modulus() const { return mu; }
     // no positivity requirement on J for linear elasticity, but J > 0 is kept like
     // for the other laws: small steps from a state with J > 0 are accepted directly
+    __device__ __forceinline__ float safety_scale(const float*) const { return 0.f; }
     __device__ __forceinline__ bool small_step_safe(const float*, float size) const { return size < 1e-2f; }
 };
 
@@ -358,6 +378,82 @@ __device__ __forceinline__ int newton(const Law& m, T* F, const T* B, T rho, int
         if (t == T(0)) break;
     }
     return it;
+}
+
+// The rare branch of newton_incr (large or unsafe first step): the general Newton
+// from F_{k+1}.  (Kept inline: an out-of-line call makes the compiler spill its
+// array arguments to the stack on every voxel.)
+template <int D, typename Law>
+__device__ __forceinline__ int polish_general(const Law& m, double* F, const double* Bm, double rho, int cap,
+                                           double tol, bool& conv, float* eR, const double* __restrict__ Fstart,
+                                           long long V) {
+    constexpr int NN = D * D;
+    double B[NN];
+#pragma unroll
+    for (int p = 0; p < NN; ++p) B[p] = Bm[p] + rho * F[p];
+    const int it = newton<double, D>(m, F, B, rho, cap, tol, conv);
+#pragma unroll
+    for (int p = 0; p < NN; ++p) eR[p] = (float)((F[p] - Fstart[p * V]) - (double)eR[p]);
+    return it;
+}
+
+// Local step of the double polish in increment form.  On entry F = F_{k+1},
+// Bm = Lambda_{k+1} + rho e and eR = e = G_{k+1} - F_{k+1} (float).  With
+// G = F_{k+1} + e the gradient of phi is W_F(F) + rho (F - F_{k+1}) - Bm, so at
+// the start it is W_F(F) - Bm: neither G nor B = Lambda + rho G is formed in
+// double.
+//
+// The polish takes ONE refinement step per iteration (double gradient, float
+// Hessian factor) whenever that step is a safe full step (no line search, J stays
+// positive): F becomes F_{k+1} + dF and R = F_{k+2} - G_{k+1} = dF - e is formed
+// in float.  The local problem is then solved inexactly, with a gradient left of
+// about eps_float cond(H) |g| + c |dF|^2; in the polish |g| and |dF| are of the
+// order of the ADMM residuals themselves, so that error is many orders below
+// them and is corrected by the next iteration's step, which starts from this F
+// (the inexact local solves of Sections 2.1 and 4.2, r_l << r_d).  A fixed point
+// still has an exactly stationary local problem: the step from it is zero only
+// where the double gradient vanishes.  Otherwise (large or unsafe step, failed
+// factorisation) the general Newton runs to the tolerance from F_{k+1}
+// (polish_general).  On exit eR holds R.
+template <int D, typename Law>
+__device__ __forceinline__ int newton_incr(const Law& m, double* F, const double* Bm, double rho, int cap,
+                                           double tol, bool& conv, float* eR, const double* __restrict__ Fstart,
+                                           long long V) {
+    constexpr int NN = D * D;
+    constexpr int NP = NN * (NN + 1) / 2;
+    constexpr int NAUX = Law::NAUX;
+    {
+        double g[NN], aux[NAUX];
+        if (m.grad(F, Bm, 0.0, g, aux)) {
+            float af[NAUX], gf[NN], df[NN];
+            bool ok;
+            {
+                float Hf[NP];
+#pragma unroll
+                for (int p = 0; p < NAUX; ++p) af[p] = (float)aux[p];
+#pragma unroll
+                for (int p = 0; p < NN; ++p) gf[p] = (float)g[p];
+                m.hess(af, (float)rho, Hf);
+                ok = chol_solve<float, NN>(Hf, gf, df);
+            }
+            float slope = 0.f, size = 0.f;
+#pragma unroll
+            for (int p = 0; p < NN; ++p) {
+                slope += gf[p] * df[p];
+                size = fmaxf(size, fabsf(df[p]));
+            }
+            if (ok && slope < 0.f && size <= NewtonConst<float>::big && m.small_step_safe(af, size)) {
+#pragma unroll
+                for (int p = 0; p < NN; ++p) {
+                    F[p] += (double)df[p];
+                    eR[p] = df[p] - eR[p];
+                }
+                conv = true;
+                return 1;
+            }
+        }
+    }
+    return polish_general<D>(m, F, Bm, rho, cap, tol, conv, eR, Fstart, V);
 }
 
 // ------------------------------------------------------------------ liquid crystal elastomer
@@ -762,13 +858,19 @@ k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const 
 //
 // DU (same polish, after its first iteration): the float increment
 // u~_{k+1} - u~_k written by the increment projection is read instead of u~_k,
-// and G_{k+1} - G_k = D(u~_{k+1} - u~_k) for r_d is formed in float.
+// and G_{k+1} - G_k = D(u~_{k+1} - u~_k) for r_d is formed in float.  For the
+// elastic laws this iteration runs in increment form (INC): with R_k =
+// F_{k+1} - G_k from the previous iteration, e = G_{k+1} - F_{k+1} =
+// D(u~_{k+1} - u~_k) - R_k is a float difference of small quantities, so r_p,
+// the multiplier update Lambda += rho e and the local step (newton_incr) need
+// neither u~ nor G in double.  Float rounding of these small increments adds a
+// few ulp of the residual level per iteration.
 // One tile = block `bid` of the RVE's local grid (L.local_blocks blocks).  FIRST
 // is a run-time flag (not a template parameter) so that the local step compiles
 // to one instruction sequence for both entry paths: a solve resumed from a saved
 // state then reproduces the uninterrupted run bit for bit.
 template <typename T, int D, int MODEL, bool WRITE_R, bool DU>
-__device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool FIRST, int only_if_rho_changed) {
+__device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool FIRST_ARG, int only_if_rho_changed) {
     constexpr int NN = D * D;
     Ctrl* __restrict__ ctrl = L.ctrl;
     double* __restrict__ hist = L.hist;
@@ -791,6 +893,10 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     __shared__ int s_int[kLocalThreads / 32][2];
     __shared__ int s_last;
 
+    // the increment form needs the previous iteration's R: never the first step of a run
+    constexpr bool INC = WRITE_R && DU && MODEL != kLce && std::is_same<T, double>::value;
+    if (INC && FIRST_ARG) return;
+    const bool FIRST = INC ? false : FIRST_ARG;
     if (ctrl->done) return;
     if (FIRST && only_if_rho_changed && !ctrl->rho_changed) return;
     const long long k = ctrl->k;
@@ -825,13 +931,29 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     for (long long v = bid * (long long)chunk + threadIdx.x; threadIdx.x < chunk && v < V; v += (long long)nblk * chunk) {
         const Nbr<D> nb = neighbours<D>((int)v, dn);
         T G[NN], L[NN], F[NN];
-        grad_u<T, D>(Unew, V, nb, Fb, half_n, G);
+        float e[NN];  // INC: G_{k+1} - F_{k+1}, then R_{k+1}
+        if constexpr (!INC) grad_u<T, D>(Unew, V, nb, Fb, half_n, G);
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
             L[p] = Lam[p * V + v];
             F[p] = Fcur[p * V + v];
         }
-        if (!FIRST) {
+        if constexpr (INC) {
+            const float zero[NN] = {};
+            float dG[NN];
+            grad_u<float, D>(DUin, V, nb, zero, 0.5f * (float)n, dG);
+            float spf = 0.f, sdf = 0.f;
+#pragma unroll
+            for (int p = 0; p < NN; ++p) {
+                e[p] = dG[p] - Rout[p * V + v];
+                L[p] += rho * (T)e[p];
+                Lam[p * V + v] = L[p];
+                spf += e[p] * e[p];
+                sdf += dG[p] * dG[p];
+            }
+            rp2 += (double)spf;
+            rd2 += (double)sdf;
+        } else if (!FIRST) {
             // squares are summed per voxel in T (9 terms) and the voxel sums in double
             T sp = T(0), sd = T(0);
 #pragma unroll
@@ -861,12 +983,21 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             rp2 += (double)sp;
             rd2 += (double)sd;
         }
-        T B[NN];
-#pragma unroll
-        for (int p = 0; p < NN; ++p) B[p] = L[p] + rho * G[p];
         bool conv;
         int it;
-        if constexpr (MODEL == kLce) {
+        T B[NN];
+        if constexpr (INC) {
+#pragma unroll
+            for (int p = 0; p < NN; ++p) B[p] = L[p] + rho * (T)e[p];
+        } else {
+#pragma unroll
+            for (int p = 0; p < NN; ++p) B[p] = L[p] + rho * G[p];
+        }
+        if constexpr (INC) {
+            using Law = typename LawOf<T, D, MODEL>::type;
+            const Law m = load_law<Law, T>(phase, mat, nparam, v);
+            it = newton_incr<D>(m, F, B, rho, cap, ntol, conv, e, Fcur + v, V);
+        } else if constexpr (MODEL == kLce) {
             // director of the current iterate (same parity as F) and the explicit Frank force
             const T* nCur = FIRST ? (par ? dir.N1 : dir.N0) : (par ? dir.N0 : dir.N1);
             T* nNext = FIRST ? (par ? dir.N0 : dir.N1) : (par ? dir.N1 : dir.N0);
@@ -891,7 +1022,10 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
         nfail += conv ? 0 : 1;
 #pragma unroll
         for (int p = 0; p < NN; ++p) Fnext[p * V + v] = F[p];
-        if constexpr (WRITE_R) {
+        if constexpr (INC) {
+#pragma unroll
+            for (int p = 0; p < NN; ++p) Rout[p * V + v] = e[p];
+        } else if constexpr (WRITE_R) {
 #pragma unroll
             for (int p = 0; p < NN; ++p) Rout[p * V + v] = (float)(F[p] - G[p]);
         }
@@ -1017,8 +1151,15 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
 }
 
 
+// Resident blocks per SM the register budget is cut for: the float elastic laws
+// are latency-bound at fewer.
+template <typename T, int MODEL>
+constexpr int local_min_blocks() {
+    return (MODEL != kLce && sizeof(T) == 4) ? 4 : 1;
+}
+
 template <typename T, int D, int MODEL, bool WRITE_R, bool DU>
-__global__ void __launch_bounds__(kLocalThreads, (sizeof(T) == 4 && MODEL != kLce) ? 4 : 1)
+__global__ void __launch_bounds__(kLocalThreads, local_min_blocks<T, MODEL>())
 k_local(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles, int first,
         int only_if_rho_changed) {
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -1150,14 +1291,21 @@ cudaError_t run_local(const Exec& E, bool first, bool only_if, int mode) {
         const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, nt);
         kern<<<grid, kLocalThreads, 0, E.stream>>>(E.rds, tl, nt, is_first, flag);
     };
-    if (first)
+    if (first) {
         go(k_local<T, D, MODEL, false, false>, 1, only_if ? 1 : 0);
-    else if (mode == 1 && std::is_same<T, double>::value)
-        go(k_local<T, D, MODEL, true, false>, 0, 0);
-    else if (mode == 2 && std::is_same<T, double>::value)
-        go(k_local<T, D, MODEL, true, true>, 0, 0);
-    else
-        go(k_local<T, D, MODEL, false, false>, 0, 0);
+        return cudaGetLastError();
+    }
+    if constexpr (std::is_same<T, double>::value) {
+        if (mode == 1) {
+            go(k_local<T, D, MODEL, true, false>, 0, 0);
+            return cudaGetLastError();
+        }
+        if (mode == 2) {
+            go(k_local<T, D, MODEL, true, true>, 0, 0);
+            return cudaGetLastError();
+        }
+    }
+    go(k_local<T, D, MODEL, false, false>, 0, 0);
     return cudaGetLastError();
 }
 
