@@ -84,6 +84,16 @@ typedef struct rve_options {
                            about 2e-7 on O(1) deformation gradients)               */
     int check_every;    /* host reads the device status every this many iterations */
     int use_graph;      /* 1: replay iteration chunks as a CUDA graph (default 1)  */
+    double local_ratio; /* f > 0: inexact local steps (Section 2.1, "Approximate
+                           solution of the local problem"; Section 4.2 adopts
+                           r_l <= f r_d with f = 0.3).  Each voxel's Newton stops
+                           once |grad phi|_F <= f mu_ref r_d, r_d of the last
+                           check complete when the local step starts (two checks
+                           back: the device fuses Step 1 with the previous check);
+                           the first two local steps of a solve are exact.  The
+                           pointwise bound implies r_l <= f r_d.  Not applied to the
+                           increment-form steps of the RVE_MIXED polish.  Default 0
+                           (exact local solves).                                   */
 } rve_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -102,6 +112,10 @@ typedef struct rve_solve_info {
     long long newton_fail; /* voxels that hit newton_max in the last pass         */
     double time_ms;        /* device time of the iteration loop (CUDA events)    */
     long long launches;    /* kernel launches this solve issued (graph nodes too) */
+    double r_l;            /* local residual (Section 2.1) of the last fused
+                              pass's local step, |grad phi| at the step's result in
+                              the unit-cell L2 norm over mu_ref; 0 unless
+                              local_ratio > 0                                      */
 } rve_solve_info;
 
 typedef struct rve* rve_t;
@@ -169,6 +183,11 @@ int rve_reset(rve_t h);
 /* Residual history of the last solve: r_p, r_d and the rho used, per iteration
  * (up to cap entries).  Returns the number of entries written (>= 0) or an error. */
 int rve_history(rve_t h, double* r_p, double* r_d, double* rho, int cap);
+
+/* Local residual r_l of the same passes (local_ratio > 0, else zeros): entry i is
+ * the local step fused with check i, i.e. Step 1 of iteration i + 2 (iterations
+ * counted from 1).  Returns the number of entries written or an error. */
+int rve_history_local(rve_t h, double* r_l, int cap);
 
 /* ------------------------------------------------------------------ batches */
 typedef struct rve_batch* rve_batch_t;

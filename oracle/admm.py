@@ -123,7 +123,7 @@ def _to_field(Tv: np.ndarray, grid_shape) -> np.ndarray:
     return Tv.transpose(1, 2, 0).reshape((d, d) + tuple(grid_shape))
 
 
-def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, small_step=1e-7):
+def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, small_step=1e-7, grad_tol=0.0):
     """Step 1 at every voxel: minimise phi(F) = W(F) - Lam:F + rho/2 |F - G|^2.
 
     Damped Newton from F0 with the analytic Hessian W_FF + rho I.  When the Newton
@@ -133,6 +133,12 @@ def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, smal
     accepted on J > 0 alone, since phi's rounding noise exceeds the decrease there).
     A voxel stops after a full step with max |step| <= step_tol.
 
+    grad_tol > 0 (inexact local step, Section 2.1 "Approximate solution of the
+    local problem"): the gradient is evaluated at the start of every Newton
+    iteration and a voxel also stops, without a further step, once its Frobenius
+    norm |grad phi| <= grad_tol.  A voxel that met the step test is then stopped at
+    the next evaluation, so that every voxel ends on an evaluated gradient.
+
     All arrays are per voxel: F0, Lam, G of shape (V, d, d).  Returns (F, iters).
     """
     V, d, _ = F0.shape
@@ -140,12 +146,13 @@ def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, smal
     F = F0.copy()
     iters = np.zeros(V, dtype=np.int64)
     active = np.ones(V, dtype=bool)
+    small = np.zeros(V, dtype=bool)
 
     def phi(sub, Fs, Lam_s, G_s):
         return (sub.W(Fs) - np.einsum("vij,vij->v", Lam_s, Fs)
                 + 0.5 * rho * np.einsum("vij,vij->v", Fs - G_s, Fs - G_s))
 
-    for _ in range(cap):
+    for _ in range(cap + 1):
         idx = np.nonzero(active)[0]
         if idx.size == 0:
             break
@@ -154,6 +161,21 @@ def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, smal
         Lam_s = Lam[idx]
         G_s = G[idx]
         g = sub.P(Fa) - Lam_s + rho * (Fa - G_s)
+        if grad_tol > 0.0:
+            stop = small[idx] | (np.sqrt(np.einsum("vij,vij->v", g, g)) <= grad_tol)
+            active[idx[stop]] = False
+            keep = ~stop
+            idx, Fa, Lam_s, G_s, g = idx[keep], Fa[keep], Lam_s[keep], G_s[keep], g[keep]
+            if idx.size == 0:
+                break
+            sub = mat.subset(idx)
+        keep = iters[idx] < cap
+        if not np.all(keep):
+            active[idx[~keep]] = False
+            idx, Fa, Lam_s, G_s, g = idx[keep], Fa[keep], Lam_s[keep], G_s[keep], g[keep]
+            if idx.size == 0:
+                break
+            sub = mat.subset(idx)
         H = sub.C(Fa).reshape(-1, n2, n2) + rho * np.eye(n2)[None]
         delta = -np.linalg.solve(H, g.reshape(-1, n2, 1))[..., 0].reshape(-1, d, d)
         slope = np.einsum("vij,vij->v", g, delta)
@@ -182,8 +204,28 @@ def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, smal
         F[idx] = Fa + t[:, None, None] * delta
         iters[idx] += 1
         done = accepted & (t == 1.0) & (size <= step_tol)
-        active[idx[done]] = False
+        if grad_tol > 0.0:
+            small[idx[done]] = True
+        else:
+            active[idx[done]] = False
     return F, iters
+
+
+def local_residual(mat, F, Lam, G, rho, mu_ref, n=None, force=None):
+    """r_l of Section 2.1: the unit-cell L2 norm of the local optimality residual
+    grad phi = W_F(F) - Lam + rho (F - G) at the local step's result, over mu_ref
+    (read as a norm, like r_p and r_d).  For the LCE the two tangential components
+    of phi_n at the director are included.  Arguments per voxel, (V, d, d)."""
+    if n is None:
+        g = mat.P(F) - Lam + rho * (F - G)
+        s2 = np.einsum("vij,vij->v", g, g)
+    else:
+        P, Wn, _, _, _ = mat.derivatives(F, n)
+        gF = P - Lam + rho * (F - G)
+        gn = Wn - force
+        a, b = tangent_basis(n)
+        s2 = (np.einsum("vij,vij->v", gF, gF) + np.sum(gn * a, axis=1) ** 2 + np.sum(gn * b, axis=1) ** 2)
+    return float(np.sqrt(np.mean(s2))) / mu_ref
 
 
 # --------------------------------------------------------------------------- Step 1 for the LCE (F and director n)
@@ -225,7 +267,8 @@ def retract(n, a, b, t1, t2):
     return v / np.linalg.norm(v, axis=1)[:, None]
 
 
-def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60, armijo=1e-4, small_step=1e-7):
+def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60, armijo=1e-4, small_step=1e-7,
+                     grad_tol=0.0):
     """Step 1 (eqs. eq and kin with the Frank gradient treated explicitly, eq. kin2) for
     the LCE at every voxel: minimise over F and the unit director n
 
@@ -234,31 +277,46 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
     force: the explicit Frank force from the previous director field (frank_force).  Newton on the 11 unknowns (F, t) with n = normalise(n + t1 a + t2 b),
     (a, b) a basis of the tangent plane at the current n: the reduced Hessian adds the
     sphere's curvature term -(n . phi_n) I, plus a shift 1e-6 mu I on that block.  Backtracking keeps J > 0 and the Armijo
-    decrease; steepest descent when Newton's direction does not descend.
+    decrease; steepest descent when Newton's direction does not descend.  grad_tol:
+    the inexact stop of local_newton on the norm of the 11-component gradient.
     F0, Lam, G (V,3,3); n_init, force (V,3).  Returns (F, n, iters)."""
     V = F0.shape[0]
     F = F0.copy()
     n = n_init.copy()
     iters = np.zeros(V, dtype=np.int64)
     active = np.ones(V, dtype=bool)
+    small = np.zeros(V, dtype=bool)
 
     def phi(sub, Fs, ns, Lam_s, G_s, f_s):
         return (sub.W(Fs, ns) - np.sum(f_s * ns, axis=1) - np.einsum("vij,vij->v", Lam_s, Fs)
                 + 0.5 * rho * np.einsum("vij,vij->v", Fs - G_s, Fs - G_s))
 
-    for _ in range(cap):
+    for _ in range(cap + 1):
         idx = np.nonzero(active)[0]
         if idx.size == 0:
             break
-        sub = mat.subset(idx)
-        Fa, na = F[idx], n[idx]
-        Lam_s, G_s, f_s = Lam[idx], G[idx], force[idx]
-        P, Wn, WFF, WFn, Wnn = sub.derivatives(Fa, na)
-        gF = P - Lam_s + rho * (Fa - G_s)
-        gn = Wn - f_s
-        a, b = tangent_basis(na)
-        E = np.stack([a, b], axis=2)                                   # (v, 3, 2)
-        gt = np.einsum("vk,vka->va", gn, E)
+        for _pass in range(2):
+            sub = mat.subset(idx)
+            Fa, na = F[idx], n[idx]
+            Lam_s, G_s, f_s = Lam[idx], G[idx], force[idx]
+            P, Wn, WFF, WFn, Wnn = sub.derivatives(Fa, na)
+            gF = P - Lam_s + rho * (Fa - G_s)
+            gn = Wn - f_s
+            a, b = tangent_basis(na)
+            E = np.stack([a, b], axis=2)                                   # (v, 3, 2)
+            gt = np.einsum("vk,vka->va", gn, E)
+            stop = iters[idx] >= cap
+            if grad_tol > 0.0:
+                gnorm = np.sqrt(np.einsum("vij,vij->v", gF, gF) + np.sum(gt * gt, axis=1))
+                stop = stop | small[idx] | (gnorm <= grad_tol)
+            if not np.any(stop):
+                break
+            active[idx[stop]] = False
+            idx = idx[~stop]
+            if idx.size == 0:
+                break
+        if idx.size == 0:
+            break
         Htt = np.einsum("vka,vkp,vpb->vab", E, Wnn, E) - np.sum(na * gn, axis=1)[:, None, None] * np.eye(2)[None]
         HFt = np.einsum("vklp,vpb->vklb", WFn, E).reshape(-1, 9, 2)
         H = np.zeros((idx.size, 11, 11))
@@ -298,7 +356,10 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
         n[idx] = retract(na, a, b, t * delta[:, 9], t * delta[:, 10])
         iters[idx] += 1
         done = accepted & (t == 1.0) & (size <= step_tol)
-        active[idx[done]] = False
+        if grad_tol > 0.0:
+            small[idx[done]] = True
+        else:
+            active[idx[done]] = False
     return F, n, iters
 
 
@@ -339,13 +400,20 @@ def initial_state(mat, Fbar_d: np.ndarray, grid_shape, lambda0: str = "stress", 
 
 def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_ref=None,
                lambda0="stress", state=None, rho_policy="fixed", kappa=1.3, tau=10.0,
-               rho_min=None, local_cap=50, step_tol=1e-10, n0=None):
+               rho_min=None, local_cap=50, step_tol=1e-10, n0=None, local_ratio=0.0):
     """Run the ADMM iteration (Steps 1-4) until r_p <= tol and r_d <= tol, or max_iter.
 
     phase: uint8 grid (N,)*d; params: per-phase (mu, lam); Fbar: 3x3 (the upper-left
     d x d block is used).  Returns a dict with F, Lam, u (final state), iters,
     converged, history (list of (r_p, r_d, rho_used)), rho (next rho) and the
     homogenised first Piola-Kirchhoff stress <W_F(F)> (d x d).
+
+    local_ratio = f > 0: inexact local steps (Section 2.1, "Approximate solution of
+    the local problem", and Section 4.2's second strategy, r_l <= f r_d): each
+    voxel's Newton stops once |grad phi| <= f mu_ref r_d, with r_d of the check two
+    iterations back (the last one complete when a fused device pass starts its
+    local step); the first two iterations solve exactly.  A pointwise bound implies
+    the L2 bound r_l <= f r_d.  out["local_residual"] lists r_l per iteration.
     """
     phase = np.asarray(phase)
     d = phase.ndim
@@ -365,18 +433,22 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
     nd = st.get("n")
     G = Fbar_d.reshape((d, d) + (1,) * d) + grad_u(u)
     history = []
+    local_res = []
     converged = False
     it = 0
     for it in range(1, max_iter + 1):
-        # Step 1
+        # Step 1 (inexact when local_ratio > 0: tolerance from r_d two checks back)
+        gtol = local_ratio * mu_ref * history[-2][1] if (local_ratio > 0.0 and len(history) >= 2) else 0.0
+        Lv, Gv = _to_voxels(Lam), _to_voxels(G)
         if lce:
             force = frank_force(nd, mat.kappa)
-            Fv, nv, _ = local_newton_lce(mat, _to_voxels(F), nd.reshape(3, -1).T, _to_voxels(Lam),
-                                         _to_voxels(G), force, rho, step_tol=step_tol, cap=local_cap)
+            Fv, nv, _ = local_newton_lce(mat, _to_voxels(F), nd.reshape(3, -1).T, Lv, Gv, force, rho,
+                                         step_tol=step_tol, cap=local_cap, grad_tol=gtol)
             nd = nv.T.reshape((3,) + tuple(grid))
+            local_res.append(local_residual(mat, Fv, Lv, Gv, rho, mu_ref, nv, force) if local_ratio > 0.0 else 0.0)
         else:
-            Fv, _ = local_newton(mat, _to_voxels(F), _to_voxels(Lam), _to_voxels(G), rho,
-                                 step_tol=step_tol, cap=local_cap)
+            Fv, _ = local_newton(mat, _to_voxels(F), Lv, Gv, rho, step_tol=step_tol, cap=local_cap, grad_tol=gtol)
+            local_res.append(local_residual(mat, Fv, Lv, Gv, rho, mu_ref) if local_ratio > 0.0 else 0.0)
         F = _to_field(Fv, grid)
         # Step 2
         uh, u = u_step(F, Lam, rho)
@@ -404,7 +476,7 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
         stress = np.mean(mat.P(_to_voxels(F)), axis=0)
     out = {"F": F, "Lam": Lam, "u": u, "iters": it if max_iter > 0 else 0,
            "converged": converged, "history": history, "rho": rho,
-           "stress": stress, "mu_ref": mu_ref}
+           "stress": stress, "mu_ref": mu_ref, "local_residual": local_res}
     if lce:
         out["n"] = nd
     return out

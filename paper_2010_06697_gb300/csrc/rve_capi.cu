@@ -101,7 +101,7 @@ Layout layout(int dim, int n, int model, int precision, int max_iter) {
         return at;
     };
     o.ctrl = take(sizeof(Ctrl));
-    o.hist = take(sizeof(double) * 3 * (size_t)(max_iter + 1));
+    o.hist = take(sizeof(double) * admm::kHistStride * (size_t)(max_iter + 1));
     o.partials = take(sizeof(double) * admm::kPartialStride * (size_t)g.local_blocks);
     o.desc = take(sizeof(Launch));
     o.tiles[admm::kTilesLocal] = take(sizeof(int2) * (size_t)admm::tiles_local(g));
@@ -212,6 +212,10 @@ int begin_solve(rve* h, const double Fbar[9], double rho, double tol, cudaStream
     c.rho_changed = 0;
     c.newton_cap = o.newton_max;
     c.hist_cap = o.max_iter + 1;
+    c.local_ratio = o.local_ratio;
+    c.r_d = 0.0;  // no check yet: the first two local steps of the solve are exact
+    c.rd_local = 0.0;
+    c.r_l = 0.0;
     c.counter = 0;
     c.counter2 = 0;
     c.newton_max = 0;
@@ -271,6 +275,7 @@ void fill_info(rve* h, long long k0, int fp64_iters, double ms, rve_solve_info* 
     info->status = status;
     info->r_p = e.r_p;
     info->r_d = e.r_d;
+    info->r_l = e.r_l;
     info->rho = e.rho;
     info->mu_ref = e.mu_ref;
     info->newton_max_iters = e.newton_max;
@@ -468,6 +473,7 @@ int check_options(const rve_options& o) {
     if (!(o.newton_tol >= 0) || !(o.rho_kappa > 1) || !(o.rho_tau > 1) || !(o.rho_min >= 0)) return RVE_E_INVALID_ARG;
     if (!(o.mu_ref >= 0) || !(o.mixed_switch >= 0)) return RVE_E_INVALID_ARG;
     if (o.check_every < 1 || o.check_every > 4096) return RVE_E_INVALID_ARG;
+    if (!(o.local_ratio >= 0) || !(o.local_ratio <= 1e6)) return RVE_E_INVALID_ARG;
     return RVE_OK;
 }
 
@@ -617,6 +623,7 @@ void rve_default_options(rve_options* o) {
     o->mixed_switch = 3e-7;
     o->check_every = 16;
     o->use_graph = 1;
+    o->local_ratio = 0.0;
 }
 
 size_t rve_workspace_bytes(int dim, int n, int model, const rve_options* opt) {
@@ -843,15 +850,30 @@ int rve_history(rve_t h, double* rp, double* rd, double* rho, int cap) {
     int cnt = h->last_iters < cap ? h->last_iters : cap;
     if (cnt > h->opt.max_iter + 1) cnt = h->opt.max_iter + 1;
     if (cnt <= 0) return 0;
-    std::vector<double> tmp(3 * (size_t)cnt);
+    constexpr int S = admm::kHistStride;
+    std::vector<double> tmp(S * (size_t)cnt);
     if (enter(h)) return RVE_E_CUDA;
     CK(cudaMemcpyAsync(tmp.data(), h->L.hist, tmp.size() * 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     for (int i = 0; i < cnt; ++i) {
-        if (rp) rp[i] = tmp[3 * i];
-        if (rd) rd[i] = tmp[3 * i + 1];
-        if (rho) rho[i] = tmp[3 * i + 2];
+        if (rp) rp[i] = tmp[S * i];
+        if (rd) rd[i] = tmp[S * i + 1];
+        if (rho) rho[i] = tmp[S * i + 2];
     }
+    return cnt;
+}
+
+int rve_history_local(rve_t h, double* r_l, int cap) {
+    if (!h || !r_l || cap < 0) return RVE_E_INVALID_ARG;
+    int cnt = h->last_iters < cap ? h->last_iters : cap;
+    if (cnt > h->opt.max_iter + 1) cnt = h->opt.max_iter + 1;
+    if (cnt <= 0) return 0;
+    constexpr int S = admm::kHistStride;
+    std::vector<double> tmp(S * (size_t)cnt);
+    if (enter(h)) return RVE_E_CUDA;
+    CK(cudaMemcpyAsync(tmp.data(), h->L.hist, tmp.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < cnt; ++i) r_l[i] = tmp[S * i + 3];
     return cnt;
 }
 

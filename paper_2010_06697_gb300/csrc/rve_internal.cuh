@@ -10,7 +10,10 @@ constexpr int kMaxPasses = 16;
 constexpr int kLocalThreads = 128;    // threads per block of the local-step kernels
 constexpr int kFftThreads = 256;      // threads per block of the FFT kernels
 constexpr int kMaxParam = 8;          // per-phase material constants
-constexpr int kPartialStride = 20;    // doubles per block in the partial-sum buffer
+constexpr int kPartialStride = 20;
+// residual history entry per iteration: r_p, r_d, rho of the check, then r_l of the
+// local step fused into the same pass (the next iteration's Step 1)
+constexpr int kHistStride = 4;    // doubles per block in the partial-sum buffer
 
 enum Done : int { kRunning = 0, kConverged = 1, kCapped = 2, kNumerical = 3, kSwitch = 4 };
 enum Model : int { kNeoHooke = 0, kLinear = 1, kLce = 2 };
@@ -29,6 +32,9 @@ struct Ctrl {
     double switch_tol;   // float phase of mixed mode: promote once max(r_p, r_d) <= this
     double best;         // best max(r_p, r_d) of the float phase (stagnation test)
     double r_p, r_d;     // residuals of the last completed iteration
+    double local_ratio;  // f > 0: inexact local steps, |grad phi| <= f mu_ref r_d per voxel
+    double rd_local;     // r_d of the check before the last one (the redone local step's)
+    double r_l;          // local residual of the last fused pass's local step (f > 0 only)
     double stress[9];    // <W_F(F)> of the current state (written by the stress kernel)
     double lam_mean[9];  // <Lambda>
     long long k;         // iterations completed over the handle's life: F_k, u~_k live in buffer k & 1

@@ -302,15 +302,27 @@ struct NewtonConst<float> { static constexpr float big = 1e-2f; };
 // max|dF| <= tol.  Returns the number of Newton steps; conv tells whether the
 // test was met.
 template <typename T, int D, typename Law>
-__device__ __forceinline__ int newton(const Law& m, T* F, const T* B, T rho, int cap, T tol, bool& conv) {
+__device__ __forceinline__ int newton(const Law& m, T* F, const T* B, T rho, int cap, T tol, bool& conv,
+                                      T gtol = T(0), T* gnorm2 = nullptr) {
     constexpr int NN = D * D;
     constexpr int NP = NN * (NN + 1) / 2;
     constexpr int NAUX = Law::NAUX;
     conv = false;
     int it = 0;
-    while (it < cap) {
+    bool small = false;  // gtol > 0: the step test was met; stop at the next gradient
+    while (it < cap || small) {
         T g[NN], aux[NAUX];
         if (!m.grad(F, B, rho, g, aux)) break;
+        if (gtol > T(0)) {
+            T s2 = T(0);
+#pragma unroll
+            for (int p = 0; p < NN; ++p) s2 += g[p] * g[p];
+            *gnorm2 = s2;
+            if (small || s2 <= gtol * gtol) {
+                conv = true;
+                break;
+            }
+        }
         float df[NN], gf[NN], af[NAUX];
         {
             float Hf[NP];
@@ -372,6 +384,10 @@ __device__ __forceinline__ int newton(const Law& m, T* F, const T* B, T rho, int
         for (int p = 0; p < NN; ++p) F[p] += t * (T)df[p];
         ++it;
         if (t == T(1) && size <= (float)tol) {
+            if (gtol > T(0)) {
+                small = true;
+                continue;
+            }
             conv = true;
             break;
         }
@@ -562,12 +578,13 @@ __device__ __forceinline__ void retract(const T* n, const T* ta, const T* tb, T 
 // newton().
 template <typename T>
 __device__ __forceinline__ int newton_lce(const Lce<T>& m, T* F, T* n, const T* B, const T* f, T rho, int cap, T tol,
-                                          bool& conv) {
+                                          bool& conv, T gtol = T(0), T* gnorm2 = nullptr) {
     constexpr int NU = 11;
     constexpr int NP = NU * (NU + 1) / 2;
     conv = false;
     int it = 0;
-    while (it < cap) {
+    bool small = false;  // as in newton()
+    while (it < cap || small) {
         T A[9], mm[3], Mm[3], g[NU], ta[3], tb[3];
         const T J = det_cof<T, 3>(F, A);
         if (!(J > T(0))) break;
@@ -590,6 +607,16 @@ __device__ __forceinline__ int newton_lce(const Lce<T>& m, T* F, T* n, const T* 
         g[9] = ta[0] * gn[0] + ta[1] * gn[1] + ta[2] * gn[2];
         g[10] = tb[0] * gn[0] + tb[1] * gn[1] + tb[2] * gn[2];
         const T ngn = n[0] * gn[0] + n[1] * gn[1] + n[2] * gn[2];
+        if (gtol > T(0)) {
+            T s2 = T(0);
+#pragma unroll
+            for (int p = 0; p < NU; ++p) s2 += g[p] * g[p];
+            *gnorm2 = s2;
+            if (small || s2 <= gtol * gtol) {
+                conv = true;
+                break;
+            }
+        }
 
         float d[NU], gf[NU];
 #pragma unroll
@@ -699,6 +726,10 @@ __device__ __forceinline__ int newton_lce(const Lce<T>& m, T* F, T* n, const T* 
         for (int i = 0; i < 3; ++i) n[i] = nt[i];
         ++it;
         if (t == T(1) && size <= (float)tol) {
+            if (gtol > T(0)) {
+                small = true;
+                continue;
+            }
             conv = true;
             break;
         }
@@ -889,7 +920,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     const float* __restrict__ DUin = L.D32;
     const Dirs<T> dir = Set<T>::dirs(L);
     const int nblk = L.local_blocks;
-    __shared__ double s_sum[kLocalThreads / 32][2];
+    __shared__ double s_sum[kLocalThreads / 32][3];
     __shared__ int s_int[kLocalThreads / 32][2];
     __shared__ int s_last;
 
@@ -918,13 +949,18 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     const T half_n = (T)(0.5 * n);
     const int cap = ctrl->newton_cap;
     const T ntol = (T)ctrl->newton_tol;
+    // inexact local steps (Section 2.1): |grad phi| <= f mu_ref r_d, with r_d of the
+    // last completed check (a redone step uses the same value as the pass it
+    // replaces); the first local step of a solve is exact
+    const double rd_use = FIRST ? (only_if_rho_changed ? ctrl->rd_local : 0.0) : ctrl->r_d;
+    const T gtol = INC ? T(0) : (T)(ctrl->local_ratio * ctrl->mu_ref * rd_use);
     T Fb[NN];
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
         for (int j = 0; j < D; ++j) Fb[i * D + j] = (T)ctrl->Fbar[i * 3 + j];
 
-    double rp2 = 0.0, rd2 = 0.0;
+    double rp2 = 0.0, rd2 = 0.0, rl2 = 0.0;
     int nmax = 0, nfail = 0;
     const int chunk = L.local_chunk;
     const FastDiv dn = L.plan.div_n;
@@ -1010,13 +1046,17 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
                 fr[i] = kf * (c[nb.xp] + c[nb.xm] + c[nb.yp] + c[nb.ym] + c[nb.zp] + c[nb.zm]);
             }
             const Lce<T> m = load_lce<T>(phase, mat, nparam, v, dir.ref, V);
-            it = newton_lce<T>(m, F, nv, B, fr, rho, cap, ntol, conv);
+            T gn2 = T(0);
+            it = newton_lce<T>(m, F, nv, B, fr, rho, cap, ntol, conv, gtol, &gn2);
+            rl2 += (double)gn2;
 #pragma unroll
             for (int i = 0; i < 3; ++i) nNext[i * V + v] = nv[i];
         } else {
             using Law = typename LawOf<T, D, MODEL>::type;
             const Law m = load_law<Law, T>(phase, mat, nparam, v);
-            it = newton<T, D>(m, F, B, rho, cap, ntol, conv);
+            T gn2 = T(0);
+            it = newton<T, D>(m, F, B, rho, cap, ntol, conv, gtol, &gn2);
+            rl2 += (double)gn2;
         }
         nmax = max(nmax, it);
         nfail += conv ? 0 : 1;
@@ -1036,21 +1076,24 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     rp2 = warp_sum(rp2);
     rd2 = warp_sum(rd2);
+    rl2 = warp_sum(rl2);
     nmax = warp_max(nmax);
     for (int o = 16; o > 0; o >>= 1) nfail += __shfl_down_sync(0xffffffffu, nfail, o);
     if (lane == 0) {
         s_sum[warp][0] = rp2;
         s_sum[warp][1] = rd2;
+        s_sum[warp][2] = rl2;
         s_int[warp][0] = nmax;
         s_int[warp][1] = nfail;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0, b = 0;
+        double a = 0, b = 0, cl = 0;
         int mx = 0, nf = 0;
         for (int w = 0; w < kLocalThreads / 32; ++w) {
             a += s_sum[w][0];
             b += s_sum[w][1];
+            cl += s_sum[w][2];
             mx = max(mx, s_int[w][0]);
             nf += s_int[w][1];
         }
@@ -1059,6 +1102,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
         pp[1] = b;
         pp[2] = (double)mx;
         pp[3] = (double)nf;
+        pp[4] = cl;
         __threadfence();
         const unsigned prev = atomicAdd(&ctrl->counter, 1u);
         s_last = (prev == nblk - 1);
@@ -1068,7 +1112,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     __threadfence();
 
     // last block: fixed-order sum over all block partials
-    double a = 0, b = 0;
+    double a = 0, b = 0, cl = 0;
     int mx = 0;
     double nf = 0;
     for (int i = threadIdx.x; i < (int)nblk; i += blockDim.x) {
@@ -1077,14 +1121,17 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
         b += __ldcg(pp + 1);
         mx = max(mx, (int)__ldcg(pp + 2));
         nf += __ldcg(pp + 3);
+        cl += __ldcg(pp + 4);
     }
     a = warp_sum(a);
     b = warp_sum(b);
+    cl = warp_sum(cl);
     nf = warp_sum(nf);
     mx = warp_max(mx);
     if (lane == 0) {
         s_sum[warp][0] = a;
         s_sum[warp][1] = b;
+        s_sum[warp][2] = cl;
         s_int[warp][0] = mx;
         s_int[warp][1] = (int)nf;
     }
@@ -1092,11 +1139,13 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     if (threadIdx.x != 0) return;
     a = 0;
     b = 0;
+    cl = 0;
     mx = 0;
     long long nft = 0;
     for (int w = 0; w < kLocalThreads / 32; ++w) {
         a += s_sum[w][0];
         b += s_sum[w][1];
+        cl += s_sum[w][2];
         mx = max(mx, s_int[w][0]);
         nft += s_int[w][1];
     }
@@ -1105,13 +1154,17 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     const double r_p = sqrt(a / (double)V);
     const double r_d = rhod / c->mu_ref * sqrt(b / (double)V);
     const long long idx = k - c->k_start;
+    const double r_l = sqrt(cl / (double)V) / c->mu_ref;
     if (idx >= 0 && idx < c->hist_cap) {
-        hist[3 * idx + 0] = r_p;
-        hist[3 * idx + 1] = r_d;
-        hist[3 * idx + 2] = rhod;
+        hist[kHistStride * idx + 0] = r_p;
+        hist[kHistStride * idx + 1] = r_d;
+        hist[kHistStride * idx + 2] = rhod;
+        hist[kHistStride * idx + 3] = r_l;
     }
     c->r_p = r_p;
+    c->rd_local = c->r_d;
     c->r_d = r_d;
+    c->r_l = r_l;
     c->k = k + 1;
     c->newton_max = mx;
     c->newton_fail = (unsigned long long)nft;

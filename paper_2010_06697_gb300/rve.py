@@ -55,6 +55,7 @@ class rve_options(ctypes.Structure):
         ("mixed_switch", ctypes.c_double),
         ("check_every", ctypes.c_int),
         ("use_graph", ctypes.c_int),
+        ("local_ratio", ctypes.c_double),
     ]
 
 
@@ -72,6 +73,7 @@ class rve_solve_info(ctypes.Structure):
         ("newton_fail", ctypes.c_longlong),
         ("time_ms", ctypes.c_double),
         ("launches", ctypes.c_longlong),
+        ("r_l", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -98,6 +100,7 @@ SIGNATURES = {
     "rve_set_field": (_I, [_VP, _I, _PD]),
     "rve_reset": (_I, [_VP]),
     "rve_history": (_I, [_VP, _PD, _PD, _PD, _I]),
+    "rve_history_local": (_I, [_VP, _PD, _I]),
     "rve_strerror": (ctypes.c_char_p, [_I]),
     "rve_set_profiling": (_I, [_VP, _I]),
     "rve_stress_noalloc": (_I, [_I, _I, _I, _VP, _VP, _VP, _I, _I, _VP, _VP]),
@@ -240,6 +243,14 @@ def rve_history(h, cap):
     if cnt < 0:
         return cnt, None
     return cnt, np.stack([rp[:cnt], rd[:cnt], rho[:cnt]], axis=1)
+
+
+def rve_history_local(h, cap):
+    rl = np.zeros(cap)
+    cnt = lib().rve_history_local(h, _dptr(rl), cap)
+    if cnt < 0:
+        return cnt, None
+    return cnt, rl[:cnt]
 
 
 def rve_stress_noalloc(dim, n, model, F_ptr, phase_ptr, params_ptr, nphase, nparam, S_ptr, stream=None):
@@ -498,6 +509,13 @@ class Rve:
         if cnt < 0:
             raise RveError(cnt, "rve_history")
         return hst
+
+    def history_local(self, cap=None):
+        """r_l of the local step fused with each check (entry i: Step 1 of iteration i + 2)."""
+        cnt, rl = rve_history_local(self.h, cap or (self.opt.max_iter + 1))
+        if cnt < 0:
+            raise RveError(cnt, "rve_history_local")
+        return rl
 
     def set_profiling(self, on):
         _check(rve_set_profiling(self.h, on), "rve_set_profiling")

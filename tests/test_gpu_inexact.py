@@ -1,0 +1,99 @@
+"""Inexact local steps (rve_options.local_ratio, Section 2.1 and Section 4.2's
+r_l <= f r_d) on the GPU vs the FP64 oracle with the same rule.
+
+A voxel whose gradient norm sits within rounding of the tolerance may take one
+Newton step more or less on one side, so iterates are compared with a tolerance
+that such a step allows; converged stresses are compared to the solve tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_06697_gb300 import build, rve, synth
+
+pytestmark = pytest.mark.gpu
+PAR = synth.two_phase_params(1.0, 10.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    rve.lib()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+def solve(ph, Fbar, tol, max_iter, precision="fp64", model="neohookean", par=PAR, n0=None, **opt):
+    s = rve.Rve(ph.ndim, ph.shape[0], model, precision, max_iter=max_iter, **opt)
+    s.set_material(ph, par, n0)
+    return s, s.solve(Fbar, 10.0, tol)
+
+
+@pytest.mark.parametrize("d,n", [(3, 16), (2, 48)])
+def test_inexact_fp64_matches_oracle(d, n):
+    f = 0.3
+    ph = synth.inclusion_phase(n, d, 2, radius=max(2, n // 6))
+    Fbar = np.diag([0.92, 1.0, 1.03])
+    s, info = solve(ph, Fbar, 1e-9, 600, local_ratio=f)
+    ref = oracle.admm_solve(ph, PAR, Fbar, 10.0, 1e-9, 600, local_ratio=f)
+    assert info.converged and ref["converged"]
+    assert abs(info.iterations - ref["iters"]) <= 2
+    assert rel(s.stress(), ref["stress"]) < 1e-8
+    st = s.state()
+    assert rel(st["F"], ref["F"]) < 1e-7
+    # residual histories follow the oracle's over the first iterations
+    h = s.history()
+    href = np.array(ref["history"])
+    m = min(len(h), len(href), 20)
+    np.testing.assert_allclose(h[:m, :2], href[:m, :2], rtol=1e-4, atol=1e-12)
+    # r_l: entry i is Step 1 of iteration i + 2; bounded by f r_d two checks back
+    rl = s.history_local()
+    rl_ref = np.array(ref["local_residual"])
+    np.testing.assert_allclose(rl[:m - 1], rl_ref[1:m], rtol=1e-3, atol=1e-11)
+    assert np.all(rl[1:len(h) - 1] <= f * h[:len(h) - 2, 1] * (1 + 1e-9))
+    assert info.r_l == pytest.approx(rl[len(h) - 1], rel=1e-12, abs=1e-300)
+
+
+def test_inexact_exact_first_steps_and_zero_ratio_unchanged():
+    """local_ratio = 0 reproduces the exact-local run bit for bit (the gradient test
+    is off), and the relaxed run differs only after its first two local steps."""
+    n = 12
+    ph = synth.inclusion_phase(n, 3, 4, radius=2)
+    Fbar = np.diag([0.95, 1.0, 1.0])
+    s0, _ = solve(ph, Fbar, -1.0, 5)
+    s1, _ = solve(ph, Fbar, -1.0, 5, local_ratio=0.0)
+    for k in ("F", "Lam", "u"):
+        assert np.array_equal(s0.state()[k], s1.state()[k])
+    s2, _ = solve(ph, Fbar, -1.0, 2, local_ratio=0.5)
+    s3, _ = solve(ph, Fbar, -1.0, 2)
+    assert rel(s2.state()["F"], s3.state()["F"]) < 1e-13
+
+
+def test_inexact_mixed_converges_to_exact_solution():
+    """Mixed precision with r_l <= 0.3 r_d on a 32^3 inclusion cell: the double
+    polish still reaches the exact solve's stress."""
+    n = 32
+    ph = synth.inclusion_phase(n, 3, 0)
+    Fbar = np.diag([0.9, 1.0, 1.0])
+    s_ex, i_ex = solve(ph, Fbar, 1e-8, 1000, precision="fp64")
+    s_in, i_in = solve(ph, Fbar, 1e-8, 1000, precision="mixed", local_ratio=0.3)
+    assert i_ex.converged and i_in.converged
+    assert rel(s_in.stress(), s_ex.stress()) < 1e-7
+
+
+def test_inexact_lce_matches_oracle():
+    """LCE cell, fixed iteration count: the inexact rule on the 11-unknown local
+    problem (F and the director's tangent coordinates)."""
+    n = 12
+    ph = np.zeros((n,) * 3, np.uint8)
+    n0 = synth.director_grf(n, 7, corr=2.5)
+    par = np.array([[1.0, 20.0, 7.71, 0.06, (2.0 / n) ** 2]])
+    Fbar = np.diag([1.2, 0.91, 0.91])
+    s, info = solve(ph, Fbar, -1.0, 12, model="lce", par=par, n0=n0, local_ratio=0.3)
+    ref = oracle.admm_solve(ph, par, Fbar, 10.0, -1.0, 12, model="lce", n0=n0, local_ratio=0.3)
+    st = s.state()
+    assert rel(st["F"], ref["F"]) < 1e-6
+    assert np.max(np.abs(st["n"] - ref["n"])) < 1e-6
+    rl = s.history_local()
+    np.testing.assert_allclose(rl[:10], np.array(ref["local_residual"])[1:11], rtol=1e-3, atol=1e-11)
