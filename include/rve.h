@@ -164,6 +164,22 @@ int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* pa
  * RVE_E_CUDA. */
 int rve_solve(rve_t h, const double Fbar[9], double rho, double tol, rve_solve_info* info);
 
+/* Mixed macroscopic control (Section 2.3: some components of <F> prescribed, the
+ * complementary components of <S> zero; Section 5.3's UNI, PE and EB loadings).
+ * free_mask bit 3i+j set: <F_ij> is free, Fbar[3i+j] is only its starting value,
+ * and the solve drives <W_F(F)>_ij to 0 (to the residual tolerance); the other
+ * components of Fbar are prescribed.  The free components join Step 2: each
+ * iteration sets them to the mean of F - Lambda/rho (Du~ has zero mean), after
+ * which <Lambda>_ij = 0.  Bits outside the d x d block are RVE_E_INVALID_ARG.  A
+ * mask leaving both <F_ij> and <F_ji> free leaves a rigid rotation to the start
+ * value (W is frame-indifferent).  rve_solve is rve_solve_mixed with mask 0.
+ * Returns as rve_solve; rve_macro_gradient gives the resulting <F>. */
+int rve_solve_mixed(rve_t h, const double Fbar[9], unsigned free_mask, double rho, double tol,
+                    rve_solve_info* info);
+
+/* Current macroscopic gradient <F> (row-major 3x3; prescribed and free parts). */
+int rve_macro_gradient(rve_t h, double F[9]);
+
 /* Homogenised first Piola-Kirchhoff stress <W_F(F)> of the current state,
  * summed in double on the device (Section 2.3: <S> is the macroscopic stress). */
 int rve_stress(rve_t h, double S[9]);

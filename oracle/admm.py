@@ -400,7 +400,7 @@ def initial_state(mat, Fbar_d: np.ndarray, grid_shape, lambda0: str = "stress", 
 
 def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_ref=None,
                lambda0="stress", state=None, rho_policy="fixed", kappa=1.3, tau=10.0,
-               rho_min=None, local_cap=50, step_tol=1e-10, n0=None, local_ratio=0.0):
+               rho_min=None, local_cap=50, step_tol=1e-10, n0=None, local_ratio=0.0, free=None):
     """Run the ADMM iteration (Steps 1-4) until r_p <= tol and r_d <= tol, or max_iter.
 
     phase: uint8 grid (N,)*d; params: per-phase (mu, lam); Fbar: 3x3 (the upper-left
@@ -414,13 +414,21 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
     iterations back (the last one complete when a fused device pass starts its
     local step); the first two iterations solve exactly.  A pointwise bound implies
     the L2 bound r_l <= f r_d.  out["local_residual"] lists r_l per iteration.
+
+    free: optional (3, 3) boolean mask of components of <F> left free (mixed
+    macroscopic control, Section 2.3; Section 5.3's UNI, PE and EB protocols): they
+    join Step 2's minimisation, whose mean part gives <F>_free = <F - Lambda/rho>_free
+    (the fluctuation Du~ has zero mean), so that <Lambda>_free = 0 after every
+    multiplier update and <W_F(F)>_free -> 0 at convergence.  Fbar gives their
+    starting values; out["Fbar"] holds the final macroscopic gradient (3 x 3).
     """
     phase = np.asarray(phase)
     d = phase.ndim
     grid = phase.shape
     lce = model == "lce"
     mat = make_lce(phase, params, n0) if lce else make_material(model, phase, params)
-    Fbar_d = np.asarray(Fbar, dtype=np.float64)[:d, :d]
+    Fbar_d = np.array(np.asarray(Fbar, dtype=np.float64)[:d, :d])
+    free_d = None if free is None else np.asarray(free, dtype=bool)[:d, :d]
     if mu_ref is None:
         mu_ref = float(np.mean(mat.mu))
     if rho_min is None:
@@ -450,8 +458,11 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
             Fv, _ = local_newton(mat, _to_voxels(F), Lv, Gv, rho, step_tol=step_tol, cap=local_cap, grad_tol=gtol)
             local_res.append(local_residual(mat, Fv, Lv, Gv, rho, mu_ref) if local_ratio > 0.0 else 0.0)
         F = _to_field(Fv, grid)
-        # Step 2
+        # Step 2 (with the free mean components of mixed control)
         uh, u = u_step(F, Lam, rho)
+        if free_d is not None and free_d.any():
+            Qbar = np.mean((F - Lam / rho).reshape(d, d, -1), axis=2)
+            Fbar_d = np.where(free_d, Qbar, Fbar_d)
         G_new = Fbar_d.reshape((d, d) + (1,) * d) + grad_from_spectrum(uh)
         # Step 3
         Lam = multiplier_update(Lam, G_new, F, rho)
@@ -477,6 +488,9 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
     out = {"F": F, "Lam": Lam, "u": u, "iters": it if max_iter > 0 else 0,
            "converged": converged, "history": history, "rho": rho,
            "stress": stress, "mu_ref": mu_ref, "local_residual": local_res}
+    Fb3 = np.array(np.asarray(Fbar, dtype=np.float64))
+    Fb3[:d, :d] = Fbar_d
+    out["Fbar"] = Fb3
     if lce:
         out["n"] = nd
     return out

@@ -49,6 +49,8 @@ struct rve {
     double mu_ref = 1.0;
     int nphase = 0;
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // float, double, double polish
+    unsigned free_mask = 0;    // mixed control of the solve in progress (bit 3i+j: <F_ij> free)
+    bool graph_free = false;   // the cached graphs contain the mixed-control kernel
     long long k = 0;        // host copy of Ctrl::k
     int last_iters = 0;
     long long launches = 0; // kernel launches issued by the running solve
@@ -194,7 +196,8 @@ int begin_solve(rve* h, const double Fbar[9], double rho, double tol, cudaStream
     int rc = read_ctrl_on(h, st);
     if (rc) return rc;
     Ctrl& c = *h->hctrl;
-    for (int i = 0; i < 9; ++i) c.Fbar[i] = Fbar[i];
+    for (int i = 0; i < 9; ++i) c.Fbar[i] = c.Fbar_prev[i] = Fbar[i];
+    c.free_mask = h->free_mask;
     c.rho = rho;
     c.inv_rho = 1.0 / rho;
     c.mu_ref = o.mu_ref > 0 ? o.mu_ref : h->mu_ref;
@@ -298,7 +301,12 @@ int fft_class(int dim, int s) {
 }
 
 int launches_per_iteration(const rve* h) {
-    return admm::fft_stages(h->dim) + 1 + (h->opt.rho_policy == RVE_RHO_ADAPTIVE ? 1 : 0);
+    return admm::fft_stages(h->dim) + 1 + (h->opt.rho_policy == RVE_RHO_ADAPTIVE ? 1 : 0) + (h->free_mask ? 1 : 0);
+}
+
+// Mixed control: the free components of <F> for the coming projection (no-op without).
+cudaError_t macro_step(rve* h, bool fp64) {
+    return h->free_mask ? admm::launch_macro(h->L, fp64, h->stream) : cudaSuccess;
 }
 
 int ensure_prof_events(rve* h) {
@@ -327,6 +335,7 @@ int run_chunk_profiled(rve* h, bool fp64, bool incr) {
     const int f = fp64 ? 1 : 0;
     for (int i = 0; i < h->opt.check_every; ++i) {
         cudaEvent_t* e = &h->pev[(size_t)i * per];
+        if (macro_step(h, fp64) != cudaSuccess) return RVE_E_CUDA;
         CK(cudaEventRecord(e[0], h->stream));
         for (int st = 0; st < S; ++st) {
             const cudaError_t le = incr ? admm::launch_fft_incr(h->E, st) : admm::launch_fft(h->E, fp64, st);
@@ -367,7 +376,8 @@ int capture_chunk(rve* h, bool fp64, bool incr, int slot) {
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < h->opt.check_every && e == cudaSuccess; ++i) {
-        e = incr ? admm::launch_fft_incr(h->E) : admm::launch_fft(h->E, fp64);
+        e = macro_step(h, fp64);
+        if (e == cudaSuccess) e = incr ? admm::launch_fft_incr(h->E) : admm::launch_fft(h->E, fp64);
         if (e == cudaSuccess) e = admm::launch_local(h->E, fp64, false, false, incr ? 2 : 0);
         if (e == cudaSuccess && h->opt.rho_policy == RVE_RHO_ADAPTIVE) e = admm::launch_local(h->E, fp64, true, true);
     }
@@ -399,6 +409,7 @@ int run_phase(rve* h, bool fp64, bool polish = false) {
     }
     h->launches += 1;
     if (polish) {
+        if (macro_step(h, true) != cudaSuccess) return RVE_E_CUDA;
         if (admm::launch_fft(h->E, true) != cudaSuccess) return RVE_E_CUDA;
         if (admm::launch_local(h->E, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
         h->launches += admm::fft_stages(h->dim) + 1;
@@ -423,6 +434,7 @@ int run_phase(rve* h, bool fp64, bool polish = false) {
             CK(cudaGraphLaunch(h->graph[slot], h->stream));
         } else {
             for (int i = 0; i < h->opt.check_every; ++i) {
+                if (macro_step(h, fp64) != cudaSuccess) return RVE_E_CUDA;
                 const cudaError_t fe = polish ? admm::launch_fft_incr(h->E) : admm::launch_fft(h->E, fp64);
                 if (fe != cudaSuccess) return RVE_E_CUDA;
                 if (admm::launch_local(h->E, fp64, false, false, polish ? 2 : 0) != cudaSuccess) return RVE_E_CUDA;
@@ -603,6 +615,41 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
     return RVE_OK;
 }
 
+// The iteration loop of one solve (Algorithm 1 for one load step) with the mixed
+// control mask already in h->free_mask.
+int solve_body(rve* h, const double Fbar[9], double rho, double tol, rve_solve_info* info) {
+    int rc;
+    const rve_options& o = h->opt;
+    if (enter(h)) return RVE_E_CUDA;
+    h->launches = 0;
+    CK(cudaEventRecord(h->ev0, h->stream));
+    rc = begin_solve(h, Fbar, rho, tol, h->stream);
+    if (rc) return rc;
+    const bool fp32_first = o.precision != RVE_FP64;
+    const long long k0 = h->hctrl->k;
+    int fp64_iters = 0;
+    if (h->hctrl->done == admm::kRunning) {
+        rc = run_phase(h, !fp32_first);
+        if (rc) return rc;
+        if (o.precision == RVE_MIXED && h->hctrl->done == admm::kSwitch) {
+            const long long ksw = h->hctrl->k;
+            if (switch_to_double(h, h->stream)) return RVE_E_CUDA;
+            rc = run_phase(h, true, o.rho_policy == RVE_RHO_FIXED);
+            if (rc) return rc;
+            fp64_iters = (int)(h->hctrl->k - ksw);
+        } else if (o.precision == RVE_FP64) {
+            fp64_iters = (int)(h->hctrl->k - k0);
+        }
+    }
+    CK(cudaEventRecord(h->ev1, h->stream));
+    CK(cudaEventSynchronize(h->ev1));
+    if (read_ctrl(h)) return RVE_E_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    fill_info(h, k0, fp64_iters, ms, info);
+    return status_of(h->hctrl->done);
+}
+
 }  // namespace
 
 extern "C" {
@@ -725,37 +772,37 @@ int rve_reset(rve_t h) {
 }
 
 int rve_solve(rve_t h, const double Fbar[9], double rho, double tol, rve_solve_info* info) {
+    return rve_solve_mixed(h, Fbar, 0u, rho, tol, info);
+}
+
+int rve_solve_mixed(rve_t h, const double Fbar[9], unsigned free_mask, double rho, double tol,
+                    rve_solve_info* info) {
     int rc = check_solve_args(h, Fbar, rho, tol);
     if (rc) return rc;
-    const rve_options& o = h->opt;
-    if (enter(h)) return RVE_E_CUDA;
-    h->launches = 0;
-    CK(cudaEventRecord(h->ev0, h->stream));
-    rc = begin_solve(h, Fbar, rho, tol, h->stream);
-    if (rc) return rc;
-    const bool fp32_first = o.precision != RVE_FP64;
-    const long long k0 = h->hctrl->k;
-    int fp64_iters = 0;
-    if (h->hctrl->done == admm::kRunning) {
-        rc = run_phase(h, !fp32_first);
-        if (rc) return rc;
-        if (o.precision == RVE_MIXED && h->hctrl->done == admm::kSwitch) {
-            const long long ksw = h->hctrl->k;
-            if (switch_to_double(h, h->stream)) return RVE_E_CUDA;
-            rc = run_phase(h, true, o.rho_policy == RVE_RHO_FIXED);
-            if (rc) return rc;
-            fp64_iters = (int)(h->hctrl->k - ksw);
-        } else if (o.precision == RVE_FP64) {
-            fp64_iters = (int)(h->hctrl->k - k0);
-        }
+    unsigned allowed = 0;
+    for (int i = 0; i < h->dim; ++i)
+        for (int j = 0; j < h->dim; ++j) allowed |= 1u << (3 * i + j);
+    if (free_mask & ~allowed) return RVE_E_INVALID_ARG;
+    if ((free_mask != 0) != h->graph_free) {  // the cached iteration graphs change shape
+        for (int i = 0; i < 3; ++i)
+            if (h->graph[i]) {
+                cudaGraphExecDestroy(h->graph[i]);
+                h->graph[i] = nullptr;
+            }
+        h->graph_free = free_mask != 0;
     }
-    CK(cudaEventRecord(h->ev1, h->stream));
-    CK(cudaEventSynchronize(h->ev1));
+    h->free_mask = free_mask;
+    rc = solve_body(h, Fbar, rho, tol, info);
+    h->free_mask = 0;
+    return rc;
+}
+
+int rve_macro_gradient(rve_t h, double F[9]) {
+    if (!h || !F) return RVE_E_INVALID_ARG;
+    if (enter(h)) return RVE_E_CUDA;
     if (read_ctrl(h)) return RVE_E_CUDA;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-    fill_info(h, k0, fp64_iters, ms, info);
-    return status_of(h->hctrl->done);
+    for (int i = 0; i < 9; ++i) F[i] = h->hctrl->Fbar[i];
+    return RVE_OK;
 }
 
 int rve_stress(rve_t h, double S[9]) {

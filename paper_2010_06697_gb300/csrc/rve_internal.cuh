@@ -35,6 +35,8 @@ struct Ctrl {
     double local_ratio;  // f > 0: inexact local steps, |grad phi| <= f mu_ref r_d per voxel
     double rd_local;     // r_d of the check before the last one (the redone local step's)
     double r_l;          // local residual of the last fused pass's local step (f > 0 only)
+    double Fbar_prev[9]; // <F> of the previous iteration (r_d under mixed control)
+    unsigned free_mask;  // mixed control: bit 3i+j set = <F_ij> free, <S_ij> -> 0
     double stress[9];    // <W_F(F)> of the current state (written by the stress kernel)
     double lam_mean[9];  // <Lambda>
     long long k;         // iterations completed over the handle's life: F_k, u~_k live in buffer k & 1
@@ -186,6 +188,8 @@ cudaError_t launch_init(const Launch& L, bool fp64, bool lambda_zero);
 // r_d from the float u~ increment D32 (see local_tile).
 cudaError_t launch_local(const Exec& E, bool fp64, bool first, bool only_if_rho_changed, int polish_mode = 0);
 cudaError_t launch_stress(const Launch& L, bool fp64);
+// mixed macroscopic control: free components of <F> from the mean of F - Lambda/rho
+cudaError_t launch_macro(const Launch& L, bool fp64, cudaStream_t st);
 cudaError_t launch_convert(const Launch& L, bool to_fp64);
 // rve_fft.cu
 cudaError_t launch_fft(const Exec& E, bool fp64, int stage = -1);

@@ -954,11 +954,16 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     // replaces); the first local step of a solve is exact
     const double rd_use = FIRST ? (only_if_rho_changed ? ctrl->rd_local : 0.0) : ctrl->r_d;
     const T gtol = INC ? T(0) : (T)(ctrl->local_ratio * ctrl->mu_ref * rd_use);
-    T Fb[NN];
+    T Fb[NN], Fb_prev[NN];
+    float dFb[NN];  // <F>_{k+1} - <F>_k (nonzero only under mixed control)
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
-        for (int j = 0; j < D; ++j) Fb[i * D + j] = (T)ctrl->Fbar[i * 3 + j];
+        for (int j = 0; j < D; ++j) {
+            Fb[i * D + j] = (T)ctrl->Fbar[i * 3 + j];
+            Fb_prev[i * D + j] = (T)ctrl->Fbar_prev[i * 3 + j];
+            dFb[i * D + j] = (float)(ctrl->Fbar[i * 3 + j] - ctrl->Fbar_prev[i * 3 + j]);
+        }
 
     double rp2 = 0.0, rd2 = 0.0, rl2 = 0.0;
     int nmax = 0, nfail = 0;
@@ -975,9 +980,8 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             F[p] = Fcur[p * V + v];
         }
         if constexpr (INC) {
-            const float zero[NN] = {};
             float dG[NN];
-            grad_u<float, D>(DUin, V, nb, zero, 0.5f * (float)n, dG);
+            grad_u<float, D>(DUin, V, nb, dFb, 0.5f * (float)n, dG);
             float spf = 0.f, sdf = 0.f;
 #pragma unroll
             for (int p = 0; p < NN; ++p) {
@@ -1000,16 +1004,15 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
                 Lam[p * V + v] = L[p];
             }
             if constexpr (DU) {
-                const float zero[NN] = {};
                 float dG[NN];
-                grad_u<float, D>(DUin, V, nb, zero, 0.5f * (float)n, dG);
+                grad_u<float, D>(DUin, V, nb, dFb, 0.5f * (float)n, dG);
                 float sdf = 0.f;
 #pragma unroll
                 for (int p = 0; p < NN; ++p) sdf += dG[p] * dG[p];
                 sd = (T)sdf;
             } else {
                 T Go[NN];
-                grad_u<T, D>(Uold, V, nb, Fb, half_n, Go);
+                grad_u<T, D>(Uold, V, nb, Fb_prev, half_n, Go);
 #pragma unroll
                 for (int p = 0; p < NN; ++p) {
                     const T dg = G[p] - Go[p];
@@ -1222,6 +1225,80 @@ k_local(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntil
     }
 }
 
+// Mixed macroscopic control (Section 2.3; the UNI, PE and EB protocols of Section
+// 5.3).  The free components of <F> join Step 2's minimisation of
+// |<F> + D u~ - Q|^2, Q = F_{k+1} - Lambda_k / rho; D u~ has zero mean, so their
+// minimiser is <Q>.  Runs before the iteration's projection, with ctrl->k = k;
+// keeps the previous <F> for r_d.  Sums in double with the fixed-order scheme.
+template <typename T, int D>
+__global__ void __launch_bounds__(kLocalThreads)
+k_macro(Ctrl* __restrict__ ctrl, double* __restrict__ partials, const T* F0, const T* F1, const T* Lam,
+        long long V) {
+    constexpr int NN = D * D;
+    __shared__ double s_sum[kLocalThreads / 32][2 * NN];
+    __shared__ int s_last;
+    if (ctrl->done) return;
+    const T* F = (ctrl->k & 1) ? F0 : F1;  // F_{k+1}
+    double acc[2 * NN];
+#pragma unroll
+    for (int p = 0; p < 2 * NN; ++p) acc[p] = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            acc[p] += (double)F[p * V + v];
+            acc[NN + p] += (double)Lam[p * V + v];
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int p = 0; p < 2 * NN; ++p) {
+        const double s = warp_sum(acc[p]);
+        if (lane == 0) s_sum[warp][p] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double* pp = partials + (size_t)blockIdx.x * kPartialStride;
+        for (int p = 0; p < 2 * NN; ++p) {
+            double s = 0;
+            for (int w = 0; w < kLocalThreads / 32; ++w) s += s_sum[w][p];
+            pp[p] = s;
+        }
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctrl->counter2, 1u);
+        s_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int p = 0; p < 2 * NN; ++p) acc[p] = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        const double* pp = partials + (size_t)i * kPartialStride;
+#pragma unroll
+        for (int p = 0; p < 2 * NN; ++p) acc[p] += __ldcg(pp + p);
+    }
+#pragma unroll
+    for (int p = 0; p < 2 * NN; ++p) {
+        const double s = warp_sum(acc[p]);
+        if (lane == 0) s_sum[warp][p] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    Ctrl* c = ctrl;
+    for (int i = 0; i < 9; ++i) c->Fbar_prev[i] = c->Fbar[i];
+    for (int p = 0; p < NN; ++p) {
+        const int i = p / D, j = p % D;
+        if (!((c->free_mask >> (3 * i + j)) & 1u)) continue;
+        double sf = 0, sl = 0;
+        for (int w = 0; w < kLocalThreads / 32; ++w) {
+            sf += s_sum[w][p];
+            sl += s_sum[w][NN + p];
+        }
+        c->Fbar[3 * i + j] = sf / (double)V - (sl / (double)V) * c->inv_rho;
+    }
+    c->counter2 = 0u;
+}
+
 // <W_F(F_k)> and <Lambda_k>, summed in double with the same fixed-order scheme.
 template <typename T, int D, int MODEL>
 __global__ void __launch_bounds__(kLocalThreads)
@@ -1391,6 +1468,18 @@ cudaError_t launch_local(const Exec& E, bool fp64, bool first, bool only_if_rho_
     const Launch& L = *E.rep;
     if (fp64) RVE_DISPATCH(run_local, double, E, first, only_if_rho_changed, polish_mode);
     RVE_DISPATCH(run_local, float, E, first, only_if_rho_changed, 0);
+}
+
+cudaError_t launch_macro(const Launch& L, bool fp64, cudaStream_t st) {
+    auto go = [&](auto kern, const auto* F0, const auto* F1, const auto* Lm) {
+        kern<<<L.local_blocks, kLocalThreads, 0, st>>>(L.ctrl, L.partials, F0, F1, Lm, L.V);
+        return cudaGetLastError();
+    };
+    if (fp64)
+        return L.dim == 3 ? go(k_macro<double, 3>, L.F64[0], L.F64[1], L.L64)
+                          : go(k_macro<double, 2>, L.F64[0], L.F64[1], L.L64);
+    return L.dim == 3 ? go(k_macro<float, 3>, L.F32[0], L.F32[1], L.L32)
+                      : go(k_macro<float, 2>, L.F32[0], L.F32[1], L.L32);
 }
 
 cudaError_t launch_stress(const Launch& L, bool fp64) {

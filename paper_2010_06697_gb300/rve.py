@@ -101,6 +101,8 @@ SIGNATURES = {
     "rve_reset": (_I, [_VP]),
     "rve_history": (_I, [_VP, _PD, _PD, _PD, _I]),
     "rve_history_local": (_I, [_VP, _PD, _I]),
+    "rve_solve_mixed": (_I, [_VP, _PD, ctypes.c_uint, _D, _D, ctypes.POINTER(rve_solve_info)]),
+    "rve_macro_gradient": (_I, [_VP, _PD]),
     "rve_strerror": (ctypes.c_char_p, [_I]),
     "rve_set_profiling": (_I, [_VP, _I]),
     "rve_stress_noalloc": (_I, [_I, _I, _I, _VP, _VP, _VP, _I, _I, _VP, _VP]),
@@ -210,6 +212,25 @@ def rve_solve(h, Fbar, rho, tol):
     info = rve_solve_info()
     rc = lib().rve_solve(h, _dptr(fb), float(rho), float(tol), ctypes.byref(info))
     return rc, info
+
+
+def free_mask_bits(free):
+    """(3, 3) boolean array of free <F> components -> the bit mask of rve_solve_mixed."""
+    f = np.asarray(free, dtype=bool).reshape(3, 3)
+    return int(sum(1 << (3 * i + j) for i in range(3) for j in range(3) if f[i, j]))
+
+
+def rve_solve_mixed(h, Fbar, free, rho, tol):
+    fb = np.ascontiguousarray(np.asarray(Fbar, dtype=np.float64).reshape(3, 3))
+    info = rve_solve_info()
+    rc = lib().rve_solve_mixed(h, _dptr(fb), free_mask_bits(free), float(rho), float(tol), ctypes.byref(info))
+    return rc, info
+
+
+def rve_macro_gradient(h):
+    F = np.zeros(9)
+    rc = lib().rve_macro_gradient(h, _dptr(F))
+    return rc, F.reshape(3, 3)
 
 
 def rve_stress(h):
@@ -452,11 +473,20 @@ class Rve:
             raise ValueError(f"phase shape {ph.shape} != {self.grid}")
         _check(rve_set_material(self.h, ph, params, n0), "rve_set_material")
 
-    def solve(self, Fbar, rho, tol, check=False):
-        rc, info = rve_solve(self.h, Fbar, rho, tol)
+    def solve(self, Fbar, rho, tol, check=False, free=None):
+        """free: optional (3, 3) boolean mask of free <F> components (rve_solve_mixed)."""
+        if free is None:
+            rc, info = rve_solve(self.h, Fbar, rho, tol)
+        else:
+            rc, info = rve_solve_mixed(self.h, Fbar, free, rho, tol)
         if rc not in (RVE_OK, RVE_E_NOT_CONVERGED) or (check and rc != RVE_OK):
             raise RveError(rc, "rve_solve")
         return info
+
+    def macro_gradient(self):
+        rc, F = rve_macro_gradient(self.h)
+        _check(rc, "rve_macro_gradient")
+        return F
 
     def stress(self):
         rc, S = rve_stress(self.h)
