@@ -954,15 +954,18 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     // replaces); the first local step of a solve is exact
     const double rd_use = FIRST ? (only_if_rho_changed ? ctrl->rd_local : 0.0) : ctrl->r_d;
     const T gtol = INC ? T(0) : (T)(ctrl->local_ratio * ctrl->mu_ref * rd_use);
-    T Fb[NN], Fb_prev[NN];
-    float dFb[NN];  // <F>_{k+1} - <F>_k (nonzero only under mixed control)
+    // G_{k+1} - G_k = (<F>_{k+1} - <F>_k) + D(u~_{k+1} - u~_k); the uniform first
+    // term (nonzero only under mixed control) enters the voxel sums of r_d in closed
+    // form in the last block (D u~ sums to zero over the cell), except in the
+    // increment form, where it is part of e voxel by voxel
+    T Fb[NN];
+    float dFb[NN];
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             Fb[i * D + j] = (T)ctrl->Fbar[i * 3 + j];
-            Fb_prev[i * D + j] = (T)ctrl->Fbar_prev[i * 3 + j];
-            dFb[i * D + j] = (float)(ctrl->Fbar[i * 3 + j] - ctrl->Fbar_prev[i * 3 + j]);
+            dFb[i * D + j] = INC ? (float)(ctrl->Fbar[i * 3 + j] - ctrl->Fbar_prev[i * 3 + j]) : 0.f;
         }
 
     double rp2 = 0.0, rd2 = 0.0, rl2 = 0.0;
@@ -1004,15 +1007,16 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
                 Lam[p * V + v] = L[p];
             }
             if constexpr (DU) {
+                const float zero[NN] = {};
                 float dG[NN];
-                grad_u<float, D>(DUin, V, nb, dFb, 0.5f * (float)n, dG);
+                grad_u<float, D>(DUin, V, nb, zero, 0.5f * (float)n, dG);
                 float sdf = 0.f;
 #pragma unroll
                 for (int p = 0; p < NN; ++p) sdf += dG[p] * dG[p];
                 sd = (T)sdf;
             } else {
                 T Go[NN];
-                grad_u<T, D>(Uold, V, nb, Fb_prev, half_n, Go);
+                grad_u<T, D>(Uold, V, nb, Fb, half_n, Go);
 #pragma unroll
                 for (int p = 0; p < NN; ++p) {
                     const T dg = G[p] - Go[p];
@@ -1154,6 +1158,15 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     }
     Ctrl* c = ctrl;
     const double rhod = c->rho;
+    if (!INC) {
+        double dm = 0.0;  // |<F>_{k+1} - <F>_k|^2 (mixed control)
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) {
+                const double x = c->Fbar[i * 3 + j] - c->Fbar_prev[i * 3 + j];
+                dm += x * x;
+            }
+        b += dm * (double)V;
+    }
     const double r_p = sqrt(a / (double)V);
     const double r_d = rhod / c->mu_ref * sqrt(b / (double)V);
     const long long idx = k - c->k_start;
