@@ -76,7 +76,7 @@ bool valid_n(int n) {
 }
 
 struct Layout {
-    size_t ctrl, hist, partials, phase, mat, desc, tiles[admm::kTileClasses];
+    size_t ctrl, hist, partials, phase, mat, mat32, desc, tiles[admm::kTileClasses];
     size_t F64[2], L64, U64[2], tw64, ksq64, N64[2], n064;
     size_t F32[2], L32, U32[2], tw32, ksq32, N32[2], n032;
     size_t total;
@@ -112,6 +112,7 @@ Layout layout(int dim, int n, int model, int precision, int max_iter) {
     o.tiles[admm::kTilesAx32] = take(sizeof(int2) * (size_t)admm::tiles_ax(g, false));
     o.phase = take((size_t)V);
     o.mat = take(sizeof(double) * 256 * admm::kMaxParam);
+    o.mat32 = take(sizeof(float) * 256 * admm::kMaxParam);
     const bool need64 = precision != RVE_FP32;
     const bool need32 = precision != RVE_FP64;
     const bool lce = model == admm::kLce;
@@ -544,6 +545,7 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
     L.partials = (double*)(b + lay.partials);
     L.phase = (const uint8_t*)(b + lay.phase);
     L.mat = (const double*)(b + lay.mat);
+    L.mat32 = (const float*)(b + lay.mat32);
     L.nparam = 2;
     const bool lce = model == admm::kLce;
     if (o.precision != RVE_FP32) {
@@ -752,6 +754,9 @@ int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* pa
     if (enter(h)) return RVE_E_CUDA;
     CK(cudaMemcpyAsync((void*)h->L.phase, phase, (size_t)h->V, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync((void*)h->L.mat, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    std::vector<float> tab32(tab.begin(), tab.end());
+    CK(cudaMemcpyAsync((void*)h->L.mat32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice,
+                       h->stream));
     if (lce && h->L.n0_64)
         CK(cudaMemcpyAsync((void*)h->L.n0_64, n0, 3 * (size_t)h->V * 8, cudaMemcpyHostToDevice, h->stream));
     if (lce && h->L.n0_32)

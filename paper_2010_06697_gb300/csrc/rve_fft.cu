@@ -211,6 +211,8 @@ struct FftArgs<double> {
     __host__ __device__ static const double2* tw(const Launch& L) { return L.tw64; }
     __host__ __device__ static const double* ksq(const Launch& L) { return L.ksq64; }
     __host__ __device__ static int tile(const Launch& L) { return L.tk64; }
+    __host__ __device__ static double half_n(const Launch& L) { return L.half_n64; }
+    __host__ __device__ static double scale(const Launch& L) { return L.scale64; }
     __host__ __device__ static const FastDiv& tile_div(const Launch& L) { return L.plan.div_tk64; }
     static constexpr int tk = 8;
 };
@@ -222,6 +224,8 @@ struct FftArgs<float> {
     __host__ __device__ static const float2* tw(const Launch& L) { return L.tw32; }
     __host__ __device__ static const float* ksq(const Launch& L) { return L.ksq32; }
     __host__ __device__ static int tile(const Launch& L) { return L.tk32; }
+    __host__ __device__ static float half_n(const Launch& L) { return L.half_n32; }
+    __host__ __device__ static float scale(const Launch& L) { return L.scale32; }
     __host__ __device__ static const FastDiv& tile_div(const Launch& L) { return L.plan.div_tk32; }
     static constexpr int tk = 16;
 };
@@ -254,7 +258,7 @@ __device__ __forceinline__ void xfwd_tile(const Launch& L, int bid) {
     const T* __restrict__ F = par ? F0 : F1;  // F_{k+1}
     V* __restrict__ S = reinterpret_cast<V*>(par ? U0 : U1);
     const T inv_rho = (T)ctrl->inv_rho;
-    const T half_n = (T)(0.5 * n);
+    const T half_n = Args::half_n(L);
 
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* A = s_tw + n;
@@ -414,7 +418,7 @@ __device__ __forceinline__ void faxis_tile(const Launch& L, int bid) {
     const FftPlan& plan = L.plan;
     const int tk = Args::tile(L);
     const FastDiv& dtk = Args::tile_div(L);
-    const T scale = (T)(2.0 / (double)L.V);
+    const T scale = Args::scale(L);
     if (ctrl->done) return;
     const int n = plan.n, H = n / 2;
     const long long Vn = (D == 3) ? (long long)n * n * n : (long long)n * n;
@@ -665,6 +669,12 @@ void apply_geometry(Launch& L, const Geometry& g) {
 }
 
 void set_geometry(Launch& L) {
+    L.half_n64 = 0.5 * (double)L.n;
+    L.scale64 = 2.0 / (double)L.V;
+    L.two_nsq64 = 2.0 * (double)L.n * (double)L.n;
+    L.half_n32 = (float)L.half_n64;
+    L.scale32 = (float)L.scale64;
+    L.two_nsq32 = (float)L.two_nsq64;
     // voxels a local tile covers per sweep: a whole block of threads, or fewer for small
     // cells so that the local step still spreads over ~2 blocks per SM (a function of the
     // RVE's size only, so results do not depend on what else runs in the launch)

@@ -113,7 +113,12 @@ struct Launch {
     double* partials;      // kPartialStride doubles per local block
     const uint8_t* phase;
     const double* mat;     // per-phase constants, nparam each
+    const float* mat32;    // the same table in float (float kernels read no doubles)
     int nparam;
+    // grid constants in both precisions, so that no kernel converts them per element
+    // (conversions and double arithmetic share the FP64 pipe, 1/64 of the FP32 rate)
+    double half_n64, scale64, two_nsq64;  // N/2 (gradient stencil), 2/V (solve), 2 N^2 (Frank force)
+    float half_n32, scale32, two_nsq32;
     // LCE directors (3 x V each, null for the other laws): ping-pong fields and the
     // reference directors n0, in both precisions
     double* N64[2];

@@ -271,11 +271,11 @@ template <typename T, int D>
 struct LawOf<T, D, kLinear> { using type = Linear<T, D>; };
 
 template <typename Law, typename T>
-__device__ __forceinline__ Law load_law(const uint8_t* phase, const double* mat, int nparam, long long v) {
+__device__ __forceinline__ Law load_law(const uint8_t* phase, const T* mat, int nparam, long long v) {
     const int ph = phase[v];
     Law m;
-    m.mu = (T)__ldg(mat + ph * nparam + 0);
-    m.lam = (T)__ldg(mat + ph * nparam + 1);
+    m.mu = __ldg(mat + ph * nparam + 0);
+    m.lam = __ldg(mat + ph * nparam + 1);
     return m;
 }
 
@@ -518,16 +518,16 @@ struct Lce {
 };
 
 template <typename T>
-__device__ __forceinline__ Lce<T> load_lce(const uint8_t* phase, const double* mat, int nparam, long long v,
+__device__ __forceinline__ Lce<T> load_lce(const uint8_t* phase, const T* mat, int nparam, long long v,
                                           const T* __restrict__ n0, long long V) {
     const int ph = phase[v];
-    const double* q = mat + ph * nparam;
+    const T* q = mat + ph * nparam;
     Lce<T> m;
-    m.mu = (T)__ldg(q + 0);
-    m.lam = (T)__ldg(q + 1);
-    m.a = (T)__ldg(q + 5);
-    m.c1 = (T)__ldg(q + 6);
-    m.c2 = (T)__ldg(q + 7);
+    m.mu = __ldg(q + 0);
+    m.lam = __ldg(q + 1);
+    m.a = __ldg(q + 5);
+    m.c1 = __ldg(q + 6);
+    m.c2 = __ldg(q + 7);
     m.n0[0] = n0[v];
     m.n0[1] = n0[V + v];
     m.n0[2] = n0[2 * V + v];
@@ -818,6 +818,9 @@ struct Set<double> {
     __host__ __device__ static double* Lm(const Launch& L) { return L.L64; }
     __host__ __device__ static double* U(const Launch& L, int i) { return L.U64[i]; }
     __host__ __device__ static Dirs<double> dirs(const Launch& L) { return Dirs<double>{L.N64[0], L.N64[1], L.n0_64}; }
+    __host__ __device__ static const double* mat(const Launch& L) { return L.mat; }
+    __host__ __device__ static double half_n(const Launch& L) { return L.half_n64; }
+    __host__ __device__ static double two_nsq(const Launch& L) { return L.two_nsq64; }
 };
 template <>
 struct Set<float> {
@@ -825,13 +828,16 @@ struct Set<float> {
     __host__ __device__ static float* Lm(const Launch& L) { return L.L32; }
     __host__ __device__ static float* U(const Launch& L, int i) { return L.U32[i]; }
     __host__ __device__ static Dirs<float> dirs(const Launch& L) { return Dirs<float>{L.N32[0], L.N32[1], L.n0_32}; }
+    __host__ __device__ static const float* mat(const Launch& L) { return L.mat32; }
+    __host__ __device__ static float half_n(const Launch& L) { return L.half_n32; }
+    __host__ __device__ static float two_nsq(const Launch& L) { return L.two_nsq32; }
 };
 
 // Fresh state: F_k = Fbar, u~_k = 0, Lambda = W_F(Fbar; x) (or 0).
 template <typename T, int D, int MODEL>
 __global__ void __launch_bounds__(kLocalThreads)
 k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const uint8_t* __restrict__ phase,
-       const double* __restrict__ mat, int nparam, long long V, int lambda_zero, Dirs<T> dir) {
+       const T* __restrict__ mat, int nparam, long long V, int lambda_zero, Dirs<T> dir) {
     const int par = (int)(ctrl->k & 1);
     T* F = par ? F1 : F0;
     T* U = par ? U1 : U0;
@@ -912,7 +918,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     const T* U0 = Set<T>::U(L, 0);
     const T* U1 = Set<T>::U(L, 1);
     const uint8_t* __restrict__ phase = L.phase;
-    const double* __restrict__ mat = L.mat;
+    const T* __restrict__ mat = Set<T>::mat(L);
     const int nparam = L.nparam;
     const int n = L.n;
     const long long V = L.V;
@@ -946,7 +952,9 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
         Uold = par ? U1 : U0;
     }
     const T rho = (T)ctrl->rho;
-    const T half_n = (T)(0.5 * n);
+    const T half_n = Set<T>::half_n(L);
+    const T two_nsq = Set<T>::two_nsq(L);
+    const float half_n32 = L.half_n32;
     const int cap = ctrl->newton_cap;
     const T ntol = (T)ctrl->newton_tol;
     // inexact local steps (Section 2.1): |grad phi| <= f mu_ref r_d, with r_d of the
@@ -968,7 +976,12 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             dFb[i * D + j] = INC ? (float)(ctrl->Fbar[i * 3 + j] - ctrl->Fbar_prev[i * 3 + j]) : 0.f;
         }
 
-    double rp2 = 0.0, rd2 = 0.0, rl2 = 0.0;
+    // per-thread residual sums: float in the float kernels and in the increment form
+    // (whose terms are float; tens of voxels per thread keep the relative error of the
+    // sums near 1e-6, ample for the tolerance tests), double otherwise; the block and
+    // grid sums are always double
+    using Acc = typename std::conditional<sizeof(T) == 4 || INC, float, double>::type;
+    Acc rp2a = Acc(0), rd2a = Acc(0), rl2a = Acc(0);
     int nmax = 0, nfail = 0;
     const int chunk = L.local_chunk;
     const FastDiv dn = L.plan.div_n;
@@ -984,7 +997,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
         }
         if constexpr (INC) {
             float dG[NN];
-            grad_u<float, D>(DUin, V, nb, dFb, 0.5f * (float)n, dG);
+            grad_u<float, D>(DUin, V, nb, dFb, half_n32, dG);
             float spf = 0.f, sdf = 0.f;
 #pragma unroll
             for (int p = 0; p < NN; ++p) {
@@ -994,8 +1007,8 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
                 spf += e[p] * e[p];
                 sdf += dG[p] * dG[p];
             }
-            rp2 += (double)spf;
-            rd2 += (double)sdf;
+            rp2a += spf;
+            rd2a += sdf;
         } else if (!FIRST) {
             // squares are summed per voxel in T (9 terms) and the voxel sums in double
             T sp = T(0), sd = T(0);
@@ -1009,7 +1022,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             if constexpr (DU) {
                 const float zero[NN] = {};
                 float dG[NN];
-                grad_u<float, D>(DUin, V, nb, zero, 0.5f * (float)n, dG);
+                grad_u<float, D>(DUin, V, nb, zero, half_n32, dG);
                 float sdf = 0.f;
 #pragma unroll
                 for (int p = 0; p < NN; ++p) sdf += dG[p] * dG[p];
@@ -1023,8 +1036,8 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
                     sd += dg * dg;
                 }
             }
-            rp2 += (double)sp;
-            rd2 += (double)sd;
+            rp2a += (Acc)sp;
+            rd2a += (Acc)sd;
         }
         bool conv;
         int it;
@@ -1044,7 +1057,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             // director of the current iterate (same parity as F) and the explicit Frank force
             const T* nCur = FIRST ? (par ? dir.N1 : dir.N0) : (par ? dir.N0 : dir.N1);
             T* nNext = FIRST ? (par ? dir.N0 : dir.N1) : (par ? dir.N1 : dir.N0);
-            const T kf = (T)(2.0 * __ldg(mat + phase[v] * nparam + 4) * (double)n * (double)n);
+            const T kf = __ldg(mat + phase[v] * nparam + 4) * two_nsq;
             T nv[3], fr[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -1055,7 +1068,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             const Lce<T> m = load_lce<T>(phase, mat, nparam, v, dir.ref, V);
             T gn2 = T(0);
             it = newton_lce<T>(m, F, nv, B, fr, rho, cap, ntol, conv, gtol, &gn2);
-            rl2 += (double)gn2;
+            rl2a += (Acc)gn2;
 #pragma unroll
             for (int i = 0; i < 3; ++i) nNext[i * V + v] = nv[i];
         } else {
@@ -1063,7 +1076,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             const Law m = load_law<Law, T>(phase, mat, nparam, v);
             T gn2 = T(0);
             it = newton<T, D>(m, F, B, rho, cap, ntol, conv, gtol, &gn2);
-            rl2 += (double)gn2;
+            rl2a += (Acc)gn2;
         }
         nmax = max(nmax, it);
         nfail += conv ? 0 : 1;
@@ -1081,6 +1094,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
 
     // block partials: r_p^2, r_d^2 sums (double), Newton max / failures
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double rp2 = (double)rp2a, rd2 = (double)rd2a, rl2 = (double)rl2a;
     rp2 = warp_sum(rp2);
     rd2 = warp_sum(rd2);
     rl2 = warp_sum(rl2);
@@ -1316,7 +1330,7 @@ k_macro(Ctrl* __restrict__ ctrl, double* __restrict__ partials, const T* F0, con
 template <typename T, int D, int MODEL>
 __global__ void __launch_bounds__(kLocalThreads)
 k_stress(Ctrl* __restrict__ ctrl, double* __restrict__ partials, const T* F0, const T* F1, const T* Lam,
-         const uint8_t* __restrict__ phase, const double* __restrict__ mat, int nparam, long long V, Dirs<T> dir) {
+         const uint8_t* __restrict__ phase, const T* __restrict__ mat, int nparam, long long V, Dirs<T> dir) {
     constexpr int NN = D * D;
     __shared__ double s_sum[kLocalThreads / 32][2 * NN];
     __shared__ int s_last;
@@ -1420,7 +1434,7 @@ __global__ void k_convert(const Ctrl* __restrict__ ctrl, const S* Fs0, const S* 
 template <typename T, int D, int MODEL>
 cudaError_t run_init(const Launch& L, bool lambda_zero) {
     k_init<T, D, MODEL><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
-        L.ctrl, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0), Set<T>::U(L, 1), L.phase, L.mat,
+        L.ctrl, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), Set<T>::U(L, 0), Set<T>::U(L, 1), L.phase, Set<T>::mat(L),
         L.nparam, L.V, lambda_zero ? 1 : 0, Set<T>::dirs(L));
     return cudaGetLastError();
 }
@@ -1455,7 +1469,7 @@ cudaError_t run_local(const Exec& E, bool first, bool only_if, int mode) {
 template <typename T, int D, int MODEL>
 cudaError_t run_stress(const Launch& L) {
     k_stress<T, D, MODEL><<<L.local_blocks, kLocalThreads, 0, L.stream>>>(
-        L.ctrl, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), L.phase, L.mat, L.nparam, L.V,
+        L.ctrl, L.partials, Set<T>::F(L, 0), Set<T>::F(L, 1), Set<T>::Lm(L), L.phase, Set<T>::mat(L), L.nparam, L.V,
         Set<T>::dirs(L));
     return cudaGetLastError();
 }
