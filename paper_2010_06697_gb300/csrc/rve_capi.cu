@@ -76,7 +76,7 @@ bool valid_n(int n) {
 }
 
 struct Layout {
-    size_t ctrl, hist, partials, phase, mat, mat32, desc, tiles[admm::kTileClasses];
+    size_t ctrl, hist, partials, phase, mat, mat32, mat32lo, desc, tiles[admm::kTileClasses];
     size_t F64[2], L64, U64[2], tw64, ksq64, N64[2], n064;
     size_t F32[2], L32, U32[2], tw32, ksq32, N32[2], n032;
     size_t total;
@@ -113,6 +113,7 @@ Layout layout(int dim, int n, int model, int precision, int max_iter) {
     o.phase = take((size_t)V);
     o.mat = take(sizeof(double) * 256 * admm::kMaxParam);
     o.mat32 = take(sizeof(float) * 256 * admm::kMaxParam);
+    o.mat32lo = take(sizeof(float) * 256 * admm::kMaxParam);
     const bool need64 = precision != RVE_FP32;
     const bool need32 = precision != RVE_FP64;
     const bool lce = model == admm::kLce;
@@ -199,6 +200,7 @@ int begin_solve(rve* h, const double Fbar[9], double rho, double tol, cudaStream
     Ctrl& c = *h->hctrl;
     for (int i = 0; i < 9; ++i) c.Fbar[i] = c.Fbar_prev[i] = Fbar[i];
     c.free_mask = h->free_mask;
+    c.dw_state = 0;
     c.rho = rho;
     c.inv_rho = 1.0 / rho;
     c.mu_ref = o.mu_ref > 0 ? o.mu_ref : h->mu_ref;
@@ -305,9 +307,11 @@ int launches_per_iteration(const rve* h) {
     return admm::fft_stages(h->dim) + 1 + (h->opt.rho_policy == RVE_RHO_ADAPTIVE ? 1 : 0) + (h->free_mask ? 1 : 0);
 }
 
-// Mixed control: the free components of <F> for the coming projection (no-op without).
-cudaError_t macro_step(rve* h, bool fp64) {
-    return h->free_mask ? admm::launch_macro(h->L, fp64, h->stream) : cudaSuccess;
+// Mixed control: the free components of <F> for the coming projection (no-op
+// without).  polish: the state is in the double-word form of the elastic laws.
+cudaError_t macro_step(rve* h, bool fp64, bool polish = false) {
+    if (!h->free_mask) return cudaSuccess;
+    return admm::launch_macro(h->L, fp64, h->stream, polish && h->model != admm::kLce);
 }
 
 int ensure_prof_events(rve* h) {
@@ -336,7 +340,7 @@ int run_chunk_profiled(rve* h, bool fp64, bool incr) {
     const int f = fp64 ? 1 : 0;
     for (int i = 0; i < h->opt.check_every; ++i) {
         cudaEvent_t* e = &h->pev[(size_t)i * per];
-        if (macro_step(h, fp64) != cudaSuccess) return RVE_E_CUDA;
+        if (macro_step(h, fp64, incr) != cudaSuccess) return RVE_E_CUDA;
         CK(cudaEventRecord(e[0], h->stream));
         for (int st = 0; st < S; ++st) {
             const cudaError_t le = incr ? admm::launch_fft_incr(h->E, st) : admm::launch_fft(h->E, fp64, st);
@@ -377,7 +381,7 @@ int capture_chunk(rve* h, bool fp64, bool incr, int slot) {
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < h->opt.check_every && e == cudaSuccess; ++i) {
-        e = macro_step(h, fp64);
+        e = macro_step(h, fp64, incr);
         if (e == cudaSuccess) e = incr ? admm::launch_fft_incr(h->E) : admm::launch_fft(h->E, fp64);
         if (e == cudaSuccess) e = admm::launch_local(h->E, fp64, false, false, incr ? 2 : 0);
         if (e == cudaSuccess && h->opt.rho_policy == RVE_RHO_ADAPTIVE) e = admm::launch_local(h->E, fp64, true, true);
@@ -392,10 +396,22 @@ int capture_chunk(rve* h, bool fp64, bool incr, int slot) {
     return e3 == cudaSuccess ? RVE_OK : RVE_E_CUDA;
 }
 
+int run_phase_body(rve* h, bool fp64, bool polish);
+
 // Run iterations in one precision until the device sets the stop flag.  polish
 // (RVE_MIXED, fixed rho): after the first step, one full double projection,
-// then increment projections in float (see admm::launch_fft_incr).
+// then increment projections in float (see admm::launch_fft_incr) with the state
+// of the elastic laws held as double-words; it returns to double on every exit.
 int run_phase(rve* h, bool fp64, bool polish = false) {
+    const int rc = run_phase_body(h, fp64, polish);
+    if (!polish) return rc;
+    if (admm::launch_polish_state(h->L, false, h->stream) != cudaSuccess) return RVE_E_CUDA;
+    h->launches += 2;
+    if (rc) return rc;
+    return read_ctrl(h);
+}
+
+int run_phase_body(rve* h, bool fp64, bool polish) {
     if (h->prof) {
         if (ensure_prof_events(h)) return RVE_E_CUDA;
         const size_t last = h->pev.size() - 2;
@@ -413,7 +429,8 @@ int run_phase(rve* h, bool fp64, bool polish = false) {
         if (macro_step(h, true) != cudaSuccess) return RVE_E_CUDA;
         if (admm::launch_fft(h->E, true) != cudaSuccess) return RVE_E_CUDA;
         if (admm::launch_local(h->E, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
-        h->launches += admm::fft_stages(h->dim) + 1;
+        if (admm::launch_polish_state(h->L, true, h->stream) != cudaSuccess) return RVE_E_CUDA;
+        h->launches += admm::fft_stages(h->dim) + 3;
         const int rc = read_ctrl(h);
         if (rc) return rc;
         if (h->hctrl->done != admm::kRunning) return RVE_OK;
@@ -435,7 +452,7 @@ int run_phase(rve* h, bool fp64, bool polish = false) {
             CK(cudaGraphLaunch(h->graph[slot], h->stream));
         } else {
             for (int i = 0; i < h->opt.check_every; ++i) {
-                if (macro_step(h, fp64) != cudaSuccess) return RVE_E_CUDA;
+                if (macro_step(h, fp64, polish) != cudaSuccess) return RVE_E_CUDA;
                 const cudaError_t fe = polish ? admm::launch_fft_incr(h->E) : admm::launch_fft(h->E, fp64);
                 if (fe != cudaSuccess) return RVE_E_CUDA;
                 if (admm::launch_local(h->E, fp64, false, false, polish ? 2 : 0) != cudaSuccess) return RVE_E_CUDA;
@@ -546,6 +563,7 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
     L.phase = (const uint8_t*)(b + lay.phase);
     L.mat = (const double*)(b + lay.mat);
     L.mat32 = (const float*)(b + lay.mat32);
+    L.mat32lo = (const float*)(b + lay.mat32lo);
     L.nparam = 2;
     const bool lce = model == admm::kLce;
     if (o.precision != RVE_FP32) {
@@ -580,6 +598,8 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
         L.R32 = L.F32[0];
         L.S32 = L.U32[0];
         L.D32 = L.U32[1];
+        L.LH32 = L.L32;
+        L.LL32 = L.F32[1];
     }
     if (L.plan.np_half < 0 || L.plan.np_full < 0) return fail(RVE_E_INVALID_ARG);
     if (admm::prepare_fft_kernels(n) != cudaSuccess) return fail(RVE_E_CUDA);
@@ -754,8 +774,14 @@ int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* pa
     if (enter(h)) return RVE_E_CUDA;
     CK(cudaMemcpyAsync((void*)h->L.phase, phase, (size_t)h->V, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync((void*)h->L.mat, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    std::vector<float> tab32(tab.begin(), tab.end());
+    std::vector<float> tab32(tab.size()), tab32lo(tab.size());
+    for (size_t i = 0; i < tab.size(); ++i) {
+        tab32[i] = (float)tab[i];
+        tab32lo[i] = (float)(tab[i] - (double)tab32[i]);
+    }
     CK(cudaMemcpyAsync((void*)h->L.mat32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaMemcpyAsync((void*)h->L.mat32lo, tab32lo.data(), tab32lo.size() * sizeof(float), cudaMemcpyHostToDevice,
                        h->stream));
     if (lce && h->L.n0_64)
         CK(cudaMemcpyAsync((void*)h->L.n0_64, n0, 3 * (size_t)h->V * 8, cudaMemcpyHostToDevice, h->stream));
@@ -1259,7 +1285,8 @@ int engine_tick(Engine& E, std::vector<int>& finished) {
             if (fixed_rho) {
                 if (admm::launch_fft(Ei, true) != cudaSuccess) return RVE_E_CUDA;
                 if (admm::launch_local(Ei, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
-                h->launches += admm::fft_stages(h->dim) + 2;
+                if (admm::launch_polish_state(h->L, true, E.stream) != cudaSuccess) return RVE_E_CUDA;
+                h->launches += admm::fft_stages(h->dim) + 4;
             } else {
                 h->launches += 1;
             }
@@ -1277,6 +1304,11 @@ int engine_tick(Engine& E, std::vector<int>& finished) {
 void engine_release(Engine& E, int slot, double ms, rve_solve_info* info) {
     Member& m = E.mem[slot];
     rve* h = m.h;
+    if (m.stage == kStagePolish) {  // back to the double state (no-op unless it was converted),
+        admm::launch_polish_state(h->L, false, E.stream);  // finished before the handle's own
+        cudaStreamSynchronize(E.stream);                   // stream reads it
+        h->launches += 2;
+    }
     int fp64_iters = 0;
     if (h->opt.precision == RVE_FP64)
         fp64_iters = (int)(h->hctrl->k - m.k0);

@@ -37,6 +37,7 @@ struct Ctrl {
     double r_l;          // local residual of the last fused pass's local step (f > 0 only)
     double Fbar_prev[9]; // <F> of the previous iteration (r_d under mixed control)
     unsigned free_mask;  // mixed control: bit 3i+j set = <F_ij> free, <S_ij> -> 0
+    int dw_state;        // 1 while F and Lambda are held as double-words (polish)
     double stress[9];    // <W_F(F)> of the current state (written by the stress kernel)
     double lam_mean[9];  // <Lambda>
     long long k;         // iterations completed over the handle's life: F_k, u~_k live in buffer k & 1
@@ -114,6 +115,7 @@ struct Launch {
     const uint8_t* phase;
     const double* mat;     // per-phase constants, nparam each
     const float* mat32;    // the same table in float (float kernels read no doubles)
+    const float* mat32lo;  // and the remainders, mat - mat32, for double-word constants
     int nparam;
     // grid constants in both precisions, so that no kernel converts them per element
     // (conversions and double arithmetic share the FP64 pipe, 1/64 of the FP32 rate)
@@ -142,6 +144,7 @@ struct Launch {
     float* R32;
     float* S32;
     float* D32;  // float u~ increment of the last increment projection (d*V)
+    float *LH32, *LL32;  // Lambda as double-word (hi, lo) during the polish (idle float buffers)
     FftPlan plan;
 };
 
@@ -194,7 +197,10 @@ cudaError_t launch_init(const Launch& L, bool fp64, bool lambda_zero);
 cudaError_t launch_local(const Exec& E, bool fp64, bool first, bool only_if_rho_changed, int polish_mode = 0);
 cudaError_t launch_stress(const Launch& L, bool fp64);
 // mixed macroscopic control: free components of <F> from the mean of F - Lambda/rho
-cudaError_t launch_macro(const Launch& L, bool fp64, cudaStream_t st);
+// (dws: the state is in the double-word form of the polish)
+cudaError_t launch_macro(const Launch& L, bool fp64, cudaStream_t st, bool dws = false);
+// double <-> double-word state at the ends of the polish of the elastic laws
+cudaError_t launch_polish_state(const Launch& L, bool enter, cudaStream_t st);
 cudaError_t launch_convert(const Launch& L, bool to_fp64);
 // rve_fft.cu
 cudaError_t launch_fft(const Exec& E, bool fp64, int stage = -1);

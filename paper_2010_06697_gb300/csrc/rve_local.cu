@@ -60,6 +60,68 @@ __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float log_t(float x) { return logf(x); }
 __device__ __forceinline__ double log_t(double x) { return log(x); }
 
+// ------------------------------------------------------------------ double-word arithmetic
+// A double-word number is the unevaluated sum hi + lo of two floats with |lo| <=
+// ulp(hi) / 2: about 48 significant bits, from FP32 instructions only.  GB300
+// executes FP32 at 64 times its FP64 rate, so the double polish keeps its state and
+// its gradient in this form (polish_voxel_dw).  Error-free transformations: two_sum
+// (Knuth), fast_two_sum (Dekker, needs |a| >= |b| or a = 0), two_prod with an FMA.
+// The sum, product and quotient are the double-word algorithms analysed by Joldes,
+// Muller and Popescu, "Tight and rigorous error bounds for basic building blocks of
+// double-word arithmetic", ACM TOMS 44(2), 2017 (relative errors of a few u^2,
+// u = 2^-24: sum of two double-words 3u^2, double-word times float 2u^2, product
+// 5u^2, quotient 15u^2).  The _rn intrinsics stop the compiler from contracting or
+// reassociating the operations these rely on.
+struct dw {
+    float hi, lo;
+};
+__device__ __forceinline__ dw fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return dw{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dw two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return dw{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dw two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return dw{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ dw dw_neg(dw x) { return dw{-x.hi, -x.lo}; }
+__device__ __forceinline__ dw dw_add(dw x, dw y) {
+    const dw s = two_sum(x.hi, y.hi);
+    const dw t = two_sum(x.lo, y.lo);
+    const dw v = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
+}
+__device__ __forceinline__ dw dw_sub(dw x, dw y) { return dw_add(x, dw_neg(y)); }
+__device__ __forceinline__ dw dw_add_f(dw x, float y) {
+    const dw s = two_sum(x.hi, y);
+    return fast_two_sum(s.hi, __fadd_rn(x.lo, s.lo));
+}
+__device__ __forceinline__ dw dw_mul_f(dw x, float y) {
+    const dw c = two_prod(x.hi, y);
+    return fast_two_sum(c.hi, __fmaf_rn(x.lo, y, c.lo));
+}
+__device__ __forceinline__ dw dw_mul(dw x, dw y) {
+    const dw c = two_prod(x.hi, y.hi);
+    const float t = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.lo));
+    return fast_two_sum(c.hi, __fadd_rn(c.lo, __fmaf_rn(x.lo, y.hi, t)));
+}
+__device__ __forceinline__ dw dw_div(dw x, dw y) {
+    const float th = __fdiv_rn(x.hi, y.hi);
+    const dw r = dw_mul_f(y, th);
+    const float d = __fadd_rn(__fsub_rn(x.hi, r.hi), __fsub_rn(x.lo, r.lo));
+    return fast_two_sum(th, __fdiv_rn(d, y.hi));
+}
+// exact split of a double into a double-word (|d| within the float range), and back
+__device__ __forceinline__ dw dw_from(double d) {
+    const float hi = (float)d;
+    return dw{hi, (float)(d - (double)hi)};
+}
+__device__ __forceinline__ double dw_to(dw x) { return (double)x.hi + (double)x.lo; }
+
 // Cholesky factor of a symmetric positive definite H in packed lower storage
 // (row p, column q <= p at p(p+1)/2 + q), in place, with the reciprocal pivots in
 // inv.  Returns false when a pivot is not positive.
@@ -396,60 +458,128 @@ __device__ __forceinline__ int newton(const Law& m, T* F, const T* B, T rho, int
     return it;
 }
 
-// The rare branch of newton_incr (large or unsafe first step): the general Newton
-// from F_{k+1}.  (Kept inline: an out-of-line call makes the compiler spill its
-// array arguments to the stack on every voxel.)
-template <int D, typename Law>
-__device__ __forceinline__ int polish_general(const Law& m, double* F, const double* Bm, double rho, int cap,
-                                           double tol, bool& conv, float* eR, const double* __restrict__ Fstart,
-                                           long long V) {
+// W_F(F) - Bm on double-word data for the elastic laws (their grad() in double-word
+// arithmetic; F, Bm, g: d*d entries row-major).  False when J <= 0.
+template <int D, int MODEL>
+__device__ __forceinline__ bool grad_dw(const dw* F, dw mu, dw lam, const dw* Bm, dw* g) {
     constexpr int NN = D * D;
-    double B[NN];
+    if constexpr (MODEL == kNeoHooke) {
+        dw K[NN], J;
+        auto m2 = [&](int a, int b, int c, int d) { return dw_sub(dw_mul(F[a], F[b]), dw_mul(F[c], F[d])); };
+        if constexpr (D == 2) {
+            K[0] = F[3];
+            K[1] = dw_neg(F[2]);
+            K[2] = dw_neg(F[1]);
+            K[3] = F[0];
+            J = m2(0, 3, 1, 2);
+        } else {
+            K[0] = m2(4, 8, 5, 7);
+            K[1] = m2(5, 6, 3, 8);
+            K[2] = m2(3, 7, 4, 6);
+            K[3] = m2(2, 7, 1, 8);
+            K[4] = m2(0, 8, 2, 6);
+            K[5] = m2(1, 6, 0, 7);
+            K[6] = m2(1, 5, 2, 4);
+            K[7] = m2(2, 3, 0, 5);
+            K[8] = m2(0, 4, 1, 3);
+            J = dw_add(dw_add(dw_mul(F[0], K[0]), dw_mul(F[1], K[1])), dw_mul(F[2], K[2]));
+        }
+        if (!(J.hi > 0.f)) return false;
+        // W_F = mu F + (c / J) K, c = lam J (J - 1) - mu
+        const dw cJ = dw_div(dw_sub(dw_mul(dw_mul(lam, J), dw_add_f(J, -1.f)), mu), J);
 #pragma unroll
-    for (int p = 0; p < NN; ++p) B[p] = Bm[p] + rho * F[p];
-    const int it = newton<double, D>(m, F, B, rho, cap, tol, conv);
+        for (int p = 0; p < NN; ++p) g[p] = dw_sub(dw_add(dw_mul(mu, F[p]), dw_mul(cJ, K[p])), Bm[p]);
+        return true;
+    } else {
+        // W_F = mu (H + H^T) + lam tr(H) I, H = F - I
+        dw tr = dw{0.f, 0.f};
 #pragma unroll
-    for (int p = 0; p < NN; ++p) eR[p] = (float)((F[p] - Fstart[p * V]) - (double)eR[p]);
-    return it;
+        for (int i = 0; i < D; ++i) tr = dw_add(tr, dw_add_f(F[i * D + i], -1.f));
+        const dw ltr = dw_mul(lam, tr);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                dw s = dw_add(F[i * D + j], F[j * D + i]);
+                if (i == j) s = dw_add_f(s, -2.f);
+                dw gij = dw_mul(mu, s);
+                if (i == j) gij = dw_add(gij, ltr);
+                g[i * D + j] = dw_sub(gij, Bm[i * D + j]);
+            }
+        return true;
+    }
 }
 
-// Local step of the double polish in increment form.  On entry F = F_{k+1},
-// Bm = Lambda_{k+1} + rho e and eR = e = G_{k+1} - F_{k+1} (float).  With
-// G = F_{k+1} + e the gradient of phi is W_F(F) + rho (F - F_{k+1}) - Bm, so at
-// the start it is W_F(F) - Bm: neither G nor B = Lambda + rho G is formed in
-// double.
+// Local step of the double polish, one voxel, on double-word state (elastic laws).
 //
-// The polish takes ONE refinement step per iteration (double gradient, float
-// Hessian factor) whenever that step is a safe full step (no line search, J stays
-// positive): F becomes F_{k+1} + dF and R = F_{k+2} - G_{k+1} = dF - e is formed
-// in float.  The local problem is then solved inexactly, with a gradient left of
-// about eps_float cond(H) |g| + c |dF|^2; in the polish |g| and |dF| are of the
-// order of the ADMM residuals themselves, so that error is many orders below
-// them and is corrected by the next iteration's step, which starts from this F
-// (the inexact local solves of Sections 2.1 and 4.2, r_l << r_d).  A fixed point
-// still has an exactly stationary local problem: the step from it is zero only
-// where the double gradient vanishes.  Otherwise (large or unsafe step, failed
-// factorisation) the general Newton runs to the tolerance from F_{k+1}
-// (polish_general).  On exit eR holds R.
-template <int D, typename Law>
-__device__ __forceinline__ int newton_incr(const Law& m, double* F, const double* Bm, double rho, int cap,
-                                           double tol, bool& conv, float* eR, const double* __restrict__ Fstart,
-                                           long long V) {
+// Increment form: with R_k = F_{k+1} - G_k from the previous iteration (float) and
+// dG = G_{k+1} - G_k = <F> change + D(u~_{k+1} - u~_k) (float), e = G_{k+1} - F_{k+1}
+// = dG - R_k is a float difference of small quantities; r_p sums e^2 and r_d dG^2.
+// Multiplier: Lambda_{k+1} = Lambda_k + rho e.  With G = F_{k+1} + e the gradient of
+// phi at F_{k+1} is W_F(F) - Bm, Bm = Lambda_{k+1} + rho e: neither G nor
+// B = Lambda + rho G is needed.
+//
+// The step is ONE refinement Newton step per iteration, dF = -H_f^{-1} g with the
+// double-word gradient g and the float Hessian H_f, whenever that is a safe full
+// step (no line search, J stays positive): F_{k+2} = F_{k+1} + dF and R_{k+1} =
+// F_{k+2} - G_{k+1} = dF - e.  The local problem is then solved inexactly, with a
+// gradient left of about eps_float cond(H) |g| + c |dF|^2; in the polish |g| and
+// |dF| are of the order of the ADMM residuals, so that error is many orders below
+// them and is corrected by the next iteration's step, which starts from this F (the
+// inexact local solves of Sections 2.1 and 4.2, r_l << r_d).  A fixed point still
+// has an exactly stationary local problem (to the 2^-48 resolution of the state):
+// the step from it is zero only where the gradient vanishes.  Otherwise (large or
+// unsafe step, failed factorisation, J <= 0) the general double Newton runs to the
+// tolerance from F_{k+1}, and its result is split back into double-words.
+//
+// Storage: F as (hi, lo) float arrays in the double F buffers (hi at p V + v, lo
+// at (d*d + p) V + v), Lambda as (Lhi, Llo), updated in place.  Returns the Newton
+// count; sp, sd get the voxel's squared residual terms.
+template <int D, int MODEL>
+__device__ __forceinline__ int polish_voxel_dw(const float* __restrict__ Fc, float* __restrict__ Fn,
+                                               float* __restrict__ Lhi, float* __restrict__ Llo,
+                                               float* __restrict__ Rio, const float* dG, dw mu, dw lam, dw rho,
+                                               int cap, double tol, long long v, long long V, float& sp, float& sd,
+                                               bool& conv) {
     constexpr int NN = D * D;
     constexpr int NP = NN * (NN + 1) / 2;
-    constexpr int NAUX = Law::NAUX;
+    using Law = typename LawOf<float, D, MODEL>::type;
+    float e[NN];
+    dw Bm[NN];
+    sp = 0.f;
+    sd = 0.f;
+#pragma unroll
+    for (int p = 0; p < NN; ++p) {
+        e[p] = dG[p] - Rio[p * V + v];
+        sp += e[p] * e[p];
+        sd += dG[p] * dG[p];
+        const dw re = dw_mul_f(rho, e[p]);
+        const dw lam_new = dw_add(dw{Lhi[p * V + v], Llo[p * V + v]}, re);
+        Lhi[p * V + v] = lam_new.hi;
+        Llo[p * V + v] = lam_new.lo;
+        Bm[p] = dw_add(lam_new, re);
+    }
+    dw F[NN];
+#pragma unroll
+    for (int p = 0; p < NN; ++p) F[p] = dw{Fc[p * V + v], Fc[(NN + p) * V + v]};
+    int it = 0;
+    bool done = false;
     {
-        double g[NN], aux[NAUX];
-        if (m.grad(F, Bm, 0.0, g, aux)) {
-            float af[NAUX], gf[NN], df[NN];
-            bool ok;
-            {
+        dw g[NN];
+        if (grad_dw<D, MODEL>(F, mu, lam, Bm, g)) {
+            const Law m{mu.hi, lam.hi};
+            float Ff[NN], aux[Law::NAUX], gf[NN], df[NN];
+#pragma unroll
+            for (int p = 0; p < NN; ++p) {
+                Ff[p] = F[p].hi;
+                gf[p] = g[p].hi;
+            }
+            if constexpr (MODEL == kNeoHooke) aux[NN] = det_cof<float, D>(Ff, aux);
+            else aux[0] = 1.f;
+            bool ok = MODEL != kNeoHooke || aux[NN] > 0.f;
+            if (ok) {
                 float Hf[NP];
-#pragma unroll
-                for (int p = 0; p < NAUX; ++p) af[p] = (float)aux[p];
-#pragma unroll
-                for (int p = 0; p < NN; ++p) gf[p] = (float)g[p];
-                m.hess(af, (float)rho, Hf);
+                m.hess(aux, rho.hi, Hf);
                 ok = chol_solve<float, NN>(Hf, gf, df);
             }
             float slope = 0.f, size = 0.f;
@@ -458,18 +588,43 @@ __device__ __forceinline__ int newton_incr(const Law& m, double* F, const double
                 slope += gf[p] * df[p];
                 size = fmaxf(size, fabsf(df[p]));
             }
-            if (ok && slope < 0.f && size <= NewtonConst<float>::big && m.small_step_safe(af, size)) {
+            if (ok && slope < 0.f && size <= NewtonConst<float>::big && m.small_step_safe(aux, size)) {
 #pragma unroll
                 for (int p = 0; p < NN; ++p) {
-                    F[p] += (double)df[p];
-                    eR[p] = df[p] - eR[p];
+                    F[p] = dw_add_f(F[p], df[p]);
+                    e[p] = df[p] - e[p];
                 }
+                it = 1;
                 conv = true;
-                return 1;
+                done = true;
             }
         }
     }
-    return polish_general<D>(m, F, Bm, rho, cap, tol, conv, eR, Fstart, V);
+    if (!done) {
+        // general double Newton from F_{k+1}: B = Bm + rho F_{k+1}
+        using Law64 = typename LawOf<double, D, MODEL>::type;
+        const Law64 m64{dw_to(mu), dw_to(lam)};
+        const double rh = dw_to(rho);
+        double Fd[NN], B[NN];
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            Fd[p] = dw_to(F[p]);
+            B[p] = dw_to(Bm[p]) + rh * Fd[p];
+        }
+        it = newton<double, D>(m64, Fd, B, rh, cap, tol, conv);
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            e[p] = (float)((Fd[p] - dw_to(F[p])) - (double)e[p]);
+            F[p] = dw_from(Fd[p]);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < NN; ++p) {
+        Fn[p * V + v] = F[p].hi;
+        Fn[(NN + p) * V + v] = F[p].lo;
+        Rio[p * V + v] = e[p];
+    }
+    return it;
 }
 
 // ------------------------------------------------------------------ liquid crystal elastomer
@@ -896,12 +1051,10 @@ k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const 
 // DU (same polish, after its first iteration): the float increment
 // u~_{k+1} - u~_k written by the increment projection is read instead of u~_k,
 // and G_{k+1} - G_k = D(u~_{k+1} - u~_k) for r_d is formed in float.  For the
-// elastic laws this iteration runs in increment form (INC): with R_k =
-// F_{k+1} - G_k from the previous iteration, e = G_{k+1} - F_{k+1} =
-// D(u~_{k+1} - u~_k) - R_k is a float difference of small quantities, so r_p,
-// the multiplier update Lambda += rho e and the local step (newton_incr) need
-// neither u~ nor G in double.  Float rounding of these small increments adds a
-// few ulp of the residual level per iteration.
+// elastic laws this iteration runs in increment form on double-word state (INC,
+// polish_voxel_dw): F and Lambda are float pairs, and at ctrl->k = k the state
+// F_{k+1} sits in F buffer k & 1 (one parity off the double convention) so that
+// the conversions at the polish's ends read and write different buffers.
 // One tile = block `bid` of the RVE's local grid (L.local_blocks blocks).  FIRST
 // is a run-time flag (not a template parameter) so that the local step compiles
 // to one instruction sequence for both entry paths: a solve resumed from a saved
@@ -955,6 +1108,10 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     const T half_n = Set<T>::half_n(L);
     const T two_nsq = Set<T>::two_nsq(L);
     const float half_n32 = L.half_n32;
+    // double-word polish: F_{k+1} in buffer k & 1 (see above), rho split once
+    const float* Fc_dw = reinterpret_cast<const float*>(par ? F1 : F0);
+    float* Fn_dw = reinterpret_cast<float*>(par ? F0 : F1);
+    const dw rho_dw = INC ? dw_from(ctrl->rho) : dw{0.f, 0.f};
     const int cap = ctrl->newton_cap;
     const T ntol = (T)ctrl->newton_tol;
     // inexact local steps (Section 2.1): |grad phi| <= f mu_ref r_d, with r_d of the
@@ -987,29 +1144,29 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     const FastDiv dn = L.plan.div_n;
     for (long long v = bid * (long long)chunk + threadIdx.x; threadIdx.x < chunk && v < V; v += (long long)nblk * chunk) {
         const Nbr<D> nb = neighbours<D>((int)v, dn);
+        if constexpr (INC) {
+            float dG[NN], spf, sdf;
+            grad_u<float, D>(DUin, V, nb, dFb, half_n32, dG);
+            const int ph = phase[v];
+            const dw mu{__ldg(L.mat32 + ph * nparam), __ldg(L.mat32lo + ph * nparam)};
+            const dw lam{__ldg(L.mat32 + ph * nparam + 1), __ldg(L.mat32lo + ph * nparam + 1)};
+            bool conv;
+            const int it = polish_voxel_dw<D, MODEL>(Fc_dw, Fn_dw, L.LH32, L.LL32, Rout, dG, mu, lam, rho_dw, cap,
+                                                     (double)ntol, v, V, spf, sdf, conv);
+            rp2a += spf;
+            rd2a += sdf;
+            nmax = max(nmax, it);
+            nfail += conv ? 0 : 1;
+            continue;
+        }
         T G[NN], L[NN], F[NN];
-        float e[NN];  // INC: G_{k+1} - F_{k+1}, then R_{k+1}
-        if constexpr (!INC) grad_u<T, D>(Unew, V, nb, Fb, half_n, G);
+        grad_u<T, D>(Unew, V, nb, Fb, half_n, G);
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
             L[p] = Lam[p * V + v];
             F[p] = Fcur[p * V + v];
         }
-        if constexpr (INC) {
-            float dG[NN];
-            grad_u<float, D>(DUin, V, nb, dFb, half_n32, dG);
-            float spf = 0.f, sdf = 0.f;
-#pragma unroll
-            for (int p = 0; p < NN; ++p) {
-                e[p] = dG[p] - Rout[p * V + v];
-                L[p] += rho * (T)e[p];
-                Lam[p * V + v] = L[p];
-                spf += e[p] * e[p];
-                sdf += dG[p] * dG[p];
-            }
-            rp2a += spf;
-            rd2a += sdf;
-        } else if (!FIRST) {
+        if (!FIRST) {
             // squares are summed per voxel in T (9 terms) and the voxel sums in double
             T sp = T(0), sd = T(0);
 #pragma unroll
@@ -1042,18 +1199,9 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
         bool conv;
         int it;
         T B[NN];
-        if constexpr (INC) {
 #pragma unroll
-            for (int p = 0; p < NN; ++p) B[p] = L[p] + rho * (T)e[p];
-        } else {
-#pragma unroll
-            for (int p = 0; p < NN; ++p) B[p] = L[p] + rho * G[p];
-        }
-        if constexpr (INC) {
-            using Law = typename LawOf<T, D, MODEL>::type;
-            const Law m = load_law<Law, T>(phase, mat, nparam, v);
-            it = newton_incr<D>(m, F, B, rho, cap, ntol, conv, e, Fcur + v, V);
-        } else if constexpr (MODEL == kLce) {
+        for (int p = 0; p < NN; ++p) B[p] = L[p] + rho * G[p];
+        if constexpr (MODEL == kLce) {
             // director of the current iterate (same parity as F) and the explicit Frank force
             const T* nCur = FIRST ? (par ? dir.N1 : dir.N0) : (par ? dir.N0 : dir.N1);
             T* nNext = FIRST ? (par ? dir.N0 : dir.N1) : (par ? dir.N1 : dir.N0);
@@ -1082,10 +1230,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
         nfail += conv ? 0 : 1;
 #pragma unroll
         for (int p = 0; p < NN; ++p) Fnext[p * V + v] = F[p];
-        if constexpr (INC) {
-#pragma unroll
-            for (int p = 0; p < NN; ++p) Rout[p * V + v] = e[p];
-        } else if constexpr (WRITE_R) {
+        if constexpr (WRITE_R) {
 #pragma unroll
             for (int p = 0; p < NN; ++p) Rout[p * V + v] = (float)(F[p] - G[p]);
         }
@@ -1257,23 +1402,30 @@ k_local(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntil
 // |<F> + D u~ - Q|^2, Q = F_{k+1} - Lambda_k / rho; D u~ has zero mean, so their
 // minimiser is <Q>.  Runs before the iteration's projection, with ctrl->k = k;
 // keeps the previous <F> for r_d.  Sums in double with the fixed-order scheme.
-template <typename T, int D>
+// DWS: the double polish's double-word state (F_{k+1} in F buffer k & 1, Lambda in
+// Lh, Ll), read through T = float pointers.
+template <typename T, int D, bool DWS>
 __global__ void __launch_bounds__(kLocalThreads)
 k_macro(Ctrl* __restrict__ ctrl, double* __restrict__ partials, const T* F0, const T* F1, const T* Lam,
-        long long V) {
+        const float* __restrict__ Lh, const float* __restrict__ Ll, long long V) {
     constexpr int NN = D * D;
     __shared__ double s_sum[kLocalThreads / 32][2 * NN];
     __shared__ int s_last;
     if (ctrl->done) return;
-    const T* F = (ctrl->k & 1) ? F0 : F1;  // F_{k+1}
+    const T* F = ((ctrl->k & 1) != 0) != DWS ? F0 : F1;  // F_{k+1}
     double acc[2 * NN];
 #pragma unroll
     for (int p = 0; p < 2 * NN; ++p) acc[p] = 0.0;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
-            acc[p] += (double)F[p * V + v];
-            acc[NN + p] += (double)Lam[p * V + v];
+            if constexpr (DWS) {
+                acc[p] += (double)F[p * V + v] + (double)F[(NN + p) * V + v];
+                acc[NN + p] += (double)Lh[p * V + v] + (double)Ll[p * V + v];
+            } else {
+                acc[p] += (double)F[p * V + v];
+                acc[NN + p] += (double)Lam[p * V + v];
+            }
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1497,16 +1649,73 @@ cudaError_t launch_local(const Exec& E, bool fp64, bool first, bool only_if_rho_
     RVE_DISPATCH(run_local, float, E, first, only_if_rho_changed, 0);
 }
 
-cudaError_t launch_macro(const Launch& L, bool fp64, cudaStream_t st) {
+cudaError_t launch_macro(const Launch& L, bool fp64, cudaStream_t st, bool dws) {
     auto go = [&](auto kern, const auto* F0, const auto* F1, const auto* Lm) {
-        kern<<<L.local_blocks, kLocalThreads, 0, st>>>(L.ctrl, L.partials, F0, F1, Lm, L.V);
+        kern<<<L.local_blocks, kLocalThreads, 0, st>>>(L.ctrl, L.partials, F0, F1, Lm, L.LH32, L.LL32, L.V);
         return cudaGetLastError();
     };
+    if (dws) {
+        const float* f0 = reinterpret_cast<const float*>(L.F64[0]);
+        const float* f1 = reinterpret_cast<const float*>(L.F64[1]);
+        return L.dim == 3 ? go(k_macro<float, 3, true>, f0, f1, L.LH32) : go(k_macro<float, 2, true>, f0, f1, L.LH32);
+    }
     if (fp64)
-        return L.dim == 3 ? go(k_macro<double, 3>, L.F64[0], L.F64[1], L.L64)
-                          : go(k_macro<double, 2>, L.F64[0], L.F64[1], L.L64);
-    return L.dim == 3 ? go(k_macro<float, 3>, L.F32[0], L.F32[1], L.L32)
-                      : go(k_macro<float, 2>, L.F32[0], L.F32[1], L.L32);
+        return L.dim == 3 ? go(k_macro<double, 3, false>, L.F64[0], L.F64[1], L.L64)
+                          : go(k_macro<double, 2, false>, L.F64[0], L.F64[1], L.L64);
+    return L.dim == 3 ? go(k_macro<float, 3, false>, L.F32[0], L.F32[1], L.L32)
+                      : go(k_macro<float, 2, false>, L.F32[0], L.F32[1], L.L32);
+}
+
+// Double <-> double-word state at the ends of the polish (see local_tile).  With
+// k = ctrl->k.  enter (after the polish's first, double iteration, unless the solve
+// already stopped): the double F_{k+1} (buffer (k+1) & 1) becomes the double-word
+// F_{k+1} in buffer k & 1 and Lambda_k moves to (Lh, Ll).  leave (only after an
+// enter): the double-word F_k (buffer (k+1) & 1) becomes the double F_k in buffer
+// k & 1 and Lambda_k returns to its double buffer; u~ stayed double throughout.  The
+// speculative next iterate is dropped: every solve begins by recomputing it.
+template <int D>
+__global__ void k_polish_state(Ctrl* __restrict__ ctrl, double* F0, double* F1, double* __restrict__ Lam,
+                               float* __restrict__ Lh, float* __restrict__ Ll, long long V, int enter) {
+    constexpr int NN = D * D;
+    if (enter ? (ctrl->done != kRunning || ctrl->dw_state) : !ctrl->dw_state) return;
+    const long long k = ctrl->k;
+    double* Fa = ((k + 1) & 1) ? F1 : F0;  // buffer (k + 1) & 1
+    double* Fb = (k & 1) ? F1 : F0;        // buffer k & 1
+    const long long n = (long long)NN * V;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (enter) {
+            const dw f = dw_from(Fa[i]);
+            float* Fo = reinterpret_cast<float*>(Fb);
+            Fo[i] = f.hi;
+            Fo[n + i] = f.lo;
+            const dw l = dw_from(Lam[i]);
+            Lh[i] = l.hi;
+            Ll[i] = l.lo;
+        } else {
+            const float* Fi = reinterpret_cast<const float*>(Fa);
+            Fb[i] = (double)Fi[i] + (double)Fi[n + i];
+            Lam[i] = (double)Lh[i] + (double)Ll[i];
+        }
+    }
+}
+
+// Flips ctrl->dw_state after the conversion (a separate launch: every block of
+// k_polish_state reads the flag first).
+__global__ void k_polish_flag(Ctrl* __restrict__ ctrl, int enter) {
+    if (enter ? (ctrl->done == kRunning && !ctrl->dw_state) : ctrl->dw_state) ctrl->dw_state = enter;
+}
+
+cudaError_t launch_polish_state(const Launch& L, bool enter, cudaStream_t st) {
+    if (L.model == kLce) return cudaSuccess;  // the LCE polish stays in double
+    const int blocks = L.local_blocks;
+    if (L.dim == 3)
+        k_polish_state<3><<<blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.L64, L.LH32, L.LL32, L.V,
+                                                   enter ? 1 : 0);
+    else
+        k_polish_state<2><<<blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.L64, L.LH32, L.LL32, L.V,
+                                                   enter ? 1 : 0);
+    k_polish_flag<<<1, 1, 0, st>>>(L.ctrl, enter ? 1 : 0);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_stress(const Launch& L, bool fp64) {
