@@ -510,6 +510,43 @@ __device__ __forceinline__ bool grad_dw(const dw* F, dw mu, dw lam, const dw* Bm
     }
 }
 
+// The rare branch of polish_voxel_dw: the general double Newton from F_{k+1}, with
+// B = Bm + rho F_{k+1}, Bm = Lambda_{k+1} + rho e.  Everything is read back from
+// memory (F_{k+1} from Fc, Lambda_{k+1} from Lhi / Llo, e from Rio) and the call is
+// kept out of line with scalar arguments only, so that the one-step path carries
+// none of its registers.  Writes F_{k+2} (double-words) and R_{k+1}; returns the
+// Newton count, plus 1 << 16 when it met the tolerance.
+template <int D, int MODEL>
+__device__ __noinline__ int polish_fallback(const float* __restrict__ Fc, float* __restrict__ Fn,
+                                            const float* __restrict__ Lhi, const float* __restrict__ Llo,
+                                            float* __restrict__ Rio, float mu_hi, float mu_lo, float lam_hi,
+                                            float lam_lo, float rho_hi, float rho_lo, int cap, double tol, long long v,
+                                            long long V) {
+    constexpr int NN = D * D;
+    using Law64 = typename LawOf<double, D, MODEL>::type;
+    const Law64 m64{(double)mu_hi + (double)mu_lo, (double)lam_hi + (double)lam_lo};
+    const double rh = (double)rho_hi + (double)rho_lo;
+    double F0[NN], Fd[NN], B[NN];
+#pragma unroll
+    for (int p = 0; p < NN; ++p) {
+        F0[p] = (double)Fc[p * V + v] + (double)Fc[(NN + p) * V + v];
+        Fd[p] = F0[p];
+        const double e = (double)Rio[p * V + v];
+        B[p] = (double)Lhi[p * V + v] + (double)Llo[p * V + v] + rh * e + rh * F0[p];
+    }
+    bool conv;
+    const int it = newton<double, D>(m64, Fd, B, rh, cap, tol, conv);
+#pragma unroll
+    for (int p = 0; p < NN; ++p) {
+        const double e = (double)Rio[p * V + v];
+        Rio[p * V + v] = (float)((Fd[p] - F0[p]) - e);
+        const dw f = dw_from(Fd[p]);
+        Fn[p * V + v] = f.hi;
+        Fn[(NN + p) * V + v] = f.lo;
+    }
+    return it | (conv ? 1 << 16 : 0);
+}
+
 // Local step of the double polish, one voxel, on double-word state (elastic laws).
 //
 // Increment form: with R_k = F_{k+1} - G_k from the previous iteration (float) and
@@ -601,22 +638,12 @@ __device__ __forceinline__ int polish_voxel_dw(const float* __restrict__ Fc, flo
         }
     }
     if (!done) {
-        // general double Newton from F_{k+1}: B = Bm + rho F_{k+1}
-        using Law64 = typename LawOf<double, D, MODEL>::type;
-        const Law64 m64{dw_to(mu), dw_to(lam)};
-        const double rh = dw_to(rho);
-        double Fd[NN], B[NN];
 #pragma unroll
-        for (int p = 0; p < NN; ++p) {
-            Fd[p] = dw_to(F[p]);
-            B[p] = dw_to(Bm[p]) + rh * Fd[p];
-        }
-        it = newton<double, D>(m64, Fd, B, rh, cap, tol, conv);
-#pragma unroll
-        for (int p = 0; p < NN; ++p) {
-            e[p] = (float)((Fd[p] - dw_to(F[p])) - (double)e[p]);
-            F[p] = dw_from(Fd[p]);
-        }
+        for (int p = 0; p < NN; ++p) Rio[p * V + v] = e[p];
+        const int r = polish_fallback<D, MODEL>(Fc, Fn, Lhi, Llo, Rio, mu.hi, mu.lo, lam.hi, lam.lo, rho.hi, rho.lo,
+                                                cap, tol, v, V);
+        conv = (r >> 16) != 0;
+        return r & 0xffff;
     }
 #pragma unroll
     for (int p = 0; p < NN; ++p) {
@@ -1381,13 +1408,15 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
 
 // Resident blocks per SM the register budget is cut for: the float elastic laws
 // are latency-bound at fewer.
-template <typename T, int MODEL>
+template <typename T, int MODEL, bool WRITE_R, bool DU>
 constexpr int local_min_blocks() {
-    return (MODEL != kLce && sizeof(T) == 4) ? 4 : 1;
+    if (MODEL == kLce) return 1;
+    if (sizeof(T) == 4) return 4;
+    return (WRITE_R && DU) ? 4 : 1;  // the double-word polish: FP32 work, latency-bound
 }
 
 template <typename T, int D, int MODEL, bool WRITE_R, bool DU>
-__global__ void __launch_bounds__(kLocalThreads, local_min_blocks<T, MODEL>())
+__global__ void __launch_bounds__(kLocalThreads, local_min_blocks<T, MODEL, WRITE_R, DU>())
 k_local(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles, int first,
         int only_if_rho_changed) {
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
