@@ -52,11 +52,11 @@ def bytes_per_voxel(cls: str, s: int, d: int = 3) -> float:
             "xfwd_incr": (d * d + d) * 4, "xinv_incr": d * 4 + 2 * d * 8}[cls]
 
 
-# FP64 flops per voxel of the double polish's local kernel (k_local<double,...,R,DU>), counted with
-# ncu on the 128^3 inclusion cell: 70 DFMA + 41 DADD + 32 DMUL per voxel per launch
-FP64_FLOPS_PER_VOXEL = {"local_r": 2 * 70.0 + 41.0 + 32.0}
-# FP64 peak from unit counts and clocks: 2 FP64 FMA/clk/SM x 152 SMs x 2 flops x 2.07 GHz
-FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per launch measured with ncu on the 128^3 inclusion cell
+# (profiles/), keyed by (kernel class, precision); absent = not captured since the
+# kernel last changed
+TRAFFIC = {("local", "fp32"): 220838144 + 120816384, ("local_r", "fp64"): 421992704 + 358247936,
+           ("xfwd", "fp32"): 151885056 + 13613312, ("solve", "fp32"): 25204480}
 
 
 def combine_ranks(ms, vox_it, dist=None, device="cpu"):
@@ -308,20 +308,12 @@ def run_ours(args):
     kern.sort(key=lambda k: -k["total_ms"])
     top = kern[0]
     share = top["total_ms"] / sum(k["total_ms"] for k in kern)
-    if top["precision"] == "fp64" and top["kernel"] in FP64_FLOPS_PER_VOXEL:
-        # the double polish's local kernel is bound by the FP64 pipe, not by HBM
-        tf = FP64_FLOPS_PER_VOXEL[top["kernel"]] * V / (top["ms_per_launch"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": f"{top['kernel']} ({top['precision']})",
-                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe measured 1.20 at 1995 MHz)",
-                "hbm_view": {"achieved_gbs": top["gbs"], "frac_of_measured_hbm": top["gbs"] / pk["hbm_gbs"]},
-                "share_of_profiled_time": share}
-    else:
-        roof = {"bound": "hbm", "achieved": top["gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": top["gbs"] / pk["hbm_gbs"], "traffic": None,
-                "kernel": f"{top['kernel']} ({top['precision']})", "peak_source": pk["source"],
-                "share_of_profiled_time": share}
+    # every kernel of the path is bounded by HBM traffic in the byte model above (the local
+    # kernels also by FP32 issue: their Newton work varies per voxel and iteration)
+    roof = {"bound": "hbm", "achieved": top["gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": top["gbs"] / pk["hbm_gbs"], "traffic": TRAFFIC.get((top["kernel"], top["precision"])),
+            "kernel": f"{top['kernel']} ({top['precision']})", "peak_source": pk["source"],
+            "share_of_profiled_time": share}
     line = {
         "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps, "higher_is_better": True,
