@@ -91,9 +91,13 @@ def inclusion_phase(n: int, dim: int, seed: int, radius: int = 6,
         cs = np.minimum((u * n).astype(np.int64), n - 1).reshape(batch, dim)
         for c in cs:
             idx = tuple((c[a] + offs[a]) % n for a in range(dim))
-            ph[idx] = 1
+            if n > 2 * r:  # the ball's voxels are distinct: count the new ones
+                count += int(np.count_nonzero(ph[idx] == 0))
+                ph[idx] = 1
+            else:
+                ph[idx] = 1
+                count = int(np.count_nonzero(ph))
             drawn += 1
-            count = int(np.count_nonzero(ph))
             if count >= target:
                 break
     return ph

@@ -284,3 +284,64 @@ def test_full_size_converged_stress_matches_stored_oracle_run():
     m, im = run_gpu(ph, PAR, Fbar, g["recipe"]["rho"], g["recipe"]["tol"], 1000, precision="mixed")
     assert im.converged
     assert rel(m.stress(), np.array(g["stress"])) < 1e-5
+
+
+# ------------------------------------------------------------------ maximum size (512^3)
+
+def test_max_size_first_iteration_sampled():
+    """The largest cell the library accepts, 512^3 (134M voxels), one FP64 iteration:
+    at 2048 sampled voxels F_1 equals the oracle's local solve from the inputs alone,
+    and u~_1, Lambda_1 satisfy Step 2's normal equations and Step 3 there (the
+    stencils are gathered around each sampled voxel; each field is fetched, sampled
+    and dropped in turn to bound host memory)."""
+    n = 512
+    ph = synth.inclusion_phase(n, 3, 1)
+    Fbar = np.diag([0.9, 1.0, 1.0])
+    rho = 10.0
+    s, info = run_gpu(ph, PAR, Fbar, rho, -1.0, 1)
+    assert info.iterations == 1
+    V = ph.size
+    rng = np.random.default_rng(3)
+    idx = rng.choice(V, 2048, replace=False)
+    z, y, x = np.unravel_index(idx, ph.shape)
+
+    def at(dz=0, dy=0, dx=0):
+        return np.ravel_multi_index(((z + dz) % n, (y + dy) % n, (x + dx) % n), ph.shape)
+
+    off = [(0, 0, 1), (0, 1, 0), (1, 0, 0)]  # e_1 (x), e_2 (y), e_3 (z) as (dz, dy, dx)
+    plus = [at(*o) for o in off]
+    minus = [at(-o[0], -o[1], -o[2]) for o in off]
+    phf = ph.reshape(-1)
+    mat_s = oracle.make_material("neohookean", phf[idx], PAR)
+    F0 = np.broadcast_to(Fbar, (idx.size, 3, 3)).copy()
+    F1, _ = oracle.local_newton(mat_s, F0, mat_s.P(F0), F0.copy(), rho)
+    # Lambda_0 = W_F(Fbar) per phase
+    P_phase = oracle.make_material("neohookean", np.arange(2, dtype=np.uint8), PAR).P(
+        np.broadcast_to(Fbar, (2, 3, 3)).copy()).reshape(2, 9)
+    Fg = s.get_field(rve.RVE_FIELD_F).reshape(9, V)
+    F_c = Fg[:, idx].copy()
+    F_p = [Fg[:, pts].copy() for pts in plus]
+    F_m = [Fg[:, pts].copy() for pts in minus]
+    del Fg
+    assert rel(F_c.T.reshape(-1, 3, 3), F1) < TOL64
+    U = s.get_field(rve.RVE_FIELD_U).reshape(3, V)
+    half = n / 2.0
+    G = np.zeros((3, 3, idx.size))
+    for i in range(3):
+        lhs = np.zeros(idx.size)
+        rhs = np.zeros(idx.size)
+        for j, (dz, dy, dx) in enumerate(off):
+            lhs += (U[i, at(2 * dz, 2 * dy, 2 * dx)] - 2 * U[i, idx] + U[i, at(-2 * dz, -2 * dy, -2 * dx)]) * half * half
+            qp = F_p[j][3 * i + j] - P_phase[phf[plus[j]], 3 * i + j] / rho
+            qm = F_m[j][3 * i + j] - P_phase[phf[minus[j]], 3 * i + j] / rho
+            rhs += (qp - qm) * half
+            G[i, j] = Fbar[i, j] + (U[i, plus[j]] - U[i, minus[j]]) * half
+        assert np.max(np.abs(lhs - rhs)) < 1e-9 * max(np.max(np.abs(rhs)), 1e-300)
+    del U
+    # Step 3: Lambda_1 = Lambda_0 + rho (Fbar + D u~_1 - F_1)
+    Lg = s.get_field(rve.RVE_FIELD_LAMBDA).reshape(9, V)[:, idx].copy()
+    for i in range(3):
+        for j in range(3):
+            want = P_phase[phf[idx], 3 * i + j] + rho * (G[i, j] - F_c[3 * i + j])
+            assert np.max(np.abs(Lg[3 * i + j] - want)) < TOL64 * max(np.max(np.abs(want)), 1.0)
+    s.close()
