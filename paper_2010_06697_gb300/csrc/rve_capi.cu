@@ -628,6 +628,7 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
             E.smem_x[f] = admm::smem_x_bytes(L, f == 1);
             E.smem_a[f] = admm::smem_a_bytes(L, f == 1);
         }
+        E.uniform_n = n;
     }
     h->state_fp64 = o.precision == RVE_FP64 ? 1 : 0;
     h->hctrl->hist_cap = o.max_iter + 1;
@@ -1136,6 +1137,9 @@ int run_upload(Engine& E, BatchRun& r) {
     r.E.stream = E.stream;
     r.E.rds = E.d_rds;
     r.E.rep = &E.mem[r.active.front()].h->L;
+    r.E.uniform_n = E.mem[r.active.front()].h->n;
+    for (int slot : r.active)
+        if (E.mem[slot].h->n != r.E.uniform_n) r.E.uniform_n = 0;
     for (int f = 0; f < 2; ++f) {
         r.E.smem_x[f] = 0;
         r.E.smem_a[f] = 0;

@@ -477,6 +477,134 @@ __device__ __forceinline__ void faxis_tile(const Launch& L, int bid) {
     }
 }
 
+// ------------------------------------------------------------------ fixed-size column passes
+
+// Columns of power-of-two length N in {64, 128, 256, 512}: N/8 threads per column and
+// 2048/N columns per block of 256 threads.  Each thread keeps 8 elements of its column
+// in registers through all passes (radix 8, then a last radix 2 or 4 where N is not a
+// power of 8) and exchanges them through shared memory between passes.  After a whole
+// transform a thread holds elements j + (N/8) r again, the positions it loaded, so the
+// forward transform, the spectral scaling and the inverse of the z solve follow one
+// another in registers.  All index arithmetic is fixed at compile time.
+template <int N>
+struct ColPlan {
+    static constexpr int T = N / 8;                                // threads per column
+    static constexpr int TK = 256 / T;                             // columns per block
+    static constexpr int P8 = N == 512 ? 3 : 2;                    // radix-8 passes
+    static constexpr int RL = N == 128 ? 2 : (N == 256 ? 4 : 1);   // last radix (1: none)
+};
+
+template <bool INV, typename V>
+__device__ __forceinline__ V twiddled(V a, V w) {
+    return cmul(a, INV ? cconj(w) : w);
+}
+
+// One Stockham transform (sign by INV, unnormalised) of the block's columns.  x: the
+// thread's elements j + T r of column cl, on entry and on exit.  buf: two shared
+// buffers of N * TK values (element-major, column fastest); tw: exp(-2 pi i m / N).
+template <int N, bool INV, typename V>
+__device__ __forceinline__ void col_fft(V (&x)[8], V* __restrict__ buf, const V* __restrict__ tw, int j, int cl) {
+    using P = ColPlan<N>;
+    constexpr int T = P::T, TK = P::TK;
+    __syncthreads();  // the previous transform's readers are done with both buffers
+#pragma unroll
+    for (int p = 0; p < P::P8; ++p) {
+        const int Ns = 1 << (3 * p);
+        V* in = buf + ((p + 1) & 1) * (N * TK);
+        V* out = buf + (p & 1) * (N * TK);
+        const int k = j & (Ns - 1);
+        if (p > 0) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) x[r] = in[(j + T * r) * TK + cl];
+#pragma unroll
+            for (int r = 1; r < 8; ++r) x[r] = twiddled<INV>(x[r], tw[k * r * (N / (8 * Ns))]);
+        }
+        dft8<INV>(x);
+        const bool last = (p == P::P8 - 1) && P::RL == 1;
+        if (!last) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) out[((j - k) * 8 + r * Ns + k) * TK + cl] = x[r];
+            __syncthreads();
+        }
+    }
+    if constexpr (P::RL > 1) {
+        constexpr int RL = P::RL, Q = 8 / RL, Ns = N / RL;
+        const V* in = buf + ((P::P8 - 1) & 1) * (N * TK);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int b = j + T * q;  // butterfly index (< Ns): twiddle exponent b r
+            V v[RL];
+#pragma unroll
+            for (int r = 0; r < RL; ++r) {
+                v[r] = in[(b + Ns * r) * TK + cl];
+                if (r > 0) v[r] = twiddled<INV>(v[r], tw[b * r]);
+            }
+            if constexpr (RL == 2) dft2<INV>(v);
+            else dft4<INV>(v);
+#pragma unroll
+            for (int r = 0; r < RL; ++r) x[q + r * Q] = v[r];  // element b + Ns r = j + T (q + r Q)
+        }
+    }
+}
+
+// faxis_tile with a fixed column length N (see ColPlan); same tiles and modes.
+template <typename T, int N, int D, int AXIS, int MODE, bool INCR>
+__device__ __forceinline__ void faxis_fixed_tile(const Launch& L, int bid) {
+    using V = typename Cx<T>::t;
+    using Args = FftArgs<T>;
+    using P = ColPlan<N>;
+    constexpr int H = N / 2, TK = P::TK, TT = P::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Ctrl* __restrict__ ctrl = L.ctrl;
+    T* U0 = INCR ? (T*)L.S32 : Args::U(L, 0);
+    T* U1 = INCR ? (T*)L.S32 : Args::U(L, 1);
+    const V* __restrict__ g_tw = Args::tw(L);
+    const T* __restrict__ ksq = Args::ksq(L);
+    const T scale = Args::scale(L);
+    if (ctrl->done) return;
+    constexpr long long Vn = (D == 3) ? (long long)N * N * N : (long long)N * N;
+    const int par = (int)(ctrl->k & 1);
+    V* S = reinterpret_cast<V*>(par ? U0 : U1);
+    V* s_tw = reinterpret_cast<V*>(smem_raw);
+    V* buf = s_tw + N;
+    load_twiddles(s_tw, g_tw, N);
+    constexpr int gxa = H / TK;
+    constexpr int gya = (D == 3) ? N : 1;
+    const int col0 = (bid % gxa) * TK;
+    const int outer = (bid / gxa) % gya;
+    const int c = bid / (gxa * gya);
+    long long base;
+    constexpr long long es_g = (D == 3 && AXIS == 2) ? (long long)N * H : H;
+    if (D == 3 && AXIS == 1)
+        base = (long long)c * (Vn / 2) + (long long)outer * N * H + col0;
+    else if (D == 3 && AXIS == 2)
+        base = (long long)c * (Vn / 2) + (long long)outer * H + col0;
+    else
+        base = (long long)c * (Vn / 2) + col0;
+    const int cl = threadIdx.x % TK;
+    const int j = threadIdx.x / TK;
+    V x[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) x[r] = S[base + (j + TT * r) * es_g + cl];
+    if (MODE == 1) {
+        col_fft<N, true>(x, buf, s_tw, j, cl);
+    } else {
+        col_fft<N, false>(x, buf, s_tw, j, cl);
+        if (MODE == 2) {
+            const T kout = (D == 3) ? __ldg(ksq + outer) : T(0);
+            const T kcol = __ldg(ksq + min(col0 + cl, H - 1)) + kout;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const T den = __ldg(ksq + j + TT * r) + kcol;
+                x[r] = cscale(x[r], den > T(0) ? scale / den : T(0));
+            }
+            col_fft<N, true>(x, buf, s_tw, j, cl);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) S[base + (j + TT * r) * es_g + cl] = x[r];
+}
+
 // ------------------------------------------------------------------ launch
 
 inline int lines_per_block(int n, int nlines) {
@@ -516,11 +644,52 @@ k_faxis(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntil
     }
 }
 
+template <typename T, int N, int D, int AXIS, int MODE, bool INCR>
+__global__ void __launch_bounds__(kFftThreads)
+k_faxis_fixed(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        faxis_fixed_tile<T, N, D, AXIS, MODE, INCR>(rds[tl.x], tl.y);
+        __syncthreads();
+    }
+}
+
+template <typename T, int N>
+constexpr size_t fixed_smem() {
+    return (size_t)(N + 2 * N * ColPlan<N>::TK) * sizeof(typename Cx<T>::t);
+}
+
 template <typename K>
 void go(K kern, const Exec& E, int cls, size_t smem) {
     const int nt = E.ntiles[cls];
     const int grid = persistent_grid((const void*)kern, kFftThreads, smem, nt);
     kern<<<grid, kFftThreads, smem, E.stream>>>(E.rds, E.tiles[cls], nt);
+}
+
+// y/z pass: the fixed-length kernel when every member of the launch is a 3D grid of
+// N in {128, 256, 512} with the fixed kernel's column tile, else the general one.
+template <typename T, int D, int AXIS, int MODE, bool INCR>
+void go_axis(const Exec& E, int cls, size_t sma) {
+    const int tk = std::is_same<T, double>::value ? E.rep->tk64 : E.rep->tk32;
+    if constexpr (D == 3) {
+        switch (E.uniform_n) {
+            case 128:
+                if (tk == ColPlan<128>::TK)
+                    return go(k_faxis_fixed<T, 128, D, AXIS, MODE, INCR>, E, cls, fixed_smem<T, 128>());
+                break;
+            case 256:
+                if (tk == ColPlan<256>::TK)
+                    return go(k_faxis_fixed<T, 256, D, AXIS, MODE, INCR>, E, cls, fixed_smem<T, 256>());
+                break;
+            case 512:
+                if (tk == ColPlan<512>::TK)
+                    return go(k_faxis_fixed<T, 512, D, AXIS, MODE, INCR>, E, cls, fixed_smem<T, 512>());
+                break;
+            default:
+                break;
+        }
+    }
+    go(k_faxis<T, D, AXIS, MODE, INCR>, E, cls, sma);
 }
 
 // stage < 0: all passes of one iteration; otherwise only pass `stage`
@@ -536,12 +705,12 @@ cudaError_t run_fft(const Exec& E, int stage) {
     auto want = [&](int s) { return stage < 0 || stage == s; };
     static_assert(!INCR || std::is_same<T, float>::value, "increment projection runs in float");
     if (want(0)) go(k_xfwd<T, D, INCR>, E, kTilesX, smx);
-    if (D == 3) {
-        if (want(1)) go(k_faxis<T, D, 1, 0, INCR>, E, ax, sma);
-        if (want(2)) go(k_faxis<T, D, 2, 2, INCR>, E, ax, sma);
-        if (want(3)) go(k_faxis<T, D, 1, 1, INCR>, E, ax, sma);
+    if constexpr (D == 3) {
+        if (want(1)) go_axis<T, D, 1, 0, INCR>(E, ax, sma);
+        if (want(2)) go_axis<T, D, 2, 2, INCR>(E, ax, sma);
+        if (want(3)) go_axis<T, D, 1, 1, INCR>(E, ax, sma);
     } else if (want(1)) {
-        go(k_faxis<T, D, 1, 2, INCR>, E, ax, sma);
+        go_axis<T, D, 1, 2, INCR>(E, ax, sma);
     }
     if (want(last)) {
         if constexpr (INCR)
@@ -565,6 +734,22 @@ cudaError_t set_smem_attrs(int bytes) {
     set((const void*)k_faxis<T, D, 1, 1, false>);
     set((const void*)k_faxis<T, D, 1, 2, false>);
     set((const void*)k_faxis<T, D, 2, 2, false>);
+    if constexpr (D == 3) {
+        auto fixed = [&](auto tag) {
+            constexpr int N = decltype(tag)::value;
+            set((const void*)k_faxis_fixed<T, N, D, 1, 0, false>);
+            set((const void*)k_faxis_fixed<T, N, D, 1, 1, false>);
+            set((const void*)k_faxis_fixed<T, N, D, 2, 2, false>);
+            if constexpr (std::is_same<T, float>::value) {
+                set((const void*)k_faxis_fixed<T, N, D, 1, 0, true>);
+                set((const void*)k_faxis_fixed<T, N, D, 1, 1, true>);
+                set((const void*)k_faxis_fixed<T, N, D, 2, 2, true>);
+            }
+        };
+        fixed(std::integral_constant<int, 128>());
+        fixed(std::integral_constant<int, 256>());
+        fixed(std::integral_constant<int, 512>());
+    }
     if constexpr (std::is_same<T, float>::value) {
         set((const void*)k_xfwd<float, D, true>);
         set((const void*)k_xinv<float, double, D, true>);
@@ -629,6 +814,7 @@ Geometry default_geometry(int dim, int n) {
     g.tk32 = FftArgs<float>::tk < H ? FftArgs<float>::tk : H;
     while (g.tk64 > 1 && ax_blocks(g.tk64) < want_blocks) g.tk64 /= 2;
     while (g.tk32 > 1 && ax_blocks(g.tk32) < want_blocks) g.tk32 /= 2;
+    if (dim == 3 && (n == 128 || n == 256 || n == 512)) g.tk64 = g.tk32 = 2048 / n;  // fixed-length y/z kernels
     g.np_half = factor_radices(H, g.rad_half);
     g.np_full = factor_radices(n, g.rad_full);
     return g;

@@ -162,6 +162,7 @@ struct Exec {
     int ntiles[kTileClasses];
     size_t smem_x[2];             // dynamic shared memory of the x passes [fp64], max over members
     size_t smem_a[2];             // and of the y/z passes
+    int uniform_n;                // N shared by every member (0 if sizes differ)
 };
 
 // FFT geometry of one grid shape: x-pass lines per block and half-length radices,

@@ -286,15 +286,15 @@ def test_full_size_converged_stress_matches_stored_oracle_run():
     assert rel(m.stress(), np.array(g["stress"])) < 1e-5
 
 
-# ------------------------------------------------------------------ maximum size (512^3)
+# ------------------------------------------------------------------ large sizes (256^3, maximum 512^3)
 
-def test_max_size_first_iteration_sampled():
-    """The largest cell the library accepts, 512^3 (134M voxels), one FP64 iteration:
-    at 2048 sampled voxels F_1 equals the oracle's local solve from the inputs alone,
-    and u~_1, Lambda_1 satisfy Step 2's normal equations and Step 3 there (the
-    stencils are gathered around each sampled voxel; each field is fetched, sampled
-    and dropped in turn to bound host memory)."""
-    n = 512
+@pytest.mark.parametrize("n", [256, 512])
+def test_large_first_iteration_sampled(n):
+    """256^3 and the largest cell the library accepts, 512^3 (134M voxels), one FP64
+    iteration with the fixed-length y/z kernels: at 2048 sampled voxels F_1 equals the
+    oracle's local solve from the inputs alone, and u~_1, Lambda_1 satisfy Step 2's
+    normal equations and Step 3 there (the stencils are gathered around each sampled
+    voxel; each field is fetched, sampled and dropped in turn to bound host memory)."""
     ph = synth.inclusion_phase(n, 3, 1)
     Fbar = np.diag([0.9, 1.0, 1.0])
     rho = 10.0
@@ -345,3 +345,16 @@ def test_max_size_first_iteration_sampled():
             want = P_phase[phf[idx], 3 * i + j] + rho * (G[i, j] - F_c[3 * i + j])
             assert np.max(np.abs(Lg[3 * i + j] - want)) < TOL64 * max(np.max(np.abs(want)), 1.0)
     s.close()
+
+
+def test_float_path_fixed_length_kernels_match_double():
+    """128^3, two iterations in float (fixed-length float y/z kernels) against the same
+    two iterations in double: the fields agree to float accuracy."""
+    ph = _inclusions128()
+    Fbar = np.diag([0.9, 1.0, 1.0])
+    s64, _ = run_gpu(ph, PAR, Fbar, 10.0, -1.0, 2)
+    s32, _ = run_gpu(ph, PAR, Fbar, 10.0, -1.0, 2, precision="fp32")
+    a, b = s32.state(), s64.state()
+    assert rel(a["F"], b["F"]) < 2e-5
+    assert rel(a["u"], b["u"]) < 2e-4
+    assert rel(a["Lam"], b["Lam"]) < 2e-5
