@@ -501,11 +501,13 @@ __device__ __forceinline__ V twiddled(V a, V w) {
 
 // One Stockham transform (sign by INV, unnormalised) of the block's columns.  x: the
 // thread's elements j + T r of column cl, on entry and on exit.  buf: two shared
-// buffers of N * TK values (element-major, column fastest); tw: exp(-2 pi i m / N).
-template <int N, bool INV, typename V>
+// buffers of N * S values (element e of column cl at e S + cl; S >= TK, padded for
+// the x passes); tw: the table exp(-2 pi i m / (N TWS)) (TWS = 2: the half-length
+// transforms of the x passes use every other entry of the grid's table).
+template <int N, bool INV, int TWS = 1, int S = ColPlan<N>::TK, typename V>
 __device__ __forceinline__ void col_fft(V (&x)[8], V* __restrict__ buf, const V* __restrict__ tw, int j, int cl) {
     using P = ColPlan<N>;
-    constexpr int T = P::T, TK = P::TK;
+    constexpr int T = P::T, TK = S;
     __syncthreads();  // the previous transform's readers are done with both buffers
 #pragma unroll
     for (int p = 0; p < P::P8; ++p) {
@@ -517,7 +519,7 @@ __device__ __forceinline__ void col_fft(V (&x)[8], V* __restrict__ buf, const V*
 #pragma unroll
             for (int r = 0; r < 8; ++r) x[r] = in[(j + T * r) * TK + cl];
 #pragma unroll
-            for (int r = 1; r < 8; ++r) x[r] = twiddled<INV>(x[r], tw[k * r * (N / (8 * Ns))]);
+            for (int r = 1; r < 8; ++r) x[r] = twiddled<INV>(x[r], tw[k * r * (N / (8 * Ns)) * TWS]);
         }
         dft8<INV>(x);
         const bool last = (p == P::P8 - 1) && P::RL == 1;
@@ -537,12 +539,190 @@ __device__ __forceinline__ void col_fft(V (&x)[8], V* __restrict__ buf, const V*
 #pragma unroll
             for (int r = 0; r < RL; ++r) {
                 v[r] = in[(b + Ns * r) * TK + cl];
-                if (r > 0) v[r] = twiddled<INV>(v[r], tw[b * r]);
+                if (r > 0) v[r] = twiddled<INV>(v[r], tw[b * r * TWS]);
             }
             if constexpr (RL == 2) dft2<INV>(v);
             else dft4<INV>(v);
 #pragma unroll
             for (int r = 0; r < RL; ++r) x[q + r * Q] = v[r];  // element b + Ns r = j + T (q + r Q)
+        }
+    }
+}
+
+// xfwd_tile and xinv_tile for 3D grids of N in {128, 256, 512}: the half-length
+// transforms (H = N/2) of the block's 4096/N lines run through col_fft with the
+// lines as columns; staging, the stencil and the real-to-complex split are those of
+// the general kernels, in shared buffers padded to a stride of 4096/N + 1 values.
+template <int N>
+struct XPlan {
+    static constexpr int H = N / 2;
+    static constexpr int LPB = ColPlan<H>::TK;  // lines per block
+    static constexpr int S = LPB + 1;            // padded element stride
+    static constexpr int LOGN = N == 128 ? 7 : (N == 256 ? 8 : 9);
+};
+
+template <typename T, int N, int D, bool INCR>
+__device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid) {
+    using V = typename Cx<T>::t;
+    using Args = FftArgs<T>;
+    using X = XPlan<N>;
+    constexpr int H = X::H, LPB = X::LPB, S = X::S, TT = ColPlan<H>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Ctrl* __restrict__ ctrl = L.ctrl;
+    const T* F0 = INCR ? (const T*)L.R32 : Args::F(L, 0);
+    const T* F1 = INCR ? (const T*)L.R32 : Args::F(L, 1);
+    const T* __restrict__ Lam = Args::Lm(L);
+    T* U0 = INCR ? (T*)L.S32 : Args::U(L, 0);
+    T* U1 = INCR ? (T*)L.S32 : Args::U(L, 1);
+    if (ctrl->done) return;
+    constexpr long long Vn = (D == 3) ? (long long)N * N * N : (long long)N * N;
+    constexpr int nlines = (D == 3) ? N * N : N;
+    const int par = (int)(ctrl->k & 1);
+    const T* __restrict__ F = par ? F0 : F1;  // F_{k+1}
+    V* __restrict__ Sp = reinterpret_cast<V*>(par ? U0 : U1);
+    const T inv_rho = (T)ctrl->inv_rho;
+    const T half_n = Args::half_n(L);
+    V* s_tw = reinterpret_cast<V*>(smem_raw);
+    V* buf = s_tw + N;          // two buffers of H * S values
+    V* stage = buf + H * S;     // the second one stages the input lines
+    T* stage_r = reinterpret_cast<T*>(stage);
+    load_twiddles(s_tw, Args::tw(L), N);
+    const int line0 = bid * LPB;
+    const int lt = threadIdx.x % LPB, jt = threadIdx.x / LPB;
+    constexpr long long sn = N, s2 = sn * sn;
+    for (int c = 0; c < D; ++c) {
+        const T* F_c0 = F + (long long)(c * D + 0) * Vn;
+        const T* F_c1 = F + (long long)(c * D + 1) * Vn;
+        const T* L_c0 = INCR ? nullptr : Lam + (long long)(c * D + 0) * Vn;
+        const T* L_c1 = INCR ? nullptr : Lam + (long long)(c * D + 1) * Vn;
+        __syncthreads();  // the previous component's readers of the staging buffer are done
+        for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
+            const int l = idx >> X::LOGN;
+            const int x = idx & (N - 1);
+            const int line = line0 + l;
+            T r = T(0);
+            if (line < nlines) {
+                const int y = line & (N - 1), z = line >> X::LOGN;
+                const long long v = (long long)line * N + x;
+                const long long xp = v + (x + 1 == N ? 1 - N : 1), xm = v + (x == 0 ? N - 1 : -1);
+                const long long yp = v + (y + 1 == N ? (1 - N) * sn : sn), ym = v + (y == 0 ? (N - 1) * sn : -sn);
+                T q = (F_c0[xp] - F_c0[xm]) + (F_c1[yp] - F_c1[ym]);
+                if (!INCR) q -= ((L_c0[xp] - L_c0[xm]) + (L_c1[yp] - L_c1[ym])) * inv_rho;
+                const T* F_c2 = F + (long long)(c * D + 2) * Vn;
+                const long long zp = v + (z + 1 == N ? (1 - N) * s2 : s2);
+                const long long zm = v + (z == 0 ? (N - 1) * s2 : -s2);
+                q += F_c2[zp] - F_c2[zm];
+                if (!INCR) {
+                    const T* L_c2 = Lam + (long long)(c * D + 2) * Vn;
+                    q -= (L_c2[zp] - L_c2[zm]) * inv_rho;
+                }
+                r = -q * half_n;
+            }
+            stage_r[((x >> 1) * S + l) * 2 + (x & 1)] = r;  // z_m = r_{2m} + i r_{2m+1}
+        }
+        __syncthreads();
+        V xr[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) xr[r] = stage[(jt + TT * r) * S + lt];
+        col_fft<H, false, 2, S>(xr, buf, s_tw, jt, lt);
+        __syncthreads();  // col_fft's last readers are done with both buffers
+#pragma unroll
+        for (int r = 0; r < 8; ++r) stage[(jt + TT * r) * S + lt] = xr[r];
+        __syncthreads();
+        V* S_c = Sp + (long long)c * (Vn / 2);
+        for (int idx = threadIdx.x; idx < LPB * H; idx += blockDim.x) {
+            const int l = idx >> (X::LOGN - 1);
+            const int kk = idx & (H - 1);
+            const int line = line0 + l;
+            if (line >= nlines) continue;
+            const V Zk = stage[kk * S + l];
+            V out;
+            if (kk == 0) {
+                out = V{Zk.x + Zk.y, Zk.x - Zk.y};  // (X_0, X_{N/2}) packed
+            } else {
+                const V Zc = cconj(stage[(H - kk) * S + l]);
+                const V E = cscale(cadd(Zk, Zc), T(0.5));
+                const V O = cscale(mul_mi(csub(Zk, Zc)), T(0.5));
+                out = cadd(E, cmul(s_tw[kk], O));
+            }
+            S_c[(long long)line * H + kk] = out;
+        }
+    }
+}
+
+template <typename T, typename TO, int N, int D, bool INCR>
+__device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
+    using V = typename Cx<T>::t;
+    using Args = FftArgs<T>;
+    using X = XPlan<N>;
+    constexpr int H = X::H, LPB = X::LPB, S = X::S, TT = ColPlan<H>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Ctrl* __restrict__ ctrl = L.ctrl;
+    T* S0 = INCR ? (T*)L.S32 : Args::U(L, 0);
+    T* S1 = INCR ? (T*)L.S32 : Args::U(L, 1);
+    TO* O0 = INCR ? (TO*)L.U64[0] : (TO*)Args::U(L, 0);
+    TO* O1 = INCR ? (TO*)L.U64[1] : (TO*)Args::U(L, 1);
+    T* __restrict__ DUout = (T*)L.D32;
+    if (ctrl->done) return;
+    constexpr long long Vn = (D == 3) ? (long long)N * N * N : (long long)N * N;
+    constexpr int nlines = (D == 3) ? N * N : N;
+    const int par = (int)(ctrl->k & 1);
+    V* Sp = reinterpret_cast<V*>(INCR ? S0 : (par ? S0 : S1));
+    TO* Out = par ? O0 : O1;
+    const TO* In = par ? O1 : O0;
+    V* s_tw = reinterpret_cast<V*>(smem_raw);
+    V* buf = s_tw + N;
+    V* stage = buf + H * S;
+    load_twiddles(s_tw, Args::tw(L), N);
+    const int line0 = bid * LPB;
+    const int lt = threadIdx.x % LPB, jt = threadIdx.x / LPB;
+    for (int c = 0; c < D; ++c) {
+        V* S_c = Sp + (long long)c * (Vn / 2);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < LPB * H; idx += blockDim.x) {
+            const int l = idx >> (X::LOGN - 1);
+            const int kk = idx & (H - 1);
+            const int line = line0 + l;
+            V Z = V{T(0), T(0)};
+            if (line < nlines) {
+                const V Xk = S_c[(long long)line * H + kk];
+                if (kk == 0) {
+                    Z = V{T(0.5) * (Xk.x + Xk.y), T(0.5) * (Xk.x - Xk.y)};
+                } else {
+                    const V Xc = cconj(S_c[(long long)line * H + (H - kk)]);
+                    const V E = cscale(cadd(Xk, Xc), T(0.5));
+                    const V O = cmul(cscale(csub(Xk, Xc), T(0.5)), cconj(s_tw[kk]));
+                    Z = cadd(E, mul_i(O));
+                }
+            }
+            stage[kk * S + l] = Z;
+        }
+        __syncthreads();
+        V xr[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) xr[r] = stage[(jt + TT * r) * S + lt];
+        col_fft<H, true, 2, S>(xr, buf, s_tw, jt, lt);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 8; ++r) stage[(jt + TT * r) * S + lt] = xr[r];
+        __syncthreads();
+        const T* stage_r = reinterpret_cast<const T*>(stage);
+        TO* O_c = Out + (long long)c * Vn;
+        const TO* I_c = In + (long long)c * Vn;
+        for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
+            const int l = idx >> X::LOGN;
+            const int xi = idx & (N - 1);
+            const int line = line0 + l;
+            if (line < nlines) {
+                const T v = stage_r[((xi >> 1) * S + l) * 2 + (xi & 1)];
+                const long long o = (long long)line * N + xi;
+                if (INCR) {
+                    O_c[o] = I_c[o] + (TO)v;
+                    DUout[(long long)c * Vn + o] = v;
+                } else {
+                    O_c[o] = (TO)v;
+                }
+            }
         }
     }
 }
@@ -654,6 +834,31 @@ k_faxis_fixed(const Launch* __restrict__ rds, const int2* __restrict__ tiles, in
     }
 }
 
+template <typename T, int N, int D, bool INCR>
+__global__ void __launch_bounds__(kFftThreads)
+k_xfwd_fixed(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        xfwd_fixed_tile<T, N, D, INCR>(rds[tl.x], tl.y);
+        __syncthreads();
+    }
+}
+
+template <typename T, typename TO, int N, int D, bool INCR>
+__global__ void __launch_bounds__(kFftThreads)
+k_xinv_fixed(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        xinv_fixed_tile<T, TO, N, D, INCR>(rds[tl.x], tl.y);
+        __syncthreads();
+    }
+}
+
+template <typename T, int N>
+constexpr size_t xfixed_smem() {
+    return (size_t)(N + 2 * XPlan<N>::H * XPlan<N>::S) * sizeof(typename Cx<T>::t);
+}
+
 template <typename T, int N>
 constexpr size_t fixed_smem() {
     return (size_t)(N + 2 * N * ColPlan<N>::TK) * sizeof(typename Cx<T>::t);
@@ -692,6 +897,53 @@ void go_axis(const Exec& E, int cls, size_t sma) {
     go(k_faxis<T, D, AXIS, MODE, INCR>, E, cls, sma);
 }
 
+// x passes: the fixed-length kernels under the same conditions (3D, one N of 128, 256
+// or 512 for every member, lines per block of the fixed kernels).
+template <typename T, int D, bool INCR>
+void go_xfwd(const Exec& E, size_t smx) {
+    if constexpr (D == 3) {
+        const int lpb = E.rep->lpb;
+        switch (E.uniform_n) {
+            case 128:
+                if (lpb == XPlan<128>::LPB) return go(k_xfwd_fixed<T, 128, D, INCR>, E, kTilesX, xfixed_smem<T, 128>());
+                break;
+            case 256:
+                if (lpb == XPlan<256>::LPB) return go(k_xfwd_fixed<T, 256, D, INCR>, E, kTilesX, xfixed_smem<T, 256>());
+                break;
+            case 512:
+                if (lpb == XPlan<512>::LPB) return go(k_xfwd_fixed<T, 512, D, INCR>, E, kTilesX, xfixed_smem<T, 512>());
+                break;
+            default:
+                break;
+        }
+    }
+    go(k_xfwd<T, D, INCR>, E, kTilesX, smx);
+}
+
+template <typename T, typename TO, int D, bool INCR>
+void go_xinv(const Exec& E, size_t smx) {
+    if constexpr (D == 3) {
+        const int lpb = E.rep->lpb;
+        switch (E.uniform_n) {
+            case 128:
+                if (lpb == XPlan<128>::LPB)
+                    return go(k_xinv_fixed<T, TO, 128, D, INCR>, E, kTilesX, xfixed_smem<T, 128>());
+                break;
+            case 256:
+                if (lpb == XPlan<256>::LPB)
+                    return go(k_xinv_fixed<T, TO, 256, D, INCR>, E, kTilesX, xfixed_smem<T, 256>());
+                break;
+            case 512:
+                if (lpb == XPlan<512>::LPB)
+                    return go(k_xinv_fixed<T, TO, 512, D, INCR>, E, kTilesX, xfixed_smem<T, 512>());
+                break;
+            default:
+                break;
+        }
+    }
+    go(k_xinv<T, TO, D, INCR>, E, kTilesX, smx);
+}
+
 // stage < 0: all passes of one iteration; otherwise only pass `stage`
 // (3D: 0 x-forward, 1 y-forward, 2 z solve, 3 y-inverse, 4 x-inverse;
 //  2D: 0 x-forward, 1 y solve, 2 x-inverse).  INCR: the float increment
@@ -704,7 +956,7 @@ cudaError_t run_fft(const Exec& E, int stage) {
     const int last = D == 3 ? 4 : 2;
     auto want = [&](int s) { return stage < 0 || stage == s; };
     static_assert(!INCR || std::is_same<T, float>::value, "increment projection runs in float");
-    if (want(0)) go(k_xfwd<T, D, INCR>, E, kTilesX, smx);
+    if (want(0)) go_xfwd<T, D, INCR>(E, smx);
     if constexpr (D == 3) {
         if (want(1)) go_axis<T, D, 1, 0, INCR>(E, ax, sma);
         if (want(2)) go_axis<T, D, 2, 2, INCR>(E, ax, sma);
@@ -714,9 +966,9 @@ cudaError_t run_fft(const Exec& E, int stage) {
     }
     if (want(last)) {
         if constexpr (INCR)
-            go(k_xinv<float, double, D, true>, E, kTilesX, smx);
+            go_xinv<float, double, D, true>(E, smx);
         else
-            go(k_xinv<T, T, D, false>, E, kTilesX, smx);
+            go_xinv<T, T, D, false>(E, smx);
     }
     return cudaGetLastError();
 }
@@ -737,6 +989,12 @@ cudaError_t set_smem_attrs(int bytes) {
     if constexpr (D == 3) {
         auto fixed = [&](auto tag) {
             constexpr int N = decltype(tag)::value;
+            set((const void*)k_xfwd_fixed<T, N, D, false>);
+            set((const void*)k_xinv_fixed<T, T, N, D, false>);
+            if constexpr (std::is_same<T, float>::value) {
+                set((const void*)k_xfwd_fixed<float, N, D, true>);
+                set((const void*)k_xinv_fixed<float, double, N, D, true>);
+            }
             set((const void*)k_faxis_fixed<T, N, D, 1, 0, false>);
             set((const void*)k_faxis_fixed<T, N, D, 1, 1, false>);
             set((const void*)k_faxis_fixed<T, N, D, 2, 2, false>);
@@ -814,7 +1072,10 @@ Geometry default_geometry(int dim, int n) {
     g.tk32 = FftArgs<float>::tk < H ? FftArgs<float>::tk : H;
     while (g.tk64 > 1 && ax_blocks(g.tk64) < want_blocks) g.tk64 /= 2;
     while (g.tk32 > 1 && ax_blocks(g.tk32) < want_blocks) g.tk32 /= 2;
-    if (dim == 3 && (n == 128 || n == 256 || n == 512)) g.tk64 = g.tk32 = 2048 / n;  // fixed-length y/z kernels
+    if (dim == 3 && (n == 128 || n == 256 || n == 512)) {  // the fixed-length kernels' tiles
+        g.tk64 = g.tk32 = 2048 / n;
+        g.lpb = 4096 / n;
+    }
     g.np_half = factor_radices(H, g.rad_half);
     g.np_full = factor_radices(n, g.rad_full);
     return g;
