@@ -94,6 +94,16 @@ typedef struct rve_options {
                            pointwise bound implies r_l <= f r_d.  Not applied to the
                            increment-form steps of the RVE_MIXED polish.  Default 0
                            (exact local solves).                                   */
+    double local_fraction; /* p in (0, 1], elastic laws: fraction-converged local steps (Section
+                           4.2's first strategy: proceed once a fraction p of the
+                           voxels met the pointwise Newton test, checked every two
+                           local iterations).  Built without a grid-wide barrier:
+                           each voxel's Newton is capped at K, the smallest even
+                           count by which a fraction p converged in the previous
+                           pass (K + 2 if fewer converged within K, at most
+                           newton_max); the first two local steps of a solve use
+                           newton_max.  Not applied to the increment-form steps of
+                           the RVE_MIXED polish.  Default 0 (off).                 */
 } rve_options;
 
 /* Fill *opt with the defaults listed above. */

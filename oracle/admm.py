@@ -123,7 +123,8 @@ def _to_field(Tv: np.ndarray, grid_shape) -> np.ndarray:
     return Tv.transpose(1, 2, 0).reshape((d, d) + tuple(grid_shape))
 
 
-def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, small_step=1e-7, grad_tol=0.0):
+def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, small_step=1e-7, grad_tol=0.0,
+                 return_conv=False):
     """Step 1 at every voxel: minimise phi(F) = W(F) - Lam:F + rho/2 |F - G|^2.
 
     Damped Newton from F0 with the analytic Hessian W_FF + rho I.  When the Newton
@@ -139,7 +140,8 @@ def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, smal
     norm |grad phi| <= grad_tol.  A voxel that met the step test is then stopped at
     the next evaluation, so that every voxel ends on an evaluated gradient.
 
-    All arrays are per voxel: F0, Lam, G of shape (V, d, d).  Returns (F, iters).
+    All arrays are per voxel: F0, Lam, G of shape (V, d, d).  Returns (F, iters), and
+    with return_conv=True also the mask of voxels that met a stopping test.
     """
     V, d, _ = F0.shape
     n2 = d * d
@@ -147,6 +149,7 @@ def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, smal
     iters = np.zeros(V, dtype=np.int64)
     active = np.ones(V, dtype=bool)
     small = np.zeros(V, dtype=bool)
+    conv = np.zeros(V, dtype=bool)
 
     def phi(sub, Fs, Lam_s, G_s):
         return (sub.W(Fs) - np.einsum("vij,vij->v", Lam_s, Fs)
@@ -164,6 +167,7 @@ def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, smal
         if grad_tol > 0.0:
             stop = small[idx] | (np.sqrt(np.einsum("vij,vij->v", g, g)) <= grad_tol)
             active[idx[stop]] = False
+            conv[idx[stop]] = True
             keep = ~stop
             idx, Fa, Lam_s, G_s, g = idx[keep], Fa[keep], Lam_s[keep], G_s[keep], g[keep]
             if idx.size == 0:
@@ -208,7 +212,21 @@ def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, smal
             small[idx[done]] = True
         else:
             active[idx[done]] = False
-    return F, iters
+            conv[idx[done]] = True
+    return (F, iters, conv) if return_conv else (F, iters)
+
+
+def fraction_cap(iters, conv, fraction, cap, cap_max, bins=16):
+    """Section 4.2's first strategy (proceed once a fraction of the points converged,
+    checked every two local iterations), with one pass of lag: the next pass's
+    Newton cap is the smallest even count 2b (b <= bins) by which at least
+    fraction * V voxels met their test in this pass; if fewer did, cap + 2; never
+    above cap_max."""
+    V = iters.size
+    b = np.minimum(np.maximum(iters[conv] + 1, 2) // 2, bins) - 1
+    cum = np.cumsum(np.bincount(b, minlength=bins)[:bins])
+    hit = np.nonzero(cum >= fraction * V)[0]
+    return min(2 * (int(hit[0]) + 1), cap_max) if hit.size else min(cap + 2, cap_max)
 
 
 def local_residual(mat, F, Lam, G, rho, mu_ref, n=None, force=None):
@@ -400,7 +418,8 @@ def initial_state(mat, Fbar_d: np.ndarray, grid_shape, lambda0: str = "stress", 
 
 def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_ref=None,
                lambda0="stress", state=None, rho_policy="fixed", kappa=1.3, tau=10.0,
-               rho_min=None, local_cap=50, step_tol=1e-10, n0=None, local_ratio=0.0, free=None):
+               rho_min=None, local_cap=50, step_tol=1e-10, n0=None, local_ratio=0.0, free=None,
+               local_fraction=0.0):
     """Run the ADMM iteration (Steps 1-4) until r_p <= tol and r_d <= tol, or max_iter.
 
     phase: uint8 grid (N,)*d; params: per-phase (mu, lam); Fbar: 3x3 (the upper-left
@@ -421,6 +440,10 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
     (the fluctuation Du~ has zero mean), so that <Lambda>_free = 0 after every
     multiplier update and <W_F(F)>_free -> 0 at convergence.  Fbar gives their
     starting values; out["Fbar"] holds the final macroscopic gradient (3 x 3).
+
+    local_fraction = p > 0 (elastic laws): fraction-converged local steps with the
+    Newton cap of fraction_cap, set from each pass's counts for the next pass (the
+    first two passes use local_cap); out["newton_caps"] lists the cap of every pass.
     """
     phase = np.asarray(phase)
     d = phase.ndim
@@ -442,6 +465,8 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
     G = Fbar_d.reshape((d, d) + (1,) * d) + grad_u(u)
     history = []
     local_res = []
+    caps = []
+    cap = local_cap
     converged = False
     it = 0
     for it in range(1, max_iter + 1):
@@ -455,7 +480,11 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
             nd = nv.T.reshape((3,) + tuple(grid))
             local_res.append(local_residual(mat, Fv, Lv, Gv, rho, mu_ref, nv, force) if local_ratio > 0.0 else 0.0)
         else:
-            Fv, _ = local_newton(mat, _to_voxels(F), Lv, Gv, rho, step_tol=step_tol, cap=local_cap, grad_tol=gtol)
+            Fv, iters_v, conv_v = local_newton(mat, _to_voxels(F), Lv, Gv, rho, step_tol=step_tol, cap=cap,
+                                               grad_tol=gtol, return_conv=True)
+            caps.append(cap)
+            if local_fraction > 0.0 and it >= 2:
+                cap = fraction_cap(iters_v, conv_v, local_fraction, cap, local_cap)
             local_res.append(local_residual(mat, Fv, Lv, Gv, rho, mu_ref) if local_ratio > 0.0 else 0.0)
         F = _to_field(Fv, grid)
         # Step 2 (with the free mean components of mixed control)
@@ -487,7 +516,7 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
         stress = np.mean(mat.P(_to_voxels(F)), axis=0)
     out = {"F": F, "Lam": Lam, "u": u, "iters": it if max_iter > 0 else 0,
            "converged": converged, "history": history, "rho": rho,
-           "stress": stress, "mu_ref": mu_ref, "local_residual": local_res}
+           "stress": stress, "mu_ref": mu_ref, "local_residual": local_res, "newton_caps": caps}
     Fb3 = np.array(np.asarray(Fbar, dtype=np.float64))
     Fb3[:d, :d] = Fbar_d
     out["Fbar"] = Fb3

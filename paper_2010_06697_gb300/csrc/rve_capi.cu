@@ -217,8 +217,11 @@ int begin_solve(rve* h, const double Fbar[9], double rho, double tol, cudaStream
     c.adaptive = o.rho_policy == RVE_RHO_ADAPTIVE;
     c.rho_changed = 0;
     c.newton_cap = o.newton_max;
+    for (int b = 0; b < admm::kNewtonBins; ++b) c.newton_hist[b] = 0u;
     c.hist_cap = o.max_iter + 1;
     c.local_ratio = o.local_ratio;
+    c.local_fraction = o.local_fraction;
+    c.newton_cap_max = o.newton_max;
     c.r_d = 0.0;  // no check yet: the first two local steps of the solve are exact
     c.rd_local = 0.0;
     c.r_l = 0.0;
@@ -504,6 +507,7 @@ int check_options(const rve_options& o) {
     if (!(o.mu_ref >= 0) || !(o.mixed_switch >= 0)) return RVE_E_INVALID_ARG;
     if (o.check_every < 1 || o.check_every > 4096) return RVE_E_INVALID_ARG;
     if (!(o.local_ratio >= 0) || !(o.local_ratio <= 1e6)) return RVE_E_INVALID_ARG;
+    if (!(o.local_fraction >= 0) || !(o.local_fraction <= 1)) return RVE_E_INVALID_ARG;
     return RVE_OK;
 }
 
@@ -694,6 +698,7 @@ void rve_default_options(rve_options* o) {
     o->check_every = 16;
     o->use_graph = 1;
     o->local_ratio = 0.0;
+    o->local_fraction = 0.0;
 }
 
 size_t rve_workspace_bytes(int dim, int n, int model, const rve_options* opt) {

@@ -11,6 +11,9 @@ constexpr int kLocalThreads = 128;    // threads per block of the local-step ker
 constexpr int kFftThreads = 256;      // threads per block of the FFT kernels
 constexpr int kMaxParam = 8;          // per-phase material constants
 constexpr int kPartialStride = 20;
+// fraction-converged local steps: counts of voxels whose Newton met its test within
+// 2, 4, ..., 2 kNewtonBins iterations
+constexpr int kNewtonBins = 16;
 // residual history entry per iteration: r_p, r_d, rho of the check, then r_l of the
 // local step fused into the same pass (the next iteration's Step 1)
 constexpr int kHistStride = 4;    // doubles per block in the partial-sum buffer
@@ -33,6 +36,9 @@ struct Ctrl {
     double best;         // best max(r_p, r_d) of the float phase (stagnation test)
     double r_p, r_d;     // residuals of the last completed iteration
     double local_ratio;  // f > 0: inexact local steps, |grad phi| <= f mu_ref r_d per voxel
+    double local_fraction; // p > 0: Newton capped where a fraction p of voxels converged
+    int newton_cap_max;  // the configured per-voxel Newton cap
+    unsigned int newton_hist[kNewtonBins];  // this pass's converged-voxel counts (zeroed by the last block)
     double rd_local;     // r_d of the check before the last one (the redone local step's)
     double r_l;          // local residual of the last fused pass's local step (f > 0 only)
     double Fbar_prev[9]; // <F> of the previous iteration (r_d under mixed control)

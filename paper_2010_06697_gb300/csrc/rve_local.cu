@@ -1109,6 +1109,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     __shared__ double s_sum[kLocalThreads / 32][3];
     __shared__ int s_int[kLocalThreads / 32][2];
     __shared__ int s_last;
+    __shared__ int s_hist[kNewtonBins];       // fraction-converged local steps
 
     // the increment form needs the previous iteration's R: never the first step of a run
     constexpr bool INC = WRITE_R && DU && MODEL != kLce && std::is_same<T, double>::value;
@@ -1165,6 +1166,13 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     // sums near 1e-6, ample for the tolerance tests), double otherwise; the block and
     // grid sums are always double
     using Acc = typename std::conditional<sizeof(T) == 4 || INC, float, double>::type;
+    // Section 4.2's first strategy (fraction-converged local steps): this pass's
+    // histogram of Newton counts sets the next pass's cap (one pass of lag, no barrier)
+    const bool frac_on = !INC && !FIRST && MODEL != kLce && ctrl->local_fraction > 0.0;
+    if (frac_on) {
+        if (threadIdx.x < kNewtonBins) s_hist[threadIdx.x] = 0;
+        __syncthreads();
+    }
     Acc rp2a = Acc(0), rd2a = Acc(0), rl2a = Acc(0);
     int nmax = 0, nfail = 0;
     const int chunk = L.local_chunk;
@@ -1255,6 +1263,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
         }
         nmax = max(nmax, it);
         nfail += conv ? 0 : 1;
+        if (frac_on && conv) atomicAdd(&s_hist[min(max(it + 1, 2) / 2, kNewtonBins) - 1], 1);
 #pragma unroll
         for (int p = 0; p < NN; ++p) Fnext[p * V + v] = F[p];
         if constexpr (WRITE_R) {
@@ -1296,6 +1305,9 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
         pp[2] = (double)mx;
         pp[3] = (double)nf;
         pp[4] = cl;
+        if (frac_on)
+            for (int b = 0; b < kNewtonBins; ++b)
+                if (s_hist[b]) atomicAdd(&ctrl->newton_hist[b], (unsigned)s_hist[b]);
         __threadfence();
         const unsigned prev = atomicAdd(&ctrl->counter, 1u);
         s_last = (prev == nblk - 1);
@@ -1370,6 +1382,23 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     c->k = k + 1;
     c->newton_max = mx;
     c->newton_fail = (unsigned long long)nft;
+    if (frac_on) {
+        // the smallest even count by which a fraction p of the voxels converged; if
+        // fewer converged within the cap, raise the cap by 2 (up to the configured one)
+        const double need = c->local_fraction * (double)V;
+        int cap_next = min(c->newton_cap + 2, c->newton_cap_max);
+        double cum = 0.0;
+        bool found = false;
+        for (int bin = 0; bin < kNewtonBins; ++bin) {
+            cum += (double)__ldcg(&c->newton_hist[bin]);
+            if (!found && cum >= need) {
+                cap_next = min(2 * (bin + 1), c->newton_cap_max);
+                found = true;
+            }
+            c->newton_hist[bin] = 0u;
+        }
+        c->newton_cap = cap_next;
+    }
     int done = kRunning;
     if (!(isfinite(r_p) && isfinite(r_d))) {
         done = kNumerical;

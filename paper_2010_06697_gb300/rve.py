@@ -56,6 +56,7 @@ class rve_options(ctypes.Structure):
         ("check_every", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("local_ratio", ctypes.c_double),
+        ("local_fraction", ctypes.c_double),
     ]
 
 

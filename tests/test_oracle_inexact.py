@@ -66,3 +66,32 @@ def test_local_residual_definition():
     want = np.sqrt(np.mean(np.sum(dg * dg, axis=(1, 2)))) / mu_ref
     got = oadmm.local_residual(mat, F + dF, Lam, G, rho, mu_ref)
     assert abs(got - want) < 1e-9 * want
+
+
+# ------------------------------------------------------------------ fraction-converged local steps
+
+def test_fraction_cap_rule():
+    """The cap rule on hand-counted Newton counts: bins of 2 iterations, cumulative."""
+    iters = np.array([1, 1, 2, 3, 5, 7])
+    conv = np.ones(6, bool)
+    assert oadmm.fraction_cap(iters, conv, 0.5, 30, 30) == 2     # 3 of 6 within 2
+    assert oadmm.fraction_cap(iters, conv, 0.8, 30, 30) == 6     # 5 of 6 within 6 (need 4.8)
+    assert oadmm.fraction_cap(iters, conv, 1.0, 30, 30) == 8
+    conv[5] = False                                               # the 7-step voxel hit the cap
+    assert oadmm.fraction_cap(iters, conv, 0.9, 8, 30) == 10      # only 5 of 6 converged: cap + 2
+    assert oadmm.fraction_cap(iters, conv, 0.9, 30, 30) == 30     # never above the configured cap
+
+
+@pytest.mark.parametrize("model,d,n", [("linear", 2, 16), ("neohookean", 3, 8)])
+def test_fraction_converged_steps_reach_laminate_closed_form(model, d, n):
+    rng = np.random.default_rng(6)
+    ph = synth.laminate_phase(n, d)
+    par = synth.two_phase_params(1.0, 10.0)
+    Fbar3 = np.eye(3)
+    Fbar3[:d, :d] = _near_identity(d, 0.06, rng)
+    _, _, S = _laminate_exact(model, par, Fbar3[:d, :d])
+    r = oracle.admm_solve(ph, par, Fbar3, 10.0, 1e-12, 3000, model=model, local_fraction=0.5)
+    assert r["converged"]
+    np.testing.assert_allclose(r["stress"], S, atol=1e-9)
+    caps = np.array(r["newton_caps"])
+    assert caps[0] == caps[1] == 50 and np.all(caps >= 2) and np.all(caps % 2 == 0)
