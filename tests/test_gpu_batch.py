@@ -97,3 +97,24 @@ def test_batch_rejects_mixed_precision_and_duplicates():
     assert rc == rve.RVE_E_INVALID_ARG
     rc, _ = rve.rve_batch_create([a.h, a.h])
     assert rc == rve.RVE_E_INVALID_ARG
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_uniform_batch_fixed_length_kernels_bitwise(precision):
+    """Three 128^3 members (one grid size: the batched passes take the fixed-length FFT
+    kernels, as a single handle does): bitwise equal to solving each alone."""
+    specs = [(3, 128, "inclusion", 11), (3, 128, "laminate", 12), (3, 128, "inclusion", 13)]
+    Fb = fbars(len(specs), 50)
+    alone = members(specs, precision, max_iter=60)
+    ref = []
+    for s, F in zip(alone, Fb):
+        s.solve(F, 10.0, -1.0)
+        ref.append((s.state(), s.stress()))
+        s.close()
+    mix = members(specs, precision, max_iter=60)
+    rve.Batch(mix).solve(Fb, np.full(len(specs), 10.0), -1.0)
+    for s, (st, S) in zip(mix, ref):
+        st2 = s.state()
+        for k in st:
+            assert np.array_equal(st2[k], st[k]), k
+        assert np.array_equal(s.stress(), S)

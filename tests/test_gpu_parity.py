@@ -51,7 +51,8 @@ def run_gpu(ph, par, Fbar, rho, tol, max_iter, model="neohookean", precision="fp
 
 SIZES = [("laminate", 2, 32), ("inclusion", 2, 48), ("inclusion", 2, 6), ("inclusion", 2, 36),
          ("laminate", 3, 8), ("inclusion", 3, 12), ("inclusion", 3, 16), ("inclusion", 3, 24),
-         ("inclusion", 3, 6), ("inclusion", 3, 18)]
+         ("inclusion", 3, 6), ("inclusion", 3, 18),
+         ("inclusion", 3, 4), ("laminate", 2, 4), ("inclusion", 2, 512)]  # smallest and largest 2D grids
 
 
 @pytest.mark.parametrize("kind,d,n", SIZES)
