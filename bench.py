@@ -55,8 +55,8 @@ def bytes_per_voxel(cls: str, s: int, d: int = 3) -> float:
 # DRAM bytes (read + write) per launch measured with ncu on the 128^3 inclusion cell
 # (profiles/), keyed by (kernel class, precision); absent = not captured since the
 # kernel last changed
-TRAFFIC = {("local", "fp32"): 220838144 + 120816384, ("local_r", "fp64"): 421992704 + 358247936,
-           ("xfwd", "fp32"): 151885056 + 13613312, ("solve", "fp32"): 25204480}
+TRAFFIC = {("local", "fp32"): 220703232 + 120778240, ("local_r", "fp64"): 421989120 + 358003456,
+           ("xfwd", "fp32"): 151043840 + 11952640, ("solve", "fp32"): 25196800}
 
 
 def combine_ranks(ms, vox_it, dist=None, device="cpu"):

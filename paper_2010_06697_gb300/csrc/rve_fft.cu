@@ -589,36 +589,34 @@ __device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid) {
     load_twiddles(s_tw, Args::tw(L), N);
     const int line0 = bid * LPB;
     const int lt = threadIdx.x % LPB, jt = threadIdx.x / LPB;
-    constexpr long long sn = N, s2 = sn * sn;
+    // a tile's LPB lines are consecutive y of one z plane (LPB divides N): the z
+    // neighbours are fixed offsets.  Voxel indices fit 32 bits (N^3 < 2^31); the
+    // increment variant runs faster with them, the plain one (twice the loads) with
+    // 64-bit ones (measured on GB300)
+    using Idx = typename std::conditional<INCR, int, long long>::type;
+    const int z = line0 >> X::LOGN, y0 = line0 & (N - 1);
+    constexpr Idx sn = N, s2 = (Idx)N * N;
+    const Idx zp = (z + 1 == N ? (1 - N) * s2 : s2), zm = (z == 0 ? (N - 1) * s2 : -s2);
     for (int c = 0; c < D; ++c) {
         const T* F_c0 = F + (long long)(c * D + 0) * Vn;
         const T* F_c1 = F + (long long)(c * D + 1) * Vn;
+        const T* F_c2 = F + (long long)(c * D + 2) * Vn;
         const T* L_c0 = INCR ? nullptr : Lam + (long long)(c * D + 0) * Vn;
         const T* L_c1 = INCR ? nullptr : Lam + (long long)(c * D + 1) * Vn;
+        const T* L_c2 = INCR ? nullptr : Lam + (long long)(c * D + 2) * Vn;
         __syncthreads();  // the previous component's readers of the staging buffer are done
         for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
             const int l = idx >> X::LOGN;
             const int x = idx & (N - 1);
-            const int line = line0 + l;
-            T r = T(0);
-            if (line < nlines) {
-                const int y = line & (N - 1), z = line >> X::LOGN;
-                const long long v = (long long)line * N + x;
-                const long long xp = v + (x + 1 == N ? 1 - N : 1), xm = v + (x == 0 ? N - 1 : -1);
-                const long long yp = v + (y + 1 == N ? (1 - N) * sn : sn), ym = v + (y == 0 ? (N - 1) * sn : -sn);
-                T q = (F_c0[xp] - F_c0[xm]) + (F_c1[yp] - F_c1[ym]);
-                if (!INCR) q -= ((L_c0[xp] - L_c0[xm]) + (L_c1[yp] - L_c1[ym])) * inv_rho;
-                const T* F_c2 = F + (long long)(c * D + 2) * Vn;
-                const long long zp = v + (z + 1 == N ? (1 - N) * s2 : s2);
-                const long long zm = v + (z == 0 ? (N - 1) * s2 : -s2);
-                q += F_c2[zp] - F_c2[zm];
-                if (!INCR) {
-                    const T* L_c2 = Lam + (long long)(c * D + 2) * Vn;
-                    q -= (L_c2[zp] - L_c2[zm]) * inv_rho;
-                }
-                r = -q * half_n;
-            }
-            stage_r[((x >> 1) * S + l) * 2 + (x & 1)] = r;  // z_m = r_{2m} + i r_{2m+1}
+            const int y = y0 + l;
+            const Idx v = (Idx)line0 * N + idx;
+            const Idx xp = v + (x + 1 == N ? 1 - N : 1), xm = v + (x == 0 ? N - 1 : -1);
+            const Idx yp = v + (y + 1 == N ? (1 - N) * sn : sn), ym = v + (y == 0 ? (N - 1) * sn : -sn);
+            T q = (F_c0[xp] - F_c0[xm]) + (F_c1[yp] - F_c1[ym]);
+            if (!INCR) q -= ((L_c0[xp] - L_c0[xm]) + (L_c1[yp] - L_c1[ym])) * inv_rho;
+            q += F_c2[v + zp] - F_c2[v + zm];
+            if (!INCR) q -= (L_c2[v + zp] - L_c2[v + zm]) * inv_rho;
+            stage_r[((x >> 1) * S + l) * 2 + (x & 1)] = -q * half_n;  // z_m = r_{2m} + i r_{2m+1}
         }
         __syncthreads();
         V xr[8];
