@@ -161,6 +161,11 @@ void rve_destroy(rve_t h);
  * nparam too small, missing n0), RVE_E_CUDA. */
 int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* params, int nparam,
                      const double* n0);
+/* RVE_LCE parameters per phase: mu, lambda, r, alpha, kappa_F (Section 5.1 with the
+ * readings of the build), optionally nu_F/dt and nu_n/dt: the dissipation weights of
+ * one implicit time step, dt D((F - F^n)/dt, (n - n^n)/dt) = nu_F/(2 dt) |F - F^n|^2 +
+ * nu_n/(2 dt) |n - n^n|^2, with (F^n, n^n) the state the solve starts from (default 0:
+ * the equilibrium problem).  <S> then includes the viscous part nu_F/dt (F - F^n). */
 
 /* ------------------------------------------------------------------ solve */
 /* Run ADMM iterations (Section 2.1, Steps 1-4) at macroscopic gradient Fbar
@@ -189,6 +194,18 @@ int rve_solve_mixed(rve_t h, const double Fbar[9], unsigned free_mask, double rh
 
 /* Current macroscopic gradient <F> (row-major 3x3; prescribed and free parts). */
 int rve_macro_gradient(rve_t h, double F[9]);
+
+/* A loading path (Section 5.3: quasi-static steps along UNI, PE or EB with the
+ * implicit time discretisation of Section 5.1): `steps` solves in order, each warm
+ * started from the previous state, which is also the previous time step of the LCE
+ * dissipation terms.  Fbars[9 s ...] gives step s's prescribed <F> (row-major);
+ * components in free_mask (as in rve_solve_mixed) start from the previous step's
+ * result.  Per step: S_out[9 s ...] = <S> after the step, Fbar_out[9 s ...] = <F>
+ * (either may be NULL), infos[s] (may be NULL).  Returns RVE_OK, or
+ * RVE_E_NOT_CONVERGED if some step stopped at max_iter (all steps still run), or
+ * the first other error. */
+int rve_solve_path(rve_t h, const double* Fbars, int steps, unsigned free_mask, double rho, double tol,
+                   double* S_out, double* Fbar_out, rve_solve_info* infos);
 
 /* Homogenised first Piola-Kirchhoff stress <W_F(F)> of the current state,
  * summed in double on the device (Section 2.3: <S> is the macroscopic stress). */

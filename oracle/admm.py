@@ -229,7 +229,7 @@ def fraction_cap(iters, conv, fraction, cap, cap_max, bins=16):
     return min(2 * (int(hit[0]) + 1), cap_max) if hit.size else min(cap + 2, cap_max)
 
 
-def local_residual(mat, F, Lam, G, rho, mu_ref, n=None, force=None):
+def local_residual(mat, F, Lam, G, rho, mu_ref, n=None, force=None, Fprev=None, nprev=None):
     """r_l of Section 2.1: the unit-cell L2 norm of the local optimality residual
     grad phi = W_F(F) - Lam + rho (F - G) at the local step's result, over mu_ref
     (read as a norm, like r_p and r_d).  For the LCE the two tangential components
@@ -241,6 +241,9 @@ def local_residual(mat, F, Lam, G, rho, mu_ref, n=None, force=None):
         P, Wn, _, _, _ = mat.derivatives(F, n)
         gF = P - Lam + rho * (F - G)
         gn = Wn - force
+        if Fprev is not None:  # dissipation terms of the LCE time step
+            gF = gF + mat.cF[:, None, None] * (F - Fprev)
+            gn = gn + mat.cn[:, None] * (n - nprev)
         a, b = tangent_basis(n)
         s2 = (np.einsum("vij,vij->v", gF, gF) + np.sum(gn * a, axis=1) ** 2 + np.sum(gn * b, axis=1) ** 2)
     return float(np.sqrt(np.mean(s2))) / mu_ref
@@ -286,7 +289,7 @@ def retract(n, a, b, t1, t2):
 
 
 def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60, armijo=1e-4, small_step=1e-7,
-                     grad_tol=0.0):
+                     grad_tol=0.0, Fprev=None, nprev=None):
     """Step 1 (eqs. eq and kin with the Frank gradient treated explicitly, eq. kin2) for
     the LCE at every voxel: minimise over F and the unit director n
 
@@ -297,7 +300,14 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
     sphere's curvature term -(n . phi_n) I, plus a shift 1e-6 mu I on that block.  Backtracking keeps J > 0 and the Armijo
     decrease; steepest descent when Newton's direction does not descend.  grad_tol:
     the inexact stop of local_newton on the norm of the 11-component gradient.
+    Fprev, nprev (V,3,3), (V,3): the previous time step's fields; with the material's
+    dissipation weights cF = nu_F/dt, cn = nu_n/dt the objective gains Section 5.1's
+    dt D((F - Fprev)/dt, (n - nprev)/dt) = cF/2 |F - Fprev|^2 + cn/2 |n - nprev|^2.
     F0, Lam, G (V,3,3); n_init, force (V,3).  Returns (F, n, iters)."""
+    if Fprev is None:
+        Fprev = F0
+    if nprev is None:
+        nprev = n_init
     V = F0.shape[0]
     F = F0.copy()
     n = n_init.copy()
@@ -305,9 +315,11 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
     active = np.ones(V, dtype=bool)
     small = np.zeros(V, dtype=bool)
 
-    def phi(sub, Fs, ns, Lam_s, G_s, f_s):
+    def phi(sub, Fs, ns, Lam_s, G_s, f_s, Fp, np_):
+        dF, dn = Fs - Fp, ns - np_
         return (sub.W(Fs, ns) - np.sum(f_s * ns, axis=1) - np.einsum("vij,vij->v", Lam_s, Fs)
-                + 0.5 * rho * np.einsum("vij,vij->v", Fs - G_s, Fs - G_s))
+                + 0.5 * rho * np.einsum("vij,vij->v", Fs - G_s, Fs - G_s)
+                + 0.5 * sub.cF * np.einsum("vij,vij->v", dF, dF) + 0.5 * sub.cn * np.sum(dn * dn, axis=1))
 
     for _ in range(cap + 1):
         idx = np.nonzero(active)[0]
@@ -317,9 +329,10 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
             sub = mat.subset(idx)
             Fa, na = F[idx], n[idx]
             Lam_s, G_s, f_s = Lam[idx], G[idx], force[idx]
+            Fp_s, np_s = Fprev[idx], nprev[idx]
             P, Wn, WFF, WFn, Wnn = sub.derivatives(Fa, na)
-            gF = P - Lam_s + rho * (Fa - G_s)
-            gn = Wn - f_s
+            gF = P - Lam_s + rho * (Fa - G_s) + sub.cF[:, None, None] * (Fa - Fp_s)
+            gn = Wn - f_s + sub.cn[:, None] * (na - np_s)
             a, b = tangent_basis(na)
             E = np.stack([a, b], axis=2)                                   # (v, 3, 2)
             gt = np.einsum("vk,vka->va", gn, E)
@@ -338,7 +351,8 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
         Htt = np.einsum("vka,vkp,vpb->vab", E, Wnn, E) - np.sum(na * gn, axis=1)[:, None, None] * np.eye(2)[None]
         HFt = np.einsum("vklp,vpb->vklb", WFn, E).reshape(-1, 9, 2)
         H = np.zeros((idx.size, 11, 11))
-        H[:, :9, :9] = WFF.reshape(-1, 9, 9) + rho * np.eye(9)[None]
+        H[:, :9, :9] = WFF.reshape(-1, 9, 9) + (rho + sub.cF)[:, None, None] * np.eye(9)[None]
+        Htt = Htt + sub.cn[:, None, None] * np.eye(2)[None]
         H[:, :9, 9:] = HFt
         H[:, 9:, :9] = HFt.transpose(0, 2, 1)
         # Levenberg shift on the two director unknowns: keeps the step defined where W does
@@ -351,7 +365,7 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
         if np.any(bad):
             delta[bad] = -g[bad]
             slope[bad] = -np.sum(g[bad] * g[bad], axis=1)
-        phi0 = phi(sub, Fa, na, Lam_s, G_s, f_s)
+        phi0 = phi(sub, Fa, na, Lam_s, G_s, f_s, Fp_s, np_s)
         size = np.max(np.abs(delta), axis=1)
         t = np.ones(idx.size)
         accepted = np.zeros(idx.size, dtype=bool)
@@ -364,7 +378,7 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
             J = np.linalg.det(Ft)
             ok = J > 0.0
             with np.errstate(invalid="ignore", divide="ignore"):
-                ph = phi(sub, Ft, nt, Lam_s, G_s, f_s)
+                ph = phi(sub, Ft, nt, Lam_s, G_s, f_s, Fp_s, np_s)
             dec = ph <= phi0 + armijo * t * slope
             acc = pend & ok & (dec | (t * size <= small_step))
             accepted |= acc
@@ -463,6 +477,9 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
     F, Lam, u = st["F"], st["Lam"], st["u"]
     nd = st.get("n")
     G = Fbar_d.reshape((d, d) + (1,) * d) + grad_u(u)
+    if lce:  # the previous time step of the dissipation terms: the state the solve starts from
+        Fprev_v = _to_voxels(F).copy()
+        nprev_v = nd.reshape(3, -1).T.copy()
     history = []
     local_res = []
     caps = []
@@ -476,9 +493,11 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
         if lce:
             force = frank_force(nd, mat.kappa)
             Fv, nv, _ = local_newton_lce(mat, _to_voxels(F), nd.reshape(3, -1).T, Lv, Gv, force, rho,
-                                         step_tol=step_tol, cap=local_cap, grad_tol=gtol)
+                                         step_tol=step_tol, cap=local_cap, grad_tol=gtol, Fprev=Fprev_v,
+                                         nprev=nprev_v)
             nd = nv.T.reshape((3,) + tuple(grid))
-            local_res.append(local_residual(mat, Fv, Lv, Gv, rho, mu_ref, nv, force) if local_ratio > 0.0 else 0.0)
+            local_res.append(local_residual(mat, Fv, Lv, Gv, rho, mu_ref, nv, force, Fprev_v, nprev_v)
+                             if local_ratio > 0.0 else 0.0)
         else:
             Fv, iters_v, conv_v = local_newton(mat, _to_voxels(F), Lv, Gv, rho, step_tol=step_tol, cap=cap,
                                                grad_tol=gtol, return_conv=True)
@@ -510,8 +529,9 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
                 rho = kappa * rho
             elif r_p > 0.0 and r_d / r_p > tau:
                 rho = max(rho / kappa, rho_min)
-    if lce:
-        stress = np.mean(mat.P(_to_voxels(F), nd.reshape(3, -1).T), axis=0)
+    if lce:  # with the dissipation's viscous stress cF (F - Fprev)
+        Fv = _to_voxels(F)
+        stress = np.mean(mat.P(Fv, nd.reshape(3, -1).T) + mat.cF[:, None, None] * (Fv - Fprev_v), axis=0)
     else:
         stress = np.mean(mat.P(_to_voxels(F)), axis=0)
     out = {"F": F, "Lam": Lam, "u": u, "iters": it if max_iter > 0 else 0,

@@ -136,16 +136,21 @@ class LCE:
 
     nparam = 5
 
-    def __init__(self, mu, lam, r, alpha, kappa, n0):
+    def __init__(self, mu, lam, r, alpha, kappa, n0, cF=None, cn=None):
         self.mu = np.asarray(mu, dtype=np.float64)
         self.lam = np.asarray(lam, dtype=np.float64)
         self.r = np.asarray(r, dtype=np.float64)
         self.alpha = np.asarray(alpha, dtype=np.float64)
         self.kappa = np.asarray(kappa, dtype=np.float64)
         self.n0 = np.asarray(n0, dtype=np.float64)
+        # dissipation weights of one implicit time step (Section 5.1's potential
+        # D = nu_F/2 |F'|^2 + nu_n/2 |n'|^2): cF = nu_F/dt, cn = nu_n/dt
+        self.cF = np.zeros_like(self.mu) if cF is None else np.asarray(cF, dtype=np.float64)
+        self.cn = np.zeros_like(self.mu) if cn is None else np.asarray(cn, dtype=np.float64)
 
     def subset(self, idx):
-        return LCE(self.mu[idx], self.lam[idx], self.r[idx], self.alpha[idx], self.kappa[idx], self.n0[idx])
+        return LCE(self.mu[idx], self.lam[idx], self.r[idx], self.alpha[idx], self.kappa[idx], self.n0[idx],
+                   self.cF[idx], self.cn[idx])
 
     def ell_inv(self, n):
         r13 = np.cbrt(self.r)
@@ -196,9 +201,11 @@ class LCE:
 
 
 def make_lce(phase: np.ndarray, params: np.ndarray, n0: np.ndarray):
-    """Per-voxel LCE material: params[p] = (mu, lam, r, alpha, kappa_F); n0 of shape
-    (3, *grid) (component-major, like the fields)."""
+    """Per-voxel LCE material: params[p] = (mu, lam, r, alpha, kappa_F[, nu_F/dt, nu_n/dt]);
+    n0 of shape (3, *grid) (component-major, like the fields)."""
     ph = np.asarray(phase).reshape(-1).astype(np.int64)
     tab = np.asarray(params, dtype=np.float64)
     n0v = np.asarray(n0, dtype=np.float64).reshape(3, -1).T
-    return LCE(tab[ph, 0], tab[ph, 1], tab[ph, 2], tab[ph, 3], tab[ph, 4], n0v)
+    cF = tab[ph, 5] if tab.shape[1] > 5 else None
+    cn = tab[ph, 6] if tab.shape[1] > 6 else None
+    return LCE(tab[ph, 0], tab[ph, 1], tab[ph, 2], tab[ph, 3], tab[ph, 4], n0v, cF, cn)

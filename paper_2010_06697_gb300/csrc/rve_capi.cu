@@ -77,8 +77,8 @@ bool valid_n(int n) {
 
 struct Layout {
     size_t ctrl, hist, partials, phase, mat, mat32, mat32lo, desc, tiles[admm::kTileClasses];
-    size_t F64[2], L64, U64[2], tw64, ksq64, N64[2], n064;
-    size_t F32[2], L32, U32[2], tw32, ksq32, N32[2], n032;
+    size_t F64[2], L64, U64[2], tw64, ksq64, N64[2], n064, Fp64, np64;
+    size_t F32[2], L32, U32[2], tw32, ksq32, N32[2], n032, Fp32, np32;
     size_t total;
 };
 
@@ -129,6 +129,8 @@ Layout layout(int dim, int n, int model, int precision, int max_iter) {
             o.N64[0] = take(8 * 3 * (size_t)V);
             o.N64[1] = take(8 * 3 * (size_t)V);
             o.n064 = take(8 * 3 * (size_t)V);
+            o.Fp64 = take(8 * 9 * (size_t)V);
+            o.np64 = take(8 * 3 * (size_t)V);
         }
     }
     if (need32) {
@@ -143,6 +145,8 @@ Layout layout(int dim, int n, int model, int precision, int max_iter) {
             o.N32[0] = take(4 * 3 * (size_t)V);
             o.N32[1] = take(4 * 3 * (size_t)V);
             o.n032 = take(4 * 3 * (size_t)V);
+            o.Fp32 = take(4 * 9 * (size_t)V);
+            o.np32 = take(4 * 3 * (size_t)V);
         }
     }
     o.total = off;
@@ -245,6 +249,10 @@ int begin_solve(rve* h, const double Fbar[9], double rho, double tol, cudaStream
         h->launches += 1;
         if (admm::launch_convert(Ls, false) != cudaSuccess) return RVE_E_CUDA;
         h->state_fp64 = 0;
+    }
+    if (h->model == admm::kLce) {  // the time step's starting state, for the dissipation terms
+        h->launches += 1;
+        if (admm::launch_save_prev(Ls, h->state_fp64 != 0, st) != cudaSuccess) return RVE_E_CUDA;
     }
     return RVE_OK;
 }
@@ -582,6 +590,8 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
             L.N64[0] = (double*)(b + lay.N64[0]);
             L.N64[1] = (double*)(b + lay.N64[1]);
             L.n0_64 = (const double*)(b + lay.n064);
+            L.Fp64 = (double*)(b + lay.Fp64);
+            L.np64 = (double*)(b + lay.np64);
         }
     }
     if (o.precision != RVE_FP64) {
@@ -596,6 +606,8 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
             L.N32[0] = (float*)(b + lay.N32[0]);
             L.N32[1] = (float*)(b + lay.N32[1]);
             L.n0_32 = (const float*)(b + lay.n032);
+            L.Fp32 = (float*)(b + lay.Fp32);
+            L.np32 = (float*)(b + lay.np32);
         }
     }
     if (o.precision == RVE_MIXED) {
@@ -752,6 +764,11 @@ int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* pa
         if (!(mu > 0) || !(lam >= 0) || !isfinite(mu) || !isfinite(lam)) return RVE_E_INVALID_ARG;
         double* row = &tab[p * admm::kMaxParam];
         for (int q = 0; q < (lce ? 5 : nparam); ++q) row[q] = params[p * nparam + q];
+        if (lce && nparam > 5) {  // nu_F/dt and nu_n/dt of the dissipation (default 0)
+            row[8] = params[p * nparam + 5];
+            row[9] = nparam > 6 ? params[p * nparam + 6] : 0.0;
+            if (!(row[8] >= 0) || !(row[9] >= 0) || !isfinite(row[8]) || !isfinite(row[9])) return RVE_E_INVALID_ARG;
+        }
         if (lce) {
             // {mu, lam, r, alpha, kappa_F}; derived a = mu r^{1/3}, c1, c2 of the m = F^T n form
             const double r = row[2], alpha = row[3], kap = row[4];
@@ -832,6 +849,32 @@ int rve_solve_mixed(rve_t h, const double Fbar[9], unsigned free_mask, double rh
     rc = solve_body(h, Fbar, rho, tol, info);
     h->free_mask = 0;
     return rc;
+}
+
+int rve_solve_path(rve_t h, const double* Fbars, int steps, unsigned free_mask, double rho, double tol,
+                   double* S_out, double* Fbar_out, rve_solve_info* infos) {
+    if (!h || !Fbars || steps < 1) return RVE_E_INVALID_ARG;
+    double prev[9];
+    int status = RVE_OK;
+    for (int s = 0; s < steps; ++s) {
+        double Fb[9];
+        for (int i = 0; i < 9; ++i)  // free components start from the previous step's result
+            Fb[i] = (s > 0 && ((free_mask >> i) & 1u)) ? prev[i] : Fbars[9 * s + i];
+        rve_solve_info info{};
+        const int rc = rve_solve_mixed(h, Fb, free_mask, rho, tol, &info);
+        if (rc != RVE_OK && rc != RVE_E_NOT_CONVERGED) return rc;
+        if (rc != RVE_OK) status = rc;
+        if (infos) infos[s] = info;
+        double S[9];
+        int e = rve_stress(h, S);
+        if (e) return e;
+        if ((e = rve_macro_gradient(h, prev))) return e;
+        for (int i = 0; i < 9; ++i) {
+            if (S_out) S_out[9 * s + i] = S[i];
+            if (Fbar_out) Fbar_out[9 * s + i] = prev[i];
+        }
+    }
+    return status;
 }
 
 int rve_macro_gradient(rve_t h, double F[9]) {

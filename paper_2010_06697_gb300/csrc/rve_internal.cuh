@@ -9,7 +9,7 @@ namespace admm {
 constexpr int kMaxPasses = 16;
 constexpr int kLocalThreads = 128;    // threads per block of the local-step kernels
 constexpr int kFftThreads = 256;      // threads per block of the FFT kernels
-constexpr int kMaxParam = 8;          // per-phase material constants
+constexpr int kMaxParam = 10;          // per-phase material constants
 constexpr int kPartialStride = 20;
 // fraction-converged local steps: counts of voxels whose Newton met its test within
 // 2, 4, ..., 2 kNewtonBins iterations
@@ -133,6 +133,10 @@ struct Launch {
     const double* n0_64;
     float* N32[2];
     const float* n0_32;
+    // the previous time step of the LCE dissipation terms (F: d*d*V, n: 3*V): the state a
+    // solve starts from, saved by launch_save_prev
+    double *Fp64, *np64;
+    float *Fp32, *np32;
     // double precision state
     double* F64[2];
     double* L64;
@@ -203,6 +207,8 @@ cudaError_t launch_init(const Launch& L, bool fp64, bool lambda_zero);
 // r_d from the float u~ increment D32 (see local_tile).
 cudaError_t launch_local(const Exec& E, bool fp64, bool first, bool only_if_rho_changed, int polish_mode = 0);
 cudaError_t launch_stress(const Launch& L, bool fp64);
+// LCE: save the current state (F_k, n_k) as the previous time step, in every precision held
+cudaError_t launch_save_prev(const Launch& L, bool from_fp64, cudaStream_t st);
 // mixed macroscopic control: free components of <F> from the mean of F - Lambda/rho
 // (dws: the state is in the double-word form of the polish)
 cudaError_t launch_macro(const Launch& L, bool fp64, cudaStream_t st, bool dws = false);

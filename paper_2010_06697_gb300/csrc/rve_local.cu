@@ -990,6 +990,8 @@ struct Dirs {
     T* N0;
     T* N1;
     const T* ref;
+    const T* Fp;  // previous time step (dissipation): F and n
+    const T* np;
 };
 
 template <typename T>
@@ -999,7 +1001,9 @@ struct Set<double> {
     __host__ __device__ static double* F(const Launch& L, int i) { return L.F64[i]; }
     __host__ __device__ static double* Lm(const Launch& L) { return L.L64; }
     __host__ __device__ static double* U(const Launch& L, int i) { return L.U64[i]; }
-    __host__ __device__ static Dirs<double> dirs(const Launch& L) { return Dirs<double>{L.N64[0], L.N64[1], L.n0_64}; }
+    __host__ __device__ static Dirs<double> dirs(const Launch& L) {
+        return Dirs<double>{L.N64[0], L.N64[1], L.n0_64, L.Fp64, L.np64};
+    }
     __host__ __device__ static const double* mat(const Launch& L) { return L.mat; }
     __host__ __device__ static double half_n(const Launch& L) { return L.half_n64; }
     __host__ __device__ static double two_nsq(const Launch& L) { return L.two_nsq64; }
@@ -1009,7 +1013,9 @@ struct Set<float> {
     __host__ __device__ static float* F(const Launch& L, int i) { return L.F32[i]; }
     __host__ __device__ static float* Lm(const Launch& L) { return L.L32; }
     __host__ __device__ static float* U(const Launch& L, int i) { return L.U32[i]; }
-    __host__ __device__ static Dirs<float> dirs(const Launch& L) { return Dirs<float>{L.N32[0], L.N32[1], L.n0_32}; }
+    __host__ __device__ static Dirs<float> dirs(const Launch& L) {
+        return Dirs<float>{L.N32[0], L.N32[1], L.n0_32, L.Fp32, L.np32};
+    }
     __host__ __device__ static const float* mat(const Launch& L) { return L.mat32; }
     __host__ __device__ static float half_n(const Launch& L) { return L.half_n32; }
     __host__ __device__ static float two_nsq(const Launch& L) { return L.two_nsq32; }
@@ -1240,17 +1246,24 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             // director of the current iterate (same parity as F) and the explicit Frank force
             const T* nCur = FIRST ? (par ? dir.N1 : dir.N0) : (par ? dir.N0 : dir.N1);
             T* nNext = FIRST ? (par ? dir.N0 : dir.N1) : (par ? dir.N1 : dir.N0);
-            const T kf = __ldg(mat + phase[v] * nparam + 4) * two_nsq;
+            const T* q = mat + phase[v] * nparam;
+            const T kf = __ldg(q + 4) * two_nsq;
+            // dissipation of one time step (Section 5.1): cF/2 |F - Fprev|^2 adds cF to the
+            // penalty and cF Fprev to B; on |n| = 1, cn/2 |n - nprev|^2 is -cn n.nprev + const,
+            // a force cn nprev next to the explicit Frank force
+            const T cF = __ldg(q + 8), cn = __ldg(q + 9);
             T nv[3], fr[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const T* c = nCur + i * V;
                 nv[i] = c[v];
-                fr[i] = kf * (c[nb.xp] + c[nb.xm] + c[nb.yp] + c[nb.ym] + c[nb.zp] + c[nb.zm]);
+                fr[i] = kf * (c[nb.xp] + c[nb.xm] + c[nb.yp] + c[nb.ym] + c[nb.zp] + c[nb.zm]) + cn * dir.np[i * V + v];
             }
+#pragma unroll
+            for (int p = 0; p < NN; ++p) B[p] += cF * dir.Fp[p * V + v];
             const Lce<T> m = load_lce<T>(phase, mat, nparam, v, dir.ref, V);
             T gn2 = T(0);
-            it = newton_lce<T>(m, F, nv, B, fr, rho, cap, ntol, conv, gtol, &gn2);
+            it = newton_lce<T>(m, F, nv, B, fr, rho + cF, cap, ntol, conv, gtol, &gn2);
             rl2a += (Acc)gn2;
 #pragma unroll
             for (int i = 0; i < 3; ++i) nNext[i * V + v] = nv[i];
@@ -1556,6 +1569,9 @@ k_stress(Ctrl* __restrict__ ctrl, double* __restrict__ partials, const T* F0, co
             const T* Nk = (ctrl->k & 1) ? dir.N1 : dir.N0;
             const T nv[3] = {Nk[v], Nk[V + v], Nk[2 * V + v]};
             load_lce<T>(phase, mat, nparam, v, dir.ref, V).stress(Fv, nv, P);
+            const T cF = __ldg(mat + phase[v] * nparam + 8);  // with the viscous stress cF (F - Fprev)
+#pragma unroll
+            for (int p = 0; p < NN; ++p) P[p] += cF * (Fv[p] - dir.Fp[p * V + v]);
         } else {
             using Law = typename LawOf<T, D, MODEL>::type;
             const Law m = load_law<Law, T>(phase, mat, nparam, v);
@@ -1773,6 +1789,36 @@ cudaError_t launch_polish_state(const Launch& L, bool enter, cudaStream_t st) {
         k_polish_state<2><<<blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.L64, L.LH32, L.LL32, L.V,
                                                    enter ? 1 : 0);
     k_polish_flag<<<1, 1, 0, st>>>(L.ctrl, enter ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// LCE: the state F_k, n_k (buffer k & 1, precision TS) saved as the previous time step
+// of the dissipation terms in the double and the float copies that exist.
+template <typename TS>
+__global__ void k_save_prev(const Ctrl* __restrict__ ctrl, const TS* F0, const TS* F1, const TS* N0, const TS* N1,
+                            double* Fp64, double* np64, float* Fp32, float* np32, long long V) {
+    const int par = (int)(ctrl->k & 1);
+    const TS* F = par ? F1 : F0;
+    const TS* N = par ? N1 : N0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 9 * V; i += (long long)gridDim.x * blockDim.x) {
+        const double f = (double)F[i];
+        if (Fp64) Fp64[i] = f;
+        if (Fp32) Fp32[i] = (float)F[i];
+        if (i < 3 * V) {
+            if (np64) np64[i] = (double)N[i];
+            if (np32) np32[i] = (float)N[i];
+        }
+    }
+}
+
+cudaError_t launch_save_prev(const Launch& L, bool from_fp64, cudaStream_t st) {
+    if (L.model != kLce) return cudaSuccess;
+    if (from_fp64)
+        k_save_prev<double><<<L.local_blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.N64[0], L.N64[1], L.Fp64,
+                                                          L.np64, L.Fp32, L.np32, L.V);
+    else
+        k_save_prev<float><<<L.local_blocks, 256, 0, st>>>(L.ctrl, L.F32[0], L.F32[1], L.N32[0], L.N32[1], L.Fp64,
+                                                         L.np64, L.Fp32, L.np32, L.V);
     return cudaGetLastError();
 }
 

@@ -104,6 +104,7 @@ SIGNATURES = {
     "rve_history_local": (_I, [_VP, _PD, _I]),
     "rve_solve_mixed": (_I, [_VP, _PD, ctypes.c_uint, _D, _D, ctypes.POINTER(rve_solve_info)]),
     "rve_macro_gradient": (_I, [_VP, _PD]),
+    "rve_solve_path": (_I, [_VP, _PD, _I, ctypes.c_uint, _D, _D, _PD, _PD, ctypes.POINTER(rve_solve_info)]),
     "rve_strerror": (ctypes.c_char_p, [_I]),
     "rve_set_profiling": (_I, [_VP, _I]),
     "rve_stress_noalloc": (_I, [_I, _I, _I, _VP, _VP, _VP, _I, _I, _VP, _VP]),
@@ -483,6 +484,20 @@ class Rve:
         if rc not in (RVE_OK, RVE_E_NOT_CONVERGED) or (check and rc != RVE_OK):
             raise RveError(rc, "rve_solve")
         return info
+
+    def solve_path(self, Fbars, rho, tol, free=None):
+        """Loading path (rve_solve_path): Fbars of shape (steps, 3, 3); returns (S, Fbar, infos)
+        with S and Fbar of shape (steps, 3, 3)."""
+        fb = np.ascontiguousarray(np.asarray(Fbars, dtype=np.float64).reshape(-1, 9))
+        steps = fb.shape[0]
+        S = np.zeros((steps, 9))
+        Fo = np.zeros((steps, 9))
+        infos = (rve_solve_info * steps)()
+        mask = 0 if free is None else free_mask_bits(free)
+        rc = lib().rve_solve_path(self.h, _dptr(fb), steps, mask, float(rho), float(tol), _dptr(S), _dptr(Fo), infos)
+        if rc not in (RVE_OK, RVE_E_NOT_CONVERGED):
+            raise RveError(rc, "rve_solve_path")
+        return S.reshape(steps, 3, 3), Fo.reshape(steps, 3, 3), list(infos)
 
     def macro_gradient(self):
         rc, F = rve_macro_gradient(self.h)

@@ -109,3 +109,62 @@ def test_lce_mixed_precision_tracks_fp64():
     assert rel(s32.stress(), s64.stress()) < 1e-4
     n32 = s32.get_field(rve.RVE_FIELD_N)
     assert np.max(np.abs(np.sum(n32 ** 2, axis=0) - 1.0)) < 1e-5
+
+
+# ------------------------------------------------------------------ time steps and loading paths
+
+def lce_params_dt(n, cF=5.6, cn=0.0106):
+    """Polydomain constants with Section 5.3's viscosities over its time step, normalised
+    by mu: nu_F/(mu dt) = 2.65/23.63/0.02 = 5.6, nu_n/(mu dt) = 0.005/23.63/0.02 = 0.0106."""
+    return np.array([[1.0, 20.0, 7.71, 0.06, (2.0 / n) ** 2, cF, cn]])
+
+
+def test_lce_time_step_matches_oracle():
+    """One time step with dissipation from a warm state, fixed iteration count,
+    element by element against the oracle (FP64)."""
+    n = 12
+    ph = np.zeros((n,) * 3, np.uint8)
+    n0 = synth.director_grf(n, 9, corr=2.5)
+    par = lce_params_dt(n)
+    s, _ = run_gpu(ph, par, n0, FBAR, 10.0, -1.0, 5)
+    warm = s.state()
+    ref0 = oracle.admm_solve(ph, par, FBAR, 10.0, -1.0, 5, model="lce", n0=n0)
+    F2 = FBAR.copy()
+    F2[0, 0] += 0.02
+    s.solve(F2, 10.0, -1.0)
+    st = s.state()
+    ref = oracle.admm_solve(ph, par, F2, 10.0, -1.0, 5, model="lce", n0=n0,
+                            state={"F": ref0["F"], "Lam": ref0["Lam"], "u": ref0["u"], "n": ref0["n"]})
+    assert rel(warm["F"], ref0["F"]) < TOL64
+    assert rel(st["F"], ref["F"]) < TOL64
+    assert rel(st["Lam"], ref["Lam"]) < TOL64
+    assert np.max(np.abs(st["n"] - ref["n"])) < TOL64
+    assert rel(s.stress(), ref["stress"]) < TOL64
+
+
+def test_lce_plane_stress_path_matches_oracle():
+    """A 3-step PE loading path (Section 5.3: <F_11> rising, <F_12> = 0, <F_22> = 1,
+    the rest free) with dissipation through rve_solve_path, against the oracle's steps
+    run one after another from each other's states: <S> and <F> of every step."""
+    n = 12
+    ph = np.zeros((n,) * 3, np.uint8)
+    n0 = synth.director_grf(n, 10, corr=2.5)
+    par = lce_params_dt(n)
+    free = np.ones((3, 3), bool)
+    free[0, 0] = free[0, 1] = free[1, 1] = False
+    lam = [1.02, 1.04, 1.06]
+    Fbars = np.stack([np.diag([l, 1.0, 1.0]) for l in lam])
+    s = rve.Rve(3, n, "lce", "fp64", max_iter=6)
+    s.set_material(ph, par, n0)
+    S, Fo, infos = s.solve_path(Fbars, 10.0, -1.0, free=free)
+    state, Fprev = None, None
+    for k in range(3):
+        Fb = Fbars[k].copy()
+        if Fprev is not None:
+            Fb[free] = Fprev[free]
+        r = oracle.admm_solve(ph, par, Fb, 10.0, -1.0, 6, model="lce", n0=n0, free=free, state=state)
+        state = {"F": r["F"], "Lam": r["Lam"], "u": r["u"], "n": r["n"]}
+        Fprev = r["Fbar"]
+        assert infos[k].iterations == 6
+        assert rel(S[k], r["stress"]) < 1e-9
+        assert np.max(np.abs(Fo[k] - r["Fbar"])) < 1e-11

@@ -168,3 +168,48 @@ def test_lce_local_solve_matches_brute_force(trial):
     np.testing.assert_allclose(Fn[0].ravel(), best.x[:9], atol=1e-5)
     nb = np.array([np.sin(best.x[9]) * np.cos(best.x[10]), np.sin(best.x[9]) * np.sin(best.x[10]), np.cos(best.x[9])])
     assert min(np.max(np.abs(nb - nn[0])), np.max(np.abs(nb + nn[0]))) < 1e-5
+
+
+# ------------------------------------------------------------------ dissipation (one time step)
+
+def test_lce_time_step_homogeneous_cell_matches_brute_force():
+    """One implicit time step with Section 5.1's dissipation on a homogeneous cell: from
+    a state (F_old, n_old), a new <F> makes F = <F> everywhere, the director minimises
+    W(<F>, n) + cn/2 |n - n_old|^2 on the unit sphere (found here by multi-start
+    Nelder-Mead over two angles, with the energy typed separately in tests/energies.py),
+    and <S> = W_F(<F>, n*) + cF (<F> - F_old).  A uniform director has no Frank torque."""
+    n = 4
+    mu, lam, r, alpha, cF, cn = 1.0, 20.0, 4.0, 0.1, 5.6, 0.4
+    ph = np.zeros((n,) * 3, np.uint8)
+    n0 = np.array([0.0, 1.0, 0.0])
+    par = np.array([[mu, lam, r, alpha, (2.0 / n) ** 2, cF, cn]])
+    n0f = np.broadcast_to(n0.reshape(3, 1, 1, 1), (3, n, n, n)).copy()
+    F_old = np.diag([1.05, 0.97, 0.98])
+    th = 0.4
+    n_old = np.array([np.sin(th), np.cos(th), 0.0])
+    V = n ** 3
+    state = {"F": np.broadcast_to(F_old.reshape(3, 3, 1, 1, 1), (3, 3, n, n, n)).copy(),
+             "Lam": np.zeros((3, 3, n, n, n)), "u": np.zeros((3, n, n, n)),
+             "n": np.broadcast_to(n_old.reshape(3, 1, 1, 1), (3, n, n, n)).copy()}
+    F_new = np.diag([1.12, 0.95, 0.96])
+    res = oracle.admm_solve(ph, par, F_new, 10.0, 1e-11, 3000, model="lce", n0=n0f, state=state)
+    assert res["converged"]
+
+    def energy(angles):
+        a, b = angles
+        nn = np.array([np.sin(a) * np.cos(b), np.cos(a), np.sin(a) * np.sin(b)])
+        w = E.w_lce(F_new, nn, mu, lam, r, alpha, n0)
+        return w + 0.5 * cn * np.sum((nn - n_old) ** 2)
+
+    best = min((optimize.minimize(energy, x0, method="Nelder-Mead",
+                                  options={"xatol": 1e-12, "fatol": 1e-15, "maxiter": 20000})
+                for x0 in ([0.1, 0.0], [0.5, 0.3], [1.2, -0.4], [2.0, 1.0])), key=lambda o: o.fun)
+    a, b = best.x
+    n_star = np.array([np.sin(a) * np.cos(b), np.cos(a), np.sin(a) * np.sin(b)])
+    nv = res["n"].reshape(3, -1).T
+    # the director is determined up to sign (n and -n are the same state)
+    s = np.sign(nv @ n_star)[:, None]
+    np.testing.assert_allclose(nv * s, np.broadcast_to(n_star, (V, 3)), atol=1e-6)
+    np.testing.assert_allclose(res["F"].reshape(9, -1).T, np.broadcast_to(F_new.ravel(), (V, 9)), atol=1e-9)
+    P_star, _ = E.lce_grad_cs(F_new, n_star, (mu, lam, r, alpha, n0))
+    np.testing.assert_allclose(res["stress"], P_star + cF * (F_new - F_old), atol=1e-8)
