@@ -395,6 +395,101 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
     return F, n, iters
 
 
+_EPS = np.zeros((3, 3, 3))
+_EPS[0, 1, 2] = _EPS[1, 2, 0] = _EPS[2, 0, 1] = 1.0
+_EPS[0, 2, 1] = _EPS[2, 1, 0] = _EPS[1, 0, 2] = -1.0
+
+
+def cofactor(F):
+    """Cofactor matrix d(det F)/dF = det(F) F^{-T}, per voxel (V,3,3), from its polynomial form."""
+    return 0.5 * np.einsum("kri,lsj,vrs,vij->vkl", _EPS, _EPS, F, F)
+
+
+def d2det(F):
+    """Second derivative of det F: d2J/dF_kl dF_rs = sum_ij eps_kri eps_lsj F_ij, shape (V,3,3,3,3)."""
+    return np.einsum("kri,lsj,vij->vklrs", _EPS, _EPS, F)
+
+
+def local_newton_lce_inc(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60, big=1e-2,
+                         Fprev=None, nprev=None):
+    """Step 1 for the incompressible LCE (Section 5.1: det F = 1 enforced in the local
+    step by a Lagrange multiplier p; the director on the unit sphere as in
+    local_newton_lce).  Newton on the stationarity of phi - p (det F - 1) in (F, t, p):
+    the 12 x 12 system [[K, -a], [-a^T, 0]] (dx, dp) = (-g, det F - 1), with g the
+    gradient of phi - p det F, K its Hessian in (F, t) (phi's plus -p d2det on the F
+    block, the sphere's curvature term and the 1e-6 mu shift on the director block;
+    (mu + rho) I is added where K is not positive definite) and a = (cof F, 0, 0).  p starts from the least-squares fit of cof F to phi's F-gradient.
+    A step longer than `big` (max norm over F and t) is scaled to `big`; every step
+    keeps det F > 0 by halving; no merit line search.  A voxel stops after a full step
+    of size <= step_tol.  Returns (F, n, iters)."""
+    V = F0.shape[0]
+    F = F0.copy()
+    n = n_init.copy()
+    if Fprev is None:
+        Fprev = F0
+    if nprev is None:
+        nprev = n_init
+    iters = np.zeros(V, dtype=np.int64)
+    active = np.ones(V, dtype=bool)
+    p = np.full(V, np.nan)
+    for _ in range(cap):
+        idx = np.nonzero(active)[0]
+        if idx.size == 0:
+            break
+        sub = mat.subset(idx)
+        Fa, na = F[idx], n[idx]
+        Lam_s, G_s, f_s = Lam[idx], G[idx], force[idx]
+        Fp_s, np_s = Fprev[idx], nprev[idx]
+        P, Wn, WFF, WFn, Wnn = sub.derivatives(Fa, na)
+        K9 = cofactor(Fa)
+        J = np.einsum("vij,vij->v", Fa, K9) / 3.0
+        gF0 = P - Lam_s + rho * (Fa - G_s) + sub.cF[:, None, None] * (Fa - Fp_s)
+        pa = p[idx]
+        fresh = np.isnan(pa)
+        if np.any(fresh):
+            pa[fresh] = (np.einsum("vij,vij->v", K9, gF0) / np.einsum("vij,vij->v", K9, K9))[fresh]
+        gF = gF0 - pa[:, None, None] * K9
+        gn = Wn - f_s + sub.cn[:, None] * (na - np_s)
+        a, b = tangent_basis(na)
+        E = np.stack([a, b], axis=2)
+        gt = np.einsum("vk,vka->va", gn, E)
+        Htt = (np.einsum("vka,vkp,vpb->vab", E, Wnn, E) - np.sum(na * gn, axis=1)[:, None, None] * np.eye(2)[None]
+               + sub.cn[:, None, None] * np.eye(2)[None] + 1e-6 * sub.mu[:, None, None] * np.eye(2)[None])
+        HFt = np.einsum("vklp,vpb->vklb", WFn, E).reshape(-1, 9, 2)
+        KKT = np.zeros((idx.size, 12, 12))
+        KKT[:, :9, :9] = ((WFF - pa[:, None, None, None, None] * d2det(Fa)).reshape(-1, 9, 9)
+                          + (rho + sub.cF)[:, None, None] * np.eye(9)[None])
+        KKT[:, :9, 9:11] = HFt
+        KKT[:, 9:11, :9] = HFt.transpose(0, 2, 1)
+        KKT[:, 9:11, 9:11] = Htt
+        # a K that is not positive definite (the director near a maximum of W on the
+        # sphere) gets the shift (mu + rho) I, so that the step descends on the constraint
+        # manifold instead of converging to that stationary point
+        notpd = np.linalg.eigvalsh(KKT[:, :11, :11])[:, 0] <= 0.0
+        if np.any(notpd):
+            KKT[notpd, :11, :11] += (sub.mu[notpd] + rho)[:, None, None] * np.eye(11)[None]
+        KKT[:, :9, 11] = -K9.reshape(-1, 9)
+        KKT[:, 11, :9] = -K9.reshape(-1, 9)
+        rhs = np.concatenate([-gF.reshape(-1, 9), -gt, (J - 1.0)[:, None]], axis=1)
+        sol = np.linalg.solve(KKT, rhs[..., None])[..., 0]
+        dx, dp = sol[:, :11], sol[:, 11]
+        size = np.max(np.abs(dx), axis=1)
+        t = np.where(size > big, big / np.maximum(size, 1e-300), 1.0)
+        for _h in range(40):
+            Ft = Fa + t[:, None, None] * dx[:, :9].reshape(-1, 3, 3)
+            bad = ~(np.linalg.det(Ft) > 0.0)
+            if not np.any(bad):
+                break
+            t = np.where(bad, 0.5 * t, t)
+        F[idx] = Fa + t[:, None, None] * dx[:, :9].reshape(-1, 3, 3)
+        n[idx] = retract(na, a, b, t * dx[:, 9], t * dx[:, 10])
+        p[idx] = pa + t * dp
+        iters[idx] += 1
+        done = (t == 1.0) & (size <= step_tol)
+        active[idx[done]] = False
+    return F, n, iters
+
+
 # --------------------------------------------------------------------------- Steps 3 and 4
 
 
@@ -433,7 +528,7 @@ def initial_state(mat, Fbar_d: np.ndarray, grid_shape, lambda0: str = "stress", 
 def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_ref=None,
                lambda0="stress", state=None, rho_policy="fixed", kappa=1.3, tau=10.0,
                rho_min=None, local_cap=50, step_tol=1e-10, n0=None, local_ratio=0.0, free=None,
-               local_fraction=0.0):
+               local_fraction=0.0, incompressible=False):
     """Run the ADMM iteration (Steps 1-4) until r_p <= tol and r_d <= tol, or max_iter.
 
     phase: uint8 grid (N,)*d; params: per-phase (mu, lam); Fbar: 3x3 (the upper-left
@@ -458,12 +553,16 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
     local_fraction = p > 0 (elastic laws): fraction-converged local steps with the
     Newton cap of fraction_cap, set from each pass's counts for the next pass (the
     first two passes use local_cap); out["newton_caps"] lists the cap of every pass.
+
+    incompressible (model "lce"): the network of Section 5.1 with det F = 1 enforced in
+    Step 1 by a multiplier (local_newton_lce_inc); out["stress"] is then <Lambda>,
+    which equals <W_F - p cof F> (+ the viscous part) once the iteration has converged.
     """
     phase = np.asarray(phase)
     d = phase.ndim
     grid = phase.shape
     lce = model == "lce"
-    mat = make_lce(phase, params, n0) if lce else make_material(model, phase, params)
+    mat = make_lce(phase, params, n0, incompressible) if lce else make_material(model, phase, params)
     Fbar_d = np.array(np.asarray(Fbar, dtype=np.float64)[:d, :d])
     free_d = None if free is None else np.asarray(free, dtype=bool)[:d, :d]
     if mu_ref is None:
@@ -492,9 +591,13 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
         Lv, Gv = _to_voxels(Lam), _to_voxels(G)
         if lce:
             force = frank_force(nd, mat.kappa)
-            Fv, nv, _ = local_newton_lce(mat, _to_voxels(F), nd.reshape(3, -1).T, Lv, Gv, force, rho,
-                                         step_tol=step_tol, cap=local_cap, grad_tol=gtol, Fprev=Fprev_v,
-                                         nprev=nprev_v)
+            if incompressible:
+                Fv, nv, _ = local_newton_lce_inc(mat, _to_voxels(F), nd.reshape(3, -1).T, Lv, Gv, force, rho,
+                                                 step_tol=step_tol, cap=local_cap, Fprev=Fprev_v, nprev=nprev_v)
+            else:
+                Fv, nv, _ = local_newton_lce(mat, _to_voxels(F), nd.reshape(3, -1).T, Lv, Gv, force, rho,
+                                             step_tol=step_tol, cap=local_cap, grad_tol=gtol, Fprev=Fprev_v,
+                                             nprev=nprev_v)
             nd = nv.T.reshape((3,) + tuple(grid))
             local_res.append(local_residual(mat, Fv, Lv, Gv, rho, mu_ref, nv, force, Fprev_v, nprev_v)
                              if local_ratio > 0.0 else 0.0)
@@ -529,7 +632,9 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
                 rho = kappa * rho
             elif r_p > 0.0 and r_d / r_p > tau:
                 rho = max(rho / kappa, rho_min)
-    if lce:  # with the dissipation's viscous stress cF (F - Fprev)
+    if lce and incompressible:  # the pressure is not part of the state: <Lambda>
+        stress = np.mean(_to_voxels(Lam), axis=0)
+    elif lce:  # with the dissipation's viscous stress cF (F - Fprev)
         Fv = _to_voxels(F)
         stress = np.mean(mat.P(Fv, nd.reshape(3, -1).T) + mat.cF[:, None, None] * (Fv - Fprev_v), axis=0)
     else:

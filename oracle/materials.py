@@ -136,7 +136,7 @@ class LCE:
 
     nparam = 5
 
-    def __init__(self, mu, lam, r, alpha, kappa, n0, cF=None, cn=None):
+    def __init__(self, mu, lam, r, alpha, kappa, n0, cF=None, cn=None, incompressible=False):
         self.mu = np.asarray(mu, dtype=np.float64)
         self.lam = np.asarray(lam, dtype=np.float64)
         self.r = np.asarray(r, dtype=np.float64)
@@ -147,10 +147,13 @@ class LCE:
         # D = nu_F/2 |F'|^2 + nu_n/2 |n'|^2): cF = nu_F/dt, cn = nu_n/dt
         self.cF = np.zeros_like(self.mu) if cF is None else np.asarray(cF, dtype=np.float64)
         self.cn = np.zeros_like(self.mu) if cn is None else np.asarray(cn, dtype=np.float64)
+        # incompressible network (Section 5.1 as printed): W = mu/2 (tr(F^T l^-1 F) - 3) +
+        # non-ideality, det F = 1 enforced by the local step's multiplier; no volumetric terms
+        self.incompressible = bool(incompressible)
 
     def subset(self, idx):
         return LCE(self.mu[idx], self.lam[idx], self.r[idx], self.alpha[idx], self.kappa[idx], self.n0[idx],
-                   self.cF[idx], self.cn[idx])
+                   self.cF[idx], self.cn[idx], self.incompressible)
 
     def ell_inv(self, n):
         r13 = np.cbrt(self.r)
@@ -165,8 +168,8 @@ class LCE:
         P0 = np.eye(3)[None] - np.einsum("vi,vj->vij", self.n0, self.n0)
         FtnnF = np.einsum("vji,vj,vk,vkl->vil", F, n, n, F)
         tr_ni = np.einsum("vij,vji->v", P0, FtnnF)
-        return (0.5 * self.mu * (tr_el - 3.0 - 2.0 * lnJ) + 0.5 * self.lam * (J - 1.0) ** 2
-                + 0.5 * self.mu * self.alpha * tr_ni)
+        vol = 0.0 if self.incompressible else -self.mu * lnJ + 0.5 * self.lam * (J - 1.0) ** 2
+        return 0.5 * self.mu * (tr_el - 3.0) + vol + 0.5 * self.mu * self.alpha * tr_ni
 
     def _M(self):
         r13 = np.cbrt(self.r)
@@ -184,6 +187,9 @@ class LCE:
         Mm = np.einsum("vjl,vl->vj", M, m)
         c = self.lam * J * (J - 1.0) - self.mu
         b = self.lam * (2.0 * J - 1.0) * J
+        if self.incompressible:
+            c = np.zeros_like(c)
+            b = np.zeros_like(b)
         P = (self.mu * r13)[:, None, None] * F + np.einsum("vk,vl->vkl", n, Mm) + c[:, None, None] * A
         Wn = np.einsum("vkj,vj->vk", F, Mm)
         I = np.eye(3)
@@ -200,7 +206,7 @@ class LCE:
         return self.derivatives(F, n)[0]
 
 
-def make_lce(phase: np.ndarray, params: np.ndarray, n0: np.ndarray):
+def make_lce(phase: np.ndarray, params: np.ndarray, n0: np.ndarray, incompressible: bool = False):
     """Per-voxel LCE material: params[p] = (mu, lam, r, alpha, kappa_F[, nu_F/dt, nu_n/dt]);
     n0 of shape (3, *grid) (component-major, like the fields)."""
     ph = np.asarray(phase).reshape(-1).astype(np.int64)
@@ -208,4 +214,4 @@ def make_lce(phase: np.ndarray, params: np.ndarray, n0: np.ndarray):
     n0v = np.asarray(n0, dtype=np.float64).reshape(3, -1).T
     cF = tab[ph, 5] if tab.shape[1] > 5 else None
     cn = tab[ph, 6] if tab.shape[1] > 6 else None
-    return LCE(tab[ph, 0], tab[ph, 1], tab[ph, 2], tab[ph, 3], tab[ph, 4], n0v, cF, cn)
+    return LCE(tab[ph, 0], tab[ph, 1], tab[ph, 2], tab[ph, 3], tab[ph, 4], n0v, cF, cn, incompressible)

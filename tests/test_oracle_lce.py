@@ -213,3 +213,71 @@ def test_lce_time_step_homogeneous_cell_matches_brute_force():
     np.testing.assert_allclose(res["F"].reshape(9, -1).T, np.broadcast_to(F_new.ravel(), (V, 9)), atol=1e-9)
     P_star, _ = E.lce_grad_cs(F_new, n_star, (mu, lam, r, alpha, n0))
     np.testing.assert_allclose(res["stress"], P_star + cF * (F_new - F_old), atol=1e-8)
+
+
+# ------------------------------------------------------------------ incompressible network
+
+def test_incompressible_uniaxial_stress_closed_form():
+    """r = 1, alpha = 0 turns the incompressible LCE into incompressible neo-Hookean,
+    W = mu/2 (|F|^2 - 3) with det F = 1.  Under uniaxial stress (<F_11> = s prescribed,
+    every other component free: mixed control) the exact cell state is F =
+    diag(s, s^-1/2, s^-1/2) with P_11 = mu (s - s^-2) and the other components zero."""
+    n, mu, s = 4, 1.0, 1.15
+    ph = np.zeros((n,) * 3, np.uint8)
+    n0 = np.broadcast_to(np.array([0.0, 1.0, 0.0]).reshape(3, 1, 1, 1), (3, n, n, n)).copy()
+    par = np.array([[mu, 0.0, 1.0, 0.0, 0.0]])
+    free = np.ones((3, 3), bool)
+    free[0, 0] = False
+    r = oracle.admm_solve(ph, par, np.diag([s, 1.0, 1.0]), 10.0, 1e-11, 3000, model="lce", n0=n0,
+                          free=free, incompressible=True)
+    assert r["converged"]
+    q = s ** -0.5
+    np.testing.assert_allclose(r["Fbar"], np.diag([s, q, q]), atol=1e-9)
+    np.testing.assert_allclose(np.linalg.det(r["F"].reshape(9, -1).T.reshape(-1, 3, 3)), 1.0, atol=1e-12)
+    np.testing.assert_allclose(r["stress"], np.diag([mu * (s - s ** -2), 0.0, 0.0]), atol=1e-9)
+
+
+def test_incompressible_homogeneous_cell_director_and_reaction():
+    """Homogeneous incompressible cell at an isochoric <F> (all components prescribed):
+    F = <F> everywhere, the director minimises W(<F>, n) (brute force over the sphere,
+    energy typed separately) and Lambda differs from W_F(<F>, n*) by a multiple of
+    cof <F> only: the undetermined reaction pressure of the constraint."""
+    n = 4
+    mu, r_, alpha = 1.0, 4.0, 0.1
+    ph = np.zeros((n,) * 3, np.uint8)
+    n0 = np.array([1.0, 0.0, 0.0])  # along the stretch: the director's stable minimum is nearby
+    n0f = np.broadcast_to(n0.reshape(3, 1, 1, 1), (3, n, n, n)).copy()
+    par = np.array([[mu, 0.0, r_, alpha, 0.0]])  # a uniform director has no Frank torque anyway
+    s = 1.12
+    Fb = np.diag([s, s ** -0.5, s ** -0.5])
+    Fb[0, 1] = 0.05
+    Fb[1, 2] = -0.03
+    res = oracle.admm_solve(ph, par, Fb, 10.0, 1e-11, 3000, model="lce", n0=n0f, incompressible=True)
+    assert res["converged"]
+    np.testing.assert_allclose(res["F"].reshape(9, -1).T, np.broadcast_to(Fb.ravel(), (n ** 3, 9)), atol=1e-9)
+
+    def w_inc(F, nn):  # incompressible network + non-ideality: the compressible form minus its volumetric terms
+        lnJ = np.log(np.linalg.det(F))
+        return E.w_lce(F, nn, mu, 0.0, r_, alpha, n0) + mu * lnJ
+
+    # the director's minimum near n0 (local search in the tangent plane of n0)
+    def nvec(c):
+        v = n0 + c[0] * np.array([0.0, 1.0, 0.0]) + c[1] * np.array([0.0, 0.0, 1.0])
+        return v / np.linalg.norm(v)
+
+    best = optimize.minimize(lambda c: w_inc(Fb, nvec(c)), [0.0, 0.0], method="Nelder-Mead",
+                             options={"xatol": 1e-12, "fatol": 1e-16, "maxiter": 20000})
+    n_star = nvec(best.x)
+    nv = res["n"].reshape(3, -1).T
+    np.testing.assert_allclose(nv * np.sign(nv @ n_star)[:, None], np.broadcast_to(n_star, (n ** 3, 3)), atol=1e-6)
+    # W_F of the incompressible energy by complex step (the compressible one minus
+    # -mu F^-T), at the cell's director: it matches the brute-force minimiser above to
+    # the search's accuracy, and W_F is not stationary in n, so the exact one is used
+    n_cell = nv[0] * np.sign(nv[0] @ n_star)
+    gF, _ = E.lce_grad_cs(Fb, n_cell, (mu, 0.0, r_, alpha, n0))
+    WF = gF + mu * np.linalg.inv(Fb).T
+    lam_mean = res["Lam"].reshape(9, -1).mean(axis=1).reshape(3, 3)
+    cof = np.linalg.det(Fb) * np.linalg.inv(Fb).T
+    d = lam_mean - WF
+    p_fit = -np.sum(d * cof) / np.sum(cof * cof)
+    np.testing.assert_allclose(d, -p_fit * cof, atol=1e-8)
