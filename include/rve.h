@@ -165,7 +165,13 @@ int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* pa
  * readings of the build), optionally nu_F/dt and nu_n/dt: the dissipation weights of
  * one implicit time step, dt D((F - F^n)/dt, (n - n^n)/dt) = nu_F/(2 dt) |F - F^n|^2 +
  * nu_n/(2 dt) |n - n^n|^2, with (F^n, n^n) the state the solve starts from (default 0:
- * the equilibrium problem).  <S> then includes the viscous part nu_F/dt (F - F^n). */
+ * the equilibrium problem).  <S> then includes the viscous part nu_F/dt (F - F^n).
+ * An eighth entry 1 (0: default) makes the network incompressible: W loses its
+ * volumetric terms (-mu ln J, lambda is ignored) and det F = 1 is enforced in the
+ * local step by a Lagrange multiplier (Section 5.1), always solved to the step
+ * tolerance (opt.local_ratio does not apply to it).  Every phase must give the same
+ * value.  The reaction pressure is not part of the state: rve_stress then returns
+ * <Lambda>, which equals <W_F - p cof F> (+ the viscous part) once converged. */
 
 /* ------------------------------------------------------------------ solve */
 /* Run ADMM iterations (Section 2.1, Steps 1-4) at macroscopic gradient Fbar
@@ -208,7 +214,8 @@ int rve_solve_path(rve_t h, const double* Fbars, int steps, unsigned free_mask, 
                    double* S_out, double* Fbar_out, rve_solve_info* infos);
 
 /* Homogenised first Piola-Kirchhoff stress <W_F(F)> of the current state,
- * summed in double on the device (Section 2.3: <S> is the macroscopic stress). */
+ * summed in double on the device (Section 2.3: <S> is the macroscopic stress);
+ * <Lambda> for the incompressible LCE network. */
 int rve_stress(rve_t h, double S[9]);
 
 /* Mean of the multiplier field <Lambda> (equals <W_F(F)> at an exact local solve). */

@@ -410,7 +410,7 @@ def d2det(F):
     return np.einsum("kri,lsj,vij->vklrs", _EPS, _EPS, F)
 
 
-def local_newton_lce_inc(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60, big=1e-2,
+def local_newton_lce_inc(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60, big=0.25,
                          Fprev=None, nprev=None):
     """Step 1 for the incompressible LCE (Section 5.1: det F = 1 enforced in the local
     step by a Lagrange multiplier p; the director on the unit sphere as in

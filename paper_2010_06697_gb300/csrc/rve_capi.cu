@@ -759,6 +759,7 @@ int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* pa
     }
     std::vector<double> tab(256 * (size_t)admm::kMaxParam, 0.0);
     double musum = 0.0;
+    const double inc0 = lce && nparam > 7 ? params[7] : 0.0;  // every phase the same network
     for (int p = 0; p < nphase; ++p) {
         const double mu = params[p * nparam + 0], lam = params[p * nparam + 1];
         if (!(mu > 0) || !(lam >= 0) || !isfinite(mu) || !isfinite(lam)) return RVE_E_INVALID_ARG;
@@ -768,6 +769,10 @@ int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* pa
             row[8] = params[p * nparam + 5];
             row[9] = nparam > 6 ? params[p * nparam + 6] : 0.0;
             if (!(row[8] >= 0) || !(row[9] >= 0) || !isfinite(row[8]) || !isfinite(row[9])) return RVE_E_INVALID_ARG;
+        }
+        if (lce && nparam > 7) {  // incompressible network: det F = 1 by the local step's multiplier
+            const double inc = params[p * nparam + 7];
+            if ((inc != 0.0 && inc != 1.0) || inc != inc0) return RVE_E_INVALID_ARG;
         }
         if (lce) {
             // {mu, lam, r, alpha, kappa_F}; derived a = mu r^{1/3}, c1, c2 of the m = F^T n form
@@ -812,6 +817,16 @@ int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* pa
         CK(cudaMemcpyAsync((void*)h->L.n0_32, n0f.data(), n0f.size() * 4, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->L.nparam = admm::kMaxParam;
+    if (lce) {  // the kernels of the incompressible network are their own instances
+        const int m = inc0 != 0.0 ? admm::kLceInc : admm::kLce;
+        if (m != h->L.model)
+            for (int i = 0; i < 3; ++i)
+                if (h->graph[i]) {
+                    cudaGraphExecDestroy(h->graph[i]);
+                    h->graph[i] = nullptr;
+                }
+        h->L.model = m;
+    }
     h->nphase = nphase;
     h->mu_ref = musum / (double)h->V;
     h->material_set = true;
@@ -1237,14 +1252,14 @@ int run_chunk(Engine& E, BatchRun& r, int stage) {
 
 void run_insert(Engine& E, int slot) {
     const Member& m = E.mem[slot];
-    BatchRun& r = E.runs[RunKey(m.h->dim, m.h->model, m.stage)];
+    BatchRun& r = E.runs[RunKey(m.h->dim, m.h->L.model, m.stage)];
     r.active.insert(std::lower_bound(r.active.begin(), r.active.end(), slot), slot);
     r.dirty = true;
 }
 
 void run_remove(Engine& E, int slot) {
     const Member& m = E.mem[slot];
-    auto it = E.runs.find(RunKey(m.h->dim, m.h->model, m.stage));
+    auto it = E.runs.find(RunKey(m.h->dim, m.h->L.model, m.stage));
     if (it == E.runs.end()) return;
     auto pos = std::find(it->second.active.begin(), it->second.active.end(), slot);
     if (pos != it->second.active.end()) {

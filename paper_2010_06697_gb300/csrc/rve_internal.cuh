@@ -9,7 +9,10 @@ namespace admm {
 constexpr int kMaxPasses = 16;
 constexpr int kLocalThreads = 128;    // threads per block of the local-step kernels
 constexpr int kFftThreads = 256;      // threads per block of the FFT kernels
-constexpr int kMaxParam = 10;          // per-phase material constants
+// per-phase material constants: the law's own (mu, lam first); the LCE adds r, alpha,
+// kappa_F (2-4), the derived a, c1, c2 (5-7), the dissipation weights nu_F/dt, nu_n/dt
+// (8, 9) and the incompressibility flag (10)
+constexpr int kMaxParam = 12;
 constexpr int kPartialStride = 20;
 // fraction-converged local steps: counts of voxels whose Newton met its test within
 // 2, 4, ..., 2 kNewtonBins iterations
@@ -19,7 +22,10 @@ constexpr int kNewtonBins = 16;
 constexpr int kHistStride = 4;    // doubles per block in the partial-sum buffer
 
 enum Done : int { kRunning = 0, kConverged = 1, kCapped = 2, kNumerical = 3, kSwitch = 4 };
-enum Model : int { kNeoHooke = 0, kLinear = 1, kLce = 2 };
+// kLceInc: the LCE with the incompressible network, chosen by the material table
+// (the public model stays RVE_LCE)
+enum Model : int { kNeoHooke = 0, kLinear = 1, kLce = 2, kLceInc = 3 };
+__host__ __device__ constexpr bool is_lce(int m) { return m == kLce || m == kLceInc; }
 
 // Per-RVE control block in device memory.  Every kernel reads it at entry (the
 // ping-pong parity, the penalty, the stop flag); only the last block of the

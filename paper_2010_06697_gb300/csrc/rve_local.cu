@@ -662,9 +662,12 @@ __device__ __forceinline__ int polish_voxel_dw(const float* __restrict__ Fc, flo
 //   W = a/2 |F|^2 + 1/2 m.M m - mu ln J + lam/2 (J-1)^2 + const,   a = mu r^{1/3}.
 // Local objective: phi(F, n) = W - f.n - Lambda:F + rho/2 |F - G|^2 on |n| = 1,
 // f = 2 kappa_F / h^2 * (sum of the neighbours' directors of the previous iterate).
+// The incompressible network (inc) drops the volumetric terms (muv = lam = 0): its
+// constraint det F = 1 is the local step's (newton_lce_inc).
 template <typename T>
 struct Lce {
     T mu, lam, a, c1, c2;
+    T muv;  // coefficient of -ln J: mu, or 0 for the incompressible network
     T n0[3];
     __device__ __forceinline__ void Mv(const T* v, T* o) const {
         const T d = n0[0] * v[0] + n0[1] * v[1] + n0[2] * v[2];
@@ -681,14 +684,14 @@ struct Lce {
         for (int j = 0; j < 3; ++j) mm[j] = n[0] * F[j] + n[1] * F[3 + j] + n[2] * F[6 + j];
         Mv(mm, Mm);
         const T q = mm[0] * Mm[0] + mm[1] * Mm[1] + mm[2] * Mm[2];
-        return T(0.5) * (a + rho) * ff + T(0.5) * q - mu * log_t(J) + T(0.5) * lam * (J - T(1)) * (J - T(1)) -
+        return T(0.5) * (a + rho) * ff + T(0.5) * q - muv * log_t(J) + T(0.5) * lam * (J - T(1)) * (J - T(1)) -
                (f[0] * n[0] + f[1] * n[1] + f[2] * n[2]) - bf;
     }
-    // W_F = a F + n (x) M m + (lam J (J-1) - mu) F^{-T}
+    // W_F = a F + n (x) M m + (lam J (J-1) - muv) F^{-T}
     __device__ __forceinline__ void stress(const T* F, const T* n, T* P) const {
         T K[9], mm[3], Mm[3];
         const T J = det_cof<T, 3>(F, K);
-        const T c = (lam * J * (J - T(1)) - mu) / J;
+        const T c = (lam * J * (J - T(1)) - muv) / J;
 #pragma unroll
         for (int j = 0; j < 3; ++j) mm[j] = n[0] * F[j] + n[1] * F[3 + j] + n[2] * F[6 + j];
         Mv(mm, Mm);
@@ -699,14 +702,15 @@ struct Lce {
     }
 };
 
-template <typename T>
+template <typename T, bool INC = false>
 __device__ __forceinline__ Lce<T> load_lce(const uint8_t* phase, const T* mat, int nparam, long long v,
                                           const T* __restrict__ n0, long long V) {
     const int ph = phase[v];
     const T* q = mat + ph * nparam;
     Lce<T> m;
     m.mu = __ldg(q + 0);
-    m.lam = __ldg(q + 1);
+    m.lam = INC ? T(0) : __ldg(q + 1);
+    m.muv = INC ? T(0) : m.mu;
     m.a = __ldg(q + 5);
     m.c1 = __ldg(q + 6);
     m.c2 = __ldg(q + 7);
@@ -752,6 +756,65 @@ __device__ __forceinline__ void retract(const T* n, const T* ta, const T* tb, T 
     for (int i = 0; i < 3; ++i) out[i] *= inv;
 }
 
+// Hessian of phi in (F, t1, t2) at (F, n), packed lower triangle, in float:
+// F-F block diag I + n_k n_r M_ls + bv A_kl A_rs - cv A_ks A_rl (A = F^{-T}), F-t rows
+// e_r (M m)_s + n_r (M F^T e)_s, t-t block (F^T e).M (F^T e') + shift I.
+template <typename T>
+__device__ __forceinline__ void lce_hessian(const Lce<T>& m, const T* F, const T* n, const T* ta, const T* tb,
+                                            const T* A, const T* Mm, float bv, float cv, float diag, float shift,
+                                            float* H) {
+    float Af[9], nf[3], n0f[3], Mmf[3], Ftaf[3], Ftbf[3], MFta[3], MFtb[3];
+    const float c1 = (float)m.c1, c2 = (float)m.c2;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) Af[p] = (float)A[p];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        nf[i] = (float)n[i];
+        n0f[i] = (float)m.n0[i];
+        Mmf[i] = (float)Mm[i];
+    }
+    // F^T ta, F^T tb and M applied to them
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        Ftaf[j] = (float)(F[j] * ta[0] + F[3 + j] * ta[1] + F[6 + j] * ta[2]);
+        Ftbf[j] = (float)(F[j] * tb[0] + F[3 + j] * tb[1] + F[6 + j] * tb[2]);
+    }
+    {
+        const float da = n0f[0] * Ftaf[0] + n0f[1] * Ftaf[1] + n0f[2] * Ftaf[2];
+        const float db = n0f[0] * Ftbf[0] + n0f[1] * Ftbf[1] + n0f[2] * Ftbf[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            MFta[i] = c1 * Ftaf[i] - c2 * da * n0f[i];
+            MFtb[i] = c1 * Ftbf[i] - c2 * db * n0f[i];
+        }
+    }
+    // F-F block
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const int k = p / 3, l = p % 3;
+#pragma unroll
+        for (int q = 0; q <= p; ++q) {
+            const int r = q / 3, s2 = q % 3;
+            const float Mls = (l == s2 ? c1 : 0.f) - c2 * n0f[l] * n0f[s2];
+            float h = nf[k] * nf[r] * Mls + bv * Af[p] * Af[q] - cv * Af[k * 3 + s2] * Af[r * 3 + l];
+            if (p == q) h += diag;
+            H[p * (p + 1) / 2 + q] = h;
+        }
+    }
+    // director rows: d2/dF_rs dt_beta = e_r (M m)_s + n_r (M F^T e)_s
+    const float taf[3] = {(float)ta[0], (float)ta[1], (float)ta[2]};
+    const float tbf[3] = {(float)tb[0], (float)tb[1], (float)tb[2]};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const int r = q / 3, s2 = q % 3;
+        H[9 * 10 / 2 + q] = taf[r] * Mmf[s2] + nf[r] * MFta[s2];
+        H[10 * 11 / 2 + q] = tbf[r] * Mmf[s2] + nf[r] * MFtb[s2];
+    }
+    H[9 * 10 / 2 + 9] = Ftaf[0] * MFta[0] + Ftaf[1] * MFta[1] + Ftaf[2] * MFta[2] + shift;
+    H[10 * 11 / 2 + 9] = Ftbf[0] * MFta[0] + Ftbf[1] * MFta[1] + Ftbf[2] * MFta[2];
+    H[10 * 11 / 2 + 10] = Ftbf[0] * MFtb[0] + Ftbf[1] * MFtb[1] + Ftbf[2] * MFtb[2] + shift;
+}
+
 // Newton on (F, t1, t2) with n <- normalise(n + t1 ta + t2 tb) (tangent plane at the
 // current n): gradient and objective in T, Hessian (11x11) assembled and factored
 // in float; the director block gets the curvature term -(n . phi_n) I and a shift
@@ -776,7 +839,7 @@ __device__ __forceinline__ int newton_lce(const Lce<T>& m, T* F, T* n, const T* 
 #pragma unroll
         for (int j = 0; j < 3; ++j) mm[j] = n[0] * F[j] + n[1] * F[3 + j] + n[2] * F[6 + j];
         m.Mv(mm, Mm);
-        const T c = m.lam * J * (J - T(1)) - m.mu;
+        const T c = m.lam * J * (J - T(1)) - m.muv;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
@@ -805,60 +868,9 @@ __device__ __forceinline__ int newton_lce(const Lce<T>& m, T* F, T* n, const T* 
         for (int p = 0; p < NU; ++p) gf[p] = (float)g[p];
         {
             float H[NP];
-            float Af[9], nf[3], n0f[3], Mmf[3], Ftaf[3], Ftbf[3], MFta[3], MFtb[3];
-            const float c1 = (float)m.c1, c2 = (float)m.c2;
-#pragma unroll
-            for (int p = 0; p < 9; ++p) Af[p] = (float)A[p];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                nf[i] = (float)n[i];
-                n0f[i] = (float)m.n0[i];
-                Mmf[i] = (float)Mm[i];
-            }
-            // F^T ta, F^T tb and M applied to them
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                Ftaf[j] = (float)(F[j] * ta[0] + F[3 + j] * ta[1] + F[6 + j] * ta[2]);
-                Ftbf[j] = (float)(F[j] * tb[0] + F[3 + j] * tb[1] + F[6 + j] * tb[2]);
-            }
-            {
-                const float da = n0f[0] * Ftaf[0] + n0f[1] * Ftaf[1] + n0f[2] * Ftaf[2];
-                const float db = n0f[0] * Ftbf[0] + n0f[1] * Ftbf[1] + n0f[2] * Ftbf[2];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    MFta[i] = c1 * Ftaf[i] - c2 * da * n0f[i];
-                    MFtb[i] = c1 * Ftbf[i] - c2 * db * n0f[i];
-                }
-            }
-            const float Jf = (float)J, cf = (float)c;
-            const float bf = (float)m.lam * (2.f * Jf - 1.f) * Jf;
-            const float diag = (float)(m.a + rho);
-            // F-F block: (a+rho) d d + n_k n_r M_ls + b A_kl A_rs - c A_ks A_rl
-#pragma unroll
-            for (int p = 0; p < 9; ++p) {
-                const int k = p / 3, l = p % 3;
-#pragma unroll
-                for (int q = 0; q <= p; ++q) {
-                    const int r = q / 3, s2 = q % 3;
-                    const float Mls = (l == s2 ? c1 : 0.f) - c2 * n0f[l] * n0f[s2];
-                    float h = nf[k] * nf[r] * Mls + bf * Af[p] * Af[q] - cf * Af[k * 3 + s2] * Af[r * 3 + l];
-                    if (p == q) h += diag;
-                    H[p * (p + 1) / 2 + q] = h;
-                }
-            }
-            // director rows: d2/dF_rs dt_beta = e_r (M m)_s + n_r (M F^T e)_s
-            const float taf[3] = {(float)ta[0], (float)ta[1], (float)ta[2]};
-            const float tbf[3] = {(float)tb[0], (float)tb[1], (float)tb[2]};
-#pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                const int r = q / 3, s2 = q % 3;
-                H[9 * 10 / 2 + q] = taf[r] * Mmf[s2] + nf[r] * MFta[s2];
-                H[10 * 11 / 2 + q] = tbf[r] * Mmf[s2] + nf[r] * MFtb[s2];
-            }
-            const float shift = 1e-6f * (float)m.mu - (float)ngn;
-            H[9 * 10 / 2 + 9] = Ftaf[0] * MFta[0] + Ftaf[1] * MFta[1] + Ftaf[2] * MFta[2] + shift;
-            H[10 * 11 / 2 + 9] = Ftbf[0] * MFta[0] + Ftbf[1] * MFta[1] + Ftbf[2] * MFta[2];
-            H[10 * 11 / 2 + 10] = Ftbf[0] * MFtb[0] + Ftbf[1] * MFtb[1] + Ftbf[2] * MFtb[2] + shift;
+            const float Jf = (float)J;
+            lce_hessian<T>(m, F, n, ta, tb, A, Mm, (float)m.lam * (2.f * Jf - 1.f) * Jf, (float)c, (float)(m.a + rho),
+                           1e-6f * (float)m.mu - (float)ngn, H);
             if (!chol_solve<float, NU>(H, gf, d)) {
                 const float sc = 1.f / (float)(m.mu + rho);
 #pragma unroll
@@ -916,6 +928,117 @@ __device__ __forceinline__ int newton_lce(const Lce<T>& m, T* F, T* n, const T* 
             break;
         }
         if (t == T(0)) break;
+    }
+    return it;
+}
+
+// The incompressible network (Section 5.1, det F = 1 by a multiplier p of the local
+// step): Newton on the stationarity of phi - p (det F - 1) in (F, t1, t2, p).  Each step
+// solves the KKT system [[K, -c], [-c^T, 0]] (dx, dp) = (-g, J - 1), c = (cof F, 0, 0),
+// K = phi's Hessian in (F, t) with -p d2(det) on the F block (float), by its Schur
+// complement on p: with y = K^-1 g and z = K^-1 c, dp = (c.y - (J - 1)) / (c.z) and
+// dx = dp z - y.  Where K is not positive definite (its Cholesky factorisation fails:
+// the director near a maximum) (mu + rho_pen) I is added.  p starts from the
+// least-squares fit of cof F to phi's F-gradient; steps longer than kIncBig are scaled
+// to it and halved while det F <= 0; no merit line search.  Stops after a full step
+// of size <= tol.  rho: F-penalty including the dissipation weight; rho_pen: ADMM rho.
+constexpr float kIncBig = 0.25f;  // longest step (max norm over F and t) of newton_lce_inc
+
+template <typename T>
+__device__ __forceinline__ int newton_lce_inc(const Lce<T>& m, T* F, T* n, const T* B, const T* f, T rho, T rho_pen,
+                                              int cap, T tol, bool& conv) {
+    constexpr int NU = 11;
+    constexpr int NP = NU * (NU + 1) / 2;
+    conv = false;
+    T pm = T(0);
+    int it = 0;
+    while (it < cap) {
+        T C[9], A[9], mm[3], Mm[3], g[NU], ta[3], tb[3];
+        const T J = det_cof<T, 3>(F, C);
+        if (!(J > T(0))) break;
+        const T iJ = T(1) / J;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) A[q] = C[q] * iJ;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) mm[j] = n[0] * F[j] + n[1] * F[3 + j] + n[2] * F[6 + j];
+        m.Mv(mm, Mm);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) g[k * 3 + l] = (m.a + rho) * F[k * 3 + l] + n[k] * Mm[l] - B[k * 3 + l];
+        if (it == 0) {
+            T cc = T(0), cg = T(0);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                cc += C[q] * C[q];
+                cg += C[q] * g[q];
+            }
+            pm = cg / cc;
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) g[q] -= pm * C[q];
+        T gn[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gn[k] = F[k * 3 + 0] * Mm[0] + F[k * 3 + 1] * Mm[1] + F[k * 3 + 2] * Mm[2] - f[k];
+        tangent_basis(n, ta, tb);
+        g[9] = ta[0] * gn[0] + ta[1] * gn[1] + ta[2] * gn[2];
+        g[10] = tb[0] * gn[0] + tb[1] * gn[1] + tb[2] * gn[2];
+        const T ngn = n[0] * gn[0] + n[1] * gn[1] + n[2] * gn[2];
+
+        float d[NU], dp;
+        {
+            float H[NP], inv[NU], gf[NU], cf[NU], y[NU], z[NU];
+#pragma unroll
+            for (int q = 0; q < NU; ++q) {
+                gf[q] = (float)g[q];
+                cf[q] = q < 9 ? (float)C[q] : 0.f;
+            }
+            const float pJ = (float)(pm * J), diag = (float)(m.a + rho);
+            const float shift = 1e-6f * (float)m.mu - (float)ngn;
+            lce_hessian<T>(m, F, n, ta, tb, A, Mm, -pJ, -pJ, diag, shift, H);
+            if (!chol_factor<float, NU>(H, inv)) {
+                const float sh = (float)(m.mu + rho_pen);
+                lce_hessian<T>(m, F, n, ta, tb, A, Mm, -pJ, -pJ, diag + sh, shift + sh, H);
+                if (!chol_factor<float, NU>(H, inv)) break;
+            }
+            chol_subst<float, NU>(H, inv, gf, y);  // -K^-1 g
+            chol_subst<float, NU>(H, inv, cf, z);  // -K^-1 c
+            float cy = 0.f, cz = 0.f;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                cy += cf[q] * y[q];
+                cz += cf[q] * z[q];
+            }
+            dp = (cy + (float)(J - T(1))) / cz;
+#pragma unroll
+            for (int q = 0; q < NU; ++q) d[q] = y[q] - dp * z[q];
+        }
+        float size = 0.f;
+#pragma unroll
+        for (int q = 0; q < NU; ++q) size = fmaxf(size, fabsf(d[q]));
+        if (!(size < 1e30f) || !(fabsf(dp) < 1e30f)) break;
+        T t = size > kIncBig ? T(kIncBig) / (T)size : T(1);
+        T Ft[9];
+        int h = 0;
+        for (; h < 40; ++h) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) Ft[q] = F[q] + t * (T)d[q];
+            if (det<T, 3>(Ft) > T(0)) break;
+            t *= T(0.5);
+        }
+        if (h == 40) break;
+        T nt[3];
+        retract(n, ta, tb, t * (T)d[9], t * (T)d[10], nt);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) F[q] = Ft[q];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) n[i] = nt[i];
+        pm += t * (T)dp;
+        ++it;
+        if (t == T(1) && size <= (float)tol) {
+            conv = true;
+            break;
+        }
     }
     return it;
 }
@@ -1036,7 +1159,7 @@ k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const 
         for (int j = 0; j < D; ++j) Fb[i * D + j] = (T)ctrl->Fbar[i * 3 + j];
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
         T P[D * D];
-        if constexpr (MODEL == kLce) {
+        if constexpr (is_lce(MODEL)) {
             T* Nk = par ? dir.N1 : dir.N0;
             T nv[3];
 #pragma unroll
@@ -1048,7 +1171,7 @@ k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const 
 #pragma unroll
                 for (int p = 0; p < 9; ++p) P[p] = T(0);
             } else {
-                load_lce<T>(phase, mat, nparam, v, dir.ref, V).stress(Fb, nv, P);
+                load_lce<T, MODEL == kLceInc>(phase, mat, nparam, v, dir.ref, V).stress(Fb, nv, P);
             }
         } else if (lambda_zero) {
 #pragma unroll
@@ -1118,7 +1241,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     __shared__ int s_hist[kNewtonBins];       // fraction-converged local steps
 
     // the increment form needs the previous iteration's R: never the first step of a run
-    constexpr bool INC = WRITE_R && DU && MODEL != kLce && std::is_same<T, double>::value;
+    constexpr bool INC = WRITE_R && DU && !is_lce(MODEL) && std::is_same<T, double>::value;
     if (INC && FIRST_ARG) return;
     const bool FIRST = INC ? false : FIRST_ARG;
     if (ctrl->done) return;
@@ -1174,7 +1297,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     using Acc = typename std::conditional<sizeof(T) == 4 || INC, float, double>::type;
     // Section 4.2's first strategy (fraction-converged local steps): this pass's
     // histogram of Newton counts sets the next pass's cap (one pass of lag, no barrier)
-    const bool frac_on = !INC && !FIRST && MODEL != kLce && ctrl->local_fraction > 0.0;
+    const bool frac_on = !INC && !FIRST && !is_lce(MODEL) && ctrl->local_fraction > 0.0;
     if (frac_on) {
         if (threadIdx.x < kNewtonBins) s_hist[threadIdx.x] = 0;
         __syncthreads();
@@ -1242,7 +1365,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
         T B[NN];
 #pragma unroll
         for (int p = 0; p < NN; ++p) B[p] = L[p] + rho * G[p];
-        if constexpr (MODEL == kLce) {
+        if constexpr (is_lce(MODEL)) {
             // director of the current iterate (same parity as F) and the explicit Frank force
             const T* nCur = FIRST ? (par ? dir.N1 : dir.N0) : (par ? dir.N0 : dir.N1);
             T* nNext = FIRST ? (par ? dir.N0 : dir.N1) : (par ? dir.N1 : dir.N0);
@@ -1261,9 +1384,12 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             }
 #pragma unroll
             for (int p = 0; p < NN; ++p) B[p] += cF * dir.Fp[p * V + v];
-            const Lce<T> m = load_lce<T>(phase, mat, nparam, v, dir.ref, V);
+            const Lce<T> m = load_lce<T, MODEL == kLceInc>(phase, mat, nparam, v, dir.ref, V);
             T gn2 = T(0);
-            it = newton_lce<T>(m, F, nv, B, fr, rho + cF, cap, ntol, conv, gtol, &gn2);
+            if constexpr (MODEL == kLceInc)  // always solved to the step tolerance (no gradient stop)
+                it = newton_lce_inc<T>(m, F, nv, B, fr, rho + cF, rho, cap, ntol, conv);
+            else
+                it = newton_lce<T>(m, F, nv, B, fr, rho + cF, cap, ntol, conv, gtol, &gn2);
             rl2a += (Acc)gn2;
 #pragma unroll
             for (int i = 0; i < 3; ++i) nNext[i * V + v] = nv[i];
@@ -1452,7 +1578,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
 // are latency-bound at fewer.
 template <typename T, int MODEL, bool WRITE_R, bool DU>
 constexpr int local_min_blocks() {
-    if (MODEL == kLce) return 1;
+    if (is_lce(MODEL)) return 1;
     if (sizeof(T) == 4) return 4;
     return (WRITE_R && DU) ? 4 : 1;  // the double-word polish: FP32 work, latency-bound
 }
@@ -1565,7 +1691,11 @@ k_stress(Ctrl* __restrict__ ctrl, double* __restrict__ partials, const T* F0, co
         T Fv[NN], P[NN];
 #pragma unroll
         for (int p = 0; p < NN; ++p) Fv[p] = F[p * V + v];
-        if constexpr (MODEL == kLce) {
+        if constexpr (MODEL == kLceInc) {
+            // the reaction pressure is not part of the state: Lambda stands for the stress
+#pragma unroll
+            for (int p = 0; p < NN; ++p) P[p] = Lam[p * V + v];
+        } else if constexpr (MODEL == kLce) {
             const T* Nk = (ctrl->k & 1) ? dir.N1 : dir.N0;
             const T nv[3] = {Nk[v], Nk[V + v], Nk[2 * V + v]};
             load_lce<T>(phase, mat, nparam, v, dir.ref, V).stress(Fv, nv, P);
@@ -1707,6 +1837,7 @@ cudaError_t run_stress(const Launch& L) {
         if (L.dim == 2 && L.model == kLinear) return FN<T, 2, kLinear>(__VA_ARGS__);        \
         if (L.dim == 3 && L.model == kLinear) return FN<T, 3, kLinear>(__VA_ARGS__);        \
         if (L.dim == 3 && L.model == kLce) return FN<T, 3, kLce>(__VA_ARGS__);              \
+        if (L.dim == 3 && L.model == kLceInc) return FN<T, 3, kLceInc>(__VA_ARGS__);        \
         return cudaErrorInvalidValue;                                                       \
     } while (0)
 
@@ -1780,7 +1911,7 @@ __global__ void k_polish_flag(Ctrl* __restrict__ ctrl, int enter) {
 }
 
 cudaError_t launch_polish_state(const Launch& L, bool enter, cudaStream_t st) {
-    if (L.model == kLce) return cudaSuccess;  // the LCE polish stays in double
+    if (is_lce(L.model)) return cudaSuccess;  // the LCE polish stays in double
     const int blocks = L.local_blocks;
     if (L.dim == 3)
         k_polish_state<3><<<blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.L64, L.LH32, L.LL32, L.V,
@@ -1812,7 +1943,7 @@ __global__ void k_save_prev(const Ctrl* __restrict__ ctrl, const TS* F0, const T
 }
 
 cudaError_t launch_save_prev(const Launch& L, bool from_fp64, cudaStream_t st) {
-    if (L.model != kLce) return cudaSuccess;
+    if (!is_lce(L.model)) return cudaSuccess;
     if (from_fp64)
         k_save_prev<double><<<L.local_blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.N64[0], L.N64[1], L.Fp64,
                                                           L.np64, L.Fp32, L.np32, L.V);
@@ -1830,7 +1961,7 @@ cudaError_t launch_stress(const Launch& L, bool fp64) {
 cudaError_t launch_convert(const Launch& L, bool to_fp64) {
     const long long nF = (long long)L.dim * L.dim * L.V;
     const long long nU = (long long)L.dim * L.V;
-    const long long nN = L.model == kLce ? 3 * L.V : 0;
+    const long long nN = is_lce(L.model) ? 3 * L.V : 0;
     const int blocks = 152 * 8;
     if (to_fp64)
         k_convert<float, double><<<blocks, 256, 0, L.stream>>>(L.ctrl, L.F32[0], L.F32[1], L.L32, L.U32[0],

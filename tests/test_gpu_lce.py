@@ -168,3 +168,97 @@ def test_lce_plane_stress_path_matches_oracle():
         assert infos[k].iterations == 6
         assert rel(S[k], r["stress"]) < 1e-9
         assert np.max(np.abs(Fo[k] - r["Fbar"])) < 1e-11
+
+
+# ------------------------------------------------------------------ incompressible network
+
+def inc_params(n, r=4.0, alpha=0.1, wall=2.0, cF=0.0, cn=0.0):
+    """Eighth entry 1: det F = 1 by the local step's multiplier (lambda unused)."""
+    return np.array([[1.0, 0.0, r, alpha, (wall / n) ** 2, cF, cn, 1.0]])
+
+
+def isochoric(s):
+    return np.diag([s, s ** -0.5, s ** -0.5])
+
+
+@pytest.mark.parametrize("n,iters,seed,cF,cn", [(8, 3, 13, 0.0, 0.0), (12, 5, 17, 0.0, 0.0),
+                                                (12, 4, 9, 5.6, 0.0106)])
+def test_incompressible_iterations_match_oracle(n, iters, seed, cF, cn):
+    """Polydomain incompressible cell (with and without the dissipation terms), fixed
+    iteration count, element by element against the oracle's KKT local step; every
+    voxel's det F is 1 after each local step."""
+    ph = np.zeros((n,) * 3, np.uint8)
+    n0 = synth.director_grf(n, seed, corr=3.0)
+    par = inc_params(n, cF=cF, cn=cn)
+    Fb = isochoric(1.1)
+    s, info = run_gpu(ph, par, n0, Fb, 10.0, -1.0, iters)
+    ref = oracle.admm_solve(ph, par, Fb, 10.0, -1.0, iters, model="lce", n0=n0, incompressible=True)
+    assert info.iterations == iters
+    st = s.state()
+    assert rel(st["F"], ref["F"]) < TOL64
+    assert rel(st["Lam"], ref["Lam"]) < TOL64
+    assert np.max(np.abs(st["n"] - ref["n"])) < TOL64
+    assert np.max(np.abs(st["u"] - ref["u"])) < TOL64
+    np.testing.assert_allclose(s.history()[:, :2], np.array(ref["history"])[:, :2], rtol=1e-8, atol=1e-13)
+    assert rel(s.stress(), ref["stress"]) < TOL64
+    F = st["F"].reshape(9, -1).T.reshape(-1, 3, 3)
+    assert np.max(np.abs(np.linalg.det(F) - 1.0)) < 1e-9
+
+
+def test_incompressible_uniaxial_stress_on_gpu():
+    """r = 1, alpha = 0: incompressible neo-Hookean.  Uniaxial stress by mixed control
+    (<F_11> = s, the rest free): <F> = diag(s, s^-1/2, s^-1/2), <S_11> = mu (s - s^-2),
+    every other component 0."""
+    n, mu, s = 8, 1.0, 1.15
+    ph = np.zeros((n,) * 3, np.uint8)
+    n0 = np.broadcast_to(np.array([0.0, 1.0, 0.0]).reshape(3, 1, 1, 1), (3, n, n, n)).copy()
+    par = np.array([[mu, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 1.0]])
+    free = np.ones((3, 3), bool)
+    free[0, 0] = False
+    a = rve.Rve(3, n, "lce", "fp64", max_iter=3000)
+    a.set_material(ph, par, n0)
+    info = a.solve(np.diag([s, 1.0, 1.0]), 10.0, 1e-11, free=free)
+    assert info.converged
+    q = s ** -0.5
+    np.testing.assert_allclose(a.macro_gradient(), np.diag([s, q, q]), atol=1e-9)
+    np.testing.assert_allclose(a.stress(), np.diag([mu * (s - s ** -2), 0.0, 0.0]), atol=1e-9)
+
+
+def test_incompressible_two_phase_matches_oracle():
+    """Two incompressible phases with different r, alpha, kappa on an inclusion map."""
+    n = 12
+    ph = synth.inclusion_phase(n, 3, 4, radius=2)
+    n0 = synth.director_grf(n, 21, corr=2.5)
+    par = np.array([[1.0, 0.0, 4.0, 0.1, 0.02, 0.0, 0.0, 1.0], [2.0, 0.0, 2.0, 0.05, 0.01, 0.0, 0.0, 1.0]])
+    Fb = isochoric(1.08)
+    s, info = run_gpu(ph, par, n0, Fb, 10.0, -1.0, 5)
+    ref = oracle.admm_solve(ph, par, Fb, 10.0, -1.0, 5, model="lce", n0=n0, incompressible=True)
+    st = s.state()
+    assert rel(st["F"], ref["F"]) < TOL64
+    assert np.max(np.abs(st["n"] - ref["n"])) < TOL64
+    assert rel(s.stress(), ref["stress"]) < TOL64
+
+
+def test_incompressible_mixed_precision_tracks_fp64():
+    n = 16
+    ph = np.zeros((n,) * 3, np.uint8)
+    n0 = synth.director_grf(n, 5, corr=3.0)
+    par = inc_params(n, r=7.71, alpha=0.06)
+    Fb = isochoric(1.2)
+    s64, _ = run_gpu(ph, par, n0, Fb, 10.0, -1.0, 20)
+    s32, info = run_gpu(ph, par, n0, Fb, 10.0, -1.0, 20, precision="mixed")
+    assert info.iterations == 20
+    assert rel(s32.stress(), s64.stress()) < 1e-4
+
+
+def test_incompressible_flag_checked():
+    """The flag is 0 or 1 and the same in every phase."""
+    n = 8
+    ph = synth.inclusion_phase(n, 3, 4, radius=2)
+    n0 = synth.director_grf(n, 21, corr=2.5)
+    a = rve.Rve(3, n, "lce", "fp64", max_iter=5)
+    bad_mix = np.array([[1.0, 0.0, 4.0, 0.1, 0.02, 0.0, 0.0, 1.0], [2.0, 0.0, 2.0, 0.05, 0.01, 0.0, 0.0, 0.0]])
+    bad_val = np.array([[1.0, 0.0, 4.0, 0.1, 0.02, 0.0, 0.0, 0.5]] * 2)
+    for par in (bad_mix, bad_val):
+        with pytest.raises(rve.RveError):
+            a.set_material(ph, par, n0)
