@@ -345,7 +345,9 @@ def run_ours(args):
         for name, fn in (("laminate32_2d", bench_laminate32), ("inclusions128_inexact", bench_inexact128),
                          ("inclusions128_fraction",
                           lambda t, r, sy: bench_inexact128(t, r, sy, ratio=0.0, fraction=0.9)),
-                         ("lce256", bench_lce256), ("batch64", bench_batch64), ("serving", bench_serving)):
+                         ("lce256", bench_lce256), ("lce128_pe_path", bench_lce_path128),
+                         ("lce128_pe_path_inc", lambda t, r, sy: bench_lce_path128(t, r, sy, incompressible=True)),
+                         ("batch64", bench_batch64), ("serving", bench_serving)):
             try:
                 extra[name] = fn(torch, rve, synth)
             except Exception as e:  # report, do not lose the main line
@@ -459,6 +461,39 @@ def bench_lce256(torch, rve, synth, iters=40):
     return {"workload": "lce256", "value": ph.size * info.iterations / (ms / 1e3), "unit": UNIT,
             "ms": ms, "iterations": info.iterations, "fp64_iterations": info.fp64_iterations,
             "r_p": info.r_p, "r_d": info.r_d, "stress_xx": float(S[0, 0]), "precision": "mixed"}
+
+
+def bench_lce_path128(torch, rve, synth, incompressible=False, steps=5, iters=30):
+    """3D 128^3 LCE polydomain under a plane-strain loading path with dissipation
+    (Section 5.3): <F_11> = 1.02, 1.04, ..., <F_12> = 0, <F_22> = 1, the other components
+    free (mixed control); one time step per load step with nu_F/(mu dt) = 5.6,
+    nu_n/(mu dt) = 0.0106; r = 7.71, alpha = 0.06, wall length 2h, directors from a
+    Gaussian random field (correlation 8 voxels); FP64; a fixed iteration count per
+    step.  incompressible: the network with det F = 1 by the local multiplier."""
+    n = 128
+    n0 = synth.director_grf(n, 0, corr=8.0)
+    ph = np.zeros((n,) * 3, np.uint8)
+    par = np.array([[1.0, 20.0, 7.71, 0.06, (2.0 / n) ** 2, 5.6, 0.0106, 1.0 if incompressible else 0.0]])
+    free = np.ones((3, 3), bool)
+    free[0, 0] = free[0, 1] = free[1, 1] = False
+    Fbars = np.stack([np.diag([1.0 + 0.02 * (k + 1), 1.0, 1.0]) for k in range(steps)])
+    s = rve.Rve(3, n, "lce", "fp64", max_iter=iters)
+    s.set_material(ph, par, n0)
+    s.solve_path(Fbars[:1], RHO, -1.0, free=free)  # warm-up (kernels, graphs)
+    s.set_material(ph, par, n0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    S, Fo, infos = s.solve_path(Fbars, RHO, -1.0, free=free)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    its = sum(i.iterations for i in infos)
+    s.close()
+    return {"workload": "lce128_pe_path" + ("_inc" if incompressible else ""), "value": ph.size * its / (ms / 1e3),
+            "unit": UNIT, "ms": ms, "load_steps": steps, "iterations": its, "precision": "fp64",
+            "S11": [float(x[0, 0]) for x in S], "F33": [float(x[2, 2]) for x in Fo],
+            "r_p_last": infos[-1].r_p, "r_d_last": infos[-1].r_d}
 
 
 def bench_batch64(torch, rve, synth, count=64):
