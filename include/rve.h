@@ -213,6 +213,45 @@ int rve_macro_gradient(rve_t h, double F[9]);
 int rve_solve_path(rve_t h, const double* Fbars, int steps, unsigned free_mask, double rho, double tol,
                    double* S_out, double* Fbar_out, rve_solve_info* infos);
 
+/* ------------------------------------------------------------------ Bloch waves */
+/* Result of rve_bloch. */
+typedef struct rve_bloch_info {
+    int iterations;      /* Steps 1'-4' run                                        */
+    int converged;       /* r_p <= tol and r_d <= tol                              */
+    double beta;         /* sigma of the last Step 2' (the multiplier of ||p|| = 1):
+                            beta_k once converged                                  */
+    double rayleigh;     /* <D p, L D p> of the final p (||p|| = 1)                */
+    double r_p, r_d;     /* residuals of the last iteration                        */
+    double time_ms;      /* device time of the iterations                          */
+    long long launches;  /* kernel launches issued                                 */
+    int fail;            /* RVE_E_NUMERICAL causes, bits: 1 L + rho I not positive
+                            definite, 2 b^ has no weight at the lowest kappa (Step 2'
+                            hard case), 4 Step 2' root not found in its passes     */
+} rve_bloch_info;
+
+/* Modulus of stability beta_k (Section 2.4): the minimum over unit Bloch waves
+ * v = p(x) exp(i omega.x), omega_j = 2 pi / k_j, of <grad v, L grad v> with
+ * L(x) = W_FF(F(x)) of the handle's material at its resident state F (the
+ * solution of the last solve, or a field set with rve_set_field), computed by the
+ * Bloch-wave ADMM (Steps 1'-4') with the unit-norm constraint inside Step 2' (its
+ * secular equation) and the grid's central differences applied to v, so that beta_k
+ * is the smallest eigenvalue of the discrete D^* L D.  k: k[0..d-1] non-zero
+ * integers, at least one with |k_j| >= 2 (otherwise the Bloch operator has null
+ * modes).  p0: host, 2 d N^d doubles, the start p_0 as (re, im) pairs,
+ * component-major like the fields (normalised by the call; not all zero).  rho:
+ * penalty, L + rho I must be positive definite everywhere.  tol: bound on r_p and
+ * r_d (r_d scaled by rho / mu_ref as for rve_solve); max_iter > 0.  p_out (host,
+ * same layout as p0) receives the final p and hist (host, 3 doubles per
+ * iteration: r_p, r_d, sigma) the history; either may be NULL.  Models
+ * RVE_NEOHOOKE and RVE_LINEAR.  The call keeps a device workspace of about
+ * (48 d^2 + 8 d^2 (d^2 + 1) + 64 d) N^d bytes on the handle until rve_destroy.
+ * Returns RVE_OK, RVE_E_NOT_CONVERGED (results valid), RVE_E_INVALID_ARG (k, rho,
+ * p0, max_iter, model), RVE_E_STATE (no material, or no state yet),
+ * RVE_E_NUMERICAL (L + rho I not positive definite somewhere, or Step 2' found no
+ * root), RVE_E_OOM, RVE_E_CUDA. */
+int rve_bloch(rve_t h, const int k[3], const double* p0, double rho, double tol, int max_iter, double* p_out,
+              double* hist, rve_bloch_info* info);
+
 /* Homogenised first Piola-Kirchhoff stress <W_F(F)> of the current state,
  * summed in double on the device (Section 2.3: <S> is the macroscopic stress);
  * <Lambda> for the incompressible LCE network. */

@@ -55,6 +55,7 @@ struct rve {
     int last_iters = 0;
     long long launches = 0; // kernel launches issued by the running solve
     // profiling: every launch bracketed by events, per kernel class and precision
+    admm::BlochWork* bloch = nullptr;  // Bloch-wave workspace (rve_bloch)
     bool prof = false;
     std::vector<cudaEvent_t> pev;
     double prof_ms[2][RVE_KCLASS_COUNT] = {};
@@ -738,6 +739,7 @@ void rve_destroy(rve_t h) {
     for (int i = 0; i < 3; ++i)
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
     if (h->own_ws && h->ws) cudaFree(h->ws);
+    if (h->bloch) admm::bloch_free(h->bloch);
     if (h->hctrl) cudaFreeHost(h->hctrl);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -890,6 +892,56 @@ int rve_solve_path(rve_t h, const double* Fbars, int steps, unsigned free_mask, 
         }
     }
     return status;
+}
+
+int rve_bloch(rve_t h, const int k[3], const double* p0, double rho, double tol, int max_iter, double* p_out,
+              double* hist, rve_bloch_info* info) {
+    if (!h || !k || !p0 || !(rho > 0) || !isfinite(rho) || max_iter < 1 || !(tol == tol)) return RVE_E_INVALID_ARG;
+    if (h->model != RVE_NEOHOOKE && h->model != RVE_LINEAR) return RVE_E_INVALID_ARG;
+    bool wide = false;
+    for (int j = 0; j < h->dim; ++j) {
+        if (k[j] == 0) return RVE_E_INVALID_ARG;
+        wide = wide || k[j] > 1 || k[j] < -1;
+    }
+    if (!wide) return RVE_E_INVALID_ARG;
+    if (!h->material_set || h->fresh) return RVE_E_STATE;
+    if (enter(h)) return RVE_E_CUDA;
+    if (read_ctrl(h)) return RVE_E_CUDA;  // the resident state's parity
+    admm::BlochArgs a{};
+    a.dim = h->dim;
+    a.n = h->n;
+    a.V = h->V;
+    a.model = h->model;
+    const int par = (int)(h->k & 1);
+    a.F_fp64 = h->state_fp64 != 0;
+    a.F = a.F_fp64 ? (const void*)h->L.F64[par] : (const void*)h->L.F32[par];
+    a.phase = h->L.phase;
+    a.mat = h->L.mat;
+    a.nparam = h->L.nparam;
+    for (int j = 0; j < 3; ++j) a.k[j] = j < h->dim ? k[j] : 1;
+    a.rho = rho;
+    a.tol = tol;
+    a.mu_ref = h->opt.mu_ref > 0 ? h->opt.mu_ref : h->mu_ref;
+    a.max_iter = max_iter;
+    a.check_every = h->opt.check_every;
+    a.p0 = p0;
+    a.p_out = p_out;
+    a.hist_out = hist;
+    a.stream = h->stream;
+    admm::BlochResult r{};
+    const int rc = admm::bloch_run(&h->bloch, a, &r);
+    if (info) {
+        info->iterations = r.iterations;
+        info->converged = r.converged;
+        info->beta = r.beta;
+        info->rayleigh = r.rayleigh;
+        info->r_p = r.r_p;
+        info->r_d = r.r_d;
+        info->time_ms = r.time_ms;
+        info->launches = r.launches;
+        info->fail = r.fail;
+    }
+    return rc;
 }
 
 int rve_macro_gradient(rve_t h, double F[9]) {

@@ -228,4 +228,31 @@ cudaError_t launch_fft_incr(const Exec& E, int stage = -1);
 inline int fft_stages(int dim) { return dim == 3 ? 5 : 3; }
 cudaError_t prepare_fft_kernels(int n);
 
+// ------------------------------------------------------------------ Bloch-wave ADMM (rve_bloch.cu)
+struct BlochWork;  // device workspace, kept by the handle between calls
+struct BlochArgs {
+    int dim, n;
+    long long V;
+    int model;            // kNeoHooke or kLinear: L = W_FF(F) of the phase table
+    const void* F;        // resident deformation gradient (d*d*V, double or float)
+    bool F_fp64;
+    const uint8_t* phase;
+    const double* mat;
+    int nparam;
+    int k[3];             // Bloch wave numbers, omega_j = 2 pi / k_j
+    double rho, tol, mu_ref;
+    int max_iter, check_every;
+    const double* p0;     // host, 2 d V doubles (re, im), component-major
+    double* p_out;        // host or null
+    double* hist_out;     // host (r_p, r_d, sigma per iteration) or null
+    cudaStream_t stream;
+};
+struct BlochResult {
+    int iterations, converged, fail;
+    double beta, rayleigh, r_p, r_d, time_ms;
+    long long launches;
+};
+int bloch_run(BlochWork** w, const BlochArgs& in, BlochResult* res);
+void bloch_free(BlochWork* w);
+
 }  // namespace admm

@@ -81,6 +81,23 @@ class rve_solve_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class rve_bloch_info(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("beta", ctypes.c_double),
+        ("rayleigh", ctypes.c_double),
+        ("r_p", ctypes.c_double),
+        ("r_d", ctypes.c_double),
+        ("time_ms", ctypes.c_double),
+        ("launches", ctypes.c_longlong),
+        ("fail", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -105,6 +122,7 @@ SIGNATURES = {
     "rve_solve_mixed": (_I, [_VP, _PD, ctypes.c_uint, _D, _D, ctypes.POINTER(rve_solve_info)]),
     "rve_macro_gradient": (_I, [_VP, _PD]),
     "rve_solve_path": (_I, [_VP, _PD, _I, ctypes.c_uint, _D, _D, _PD, _PD, ctypes.POINTER(rve_solve_info)]),
+    "rve_bloch": (_I, [_VP, ctypes.POINTER(_I), _PD, _D, _D, _I, _PD, _PD, ctypes.POINTER(rve_bloch_info)]),
     "rve_strerror": (ctypes.c_char_p, [_I]),
     "rve_set_profiling": (_I, [_VP, _I]),
     "rve_stress_noalloc": (_I, [_I, _I, _I, _VP, _VP, _VP, _I, _I, _VP, _VP]),
@@ -274,6 +292,20 @@ def rve_history_local(h, cap):
     if cnt < 0:
         return cnt, None
     return cnt, rl[:cnt]
+
+
+def rve_bloch(h, k, p0, rho, tol, max_iter, want_p=True):
+    """Modulus of stability beta_k (see include/rve.h).  k: d non-zero ints; p0: complex
+    (d, *grid).  Returns (rc, info, p or None, history (iterations, 3))."""
+    kk = (ctypes.c_int * 3)(*(list(int(x) for x in k) + [1] * (3 - len(k))))
+    p = np.ascontiguousarray(np.asarray(p0, dtype=np.complex128))
+    out = np.zeros_like(p) if want_p else None
+    hist = np.zeros(3 * int(max_iter))
+    info = rve_bloch_info()
+    rc = lib().rve_bloch(h, kk, p.view(np.float64).ctypes.data_as(_PD), float(rho), float(tol), int(max_iter),
+                         out.view(np.float64).ctypes.data_as(_PD) if want_p else None, _dptr(hist),
+                         ctypes.byref(info))
+    return rc, info, out, hist.reshape(-1, 3)[: info.iterations]
 
 
 def rve_stress_noalloc(dim, n, model, F_ptr, phase_ptr, params_ptr, nphase, nparam, S_ptr, stream=None):
@@ -498,6 +530,17 @@ class Rve:
         if rc not in (RVE_OK, RVE_E_NOT_CONVERGED):
             raise RveError(rc, "rve_solve_path")
         return S.reshape(steps, 3, 3), Fo.reshape(steps, 3, 3), list(infos)
+
+    def bloch(self, k, rho, tol, max_iter, p0=None, seed=0):
+        """Modulus of stability beta_k of the resident state (rve_bloch).  p0 defaults to
+        synth.bloch_start(n, dim, seed).  Returns (info, p, history)."""
+        if p0 is None:
+            from . import synth
+            p0 = synth.bloch_start(self.n, self.dim, seed)
+        rc, info, p, hist = rve_bloch(self.h, k, p0, rho, tol, max_iter)
+        if rc not in (RVE_OK, RVE_E_NOT_CONVERGED):
+            raise RveError(rc, "rve_bloch")
+        return info, p, hist
 
     def macro_gradient(self):
         rc, F = rve_macro_gradient(self.h)

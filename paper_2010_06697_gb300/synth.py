@@ -128,6 +128,16 @@ def random_fbar(seed: int, tag: int, amp: float = 0.1) -> np.ndarray:
     return np.eye(3) + 0.5 * (e + e.T)
 
 
+# --------------------------------------------------------------------------- Bloch-wave starts
+
+def bloch_start(n: int, dim: int, seed: int) -> np.ndarray:
+    """Start p_0 of the Bloch-wave iteration: complex (dim, n, ..., n) with independent
+    standard-normal real and imaginary parts (tags 71 and 72)."""
+    a = normal(seed, 71, dim * n ** dim).reshape((dim,) + (n,) * dim)
+    b = normal(seed, 72, dim * n ** dim).reshape((dim,) + (n,) * dim)
+    return a + 1j * b
+
+
 # --------------------------------------------------------------------------- standard material tables
 
 def lame_lambda(mu: float, nu: float) -> float:

@@ -1,0 +1,136 @@
+"""Bloch-wave ADMM (Section 2.4) on the GPU vs the FP64 oracle: element-wise parity
+after fixed iteration counts, converged beta_k against the oracle and the dense
+eigenvalue, closed forms, argument and state checks."""
+import numpy as np
+import pytest
+
+from oracle import bloch
+from paper_2010_06697_gb300 import build, rve, synth
+
+from .test_oracle_bloch import dense_beta, near_identity_field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    rve.lib()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+def handle_with_state(d, n, model, ph, par, F):
+    s = rve.Rve(d, n, model, "fp64", max_iter=10)
+    s.set_material(ph, par)
+    s.set_field(rve.RVE_FIELD_F, F)
+    return s
+
+
+def two_phase_case(d, n, seed=5):
+    ph = synth.inclusion_phase(n, d, 3, radius=max(1, n // 8))
+    par = synth.two_phase_params(1.0, 4.0)
+    F = near_identity_field(n, d, seed)
+    return ph, par, F
+
+
+@pytest.mark.parametrize("d,n,k,iters", [(2, 12, (3, 4), 7), (2, 18, (2, -3), 5), (3, 8, (2, 3, -4), 4),
+                                         (3, 6, (2, 1, 1), 3)])
+def test_bloch_iterations_match_oracle(d, n, k, iters):
+    ph, par, F = two_phase_case(d, n)
+    mu_ref = float(np.mean(par[ph.reshape(-1), 0]))
+    p0 = synth.bloch_start(n, d, 11)
+    s = handle_with_state(d, n, "neohookean", ph, par, F)
+    info, p, hist = s.bloch(k, 10.0, -1.0, iters, p0=p0)
+    L = bloch.tangent_field("neohookean", ph, par, F)
+    ref = bloch.bloch_solve(L, p0, k, 10.0, -1.0, iters, mu_ref)
+    assert info.iterations == iters
+    assert rel(p, ref["p"]) < 1e-10
+    np.testing.assert_allclose(info.beta, ref["sigma"], rtol=1e-11)
+    np.testing.assert_allclose(hist[:, :2], np.array(ref["history"]), rtol=1e-8, atol=1e-13)
+    np.testing.assert_allclose(np.sum(np.abs(p) ** 2) / n ** d, 1.0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("d,n,k", [(2, 6, (3, -2)), (2, 6, (2, 1)), (3, 4, (2, 3, 1))])
+def test_bloch_converged_beta_is_smallest_eigenvalue(d, n, k):
+    ph = synth.inclusion_phase(n, d, 3, radius=1)
+    par = synth.two_phase_params(1.0, 4.0)
+    F = near_identity_field(n, d, 5)
+    L = bloch.tangent_field("neohookean", ph, par, F)
+    w, _, _ = dense_beta(L, n, d, k)
+    s = handle_with_state(d, n, "neohookean", ph, par, F)
+    info, p, _ = s.bloch(k, 10.0, 1e-10, 20000, p0=synth.bloch_start(n, d, 1))
+    assert info.converged
+    np.testing.assert_allclose(info.beta, w[0], rtol=1e-9)
+    np.testing.assert_allclose(info.rayleigh, w[0], rtol=1e-9)
+
+
+@pytest.mark.parametrize("d,n,k", [(2, 64, (2, 2)), (2, 48, (3, -5)), (3, 24, (2, 2, 3))])
+def test_bloch_homogeneous_linear_closed_form(d, n, k):
+    """Homogeneous isotropic linear elasticity: plane waves are eigenvectors with
+    eigenvalues mu |q|^2 and (lam + 2 mu) |q|^2, q_j = N sin(2 pi (m_j + 1/k_j) / N),
+    so beta_k = mu min_m |q(m)|^2."""
+    mu, lam = 1.0, 1.5
+    ph = np.zeros((n,) * d, np.uint8)
+    F = np.broadcast_to(np.eye(d).reshape((d, d) + (1,) * d), (d, d) + (n,) * d).copy()
+    s = handle_with_state(d, n, "linear", ph, np.array([[mu, lam]]), F)
+    info, p, _ = s.bloch(k, 4.0, 1e-10, 20000, seed=3)
+    m = np.arange(n)
+    qmin = sum(np.min((n * np.sin(2 * np.pi * (m + 1.0 / k[j]) / n)) ** 2) for j in range(d))
+    assert info.converged
+    np.testing.assert_allclose(info.beta, mu * qmin, rtol=1e-9)
+    np.testing.assert_allclose(info.rayleigh, mu * qmin, rtol=1e-9)
+
+
+def test_bloch_after_solve_uses_resident_state():
+    """beta_k of an equilibrium state from rve_solve (compressed two-phase cell) equals
+    the oracle's beta for the same F field read back from the handle."""
+    d, n, k = 2, 24, (2, 2)
+    ph = synth.inclusion_phase(n, d, 7, radius=4)
+    par = synth.two_phase_params(20.0, 1.0)
+    s = rve.Rve(d, n, "neohookean", "fp64", max_iter=3000)
+    s.set_material(ph, par)
+    s.solve(np.diag([0.95, 0.95, 1.0]), 10.0, 1e-9)
+    F = s.get_field(rve.RVE_FIELD_F)
+    info, p, _ = s.bloch(k, 60.0, -1.0, 6, seed=2)
+    mu_ref = float(np.mean(par[ph.reshape(-1), 0]))
+    ref = bloch.bloch_solve(bloch.tangent_field("neohookean", ph, par, F), synth.bloch_start(n, d, 2), k, 60.0,
+                            -1.0, 6, mu_ref)
+    assert rel(p, ref["p"]) < 1e-10
+    np.testing.assert_allclose(info.beta, ref["sigma"], rtol=1e-11)
+
+
+def test_bloch_arguments_and_state_checked():
+    d, n = 2, 8
+    ph, par, F = two_phase_case(d, n)
+    s = rve.Rve(d, n, "neohookean", "fp64", max_iter=10)
+    s.set_material(ph, par)
+    p0 = synth.bloch_start(n, d, 0)
+    rc, *_ = rve.rve_bloch(s.h, (2, 2), p0, 10.0, 1e-8, 10)
+    assert rc == rve.RVE_E_STATE  # no state yet
+    s.set_field(rve.RVE_FIELD_F, F)
+    for k in ((1, 1), (1, -1), (0, 2)):
+        rc, *_ = rve.rve_bloch(s.h, k, p0, 10.0, 1e-8, 10)
+        assert rc == rve.RVE_E_INVALID_ARG
+    rc, *_ = rve.rve_bloch(s.h, (2, 2), np.zeros_like(p0), 10.0, 1e-8, 10)
+    assert rc == rve.RVE_E_INVALID_ARG
+    rc, *_ = rve.rve_bloch(s.h, (2, 2), p0, -1.0, 1e-8, 10)
+    assert rc == rve.RVE_E_INVALID_ARG
+
+
+def test_bloch_indefinite_tangent_reported():
+    """A tangent with a negative eigenvalue below -rho makes L + rho I indefinite:
+    RVE_E_NUMERICAL, no iterations."""
+    d, n = 2, 8
+    ph = np.zeros((n,) * d, np.uint8)
+    par = np.array([[1.0, 50.0]])
+    Fh = np.diag([0.35, 0.35])
+    C = bloch.tangent_field("neohookean", np.zeros((1, 1), np.uint8), par, Fh.reshape(2, 2, 1, 1))[0]
+    lam_min = np.linalg.eigvalsh(C.reshape(4, 4))[0]
+    assert lam_min < -1.0  # the precondition, from the oracle's tangent
+    F = np.broadcast_to(Fh.reshape(2, 2, 1, 1), (2, 2, n, n)).copy()
+    s = handle_with_state(d, n, "neohookean", ph, par, F)
+    rc, info, _, _ = rve.rve_bloch(s.h, (2, 2), synth.bloch_start(n, d, 0), 0.5 * abs(lam_min), 1e-8, 10)
+    assert rc == rve.RVE_E_NUMERICAL

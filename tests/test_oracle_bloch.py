@@ -55,9 +55,7 @@ def near_identity_field(n, d, seed, amp=0.08):
 
 
 def start_field(n, d, seed):
-    a = synth.normal(seed, 71, d * n ** d).reshape((d,) + (n,) * d)
-    b = synth.normal(seed, 72, d * n ** d).reshape((d,) + (n,) * d)
-    return a + 1j * b
+    return synth.bloch_start(n, d, seed)
 
 
 CASES = [(2, 4, (2, 2), "homogeneous"), (2, 6, (3, -2), "two-phase"), (3, 4, (2, 3, 1), "two-phase"),
