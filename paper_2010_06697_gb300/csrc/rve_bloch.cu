@@ -64,8 +64,8 @@ struct FftPlanB {
 
 struct BArgs {
     int n, V;
-    double half_n, rho, tol, rd_scale;
-    double c[3], s[3];     // cos, sin of th_j
+    double half_n, rho, inv_rho, tol, rd_scale;
+    double c[3], s[3];     // cos, sin of th_j, times 1/(2h)
     const double* sym;     // s_j(m) at sym[j * n + m]
     double2 *P0, *P1, *B, *G, *g, *Q;
     double *Lf, *Linv, *W, *part, *hist;
@@ -113,7 +113,8 @@ __device__ __forceinline__ void block_reduce(double* v) {
 }
 
 // Block partials to part[block * 4 + q]; returns true in thread 0 of the last block,
-// whose v[] then holds the totals (summed over blocks in block order).
+// whose v[] then holds the totals.  The last block reads the partials with all its
+// threads (a fixed assignment, so the order of the sums is fixed) and reduces them.
 template <int NV, bool MIN = false>
 __device__ __forceinline__ bool grid_reduce(double* v, double* part, BCtrl* ctrl) {
     __shared__ int s_last;
@@ -127,13 +128,13 @@ __device__ __forceinline__ bool grid_reduce(double* v, double* part, BCtrl* ctrl
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
-    if (threadIdx.x != 0) return false;
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        double a = __ldcg(part + q);
-        for (unsigned b = 1; b < gridDim.x; ++b) a = MIN ? fmin(a, __ldcg(part + b * 4 + q)) : a + __ldcg(part + b * 4 + q);
-        v[q] = a;
-    }
+    for (int q = 0; q < NV; ++q) v[q] = MIN ? 1e300 : 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kBT)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = MIN ? fmin(v[q], __ldcg(part + b * 4 + q)) : v[q] + __ldcg(part + b * 4 + q);
+    block_reduce<NV, MIN>(v);
+    if (threadIdx.x != 0) return false;
     ctrl->counter = 0u;
     return true;
 }
@@ -164,10 +165,17 @@ __device__ __forceinline__ void bloch_grad(const double2* __restrict__ X, const 
         for (int j = 0; j < D; ++j) {
             const double2 u = X[(size_t)i * a.V + up[j]], w = X[(size_t)i * a.V + dn[j]];
             const double c = a.c[j], s = a.s[j];
-            const double re = (u.x * c - u.y * s) - (w.x * c + w.y * s);
-            const double im = (u.x * s + u.y * c) - (w.y * c - w.x * s);
-            out[i * D + j] = make_double2(a.half_n * re, a.half_n * im);
+            out[i * D + j] = make_double2((u.x * c - u.y * s) - (w.x * c + w.y * s),
+                                          (u.x * s + u.y * c) - (w.y * c - w.x * s));
         }
+}
+
+// (D X)_ij at v for one (i, j).
+__device__ __forceinline__ double2 bloch_grad1(const double2* __restrict__ X, const BArgs& a, int i, int j, int up,
+                                               int dn) {
+    const double2 u = X[(size_t)i * a.V + up], w = X[(size_t)i * a.V + dn];
+    const double c = a.c[j], s = a.s[j];
+    return make_double2((u.x * c - u.y * s) - (w.x * c + w.y * s), (u.x * s + u.y * c) - (w.y * c - w.x * s));
 }
 
 // Packed lower-triangle index.
@@ -198,6 +206,33 @@ __device__ __forceinline__ void fsolve(const BArgs& a, int v, const double2* b, 
             s.y -= l * x[r].y;
         }
         x[p] = cscale(s, __ldg(a.Linv + (size_t)p * a.V + v));
+    }
+}
+
+// (L + rho I) x = b in place (forward substitution into b, then backward).
+template <int NN>
+__device__ __forceinline__ void fsolve_inplace(const BArgs& a, int v, double2* b) {
+#pragma unroll
+    for (int p = 0; p < NN; ++p) {
+        double2 s = b[p];
+#pragma unroll
+        for (int r = 0; r < p; ++r) {
+            const double l = __ldg(a.Lf + (size_t)tri(p, r) * a.V + v);
+            s.x -= l * b[r].x;
+            s.y -= l * b[r].y;
+        }
+        b[p] = cscale(s, __ldg(a.Linv + (size_t)p * a.V + v));
+    }
+#pragma unroll
+    for (int p = NN - 1; p >= 0; --p) {
+        double2 s = b[p];
+#pragma unroll
+        for (int r = p + 1; r < NN; ++r) {
+            const double l = __ldg(a.Lf + (size_t)tri(r, p) * a.V + v);
+            s.x -= l * b[r].x;
+            s.y -= l * b[r].y;
+        }
+        b[p] = cscale(s, __ldg(a.Linv + (size_t)p * a.V + v));
     }
 }
 
@@ -359,7 +394,7 @@ __global__ void __launch_bounds__(kBT) k_binit(BArgs a) {
         for (int p = 0; p < NN; ++p) {
             a.g[(size_t)p * a.V + v] = y[p];
             a.G[(size_t)p * a.V + v] = G[p];
-            a.Q[(size_t)p * a.V + v] = make_double2(G[p].x - y[p].x / a.rho, G[p].y - y[p].y / a.rho);
+            a.Q[(size_t)p * a.V + v] = make_double2(G[p].x - y[p].x * a.inv_rho, G[p].y - y[p].y * a.inv_rho);
         }
     }
 }
@@ -381,7 +416,7 @@ __global__ void __launch_bounds__(kBT) k_bdiv(BArgs a) {
                 re += (w.x * c + w.y * s) - (u.x * c - u.y * s);
                 im += (w.y * c - w.x * s) - (u.x * s + u.y * c);
             }
-            a.B[(size_t)i * a.V + v] = make_double2(a.half_n * re, a.half_n * im);
+            a.B[(size_t)i * a.V + v] = make_double2(re, im);
         }
     }
 }
@@ -516,6 +551,30 @@ __device__ __forceinline__ void kw_merge(double& k, double& w, double k2, double
     }
 }
 
+// Block-wide (sum of ws, merge of (km, wm)); valid in thread 0.
+__device__ __forceinline__ void block_merge3(double& ws, double& km, double& wm) {
+    __shared__ double s3[kBT / 32][3];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ws += __shfl_down_sync(0xffffffffu, ws, o);
+        const double k2 = __shfl_down_sync(0xffffffffu, km, o), w2 = __shfl_down_sync(0xffffffffu, wm, o);
+        kw_merge(km, wm, k2, w2);
+    }
+    if (lane == 0) {
+        s3[wi][0] = ws;
+        s3[wi][1] = km;
+        s3[wi][2] = wm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 1; i < kBT / 32; ++i) {
+            ws += s3[i][0];
+            kw_merge(km, wm, s3[i][1], s3[i][2]);
+        }
+    __syncthreads();
+}
+
 template <int D>
 __global__ void __launch_bounds__(kBT) k_bweights(BArgs a) {
     if (a.ctrl->stop) return;
@@ -531,26 +590,9 @@ __global__ void __launch_bounds__(kBT) k_bweights(BArgs a) {
         ws += w;
         kw_merge(km, wm, kappa_of<D>(a, v), w);
     }
-    __shared__ double s3[kBT / 32][3];
     __shared__ int s_last;
-    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        ws += __shfl_down_sync(0xffffffffu, ws, o);
-        const double k2 = __shfl_down_sync(0xffffffffu, km, o), w2 = __shfl_down_sync(0xffffffffu, wm, o);
-        kw_merge(km, wm, k2, w2);
-    }
-    if (lane == 0) {
-        s3[wi][0] = ws;
-        s3[wi][1] = km;
-        s3[wi][2] = wm;
-    }
-    __syncthreads();
+    block_merge3(ws, km, wm);
     if (threadIdx.x == 0) {
-        for (int i = 1; i < kBT / 32; ++i) {
-            ws += s3[i][0];
-            kw_merge(km, wm, s3[i][1], s3[i][2]);
-        }
         a.part[blockIdx.x * 4 + 0] = ws;
         a.part[blockIdx.x * 4 + 1] = km;
         a.part[blockIdx.x * 4 + 2] = wm;
@@ -558,15 +600,17 @@ __global__ void __launch_bounds__(kBT) k_bweights(BArgs a) {
         s_last = atomicAdd(&a.ctrl->counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return;
     __threadfence();
-    ws = __ldcg(a.part);
-    km = __ldcg(a.part + 1);
-    wm = __ldcg(a.part + 2);
-    for (unsigned b = 1; b < gridDim.x; ++b) {
+    ws = 0.0;
+    km = 1e300;
+    wm = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kBT) {
         ws += __ldcg(a.part + b * 4);
         kw_merge(km, wm, __ldcg(a.part + b * 4 + 1), __ldcg(a.part + b * 4 + 2));
     }
+    block_merge3(ws, km, wm);
+    if (threadIdx.x != 0) return;
     BCtrl* c = a.ctrl;
     c->counter = 0u;
     const double pole = __dmul_rn(a.rho, km), Vd = (double)a.V;
@@ -596,10 +640,10 @@ __global__ void __launch_bounds__(kBT) k_broot(BArgs a, int last) {
     const double sig = cc->sigma, r2 = a.rho * a.rho;
     double v2[2] = {0.0, 0.0};
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
-        const double den = __dsub_rn(__dmul_rn(a.rho, kappa_of<D>(a, v)), sig);
-        const double q = r2 * a.W[v] / (den * den);
+        const double inv = 1.0 / __dsub_rn(__dmul_rn(a.rho, kappa_of<D>(a, v)), sig);
+        const double q = r2 * a.W[v] * inv * inv;
         v2[0] += q;
-        v2[1] += 2.0 * q / den;
+        v2[1] += 2.0 * q * inv;
     }
     if (!grid_reduce<2>(v2, a.part, a.ctrl)) return;
     BCtrl* c = a.ctrl;
@@ -652,33 +696,33 @@ __global__ void __launch_bounds__(kBT) k_bphat(BArgs a) {
 // Step 1' of iteration i + 1 (G_{i+1}, Q); p_i is copied to Pnew.  The last block
 // finishes the residuals, records them and sets the stop flag.
 template <int D>
-__global__ void __launch_bounds__(kBT) k_blocal(BArgs a, const double2* __restrict__ Pold, double2* __restrict__ Pnew) {
+__global__ void __launch_bounds__(kBT, 2) k_blocal(BArgs a, const double2* __restrict__ Pold, double2* __restrict__ Pnew) {
     constexpr int NN = D * D;
     if (a.ctrl->stop) return;
     double v2[2] = {0.0, 0.0};
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
         int up[3], dn[3];
         bneighbours<D>(v, a.n, up, dn);
-        double2 Dn[NN], Do[NN], rhs[NN], G[NN];
-        bloch_grad<D>(a.B, a, up, dn, Dn);
-        bloch_grad<D>(Pold, a, up, dn, Do);
+        double2 x[NN], gn[NN];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const int p = i * D + j;
+                const double2 Dn = bloch_grad1(a.B, a, i, j, up[j], dn[j]);
+                const double2 Do = bloch_grad1(Pold, a, i, j, up[j], dn[j]);
+                const double2 e = csub(Dn, a.G[(size_t)p * a.V + v]), dd = csub(Dn, Do);
+                v2[0] += e.x * e.x + e.y * e.y;
+                v2[1] += dd.x * dd.x + dd.y * dd.y;
+                gn[p] = cadd(a.g[(size_t)p * a.V + v], cscale(e, a.rho));  // Step 3'
+                x[p] = cadd(gn[p], cscale(Dn, a.rho));
+            }
+        fsolve_inplace<NN>(a, v, x);  // Step 1' of the next iteration
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
-            const double2 Gp = a.G[(size_t)p * a.V + v];
-            double2 gp = a.g[(size_t)p * a.V + v];
-            const double2 e = csub(Dn[p], Gp), dd = csub(Dn[p], Do[p]);
-            v2[0] += e.x * e.x + e.y * e.y;
-            v2[1] += dd.x * dd.x + dd.y * dd.y;
-            gp = cadd(gp, cscale(e, a.rho));  // Step 3'
-            Do[p] = gp;
-            rhs[p] = cadd(gp, cscale(Dn[p], a.rho));
-        }
-        fsolve<NN>(a, v, rhs, G);  // Step 1' of the next iteration
-#pragma unroll
-        for (int p = 0; p < NN; ++p) {
-            a.g[(size_t)p * a.V + v] = Do[p];
-            a.G[(size_t)p * a.V + v] = G[p];
-            a.Q[(size_t)p * a.V + v] = make_double2(G[p].x - Do[p].x / a.rho, G[p].y - Do[p].y / a.rho);
+            a.g[(size_t)p * a.V + v] = gn[p];
+            a.G[(size_t)p * a.V + v] = x[p];
+            a.Q[(size_t)p * a.V + v] = make_double2(x[p].x - gn[p].x * a.inv_rho, x[p].y - gn[p].y * a.inv_rho);
         }
 #pragma unroll
         for (int i = 0; i < D; ++i) Pnew[(size_t)i * a.V + v] = a.B[(size_t)i * a.V + v];
@@ -799,12 +843,13 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     a.V = (int)V;
     a.half_n = 0.5 * n;
     a.rho = in.rho;
+    a.inv_rho = 1.0 / in.rho;
     a.tol = in.tol;
     a.rd_scale = in.rho / in.mu_ref;
     for (int j = 0; j < 3; ++j) {
         const double th = j < D ? 2.0 * kPi / ((double)in.k[j] * n) : 0.0;
-        a.c[j] = cos(th);
-        a.s[j] = sin(th);
+        a.c[j] = a.half_n * cos(th);
+        a.s[j] = a.half_n * sin(th);
     }
     a.P0 = (double2*)(b + oP0);
     a.P1 = (double2*)(b + oP1);
@@ -871,30 +916,66 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     CKB(cudaEventCreate(&e0));
     CKB(cudaEventCreate(&e1));
     CKB(cudaEventRecord(e0, st));
+    auto iteration = [&](long long i) {  // iteration i reads p_{i-1} and writes p_i
+        double2* Pold = ((i - 1) & 1) ? a.P1 : a.P0;
+        double2* Pnew = (i & 1) ? a.P1 : a.P0;
+        const int passes = i == 1 ? kRootPasses0 : (i == 2 ? kRootPasses1 : kRootPasses);
+        k_bdiv<D><<<eg, kBT, 0, st>>>(a);
+        fft_all<D, false>(a, tw, pl, smem, fg, st);
+        k_bweights<D><<<eg, kBT, 0, st>>>(a);
+        for (int r = 0; r < passes; ++r) k_broot<D><<<eg, kBT, 0, st>>>(a, r == passes - 1);
+        k_bphat<D><<<eg, kBT, 0, st>>>(a);
+        fft_all<D, true>(a, tw, pl, smem, fg, st);
+        k_blocal<D><<<eg, kBT, 0, st>>>(a, Pold, Pnew);
+        return 4 + 2 * D + passes;
+    };
+    // The first chunk runs as plain launches (its first iterations take more root
+    // passes); later full chunks replay a graph per starting parity of p.
     long long it = 0;
     const int chunk = std::max(1, in.check_every);
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int per_chunk = 0;
+    auto drop_graphs = [&]() {
+        for (auto& g : graph)
+            if (g) cudaGraphExecDestroy(g);
+    };
     while (it < in.max_iter) {
         const long long m = std::min<long long>(chunk, in.max_iter - it);
-        for (long long q = 0; q < m; ++q) {
-            const long long i = it + q + 1;  // iteration i reads p_{i-1} and writes p_i
-            double2* Pold = ((i - 1) & 1) ? a.P1 : a.P0;
-            double2* Pnew = (i & 1) ? a.P1 : a.P0;
-            k_bdiv<D><<<eg, kBT, 0, st>>>(a);
-            fft_all<D, false>(a, tw, pl, smem, fg, st);
-            k_bweights<D><<<eg, kBT, 0, st>>>(a);
-            const int passes = i == 1 ? kRootPasses0 : (i == 2 ? kRootPasses1 : kRootPasses);
-            for (int r = 0; r < passes; ++r) k_broot<D><<<eg, kBT, 0, st>>>(a, r == passes - 1);
-            k_bphat<D><<<eg, kBT, 0, st>>>(a);
-            fft_all<D, true>(a, tw, pl, smem, fg, st);
-            k_blocal<D><<<eg, kBT, 0, st>>>(a, Pold, Pnew);
-            launches += 4 + 2 * D + passes;
+        if (it >= 2 && m == chunk) {
+            const int par = (int)(it & 1);
+            if (!graph[par]) {
+                cudaGraph_t g = nullptr;
+                per_chunk = 0;
+                if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                    drop_graphs();
+                    return RVE_E_CUDA;
+                }
+                for (long long q = 0; q < m; ++q) per_chunk += iteration(it + q + 1);
+                const cudaError_t ec = cudaStreamEndCapture(st, &g);
+                const cudaError_t ei = ec == cudaSuccess ? cudaGraphInstantiate(&graph[par], g, 0) : ec;
+                if (g) cudaGraphDestroy(g);
+                if (ei != cudaSuccess) {
+                    drop_graphs();
+                    return RVE_E_CUDA;
+                }
+            }
+            if (cudaGraphLaunch(graph[par], st) != cudaSuccess) {
+                drop_graphs();
+                return RVE_E_CUDA;
+            }
+            launches += per_chunk;
+        } else {
+            for (long long q = 0; q < m; ++q) launches += iteration(it + q + 1);
         }
-        CKB(cudaGetLastError());
-        CKB(cudaMemcpyAsync(hc, a.ctrl, sizeof(BCtrl), cudaMemcpyDeviceToHost, st));
-        CKB(cudaStreamSynchronize(st));
+        if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(hc, a.ctrl, sizeof(BCtrl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            drop_graphs();
+            return RVE_E_CUDA;
+        }
         it += m;
         if (hc->stop) break;
     }
+    drop_graphs();
     CKB(cudaEventRecord(e1, st));
     const long long k = hc->k;
     double2* Pfin = (k & 1) ? a.P1 : a.P0;

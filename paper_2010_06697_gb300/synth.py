@@ -103,6 +103,14 @@ def inclusion_phase(n: int, dim: int, seed: int, radius: int = 6,
     return ph
 
 
+def disc_phase(n: int, dim: int, radius: float) -> np.ndarray:
+    """One centred circular (spherical in 3D) inclusion (phase 1) of the given radius
+    (in cell lengths) in a matrix (phase 0): a voxel is inside when its centre is."""
+    c = (np.arange(n) + 0.5) / n - 0.5
+    grids = np.meshgrid(*([c] * dim), indexing="ij")
+    return (sum(g * g for g in grids) <= radius * radius).astype(np.uint8)
+
+
 def director_grf(n: int, seed: int, corr: float = 8.0) -> np.ndarray:
     """Polydomain director field n0 on an n^3 grid, shape (3, n, n, n), unit length.
 
