@@ -347,6 +347,7 @@ def run_ours(args):
                           lambda t, r, sy: bench_inexact128(t, r, sy, ratio=0.0, fraction=0.9)),
                          ("lce256", bench_lce256), ("lce128_pe_path", bench_lce_path128),
                          ("lce128_pe_path_inc", lambda t, r, sy: bench_lce_path128(t, r, sy, incompressible=True)),
+                         ("bloch512_2d", bench_bloch512),
                          ("batch64", bench_batch64), ("serving", bench_serving)):
             try:
                 extra[name] = fn(torch, rve, synth)
@@ -494,6 +495,26 @@ def bench_lce_path128(torch, rve, synth, incompressible=False, steps=5, iters=30
             "unit": UNIT, "ms": ms, "load_steps": steps, "iterations": its, "precision": "fp64",
             "S11": [float(x[0, 0]) for x in S], "F33": [float(x[2, 2]) for x in Fo],
             "r_p_last": infos[-1].r_p, "r_d_last": infos[-1].r_d}
+
+
+def bench_bloch512(torch, rve, synth, iters=400):
+    """2D 512^2 modulus of stability beta_(2,2) (Section 2.4 with Section 4.3's example):
+    one centred soft disc of radius 0.4, mu_m / mu_i = 20, kappa / mu = 9.8 in both phases,
+    equi-biaxial compression <F> = 0.94 I solved to 1e-9 (FP64), then the Bloch-wave ADMM
+    (FP64, rho = 200) for a fixed iteration count, timed on the device."""
+    n = 512
+    ph = synth.disc_phase(n, 2, 0.4)
+    par = np.array([[20.0, 196.0], [1.0, 9.8]])
+    s = rve.Rve(2, n, "neohookean", "fp64", max_iter=20000)
+    s.set_material(ph, par)
+    si = s.solve(np.diag([0.94, 0.94, 1.0]), 30.0, 1e-9)
+    s.bloch((2, 2), 200.0, -1.0, 20, seed=0)  # warm-up (kernels, graphs)
+    bi, _, hist = s.bloch((2, 2), 200.0, -1.0, iters, seed=0)
+    s.close()
+    return {"workload": "bloch512_2d", "value": ph.size * bi.iterations / (bi.time_ms / 1e3), "unit": UNIT,
+            "ms_per_iteration": bi.time_ms / bi.iterations, "iterations": bi.iterations, "launches": bi.launches,
+            "beta22": bi.beta, "rayleigh": bi.rayleigh, "r_p": bi.r_p, "r_d": bi.r_d, "precision": "fp64",
+            "equilibrium_iterations": si.iterations, "equilibrium_converged": bool(si.converged)}
 
 
 def bench_batch64(torch, rve, synth, count=64):
