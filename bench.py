@@ -342,13 +342,7 @@ def run_ours(args):
     if world == 1 and not args.no_extra:
         from paper_2010_06697_gb300 import synth
         extra = {}
-        for name, fn in (("laminate32_2d", bench_laminate32), ("inclusions128_inexact", bench_inexact128),
-                         ("inclusions128_fraction",
-                          lambda t, r, sy: bench_inexact128(t, r, sy, ratio=0.0, fraction=0.9)),
-                         ("lce256", bench_lce256), ("lce128_pe_path", bench_lce_path128),
-                         ("lce128_pe_path_inc", lambda t, r, sy: bench_lce_path128(t, r, sy, incompressible=True)),
-                         ("bloch512_2d", bench_bloch512),
-                         ("batch64", bench_batch64), ("serving", bench_serving)):
+        for name, fn in other_workloads():
             try:
                 extra[name] = fn(torch, rve, synth)
             except Exception as e:  # report, do not lose the main line
@@ -359,6 +353,30 @@ def run_ours(args):
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def other_workloads():
+    """The workloads reported beside the headline line, as (name, function) pairs."""
+    return (("laminate32_2d", bench_laminate32), ("inclusions128_inexact", bench_inexact128),
+            ("inclusions128_fraction", lambda t, r, sy: bench_inexact128(t, r, sy, ratio=0.0, fraction=0.9)),
+            ("lce256", bench_lce256), ("lce128_pe_path", bench_lce_path128),
+            ("lce128_pe_path_inc", lambda t, r, sy: bench_lce_path128(t, r, sy, incompressible=True)),
+            ("bloch512_2d", bench_bloch512), ("batch64", bench_batch64), ("serving", bench_serving))
+
+
+def run_workload(args):
+    """One of the other workloads alone (for profiler captures); prints its JSON object."""
+    import torch
+    from paper_2010_06697_gb300 import build, rve, synth
+    torch.cuda.set_device(0)
+    build.build()
+    rve.lib()
+    fns = dict(other_workloads())
+    if args.workload not in fns:
+        print(json.dumps({"error": f"unknown workload {args.workload}", "known": sorted(fns)}))
+        return 2
+    print(json.dumps(fns[args.workload](torch, rve, synth)))
     return 0
 
 
@@ -632,9 +650,13 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the LCE, batch and serving workloads")
     ap.add_argument("--single", action="store_true",
                     help="one solve of the workload (for profiler captures), prints a short summary")
+    ap.add_argument("--workload", default=None,
+                    help="run one of the other workloads alone (for profiler captures) and print its JSON")
     args = ap.parse_args()
     if args.single:
         return run_single(args)
+    if args.workload:
+        return run_workload(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
