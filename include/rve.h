@@ -239,7 +239,10 @@ typedef struct rve_bloch_info {
  * integers, at least one with |k_j| >= 2 (otherwise the Bloch operator has null
  * modes).  p0: host, 2 d N^d doubles, the start p_0 as (re, im) pairs,
  * component-major like the fields (normalised by the call; not all zero).  rho:
- * penalty, L + rho I must be positive definite everywhere.  tol: bound on r_p and
+ * penalty, L + rho I must be positive definite everywhere; the iteration count grows
+ * about linearly with rho, and a rho too close to the most negative eigenvalue of L
+ * lets the iteration diverge (measured on a compressed two-phase cell: stable and
+ * fastest near twice that eigenvalue's magnitude).  tol: bound on r_p and
  * r_d (r_d scaled by rho / mu_ref as for rve_solve); max_iter > 0.  p_out (host,
  * same layout as p0) receives the final p and hist (host, 3 doubles per
  * iteration: r_p, r_d, sigma) the history; either may be NULL.  Models

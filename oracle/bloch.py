@@ -96,8 +96,10 @@ def constrained_step(b_hat: np.ndarray, kappa: np.ndarray, rho: float, nvox: int
         S = np.sum(rho * rho * W / (rho * kappa - sig) ** 2) / (nvox * nvox)
         return 1.0 / np.sqrt(S) - 1.0
 
-    lo = pole - rho * np.sqrt(total) / nvox  # ||p(lo)|| <= 1
+    lo = pole - 2.0 * rho * np.sqrt(total) / nvox  # ||p(lo)|| <= 1/2
     hi = pole
+    if not (np.isfinite(total) and total > 0.0):
+        raise FloatingPointError("Step 2': b is zero or not finite (the iteration diverged?)")
     if not psi(np.nextafter(hi, -np.inf)) < 0.0:
         raise FloatingPointError("Step 2': no root below the pole (hard case)")
     sigma = brentq(psi, lo, np.nextafter(hi, -np.inf), xtol=1e-300, rtol=4 * np.finfo(float).eps, maxiter=500)

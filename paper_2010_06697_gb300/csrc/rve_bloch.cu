@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(kBT) k_bfft(BArgs a, const double2* __restrict
 
 // W(m) = sum_i |b^_i(m)|^2, with sum W, min kappa and W_min, the sum of W where kappa
 // is minimal.  The last block brackets the root of ||p(sigma)|| = 1 below the pole
-// rho min kappa: lo = pole - rho sqrt(sum W) / V has ||p|| <= 1, and
+// rho min kappa: lo = pole - 2 rho sqrt(sum W) / V has ||p|| <= 1/2, and
 // sigma_R = pole - rho sqrt(W_min) / V has ||p|| >= 1 (its W_min terms alone reach 1),
 // so the root lies in [lo, sigma_R]; Newton starts from the previous sigma when it
 // lies inside, else from sigma_R (where phi is concave and Newton is monotone).
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(kBT) k_bweights(BArgs a) {
     BCtrl* c = a.ctrl;
     c->counter = 0u;
     const double pole = __dmul_rn(a.rho, km), Vd = (double)a.V;
-    const double lo = pole - a.rho * sqrt(ws) / Vd;
+    const double lo = pole - 2.0 * a.rho * sqrt(ws) / Vd;
     const double sr = fmin(pole - a.rho * sqrt(wm) / Vd, nextafter(pole, -1e300));
     c->pole = pole;
     c->root_done = 0;
