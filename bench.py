@@ -362,7 +362,8 @@ def other_workloads():
             ("inclusions128_fraction", lambda t, r, sy: bench_inexact128(t, r, sy, ratio=0.0, fraction=0.9)),
             ("lce256", bench_lce256), ("lce128_pe_path", bench_lce_path128),
             ("lce128_pe_path_inc", lambda t, r, sy: bench_lce_path128(t, r, sy, incompressible=True)),
-            ("bloch512_2d", bench_bloch512), ("batch64", bench_batch64), ("serving", bench_serving))
+            ("bloch512_2d", bench_bloch512), ("bloch128_3d", bench_bloch128_3d), ("batch64", bench_batch64),
+            ("serving", bench_serving))
 
 
 def run_workload(args):
@@ -532,6 +533,26 @@ def bench_bloch512(torch, rve, synth, iters=400):
     return {"workload": "bloch512_2d", "value": ph.size * bi.iterations / (bi.time_ms / 1e3), "unit": UNIT,
             "ms_per_iteration": bi.time_ms / bi.iterations, "iterations": bi.iterations, "launches": bi.launches,
             "beta22": bi.beta, "rayleigh": bi.rayleigh, "r_p": bi.r_p, "r_d": bi.r_d, "precision": "fp64",
+            "equilibrium_iterations": si.iterations, "equilibrium_converged": bool(si.converged)}
+
+
+def bench_bloch128_3d(torch, rve, synth, iters=100):
+    """3D 128^3 modulus of stability beta_(2,2,2): the 128^3 inclusion cell of the headline
+    (matrix mu = 1, spherical inclusions mu = 10, nu = 0.3) compressed to <F> = 0.95 I and
+    solved to 1e-8 (mixed), then the Bloch-wave ADMM (FP64, rho = 40) for a fixed
+    iteration count, timed on the device."""
+    n = 128
+    ph = synth.inclusion_phase(n, 3, 0, radius=6)
+    par = synth.two_phase_params(1.0, 10.0)
+    s = rve.Rve(3, n, "neohookean", "mixed", max_iter=4000)
+    s.set_material(ph, par)
+    si = s.solve(np.diag([0.95, 0.95, 0.95]), RHO, 1e-8)
+    s.bloch((2, 2, 2), 40.0, -1.0, 10, seed=0)  # warm-up (kernels, graphs)
+    bi, _, _ = s.bloch((2, 2, 2), 40.0, -1.0, iters, seed=0)
+    s.close()
+    return {"workload": "bloch128_3d", "value": ph.size * bi.iterations / (bi.time_ms / 1e3), "unit": UNIT,
+            "ms_per_iteration": bi.time_ms / bi.iterations, "iterations": bi.iterations, "launches": bi.launches,
+            "beta222": bi.beta, "r_p": bi.r_p, "r_d": bi.r_d, "precision": "fp64",
             "equilibrium_iterations": si.iterations, "equilibrium_converged": bool(si.converged)}
 
 

@@ -152,3 +152,24 @@ def test_beta22_changes_sign_under_compression():
         assert info.converged
         betas.append(info.beta)
     assert betas[0] > 0.0 > betas[1]
+
+
+def test_bloch_full_size_matches_oracle():
+    """At 512^2 (the Bloch bench's grid; multi-tile FFT lines, 1024-block reductions),
+    on a synthetic near-identity F field of a two-phase neo-Hookean cell: p, sigma and
+    the residual history after 5 iterations element by element against the oracle,
+    and ||p|| = 1."""
+    d, n, k, its = 2, 512, (3, 4), 5
+    ph = synth.inclusion_phase(n, d, 5, radius=20)
+    par = synth.two_phase_params(1.0, 4.0)
+    F = near_identity_field(n, d, 9, amp=0.05)
+    p0 = synth.bloch_start(n, d, 4)
+    s = handle_with_state(d, n, "neohookean", ph, par, F)
+    info, p, hist = s.bloch(k, 8.0, -1.0, its, p0=p0)
+    mu_ref = float(np.mean(par[ph.reshape(-1), 0]))
+    ref = bloch.bloch_solve(bloch.tangent_field("neohookean", ph, par, F), p0, k, 8.0, -1.0, its, mu_ref)
+    assert info.iterations == its
+    assert rel(p, ref["p"]) < 1e-10
+    np.testing.assert_allclose(info.beta, ref["sigma"], rtol=1e-11)
+    np.testing.assert_allclose(hist[:, :2], np.array(ref["history"]), rtol=1e-8, atol=1e-13)
+    assert abs(np.sum(np.abs(p) ** 2) / n ** d - 1.0) < 1e-12
