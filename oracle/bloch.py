@@ -31,6 +31,12 @@ i.e. the smallest eigenvalue of D^* L D.  Steps of one iteration i -> i + 1:
 At a fixed point D p = G, L G = g and D^* L D p = sigma p: sigma is the eigenvalue
 (and the minimum of the augmented Lagrangian is reached at the smallest one).
 Start: p_0 = the given field normalised, g_0 = L D p_0.
+
+Penalty: fixed, or Section 2.1's residual balancing after every Step 4' (rho <- kappa rho
+if r_p > tau r_d, rho <- max(rho / kappa, rho_floor) if r_d > tau r_p), with
+rho_floor = max(rho_min (default mu_ref), 2 max(0, -lambda_min(L))): L + rho I must stay
+positive definite for Step 1', and below about twice the most negative eigenvalue of L
+the iteration was seen to diverge.
 """
 from __future__ import annotations
 
@@ -106,20 +112,29 @@ def constrained_step(b_hat: np.ndarray, kappa: np.ndarray, rho: float, nvox: int
     return sigma, rho * b_hat / (rho * kappa - sigma)
 
 
-def bloch_solve(L: np.ndarray, p0: np.ndarray, k, rho: float, tol: float, max_iter: int, mu_ref: float):
+def rho_floor(L: np.ndarray, mu_ref: float, rho_min=None) -> float:
+    """max(rho_min (default mu_ref), 2 max(0, -lambda_min)) over the voxels' L."""
+    d2 = L.shape[1] * L.shape[2]
+    lmin = float(np.min(np.linalg.eigvalsh(L.reshape(-1, d2, d2))))
+    return max(rho_min if rho_min else mu_ref, 2.0 * max(0.0, -lmin))
+
+
+def bloch_solve(L: np.ndarray, p0: np.ndarray, k, rho: float, tol: float, max_iter: int, mu_ref: float,
+                rho_policy: str = "fixed", kappa: float = 1.3, tau: float = 10.0, rho_min=None):
     """Steps 1'-4' from p_0 (normalised here) until r_p <= tol and r_d <= tol or max_iter.
 
     L: (V, d, d, d, d) tangent field (voxels in C order of the grid); p0: (d, *grid)
     complex.  Returns dict with p, G, g, sigma (Step 2's multiplier of the last
-    iteration), history [(r_p, r_d)], iterations, converged, rayleigh = <Dp, L Dp>."""
+    iteration), history [(r_p, r_d)], rhos (the penalty of every iteration),
+    iterations, converged, rayleigh = <Dp, L Dp>."""
     d = p0.shape[0]
     grid = p0.shape[1:]
     V = int(np.prod(grid))
     n = grid[-1]
     s = bloch_symbols(n, d, k)
-    kappa = sum(sj * sj for sj in s) * np.ones(grid)
+    kap = sum(sj * sj for sj in s) * np.ones(grid)  # |s|^2 per frequency
     Lm = L.reshape(V, d * d, d * d)
-    A = Lm + rho * np.eye(d * d)[None]
+    floor = rho_floor(L, mu_ref, rho_min) if rho_policy == "adaptive" else None
 
     def apply(M, T):  # per-voxel (d*d, d*d) matrix on a (d, d, *grid) field
         Tv = T.reshape(d * d, V).T
@@ -127,6 +142,7 @@ def bloch_solve(L: np.ndarray, p0: np.ndarray, k, rho: float, tol: float, max_it
 
     def solve(T):
         Tv = T.reshape(d * d, V).T
+        A = Lm + rho * np.eye(d * d)[None]
         return np.linalg.solve(A, Tv[..., None])[..., 0].T.reshape((d, d) + grid)
 
     p = np.array(p0, dtype=np.complex128)
@@ -134,6 +150,7 @@ def bloch_solve(L: np.ndarray, p0: np.ndarray, k, rho: float, tol: float, max_it
     Dp = bloch_grad(p, k)
     g = apply(Lm, Dp)
     hist = []
+    rhos = []
     sigma = np.nan
     converged = False
     it = 0
@@ -142,17 +159,23 @@ def bloch_solve(L: np.ndarray, p0: np.ndarray, k, rho: float, tol: float, max_it
         Q = G - g / rho                                                # Step 2'
         Qh = np.fft.fftn(Q, axes=_axes(d, 2))
         b_hat = np.stack([sum(-1j * s[j] * Qh[i, j] for j in range(d)) for i in range(d)])
-        sigma, p_hat = constrained_step(b_hat, kappa, rho, V)
+        sigma, p_hat = constrained_step(b_hat, kap, rho, V)
         p_new = np.fft.ifftn(p_hat, axes=_axes(d, 1))
         Dp_new = bloch_grad(p_new, k)
         g = g + rho * (Dp_new - G)                                     # Step 3'
         r_p = norm(Dp_new - G)                                         # Step 4'
         r_d = rho / mu_ref * norm(Dp_new - Dp)
         hist.append((r_p, r_d))
+        rhos.append(rho)
         p, Dp = p_new, Dp_new
         if r_p <= tol and r_d <= tol:
             converged = True
             break
+        if rho_policy == "adaptive":
+            if r_d > 0.0 and r_p / r_d > tau:
+                rho = kappa * rho
+            elif r_p > 0.0 and r_d / r_p > tau:
+                rho = max(rho / kappa, floor)
     rq = float(np.real(np.sum(np.conj(Dp) * apply(Lm, Dp))) / V)
-    return {"p": p, "G": G if max_iter > 0 else None, "g": g, "sigma": sigma, "history": hist,
+    return {"p": p, "G": G if max_iter > 0 else None, "g": g, "sigma": sigma, "history": hist, "rhos": rhos,
             "iterations": it if max_iter > 0 else 0, "converged": converged, "rayleigh": rq}

@@ -155,3 +155,24 @@ def test_planted_mistakes_fail_the_dense_pin(monkeypatch, name, fn):
     monkeypatch.setattr(bloch, name, fn)
     r = bloch.bloch_solve(L, start_field(n, d, 1), k, 10.0, 1e-10, 3000, 1.0)
     assert not (r["converged"] and abs(r["rayleigh"] - w[0]) <= 1e-9 * abs(w[0]))
+
+
+@pytest.mark.parametrize("d,n,k", [(2, 6, (3, -2)), (3, 4, (2, 3, 1))])
+def test_adaptive_rho_reaches_the_same_eigenvalue(d, n, k):
+    """Section 2.1's residual balancing applied to Steps 1'-4' changes the path, not the
+    fixed point: the converged sigma is the dense smallest eigenvalue, rho never drops
+    below the floor and it changes by the factor kappa."""
+    ph = synth.inclusion_phase(n, d, 3, radius=1)
+    par = synth.two_phase_params(1.0, 4.0)
+    L = bloch.tangent_field("neohookean", ph, par, near_identity_field(n, d, 5))
+    w, _, _ = dense_beta(L, n, d, k)
+    r = bloch.bloch_solve(L, start_field(n, d, 1), k, 60.0, 1e-10, 20000, 1.0, rho_policy="adaptive")
+    assert r["converged"]
+    np.testing.assert_allclose(r["sigma"], w[0], rtol=1e-9)
+    floor = bloch.rho_floor(L, 1.0)
+    rh = np.array(r["rhos"])
+    assert np.all(rh >= floor * (1 - 1e-12))
+    ratios = rh[1:] / rh[:-1]
+    assert np.all(np.isclose(ratios, 1.0) | np.isclose(ratios, 1.3) | np.isclose(ratios, 1 / 1.3)
+                  | np.isclose(rh[1:], floor))
+    assert rh[-1] < 60.0
