@@ -227,6 +227,7 @@ typedef struct rve_bloch_info {
     int fail;            /* RVE_E_NUMERICAL causes, bits: 1 L + rho I not positive
                             definite, 2 b^ has no weight at the lowest kappa (Step 2'
                             hard case), 4 Step 2' root not found in its passes     */
+    double rho;          /* penalty of the last iteration                          */
 } rve_bloch_info;
 
 /* Modulus of stability beta_k (Section 2.4): the minimum over unit Bloch waves
@@ -243,9 +244,14 @@ typedef struct rve_bloch_info {
  * about linearly with rho, and a rho too close to the most negative eigenvalue of L
  * lets the iteration diverge (measured on a compressed two-phase cell: stable and
  * fastest near twice that eigenvalue's magnitude).  tol: bound on r_p and
- * r_d (r_d scaled by rho / mu_ref as for rve_solve); max_iter > 0.  p_out (host,
- * same layout as p0) receives the final p and hist (host, 3 doubles per
- * iteration: r_p, r_d, sigma) the history; either may be NULL.  Models
+ * r_d (r_d scaled by rho / mu_ref as for rve_solve); max_iter > 0.  The handle's
+ * opt.rho_policy applies: RVE_RHO_ADAPTIVE balances the residuals as for rve_solve
+ * (Section 2.1: rho times opt.rho_kappa when r_p > opt.rho_tau r_d, divided by it when
+ * r_d > opt.rho_tau r_p) with the floor max(opt.rho_min or mu_ref, 2 s*), s* the
+ * smallest shift making L + s* I positive definite everywhere (found by bisection,
+ * once per call); rho is then the starting penalty, and a large one is fine.  p_out
+ * (host, same layout as p0) receives the final p and hist (host, 4 doubles per
+ * iteration: r_p, r_d, sigma, rho) the history; either may be NULL.  Models
  * RVE_NEOHOOKE and RVE_LINEAR.  The call keeps a device workspace of about
  * (48 d^2 + 8 d^2 (d^2 + 1) + 64 d) N^d bytes on the handle until rve_destroy.
  * Returns RVE_OK, RVE_E_NOT_CONVERGED (results valid), RVE_E_INVALID_ARG (k, rho,

@@ -49,6 +49,8 @@ constexpr double kPi = 3.141592653589793238462643383279502884;
 struct BCtrl {
     double sigma, lo, hi, pole;
     double rp, rd;
+    double rho;        // penalty of the current iteration
+    int rho_changed;   // set by the rule after an iteration, cleared by the next k_bdiv
     long long k;       // iterations done
     int stop;          // 1 converged, 3 non-finite residual
     int root_done;     // Step 2' root of the current iteration found
@@ -64,7 +66,9 @@ struct FftPlanB {
 
 struct BArgs {
     int n, V;
-    double half_n, rho, inv_rho, tol, rd_scale;
+    double half_n, tol, inv_mu_ref;
+    int adaptive;          // Section 2.1's residual balancing of rho
+    double kappa, tau, rho_floor;
     double c[3], s[3];     // cos, sin of th_j, times 1/(2h)
     const double* sym;     // s_j(m) at sym[j * n + m]
     double2 *P0, *P1, *B, *G, *g, *Q;
@@ -281,13 +285,20 @@ __device__ __forceinline__ double kappa_of(const BArgs& a, int v) {
 }
 
 // ------------------------------------------------------------------ kernels
+// Every kernel takes rho from the control block: the adaptive rule changes it between
+// iterations.
 
 // L + rho I = W_FF(F) + rho I per voxel (compressible neo-Hookean, Section 4.1, or
 // isotropic linear elasticity), Cholesky-factored in double.
+// mode 0: factor with ctrl->rho; mode 1: the same, only when rho changed (redo after the
+// rule); mode 2: no factor stored, only the positive-definiteness test of L + shift I
+// (fail bit 1), for the floor's bisection.
 template <int D, int MODEL, typename TF>
 __global__ void __launch_bounds__(kBT) k_bfactor(BArgs a, const TF* __restrict__ F, const uint8_t* __restrict__ phase,
-                                                 const double* __restrict__ mat, int nparam) {
+                                                 const double* __restrict__ mat, int nparam, int mode, double shift) {
     constexpr int NN = D * D;
+    if (mode == 1 && !a.ctrl->rho_changed) return;
+    const double rho = mode == 2 ? shift : a.ctrl->rho;
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
         const int ph = phase[v];
         const double mu = __ldg(mat + ph * nparam), lam = __ldg(mat + ph * nparam + 1);
@@ -327,7 +338,7 @@ __global__ void __launch_bounds__(kBT) k_bfactor(BArgs a, const TF* __restrict__
                 for (int q = 0; q <= p; ++q) {
                     const int k = q / D, l = q % D;
                     double h = b * A[p] * A[q] - c * A[i * D + l] * A[k * D + j];
-                    if (p == q) h += mu + a.rho;
+                    if (p == q) h += mu + rho;
                     H[tri(p, q)] = h;
                 }
             }
@@ -340,7 +351,7 @@ __global__ void __launch_bounds__(kBT) k_bfactor(BArgs a, const TF* __restrict__
                 for (int q = 0; q <= p; ++q) {
                     const int k = q / D, l = q % D;
                     double h = mu * (double(i == k && j == l) + double(i == l && j == k)) + lam * double(i == j && k == l);
-                    if (p == q) h += a.rho;
+                    if (p == q) h += rho;
                     H[tri(p, q)] = h;
                 }
             }
@@ -357,7 +368,7 @@ __global__ void __launch_bounds__(kBT) k_bfactor(BArgs a, const TF* __restrict__
                     ok = ok && s > 0.0;
                     const double d = sqrt(fmax(s, 0.0));
                     H[tri(p, p)] = d;
-                    a.Linv[(size_t)p * a.V + v] = ok ? 1.0 / d : 0.0;
+                    if (mode != 2) a.Linv[(size_t)p * a.V + v] = ok ? 1.0 / d : 0.0;
                 } else {
                     H[tri(p, q)] = s / H[tri(q, q)];
                 }
@@ -368,6 +379,7 @@ __global__ void __launch_bounds__(kBT) k_bfactor(BArgs a, const TF* __restrict__
 #pragma unroll
             for (int p = 0; p < NN * (NN + 1) / 2; ++p) H[p] = 0.0;
         }
+        if (mode == 2) continue;
 #pragma unroll
         for (int p = 0; p < NN * (NN + 1) / 2; ++p) a.Lf[(size_t)p * a.V + v] = H[p];
     }
@@ -377,6 +389,7 @@ __global__ void __launch_bounds__(kBT) k_bfactor(BArgs a, const TF* __restrict__
 template <int D>
 __global__ void __launch_bounds__(kBT) k_binit(BArgs a) {
     constexpr int NN = D * D;
+    const double rho = a.ctrl->rho, inv_rho = 1.0 / rho;
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
         int up[3], dn[3];
         bneighbours<D>(v, a.n, up, dn);
@@ -385,16 +398,16 @@ __global__ void __launch_bounds__(kBT) k_binit(BArgs a) {
         fapply<NN>(a, v, Dp, y);
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
-            const double2 g0 = csub(y[p], cscale(Dp[p], a.rho));
+            const double2 g0 = csub(y[p], cscale(Dp[p], rho));
             y[p] = g0;
-            rhs[p] = cadd(g0, cscale(Dp[p], a.rho));
+            rhs[p] = cadd(g0, cscale(Dp[p], rho));
         }
         fsolve<NN>(a, v, rhs, G);
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
             a.g[(size_t)p * a.V + v] = y[p];
             a.G[(size_t)p * a.V + v] = G[p];
-            a.Q[(size_t)p * a.V + v] = make_double2(G[p].x - y[p].x * a.inv_rho, G[p].y - y[p].y * a.inv_rho);
+            a.Q[(size_t)p * a.V + v] = make_double2(G[p].x - y[p].x * inv_rho, G[p].y - y[p].y * inv_rho);
         }
     }
 }
@@ -403,6 +416,7 @@ __global__ void __launch_bounds__(kBT) k_binit(BArgs a) {
 template <int D>
 __global__ void __launch_bounds__(kBT) k_bdiv(BArgs a) {
     if (a.ctrl->stop) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->rho_changed = 0;  // the redo (if any) has run
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
         int up[3], dn[3];
         bneighbours<D>(v, a.n, up, dn);
@@ -613,9 +627,10 @@ __global__ void __launch_bounds__(kBT) k_bweights(BArgs a) {
     if (threadIdx.x != 0) return;
     BCtrl* c = a.ctrl;
     c->counter = 0u;
-    const double pole = __dmul_rn(a.rho, km), Vd = (double)a.V;
-    const double lo = pole - 2.0 * a.rho * sqrt(ws) / Vd;
-    const double sr = fmin(pole - a.rho * sqrt(wm) / Vd, nextafter(pole, -1e300));
+    const double rho = c->rho;
+    const double pole = __dmul_rn(rho, km), Vd = (double)a.V;
+    const double lo = pole - 2.0 * rho * sqrt(ws) / Vd;
+    const double sr = fmin(pole - rho * sqrt(wm) / Vd, nextafter(pole, -1e300));
     c->pole = pole;
     c->root_done = 0;
     if (!(wm > 0.0) || !(lo < sr)) {  // no weight at the lowest kappa: the hard case
@@ -637,10 +652,10 @@ template <int D>
 __global__ void __launch_bounds__(kBT) k_broot(BArgs a, int last) {
     const BCtrl* cc = a.ctrl;
     if (cc->stop || cc->root_done) return;
-    const double sig = cc->sigma, r2 = a.rho * a.rho;
+    const double sig = cc->sigma, rho = cc->rho, r2 = rho * rho;
     double v2[2] = {0.0, 0.0};
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
-        const double inv = 1.0 / __dsub_rn(__dmul_rn(a.rho, kappa_of<D>(a, v)), sig);
+        const double inv = 1.0 / __dsub_rn(__dmul_rn(rho, kappa_of<D>(a, v)), sig);
         const double q = r2 * a.W[v] * inv * inv;
         v2[0] += q;
         v2[1] += 2.0 * q * inv;
@@ -680,10 +695,10 @@ __global__ void __launch_bounds__(kBT) k_broot(BArgs a, int last) {
 template <int D>
 __global__ void __launch_bounds__(kBT) k_bphat(BArgs a) {
     if (a.ctrl->stop) return;
-    const double sig = a.ctrl->sigma, Vd = (double)a.V;
+    const double sig = a.ctrl->sigma, rho = a.ctrl->rho, Vd = (double)a.V;
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
-        const double den = __dsub_rn(__dmul_rn(a.rho, kappa_of<D>(a, v)), sig);
-        const double f = a.rho / (den * Vd);
+        const double den = __dsub_rn(__dmul_rn(rho, kappa_of<D>(a, v)), sig);
+        const double f = rho / (den * Vd);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             const double2 b = a.B[(size_t)i * a.V + v];
@@ -699,6 +714,7 @@ template <int D>
 __global__ void __launch_bounds__(kBT, 2) k_blocal(BArgs a, const double2* __restrict__ Pold, double2* __restrict__ Pnew) {
     constexpr int NN = D * D;
     if (a.ctrl->stop) return;
+    const double rho = a.ctrl->rho, inv_rho = 1.0 / rho;
     double v2[2] = {0.0, 0.0};
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
         int up[3], dn[3];
@@ -714,38 +730,77 @@ __global__ void __launch_bounds__(kBT, 2) k_blocal(BArgs a, const double2* __res
                 const double2 e = csub(Dn, a.G[(size_t)p * a.V + v]), dd = csub(Dn, Do);
                 v2[0] += e.x * e.x + e.y * e.y;
                 v2[1] += dd.x * dd.x + dd.y * dd.y;
-                gn[p] = cadd(a.g[(size_t)p * a.V + v], cscale(e, a.rho));  // Step 3'
-                x[p] = cadd(gn[p], cscale(Dn, a.rho));
+                gn[p] = cadd(a.g[(size_t)p * a.V + v], cscale(e, rho));  // Step 3'
+                x[p] = cadd(gn[p], cscale(Dn, rho));
             }
         fsolve_inplace<NN>(a, v, x);  // Step 1' of the next iteration
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
             a.g[(size_t)p * a.V + v] = gn[p];
             a.G[(size_t)p * a.V + v] = x[p];
-            a.Q[(size_t)p * a.V + v] = make_double2(x[p].x - gn[p].x * a.inv_rho, x[p].y - gn[p].y * a.inv_rho);
+            a.Q[(size_t)p * a.V + v] = make_double2(x[p].x - gn[p].x * inv_rho, x[p].y - gn[p].y * inv_rho);
         }
 #pragma unroll
         for (int i = 0; i < D; ++i) Pnew[(size_t)i * a.V + v] = a.B[(size_t)i * a.V + v];
     }
     if (!grid_reduce<2>(v2, a.part, a.ctrl)) return;
     BCtrl* c = a.ctrl;
-    const double rp = sqrt(v2[0] / (double)a.V), rd = a.rd_scale * sqrt(v2[1] / (double)a.V);
+    const double rp = sqrt(v2[0] / (double)a.V), rd = rho * a.inv_mu_ref * sqrt(v2[1] / (double)a.V);
     if (c->k < a.max_hist) {
-        a.hist[3 * c->k] = rp;
-        a.hist[3 * c->k + 1] = rd;
-        a.hist[3 * c->k + 2] = c->sigma;
+        a.hist[4 * c->k] = rp;
+        a.hist[4 * c->k + 1] = rd;
+        a.hist[4 * c->k + 2] = c->sigma;
+        a.hist[4 * c->k + 3] = rho;
     }
     c->k += 1;
     c->rp = rp;
     c->rd = rd;
     if (!(rp == rp) || !(rd == rd)) c->stop = 3;
     else if (rp <= a.tol && rd <= a.tol) c->stop = 1;
+    else if (a.adaptive) {  // Section 2.1's rule; Step 1' of the next iteration is redone
+        double nr = rho;
+        if (rd > 0.0 && rp / rd > a.tau) nr = a.kappa * rho;
+        else if (rp > 0.0 && rd / rp > a.tau) nr = fmax(rho / a.kappa, a.rho_floor);
+        if (nr != rho) {
+            c->rho = nr;
+            c->rho_changed = 1;
+        }
+    }
+}
+
+// Step 1' again after the rule changed rho (the fused step used the old one):
+// G = (L + rho I)^{-1} (g + rho D p), Q = G - g / rho with p in P and the new factor.
+template <int D>
+__global__ void __launch_bounds__(kBT) k_bredo(BArgs a, const double2* __restrict__ P) {
+    constexpr int NN = D * D;
+    if (a.ctrl->stop || !a.ctrl->rho_changed) return;
+    const double rho = a.ctrl->rho, inv_rho = 1.0 / rho;
+    for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
+        int up[3], dn[3];
+        bneighbours<D>(v, a.n, up, dn);
+        double2 x[NN], gv[NN];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const int p = i * D + j;
+                gv[p] = a.g[(size_t)p * a.V + v];
+                x[p] = cadd(gv[p], cscale(bloch_grad1(P, a, i, j, up[j], dn[j]), rho));
+            }
+        fsolve_inplace<NN>(a, v, x);
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            a.G[(size_t)p * a.V + v] = x[p];
+            a.Q[(size_t)p * a.V + v] = make_double2(x[p].x - gv[p].x * inv_rho, x[p].y - gv[p].y * inv_rho);
+        }
+    }
 }
 
 // <D p, L D p> = mean over voxels of |F^T Dp|^2 - rho |Dp|^2 (F the stored factor).
 template <int D>
 __global__ void __launch_bounds__(kBT) k_brayleigh(BArgs a, const double2* __restrict__ P, double* out) {
     constexpr int NN = D * D;
+    const double rho = a.ctrl->rho;
     double v1[1] = {0.0};
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
         int up[3], dn[3];
@@ -754,7 +809,7 @@ __global__ void __launch_bounds__(kBT) k_brayleigh(BArgs a, const double2* __res
         bloch_grad<D>(P, a, up, dn, Dp);
         fapply<NN>(a, v, Dp, y);
 #pragma unroll
-        for (int p = 0; p < NN; ++p) v1[0] += (Dp[p].x * y[p].x + Dp[p].y * y[p].y) - a.rho * (Dp[p].x * Dp[p].x + Dp[p].y * Dp[p].y);
+        for (int p = 0; p < NN; ++p) v1[0] += (Dp[p].x * y[p].x + Dp[p].y * y[p].y) - rho * (Dp[p].x * Dp[p].x + Dp[p].y * Dp[p].y);
     }
     if (!grid_reduce<1>(v1, a.part, a.ctrl)) return;
     *out = v1[0] / (double)a.V;
@@ -827,7 +882,7 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     const size_t oP0 = take(16 * D * V), oP1 = take(16 * D * V), oB = take(16 * D * V);
     const size_t oG = take(16 * NN * V), og = take(16 * NN * V), oQ = take(16 * NN * V);
     const size_t oL = take(8 * (size_t)(NN * (NN + 1) / 2) * V), oLi = take(8 * NN * V), oW = take(8 * V);
-    const size_t opart = take(8 * 4 * kBlochBlocks), ohist = take(8 * 3 * (size_t)in.max_iter);
+    const size_t opart = take(8 * 4 * kBlochBlocks), ohist = take(8 * 4 * (size_t)in.max_iter);
     const size_t osym = take(8 * 3 * n), otw = take(16 * n), octrl = take(sizeof(BCtrl)), orq = take(8);
     if (w->bytes < off) {
         if (w->base) cudaFree(w->base);
@@ -842,10 +897,12 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     a.n = n;
     a.V = (int)V;
     a.half_n = 0.5 * n;
-    a.rho = in.rho;
-    a.inv_rho = 1.0 / in.rho;
     a.tol = in.tol;
-    a.rd_scale = in.rho / in.mu_ref;
+    a.inv_mu_ref = 1.0 / in.mu_ref;
+    a.adaptive = in.adaptive ? 1 : 0;
+    a.kappa = in.rho_kappa;
+    a.tau = in.rho_tau;
+    a.rho_floor = 0.0;
     for (int j = 0; j < 3; ++j) {
         const double th = j < D ? 2.0 * kPi / ((double)in.k[j] * n) : 0.0;
         a.c[j] = a.half_n * cos(th);
@@ -882,6 +939,7 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     for (size_t i = 0; i < p0.size(); ++i) p0[i] = in.p0[i] / nrm;
     BCtrl c0{};
     c0.sigma = NAN;
+    c0.rho = in.rho;
 #define CKB(x)                                  \
     do {                                        \
         if ((x) != cudaSuccess) return RVE_E_CUDA; \
@@ -897,20 +955,61 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     const int ntiles = (int)((V / n + pl.tl - 1) / pl.tl) * D;
     const int fg = std::min(ntiles, 152 * 3);
     long long launches = 0;
-    if (in.model == kNeoHooke) {
-        if (in.F_fp64) k_bfactor<D, kNeoHooke, double><<<eg, kBT, 0, st>>>(a, (const double*)in.F, in.phase, in.mat, in.nparam);
-        else k_bfactor<D, kNeoHooke, float><<<eg, kBT, 0, st>>>(a, (const float*)in.F, in.phase, in.mat, in.nparam);
-    } else {
-        if (in.F_fp64) k_bfactor<D, kLinear, double><<<eg, kBT, 0, st>>>(a, (const double*)in.F, in.phase, in.mat, in.nparam);
-        else k_bfactor<D, kLinear, float><<<eg, kBT, 0, st>>>(a, (const float*)in.F, in.phase, in.mat, in.nparam);
-    }
-    k_binit<D><<<eg, kBT, 0, st>>>(a);
-    launches += 2;
+    auto factor = [&](int mode, double shift) {
+        if (in.model == kNeoHooke) {
+            if (in.F_fp64)
+                k_bfactor<D, kNeoHooke, double><<<eg, kBT, 0, st>>>(a, (const double*)in.F, in.phase, in.mat, in.nparam,
+                                                                    mode, shift);
+            else
+                k_bfactor<D, kNeoHooke, float><<<eg, kBT, 0, st>>>(a, (const float*)in.F, in.phase, in.mat, in.nparam,
+                                                                   mode, shift);
+        } else {
+            if (in.F_fp64)
+                k_bfactor<D, kLinear, double><<<eg, kBT, 0, st>>>(a, (const double*)in.F, in.phase, in.mat, in.nparam,
+                                                                  mode, shift);
+            else
+                k_bfactor<D, kLinear, float><<<eg, kBT, 0, st>>>(a, (const float*)in.F, in.phase, in.mat, in.nparam,
+                                                                 mode, shift);
+        }
+    };
     BCtrl* hc = (BCtrl*)w->hctrl;
+    factor(0, 0.0);
+    launches += 1;
     CKB(cudaMemcpyAsync(hc, a.ctrl, sizeof(BCtrl), cudaMemcpyDeviceToHost, st));
     CKB(cudaStreamSynchronize(st));
     CKB(cudaGetLastError());
     if (hc->fail & 1) return RVE_E_NUMERICAL;
+    if (a.adaptive) {
+        // floor of the rule: max(rho_min or mu_ref, 2 s*), s* the smallest shift with
+        // L + s* I positive definite everywhere (bisection on [0, rho], to 2^-16 rho)
+        auto pd = [&](double sft) -> int {
+            if (cudaMemsetAsync(&a.ctrl->fail, 0, sizeof(int), st) != cudaSuccess) return -1;
+            factor(2, sft);
+            launches += 1;
+            if (cudaMemcpyAsync(hc, a.ctrl, sizeof(BCtrl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return -1;
+            return (hc->fail & 1) ? 0 : 1;
+        };
+        double smin = 0.0;
+        int r0 = pd(0.0);
+        if (r0 < 0) return RVE_E_CUDA;
+        if (!r0) {
+            double lo = 0.0, hi = in.rho;
+            for (int b = 0; b < 16; ++b) {
+                const double mid = 0.5 * (lo + hi);
+                const int r = pd(mid);
+                if (r < 0) return RVE_E_CUDA;
+                if (r) hi = mid;
+                else lo = mid;
+            }
+            smin = hi;
+        }
+        CKB(cudaMemsetAsync(&a.ctrl->fail, 0, sizeof(int), st));
+        a.rho_floor = std::max(in.rho_min > 0.0 ? in.rho_min : in.mu_ref, 2.0 * smin);
+    }
+    k_binit<D><<<eg, kBT, 0, st>>>(a);
+    launches += 1;
 
     cudaEvent_t e0, e1;
     CKB(cudaEventCreate(&e0));
@@ -927,7 +1026,11 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
         k_bphat<D><<<eg, kBT, 0, st>>>(a);
         fft_all<D, true>(a, tw, pl, smem, fg, st);
         k_blocal<D><<<eg, kBT, 0, st>>>(a, Pold, Pnew);
-        return 4 + 2 * D + passes;
+        if (a.adaptive) {  // after a change of rho: new factor, Step 1' again
+            factor(1, 0.0);
+            k_bredo<D><<<eg, kBT, 0, st>>>(a, Pnew);
+        }
+        return 4 + 2 * D + passes + (a.adaptive ? 2 : 0);
     };
     // The first chunk runs as plain launches (its first iterations take more root
     // passes); later full chunks replay a graph per starting parity of p.
@@ -998,8 +1101,9 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     res->time_ms = (double)ms;
     res->launches = launches;
     res->fail = hc->fail;
+    res->rho = hc->rho;
     if (in.hist_out && k > 0)
-        CKB(cudaMemcpy(in.hist_out, a.hist, 8 * 3 * (size_t)std::min<long long>(k, in.max_iter),
+        CKB(cudaMemcpy(in.hist_out, a.hist, 8 * 4 * (size_t)std::min<long long>(k, in.max_iter),
                        cudaMemcpyDeviceToHost));
 #undef CKB
     if (hc->stop == 3) return RVE_E_NUMERICAL;

@@ -922,6 +922,10 @@ int rve_bloch(rve_t h, const int k[3], const double* p0, double rho, double tol,
     a.rho = rho;
     a.tol = tol;
     a.mu_ref = h->opt.mu_ref > 0 ? h->opt.mu_ref : h->mu_ref;
+    a.adaptive = h->opt.rho_policy == RVE_RHO_ADAPTIVE;
+    a.rho_kappa = h->opt.rho_kappa;
+    a.rho_tau = h->opt.rho_tau;
+    a.rho_min = h->opt.rho_min;
     a.max_iter = max_iter;
     a.check_every = h->opt.check_every;
     a.p0 = p0;
@@ -940,6 +944,7 @@ int rve_bloch(rve_t h, const int k[3], const double* p0, double rho, double tol,
         info->time_ms = r.time_ms;
         info->launches = r.launches;
         info->fail = r.fail;
+        info->rho = r.rho;
     }
     return rc;
 }

@@ -241,15 +241,17 @@ struct BlochArgs {
     int nparam;
     int k[3];             // Bloch wave numbers, omega_j = 2 pi / k_j
     double rho, tol, mu_ref;
+    bool adaptive;        // Section 2.1's residual balancing of rho
+    double rho_kappa, rho_tau, rho_min;
     int max_iter, check_every;
     const double* p0;     // host, 2 d V doubles (re, im), component-major
     double* p_out;        // host or null
-    double* hist_out;     // host (r_p, r_d, sigma per iteration) or null
+    double* hist_out;     // host (r_p, r_d, sigma, rho per iteration) or null
     cudaStream_t stream;
 };
 struct BlochResult {
     int iterations, converged, fail;
-    double beta, rayleigh, r_p, r_d, time_ms;
+    double beta, rayleigh, r_p, r_d, time_ms, rho;
     long long launches;
 };
 int bloch_run(BlochWork** w, const BlochArgs& in, BlochResult* res);

@@ -92,6 +92,7 @@ class rve_bloch_info(ctypes.Structure):
         ("time_ms", ctypes.c_double),
         ("launches", ctypes.c_longlong),
         ("fail", ctypes.c_int),
+        ("rho", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -296,16 +297,16 @@ def rve_history_local(h, cap):
 
 def rve_bloch(h, k, p0, rho, tol, max_iter, want_p=True):
     """Modulus of stability beta_k (see include/rve.h).  k: d non-zero ints; p0: complex
-    (d, *grid).  Returns (rc, info, p or None, history (iterations, 3))."""
+    (d, *grid).  Returns (rc, info, p or None, history (iterations, 4): r_p, r_d, sigma, rho)."""
     kk = (ctypes.c_int * 3)(*(list(int(x) for x in k) + [1] * (3 - len(k))))
     p = np.ascontiguousarray(np.asarray(p0, dtype=np.complex128))
     out = np.zeros_like(p) if want_p else None
-    hist = np.zeros(3 * int(max_iter))
+    hist = np.zeros(4 * int(max_iter))
     info = rve_bloch_info()
     rc = lib().rve_bloch(h, kk, p.view(np.float64).ctypes.data_as(_PD), float(rho), float(tol), int(max_iter),
                          out.view(np.float64).ctypes.data_as(_PD) if want_p else None, _dptr(hist),
                          ctypes.byref(info))
-    return rc, info, out, hist.reshape(-1, 3)[: info.iterations]
+    return rc, info, out, hist.reshape(-1, 4)[: info.iterations]
 
 
 def rve_stress_noalloc(dim, n, model, F_ptr, phase_ptr, params_ptr, nphase, nparam, S_ptr, stream=None):

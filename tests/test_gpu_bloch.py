@@ -173,3 +173,61 @@ def test_bloch_full_size_matches_oracle():
     np.testing.assert_allclose(info.beta, ref["sigma"], rtol=1e-11)
     np.testing.assert_allclose(hist[:, :2], np.array(ref["history"]), rtol=1e-8, atol=1e-13)
     assert abs(np.sum(np.abs(p) ** 2) / n ** d - 1.0) < 1e-12
+
+
+# ------------------------------------------------------------------ adaptive penalty
+
+def test_bloch_adaptive_rho_matches_oracle():
+    """Section 2.1's residual balancing on Steps 1'-4' (RVE_RHO_ADAPTIVE), from rho = 60 on
+    a positive-definite tangent (F = I, floor mu_ref): p, sigma, residuals and the rho
+    sequence after 30 iterations element by element against the oracle."""
+    d, n, k, its = 2, 24, (3, 4), 30
+    ph = synth.inclusion_phase(n, d, 5, radius=3)
+    par = synth.two_phase_params(1.0, 4.0)
+    F = np.broadcast_to(np.eye(d).reshape(d, d, 1, 1), (d, d, n, n)).copy()
+    mu_ref = float(np.mean(par[ph.reshape(-1), 0]))
+    p0 = synth.bloch_start(n, d, 2)
+    s = rve.Rve(d, n, "neohookean", "fp64", max_iter=10, rho_policy="adaptive")
+    s.set_material(ph, par)
+    s.set_field(rve.RVE_FIELD_F, F)
+    info, p, hist = s.bloch(k, 60.0, -1.0, its, p0=p0)
+    ref = bloch.bloch_solve(bloch.tangent_field("neohookean", ph, par, F), p0, k, 60.0, -1.0, its, mu_ref,
+                            rho_policy="adaptive")
+    np.testing.assert_allclose(hist[:, 3], ref["rhos"], rtol=1e-14)
+    assert len(set(np.round(hist[:, 3], 9))) > 3  # the rule acted
+    assert rel(p, ref["p"]) < 1e-10
+    np.testing.assert_allclose(info.beta, ref["sigma"], rtol=1e-11)
+    np.testing.assert_allclose(hist[:, :2], np.array(ref["history"]), rtol=1e-8, atol=1e-13)
+
+
+@pytest.mark.parametrize("d,n,k", [(2, 6, (3, -2)), (3, 4, (2, 3, 1))])
+def test_bloch_adaptive_converges_to_smallest_eigenvalue(d, n, k):
+    ph = synth.inclusion_phase(n, d, 3, radius=1)
+    par = synth.two_phase_params(1.0, 4.0)
+    F = near_identity_field(n, d, 5)
+    L = bloch.tangent_field("neohookean", ph, par, F)
+    w, _, _ = dense_beta(L, n, d, k)
+    s = rve.Rve(d, n, "neohookean", "fp64", max_iter=10, rho_policy="adaptive")
+    s.set_material(ph, par)
+    s.set_field(rve.RVE_FIELD_F, F)
+    info, _, _ = s.bloch(k, 60.0, 1e-10, 20000, p0=synth.bloch_start(n, d, 1))
+    assert info.converged
+    np.testing.assert_allclose(info.beta, w[0], rtol=1e-9)
+
+
+def test_bloch_adaptive_is_faster_on_a_compressed_cell():
+    """The compressed soft-disc cell (<F> = 0.92 I): the same beta_(2,2) in far fewer
+    iterations than at the fixed starting penalty."""
+    n = 32
+    ph = synth.disc_phase(n, 2, 0.4)
+    par = np.array([[20.0, 196.0], [1.0, 9.8]])
+    out = {}
+    for pol in ("fixed", "adaptive"):
+        s = rve.Rve(2, n, "neohookean", "fp64", max_iter=20000, rho_policy=pol)
+        s.set_material(ph, par)
+        assert s.solve(np.diag([0.92, 0.92, 1.0]), 30.0, 1e-9).converged
+        info, _, _ = s.bloch((2, 2), 200.0, 1e-7, 60000, seed=0)
+        assert info.converged
+        out[pol] = info
+    np.testing.assert_allclose(out["adaptive"].beta, out["fixed"].beta, rtol=1e-5, atol=1e-6)
+    assert out["adaptive"].iterations < out["fixed"].iterations / 3
