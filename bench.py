@@ -57,6 +57,12 @@ def bytes_per_voxel(cls: str, s: int, d: int = 3) -> float:
 # kernel last changed
 TRAFFIC = {("local", "fp32"): 220703232 + 120778240, ("local_r", "fp64"): 421989120 + 358003456,
            ("xfwd", "fp32"): 151043840 + 11952640, ("solve", "fp32"): 25196800}
+# FP32 flops (fadd + fmul + 2 ffma, ncu instruction counters) per launch of the float local
+# step, averaged over all 97 of its launches in one solve of the 128^3 inclusion cell,
+# including the launches that exit at once after the stop flag (profiles/)
+FLOPS = {("local", "fp32"): 2.776e9}
+# FP32 peak from unit counts and clock: 128 lanes x 2 flops x 152 SMs x 2.07 GHz
+FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
 
 
 def combine_ranks(ms, vox_it, dist=None, device="cpu"):
@@ -314,6 +320,13 @@ def run_ours(args):
             "frac": top["gbs"] / pk["hbm_gbs"], "traffic": TRAFFIC.get((top["kernel"], top["precision"])),
             "kernel": f"{top['kernel']} ({top['precision']})", "peak_source": pk["source"],
             "share_of_profiled_time": share}
+    fl = FLOPS.get((top["kernel"], top["precision"]))
+    if fl:  # the same kernel against the FP32 pipe (its Newton solve is compute-heavy)
+        tf = fl / (top["ms_per_launch"] / 1e3) / 1e12
+        roof["alu_view"] = {"achieved_tflops": tf, "peak_tflops": FP32_PEAK_TFLOPS, "frac": tf / FP32_PEAK_TFLOPS,
+                            "flops_per_launch": fl,
+                            "peak_source": "derived: 128 FP32 lanes x 2 x 152 SMs x 2.07 GHz (FMA-chain probe "
+                                           "74.8 TFLOP/s at 1995 MHz)"}
     line = {
         "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps, "higher_is_better": True,
@@ -363,7 +376,8 @@ def other_workloads():
             ("lce256", bench_lce256), ("lce128_pe_path", bench_lce_path128),
             ("lce128_pe_path_inc", lambda t, r, sy: bench_lce_path128(t, r, sy, incompressible=True)),
             ("bloch512_2d", bench_bloch512), ("bloch128_3d", bench_bloch128_3d), ("batch64", bench_batch64),
-            ("serving", bench_serving))
+            ("serving", bench_serving),
+            ("serving_20hz", lambda t, r, sy: bench_serving(t, r, sy, count=48, rate=20.0)))
 
 
 def run_workload(args):

@@ -231,3 +231,19 @@ def test_bloch_adaptive_is_faster_on_a_compressed_cell():
         out[pol] = info
     np.testing.assert_allclose(out["adaptive"].beta, out["fixed"].beta, rtol=1e-5, atol=1e-6)
     assert out["adaptive"].iterations < out["fixed"].iterations / 3
+
+
+def test_bloch_on_a_float_state_handle():
+    """A handle in RVE_FP32 keeps F in float: the tangent is formed from the float F
+    (promoted to double), so beta_k agrees with the FP64 handle's to float rounding of F."""
+    d, n, k = 2, 16, (3, 4)
+    ph, par, F = two_phase_case(d, n)
+    out = []
+    for prec in ("fp64", "fp32"):
+        s = rve.Rve(d, n, "neohookean", prec, max_iter=10, rho_policy="adaptive")
+        s.set_material(ph, par)
+        s.set_field(rve.RVE_FIELD_F, F)
+        info, _, _ = s.bloch(k, 20.0, 1e-9, 20000, seed=1)
+        assert info.converged
+        out.append(info.beta)
+    np.testing.assert_allclose(out[1], out[0], rtol=1e-5)
