@@ -228,6 +228,7 @@ typedef struct rve_bloch_info {
                             definite, 2 b^ has no weight at the lowest kappa (Step 2'
                             hard case), 4 Step 2' root not found in its passes     */
     double rho;          /* penalty of the last iteration                          */
+    int float_iterations; /* of which in the float phase (RVE_MIXED, RVE_FP32)     */
 } rve_bloch_info;
 
 /* Modulus of stability beta_k (Section 2.4): the minimum over unit Bloch waves
@@ -251,7 +252,13 @@ typedef struct rve_bloch_info {
  * smallest shift making L + s* I positive definite everywhere (found by bisection,
  * once per call); rho is then the starting penalty, and a large one is fine.  p_out
  * (host, same layout as p0) receives the final p and hist (host, 4 doubles per
- * iteration: r_p, r_d, sigma, rho) the history; either may be NULL.  Models
+ * iteration: r_p, r_d, sigma, rho) the history; either may be NULL.  Precision follows
+ * opt.precision: RVE_FP64 runs every step in double; RVE_MIXED runs a float bulk
+ * (fields, factor, FFTs and the fused step in float; spectrum weights, the Step 2'
+ * root and the residual sums in double) until both residuals are within a few hundred
+ * float roundings of their scale or stop improving, then converts p and g to double,
+ * redoes the factor and Step 1' in double and continues in FP64 to tol; RVE_FP32 stops
+ * after the float phase.  Models
  * RVE_NEOHOOKE and RVE_LINEAR.  The call keeps a device workspace of about
  * (48 d^2 + 8 d^2 (d^2 + 1) + 64 d) N^d bytes on the handle until rve_destroy.
  * Returns RVE_OK, RVE_E_NOT_CONVERGED (results valid), RVE_E_INVALID_ARG (k, rho,

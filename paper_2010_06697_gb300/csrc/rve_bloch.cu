@@ -14,9 +14,14 @@
 //       bisection safeguard)
 //   3'. g += rho (D p - G)
 //   4'. r_p = ||D p - G||, r_d = rho / mu_ref ||D (p - p_old)||.
-// Fields are complex double (double2), component-major (c * V + v), x fastest.
-// The complex FFTs are this file's own: one block per tile of lines along an axis,
-// the line in shared memory, Stockham radix-4/2/3 passes.
+// Fields are complex (float2 or double2), component-major (c * V + v), x fastest.
+// Precision: FP64 throughout, or (handle precision RVE_MIXED / RVE_FP32) a float bulk --
+// fields, factor, FFTs and the fused step in float; the spectrum weights, the Step 2'
+// root, residuals and their sums in double -- promoted to FP64 (p and g converted, the
+// factor and Step 1' redone in double) once the float residuals reach the float
+// rounding level, as in the solver's RVE_MIXED.  The complex FFTs are this file's own:
+// one block per tile of lines along an axis, the line in shared memory, Stockham
+// radix-4/2/3 passes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,25 +69,47 @@ struct FftPlanB {
     int radix[12];
 };
 
+template <typename T>
+struct Cx;
+template <>
+struct Cx<double> {
+    using type = double2;
+    __host__ __device__ static double2 make(double x, double y) { return make_double2(x, y); }
+};
+template <>
+struct Cx<float> {
+    using type = float2;
+    __host__ __device__ static float2 make(float x, float y) { return make_float2(x, y); }
+};
+
+// Kernel arguments for fields of precision T (the spectrum weights, partial sums,
+// history and symbol table are double in both).
+template <typename T>
 struct BArgs {
+    using C = typename Cx<T>::type;
     int n, V;
-    double half_n, tol, inv_mu_ref;
+    double tol, inv_mu_ref;
     int adaptive;          // Section 2.1's residual balancing of rho
     double kappa, tau, rho_floor;
-    double c[3], s[3];     // cos, sin of th_j, times 1/(2h)
+    T c[3], s[3];          // cos, sin of th_j, times 1/(2h)
     const double* sym;     // s_j(m) at sym[j * n + m]
-    double2 *P0, *P1, *B, *G, *g, *Q;
-    double *Lf, *Linv, *W, *part, *hist;
+    C *P0, *P1, *B, *G, *g, *Q;
+    T *Lf, *Linv;
+    double *W, *part, *hist;
     BCtrl* ctrl;
     int max_hist;
 };
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+    return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C, typename S>
+__device__ __forceinline__ C cscale(C a, S s) { return C{a.x * s, a.y * s}; }
 
 __device__ __forceinline__ double bwarp_sum(double v) {
 #pragma unroll
@@ -159,42 +186,38 @@ __device__ __forceinline__ void bneighbours(int v, int n, int* up, int* dn) {
     }
 }
 
+// (D X)_ij at v for one (i, j).
+template <typename T>
+__device__ __forceinline__ typename Cx<T>::type bloch_grad1(const typename Cx<T>::type* __restrict__ X,
+                                                            const BArgs<T>& a, int i, int j, int up, int dn) {
+    const auto u = X[(size_t)i * a.V + up], w = X[(size_t)i * a.V + dn];
+    const T c = a.c[j], s = a.s[j];
+    return Cx<T>::make((u.x * c - u.y * s) - (w.x * c + w.y * s), (u.x * s + u.y * c) - (w.y * c - w.x * s));
+}
+
 // (D X)_ij at v from the neighbours of X (d complex components).
-template <int D>
-__device__ __forceinline__ void bloch_grad(const double2* __restrict__ X, const BArgs& a, const int* up,
-                                           const int* dn, double2* out) {
+template <int D, typename T>
+__device__ __forceinline__ void bloch_grad(const typename Cx<T>::type* __restrict__ X, const BArgs<T>& a,
+                                           const int* up, const int* dn, typename Cx<T>::type* out) {
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-            const double2 u = X[(size_t)i * a.V + up[j]], w = X[(size_t)i * a.V + dn[j]];
-            const double c = a.c[j], s = a.s[j];
-            out[i * D + j] = make_double2((u.x * c - u.y * s) - (w.x * c + w.y * s),
-                                          (u.x * s + u.y * c) - (w.y * c - w.x * s));
-        }
-}
-
-// (D X)_ij at v for one (i, j).
-__device__ __forceinline__ double2 bloch_grad1(const double2* __restrict__ X, const BArgs& a, int i, int j, int up,
-                                               int dn) {
-    const double2 u = X[(size_t)i * a.V + up], w = X[(size_t)i * a.V + dn];
-    const double c = a.c[j], s = a.s[j];
-    return make_double2((u.x * c - u.y * s) - (w.x * c + w.y * s), (u.x * s + u.y * c) - (w.y * c - w.x * s));
+        for (int j = 0; j < D; ++j) out[i * D + j] = bloch_grad1<T>(X, a, i, j, up[j], dn[j]);
 }
 
 // Packed lower-triangle index.
 __host__ __device__ constexpr int tri(int p, int q) { return p * (p + 1) / 2 + q; }
 
 // (L + rho I) x = b by the stored factor (real L, complex x and b).
-template <int NN>
-__device__ __forceinline__ void fsolve(const BArgs& a, int v, const double2* b, double2* x) {
-    double2 y[NN];
+template <int NN, typename T, typename C>
+__device__ __forceinline__ void fsolve(const BArgs<T>& a, int v, const C* b, C* x) {
+    C y[NN];
 #pragma unroll
     for (int p = 0; p < NN; ++p) {
-        double2 s = b[p];
+        C s = b[p];
 #pragma unroll
         for (int r = 0; r < p; ++r) {
-            const double l = __ldg(a.Lf + (size_t)tri(p, r) * a.V + v);
+            const T l = __ldg(a.Lf + (size_t)tri(p, r) * a.V + v);
             s.x -= l * y[r].x;
             s.y -= l * y[r].y;
         }
@@ -202,10 +225,10 @@ __device__ __forceinline__ void fsolve(const BArgs& a, int v, const double2* b, 
     }
 #pragma unroll
     for (int p = NN - 1; p >= 0; --p) {
-        double2 s = y[p];
+        C s = y[p];
 #pragma unroll
         for (int r = p + 1; r < NN; ++r) {
-            const double l = __ldg(a.Lf + (size_t)tri(r, p) * a.V + v);
+            const T l = __ldg(a.Lf + (size_t)tri(r, p) * a.V + v);
             s.x -= l * x[r].x;
             s.y -= l * x[r].y;
         }
@@ -214,14 +237,14 @@ __device__ __forceinline__ void fsolve(const BArgs& a, int v, const double2* b, 
 }
 
 // (L + rho I) x = b in place (forward substitution into b, then backward).
-template <int NN>
-__device__ __forceinline__ void fsolve_inplace(const BArgs& a, int v, double2* b) {
+template <int NN, typename T, typename C>
+__device__ __forceinline__ void fsolve_inplace(const BArgs<T>& a, int v, C* b) {
 #pragma unroll
     for (int p = 0; p < NN; ++p) {
-        double2 s = b[p];
+        C s = b[p];
 #pragma unroll
         for (int r = 0; r < p; ++r) {
-            const double l = __ldg(a.Lf + (size_t)tri(p, r) * a.V + v);
+            const T l = __ldg(a.Lf + (size_t)tri(p, r) * a.V + v);
             s.x -= l * b[r].x;
             s.y -= l * b[r].y;
         }
@@ -229,10 +252,10 @@ __device__ __forceinline__ void fsolve_inplace(const BArgs& a, int v, double2* b
     }
 #pragma unroll
     for (int p = NN - 1; p >= 0; --p) {
-        double2 s = b[p];
+        C s = b[p];
 #pragma unroll
         for (int r = p + 1; r < NN; ++r) {
-            const double l = __ldg(a.Lf + (size_t)tri(r, p) * a.V + v);
+            const T l = __ldg(a.Lf + (size_t)tri(r, p) * a.V + v);
             s.x -= l * b[r].x;
             s.y -= l * b[r].y;
         }
@@ -241,15 +264,15 @@ __device__ __forceinline__ void fsolve_inplace(const BArgs& a, int v, double2* b
 }
 
 // y = (L + rho I) x = F (F^T x) with the stored factor F.
-template <int NN>
-__device__ __forceinline__ void fapply(const BArgs& a, int v, const double2* x, double2* y) {
-    double2 t[NN];
+template <int NN, typename T, typename C>
+__device__ __forceinline__ void fapply(const BArgs<T>& a, int v, const C* x, C* y) {
+    C t[NN];
 #pragma unroll
     for (int p = 0; p < NN; ++p) {
-        double2 s = make_double2(0.0, 0.0);
+        C s{T(0), T(0)};
 #pragma unroll
         for (int r = p; r < NN; ++r) {
-            const double l = __ldg(a.Lf + (size_t)tri(r, p) * a.V + v);
+            const T l = __ldg(a.Lf + (size_t)tri(r, p) * a.V + v);
             s.x += l * x[r].x;
             s.y += l * x[r].y;
         }
@@ -257,10 +280,10 @@ __device__ __forceinline__ void fapply(const BArgs& a, int v, const double2* x, 
     }
 #pragma unroll
     for (int p = 0; p < NN; ++p) {
-        double2 s = make_double2(0.0, 0.0);
+        C s{T(0), T(0)};
 #pragma unroll
         for (int r = 0; r <= p; ++r) {
-            const double l = __ldg(a.Lf + (size_t)tri(p, r) * a.V + v);
+            const T l = __ldg(a.Lf + (size_t)tri(p, r) * a.V + v);
             s.x += l * t[r].x;
             s.y += l * t[r].y;
         }
@@ -270,8 +293,8 @@ __device__ __forceinline__ void fapply(const BArgs& a, int v, const double2* x, 
 
 // kappa(m) = sum_j s_j(m_j)^2 with explicit roundings (no contraction), so that every
 // kernel forms the same value.
-template <int D>
-__device__ __forceinline__ double kappa_of(const BArgs& a, int v) {
+template <int D, typename T>
+__device__ __forceinline__ double kappa_of(const BArgs<T>& a, int v) {
     const int n = a.n;
     const int mx = v % n, r = v / n;
     const int my = D == 3 ? r % n : r;
@@ -293,8 +316,8 @@ __device__ __forceinline__ double kappa_of(const BArgs& a, int v) {
 // mode 0: factor with ctrl->rho; mode 1: the same, only when rho changed (redo after the
 // rule); mode 2: no factor stored, only the positive-definiteness test of L + shift I
 // (fail bit 1), for the floor's bisection.
-template <int D, int MODEL, typename TF>
-__global__ void __launch_bounds__(kBT) k_bfactor(BArgs a, const TF* __restrict__ F, const uint8_t* __restrict__ phase,
+template <int D, int MODEL, typename TF, typename T>
+__global__ void __launch_bounds__(kBT) k_bfactor(BArgs<T> a, const TF* __restrict__ F, const uint8_t* __restrict__ phase,
                                                  const double* __restrict__ mat, int nparam, int mode, double shift) {
     constexpr int NN = D * D;
     if (mode == 1 && !a.ctrl->rho_changed) return;
@@ -368,7 +391,7 @@ __global__ void __launch_bounds__(kBT) k_bfactor(BArgs a, const TF* __restrict__
                     ok = ok && s > 0.0;
                     const double d = sqrt(fmax(s, 0.0));
                     H[tri(p, p)] = d;
-                    if (mode != 2) a.Linv[(size_t)p * a.V + v] = ok ? 1.0 / d : 0.0;
+                    if (mode != 2) a.Linv[(size_t)p * a.V + v] = (T)(ok ? 1.0 / d : 0.0);
                 } else {
                     H[tri(p, q)] = s / H[tri(q, q)];
                 }
@@ -381,24 +404,25 @@ __global__ void __launch_bounds__(kBT) k_bfactor(BArgs a, const TF* __restrict__
         }
         if (mode == 2) continue;
 #pragma unroll
-        for (int p = 0; p < NN * (NN + 1) / 2; ++p) a.Lf[(size_t)p * a.V + v] = H[p];
+        for (int p = 0; p < NN * (NN + 1) / 2; ++p) a.Lf[(size_t)p * a.V + v] = (T)H[p];
     }
 }
 
 // Start: g_0 = L D p_0, then Step 1' of the first iteration (G, Q).
-template <int D>
-__global__ void __launch_bounds__(kBT) k_binit(BArgs a) {
+template <int D, typename T>
+__global__ void __launch_bounds__(kBT) k_binit(BArgs<T> a) {
     constexpr int NN = D * D;
-    const double rho = a.ctrl->rho, inv_rho = 1.0 / rho;
+    using C = typename Cx<T>::type;
+    const T rho = (T)a.ctrl->rho, inv_rho = (T)(1.0 / a.ctrl->rho);
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
         int up[3], dn[3];
         bneighbours<D>(v, a.n, up, dn);
-        double2 Dp[NN], y[NN], rhs[NN], G[NN];
-        bloch_grad<D>(a.P0, a, up, dn, Dp);
+        C Dp[NN], y[NN], rhs[NN], G[NN];
+        bloch_grad<D, T>(a.P0, a, up, dn, Dp);
         fapply<NN>(a, v, Dp, y);
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
-            const double2 g0 = csub(y[p], cscale(Dp[p], rho));
+            const C g0 = csub(y[p], cscale(Dp[p], rho));
             y[p] = g0;
             rhs[p] = cadd(g0, cscale(Dp[p], rho));
         }
@@ -407,14 +431,14 @@ __global__ void __launch_bounds__(kBT) k_binit(BArgs a) {
         for (int p = 0; p < NN; ++p) {
             a.g[(size_t)p * a.V + v] = y[p];
             a.G[(size_t)p * a.V + v] = G[p];
-            a.Q[(size_t)p * a.V + v] = make_double2(G[p].x - y[p].x * inv_rho, G[p].y - y[p].y * inv_rho);
+            a.Q[(size_t)p * a.V + v] = Cx<T>::make(G[p].x - y[p].x * inv_rho, G[p].y - y[p].y * inv_rho);
         }
     }
 }
 
 // b = D^* Q: (D^* Q)_i = sum_j (Q_ij(x - h e_j) e^{-i th_j} - Q_ij(x + h e_j) e^{i th_j}) / (2h).
-template <int D>
-__global__ void __launch_bounds__(kBT) k_bdiv(BArgs a) {
+template <int D, typename T>
+__global__ void __launch_bounds__(kBT) k_bdiv(BArgs<T> a) {
     if (a.ctrl->stop) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->rho_changed = 0;  // the redo (if any) has run
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
@@ -422,15 +446,15 @@ __global__ void __launch_bounds__(kBT) k_bdiv(BArgs a) {
         bneighbours<D>(v, a.n, up, dn);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            double re = 0.0, im = 0.0;
+            T re = T(0), im = T(0);
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const double2 w = a.Q[(size_t)(i * D + j) * a.V + dn[j]], u = a.Q[(size_t)(i * D + j) * a.V + up[j]];
-                const double c = a.c[j], s = a.s[j];
+                const auto w = a.Q[(size_t)(i * D + j) * a.V + dn[j]], u = a.Q[(size_t)(i * D + j) * a.V + up[j]];
+                const T c = a.c[j], s = a.s[j];
                 re += (w.x * c + w.y * s) - (u.x * c - u.y * s);
                 im += (w.y * c - w.x * s) - (u.x * s + u.y * c);
             }
-            a.B[(size_t)i * a.V + v] = make_double2(re, im);
+            a.B[(size_t)i * a.V + v] = Cx<T>::make(re, im);
         }
     }
 }
@@ -439,15 +463,17 @@ __global__ void __launch_bounds__(kBT) k_bdiv(BArgs a) {
 // of tl lines (consecutive rows for the x axis, consecutive x (or x-y plane
 // positions) for the others, so that loads coalesce), holds it in shared memory and
 // runs Stockham passes of radix 4, 2 and 3 (tw[t] = exp(-2 pi i t / n)).
-template <int D, int AXIS, bool INV>
-__global__ void __launch_bounds__(kBT) k_bfft(BArgs a, const double2* __restrict__ tw, FftPlanB pl) {
+template <int D, int AXIS, bool INV, typename T>
+__global__ void __launch_bounds__(kBT) k_bfft(BArgs<T> a, const typename Cx<T>::type* __restrict__ tw, FftPlanB pl) {
+    using C = typename Cx<T>::type;
     if (a.ctrl->stop) return;
-    extern __shared__ double2 bsm[];
+    extern __shared__ __align__(16) unsigned char bsm_raw[];
+    C* bsm = reinterpret_cast<C*>(bsm_raw);
     const int n = pl.n, tl = pl.tl;
     const int nl = a.V / n;
     const int ntile = (nl + tl - 1) / tl;
-    double2* s0 = bsm;
-    double2* s1 = bsm + tl * n;
+    C* s0 = bsm;
+    C* s1 = bsm + tl * n;
     auto addr = [&](int line, int i) -> size_t {
         if (AXIS == 0) return (size_t)line * n + i;
         if (AXIS == 1) {
@@ -459,7 +485,7 @@ __global__ void __launch_bounds__(kBT) k_bfft(BArgs a, const double2* __restrict
     };
     for (int tile = blockIdx.x; tile < ntile * D; tile += gridDim.x) {
         const int comp = tile / ntile, t0 = (tile - comp * ntile) * tl;
-        double2* base = a.B + (size_t)comp * a.V;
+        C* base = a.B + (size_t)comp * a.V;
         for (int t = threadIdx.x; t < tl * n; t += kBT) {
             int l, i;
             if (AXIS == 0) {
@@ -472,19 +498,19 @@ __global__ void __launch_bounds__(kBT) k_bfft(BArgs a, const double2* __restrict
             if (t0 + l < nl) s0[l * n + i] = base[addr(t0 + l, i)];
         }
         __syncthreads();
-        double2* in = s0;
-        double2* out = s1;
+        C* in = s0;
+        C* out = s1;
         int ns = 1;
         for (int ps = 0; ps < pl.npass; ++ps) {
             const int R = pl.radix[ps], m = n / R, tws = n / (ns * R);
             for (int t = threadIdx.x; t < tl * m; t += kBT) {
                 const int l = t / m, j = t - l * m, kk = j % ns;
-                const double2* li = in + l * n;
-                double2* lo = out + l * n;
+                const C* li = in + l * n;
+                C* lo = out + l * n;
                 const int o = (j - kk) * R + kk;
-                double2 x0 = li[j], x1 = li[j + m];
+                C x0 = li[j], x1 = li[j + m];
                 if (kk) {
-                    double2 w = tw[kk * tws];
+                    C w = tw[kk * tws];
                     if (INV) w.y = -w.y;
                     x1 = cmul(x1, w);
                 }
@@ -492,23 +518,23 @@ __global__ void __launch_bounds__(kBT) k_bfft(BArgs a, const double2* __restrict
                     lo[o] = cadd(x0, x1);
                     lo[o + ns] = csub(x0, x1);
                 } else if (R == 3) {
-                    double2 x2 = li[j + 2 * m];
+                    C x2 = li[j + 2 * m];
                     if (kk) {
-                        double2 w = tw[2 * kk * tws];
+                        C w = tw[2 * kk * tws];
                         if (INV) w.y = -w.y;
                         x2 = cmul(x2, w);
                     }
                     // y1,2 = x0 - (x1 + x2)/2 -+ i sqrt(3)/2 (x1 - x2) (forward; signs swap inverse)
-                    const double h3 = INV ? -0.86602540378443864676 : 0.86602540378443864676;
-                    const double2 t1 = cadd(x1, x2), t2 = csub(x1, x2);
-                    const double2 mid = make_double2(x0.x - 0.5 * t1.x, x0.y - 0.5 * t1.y);
+                    const T h3 = INV ? T(-0.86602540378443864676) : T(0.86602540378443864676);
+                    const C t1 = cadd(x1, x2), t2 = csub(x1, x2);
+                    const C mid = Cx<T>::make(x0.x - T(0.5) * t1.x, x0.y - T(0.5) * t1.y);
                     lo[o] = cadd(x0, t1);
-                    lo[o + ns] = make_double2(mid.x + h3 * t2.y, mid.y - h3 * t2.x);
-                    lo[o + 2 * ns] = make_double2(mid.x - h3 * t2.y, mid.y + h3 * t2.x);
+                    lo[o + ns] = Cx<T>::make(mid.x + h3 * t2.y, mid.y - h3 * t2.x);
+                    lo[o + 2 * ns] = Cx<T>::make(mid.x - h3 * t2.y, mid.y + h3 * t2.x);
                 } else {
-                    double2 x2 = li[j + 2 * m], x3 = li[j + 3 * m];
+                    C x2 = li[j + 2 * m], x3 = li[j + 3 * m];
                     if (kk) {
-                        double2 w2 = tw[2 * kk * tws], w3 = tw[3 * kk * tws];
+                        C w2 = tw[2 * kk * tws], w3 = tw[3 * kk * tws];
                         if (INV) {
                             w2.y = -w2.y;
                             w3.y = -w3.y;
@@ -517,20 +543,20 @@ __global__ void __launch_bounds__(kBT) k_bfft(BArgs a, const double2* __restrict
                         x3 = cmul(x3, w3);
                     }
                     // y0 = a0+a1+a2+a3, y2 = a0-a1+a2-a3, y1,3 = (a0-a2) -+ i (a1-a3) (forward)
-                    const double2 e = cadd(x0, x2), f = csub(x0, x2), g2 = cadd(x1, x3), h = csub(x1, x3);
+                    const C e = cadd(x0, x2), f = csub(x0, x2), g2 = cadd(x1, x3), h = csub(x1, x3);
                     lo[o] = cadd(e, g2);
                     lo[o + 2 * ns] = csub(e, g2);
                     if (!INV) {
-                        lo[o + ns] = make_double2(f.x + h.y, f.y - h.x);
-                        lo[o + 3 * ns] = make_double2(f.x - h.y, f.y + h.x);
+                        lo[o + ns] = Cx<T>::make(f.x + h.y, f.y - h.x);
+                        lo[o + 3 * ns] = Cx<T>::make(f.x - h.y, f.y + h.x);
                     } else {
-                        lo[o + ns] = make_double2(f.x - h.y, f.y + h.x);
-                        lo[o + 3 * ns] = make_double2(f.x + h.y, f.y - h.x);
+                        lo[o + ns] = Cx<T>::make(f.x - h.y, f.y + h.x);
+                        lo[o + 3 * ns] = Cx<T>::make(f.x + h.y, f.y - h.x);
                     }
                 }
             }
             __syncthreads();
-            double2* sw = in;
+            C* sw = in;
             in = out;
             out = sw;
             ns *= R;
@@ -589,20 +615,20 @@ __device__ __forceinline__ void block_merge3(double& ws, double& km, double& wm)
     __syncthreads();
 }
 
-template <int D>
-__global__ void __launch_bounds__(kBT) k_bweights(BArgs a) {
+template <int D, typename T>
+__global__ void __launch_bounds__(kBT) k_bweights(BArgs<T> a) {
     if (a.ctrl->stop) return;
     double ws = 0.0, km = 1e300, wm = 0.0;
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
         double w = 0.0;
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const double2 b = a.B[(size_t)i * a.V + v];
-            w += b.x * b.x + b.y * b.y;
+            const auto b = a.B[(size_t)i * a.V + v];
+            w += (double)b.x * (double)b.x + (double)b.y * (double)b.y;
         }
         a.W[v] = w;
         ws += w;
-        kw_merge(km, wm, kappa_of<D>(a, v), w);
+        kw_merge(km, wm, kappa_of<D, T>(a, v), w);
     }
     __shared__ int s_last;
     block_merge3(ws, km, wm);
@@ -648,14 +674,14 @@ __global__ void __launch_bounds__(kBT) k_bweights(BArgs a) {
 // One Newton pass on phi(sigma) = V / sqrt(S) - 1, S = sum rho^2 W / (rho kappa - sigma)^2
 // (phi decreasing; phi = 0 is ||p|| = 1), keeping the bracket [lo, hi] of the root and
 // bisecting when Newton leaves it.
-template <int D>
-__global__ void __launch_bounds__(kBT) k_broot(BArgs a, int last) {
+template <int D, typename T>
+__global__ void __launch_bounds__(kBT) k_broot(BArgs<T> a, int last) {
     const BCtrl* cc = a.ctrl;
     if (cc->stop || cc->root_done) return;
     const double sig = cc->sigma, rho = cc->rho, r2 = rho * rho;
     double v2[2] = {0.0, 0.0};
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
-        const double inv = 1.0 / __dsub_rn(__dmul_rn(rho, kappa_of<D>(a, v)), sig);
+        const double inv = 1.0 / __dsub_rn(__dmul_rn(rho, kappa_of<D, T>(a, v)), sig);
         const double q = r2 * a.W[v] * inv * inv;
         v2[0] += q;
         v2[1] += 2.0 * q * inv;
@@ -692,17 +718,17 @@ __global__ void __launch_bounds__(kBT) k_broot(BArgs a, int last) {
 }
 
 // p^ = rho b^ / (rho kappa - sigma), with the 1/V of the inverse transform.
-template <int D>
-__global__ void __launch_bounds__(kBT) k_bphat(BArgs a) {
+template <int D, typename T>
+__global__ void __launch_bounds__(kBT) k_bphat(BArgs<T> a) {
     if (a.ctrl->stop) return;
     const double sig = a.ctrl->sigma, rho = a.ctrl->rho, Vd = (double)a.V;
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
-        const double den = __dsub_rn(__dmul_rn(rho, kappa_of<D>(a, v)), sig);
-        const double f = rho / (den * Vd);
+        const double den = __dsub_rn(__dmul_rn(rho, kappa_of<D, T>(a, v)), sig);
+        const T f = (T)(rho / (den * Vd));
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const double2 b = a.B[(size_t)i * a.V + v];
-            a.B[(size_t)i * a.V + v] = make_double2(b.x * f, b.y * f);
+            const auto b = a.B[(size_t)i * a.V + v];
+            a.B[(size_t)i * a.V + v] = Cx<T>::make(b.x * f, b.y * f);
         }
     }
 }
@@ -710,35 +736,41 @@ __global__ void __launch_bounds__(kBT) k_bphat(BArgs a) {
 // Steps 3' and 4' of iteration i (p_i in B, p_{i-1} in Pold, G_i, g_{i-1}) fused with
 // Step 1' of iteration i + 1 (G_{i+1}, Q); p_i is copied to Pnew.  The last block
 // finishes the residuals, records them and sets the stop flag.
-template <int D>
-__global__ void __launch_bounds__(kBT, 2) k_blocal(BArgs a, const double2* __restrict__ Pold, double2* __restrict__ Pnew) {
+template <int D, typename T>
+__global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 2 : 1)
+k_blocal(BArgs<T> a, const typename Cx<T>::type* __restrict__ Pold, typename Cx<T>::type* __restrict__ Pnew) {
     constexpr int NN = D * D;
+    using C = typename Cx<T>::type;
     if (a.ctrl->stop) return;
-    const double rho = a.ctrl->rho, inv_rho = 1.0 / rho;
+    const double rho = a.ctrl->rho;
+    const T rho_t = (T)rho, inv_rho = (T)(1.0 / rho);
     double v2[2] = {0.0, 0.0};
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
         int up[3], dn[3];
         bneighbours<D>(v, a.n, up, dn);
-        double2 x[NN], gn[NN];
+        C x[NN], gn[NN];
+        T sp = T(0), sd = T(0);
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 const int p = i * D + j;
-                const double2 Dn = bloch_grad1(a.B, a, i, j, up[j], dn[j]);
-                const double2 Do = bloch_grad1(Pold, a, i, j, up[j], dn[j]);
-                const double2 e = csub(Dn, a.G[(size_t)p * a.V + v]), dd = csub(Dn, Do);
-                v2[0] += e.x * e.x + e.y * e.y;
-                v2[1] += dd.x * dd.x + dd.y * dd.y;
-                gn[p] = cadd(a.g[(size_t)p * a.V + v], cscale(e, rho));  // Step 3'
-                x[p] = cadd(gn[p], cscale(Dn, rho));
+                const C Dn = bloch_grad1<T>(a.B, a, i, j, up[j], dn[j]);
+                const C Do = bloch_grad1<T>(Pold, a, i, j, up[j], dn[j]);
+                const C e = csub(Dn, a.G[(size_t)p * a.V + v]), dd = csub(Dn, Do);
+                sp += e.x * e.x + e.y * e.y;
+                sd += dd.x * dd.x + dd.y * dd.y;
+                gn[p] = cadd(a.g[(size_t)p * a.V + v], cscale(e, rho_t));  // Step 3'
+                x[p] = cadd(gn[p], cscale(Dn, rho_t));
             }
+        v2[0] += (double)sp;  // per voxel in T, over voxels in double
+        v2[1] += (double)sd;
         fsolve_inplace<NN>(a, v, x);  // Step 1' of the next iteration
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
             a.g[(size_t)p * a.V + v] = gn[p];
             a.G[(size_t)p * a.V + v] = x[p];
-            a.Q[(size_t)p * a.V + v] = make_double2(x[p].x - gn[p].x * inv_rho, x[p].y - gn[p].y * inv_rho);
+            a.Q[(size_t)p * a.V + v] = Cx<T>::make(x[p].x - gn[p].x * inv_rho, x[p].y - gn[p].y * inv_rho);
         }
 #pragma unroll
         for (int i = 0; i < D; ++i) Pnew[(size_t)i * a.V + v] = a.B[(size_t)i * a.V + v];
@@ -770,46 +802,69 @@ __global__ void __launch_bounds__(kBT, 2) k_blocal(BArgs a, const double2* __res
 
 // Step 1' again after the rule changed rho (the fused step used the old one):
 // G = (L + rho I)^{-1} (g + rho D p), Q = G - g / rho with p in P and the new factor.
-template <int D>
-__global__ void __launch_bounds__(kBT) k_bredo(BArgs a, const double2* __restrict__ P) {
+template <int D, typename T>
+__global__ void __launch_bounds__(kBT) k_bredo(BArgs<T> a, const typename Cx<T>::type* __restrict__ P) {
     constexpr int NN = D * D;
+    using C = typename Cx<T>::type;
     if (a.ctrl->stop || !a.ctrl->rho_changed) return;
-    const double rho = a.ctrl->rho, inv_rho = 1.0 / rho;
+    const T rho = (T)a.ctrl->rho, inv_rho = (T)(1.0 / a.ctrl->rho);
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
         int up[3], dn[3];
         bneighbours<D>(v, a.n, up, dn);
-        double2 x[NN], gv[NN];
+        C x[NN], gv[NN];
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 const int p = i * D + j;
                 gv[p] = a.g[(size_t)p * a.V + v];
-                x[p] = cadd(gv[p], cscale(bloch_grad1(P, a, i, j, up[j], dn[j]), rho));
+                x[p] = cadd(gv[p], cscale(bloch_grad1<T>(P, a, i, j, up[j], dn[j]), rho));
             }
         fsolve_inplace<NN>(a, v, x);
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
             a.G[(size_t)p * a.V + v] = x[p];
-            a.Q[(size_t)p * a.V + v] = make_double2(x[p].x - gv[p].x * inv_rho, x[p].y - gv[p].y * inv_rho);
+            a.Q[(size_t)p * a.V + v] = Cx<T>::make(x[p].x - gv[p].x * inv_rho, x[p].y - gv[p].y * inv_rho);
+        }
+    }
+}
+
+// Promotion of the float bulk to FP64: p (d components) and g (d^2) converted; the
+// double factor and Step 1' are then redone (k_bfactor mode 1, k_bredo).
+template <int D>
+__global__ void __launch_bounds__(kBT) k_bpromote(const float2* __restrict__ pf, const float2* __restrict__ gf,
+                                                  double2* __restrict__ pd, double2* __restrict__ gd, int V) {
+    for (int v = blockIdx.x * kBT + threadIdx.x; v < V; v += gridDim.x * kBT) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const float2 q = pf[(size_t)i * V + v];
+            pd[(size_t)i * V + v] = make_double2(q.x, q.y);
+        }
+#pragma unroll
+        for (int p = 0; p < D * D; ++p) {
+            const float2 q = gf[(size_t)p * V + v];
+            gd[(size_t)p * V + v] = make_double2(q.x, q.y);
         }
     }
 }
 
 // <D p, L D p> = mean over voxels of |F^T Dp|^2 - rho |Dp|^2 (F the stored factor).
-template <int D>
-__global__ void __launch_bounds__(kBT) k_brayleigh(BArgs a, const double2* __restrict__ P, double* out) {
+template <int D, typename T>
+__global__ void __launch_bounds__(kBT) k_brayleigh(BArgs<T> a, const typename Cx<T>::type* __restrict__ P, double* out) {
     constexpr int NN = D * D;
+    using C = typename Cx<T>::type;
     const double rho = a.ctrl->rho;
     double v1[1] = {0.0};
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
         int up[3], dn[3];
         bneighbours<D>(v, a.n, up, dn);
-        double2 Dp[NN], y[NN];
-        bloch_grad<D>(P, a, up, dn, Dp);
+        C Dp[NN], y[NN];
+        bloch_grad<D, T>(P, a, up, dn, Dp);
         fapply<NN>(a, v, Dp, y);
 #pragma unroll
-        for (int p = 0; p < NN; ++p) v1[0] += (Dp[p].x * y[p].x + Dp[p].y * y[p].y) - rho * (Dp[p].x * Dp[p].x + Dp[p].y * Dp[p].y);
+        for (int p = 0; p < NN; ++p)
+            v1[0] += ((double)Dp[p].x * y[p].x + (double)Dp[p].y * y[p].y) -
+                     rho * ((double)Dp[p].x * Dp[p].x + (double)Dp[p].y * Dp[p].y);
     }
     if (!grid_reduce<1>(v1, a.part, a.ctrl)) return;
     *out = v1[0] / (double)a.V;
@@ -839,51 +894,155 @@ FftPlanB make_plan(int n) {
 
 int grid_for(long long V) { return (int)std::min<long long>(kBlochBlocks, (V + kBT - 1) / kBT); }
 
-template <int D>
+template <int D, typename T>
 cudaError_t set_fft_attrs(size_t smem) {
-    static size_t done[2] = {0, 0};
-    if (done[D - 2] >= smem) return cudaSuccess;
+    static size_t done = 0;
+    if (done >= smem) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     const int b = (int)smem;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bfft<D, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bfft<D, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bfft<D, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bfft<D, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bfft<D, 0, false, T>, at, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bfft<D, 0, true, T>, at, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bfft<D, 1, false, T>, at, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bfft<D, 1, true, T>, at, b);
     if (D == 3) {
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_bfft<D, D - 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_bfft<D, D - 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bfft<D, D - 1, false, T>, at, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bfft<D, D - 1, true, T>, at, b);
     }
-    if (e == cudaSuccess) done[D - 2] = smem;
+    if (e == cudaSuccess) done = smem;
     return e;
 }
 
-template <int D, bool INV>
-void fft_all(const BArgs& a, const double2* tw, const FftPlanB& pl, size_t smem, int fg, cudaStream_t st) {
-    k_bfft<D, 0, INV><<<fg, kBT, smem, st>>>(a, tw, pl);
-    k_bfft<D, 1, INV><<<fg, kBT, smem, st>>>(a, tw, pl);
-    if (D == 3) k_bfft<D, D - 1, INV><<<fg, kBT, smem, st>>>(a, tw, pl);
+template <int D, bool INV, typename T>
+void fft_all(const BArgs<T>& a, const typename Cx<T>::type* tw, const FftPlanB& pl, size_t smem, int fg,
+             cudaStream_t st) {
+    k_bfft<D, 0, INV, T><<<fg, kBT, smem, st>>>(a, tw, pl);
+    k_bfft<D, 1, INV, T><<<fg, kBT, smem, st>>>(a, tw, pl);
+    if (D == 3) k_bfft<D, D - 1, INV, T><<<fg, kBT, smem, st>>>(a, tw, pl);
+}
+
+// The launches of one precision phase: factor, init, iteration, graphs.
+template <int D, typename T>
+struct Phase {
+    using C = typename Cx<T>::type;
+    BArgs<T> a{};
+    const BlochArgs* in = nullptr;
+    C* tw = nullptr;
+    FftPlanB pl{};
+    size_t smem = 0;
+    int eg = 0, fg = 0;
+    cudaStream_t st = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int per_chunk = 0;
+
+    void factor(int mode, double shift) const {
+        const BlochArgs& b = *in;
+        if (b.model == kNeoHooke) {
+            if (b.F_fp64)
+                k_bfactor<D, kNeoHooke, double, T><<<eg, kBT, 0, st>>>(a, (const double*)b.F, b.phase, b.mat, b.nparam,
+                                                                       mode, shift);
+            else
+                k_bfactor<D, kNeoHooke, float, T><<<eg, kBT, 0, st>>>(a, (const float*)b.F, b.phase, b.mat, b.nparam,
+                                                                      mode, shift);
+        } else {
+            if (b.F_fp64)
+                k_bfactor<D, kLinear, double, T><<<eg, kBT, 0, st>>>(a, (const double*)b.F, b.phase, b.mat, b.nparam,
+                                                                     mode, shift);
+            else
+                k_bfactor<D, kLinear, float, T><<<eg, kBT, 0, st>>>(a, (const float*)b.F, b.phase, b.mat, b.nparam,
+                                                                    mode, shift);
+        }
+    }
+    C* pold(long long i) const { return ((i - 1) & 1) ? a.P1 : a.P0; }
+    C* pnew(long long i) const { return (i & 1) ? a.P1 : a.P0; }
+    // iteration i (1-based, counted over both phases) reads p_{i-1} and writes p_i
+    int iteration(long long i) const {
+        const int passes = i == 1 ? kRootPasses0 : (i == 2 ? kRootPasses1 : kRootPasses);
+        k_bdiv<D, T><<<eg, kBT, 0, st>>>(a);
+        fft_all<D, false, T>(a, tw, pl, smem, fg, st);
+        k_bweights<D, T><<<eg, kBT, 0, st>>>(a);
+        for (int r = 0; r < passes; ++r) k_broot<D, T><<<eg, kBT, 0, st>>>(a, r == passes - 1);
+        k_bphat<D, T><<<eg, kBT, 0, st>>>(a);
+        fft_all<D, true, T>(a, tw, pl, smem, fg, st);
+        k_blocal<D, T><<<eg, kBT, 0, st>>>(a, pold(i), pnew(i));
+        if (a.adaptive) {  // after a change of rho: new factor, Step 1' again
+            factor(1, 0.0);
+            k_bredo<D, T><<<eg, kBT, 0, st>>>(a, pnew(i));
+        }
+        return 4 + 2 * D + passes + (a.adaptive ? 2 : 0);
+    }
+    // m iterations from it (plain launches, or the graph of this phase for the
+    // starting parity once past the first two iterations); returns launches or -1
+    long long chunk(long long it, long long m, int full) {
+        if (it >= 2 && m == full) {
+            const int par = (int)(it & 1);
+            if (!graph[par]) {
+                cudaGraph_t g = nullptr;
+                per_chunk = 0;
+                if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return -1;
+                for (long long q = 0; q < m; ++q) per_chunk += iteration(it + q + 1);
+                const cudaError_t ec = cudaStreamEndCapture(st, &g);
+                const cudaError_t ei = ec == cudaSuccess ? cudaGraphInstantiate(&graph[par], g, 0) : ec;
+                if (g) cudaGraphDestroy(g);
+                if (ei != cudaSuccess) return -1;
+            }
+            if (cudaGraphLaunch(graph[par], st) != cudaSuccess) return -1;
+            return per_chunk;
+        }
+        long long l = 0;
+        for (long long q = 0; q < m; ++q) l += iteration(it + q + 1);
+        return l;
+    }
+    void drop() {
+        for (auto& g : graph)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
+};
+
+template <int D, typename T>
+void bind(Phase<D, T>& ph, unsigned char* b, size_t oP0, size_t oP1, size_t oB, size_t oG, size_t og, size_t oQ,
+          size_t oL, size_t oLi, size_t otw) {
+    using C = typename Cx<T>::type;
+    ph.a.P0 = (C*)(b + oP0);
+    ph.a.P1 = (C*)(b + oP1);
+    ph.a.B = (C*)(b + oB);
+    ph.a.G = (C*)(b + oG);
+    ph.a.g = (C*)(b + og);
+    ph.a.Q = (C*)(b + oQ);
+    ph.a.Lf = (T*)(b + oL);
+    ph.a.Linv = (T*)(b + oLi);
+    ph.tw = (C*)(b + otw);
 }
 
 template <int D>
 int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     constexpr int NN = D * D;
+    constexpr int NP = NN * (NN + 1) / 2;
     const int n = in.n;
     const long long V = in.V;
     cudaStream_t st = in.stream;
-    // workspace layout
+    const bool bulk = in.float_bulk;  // float phase first
+    // workspace layout: the double set, the float set when there is a float phase, shared
     size_t off = 0;
     auto take = [&](size_t b) {
         const size_t o = off;
         off += (b + 255) / 256 * 256;
         return o;
     };
-    const size_t oP0 = take(16 * D * V), oP1 = take(16 * D * V), oB = take(16 * D * V);
-    const size_t oG = take(16 * NN * V), og = take(16 * NN * V), oQ = take(16 * NN * V);
-    const size_t oL = take(8 * (size_t)(NN * (NN + 1) / 2) * V), oLi = take(8 * NN * V), oW = take(8 * V);
-    const size_t opart = take(8 * 4 * kBlochBlocks), ohist = take(8 * 4 * (size_t)in.max_iter);
-    const size_t osym = take(8 * 3 * n), otw = take(16 * n), octrl = take(sizeof(BCtrl)), orq = take(8);
+    const size_t dP0 = take(16 * D * V), dP1 = take(16 * D * V), dB = take(16 * D * V);
+    const size_t dG = take(16 * NN * V), dg = take(16 * NN * V), dQ = take(16 * NN * V);
+    const size_t dL = take(8 * (size_t)NP * V), dLi = take(8 * NN * V), dtw = take(16 * n);
+    size_t fP0 = 0, fP1 = 0, fB = 0, fG = 0, fg_ = 0, fQ = 0, fL = 0, fLi = 0, ftw = 0;
+    if (bulk) {
+        fP0 = take(8 * D * V), fP1 = take(8 * D * V), fB = take(8 * D * V);
+        fG = take(8 * NN * V), fg_ = take(8 * NN * V), fQ = take(8 * NN * V);
+        fL = take(4 * (size_t)NP * V), fLi = take(4 * NN * V), ftw = take(8 * n);
+    }
+    const size_t oW = take(8 * V), opart = take(8 * 4 * kBlochBlocks), ohist = take(8 * 4 * (size_t)in.max_iter);
+    const size_t osym = take(8 * 3 * n), octrl = take(sizeof(BCtrl)), orq = take(8);
     if (w->bytes < off) {
         if (w->base) cudaFree(w->base);
         w->base = nullptr;
@@ -893,44 +1052,60 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     }
     if (!w->hctrl && cudaMallocHost(&w->hctrl, sizeof(BCtrl) + 64) != cudaSuccess) return RVE_E_OOM;
     unsigned char* b = w->base;
-    BArgs a{};
-    a.n = n;
-    a.V = (int)V;
-    a.half_n = 0.5 * n;
-    a.tol = in.tol;
-    a.inv_mu_ref = 1.0 / in.mu_ref;
-    a.adaptive = in.adaptive ? 1 : 0;
-    a.kappa = in.rho_kappa;
-    a.tau = in.rho_tau;
-    a.rho_floor = 0.0;
-    for (int j = 0; j < 3; ++j) {
-        const double th = j < D ? 2.0 * kPi / ((double)in.k[j] * n) : 0.0;
-        a.c[j] = a.half_n * cos(th);
-        a.s[j] = a.half_n * sin(th);
+
+    const FftPlanB pl = make_plan(n);
+    const int eg = grid_for(V);
+    const int fgrid = std::min((int)((V / n + pl.tl - 1) / pl.tl) * D, 152 * 3);
+    Phase<D, double> pd;
+    Phase<D, float> pf;
+    auto common = [&](auto& ph) {
+        auto& a = ph.a;
+        a.n = n;
+        a.V = (int)V;
+        a.tol = in.tol;
+        a.inv_mu_ref = 1.0 / in.mu_ref;
+        a.adaptive = in.adaptive ? 1 : 0;
+        a.kappa = in.rho_kappa;
+        a.tau = in.rho_tau;
+        a.rho_floor = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            const double th = j < D ? 2.0 * kPi / ((double)in.k[j] * n) : 0.0;
+            a.c[j] = 0.5 * n * cos(th);
+            a.s[j] = 0.5 * n * sin(th);
+        }
+        a.W = (double*)(b + oW);
+        a.part = (double*)(b + opart);
+        a.hist = (double*)(b + ohist);
+        a.sym = (const double*)(b + osym);
+        a.ctrl = (BCtrl*)(b + octrl);
+        a.max_hist = in.max_iter;
+        ph.in = &in;
+        ph.pl = pl;
+        ph.eg = eg;
+        ph.fg = fgrid;
+        ph.st = st;
+    };
+    common(pd);
+    bind(pd, b, dP0, dP1, dB, dG, dg, dQ, dL, dLi, dtw);
+    pd.smem = (size_t)2 * pl.tl * n * sizeof(double2);
+    if (bulk) {
+        common(pf);
+        bind(pf, b, fP0, fP1, fB, fG, fg_, fQ, fL, fLi, ftw);
+        pf.smem = (size_t)2 * pl.tl * n * sizeof(float2);
     }
-    a.P0 = (double2*)(b + oP0);
-    a.P1 = (double2*)(b + oP1);
-    a.B = (double2*)(b + oB);
-    a.G = (double2*)(b + oG);
-    a.g = (double2*)(b + og);
-    a.Q = (double2*)(b + oQ);
-    a.Lf = (double*)(b + oL);
-    a.Linv = (double*)(b + oLi);
-    a.W = (double*)(b + oW);
-    a.part = (double*)(b + opart);
-    a.hist = (double*)(b + ohist);
-    a.sym = (const double*)(b + osym);
-    a.ctrl = (BCtrl*)(b + octrl);
-    a.max_hist = in.max_iter;
     double* d_rq = (double*)(b + orq);
-    double2* tw = (double2*)(b + otw);
+    BCtrl* dctrl = pd.a.ctrl;
 
     // host-side tables and the normalised start
     std::vector<double> sym(3 * (size_t)n, 0.0);
     for (int j = 0; j < D; ++j)
         for (int m = 0; m < n; ++m) sym[(size_t)j * n + m] = n * sin(2.0 * kPi * (m + 1.0 / in.k[j]) / n);
     std::vector<double2> twh(n);
-    for (int t = 0; t < n; ++t) twh[t] = make_double2(cos(2.0 * kPi * t / n), -sin(2.0 * kPi * t / n));
+    std::vector<float2> twf(n);
+    for (int t = 0; t < n; ++t) {
+        twh[t] = make_double2(cos(2.0 * kPi * t / n), -sin(2.0 * kPi * t / n));
+        twf[t] = make_float2((float)twh[t].x, (float)twh[t].y);
+    }
     double nrm = 0.0;
     for (size_t i = 0; i < 2 * (size_t)D * V; ++i) nrm += in.p0[i] * in.p0[i];
     nrm = sqrt(nrm / (double)V);
@@ -940,159 +1115,165 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     BCtrl c0{};
     c0.sigma = NAN;
     c0.rho = in.rho;
-#define CKB(x)                                  \
-    do {                                        \
+#define CKB(x)                                     \
+    do {                                           \
         if ((x) != cudaSuccess) return RVE_E_CUDA; \
     } while (0)
-    CKB(cudaMemcpyAsync((void*)a.sym, sym.data(), sym.size() * 8, cudaMemcpyHostToDevice, st));
-    CKB(cudaMemcpyAsync(tw, twh.data(), twh.size() * 16, cudaMemcpyHostToDevice, st));
-    CKB(cudaMemcpyAsync(a.P0, p0.data(), p0.size() * 8, cudaMemcpyHostToDevice, st));
-    CKB(cudaMemcpyAsync(a.ctrl, &c0, sizeof(BCtrl), cudaMemcpyHostToDevice, st));
-    const FftPlanB pl = make_plan(n);
-    const size_t smem = (size_t)2 * pl.tl * n * sizeof(double2);
-    CKB(set_fft_attrs<D>(smem));
-    const int eg = grid_for(V);
-    const int ntiles = (int)((V / n + pl.tl - 1) / pl.tl) * D;
-    const int fg = std::min(ntiles, 152 * 3);
+    CKB(cudaMemcpyAsync((void*)pd.a.sym, sym.data(), sym.size() * 8, cudaMemcpyHostToDevice, st));
+    CKB(cudaMemcpyAsync(pd.tw, twh.data(), twh.size() * 16, cudaMemcpyHostToDevice, st));
+    CKB(cudaMemcpyAsync(dctrl, &c0, sizeof(BCtrl), cudaMemcpyHostToDevice, st));
+    CKB((set_fft_attrs<D, double>(pd.smem)));
+    if (bulk) {
+        std::vector<float> p0f(p0.size());
+        for (size_t i = 0; i < p0.size(); ++i) p0f[i] = (float)p0[i];
+        CKB(cudaMemcpyAsync(pf.tw, twf.data(), twf.size() * 8, cudaMemcpyHostToDevice, st));
+        CKB(cudaMemcpyAsync(pf.a.P0, p0f.data(), p0f.size() * 4, cudaMemcpyHostToDevice, st));
+        CKB((set_fft_attrs<D, float>(pf.smem)));
+    } else {
+        CKB(cudaMemcpyAsync(pd.a.P0, p0.data(), p0.size() * 8, cudaMemcpyHostToDevice, st));
+    }
     long long launches = 0;
-    auto factor = [&](int mode, double shift) {
-        if (in.model == kNeoHooke) {
-            if (in.F_fp64)
-                k_bfactor<D, kNeoHooke, double><<<eg, kBT, 0, st>>>(a, (const double*)in.F, in.phase, in.mat, in.nparam,
-                                                                    mode, shift);
-            else
-                k_bfactor<D, kNeoHooke, float><<<eg, kBT, 0, st>>>(a, (const float*)in.F, in.phase, in.mat, in.nparam,
-                                                                   mode, shift);
-        } else {
-            if (in.F_fp64)
-                k_bfactor<D, kLinear, double><<<eg, kBT, 0, st>>>(a, (const double*)in.F, in.phase, in.mat, in.nparam,
-                                                                  mode, shift);
-            else
-                k_bfactor<D, kLinear, float><<<eg, kBT, 0, st>>>(a, (const float*)in.F, in.phase, in.mat, in.nparam,
-                                                                 mode, shift);
-        }
-    };
     BCtrl* hc = (BCtrl*)w->hctrl;
-    factor(0, 0.0);
+    auto read_ctrl = [&]() -> bool {
+        return cudaGetLastError() == cudaSuccess &&
+               cudaMemcpyAsync(hc, dctrl, sizeof(BCtrl), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+               cudaStreamSynchronize(st) == cudaSuccess;
+    };
+    // positive definiteness at the starting rho (the double factor decides)
+    pd.factor(0, 0.0);
     launches += 1;
-    CKB(cudaMemcpyAsync(hc, a.ctrl, sizeof(BCtrl), cudaMemcpyDeviceToHost, st));
-    CKB(cudaStreamSynchronize(st));
-    CKB(cudaGetLastError());
+    if (!read_ctrl()) return RVE_E_CUDA;
     if (hc->fail & 1) return RVE_E_NUMERICAL;
-    if (a.adaptive) {
+    if (in.adaptive) {
         // floor of the rule: max(rho_min or mu_ref, 2 s*), s* the smallest shift with
         // L + s* I positive definite everywhere (bisection on [0, rho], to 2^-16 rho)
-        auto pd = [&](double sft) -> int {
-            if (cudaMemsetAsync(&a.ctrl->fail, 0, sizeof(int), st) != cudaSuccess) return -1;
-            factor(2, sft);
+        auto pdtest = [&](double sft) -> int {
+            if (cudaMemsetAsync(&dctrl->fail, 0, sizeof(int), st) != cudaSuccess) return -1;
+            pd.factor(2, sft);
             launches += 1;
-            if (cudaMemcpyAsync(hc, a.ctrl, sizeof(BCtrl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess)
-                return -1;
+            if (!read_ctrl()) return -1;
             return (hc->fail & 1) ? 0 : 1;
         };
         double smin = 0.0;
-        int r0 = pd(0.0);
+        const int r0 = pdtest(0.0);
         if (r0 < 0) return RVE_E_CUDA;
         if (!r0) {
             double lo = 0.0, hi = in.rho;
-            for (int b = 0; b < 16; ++b) {
+            for (int it = 0; it < 16; ++it) {
                 const double mid = 0.5 * (lo + hi);
-                const int r = pd(mid);
+                const int r = pdtest(mid);
                 if (r < 0) return RVE_E_CUDA;
                 if (r) hi = mid;
                 else lo = mid;
             }
             smin = hi;
         }
-        CKB(cudaMemsetAsync(&a.ctrl->fail, 0, sizeof(int), st));
-        a.rho_floor = std::max(in.rho_min > 0.0 ? in.rho_min : in.mu_ref, 2.0 * smin);
+        CKB(cudaMemsetAsync(&dctrl->fail, 0, sizeof(int), st));
+        pd.a.rho_floor = pf.a.rho_floor = std::max(in.rho_min > 0.0 ? in.rho_min : in.mu_ref, 2.0 * smin);
     }
-    k_binit<D><<<eg, kBT, 0, st>>>(a);
-    launches += 1;
 
     cudaEvent_t e0, e1;
     CKB(cudaEventCreate(&e0));
     CKB(cudaEventCreate(&e1));
     CKB(cudaEventRecord(e0, st));
-    auto iteration = [&](long long i) {  // iteration i reads p_{i-1} and writes p_i
-        double2* Pold = ((i - 1) & 1) ? a.P1 : a.P0;
-        double2* Pnew = (i & 1) ? a.P1 : a.P0;
-        const int passes = i == 1 ? kRootPasses0 : (i == 2 ? kRootPasses1 : kRootPasses);
-        k_bdiv<D><<<eg, kBT, 0, st>>>(a);
-        fft_all<D, false>(a, tw, pl, smem, fg, st);
-        k_bweights<D><<<eg, kBT, 0, st>>>(a);
-        for (int r = 0; r < passes; ++r) k_broot<D><<<eg, kBT, 0, st>>>(a, r == passes - 1);
-        k_bphat<D><<<eg, kBT, 0, st>>>(a);
-        fft_all<D, true>(a, tw, pl, smem, fg, st);
-        k_blocal<D><<<eg, kBT, 0, st>>>(a, Pold, Pnew);
-        if (a.adaptive) {  // after a change of rho: new factor, Step 1' again
-            factor(1, 0.0);
-            k_bredo<D><<<eg, kBT, 0, st>>>(a, Pnew);
-        }
-        return 4 + 2 * D + passes + (a.adaptive ? 2 : 0);
-    };
-    // The first chunk runs as plain launches (its first iterations take more root
-    // passes); later full chunks replay a graph per starting parity of p.
-    long long it = 0;
     const int chunk = std::max(1, in.check_every);
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int per_chunk = 0;
-    auto drop_graphs = [&]() {
-        for (auto& g : graph)
-            if (g) cudaGraphExecDestroy(g);
-    };
-    while (it < in.max_iter) {
-        const long long m = std::min<long long>(chunk, in.max_iter - it);
-        if (it >= 2 && m == chunk) {
-            const int par = (int)(it & 1);
-            if (!graph[par]) {
-                cudaGraph_t g = nullptr;
-                per_chunk = 0;
-                if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-                    drop_graphs();
-                    return RVE_E_CUDA;
-                }
-                for (long long q = 0; q < m; ++q) per_chunk += iteration(it + q + 1);
-                const cudaError_t ec = cudaStreamEndCapture(st, &g);
-                const cudaError_t ei = ec == cudaSuccess ? cudaGraphInstantiate(&graph[par], g, 0) : ec;
-                if (g) cudaGraphDestroy(g);
-                if (ei != cudaSuccess) {
-                    drop_graphs();
-                    return RVE_E_CUDA;
-                }
+    long long it = 0, float_iters = 0;
+    bool promoted = false;
+    int ok = RVE_OK;
+    if (bulk) {
+        pf.factor(0, 0.0);
+        k_binit<D, float><<<eg, kBT, 0, st>>>(pf.a);
+        launches += 2;
+        // switch to FP64 once both residuals are within a few hundred float roundings of
+        // their scale (sqrt(min kappa) for |D p| of a unit p; times rho / mu_ref for r_d),
+        // or after 200 iterations without a 1 % gain
+        double best = 1e300;
+        long long best_it = 0;
+        while (it < in.max_iter) {
+            const long long m = std::min<long long>(chunk, in.max_iter - it);
+            const long long l = pf.chunk(it, m, chunk);
+            if (l < 0 || !read_ctrl()) {
+                ok = RVE_E_CUDA;
+                break;
             }
-            if (cudaGraphLaunch(graph[par], st) != cudaSuccess) {
-                drop_graphs();
-                return RVE_E_CUDA;
+            launches += l;
+            it += m;
+            const double scale = sqrt(fmax(hc->pole / hc->rho, 0.0));
+            const double eps = 256.0 * 5.96e-8 * scale;
+            const double res = fmax(hc->rp, hc->rd * in.mu_ref / hc->rho);
+            if (res < 0.99 * best) {
+                best = res;
+                best_it = it;
             }
-            launches += per_chunk;
-        } else {
-            for (long long q = 0; q < m; ++q) launches += iteration(it + q + 1);
+            if (hc->stop == 3) break;
+            if (hc->stop == 1 || (hc->rp <= eps && hc->rd <= eps * hc->rho / in.mu_ref) || it - best_it >= 200) {
+                promoted = in.promote;  // RVE_FP32 ends here
+                break;
+            }
         }
-        if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(hc, a.ctrl, sizeof(BCtrl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
-            drop_graphs();
-            return RVE_E_CUDA;
+        float_iters = it;
+        pf.drop();
+        if (promoted && (ok != RVE_OK || hc->stop == 3 || it >= in.max_iter)) promoted = false;
+        if (promoted) {
+            // promote: p_k and g to double, the double factor and Step 1' (forced redo)
+            const long long k = hc->k;
+            k_bpromote<D><<<eg, kBT, 0, st>>>((k & 1) ? pf.a.P1 : pf.a.P0, pf.a.g, (k & 1) ? pd.a.P1 : pd.a.P0,
+                                              pd.a.g, (int)V);
+            const int one = 1, zero = 0;
+            CKB(cudaMemcpyAsync(&dctrl->stop, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+            CKB(cudaMemcpyAsync(&dctrl->rho_changed, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+            pd.factor(1, 0.0);
+            k_bredo<D, double><<<eg, kBT, 0, st>>>(pd.a, (k & 1) ? pd.a.P1 : pd.a.P0);
+            launches += 3;
+            hc->stop = 0;
         }
-        it += m;
-        if (hc->stop) break;
     }
-    drop_graphs();
+    if (ok == RVE_OK && (!bulk || promoted)) {
+        if (!bulk) {
+            k_binit<D, double><<<eg, kBT, 0, st>>>(pd.a);
+            launches += 1;
+        }
+        while (it < in.max_iter) {
+            const long long m = std::min<long long>(chunk, in.max_iter - it);
+            const long long l = pd.chunk(it, m, chunk);
+            if (l < 0 || !read_ctrl()) {
+                ok = RVE_E_CUDA;
+                break;
+            }
+            launches += l;
+            it += m;
+            if (hc->stop) break;
+        }
+        pd.drop();
+    }
+    if (ok != RVE_OK) return ok;
     CKB(cudaEventRecord(e1, st));
     const long long k = hc->k;
-    double2* Pfin = (k & 1) ? a.P1 : a.P0;
-    k_brayleigh<D><<<eg, kBT, 0, st>>>(a, Pfin, d_rq);
+    const bool fin_float = bulk && !promoted;
+    if (fin_float) {
+        float2* P = (k & 1) ? pf.a.P1 : pf.a.P0;
+        k_brayleigh<D, float><<<eg, kBT, 0, st>>>(pf.a, P, d_rq);
+        if (in.p_out) {
+            std::vector<float> pfh(2 * (size_t)D * V);
+            CKB(cudaMemcpyAsync(pfh.data(), P, pfh.size() * 4, cudaMemcpyDeviceToHost, st));
+            CKB(cudaStreamSynchronize(st));
+            for (size_t i = 0; i < pfh.size(); ++i) in.p_out[i] = pfh[i];
+        }
+    } else {
+        double2* P = (k & 1) ? pd.a.P1 : pd.a.P0;
+        k_brayleigh<D, double><<<eg, kBT, 0, st>>>(pd.a, P, d_rq);
+        if (in.p_out) CKB(cudaMemcpyAsync(in.p_out, P, 16 * (size_t)D * V, cudaMemcpyDeviceToHost, st));
+    }
     launches += 1;
     double rq = 0.0;
     CKB(cudaMemcpyAsync(&rq, d_rq, 8, cudaMemcpyDeviceToHost, st));
-    if (in.p_out) CKB(cudaMemcpyAsync(in.p_out, Pfin, 16 * (size_t)D * V, cudaMemcpyDeviceToHost, st));
     CKB(cudaStreamSynchronize(st));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     res->iterations = (int)k;
+    res->float_iterations = (int)std::min<long long>(float_iters, k);
     res->converged = hc->stop == 1;
     res->beta = hc->sigma;
     res->rayleigh = rq;
@@ -1103,7 +1284,7 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     res->fail = hc->fail;
     res->rho = hc->rho;
     if (in.hist_out && k > 0)
-        CKB(cudaMemcpy(in.hist_out, a.hist, 8 * 4 * (size_t)std::min<long long>(k, in.max_iter),
+        CKB(cudaMemcpy(in.hist_out, pd.a.hist, 8 * 4 * (size_t)std::min<long long>(k, in.max_iter),
                        cudaMemcpyDeviceToHost));
 #undef CKB
     if (hc->stop == 3) return RVE_E_NUMERICAL;

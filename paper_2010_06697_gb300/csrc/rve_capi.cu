@@ -923,6 +923,8 @@ int rve_bloch(rve_t h, const int k[3], const double* p0, double rho, double tol,
     a.tol = tol;
     a.mu_ref = h->opt.mu_ref > 0 ? h->opt.mu_ref : h->mu_ref;
     a.adaptive = h->opt.rho_policy == RVE_RHO_ADAPTIVE;
+    a.float_bulk = h->opt.precision != RVE_FP64;
+    a.promote = h->opt.precision == RVE_MIXED;
     a.rho_kappa = h->opt.rho_kappa;
     a.rho_tau = h->opt.rho_tau;
     a.rho_min = h->opt.rho_min;
@@ -945,6 +947,7 @@ int rve_bloch(rve_t h, const int k[3], const double* p0, double rho, double tol,
         info->launches = r.launches;
         info->fail = r.fail;
         info->rho = r.rho;
+        info->float_iterations = r.float_iterations;
     }
     return rc;
 }

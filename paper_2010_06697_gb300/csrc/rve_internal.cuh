@@ -242,6 +242,8 @@ struct BlochArgs {
     int k[3];             // Bloch wave numbers, omega_j = 2 pi / k_j
     double rho, tol, mu_ref;
     bool adaptive;        // Section 2.1's residual balancing of rho
+    bool float_bulk;      // a float phase first (RVE_MIXED, RVE_FP32)
+    bool promote;         // then FP64 to the tolerance (RVE_MIXED)
     double rho_kappa, rho_tau, rho_min;
     int max_iter, check_every;
     const double* p0;     // host, 2 d V doubles (re, im), component-major
@@ -250,7 +252,7 @@ struct BlochArgs {
     cudaStream_t stream;
 };
 struct BlochResult {
-    int iterations, converged, fail;
+    int iterations, float_iterations, converged, fail;
     double beta, rayleigh, r_p, r_d, time_ms, rho;
     long long launches;
 };

@@ -93,6 +93,7 @@ class rve_bloch_info(ctypes.Structure):
         ("launches", ctypes.c_longlong),
         ("fail", ctypes.c_int),
         ("rho", ctypes.c_double),
+        ("float_iterations", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -234,12 +234,12 @@ def test_bloch_adaptive_is_faster_on_a_compressed_cell():
 
 
 def test_bloch_on_a_float_state_handle():
-    """A handle in RVE_FP32 keeps F in float: the tangent is formed from the float F
+    """A handle in RVE_MIXED keeps a set F in float: the tangent is formed from the float F
     (promoted to double), so beta_k agrees with the FP64 handle's to float rounding of F."""
     d, n, k = 2, 16, (3, 4)
     ph, par, F = two_phase_case(d, n)
     out = []
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "mixed"):
         s = rve.Rve(d, n, "neohookean", prec, max_iter=10, rho_policy="adaptive")
         s.set_material(ph, par)
         s.set_field(rve.RVE_FIELD_F, F)
@@ -247,3 +247,43 @@ def test_bloch_on_a_float_state_handle():
         assert info.converged
         out.append(info.beta)
     np.testing.assert_allclose(out[1], out[0], rtol=1e-5)
+
+
+
+# ------------------------------------------------------------------ float bulk
+
+@pytest.mark.parametrize("d,n,k", [(2, 24, (3, 4)), (3, 12, (2, 3, -4))])
+def test_bloch_mixed_matches_fp64(d, n, k):
+    """RVE_MIXED: a float bulk, then FP64 to the tolerance; the same beta_k as the FP64
+    handle on the same F (double in both: F is set through a double handle's field, then
+    read back and set again, so both hold the float-representable values)."""
+    ph, par, F = two_phase_case(d, n)
+    F = F.astype(np.float32).astype(np.float64)  # exactly representable in both handles
+    out = {}
+    for prec in ("fp64", "mixed"):
+        s = rve.Rve(d, n, "neohookean", prec, max_iter=10, rho_policy="adaptive")
+        s.set_material(ph, par)
+        s.set_field(rve.RVE_FIELD_F, F)
+        info, p, hist = s.bloch(k, 40.0, 1e-10, 40000, seed=3)
+        assert info.converged
+        out[prec] = (info, p)
+    im, i64 = out["mixed"][0], out["fp64"][0]
+    assert 0 < im.float_iterations < im.iterations
+    np.testing.assert_allclose(im.beta, i64.beta, rtol=1e-9)
+    np.testing.assert_allclose(im.rayleigh, i64.rayleigh, rtol=1e-9)
+    assert abs(np.sum(np.abs(out["mixed"][1]) ** 2) / n ** d - 1.0) < 1e-12
+
+
+def test_bloch_fp32_stops_after_the_float_phase():
+    d, n, k = 2, 24, (3, 4)
+    ph, par, F = two_phase_case(d, n)
+    F = F.astype(np.float32).astype(np.float64)
+    s64 = handle_with_state(d, n, "neohookean", ph, par, F)
+    i64, _, _ = s64.bloch(k, 10.0, 1e-10, 40000, seed=3)
+    s = rve.Rve(d, n, "neohookean", "fp32", max_iter=10)
+    s.set_material(ph, par)
+    s.set_field(rve.RVE_FIELD_F, F)
+    rc, info, p, hist = rve.rve_bloch(s.h, k, synth.bloch_start(n, d, 3), 10.0, 1e-10, 40000)
+    assert rc in (rve.RVE_OK, rve.RVE_E_NOT_CONVERGED)
+    assert info.float_iterations == info.iterations > 0
+    np.testing.assert_allclose(info.beta, i64.beta, rtol=1e-4)
