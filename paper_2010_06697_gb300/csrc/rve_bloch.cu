@@ -737,7 +737,7 @@ __global__ void __launch_bounds__(kBT) k_bphat(BArgs<T> a) {
 // Step 1' of iteration i + 1 (G_{i+1}, Q); p_i is copied to Pnew.  The last block
 // finishes the residuals, records them and sets the stop flag.
 template <int D, typename T>
-__global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kBT, (sizeof(T) == 4 || D == 2) ? 2 : 1)
 k_blocal(BArgs<T> a, const typename Cx<T>::type* __restrict__ Pold, typename Cx<T>::type* __restrict__ Pnew) {
     constexpr int NN = D * D;
     using C = typename Cx<T>::type;
