@@ -375,9 +375,11 @@ def other_workloads():
             ("inclusions128_fraction", lambda t, r, sy: bench_inexact128(t, r, sy, ratio=0.0, fraction=0.9)),
             ("lce256", bench_lce256), ("lce128_pe_path", bench_lce_path128),
             ("lce128_pe_path_inc", lambda t, r, sy: bench_lce_path128(t, r, sy, incompressible=True)),
+            ("lce128_pe_path_mixed", lambda t, r, sy: bench_lce_path128(t, r, sy, precision="mixed")),
             ("bloch512_2d", bench_bloch512), ("bloch128_3d", bench_bloch128_3d), ("batch64", bench_batch64),
             ("serving", bench_serving),
-            ("serving_20hz", lambda t, r, sy: bench_serving(t, r, sy, count=48, rate=20.0)))
+            ("serving_20hz", lambda t, r, sy: bench_serving(t, r, sy, count=48, rate=20.0)),
+            ("serving_5hz", lambda t, r, sy: bench_serving(t, r, sy, count=32, rate=5.0)))
 
 
 def run_workload(args):
@@ -499,13 +501,14 @@ def bench_lce256(torch, rve, synth, iters=40):
             "r_p": info.r_p, "r_d": info.r_d, "stress_xx": float(S[0, 0]), "precision": "mixed"}
 
 
-def bench_lce_path128(torch, rve, synth, incompressible=False, steps=5, iters=30):
+def bench_lce_path128(torch, rve, synth, incompressible=False, steps=5, iters=30, precision="fp64"):
     """3D 128^3 LCE polydomain under a plane-strain loading path with dissipation
     (Section 5.3): <F_11> = 1.02, 1.04, ..., <F_12> = 0, <F_22> = 1, the other components
     free (mixed control); one time step per load step with nu_F/(mu dt) = 5.6,
     nu_n/(mu dt) = 0.0106; r = 7.71, alpha = 0.06, wall length 2h, directors from a
-    Gaussian random field (correlation 8 voxels); FP64; a fixed iteration count per
-    step.  incompressible: the network with det F = 1 by the local multiplier."""
+    Gaussian random field (correlation 8 voxels); FP64 (or the mixed scheme); a fixed
+    iteration count per step.  incompressible: the network with det F = 1 by the local
+    multiplier."""
     n = 128
     n0 = synth.director_grf(n, 0, corr=8.0)
     ph = np.zeros((n,) * 3, np.uint8)
@@ -513,7 +516,7 @@ def bench_lce_path128(torch, rve, synth, incompressible=False, steps=5, iters=30
     free = np.ones((3, 3), bool)
     free[0, 0] = free[0, 1] = free[1, 1] = False
     Fbars = np.stack([np.diag([1.0 + 0.02 * (k + 1), 1.0, 1.0]) for k in range(steps)])
-    s = rve.Rve(3, n, "lce", "fp64", max_iter=iters)
+    s = rve.Rve(3, n, "lce", precision, max_iter=iters)
     s.set_material(ph, par, n0)
     s.solve_path(Fbars[:1], RHO, -1.0, free=free)  # warm-up (kernels, graphs)
     s.set_material(ph, par, n0)
@@ -526,8 +529,9 @@ def bench_lce_path128(torch, rve, synth, incompressible=False, steps=5, iters=30
     ms = ev0.elapsed_time(ev1)
     its = sum(i.iterations for i in infos)
     s.close()
-    return {"workload": "lce128_pe_path" + ("_inc" if incompressible else ""), "value": ph.size * its / (ms / 1e3),
-            "unit": UNIT, "ms": ms, "load_steps": steps, "iterations": its, "precision": "fp64",
+    return {"workload": "lce128_pe_path" + ("_inc" if incompressible else "") + ("_mixed" if precision != "fp64" else ""),
+            "value": ph.size * its / (ms / 1e3),
+            "unit": UNIT, "ms": ms, "load_steps": steps, "iterations": its, "precision": precision,
             "S11": [float(x[0, 0]) for x in S], "F33": [float(x[2, 2]) for x in Fo],
             "r_p_last": infos[-1].r_p, "r_d_last": infos[-1].r_d}
 

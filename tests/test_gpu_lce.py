@@ -262,3 +262,24 @@ def test_incompressible_flag_checked():
     for par in (bad_mix, bad_val):
         with pytest.raises(rve.RveError):
             a.set_material(ph, par, n0)
+
+
+def test_lce_plane_stress_path_mixed_tracks_fp64():
+    """The same 3-step PE path with dissipation in the mixed scheme: <S> and <F> of every
+    step within 1e-4 of the FP64 path (float bulk, fixed iteration counts)."""
+    n = 12
+    ph = np.zeros((n,) * 3, np.uint8)
+    n0 = synth.director_grf(n, 10, corr=2.5)
+    par = lce_params_dt(n)
+    free = np.ones((3, 3), bool)
+    free[0, 0] = free[0, 1] = free[1, 1] = False
+    Fbars = np.stack([np.diag([l, 1.0, 1.0]) for l in (1.02, 1.04, 1.06)])
+    out = {}
+    for prec in ("fp64", "mixed"):
+        s = rve.Rve(3, n, "lce", prec, max_iter=12)
+        s.set_material(ph, par, n0)
+        out[prec] = s.solve_path(Fbars, 10.0, -1.0, free=free)
+    S64, F64, _ = out["fp64"]
+    S32, F32, _ = out["mixed"]
+    assert np.max(np.abs(S32 - S64)) < 1e-4 * max(1.0, np.max(np.abs(S64)))
+    assert np.max(np.abs(F32 - F64)) < 1e-4
