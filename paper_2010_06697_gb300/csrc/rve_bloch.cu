@@ -93,6 +93,7 @@ struct BArgs {
     double kappa, tau, rho_floor;
     T c[3], s[3];          // cos, sin of th_j, times 1/(2h)
     const double* sym;     // s_j(m) at sym[j * n + m]
+    const double* K;       // kappa(m) per frequency (k_bkappa, once per call)
     C *P0, *P1, *B, *G, *g, *Q;
     T *Lf, *Linv;
     double *W, *part, *hist;
@@ -294,7 +295,7 @@ __device__ __forceinline__ void fapply(const BArgs<T>& a, int v, const C* x, C* 
 // kappa(m) = sum_j s_j(m_j)^2 with explicit roundings (no contraction), so that every
 // kernel forms the same value.
 template <int D, typename T>
-__device__ __forceinline__ double kappa_of(const BArgs<T>& a, int v) {
+__device__ __forceinline__ double kappa_calc(const BArgs<T>& a, int v) {
     const int n = a.n;
     const int mx = v % n, r = v / n;
     const int my = D == 3 ? r % n : r;
@@ -307,9 +308,20 @@ __device__ __forceinline__ double kappa_of(const BArgs<T>& a, int v) {
     return k;
 }
 
+template <int D, typename T>
+__device__ __forceinline__ double kappa_of(const BArgs<T>& a, int v) {
+    return __ldg(a.K + v);
+}
+
 // ------------------------------------------------------------------ kernels
 // Every kernel takes rho from the control block: the adaptive rule changes it between
 // iterations.
+
+// The table of kappa(m) the spectrum passes read.
+template <int D, typename T>
+__global__ void __launch_bounds__(kBT) k_bkappa(BArgs<T> a, double* K) {
+    for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) K[v] = kappa_calc<D, T>(a, v);
+}
 
 // L + rho I = W_FF(F) + rho I per voxel (compressible neo-Hookean, Section 4.1, or
 // isotropic linear elasticity), Cholesky-factored in double.
@@ -620,12 +632,13 @@ __global__ void __launch_bounds__(kBT) k_bweights(BArgs<T> a) {
     if (a.ctrl->stop) return;
     double ws = 0.0, km = 1e300, wm = 0.0;
     for (int v = blockIdx.x * kBT + threadIdx.x; v < a.V; v += gridDim.x * kBT) {
-        double w = 0.0;
+        T wt = T(0);  // in the field precision: the spectrum of a float phase is float
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             const auto b = a.B[(size_t)i * a.V + v];
-            w += (double)b.x * (double)b.x + (double)b.y * (double)b.y;
+            wt += b.x * b.x + b.y * b.y;
         }
+        const double w = (double)wt;
         a.W[v] = w;
         ws += w;
         kw_merge(km, wm, kappa_of<D, T>(a, v), w);
@@ -1041,7 +1054,8 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
         fG = take(8 * NN * V), fg_ = take(8 * NN * V), fQ = take(8 * NN * V);
         fL = take(4 * (size_t)NP * V), fLi = take(4 * NN * V), ftw = take(8 * n);
     }
-    const size_t oW = take(8 * V), opart = take(8 * 4 * kBlochBlocks), ohist = take(8 * 4 * (size_t)in.max_iter);
+    const size_t oW = take(8 * V), oK = take(8 * V), opart = take(8 * 4 * kBlochBlocks),
+                 ohist = take(8 * 4 * (size_t)in.max_iter);
     const size_t osym = take(8 * 3 * n), octrl = take(sizeof(BCtrl)), orq = take(8);
     if (w->bytes < off) {
         if (w->base) cudaFree(w->base);
@@ -1077,6 +1091,7 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
         a.part = (double*)(b + opart);
         a.hist = (double*)(b + ohist);
         a.sym = (const double*)(b + osym);
+        a.K = (const double*)(b + oK);
         a.ctrl = (BCtrl*)(b + octrl);
         a.max_hist = in.max_iter;
         ph.in = &in;
@@ -1122,6 +1137,7 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     CKB(cudaMemcpyAsync((void*)pd.a.sym, sym.data(), sym.size() * 8, cudaMemcpyHostToDevice, st));
     CKB(cudaMemcpyAsync(pd.tw, twh.data(), twh.size() * 16, cudaMemcpyHostToDevice, st));
     CKB(cudaMemcpyAsync(dctrl, &c0, sizeof(BCtrl), cudaMemcpyHostToDevice, st));
+    k_bkappa<D, double><<<eg, kBT, 0, st>>>(pd.a, (double*)(b + oK));
     CKB((set_fft_attrs<D, double>(pd.smem)));
     if (bulk) {
         std::vector<float> p0f(p0.size());
@@ -1132,7 +1148,7 @@ int run(BlochWork* w, const BlochArgs& in, BlochResult* res) {
     } else {
         CKB(cudaMemcpyAsync(pd.a.P0, p0.data(), p0.size() * 8, cudaMemcpyHostToDevice, st));
     }
-    long long launches = 0;
+    long long launches = 1;  // k_bkappa
     BCtrl* hc = (BCtrl*)w->hctrl;
     auto read_ctrl = [&]() -> bool {
         return cudaGetLastError() == cudaSuccess &&
