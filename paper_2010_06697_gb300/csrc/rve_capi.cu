@@ -271,6 +271,10 @@ int switch_to_double(rve* h, cudaStream_t st) {
     // polish: a step of max|dF| <= 1e-7 leaves an error of about 1e-6 * 1e-7 (float
     // Hessian) + |dF|^2, i.e. ~1e-13, far below the double residual tolerance
     h->hctrl->newton_tol = h->opt.newton_tol > 0 ? h->opt.newton_tol : 1e-7;
+    // the adaptive penalty acts during the float bulk; the double polish (increment form)
+    // needs a constant rho, so it keeps the value reached here
+    h->hctrl->adaptive = 0;
+    h->hctrl->rho_changed = 0;  // a pending redo is subsumed by the polish's first local step
     return write_ctrl_on(h, st);
 }
 
@@ -411,7 +415,7 @@ int capture_chunk(rve* h, bool fp64, bool incr, int slot) {
 int run_phase_body(rve* h, bool fp64, bool polish);
 
 // Run iterations in one precision until the device sets the stop flag.  polish
-// (RVE_MIXED, fixed rho): after the first step, one full double projection,
+// (RVE_MIXED; rho constant from the switch on): after the first step, one full double projection,
 // then increment projections in float (see admm::launch_fft_incr) with the state
 // of the elastic laws held as double-words; it returns to double on every exit.
 int run_phase(rve* h, bool fp64, bool polish = false) {
@@ -674,7 +678,7 @@ int solve_body(rve* h, const double Fbar[9], double rho, double tol, rve_solve_i
         if (o.precision == RVE_MIXED && h->hctrl->done == admm::kSwitch) {
             const long long ksw = h->hctrl->k;
             if (switch_to_double(h, h->stream)) return RVE_E_CUDA;
-            rc = run_phase(h, true, o.rho_policy == RVE_RHO_FIXED);
+            rc = run_phase(h, true, true);
             if (rc) return rc;
             fp64_iters = (int)(h->hctrl->k - ksw);
         } else if (o.precision == RVE_FP64) {
@@ -1400,7 +1404,6 @@ int engine_tick(Engine& E, std::vector<int>& finished) {
         rve* h = m.h;
         run_remove(E, slot);
         if (read_ctrl_on(h, E.stream)) return RVE_E_CUDA;
-        const bool fixed_rho = h->opt.rho_policy == RVE_RHO_FIXED;
         if (h->opt.precision == RVE_MIXED && m.stage == kStageF32 && h->hctrl->done == admm::kSwitch) {
             m.ksw = h->hctrl->k;
             if (switch_to_double(h, E.stream)) return RVE_E_CUDA;
@@ -1409,15 +1412,11 @@ int engine_tick(Engine& E, std::vector<int>& finished) {
             admm::Exec Ei = h->E;
             Ei.stream = E.stream;
             if (admm::launch_local(Ei, true, true, false) != cudaSuccess) return RVE_E_CUDA;
-            if (fixed_rho) {
-                if (admm::launch_fft(Ei, true) != cudaSuccess) return RVE_E_CUDA;
-                if (admm::launch_local(Ei, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
-                if (admm::launch_polish_state(h->L, true, E.stream) != cudaSuccess) return RVE_E_CUDA;
-                h->launches += admm::fft_stages(h->dim) + 4;
-            } else {
-                h->launches += 1;
-            }
-            m.stage = fixed_rho ? kStagePolish : kStageF64;
+            if (admm::launch_fft(Ei, true) != cudaSuccess) return RVE_E_CUDA;
+            if (admm::launch_local(Ei, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
+            if (admm::launch_polish_state(h->L, true, E.stream) != cudaSuccess) return RVE_E_CUDA;
+            h->launches += admm::fft_stages(h->dim) + 4;
+            m.stage = kStagePolish;
             run_insert(E, slot);
         } else {
             m.running = false;

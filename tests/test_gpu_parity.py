@@ -285,6 +285,14 @@ def test_full_size_converged_stress_matches_stored_oracle_run():
     m, im = run_gpu(ph, PAR, Fbar, g["recipe"]["rho"], g["recipe"]["tol"], 1000, precision="mixed")
     assert im.converged
     assert rel(m.stress(), np.array(g["stress"])) < 1e-5
+    # the bench's configuration: the adaptive penalty from the same rho, FP64 and mixed
+    a64, ia64 = run_gpu(ph, PAR, Fbar, g["recipe"]["rho"], g["recipe"]["tol"], 1000, rho_policy="adaptive")
+    assert ia64.converged
+    assert rel(a64.stress(), np.array(g["stress"])) < 1e-8
+    am, iam = run_gpu(ph, PAR, Fbar, g["recipe"]["rho"], g["recipe"]["tol"], 1000, precision="mixed",
+                      rho_policy="adaptive")
+    assert iam.converged and iam.iterations < info.iterations
+    assert rel(am.stress(), np.array(g["stress"])) < 1e-5
 
 
 # ------------------------------------------------------------------ large sizes (256^3, maximum 512^3)
@@ -359,3 +367,21 @@ def test_float_path_fixed_length_kernels_match_double():
     assert rel(a["F"], b["F"]) < 2e-5
     assert rel(a["u"], b["u"]) < 2e-4
     assert rel(a["Lam"], b["Lam"]) < 2e-5
+
+
+def test_mixed_adaptive_rho_freezes_for_the_polish():
+    """RVE_MIXED with the adaptive penalty: the rule acts in the float bulk, rho stays at
+    its value from the switch on (the double-word increment polish needs a constant rho),
+    and the converged stress matches the FP64 solve's to the mixed tolerance."""
+    n = 24
+    ph = synth.inclusion_phase(n, 3, 1, radius=3)
+    Fbar = np.diag([0.9, 1.0, 1.0])
+    s, info = run_gpu(ph, PAR, Fbar, 100.0, 1e-8, 2000, precision="mixed", rho_policy="adaptive")
+    s64, info64 = run_gpu(ph, PAR, Fbar, 100.0, 1e-8, 2000, rho_policy="adaptive")
+    assert info.converged and info64.converged
+    assert 0 < info.fp64_iterations < info.iterations
+    hist = s.history()
+    rhos = hist[:, 2]
+    assert len(set(rhos[: info.iterations - info.fp64_iterations])) > 1  # the rule acted
+    assert len(set(rhos[info.iterations - info.fp64_iterations:])) == 1  # frozen in the polish
+    assert rel(s.stress(), s64.stress()) < 1e-5
