@@ -35,9 +35,9 @@ UNIT = "voxel-iterations/s"
 N, DIM, SEED = 128, 3, 0
 FBAR = np.diag([0.9, 1.0, 1.0])
 RHO, TOL = 10.0, 1e-8
-# Section 2.1's adaptive penalty from RHO (residual balancing; under RVE_MIXED it acts in the
-# float bulk and rho stays fixed through the double polish)
-RHO_POLICY = "adaptive"
+# the headline keeps rho fixed: the metric is per-iteration throughput, and the adaptive rule
+# trades iterations for polish iterations (see bench_adaptive128 for its time to solution)
+RHO_POLICY = "fixed"
 MU = (1.0, 10.0)
 NU = 0.3
 L2_BYTES = 129e6
@@ -375,7 +375,8 @@ def run_ours(args):
 
 def other_workloads():
     """The workloads reported beside the headline line, as (name, function) pairs."""
-    return (("laminate32_2d", bench_laminate32), ("inclusions128_inexact", bench_inexact128),
+    return (("laminate32_2d", bench_laminate32), ("inclusions128_adaptive_rho", bench_adaptive128),
+            ("inclusions128_inexact", bench_inexact128),
             ("inclusions128_fraction", lambda t, r, sy: bench_inexact128(t, r, sy, ratio=0.0, fraction=0.9)),
             ("lce256", bench_lce256), ("lce128_pe_path", bench_lce_path128),
             ("lce128_pe_path_inc", lambda t, r, sy: bench_lce_path128(t, r, sy, incompressible=True)),
@@ -475,6 +476,32 @@ def bench_inexact128(torch, rve, synth, ratio=0.3, fraction=0.0, reps=3):
             "value": ph.size * info.iterations / (best / 1e3), "unit": UNIT, "ms": best,
             "iterations": info.iterations, "fp64_iterations": info.fp64_iterations,
             "converged": bool(info.converged), "stress_xx": float(S[0, 0]), "precision": "mixed"}
+
+
+def bench_adaptive128(torch, rve, synth, reps=3):
+    """The headline cell and tolerance with Section 2.1's adaptive penalty from rho = 10
+    (mixed; the rule acts in the float bulk, rho stays fixed through the double polish):
+    fewer iterations per solve; reports the time per solve beside the fixed-rho headline."""
+    ph, par = make_inputs()
+    s = rve.Rve(DIM, N, "neohookean", "mixed", max_iter=2000, rho_policy="adaptive")
+    s.set_material(ph, par)
+    s.solve(FBAR, RHO, TOL)
+    best, info = None, None
+    for _ in range(reps):
+        s.reset()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        info = s.solve(FBAR, RHO, TOL)
+        S = s.stress()
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        best = ms if best is None else min(best, ms)
+    s.close()
+    return {"workload": "inclusions128_adaptive_rho", "value": ph.size * info.iterations / (best / 1e3), "unit": UNIT,
+            "ms_per_solve": best, "iterations": info.iterations, "fp64_iterations": info.fp64_iterations,
+            "final_rho": info.rho, "converged": bool(info.converged), "stress_xx": float(S[0, 0])}
 
 
 def bench_lce256(torch, rve, synth, iters=40):
