@@ -372,14 +372,16 @@ void rve_server_destroy(rve_server_t s);
  * the order of the full-length radices -- in the arithmetic of the given precision
  * mode (double for RVE_FP64, float otherwise), and keep the fastest: every later
  * rve_create of that shape in this process uses it (handles created before keep
- * theirs).  If cache_path is not NULL, one text line
- * "rve-fft-geometry dim n precision lpb tk64 tk32 nh r... nf r... ms" is appended.
+ * theirs).  If cache_path is not NULL, one JSON object is appended as a line
+ * (JSON Lines): {"kind": "rve-fft-geometry", "dim", "n", "precision", "lpb", "tk64",
+ * "tk32", "rad_half": [...], "rad_full": [...], "ms"}.
  * *best_ms (may be NULL) gets the tuned FFT time of one iteration.  Allocates a
  * scratch handle.  Returns RVE_OK or an error. */
 int rve_autotune(int dim, int n, int precision, const char* cache_path, double* best_ms);
 
 /* Register the geometries stored in a cache file written by rve_autotune (later
- * lines win).  Returns the number of lines loaded, or RVE_E_NOT_FOUND. */
+ * lines win; lines that are not valid geometries are skipped).  Returns the number
+ * of lines loaded, or RVE_E_NOT_FOUND. */
 int rve_autotune_load(const char* cache_path);
 
 /* ------------------------------------------------------------------ profiling */

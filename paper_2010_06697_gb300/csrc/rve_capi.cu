@@ -1957,54 +1957,85 @@ int rve_autotune(int dim, int n, int precision, const char* cache_path, double* 
     if (best_ms) *best_ms = best_x + best_a;
     if (cache_path) {
         FILE* f = fopen(cache_path, "a");
-        if (f) {
-            fprintf(f, "rve-fft-geometry %d %d %d %d %d %d %d", dim, n, precision, best_g.lpb, best_g.tk64,
-                    best_g.tk32, best_g.np_half);
-            for (int i = 0; i < best_g.np_half; ++i) fprintf(f, " %d", best_g.rad_half[i]);
-            fprintf(f, " %d", best_g.np_full);
-            for (int i = 0; i < best_g.np_full; ++i) fprintf(f, " %d", best_g.rad_full[i]);
-            fprintf(f, " %.6f\n", best_x + best_a);
+        if (f) {  // one JSON object per line
+            fprintf(f, "{\"kind\": \"rve-fft-geometry\", \"dim\": %d, \"n\": %d, \"precision\": %d, \"lpb\": %d, "
+                       "\"tk64\": %d, \"tk32\": %d, \"rad_half\": [",
+                    dim, n, precision, best_g.lpb, best_g.tk64, best_g.tk32);
+            for (int i = 0; i < best_g.np_half; ++i) fprintf(f, "%s%d", i ? ", " : "", best_g.rad_half[i]);
+            fprintf(f, "], \"rad_full\": [");
+            for (int i = 0; i < best_g.np_full; ++i) fprintf(f, "%s%d", i ? ", " : "", best_g.rad_full[i]);
+            fprintf(f, "], \"ms\": %.6f}\n", best_x + best_a);
             fclose(f);
         }
     }
     return cleanup(RVE_OK);
 }
 
+// Cache lines: {"kind": "rve-fft-geometry", "dim": .., "n": .., "precision": .., "lpb": ..,
+// "tk64": .., "tk32": .., "rad_half": [..], "rad_full": [..], "ms": ..} -- the fields this
+// writer emits, read back by key (not a general JSON parser).
+namespace {
+const char* json_key(const char* line, const char* key) {
+    char pat[32];
+    snprintf(pat, sizeof pat, "\"%s\"", key);
+    const char* p = strstr(line, pat);
+    if (!p) return nullptr;
+    p += strlen(pat);
+    while (*p == ' ') ++p;
+    if (*p != ':') return nullptr;
+    ++p;
+    while (*p == ' ') ++p;
+    return p;
+}
+bool json_int(const char* line, const char* key, int* out) {
+    const char* p = json_key(line, key);
+    if (!p) return false;
+    char* e = nullptr;
+    const long v = strtol(p, &e, 10);
+    if (e == p || v < INT32_MIN || v > INT32_MAX) return false;
+    *out = (int)v;
+    return true;
+}
+// a list of radices (2, 3, 4 or 8) whose product is want; count in *np
+bool json_radices(const char* line, const char* key, int* rad, int* np, int want) {
+    const char* p = json_key(line, key);
+    if (!p || *p != '[') return false;
+    ++p;
+    int cnt = 0, prod = 1;
+    for (;;) {
+        while (*p == ' ') ++p;
+        if (*p == ']') break;
+        char* e = nullptr;
+        const long r = strtol(p, &e, 10);
+        if (e == p || !(r == 2 || r == 3 || r == 4 || r == 8) || cnt >= admm::kMaxPasses) return false;
+        rad[cnt++] = (int)r;
+        prod *= (int)r;
+        p = e;
+        while (*p == ' ') ++p;
+        if (*p == ',') ++p;
+        else if (*p != ']') return false;
+    }
+    *np = cnt;
+    return cnt > 0 && prod == want;
+}
+}  // namespace
+
 int rve_autotune_load(const char* cache_path) {
     if (!cache_path) return RVE_E_INVALID_ARG;
     FILE* f = fopen(cache_path, "r");
     if (!f) return RVE_E_NOT_FOUND;
-    char line[512];
+    char line[1024];
     int loaded = 0;
     while (fgets(line, sizeof line, f)) {
         admm::Geometry g{};
-        int dim, n, prec, pos = 0;
-        if (sscanf(line, "rve-fft-geometry %d %d %d %d %d %d %d%n", &dim, &n, &prec, &g.lpb, &g.tk64, &g.tk32,
-                   &g.np_half, &pos) != 7)
-            continue;
-        const char* p = line + pos;
-        bool ok = (dim == 2 || dim == 3) && valid_n(n) && g.np_half > 0 && g.np_half <= admm::kMaxPasses;
-        int prod = 1;
-        for (int i = 0; ok && i < g.np_half; ++i) {
-            int r = 0, k = 0;
-            ok = sscanf(p, " %d%n", &r, &k) == 1 && (r == 2 || r == 3 || r == 4 || r == 8);
-            g.rad_half[i] = r;
-            prod *= r;
-            p += k;
-        }
-        ok = ok && prod == n / 2;
-        int k = 0;
-        ok = ok && sscanf(p, " %d%n", &g.np_full, &k) == 1 && g.np_full > 0 && g.np_full <= admm::kMaxPasses;
-        p += k;
-        prod = 1;
-        for (int i = 0; ok && i < g.np_full; ++i) {
-            int r = 0;
-            ok = sscanf(p, " %d%n", &r, &k) == 1 && (r == 2 || r == 3 || r == 4 || r == 8);
-            g.rad_full[i] = r;
-            prod *= r;
-            p += k;
-        }
-        ok = ok && prod == n && g.lpb >= 1 && g.tk64 >= 1 && g.tk64 <= n / 2 && g.tk32 >= 1 && g.tk32 <= n / 2;
+        int dim = 0, n = 0, prec = 0;
+        bool ok = strstr(line, "\"rve-fft-geometry\"") != nullptr && json_int(line, "dim", &dim) &&
+                  json_int(line, "n", &n) && json_int(line, "precision", &prec) && json_int(line, "lpb", &g.lpb) &&
+                  json_int(line, "tk64", &g.tk64) && json_int(line, "tk32", &g.tk32);
+        ok = ok && (dim == 2 || dim == 3) && valid_n(n);
+        ok = ok && json_radices(line, "rad_half", g.rad_half, &g.np_half, n / 2) &&
+             json_radices(line, "rad_full", g.rad_full, &g.np_full, n);
+        ok = ok && g.lpb >= 1 && g.tk64 >= 1 && g.tk64 <= n / 2 && g.tk32 >= 1 && g.tk32 <= n / 2;
         if (ok) {
             admm::register_geometry(dim, n, g);
             ++loaded;

@@ -19,11 +19,14 @@ def _lib():
 
 @pytest.mark.parametrize("dim,n,precision", [(3, 24, "fp64"), (2, 96, "fp64"), (3, 48, "mixed")])
 def test_autotuned_geometry_keeps_parity(dim, n, precision, tmp_path):
-    cache = str(tmp_path / "fft.txt")
+    import json
+    cache = str(tmp_path / "fft.jsonl")
     ms = rve.rve_autotune(dim, n, precision, cache)
     assert ms > 0
     lines = open(cache).read().splitlines()
-    assert len(lines) == 1 and lines[0].startswith(f"rve-fft-geometry {dim} {n} ")
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["kind"] == "rve-fft-geometry" and rec["dim"] == dim and rec["n"] == n
     assert rve.rve_autotune_load(cache) == 1
     ph = synth.inclusion_phase(n, dim, 3, radius=3)
     Fbar = np.diag([0.95, 1.03, 1.0])
