@@ -165,12 +165,28 @@ def oracle_child(n: int, iters: int) -> dict:
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def host_info():
+    """The host the oracle ran on: logical CPUs and the CPU model (from /proc/cpuinfo)."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model, "machine": platform.machine()}
+
+
 def cpu_baseline():
     r = oracle_child(N, 1)
     v = r["voxels"] * r["iters"] / r["seconds"]
     return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"1 ADMM iteration of the {N}^3 inclusion cell from the fresh state "
-                      f"({r['seconds']:.1f} s, FP64 numpy oracle, 1 thread)"}
+                      f"({r['seconds']:.1f} s, FP64 numpy oracle, 1 thread)", "host": host_info()}
 
 
 # ------------------------------------------------------------------ reference arm (the oracle)
@@ -197,7 +213,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"inclusions{n}", "n": n, "dim": 3},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_info()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
