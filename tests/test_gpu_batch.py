@@ -59,6 +59,25 @@ def test_batch_members_equal_alone_solves_bitwise(precision):
         assert np.array_equal(s.stress(), S)
 
 
+def test_batch_mixed_adaptive_members_equal_alone_solves():
+    """RVE_MIXED with the adaptive penalty in a batch: rho is frozen at each member's switch
+    to double and the members take the increment polish; results equal the alone solves
+    bitwise and converge."""
+    specs = SPECS[:4]
+    Fb = fbars(len(specs), 60)
+    alone = members(specs, "mixed", rho_policy="adaptive")
+    ref = []
+    for s, F in zip(alone, Fb):
+        info = s.solve(F, 30.0, 1e-8)
+        ref.append((info.iterations, info.fp64_iterations, info.converged, s.stress()))
+    mix = members(specs, "mixed", rho_policy="adaptive")
+    infos = rve.Batch(mix).solve(Fb, np.full(len(specs), 30.0), 1e-8)
+    for s, info, (it, it64, conv, S) in zip(mix, infos, ref):
+        assert conv and info.converged
+        assert info.iterations == it and info.fp64_iterations == it64
+        assert np.array_equal(s.stress(), S)
+
+
 def test_batch_with_lce_and_neohookean_groups():
     """Two model groups (neo-Hookean, LCE) in one batch, fixed iteration count."""
     specs = [(3, 12, "inclusion", 1), (3, 12, "lce", 2), (3, 16, "lce", 3), (3, 16, "laminate", 4)]
