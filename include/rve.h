@@ -141,7 +141,8 @@ int rve_create(rve_t* out, int dim, int n, int model, const rve_options* opt, vo
 
 /* Same as rve_create but carves all device state out of a caller-owned device
  * buffer of `bytes` bytes (>= rve_workspace_bytes(...), 256-byte aligned), which
- * must outlive the handle.  Nothing is allocated on the device. */
+ * must outlive the handle.  Nothing is allocated on the device.  RVE_E_INVALID_ARG
+ * for a NULL or misaligned buffer, RVE_E_OOM when `bytes` is too small. */
 int rve_create_in(rve_t* out, int dim, int n, int model, const rve_options* opt, void* cuda_stream,
                   void* device_workspace, size_t bytes);
 

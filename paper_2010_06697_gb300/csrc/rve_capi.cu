@@ -733,7 +733,7 @@ int rve_create(rve_t* out, int dim, int n, int model, const rve_options* opt, vo
 
 int rve_create_in(rve_t* out, int dim, int n, int model, const rve_options* opt, void* cuda_stream,
                   void* device_workspace, size_t bytes) {
-    if (!device_workspace) return RVE_E_INVALID_ARG;
+    if (!device_workspace || reinterpret_cast<uintptr_t>(device_workspace) % kAlign != 0) return RVE_E_INVALID_ARG;
     return create_common(out, dim, n, model, opt, cuda_stream, device_workspace, bytes);
 }
 

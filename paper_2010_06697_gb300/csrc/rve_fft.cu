@@ -605,18 +605,76 @@ __device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid) {
         const T* L_c1 = INCR ? nullptr : Lam + (long long)(c * D + 1) * Vn;
         const T* L_c2 = INCR ? nullptr : Lam + (long long)(c * D + 2) * Vn;
         __syncthreads();  // the previous component's readers of the staging buffer are done
-        for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
-            const int l = idx >> X::LOGN;
-            const int x = idx & (N - 1);
-            const int y = y0 + l;
-            const Idx v = (Idx)line0 * N + idx;
-            const Idx xp = v + (x + 1 == N ? 1 - N : 1), xm = v + (x == 0 ? N - 1 : -1);
-            const Idx yp = v + (y + 1 == N ? (1 - N) * sn : sn), ym = v + (y == 0 ? (N - 1) * sn : -sn);
-            T q = (F_c0[xp] - F_c0[xm]) + (F_c1[yp] - F_c1[ym]);
-            if (!INCR) q -= ((L_c0[xp] - L_c0[xm]) + (L_c1[yp] - L_c1[ym])) * inv_rho;
-            q += F_c2[v + zp] - F_c2[v + zm];
-            if (!INCR) q -= (L_c2[v + zp] - L_c2[v + zm]) * inv_rho;
-            stage_r[((x >> 1) * S + l) * 2 + (x & 1)] = -q * half_n;  // z_m = r_{2m} + i r_{2m+1}
+        if constexpr (std::is_same<T, float>::value) {
+            // four consecutive x per thread: float4 loads of the centre row and of the y and
+            // z neighbour rows (fields are 256-byte aligned, x and N multiples of 4); the x
+            // neighbours of the end elements come from the adjacent lanes.  A warp spans 128
+            // consecutive x of one line (LPB * N / 4 is a multiple of the block size, so
+            // every warp runs every iteration): for N = 128 the lane rotation is the periodic
+            // wrap, for longer lines the two warp-end lanes load theirs.  Same arithmetic per
+            // element, in the same order, as the scalar form below.
+            const int lane = threadIdx.x & 31;
+            for (int idx = threadIdx.x; idx < LPB * N / 4; idx += blockDim.x) {
+                const int e = idx * 4;
+                const int l = e >> X::LOGN;
+                const int x = e & (N - 1);
+                const int y = y0 + l;
+                const Idx v = (Idx)line0 * N + e;
+                const Idx yp = v + (y + 1 == N ? (1 - N) * sn : sn), ym = v + (y == 0 ? (N - 1) * sn : -sn);
+                auto diffs = [&](const T* a0, const T* a1, const T* a2, T* dx, T* dy, T* dz) {
+                    const float4 c = *reinterpret_cast<const float4*>(a0 + v);
+                    T left = __shfl_sync(0xffffffffu, c.w, (lane + 31) & 31);
+                    T right = __shfl_sync(0xffffffffu, c.x, (lane + 1) & 31);
+                    if constexpr (N > 128) {
+                        if (lane == 0) left = a0[v + (x == 0 ? N - 1 : -1)];
+                        if (lane == 31) right = a0[v + (x + 4 == N ? 4 - N : 4)];
+                    }
+                    dx[0] = c.y - left;
+                    dx[1] = c.z - c.x;
+                    dx[2] = c.w - c.y;
+                    dx[3] = right - c.z;
+                    const float4 p = *reinterpret_cast<const float4*>(a1 + yp);
+                    const float4 m = *reinterpret_cast<const float4*>(a1 + ym);
+                    dy[0] = p.x - m.x;
+                    dy[1] = p.y - m.y;
+                    dy[2] = p.z - m.z;
+                    dy[3] = p.w - m.w;
+                    const float4 zu = *reinterpret_cast<const float4*>(a2 + v + zp);
+                    const float4 zd = *reinterpret_cast<const float4*>(a2 + v + zm);
+                    dz[0] = zu.x - zd.x;
+                    dz[1] = zu.y - zd.y;
+                    dz[2] = zu.z - zd.z;
+                    dz[3] = zu.w - zd.w;
+                };
+                T fx[4], fy[4], fz[4], lx[4], ly[4], lz[4];
+                diffs(F_c0, F_c1, F_c2, fx, fy, fz);
+                if (!INCR) diffs(L_c0, L_c1, L_c2, lx, ly, lz);
+                T o[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    T q = fx[r] + fy[r];
+                    if (!INCR) q -= (lx[r] + ly[r]) * inv_rho;
+                    q += fz[r];
+                    if (!INCR) q -= lz[r] * inv_rho;
+                    o[r] = -q * half_n;
+                }
+                stage[(x >> 1) * S + l] = V{o[0], o[1]};  // z_m = r_{2m} + i r_{2m+1}
+                stage[((x >> 1) + 1) * S + l] = V{o[2], o[3]};
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
+                const int l = idx >> X::LOGN;
+                const int x = idx & (N - 1);
+                const int y = y0 + l;
+                const Idx v = (Idx)line0 * N + idx;
+                const Idx xp = v + (x + 1 == N ? 1 - N : 1), xm = v + (x == 0 ? N - 1 : -1);
+                const Idx yp = v + (y + 1 == N ? (1 - N) * sn : sn), ym = v + (y == 0 ? (N - 1) * sn : -sn);
+                T q = (F_c0[xp] - F_c0[xm]) + (F_c1[yp] - F_c1[ym]);
+                if (!INCR) q -= ((L_c0[xp] - L_c0[xm]) + (L_c1[yp] - L_c1[ym])) * inv_rho;
+                q += F_c2[v + zp] - F_c2[v + zm];
+                if (!INCR) q -= (L_c2[v + zp] - L_c2[v + zm]) * inv_rho;
+                stage_r[((x >> 1) * S + l) * 2 + (x & 1)] = -q * half_n;  // z_m = r_{2m} + i r_{2m+1}
+            }
         }
         __syncthreads();
         V xr[8];

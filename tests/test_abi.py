@@ -72,6 +72,16 @@ def test_create_rejects_bad_options(lib):
     assert rc == rve.RVE_E_INVALID_ARG
 
 
+def test_create_in_rejects_null_and_misaligned_workspaces_without_device(lib):
+    """rve_create_in checks the caller's buffer before touching the device: NULL and
+    pointers off the 256-byte boundary the field layout assumes are rejected."""
+    o = rve.rve_default_options()
+    nbytes = rve.rve_workspace_bytes(3, 16, 0, o)
+    for ptr in (0, 16, 4096 + 8):
+        rc, h = rve.rve_create_in(3, 16, 0, o, None, ptr, nbytes)
+        assert rc == rve.RVE_E_INVALID_ARG and not h.value
+
+
 def test_null_handle_is_rejected(lib):
     assert lib.rve_solve(None, None, ctypes.c_double(1.0), ctypes.c_double(1.0), None) == rve.RVE_E_INVALID_ARG
     assert lib.rve_stress(None, None) == rve.RVE_E_INVALID_ARG
