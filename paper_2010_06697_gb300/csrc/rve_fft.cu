@@ -765,6 +765,36 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
         const T* stage_r = reinterpret_cast<const T*>(stage);
         TO* O_c = Out + (long long)c * Vn;
         const TO* I_c = In + (long long)c * Vn;
+        if constexpr (std::is_same<T, float>::value) {
+            // four consecutive x per thread (two staged complex values): one float4 store,
+            // or for the increment two double2 read-modify-writes and a float4 store of the
+            // increment (fields are 256-byte aligned, x and N multiples of 4)
+            for (int idx = threadIdx.x; idx < LPB * N / 4; idx += blockDim.x) {
+                const int e = idx * 4;
+                const int l = e >> X::LOGN;
+                const int xi = e & (N - 1);
+                const int line = line0 + l;
+                if (line < nlines) {
+                    const V a = stage[(xi >> 1) * S + l];
+                    const V b = stage[((xi >> 1) + 1) * S + l];
+                    const long long o = (long long)line * N + xi;
+                    if constexpr (INCR) {
+                        static_assert(std::is_same<TO, double>::value, "increment accumulates in double");
+                        const double2 i0 = *reinterpret_cast<const double2*>(I_c + o);
+                        const double2 i1 = *reinterpret_cast<const double2*>(I_c + o + 2);
+                        *reinterpret_cast<double2*>(O_c + o) = double2{i0.x + (TO)a.x, i0.y + (TO)a.y};
+                        *reinterpret_cast<double2*>(O_c + o + 2) = double2{i1.x + (TO)b.x, i1.y + (TO)b.y};
+                        *reinterpret_cast<float4*>(DUout + (long long)c * Vn + o) = float4{a.x, a.y, b.x, b.y};
+                    } else if constexpr (std::is_same<TO, float>::value) {
+                        *reinterpret_cast<float4*>(O_c + o) = float4{a.x, a.y, b.x, b.y};
+                    } else {
+                        *reinterpret_cast<double2*>(O_c + o) = double2{(TO)a.x, (TO)a.y};
+                        *reinterpret_cast<double2*>(O_c + o + 2) = double2{(TO)b.x, (TO)b.y};
+                    }
+                }
+            }
+            continue;
+        }
         for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
             const int l = idx >> X::LOGN;
             const int xi = idx & (N - 1);
