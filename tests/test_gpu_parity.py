@@ -216,6 +216,28 @@ def test_adaptive_rho_decisions_match_oracle():
 
 # ------------------------------------------------------------------ errors
 
+@pytest.mark.parametrize("nphase", [2, 5, 11])
+def test_material_phase_counts_and_validation(nphase):
+    """rve_set_material counts the voxels of each phase (mu_ref = volume average of mu,
+    reported in the solve info) and rejects a phase id >= nphase wherever it sits: first
+    voxel, inside or at the edge of an 8-voxel word, ragged tail."""
+    n, d = 18, 3  # V = 5832: a multiple of 8; the 2D case below has V = 324 = 8*40 + 4
+    for dim, nn in ((d, n), (2, n)):
+        V = nn ** dim
+        ph = (synth.splitmix64(3, 77, V) % np.uint64(nphase)).astype(np.uint8).reshape((nn,) * dim)
+        par = np.array([[1.0 + p, 2.0] for p in range(nphase)])
+        s = rve.Rve(dim, nn, "neohookean", "fp64", max_iter=1)
+        s.set_material(ph, par)
+        info = s.solve(np.diag([1.01, 1.0, 1.0]), 10.0, 1e-30)
+        mu = par[ph.ravel(), 0]
+        assert abs(info.mu_ref - mu.mean()) <= 1e-14 * mu.mean()
+        for idx in (0, 5, 7, 8, V // 2 + 3, V - 4, V - 1):
+            bad = ph.copy()
+            bad.flat[idx] = nphase + idx % 3
+            assert rve.rve_set_material(s.h, bad, par) == rve.RVE_E_INVALID_ARG, idx
+        s.close()
+
+
 def test_error_paths():
     s = rve.Rve(2, 16, "neohookean", "fp64", max_iter=10)
     rc, _ = rve.rve_solve(s.h, np.eye(3), 10.0, 1e-8)
