@@ -752,6 +752,14 @@ void rve_destroy(rve_t h) {
     delete h;
 }
 
+// out[i] = (float)in[i] (round to nearest, as the host conversion): the float copy of the
+// reference directors of a handle that holds both precisions, made from the double copy
+// already on the device instead of a host conversion and a second upload.
+__global__ void k_narrow(const double* __restrict__ in, float* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
 // Voxel count of each phase id; false if some voxel's id is >= nphase.  For up to 8
 // phases it compares 8 voxels at a time (SWAR: a byte of x = w ^ (p in every byte) is zero
 // exactly where the voxel has phase p; the per-byte nonzero test (x | ((x & 0x7f..) +
@@ -845,7 +853,7 @@ int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* pa
             const double nn = a * a + b * b + c * c;
             if (!isfinite(nn) || fabs(nn - 1.0) > 1e-6) return RVE_E_INVALID_ARG;
         }
-        if (h->L.n0_32) {
+        if (h->L.n0_32 && !h->L.n0_64) {  // float-only handle: narrowed here, else on the device
             n0f.resize(3 * (size_t)V);
             for (size_t i = 0; i < n0f.size(); ++i) n0f[i] = (float)n0[i];
         }
@@ -864,8 +872,14 @@ int rve_set_material(rve_t h, const uint8_t* phase, int nphase, const double* pa
                        h->stream));
     if (lce && h->L.n0_64)
         CK(cudaMemcpyAsync((void*)h->L.n0_64, n0, 3 * (size_t)h->V * 8, cudaMemcpyHostToDevice, h->stream));
-    if (lce && h->L.n0_32)
+    if (lce && h->L.n0_32 && h->L.n0_64) {
+        const long long n3 = 3 * h->V;
+        const int blocks = (int)std::min<long long>((n3 + 255) / 256, 152LL * 8);
+        k_narrow<<<blocks, 256, 0, h->stream>>>(h->L.n0_64, (float*)h->L.n0_32, n3);
+        CK(cudaGetLastError());
+    } else if (lce && h->L.n0_32) {
         CK(cudaMemcpyAsync((void*)h->L.n0_32, n0f.data(), n0f.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    }
     CK(cudaStreamSynchronize(h->stream));
     h->L.nparam = admm::kMaxParam;
     if (lce) {  // the kernels of the incompressible network are their own instances
