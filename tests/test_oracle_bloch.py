@@ -128,6 +128,27 @@ def test_step2_norm_root_is_unique_and_below_pole():
     assert np.all(np.diff(norms) > 0)
 
 
+@pytest.mark.parametrize("model", ["linear", "neohookean"])
+@pytest.mark.parametrize("d,n,k", [(2, 8, (2, 3)), (2, 6, (-3, 2)), (3, 4, (2, 3, 5))])
+def test_homogeneous_beta_closed_form(model, d, n, k):
+    """Homogeneous isotropic cell at F = I (where the neo-Hookean tangent equals the linear
+    one with the same mu, lambda): a Bloch wave p = e exp(2 pi i m.x) has D p = i e (x) s(m),
+    and <Dp, L Dp> = e^H K(s) e with the acoustic tensor K = mu |s|^2 I + (mu + lam) s s^T,
+    eigenvalues mu |s|^2 and (2 mu + lam) |s|^2.  So beta = mu min_m |s(m)|^2, with
+    s_j(m) = N sin(2 pi (m_j + 1/k_j) / N); no dense matrix, no FFT."""
+    mu, lam = 1.3, 0.7
+    ph = np.zeros((n,) * d, np.uint8)
+    F = np.broadcast_to(np.eye(d).reshape((d, d) + (1,) * d), (d, d) + (n,) * d).copy()
+    L = bloch.tangent_field(model, ph, np.array([[mu, lam]]), F)
+    m = np.arange(n)
+    s2 = [(n * np.sin(2.0 * np.pi * (m + 1.0 / kj) / n)) ** 2 for kj in k]
+    beta = mu * sum(float(np.min(q)) for q in s2)  # |s|^2 separates over the directions
+    r = bloch.bloch_solve(L, start_field(n, d, 4), k, 2.0 * beta + 5.0, 1e-11, 20000, mu)
+    assert r["converged"]
+    np.testing.assert_allclose(r["sigma"], beta, rtol=1e-9)
+    np.testing.assert_allclose(r["rayleigh"], beta, rtol=1e-9)
+
+
 # ------------------------------------------------------------------ the pins bite
 
 _orig_symbols = bloch.bloch_symbols
