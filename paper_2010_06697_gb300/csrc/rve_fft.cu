@@ -552,7 +552,9 @@ __device__ __forceinline__ void col_fft(V (&x)[8], V* __restrict__ buf, const V*
 // xfwd_tile and xinv_tile for 3D grids of N in {128, 256, 512}: the half-length
 // transforms (H = N/2) of the block's 4096/N lines run through col_fft with the
 // lines as columns; staging, the stencil and the real-to-complex split are those of
-// the general kernels, in shared buffers padded to a stride of 4096/N + 1 values.
+// the general kernels (same arithmetic per element; the float instances move four x
+// per thread with vector loads and stores), in shared buffers padded to a stride of
+// 4096/N + 1 values.
 template <int N>
 struct XPlan {
     static constexpr int H = N / 2;
