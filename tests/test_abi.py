@@ -92,3 +92,73 @@ def test_null_handle_is_rejected(lib):
 def test_strerror(lib):
     for c in range(-8, 1):
         assert len(rve.rve_strerror(c)) > 0
+
+
+# ------------------------------------------------------------------ binding vs header
+
+_CTYPE = {"int": ctypes.c_int, "double": ctypes.c_double, "long long": ctypes.c_longlong,
+          "size_t": ctypes.c_size_t, "unsigned": ctypes.c_uint, "float": ctypes.c_float}
+
+
+def _header_text():
+    text = "".join(open(h).read() for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
+    return re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+
+
+def _prototypes():
+    """name -> list of parameter declarations, from the header's function prototypes."""
+    out = {}
+    for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(rve_\w+)\s*\(([^)]*)\)\s*;", _header_text(), flags=re.M):
+        params = [p.strip() for p in m.group(2).replace("\n", " ").split(",") if p.strip()]
+        if params == ["void"]:
+            params = []
+        out[m.group(1)] = params
+    return out
+
+
+def _struct_fields(name):
+    m = re.search(r"typedef\s+struct\s+" + name + r"\s*\{(.*?)\}\s*" + name + r"\s*;", _header_text(), flags=re.S)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        mm = re.fullmatch(r"(.+?)\s+(\w+(?:\s*,\s*\w+)*)", decl)  # "double r_p, r_d" declares two
+        fields += [(f.strip(), mm.group(1)) for f in mm.group(2).split(",")]
+    return fields
+
+
+def _same_ctype(a, b):
+    # ctypes aliases c_longlong to c_long where both are 64-bit: compare size and kind
+    floating = (ctypes.c_float, ctypes.c_double)
+    return ctypes.sizeof(a) == ctypes.sizeof(b) and (a in floating) == (b in floating)
+
+
+def test_binding_signatures_match_the_header():
+    """Every entry point the binding declares has as many arguments as the header's
+    prototype, and scalar arguments have the header's C type (pointers and handles are
+    checked by count only)."""
+    protos = _prototypes()
+    for name, (_, args) in rve.SIGNATURES.items():
+        assert name in protos, name
+        params = protos[name]
+        assert len(args) == len(params), (name, params)
+        for a, p in zip(args, params):
+            if "*" in p or "[" in p or p.split()[0] in ("rve_t", "rve_batch_t", "rve_server_t"):
+                continue
+            ctype = " ".join(p.split()[:-1]).replace("const ", "")
+            assert ctype in _CTYPE, (name, p)
+            assert _same_ctype(a, _CTYPE[ctype]), (name, p, a)
+
+
+@pytest.mark.parametrize("cname,pyname", [("rve_options", "rve_options"), ("rve_solve_info", "rve_solve_info"),
+                                          ("rve_bloch_info", "rve_bloch_info")])
+def test_binding_structs_match_the_header(cname, pyname):
+    """The ctypes mirrors of the header's structs have the same fields, in the same order,
+    with the same C types (so the layout the library reads is the one the binding writes)."""
+    fields = _struct_fields(cname)
+    py = getattr(rve, pyname)._fields_
+    assert [f for f, _ in fields] == [f for f, _ in py], cname
+    for (f, ctype), (_, pt) in zip(fields, py):
+        assert _same_ctype(pt, _CTYPE[ctype]), (cname, f, ctype, pt)
