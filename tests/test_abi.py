@@ -162,3 +162,33 @@ def test_binding_structs_match_the_header(cname, pyname):
     assert [f for f, _ in fields] == [f for f, _ in py], cname
     for (f, ctype), (_, pt) in zip(fields, py):
         assert _same_ctype(pt, _CTYPE[ctype]), (cname, f, ctype, pt)
+
+
+def _header_constants():
+    """RVE_* values from the header's #defines and enumerators (explicit values only)."""
+    text = _header_text()
+    out = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(RVE_\w+)\s+\(?(-?\d+)\)?", text)}
+    for body in re.findall(r"enum\s+\w+\s*\{(.*?)\}", text, flags=re.S):
+        for m in re.finditer(r"(RVE_\w+)\s*=\s*(-?\d+)", body):
+            out[m.group(1)] = int(m.group(2))
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """Status codes and enumerators the binding names have the header's values."""
+    consts = _header_constants()
+    assert {"RVE_OK", "RVE_E_INVALID_ARG", "RVE_NEOHOOKE", "RVE_MIXED", "RVE_FIELD_N"} <= set(consts)
+    shared = [n for n in consts if hasattr(rve, n)]
+    assert len(shared) >= 20
+    for n in shared:
+        assert getattr(rve, n) == consts[n], n
+
+
+def test_kernel_class_names_follow_the_header_enum():
+    """rve_kernel_times' arrays are indexed by enum rve_kernel_class; the binding labels
+    index i with the enumerator's name."""
+    consts = _header_constants()
+    kc = {n[len("RVE_KCLASS_"):].lower(): v for n, v in consts.items() if n.startswith("RVE_KCLASS_") and n != "RVE_KCLASS_COUNT"}
+    assert len(kc) == consts["RVE_KCLASS_COUNT"] == len(rve.KCLASS_NAMES)
+    for name, i in kc.items():
+        assert rve.KCLASS_NAMES[i] == name, (i, name)
