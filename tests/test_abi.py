@@ -196,3 +196,22 @@ def test_kernel_class_names_follow_the_header_enum():
     assert len(kc) == consts["RVE_KCLASS_COUNT"] == len(rve.KCLASS_NAMES)
     for name, i in kc.items():
         assert rve.KCLASS_NAMES[i] == name, (i, name)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("precision", 3), ("precision", -1), ("rho_policy", 2), ("lambda0", 2), ("max_iter", -1),
+    ("newton_max", 1001), ("newton_tol", -1e-3), ("newton_tol", float("nan")), ("rho_kappa", 1.0),
+    ("rho_tau", 0.5), ("rho_min", -1.0), ("mu_ref", -1.0), ("mixed_switch", -1.0), ("check_every", 4097),
+    ("local_ratio", -0.1), ("local_ratio", float("inf")), ("local_fraction", 1.5), ("local_fraction", float("nan"))])
+def test_create_rejects_each_invalid_option_without_device(lib, field, value):
+    o = rve.rve_default_options()
+    setattr(o, field, value)
+    rc, h = rve.rve_create(3, 16, 0, o)
+    assert rc == rve.RVE_E_INVALID_ARG and not h.value
+
+
+@pytest.mark.parametrize("dim,n,model", [(3, 10, 0), (3, 2, 0), (3, 1024, 0), (2, 9, 0), (2, 16, 2), (3, 14, 1)])
+def test_create_rejects_grids_and_models_outside_the_contract(lib, dim, n, model):
+    """N even of the form 2^a 3^b in [4, 512]; the LCE only in 3D."""
+    rc, h = rve.rve_create(dim, n, model)
+    assert rc == rve.RVE_E_INVALID_ARG and not h.value
