@@ -59,6 +59,21 @@ def test_workspace_bytes(lib):
         assert rve.rve_workspace_bytes(bad[0], bad[1], 0, None) == 0
 
 
+@pytest.mark.parametrize("precision,s", [("fp64", 8), ("mixed", 12), ("fp32", 4)])
+def test_workspace_layout_per_voxel(lib, precision, s):
+    """The HBM layout: 33 field values per voxel (F twice, Lambda, u~ twice) in each precision
+    the handle holds, one phase byte, and under 1 MB of tables, control block and residual
+    history at 128^3 (default max_iter); the LCE adds 21 values per voxel (directors twice,
+    reference directors, the time step's starting F and n)."""
+    V = 128 ** 3
+    o = rve.rve_default_options()
+    o.precision = rve.PRECISIONS[precision]
+    b = rve.rve_workspace_bytes(3, 128, rve.RVE_NEOHOOKE, o)
+    assert 33 * s * V + V <= b <= 33 * s * V + V + (1 << 20)
+    bl = rve.rve_workspace_bytes(3, 128, rve.RVE_LCE, o)
+    assert bl - b == 21 * s * V
+
+
 @pytest.mark.parametrize("dim,n,model", [(4, 16, 0), (3, 7, 0), (3, 20, 0), (2, 16, 9)])
 def test_create_rejects_bad_shapes_without_device(lib, dim, n, model):
     rc, h = rve.rve_create(dim, n, model)
