@@ -230,3 +230,21 @@ def test_create_rejects_grids_and_models_outside_the_contract(lib, dim, n, model
     """N even of the form 2^a 3^b in [4, 512]; the LCE only in 3D."""
     rc, h = rve.rve_create(dim, n, model)
     assert rc == rve.RVE_E_INVALID_ARG and not h.value
+
+
+def test_batch_and_server_argument_checks_without_device(lib):
+    """Batches need at least one non-NULL handle; servers a non-zero memory budget and
+    valid options: checked before any device work."""
+    rc, b = rve.rve_batch_create([])
+    assert rc == rve.RVE_E_INVALID_ARG and not b.value
+    rc, b = rve.rve_batch_create([None, None])
+    assert rc == rve.RVE_E_INVALID_ARG and not b.value
+    h = ctypes.c_void_p()
+    assert lib.rve_server_create(ctypes.byref(h), 0, None, None) == rve.RVE_E_INVALID_ARG and not h.value
+    o = rve.rve_default_options()
+    o.check_every = 0
+    assert lib.rve_server_create(ctypes.byref(h), 1 << 30, ctypes.byref(o), None) == rve.RVE_E_INVALID_ARG
+    assert not h.value
+    assert lib.rve_batch_solve(None, None, None, ctypes.c_double(1e-8), None) == rve.RVE_E_INVALID_ARG
+    lib.rve_batch_destroy(None)
+    lib.rve_server_destroy(None)
