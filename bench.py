@@ -59,7 +59,7 @@ def bytes_per_voxel(cls: str, s: int, d: int = 3) -> float:
 # (profiles/), keyed by (kernel class, precision); absent = not captured since the
 # kernel last changed
 TRAFFIC = {("local", "fp32"): 220703232 + 120778240, ("local_r", "fp64"): 421989120 + 358003456,
-           ("xfwd", "fp32"): 151043840 + 11952640, ("solve", "fp32"): 25196800}
+           ("xfwd", "fp32"): 151019264 + 9842176, ("xinv", "fp32"): 25181952, ("solve", "fp32"): 25196800}
 # FP32 flops (fadd + fmul + 2 ffma, ncu instruction counters) per launch of the float local
 # step, averaged over all 97 of its launches in one solve of the 128^3 inclusion cell,
 # including the launches that exit at once after the stop flag (profiles/)

@@ -1,5 +1,6 @@
-"""bench.py's multi-rank aggregation with two gloo ranks on the CPU: each rank solves its
-own RVE (replicas, weak scaling); the job time is the slowest rank's and the work the sum."""
+"""bench.py's host logic on the CPU: the multi-rank aggregation with two gloo ranks (each
+rank solves its own RVE: replicas, weak scaling; the job time is the slowest rank's and the
+work the sum), and the algorithmic byte model behind the roofline figures."""
 import os
 import socket
 import sys
@@ -42,3 +43,20 @@ def test_single_rank_is_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.combine_ranks(12.5, 7.0) == (12.5, 7.0)
+
+
+def test_byte_model_matches_the_documented_per_voxel_figures():
+    """bench.py's algorithmic bytes per voxel and launch (the roofline numerators): one
+    iteration of the 3D path is 87 s + 1 bytes (s = 4 or 8: local 42 s + 1, x-forward 21 s,
+    four FFT passes 6 s each), the double-word polish local step 373 B, its increment x
+    passes 48 and 60 B."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for s in (4, 8):
+        it = sum(bench.bytes_per_voxel(c, s) for c in ("local", "xfwd", "fwd_y", "solve", "inv_y", "xinv"))
+        assert it == 87 * s + 1
+        assert bench.bytes_per_voxel("local", s) == 42 * s + 1 and bench.bytes_per_voxel("xfwd", s) == 21 * s
+    assert bench.bytes_per_voxel("local_r", 0) == 373
+    assert bench.bytes_per_voxel("xfwd_incr", 0) == 48 and bench.bytes_per_voxel("xinv_incr", 0) == 60
+    # 2D: d = 2 in the same formulas
+    assert bench.bytes_per_voxel("local", 8, d=2) == (4 + 16) * 8 + 1
