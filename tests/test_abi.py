@@ -248,3 +248,14 @@ def test_batch_and_server_argument_checks_without_device(lib):
     assert lib.rve_batch_solve(None, None, None, ctypes.c_double(1e-8), None) == rve.RVE_E_INVALID_ARG
     lib.rve_batch_destroy(None)
     lib.rve_server_destroy(None)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No fallback: without the built library every entry point raises instead of computing
+    anything another way."""
+    monkeypatch.setattr(rve, "LIB_PATH", os.path.join(ROOT, "does-not-exist", "librve.so"))
+    monkeypatch.setattr(rve, "_lib", None)
+    with pytest.raises(RuntimeError):
+        rve.rve_default_options()
+    with pytest.raises(RuntimeError):
+        rve.Rve(3, 16, use_torch=False)
