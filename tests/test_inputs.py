@@ -76,3 +76,18 @@ def test_strain_batch_and_serving_recipes():
         assert abs(kinds.count(k) / len(kinds) - p) < 0.03
     logn = np.log([r["n"] for r in reqs])
     assert abs(np.mean(logn) - 0.5 * (np.log(32) + np.log(256))) < 0.05   # log-uniform sizes
+
+
+def test_stored_oracle_solve_matches_todays_inputs():
+    """The stored 128^3 oracle solve was made from the inclusion recipe; the recipe still
+    produces the same cell (its inclusion fraction and volume-average shear modulus), so the
+    GPU test that compares against it compares like with like."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "inclusions128.json")))
+    rcp = g["recipe"]
+    ph = synth.inclusion_phase(rcp["n"], rcp["dim"], rcp["seed"])
+    assert ph.mean() == g["phase_fraction"]
+    mu = np.asarray(rcp["mu"])[ph.ravel()]
+    assert abs(mu.mean() - g["mu_ref"]) <= 1e-12 * g["mu_ref"]
+    assert g["converged"] and np.asarray(g["stress"]).shape == (3, 3)
