@@ -123,7 +123,7 @@ def _to_field(Tv: np.ndarray, grid_shape) -> np.ndarray:
     return Tv.transpose(1, 2, 0).reshape((d, d) + tuple(grid_shape))
 
 
-def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, small_step=1e-7, grad_tol=0.0,
+def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, small_step=1e-7,
                  return_conv=False):
     """Step 1 at every voxel: minimise phi(F) = W(F) - Lam:F + rho/2 |F - G|^2.
 
@@ -132,23 +132,19 @@ def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, smal
     is used (the paper's local method).  Backtracking halves the step until
     J = det F > 0 and the Armijo decrease holds (steps below ``small_step`` are
     accepted on J > 0 alone, since phi's rounding noise exceeds the decrease there).
-    A voxel stops after a full step with max |step| <= step_tol.
-
-    grad_tol > 0 (inexact local step, Section 2.1 "Approximate solution of the
-    local problem"): the gradient is evaluated at the start of every Newton
-    iteration and a voxel also stops, without a further step, once its Frobenius
-    norm |grad phi| <= grad_tol.  A voxel that met the step test is then stopped at
-    the next evaluation, so that every voxel ends on an evaluated gradient.
+    A voxel stops after a full step with max |step| <= step_tol (its pointwise
+    convergence test); ``cap`` bounds the Newton iterations of this call, so that
+    calling it again from the returned F continues the same iteration (the rounds
+    of local_step_rounds).
 
     All arrays are per voxel: F0, Lam, G of shape (V, d, d).  Returns (F, iters), and
-    with return_conv=True also the mask of voxels that met a stopping test.
+    with return_conv=True also the mask of voxels that met the convergence test.
     """
     V, d, _ = F0.shape
     n2 = d * d
     F = F0.copy()
     iters = np.zeros(V, dtype=np.int64)
     active = np.ones(V, dtype=bool)
-    small = np.zeros(V, dtype=bool)
     conv = np.zeros(V, dtype=bool)
 
     def phi(sub, Fs, Lam_s, G_s):
@@ -164,15 +160,6 @@ def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, smal
         Lam_s = Lam[idx]
         G_s = G[idx]
         g = sub.P(Fa) - Lam_s + rho * (Fa - G_s)
-        if grad_tol > 0.0:
-            stop = small[idx] | (np.sqrt(np.einsum("vij,vij->v", g, g)) <= grad_tol)
-            active[idx[stop]] = False
-            conv[idx[stop]] = True
-            keep = ~stop
-            idx, Fa, Lam_s, G_s, g = idx[keep], Fa[keep], Lam_s[keep], G_s[keep], g[keep]
-            if idx.size == 0:
-                break
-            sub = mat.subset(idx)
         keep = iters[idx] < cap
         if not np.all(keep):
             active[idx[~keep]] = False
@@ -208,25 +195,40 @@ def local_newton(mat, F0, Lam, G, rho, step_tol=1e-10, cap=50, armijo=1e-4, smal
         F[idx] = Fa + t[:, None, None] * delta
         iters[idx] += 1
         done = accepted & (t == 1.0) & (size <= step_tol)
-        if grad_tol > 0.0:
-            small[idx[done]] = True
-        else:
-            active[idx[done]] = False
-            conv[idx[done]] = True
+        active[idx[done]] = False
+        conv[idx[done]] = True
     return (F, iters, conv) if return_conv else (F, iters)
 
 
-def fraction_cap(iters, conv, fraction, cap, cap_max, bins=16):
-    """Section 4.2's first strategy (proceed once a fraction of the points converged,
-    checked every two local iterations), with one pass of lag: the next pass's
-    Newton cap is the smallest even count 2b (b <= bins) by which at least
-    fraction * V voxels met their test in this pass; if fewer did, cap + 2; never
-    above cap_max."""
-    V = iters.size
-    b = np.minimum(np.maximum(iters[conv] + 1, 2) // 2, bins) - 1
-    cum = np.cumsum(np.bincount(b, minlength=bins)[:bins])
-    hit = np.nonzero(cum >= fraction * V)[0]
-    return min(2 * (int(hit[0]) + 1), cap_max) if hit.size else min(cap + 2, cap_max)
+def local_step_rounds(run, V, cap, round_len, enough, check_first):
+    """Step 1 solved approximately in the manner of Algorithm 1's inner loop and of
+    Section 4.2: the local iterations run in rounds of ``round_len`` iterations at
+    every point that has not yet met its pointwise convergence test, and after each
+    round a global check ``enough(conv)`` decides whether to proceed to Step 2.
+
+      run(idx, k)  advances the local iteration at voxels idx by up to k iterations
+                   from their current state and returns (iters_done, conv) for idx;
+      enough(conv) the global check (r_l <= f r_d, or the converged fraction >= p);
+      check_first  evaluate the check once before the first round (the while loop of
+                   Algorithm 1 tests r_l before iterating).
+
+    Stops at the check, when every point has converged, or after ``cap`` local
+    iterations.  Returns (iters, conv, rounds) per voxel / in total."""
+    iters = np.zeros(V, dtype=np.int64)
+    conv = np.zeros(V, dtype=bool)
+    rounds = 0
+    if check_first and enough(conv):
+        return iters, conv, rounds
+    while not conv.all() and int(iters.max(initial=0)) < cap:
+        idx = np.nonzero(~conv)[0]
+        k = min(round_len, cap - int(iters.max(initial=0)))
+        it, c = run(idx, k)
+        iters[idx] += it
+        conv[idx] = c
+        rounds += 1
+        if enough(conv):
+            break
+    return iters, conv, rounds
 
 
 def local_residual(mat, F, Lam, G, rho, mu_ref, n=None, force=None, Fprev=None, nprev=None):
@@ -289,7 +291,7 @@ def retract(n, a, b, t1, t2):
 
 
 def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60, armijo=1e-4, small_step=1e-7,
-                     grad_tol=0.0, Fprev=None, nprev=None):
+                     Fprev=None, nprev=None, return_conv=False):
     """Step 1 (eqs. eq and kin with the Frank gradient treated explicitly, eq. kin2) for
     the LCE at every voxel: minimise over F and the unit director n
 
@@ -298,12 +300,14 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
     force: the explicit Frank force from the previous director field (frank_force).  Newton on the 11 unknowns (F, t) with n = normalise(n + t1 a + t2 b),
     (a, b) a basis of the tangent plane at the current n: the reduced Hessian adds the
     sphere's curvature term -(n . phi_n) I, plus a shift 1e-6 mu I on that block.  Backtracking keeps J > 0 and the Armijo
-    decrease; steepest descent when Newton's direction does not descend.  grad_tol:
-    the inexact stop of local_newton on the norm of the 11-component gradient.
+    decrease; steepest descent when Newton's direction does not descend.  A voxel
+    stops after a full step with max |step| <= step_tol; ``cap`` bounds this call's
+    iterations (another call from the returned state continues the iteration).
     Fprev, nprev (V,3,3), (V,3): the previous time step's fields; with the material's
     dissipation weights cF = nu_F/dt, cn = nu_n/dt the objective gains Section 5.1's
     dt D((F - Fprev)/dt, (n - nprev)/dt) = cF/2 |F - Fprev|^2 + cn/2 |n - nprev|^2.
-    F0, Lam, G (V,3,3); n_init, force (V,3).  Returns (F, n, iters)."""
+    F0, Lam, G (V,3,3); n_init, force (V,3).  Returns (F, n, iters), and with
+    return_conv=True also the mask of voxels that met the convergence test."""
     if Fprev is None:
         Fprev = F0
     if nprev is None:
@@ -313,7 +317,7 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
     n = n_init.copy()
     iters = np.zeros(V, dtype=np.int64)
     active = np.ones(V, dtype=bool)
-    small = np.zeros(V, dtype=bool)
+    conv = np.zeros(V, dtype=bool)
 
     def phi(sub, Fs, ns, Lam_s, G_s, f_s, Fp, np_):
         dF, dn = Fs - Fp, ns - np_
@@ -322,32 +326,19 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
                 + 0.5 * sub.cF * np.einsum("vij,vij->v", dF, dF) + 0.5 * sub.cn * np.sum(dn * dn, axis=1))
 
     for _ in range(cap + 1):
-        idx = np.nonzero(active)[0]
+        idx = np.nonzero(active & (iters < cap))[0]
         if idx.size == 0:
             break
-        for _pass in range(2):
-            sub = mat.subset(idx)
-            Fa, na = F[idx], n[idx]
-            Lam_s, G_s, f_s = Lam[idx], G[idx], force[idx]
-            Fp_s, np_s = Fprev[idx], nprev[idx]
-            P, Wn, WFF, WFn, Wnn = sub.derivatives(Fa, na)
-            gF = P - Lam_s + rho * (Fa - G_s) + sub.cF[:, None, None] * (Fa - Fp_s)
-            gn = Wn - f_s + sub.cn[:, None] * (na - np_s)
-            a, b = tangent_basis(na)
-            E = np.stack([a, b], axis=2)                                   # (v, 3, 2)
-            gt = np.einsum("vk,vka->va", gn, E)
-            stop = iters[idx] >= cap
-            if grad_tol > 0.0:
-                gnorm = np.sqrt(np.einsum("vij,vij->v", gF, gF) + np.sum(gt * gt, axis=1))
-                stop = stop | small[idx] | (gnorm <= grad_tol)
-            if not np.any(stop):
-                break
-            active[idx[stop]] = False
-            idx = idx[~stop]
-            if idx.size == 0:
-                break
-        if idx.size == 0:
-            break
+        sub = mat.subset(idx)
+        Fa, na = F[idx], n[idx]
+        Lam_s, G_s, f_s = Lam[idx], G[idx], force[idx]
+        Fp_s, np_s = Fprev[idx], nprev[idx]
+        P, Wn, WFF, WFn, Wnn = sub.derivatives(Fa, na)
+        gF = P - Lam_s + rho * (Fa - G_s) + sub.cF[:, None, None] * (Fa - Fp_s)
+        gn = Wn - f_s + sub.cn[:, None] * (na - np_s)
+        a, b = tangent_basis(na)
+        E = np.stack([a, b], axis=2)                                       # (v, 3, 2)
+        gt = np.einsum("vk,vka->va", gn, E)
         Htt = np.einsum("vka,vkp,vpb->vab", E, Wnn, E) - np.sum(na * gn, axis=1)[:, None, None] * np.eye(2)[None]
         HFt = np.einsum("vklp,vpb->vklb", WFn, E).reshape(-1, 9, 2)
         H = np.zeros((idx.size, 11, 11))
@@ -388,11 +379,9 @@ def local_newton_lce(mat, F0, n_init, Lam, G, force, rho, step_tol=1e-10, cap=60
         n[idx] = retract(na, a, b, t * delta[:, 9], t * delta[:, 10])
         iters[idx] += 1
         done = accepted & (t == 1.0) & (size <= step_tol)
-        if grad_tol > 0.0:
-            small[idx[done]] = True
-        else:
-            active[idx[done]] = False
-    return F, n, iters
+        active[idx[done]] = False
+        conv[idx[done]] = True
+    return (F, n, iters, conv) if return_conv else (F, n, iters)
 
 
 _EPS = np.zeros((3, 3, 3))
@@ -528,7 +517,7 @@ def initial_state(mat, Fbar_d: np.ndarray, grid_shape, lambda0: str = "stress", 
 def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_ref=None,
                lambda0="stress", state=None, rho_policy="fixed", kappa=1.3, tau=10.0,
                rho_min=None, local_cap=50, step_tol=1e-10, n0=None, local_ratio=0.0, free=None,
-               local_fraction=0.0, incompressible=False):
+               local_fraction=0.0, incompressible=False, local_round=1):
     """Run the ADMM iteration (Steps 1-4) until r_p <= tol and r_d <= tol, or max_iter.
 
     phase: uint8 grid (N,)*d; params: per-phase (mu, lam); Fbar: 3x3 (the upper-left
@@ -536,12 +525,14 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
     converged, history (list of (r_p, r_d, rho_used)), rho (next rho) and the
     homogenised first Piola-Kirchhoff stress <W_F(F)> (d x d).
 
-    local_ratio = f > 0: inexact local steps (Section 2.1, "Approximate solution of
-    the local problem", and Section 4.2's second strategy, r_l <= f r_d): each
-    voxel's Newton stops once |grad phi| <= f mu_ref r_d, with r_d of the check two
-    iterations back (the last one complete when a fused device pass starts its
-    local step); the first two iterations solve exactly.  A pointwise bound implies
-    the L2 bound r_l <= f r_d.  out["local_residual"] lists r_l per iteration.
+    local_ratio = f > 0: approximate local steps with r_l <= f r_d (Section 2.1,
+    "Approximate solution of the local problem"; Algorithm 1's inner loop; Section
+    4.2's second strategy).  Step 1 of iteration i+1 runs Newton in rounds of
+    ``local_round`` iterations at the points not yet converged and stops once the
+    unit-cell L2 local residual r_l (local_residual) is <= f times the r_d of the
+    latest check (Step 4 of iteration i); r_l is also tested before the first round.
+    The first iteration has no r_d yet and solves exactly.  out["local_residual"]
+    lists r_l after every Step 1, out["local_rounds"] the rounds each one took.
 
     free: optional (3, 3) boolean mask of components of <F> left free (mixed
     macroscopic control, Section 2.3; Section 5.3's UNI, PE and EB protocols): they
@@ -550,12 +541,15 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
     multiplier update and <W_F(F)>_free -> 0 at convergence.  Fbar gives their
     starting values; out["Fbar"] holds the final macroscopic gradient (3 x 3).
 
-    local_fraction = p > 0 (elastic laws): fraction-converged local steps with the
-    Newton cap of fraction_cap, set from each pass's counts for the next pass (the
-    first two passes use local_cap); out["newton_caps"] lists the cap of every pass.
+    local_fraction = p > 0 (elastic laws): Section 4.2's first strategy.  Step 1 runs
+    Newton in rounds of two iterations at the points not yet converged and, after
+    each round, proceeds to Step 2 once at least p V points have met their pointwise
+    test (a full Newton step <= step_tol).  out["local_rounds"] lists the rounds of
+    every Step 1, out["local_converged"] the converged count after it.
 
     incompressible (model "lce"): the network of Section 5.1 with det F = 1 enforced in
-    Step 1 by a multiplier (local_newton_lce_inc); out["stress"] is then <Lambda>,
+    Step 1 by a multiplier (local_newton_lce_inc), whose local problem is always solved
+    to the step tolerance (local_ratio does not apply); out["stress"] is then <Lambda>,
     which equals <W_F - p cof F> (+ the viscous part) once the iteration has converged.
     """
     phase = np.asarray(phase)
@@ -581,33 +575,57 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
         nprev_v = nd.reshape(3, -1).T.copy()
     history = []
     local_res = []
-    caps = []
-    cap = local_cap
+    local_rounds = []
+    local_conv = []
     converged = False
     it = 0
+    V = int(np.prod(grid))
     for it in range(1, max_iter + 1):
-        # Step 1 (inexact when local_ratio > 0: tolerance from r_d two checks back)
-        gtol = local_ratio * mu_ref * history[-2][1] if (local_ratio > 0.0 and len(history) >= 2) else 0.0
         Lv, Gv = _to_voxels(Lam), _to_voxels(G)
-        if lce:
-            force = frank_force(nd, mat.kappa)
-            if incompressible:
-                Fv, nv, _ = local_newton_lce_inc(mat, _to_voxels(F), nd.reshape(3, -1).T, Lv, Gv, force, rho,
-                                                 step_tol=step_tol, cap=local_cap, Fprev=Fprev_v, nprev=nprev_v)
-            else:
-                Fv, nv, _ = local_newton_lce(mat, _to_voxels(F), nd.reshape(3, -1).T, Lv, Gv, force, rho,
-                                             step_tol=step_tol, cap=local_cap, grad_tol=gtol, Fprev=Fprev_v,
-                                             nprev=nprev_v)
-            nd = nv.T.reshape((3,) + tuple(grid))
-            local_res.append(local_residual(mat, Fv, Lv, Gv, rho, mu_ref, nv, force, Fprev_v, nprev_v)
-                             if local_ratio > 0.0 else 0.0)
+        Fv = _to_voxels(F).copy()
+        nv = nd.reshape(3, -1).T.copy() if lce else None
+        force = frank_force(nd, mat.kappa) if lce else None
+        # Step 1.  run(idx, k) advances the local Newton at voxels idx by k iterations.
+        if lce and incompressible:
+            def run(idx, k):
+                sub = mat.subset(idx)
+                Fv[idx], nv[idx], its = local_newton_lce_inc(sub, Fv[idx], nv[idx], Lv[idx], Gv[idx], force[idx],
+                                                             rho, step_tol=step_tol, cap=k, Fprev=Fprev_v[idx],
+                                                             nprev=nprev_v[idx])
+                return its, its < k
+        elif lce:
+            def run(idx, k):
+                sub = mat.subset(idx)
+                Fv[idx], nv[idx], its, c = local_newton_lce(sub, Fv[idx], nv[idx], Lv[idx], Gv[idx], force[idx], rho,
+                                                            step_tol=step_tol, cap=k, Fprev=Fprev_v[idx],
+                                                            nprev=nprev_v[idx], return_conv=True)
+                return its, c
         else:
-            Fv, iters_v, conv_v = local_newton(mat, _to_voxels(F), Lv, Gv, rho, step_tol=step_tol, cap=cap,
-                                               grad_tol=gtol, return_conv=True)
-            caps.append(cap)
-            if local_fraction > 0.0 and it >= 2:
-                cap = fraction_cap(iters_v, conv_v, local_fraction, cap, local_cap)
-            local_res.append(local_residual(mat, Fv, Lv, Gv, rho, mu_ref) if local_ratio > 0.0 else 0.0)
+            def run(idx, k):
+                Fv[idx], its, c = local_newton(mat.subset(idx), Fv[idx], Lv[idx], Gv[idx], rho, step_tol=step_tol,
+                                               cap=k, return_conv=True)
+                return its, c
+
+        def r_l():
+            if lce:
+                return local_residual(mat, Fv, Lv, Gv, rho, mu_ref, nv, force, Fprev_v, nprev_v)
+            return local_residual(mat, Fv, Lv, Gv, rho, mu_ref)
+
+        if local_ratio > 0.0 and history and not incompressible:
+            rd_latest = history[-1][1]
+            _, conv_v, rounds = local_step_rounds(run, V, local_cap, local_round,
+                                                  lambda c: r_l() <= local_ratio * rd_latest, check_first=True)
+        elif local_fraction > 0.0 and not lce:
+            _, conv_v, rounds = local_step_rounds(run, V, local_cap, 2,
+                                                  lambda c: np.count_nonzero(c) >= local_fraction * V,
+                                                  check_first=False)
+        else:
+            _, conv_v, rounds = local_step_rounds(run, V, local_cap, local_cap, lambda c: False, check_first=False)
+        local_rounds.append(rounds)
+        local_conv.append(int(np.count_nonzero(conv_v)))
+        local_res.append(r_l() if local_ratio > 0.0 else 0.0)
+        if lce:
+            nd = nv.T.reshape((3,) + tuple(grid))
         F = _to_field(Fv, grid)
         # Step 2 (with the free mean components of mixed control)
         uh, u = u_step(F, Lam, rho)
@@ -641,7 +659,8 @@ def admm_solve(phase, params, Fbar, rho, tol, max_iter, model="neohookean", mu_r
         stress = np.mean(mat.P(_to_voxels(F)), axis=0)
     out = {"F": F, "Lam": Lam, "u": u, "iters": it if max_iter > 0 else 0,
            "converged": converged, "history": history, "rho": rho,
-           "stress": stress, "mu_ref": mu_ref, "local_residual": local_res, "newton_caps": caps}
+           "stress": stress, "mu_ref": mu_ref, "local_residual": local_res, "local_rounds": local_rounds,
+           "local_converged": local_conv}
     Fb3 = np.array(np.asarray(Fbar, dtype=np.float64))
     Fb3[:d, :d] = Fbar_d
     out["Fbar"] = Fb3
