@@ -458,6 +458,150 @@ __device__ __forceinline__ int newton(const Law& m, T* F, const T* B, T rho, int
     return it;
 }
 
+// ------------------------------------------------------------------ closed-form Step 1, neo-Hookean, 3D, float
+// Stationarity of phi(F) = W(F) + rho/2 |F|^2 - B : F for the compressible
+// neo-Hookean law is  a F + c(J) F^{-T} = B,  a = mu + rho, c(J) = lam J (J - 1) - mu.
+// With F = U diag(s) V^T (U, V rotations) also F^{-T} = U diag(1/s) V^T, so B has
+// F's singular vectors and singular values b_i = a s_i + c / s_i: each s_i is a root
+// of a s^2 - b_i s + c = 0.  The minimiser takes the larger root,
+//   s_i = (b_i + q_i) / (2a),   q_i = sqrt(x_i - k),   x_i = b_i^2,   k = 4 a c,
+// and the local problem becomes one scalar equation in J:  s_1 s_2 s_3 = J.  For
+// J > 1/2, c grows with J and every s_i falls (ds_i/dc = -1/q_i), so there is at
+// most one root; it is found by Newton's method on f(J) = s_1 s_2 s_3 - J,
+//   f'(J) = -s_1 s_2 s_3 lam (2J - 1) sum_i 1/(q_i s_i) - 1,
+// safeguarded by bisection on (1/2, J_max], where c(J_max) = x_3 / (4a) (beyond it
+// s_3 is not real).  Then F = B Phi(C), C = B^T B, where Phi is the matrix function
+// of phi(x) = s/b = (1 + r(x)) / (2a), r(x) = sqrt(1 - k/x), taken at C's eigenvalues
+// x_1 >= x_2 >= x_3 and evaluated as Newton's interpolation polynomial
+//   Phi(C) = phi_1 I + phi_12 (C - x_1 I) + phi_123 (C - x_1 I)(C - x_2 I).
+// Its divided differences have closed forms free of cancellation (r_i = r(x_i),
+// w_i = x_i r_i):
+//   phi_12  = k / (2a x_1 x_2 (r_1 + r_2)),
+//   phi_123 = -k (r_2 + (x_1 + x_3 - k) / (w_1 + w_3)) / (2a x_1 x_2 x_3 (r_1 + r_2)(r_2 + r_3)),
+// so coincident eigenvalues (B near a multiple of a rotation: small strains) need no
+// special case, and no eigenvector is formed.  The eigenvalues come from the
+// trigonometric solution of C's characteristic cubic.  The cost is a few hundred
+// float operations in a few dozen registers, against the assembly and Cholesky
+// factorisation of the 9 x 9 Hessian at every step of the general Newton solve.
+// Returns false, leaving F as it was, when det B <= 0, when B is badly conditioned
+// (x_3 < 4e-3 x_1, where x_3 from C loses its relative accuracy) or when no root is
+// found in (1/2, J_max]; the caller then runs the general Newton solve.
+__device__ __forceinline__ bool nh3_closed_form(float mu, float lam, float rho, const float* B, float J0, float* F) {
+    const float a = mu + rho;
+    const float detB = B[0] * (B[4] * B[8] - B[5] * B[7]) + B[1] * (B[5] * B[6] - B[3] * B[8]) +
+                       B[2] * (B[3] * B[7] - B[4] * B[6]);
+    if (!(detB > 0.f)) return false;
+    const float C00 = B[0] * B[0] + B[3] * B[3] + B[6] * B[6];
+    const float C11 = B[1] * B[1] + B[4] * B[4] + B[7] * B[7];
+    const float C22 = B[2] * B[2] + B[5] * B[5] + B[8] * B[8];
+    const float C01 = B[0] * B[1] + B[3] * B[4] + B[6] * B[7];
+    const float C02 = B[0] * B[2] + B[3] * B[5] + B[6] * B[8];
+    const float C12 = B[1] * B[2] + B[4] * B[5] + B[7] * B[8];
+    // eigenvalues of C: m + 2 p cos(theta + 2 pi j / 3), cos(3 theta) = det((C - m I)/p) / 2
+    const float m = (C00 + C11 + C22) * (1.f / 3.f);
+    const float d0 = C00 - m, d1 = C11 - m, d2 = C22 - m;
+    const float p2 = (d0 * d0 + d1 * d1 + d2 * d2 + 2.f * (C01 * C01 + C02 * C02 + C12 * C12)) * (1.f / 6.f);
+    float x1 = m, x2 = m, x3 = m;
+    if (p2 > 0.f) {
+        const float p = sqrtf(p2);
+        const float ip = 1.f / p;
+        const float e0 = d0 * ip, e1 = d1 * ip, e2 = d2 * ip, e01 = C01 * ip, e02 = C02 * ip, e12 = C12 * ip;
+        float h = 0.5f * (e0 * (e1 * e2 - e12 * e12) - e01 * (e01 * e2 - e12 * e02) + e02 * (e01 * e12 - e1 * e02));
+        h = fminf(fmaxf(h, -1.f), 1.f);
+        float sn, cs;
+        sincosf(acosf(h) * (1.f / 3.f), &sn, &cs);
+        x1 = m + 2.f * p * cs;
+        x3 = m - p * (cs + 1.7320508f * sn);
+        x2 = 3.f * m - x1 - x3;
+    }
+    if (!(x3 > 4e-3f * x1)) return false;
+    const float b1 = sqrtf(x1), b2 = sqrtf(x2), b3 = sqrtf(x3);
+    const float inv2a = 0.5f / a;
+    float lo = 0.5f;
+    float hi = fminf(0.5f + sqrtf(0.25f + (mu + x3 * (0.25f / a)) / lam), 1e6f);
+    float J = (J0 > lo && J0 < hi) ? J0 : 0.5f * (lo + hi);
+    bool ok = false;
+    for (int it = 0; it < 24; ++it) {
+        const float k = 4.f * a * (lam * J * (J - 1.f) - mu);
+        const float q1 = sqrtf(fmaxf(x1 - k, 0.f)), q2 = sqrtf(fmaxf(x2 - k, 0.f)), q3 = sqrtf(fmaxf(x3 - k, 0.f));
+        const float s1 = (b1 + q1) * inv2a, s2 = (b2 + q2) * inv2a, s3 = (b3 + q3) * inv2a;
+        const float P = s1 * s2 * s3;
+        const float fJ = P - J;
+        if (fJ == 0.f) {
+            ok = true;
+            break;
+        }
+        if (fJ > 0.f)
+            lo = J;
+        else
+            hi = J;
+        const float t1 = q1 * s1, t2 = q2 * s2, t3 = q3 * s3;
+        const float df = -P * lam * (2.f * J - 1.f) * ((t2 * t3 + t1 * t3 + t1 * t2) / (t1 * t2 * t3)) - 1.f;
+        float Jn = J - fJ / df;
+        const bool newton_step = Jn >= lo && Jn <= hi;  // false for NaN
+        if (!newton_step) Jn = 0.5f * (lo + hi);
+        const float dJ = Jn - J;
+        J = Jn;
+        if (newton_step && fabsf(dJ) <= 1e-6f * J) {
+            ok = true;
+            break;
+        }
+    }
+    const float k = 4.f * a * (lam * J * (J - 1.f) - mu);
+    if (!ok || !(k < x3)) return false;
+    const float q1 = sqrtf(x1 - k), q2 = sqrtf(x2 - k), q3 = sqrtf(x3 - k);
+    const float r1 = q1 / b1, r2 = q2 / b2, r3 = q3 / b3;
+    const float W = b1 * q1 + b3 * q3;  // w_1 + w_3
+    const float D12 = x1 * x2 * (r1 + r2), D23 = x3 * (r2 + r3);
+    const float R = 1.f / (D12 * D23 * W);
+    const float kh = k * inv2a;
+    const float f1 = (1.f + r1) * inv2a;
+    const float f123 = -kh * (r2 * W + (x1 + x3 - k)) * R;
+    const float g = kh * D23 * W * R + f123 * (x1 - x2);  // phi_12 + phi_123 (x_1 - x_2)
+    // Phi(C) = f1 I + g E + phi_123 E^2 with E = C - x_1 I (symmetric)
+    const float E00 = C00 - x1, E11 = C11 - x1, E22 = C22 - x1;
+    const float M00 = f1 + g * E00 + f123 * (E00 * E00 + C01 * C01 + C02 * C02);
+    const float M11 = f1 + g * E11 + f123 * (C01 * C01 + E11 * E11 + C12 * C12);
+    const float M22 = f1 + g * E22 + f123 * (C02 * C02 + C12 * C12 + E22 * E22);
+    const float M01 = g * C01 + f123 * (E00 * C01 + C01 * E11 + C02 * C12);
+    const float M02 = g * C02 + f123 * (E00 * C02 + C01 * C12 + C02 * E22);
+    const float M12 = g * C12 + f123 * (C01 * C02 + E11 * C12 + C12 * E22);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float u = B[3 * i], v = B[3 * i + 1], w = B[3 * i + 2];
+        F[3 * i + 0] = u * M00 + v * M01 + w * M02;
+        F[3 * i + 1] = u * M01 + v * M11 + w * M12;
+        F[3 * i + 2] = u * M02 + v * M12 + w * M22;
+    }
+    return true;
+}
+
+// The general damped Newton solve (newton()) of the float neo-Hookean law in 3D,
+// kept out of line for the closed form's rare fallbacks and for the approximate
+// local steps (which need Newton's iteration counts and gradient test): scalar
+// arguments only, so that the closed-form path carries none of its registers.
+// Starts from Fin[p V] (the previous iterate), writes the result to Fout[p V];
+// returns the squared gradient norm (gtol > 0) and, as the bits of a float, the
+// Newton count plus 1 << 16 when the test was met.
+__device__ __noinline__ float2 nh3f_newton_out_of_line(const float* __restrict__ Fin, float* __restrict__ Fout,
+                                                       long long V, float B0, float B1, float B2, float B3, float B4,
+                                                       float B5, float B6, float B7, float B8, float mu, float lam,
+                                                       float rho, int cap, float tol, float gtol) {
+    float F[9];
+    const float B[9] = {B0, B1, B2, B3, B4, B5, B6, B7, B8};
+#pragma unroll
+    for (int p = 0; p < 9; ++p) F[p] = Fin[p * V];
+    NeoHooke<float, 3> m;
+    m.mu = mu;
+    m.lam = lam;
+    bool conv;
+    float gn2 = 0.f;
+    const int it = newton<float, 3>(m, F, B, rho, cap, tol, conv, gtol, &gn2);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) Fout[p * V] = F[p];
+    return make_float2(gn2, __int_as_float(it | (conv ? 1 << 16 : 0)));
+}
+
 // W_F(F) - Bm on double-word data for the elastic laws (their grad() in double-word
 // arithmetic; F, Bm, g: d*d entries row-major).  False when J <= 0.
 template <int D, int MODEL>
@@ -1276,6 +1420,10 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     // replaces); the first local step of a solve is exact
     const double rd_use = FIRST ? (only_if_rho_changed ? ctrl->rd_local : 0.0) : ctrl->r_d;
     const T gtol = INC ? T(0) : (T)(ctrl->local_ratio * ctrl->mu_ref * rd_use);
+    // the float neo-Hookean law in 3D solves an exact local step in closed form
+    // (nh3_closed_form); the approximate local steps keep the Newton iteration
+    constexpr bool kClosedForm = std::is_same<T, float>::value && D == 3 && MODEL == kNeoHooke && !WRITE_R && !DU;
+    const bool exact_local = gtol == T(0) && !(ctrl->local_fraction > 0.0);
     // G_{k+1} - G_k = (<F>_{k+1} - <F>_k) + D(u~_{k+1} - u~_k); the uniform first
     // term (nonzero only under mixed control) enters the voxel sums of r_d in closed
     // form in the last block (D u~ sums to zero over the cell), except in the
@@ -1397,11 +1545,31 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             using Law = typename LawOf<T, D, MODEL>::type;
             const Law m = load_law<Law, T>(phase, mat, nparam, v);
             T gn2 = T(0);
-            it = newton<T, D>(m, F, B, rho, cap, ntol, conv, gtol, &gn2);
+            if constexpr (kClosedForm) {
+                if (exact_local && nh3_closed_form(m.mu, m.lam, rho, B, det<T, 3>(F), F)) {
+                    it = 1;
+                    conv = true;
+                } else {
+                    const float2 r = nh3f_newton_out_of_line(Fcur + v, Fnext + v, V, B[0], B[1], B[2], B[3], B[4],
+                                                             B[5], B[6], B[7], B[8], m.mu, m.lam, rho, cap, ntol, gtol);
+                    gn2 = r.x;
+                    const int bits = __float_as_int(r.y);
+                    it = bits & 0xffff;
+                    conv = (bits >> 16) != 0;
+#pragma unroll
+                    for (int p = 0; p < NN; ++p) F[p] = Fnext[p * V + v];
+                }
+            } else {
+                it = newton<T, D>(m, F, B, rho, cap, ntol, conv, gtol, &gn2);
+            }
             rl2a += (Acc)gn2;
         }
         nmax = max(nmax, it);
         nfail += conv ? 0 : 1;
+        // Every Newton step keeps J > 0, so J <= 0 after the local step means the voxel
+        // started inverted (a state or <F> with det <= 0) and W is undefined there: the
+        // residual sum is made NaN, which ends the solve with RVE_E_NUMERICAL.
+        if (!conv && !(det<T, D>(F) > T(0))) rp2a = Acc(NAN);
         if (frac_on && conv) atomicAdd(&s_hist[min(max(it + 1, 2) / 2, kNewtonBins) - 1], 1);
 #pragma unroll
         for (int p = 0; p < NN; ++p) Fnext[p * V + v] = F[p];
