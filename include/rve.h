@@ -343,7 +343,11 @@ int rve_server_create(rve_server_t* out, size_t mem_budget_bytes, const rve_opti
 
 /* Queue a solve: a fresh state on an N^d cell (inputs as rve_create /
  * rve_set_material / rve_solve; host arrays are copied).  *ticket identifies it.
- * Errors: RVE_E_INVALID_ARG, RVE_E_OOM (its workspace exceeds the budget). */
+ * Errors: RVE_E_INVALID_ARG (shape, phase ids, rho, tol, or a non-finite Fbar or
+ * det Fbar <= 0, checked here as rve_solve does), RVE_E_OOM (its workspace
+ * exceeds the budget).  Material parameters are checked when the request is
+ * admitted: a request rve_set_material rejects ends by itself with
+ * RVE_E_INVALID_ARG (NaN stress) and the server carries on. */
 int rve_server_submit(rve_server_t s, int dim, int n, int model, const uint8_t* phase, int nphase,
                       const double* params, int nparam, const double* n0, const double Fbar[9], double rho,
                       double tol, long long* ticket);
@@ -420,18 +424,25 @@ int rve_kernel_times(rve_t h, int fp64, double* ms, long long* launches, int cap
  * latency-critical loop that must not call cudaMalloc/cudaFree because they may
  * synchronise the device.  The paper has no counterpart; this is a systems entry
  * point, with the same result as rve_stress on the same F.
- * Inputs, all DEVICE pointers owned by the caller: F_dev (d*d*N^d doubles, the
- * field layout above), phase_dev (N^d bytes, values < nphase), params_dev
- * (nphase * nparam doubles, {mu, lam} first).  Output: S_dev (9 doubles, device).
- * model is RVE_NEOHOOKE or RVE_LINEAR.  Work is queued on cuda_stream (NULL =
- * legacy default stream); the call returns without waiting for it.
+ * Inputs, all DEVICE pointers owned by the caller: F_dev (d*d*N^d DOUBLES in the
+ * component-major field layout above; a mixed-precision or float handle keeps F
+ * as float, so widen that field to double before passing it), phase_dev (N^d
+ * bytes, values < nphase), params_dev (nphase * nparam doubles, {mu, lam} first).
+ * Output: S_dev (9 doubles, device).  model is RVE_NEOHOOKE or RVE_LINEAR.  n is
+ * not held to the handle's grid rules (even, 2^a 3^b, <= 512): any n >= 2 with
+ * N^d within the capacity below is accepted.  Work is queued on cuda_stream
+ * (NULL = legacy default stream); the call returns without waiting for it, so
+ * it can report an error found on the device only through S_dev: a phase id >=
+ * nphase makes every entry NaN (the status is still RVE_OK) -- check S_dev for
+ * NaN after synchronising.
  * Nothing is allocated: block partial sums go to a static device array of 2 MiB
  * (+256 B) that every GPU loading this library holds until exit, which limits
  * N^d to 16,777,216 voxels (256^3); larger sizes return RVE_E_INVALID_ARG.  The
  * first call on each device looks up that array's address (call it once before
- * any stream capture).  All calls share the array and clear its header on
- * entry: calls whose work overlaps on the GPU race, so serialise them (e.g. one
- * stream).  A phase id >= nphase makes the result NaN. */
+ * any stream capture); the address is kept for the life of the process, so do
+ * not use this entry point after cudaDeviceReset on that device.  All calls
+ * share the array and clear its header on entry: calls whose work overlaps on
+ * the GPU race, so serialise them (e.g. one stream). */
 int rve_stress_noalloc(int dim, int n, int model, const double* F_dev, const uint8_t* phase_dev,
                        const double* params_dev, int nphase, int nparam, double* S_dev, void* cuda_stream);
 

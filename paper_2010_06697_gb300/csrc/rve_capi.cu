@@ -1655,6 +1655,21 @@ void server_drop_pool(rve_server* s, size_t need) {
 }
 
 // Admit queued requests in arrival order while their workspaces fit the budget.
+// A request whose material or load the library rejects when it is admitted ends
+// by itself with that status (NaN stress); the other requests and later steps are
+// unaffected.
+void server_reject(rve_server* s, const Request& r, int status) {
+    Finished f;
+    f.status = status;
+    for (int i = 0; i < 9; ++i) f.S[i] = NAN;
+    f.info.status = status;
+    const double t = now_ms();
+    f.queue_ms = t - r.t_submit;
+    f.latency_ms = t - r.t_submit;
+    s->done[r.ticket] = f;
+    s->completed += 1;
+}
+
 int server_admit(rve_server* s) {
     for (auto it = s->queue.begin(); it != s->queue.end();) {
         Request& r = *it;
@@ -1683,13 +1698,19 @@ int server_admit(rve_server* s) {
         if (rc) {
             rve_destroy(h);
             s->used -= r.bytes;
-            return rc;
+            if (rc != RVE_E_INVALID_ARG) return rc;
+            server_reject(s, r, rc);
+            it = s->queue.erase(it);
+            continue;
         }
         const int slot = engine_add(s->E, h, r.Fbar, r.rho, r.tol);
         if (slot < 0) {
             rve_destroy(h);
             s->used -= r.bytes;
-            return slot;
+            if (slot != RVE_E_INVALID_ARG) return slot;
+            server_reject(s, r, slot);
+            it = s->queue.erase(it);
+            continue;
         }
         r.t_admit = now_ms();
         r.phase.clear();
@@ -1767,6 +1788,13 @@ int rve_server_submit(rve_server_t s, int dim, int n, int model, const uint8_t* 
     if (model == RVE_LCE && (dim != 3 || !n0 || nparam < 5)) return RVE_E_INVALID_ARG;
     if (nphase < 1 || nphase > 256 || nparam < 2 || nparam > admm::kMaxParam) return RVE_E_INVALID_ARG;
     if (!(rho > 0) || !isfinite(rho) || isnan(tol)) return RVE_E_INVALID_ARG;
+    for (int i = 0; i < 9; ++i)
+        if (!isfinite(Fbar[i])) return RVE_E_INVALID_ARG;
+    const double det2 = Fbar[0] * Fbar[4] - Fbar[1] * Fbar[3];
+    const double det3 = Fbar[0] * (Fbar[4] * Fbar[8] - Fbar[5] * Fbar[7]) -
+                        Fbar[1] * (Fbar[3] * Fbar[8] - Fbar[5] * Fbar[6]) +
+                        Fbar[2] * (Fbar[3] * Fbar[7] - Fbar[4] * Fbar[6]);
+    if (!((dim == 2 ? det2 : det3) > 0)) return RVE_E_INVALID_ARG;  // as rve_solve
     const long long V = dim == 3 ? (long long)n * n * n : (long long)n * n;
     for (long long v = 0; v < V; ++v)
         if (phase[v] >= nphase) return RVE_E_INVALID_ARG;

@@ -15,7 +15,8 @@
 // every GPU which loads this library keeps until the process exits.  Its device
 // address is looked up once per device with cudaGetSymbolAddress, on the first
 // call made with that device current; make that first call before any stream
-// capture.  All calls on a device share the array: the header (counter, error
+// capture.  The address is kept for the life of the process, so this entry point
+// must not be called on a device after cudaDeviceReset there.  All calls on a device share the array: the header (counter, error
 // flag) is cleared at the start of every call, and calls whose work overlaps on
 // the GPU race on it, so order them on one stream (or otherwise serialise them).
 #include <cuda_runtime.h>
