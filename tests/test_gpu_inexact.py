@@ -1,9 +1,14 @@
-"""Inexact local steps (rve_options.local_ratio, Section 2.1 and Section 4.2's
-r_l <= f r_d) on the GPU vs the FP64 oracle with the same rule.
+"""Approximate local steps on the GPU (rve_options.local_ratio and local_fraction;
+Section 2.1, Algorithm 1's inner loop, Section 4.2's two strategies) against the
+FP64 oracle, which follows the paper's rules literally.
 
-A voxel whose gradient norm sits within rounding of the tolerance may take one
-Newton step more or less on one side, so iterates are compared with a tolerance
-that such a step allows; converged stresses are compared to the solve tolerance."""
+The device approximates both rules without a grid-wide barrier inside its fused
+pass: r_l <= f r_d is enforced pointwise (|grad phi| <= f mu_ref r_d at every voxel,
+a sufficient condition for the L2 bound) with the r_d of the check two iterations
+back, and the fraction rule caps the Newton count from the previous pass's counts.
+Its iterates therefore differ from the oracle's; both converge to the same fixed
+point of the exact iteration, so converged fields and stresses are compared, at a
+tolerance a few hundred times the solve tolerance."""
 import numpy as np
 import pytest
 
@@ -31,28 +36,26 @@ def solve(ph, Fbar, tol, max_iter, precision="fp64", model="neohookean", par=PAR
 
 
 @pytest.mark.parametrize("d,n", [(3, 16), (2, 48)])
-def test_inexact_fp64_matches_oracle(d, n):
-    f = 0.3
+def test_ratio_rule_fp64_converges_to_paper_rule_oracle(d, n):
+    f, tol = 0.3, 1e-10
     ph = synth.inclusion_phase(n, d, 2, radius=max(2, n // 6))
     Fbar = np.diag([0.92, 1.0, 1.03])
-    s, info = solve(ph, Fbar, 1e-9, 600, local_ratio=f)
-    ref = oracle.admm_solve(ph, PAR, Fbar, 10.0, 1e-9, 600, local_ratio=f)
+    s, info = solve(ph, Fbar, tol, 800, local_ratio=f)
+    ref = oracle.admm_solve(ph, PAR, Fbar, 10.0, tol, 800, local_ratio=f)
     assert info.converged and ref["converged"]
-    assert abs(info.iterations - ref["iters"]) <= 2
+    assert abs(info.iterations - ref["iters"]) <= 0.25 * ref["iters"]
     assert rel(s.stress(), ref["stress"]) < 1e-8
-    st = s.state()
-    assert rel(st["F"], ref["F"]) < 1e-7
-    # residual histories follow the oracle's over the first iterations
+    assert rel(s.state()["F"], ref["F"]) < 1e-7
+    # the device's own rule: r_l of Step 1 in iteration i + 2 is bounded by f r_d of
+    # the check of iteration i (pointwise stop, so the L2 bound holds)
     h = s.history()
-    href = np.array(ref["history"])
-    m = min(len(h), len(href), 20)
-    np.testing.assert_allclose(h[:m, :2], href[:m, :2], rtol=1e-4, atol=1e-12)
-    # r_l: entry i is Step 1 of iteration i + 2; bounded by f r_d two checks back
     rl = s.history_local()
-    rl_ref = np.array(ref["local_residual"])
-    np.testing.assert_allclose(rl[:m - 1], rl_ref[1:m], rtol=1e-3, atol=1e-11)
     assert np.all(rl[1:len(h) - 1] <= f * h[:len(h) - 2, 1] * (1 + 1e-9))
     assert info.r_l == pytest.approx(rl[len(h) - 1], rel=1e-12, abs=1e-300)
+    # the oracle's rule: r_l <= f r_d of the latest check
+    rd = np.array(ref["history"])[:, 1]
+    rl_ref = np.array(ref["local_residual"])
+    assert np.all(rl_ref[1:] <= f * rd[:-1] * (1 + 1e-12))
 
 
 def test_inexact_exact_first_steps_and_zero_ratio_unchanged():
@@ -70,47 +73,58 @@ def test_inexact_exact_first_steps_and_zero_ratio_unchanged():
     assert rel(s2.state()["F"], s3.state()["F"]) < 1e-13
 
 
-def test_inexact_mixed_converges_to_exact_solution():
-    """Mixed precision with r_l <= 0.3 r_d on a 32^3 inclusion cell: the double
-    polish still reaches the exact solve's stress."""
-    n = 32
-    ph = synth.inclusion_phase(n, 3, 0)
+def test_inexact_mixed_converges_to_oracle_solution():
+    """Mixed precision with r_l <= 0.3 r_d: the double polish still reaches the exact
+    solution, on a 16^3 inclusion cell against the oracle's exact solve (mixed stress
+    tolerance 1e-5 relative; measured far below) and on 32^3 against the FP64 GPU solve."""
+    ph = synth.inclusion_phase(16, 3, 0, radius=3)
     Fbar = np.diag([0.9, 1.0, 1.0])
+    ref = oracle.admm_solve(ph, PAR, Fbar, 10.0, 1e-8, 1000)
+    s_in, i_in = solve(ph, Fbar, 1e-8, 1000, precision="mixed", local_ratio=0.3)
+    assert ref["converged"] and i_in.converged
+    assert rel(s_in.stress(), ref["stress"]) < 1e-7
+    ph = synth.inclusion_phase(32, 3, 0)
     s_ex, i_ex = solve(ph, Fbar, 1e-8, 1000, precision="fp64")
     s_in, i_in = solve(ph, Fbar, 1e-8, 1000, precision="mixed", local_ratio=0.3)
     assert i_ex.converged and i_in.converged
     assert rel(s_in.stress(), s_ex.stress()) < 1e-7
 
 
-def test_inexact_lce_matches_oracle():
-    """LCE cell, fixed iteration count: the inexact rule on the 11-unknown local
-    problem (F and the director's tangent coordinates)."""
-    n = 12
+def test_ratio_rule_lce_time_step_converges_to_oracle():
+    """LCE cell with dissipation (one implicit time step, nu_F/dt = nu_n/dt = 10, a
+    polydomain director field): the ratio rule on the 11-unknown local problem (F and
+    the director's tangent coordinates) converges, on both sides, to the same state."""
+    n, f, tol = 8, 0.3, 1e-10
     ph = np.zeros((n,) * 3, np.uint8)
     n0 = synth.director_grf(n, 7, corr=2.5)
-    par = np.array([[1.0, 20.0, 7.71, 0.06, (2.0 / n) ** 2]])
-    Fbar = np.diag([1.2, 0.91, 0.91])
-    s, info = solve(ph, Fbar, -1.0, 12, model="lce", par=par, n0=n0, local_ratio=0.3)
-    ref = oracle.admm_solve(ph, par, Fbar, 10.0, -1.0, 12, model="lce", n0=n0, local_ratio=0.3)
+    par = np.array([[1.0, 20.0, 7.71, 0.06, (2.0 / n) ** 2, 10.0, 10.0]])
+    Fbar = np.diag([1.05, 0.98, 0.98])
+    s, info = solve(ph, Fbar, tol, 600, model="lce", par=par, n0=n0, local_ratio=f)
+    ref = oracle.admm_solve(ph, par, Fbar, 10.0, tol, 600, model="lce", n0=n0, local_ratio=f)
+    assert info.converged and ref["converged"]
     st = s.state()
-    assert rel(st["F"], ref["F"]) < 1e-6
-    assert np.max(np.abs(st["n"] - ref["n"])) < 1e-6
+    assert rel(st["F"], ref["F"]) < 1e-7
+    assert np.max(np.abs(st["n"] - ref["n"])) < 1e-7
+    assert rel(s.stress(), ref["stress"]) < 1e-8
+    h = s.history()
     rl = s.history_local()
-    np.testing.assert_allclose(rl[:10], np.array(ref["local_residual"])[1:11], rtol=1e-3, atol=1e-11)
+    assert np.all(rl[1:len(h) - 1] <= f * h[:len(h) - 2, 1] * (1 + 1e-9))
 
 
-def test_fraction_converged_fp64_and_mixed():
-    """Fraction-converged local steps (p = 0.9): FP64 on a 16^3 inclusion cell converges
-    to the oracle's solution with the same rule (Newton counts differ between the two
-    Newton variants, so the caps may differ and the comparison is on converged states),
-    and mixed precision on 32^3 reaches the exact solve's stress."""
+def test_fraction_rule_fp64_and_mixed():
+    """Fraction-converged local steps (p = 0.9).  FP64 on a 16^3 inclusion cell: the
+    device's lagged cap and the oracle's in-pass rule (rounds of two Newton
+    iterations, proceed once 90 % of the points converged) reach the same converged
+    solution.  Mixed precision on 32^3 reaches the exact FP64 solve's stress."""
+    tol = 1e-10
     ph = synth.inclusion_phase(16, 3, 2, radius=2)
     Fbar = np.diag([0.92, 1.0, 1.03])
-    s, info = solve(ph, Fbar, 1e-9, 800, local_fraction=0.9)
-    ref = oracle.admm_solve(ph, PAR, Fbar, 10.0, 1e-9, 800, local_fraction=0.9, local_cap=30)
+    s, info = solve(ph, Fbar, tol, 800, local_fraction=0.9)
+    ref = oracle.admm_solve(ph, PAR, Fbar, 10.0, tol, 800, local_fraction=0.9, local_cap=30)
     assert info.converged and ref["converged"]
     assert rel(s.stress(), ref["stress"]) < 1e-8
     assert rel(s.state()["F"], ref["F"]) < 1e-7
+    assert np.all(np.array(ref["local_converged"]) >= 0.9 * 16 ** 3)
     ph = synth.inclusion_phase(32, 3, 0)
     Fbar = np.diag([0.9, 1.0, 1.0])
     s_ex, i_ex = solve(ph, Fbar, 1e-8, 1000)
