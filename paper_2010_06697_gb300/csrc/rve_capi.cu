@@ -650,6 +650,7 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
             E.smem_a[f] = admm::smem_a_bytes(L, f == 1);
         }
         E.uniform_n = n;
+        E.exact_local = (o.local_ratio == 0.0 && o.local_fraction == 0.0) ? 1 : 0;
     }
     h->state_fp64 = o.precision == RVE_FP64 ? 1 : 0;
     h->hctrl->hist_cap = o.max_iter + 1;
@@ -1324,8 +1325,11 @@ int run_upload(Engine& E, BatchRun& r) {
     r.E.rds = E.d_rds;
     r.E.rep = &E.mem[r.active.front()].h->L;
     r.E.uniform_n = E.mem[r.active.front()].h->n;
-    for (int slot : r.active)
+    r.E.exact_local = 1;
+    for (int slot : r.active) {
         if (E.mem[slot].h->n != r.E.uniform_n) r.E.uniform_n = 0;
+        if (!E.mem[slot].h->E.exact_local) r.E.exact_local = 0;
+    }
     for (int f = 0; f < 2; ++f) {
         r.E.smem_x[f] = 0;
         r.E.smem_a[f] = 0;

@@ -179,6 +179,9 @@ struct Exec {
     size_t smem_x[2];             // dynamic shared memory of the x passes [fp64], max over members
     size_t smem_a[2];             // and of the y/z passes
     int uniform_n;                // N shared by every member (0 if sizes differ)
+    int exact_local;              // 1: no member takes approximate local steps (local_ratio,
+                                  // local_fraction both 0): the float neo-Hookean law in 3D
+                                  // then runs its closed-form local step
 };
 
 // FFT geometry of one grid shape: x-pass lines per block and half-length radices,

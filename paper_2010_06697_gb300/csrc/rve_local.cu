@@ -509,7 +509,7 @@ __device__ __forceinline__ bool nh3_closed_form(float mu, float lam, float rho, 
         float h = 0.5f * (e0 * (e1 * e2 - e12 * e12) - e01 * (e01 * e2 - e12 * e02) + e02 * (e01 * e12 - e1 * e02));
         h = fminf(fmaxf(h, -1.f), 1.f);
         float sn, cs;
-        sincosf(acosf(h) * (1.f / 3.f), &sn, &cs);
+        __sincosf(acosf(h) * (1.f / 3.f), &sn, &cs);  // |error| < 2^-21 for an angle in [0, pi/3]
         x1 = m + 2.f * p * cs;
         x3 = m - p * (cs + 1.7320508f * sn);
         x2 = 3.f * m - x1 - x3;
@@ -523,7 +523,10 @@ __device__ __forceinline__ bool nh3_closed_form(float mu, float lam, float rho, 
     bool ok = false;
     for (int it = 0; it < 24; ++it) {
         const float k = 4.f * a * (lam * J * (J - 1.f) - mu);
-        const float q1 = sqrtf(fmaxf(x1 - k, 0.f)), q2 = sqrtf(fmaxf(x2 - k, 0.f)), q3 = sqrtf(fmaxf(x3 - k, 0.f));
+        // the iterates only steer the root search: fast square roots and quotients
+        // (rsqrt, __fdividef) suffice here; the final F below uses IEEE operations
+        const float y1 = fmaxf(x1 - k, 1e-30f), y2 = fmaxf(x2 - k, 1e-30f), y3 = fmaxf(x3 - k, 1e-30f);
+        const float q1 = y1 * rsqrtf(y1), q2 = y2 * rsqrtf(y2), q3 = y3 * rsqrtf(y3);
         const float s1 = (b1 + q1) * inv2a, s2 = (b2 + q2) * inv2a, s3 = (b3 + q3) * inv2a;
         const float P = s1 * s2 * s3;
         const float fJ = P - J;
@@ -536,8 +539,8 @@ __device__ __forceinline__ bool nh3_closed_form(float mu, float lam, float rho, 
         else
             hi = J;
         const float t1 = q1 * s1, t2 = q2 * s2, t3 = q3 * s3;
-        const float df = -P * lam * (2.f * J - 1.f) * ((t2 * t3 + t1 * t3 + t1 * t2) / (t1 * t2 * t3)) - 1.f;
-        float Jn = J - fJ / df;
+        const float df = -P * lam * (2.f * J - 1.f) * __fdividef(t2 * t3 + t1 * t3 + t1 * t2, t1 * t2 * t3) - 1.f;
+        float Jn = J - __fdividef(fJ, df);
         const bool newton_step = Jn >= lo && Jn <= hi;  // false for NaN
         if (!newton_step) Jn = 0.5f * (lo + hi);
         const float dJ = Jn - J;
@@ -576,30 +579,47 @@ __device__ __forceinline__ bool nh3_closed_form(float mu, float lam, float rho, 
     return true;
 }
 
-// The general damped Newton solve (newton()) of the float neo-Hookean law in 3D,
-// kept out of line for the closed form's rare fallbacks and for the approximate
-// local steps (which need Newton's iteration counts and gradient test): scalar
-// arguments only, so that the closed-form path carries none of its registers.
-// Starts from Fin[p V] (the previous iterate), writes the result to Fout[p V];
-// returns the squared gradient norm (gtol > 0) and, as the bits of a float, the
-// Newton count plus 1 << 16 when the test was met.
-__device__ __noinline__ float2 nh3f_newton_out_of_line(const float* __restrict__ Fin, float* __restrict__ Fout,
-                                                       long long V, float B0, float B1, float B2, float B3, float B4,
-                                                       float B5, float B6, float B7, float B8, float mu, float lam,
-                                                       float rho, int cap, float tol, float gtol) {
-    float F[9];
-    const float B[9] = {B0, B1, B2, B3, B4, B5, B6, B7, B8};
+// The rare fallback of the closed-form local step: steepest descent with Armijo
+// backtracking that keeps J > 0 (Section 2.1's own local method), from the previous
+// iterate F.  Few registers beyond F and B, so that the closed-form kernel keeps its
+// occupancy.  The step starts at 1/(mu + lam + rho); stops after an accepted step with
+// max|dF| <= tol.  Returns the number of steps; conv tells whether the test was met.
+template <typename T, int D, typename Law>
+__device__ __forceinline__ int steepest_descent(const Law& m, T* F, const T* B, T rho, int cap, T tol, bool& conv) {
+    constexpr int NN = D * D;
+    conv = false;
+    const T t0 = T(1) / (m.mu + m.lam + rho);
+    int it = 0;
+    for (; it < cap; ++it) {
+        T g[NN], aux[Law::NAUX];
+        if (!m.grad(F, B, rho, g, aux)) break;
+        const T phi0 = m.phi(F, B, rho, aux[NN]);
+        T g2 = T(0), gmax = T(0);
 #pragma unroll
-    for (int p = 0; p < 9; ++p) F[p] = Fin[p * V];
-    NeoHooke<float, 3> m;
-    m.mu = mu;
-    m.lam = lam;
-    bool conv;
-    float gn2 = 0.f;
-    const int it = newton<float, 3>(m, F, B, rho, cap, tol, conv, gtol, &gn2);
+        for (int p = 0; p < NN; ++p) {
+            g2 += g[p] * g[p];
+            gmax = fmax(gmax, fabs(g[p]));
+        }
+        T t = t0;
+        bool ok = false;
+        for (int ls = 0; ls < 30 && !ok; ++ls) {
+            T Ft[NN];
 #pragma unroll
-    for (int p = 0; p < 9; ++p) Fout[p * V] = F[p];
-    return make_float2(gn2, __int_as_float(it | (conv ? 1 << 16 : 0)));
+            for (int p = 0; p < NN; ++p) Ft[p] = F[p] - t * g[p];
+            const T Jt = det<T, D>(Ft);
+            ok = Jt > T(0) && m.phi(Ft, B, rho, Jt) <= phi0 - T(1e-4) * t * g2;
+            if (!ok) t *= T(0.5);
+        }
+        if (!ok) break;
+#pragma unroll
+        for (int p = 0; p < NN; ++p) F[p] -= t * g[p];
+        if (t * gmax <= tol) {
+            conv = true;
+            ++it;
+            break;
+        }
+    }
+    return it;
 }
 
 // W_F(F) - Bm on double-word data for the elastic laws (their grad() in double-word
@@ -1359,7 +1379,7 @@ k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const 
 // is a run-time flag (not a template parameter) so that the local step compiles
 // to one instruction sequence for both entry paths: a solve resumed from a saved
 // state then reproduces the uninterrupted run bit for bit.
-template <typename T, int D, int MODEL, bool WRITE_R, bool DU>
+template <typename T, int D, int MODEL, bool WRITE_R, bool DU, bool CF>
 __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool FIRST_ARG, int only_if_rho_changed) {
     constexpr int NN = D * D;
     Ctrl* __restrict__ ctrl = L.ctrl;
@@ -1420,10 +1440,11 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     // replaces); the first local step of a solve is exact
     const double rd_use = FIRST ? (only_if_rho_changed ? ctrl->rd_local : 0.0) : ctrl->r_d;
     const T gtol = INC ? T(0) : (T)(ctrl->local_ratio * ctrl->mu_ref * rd_use);
-    // the float neo-Hookean law in 3D solves an exact local step in closed form
-    // (nh3_closed_form); the approximate local steps keep the Newton iteration
-    constexpr bool kClosedForm = std::is_same<T, float>::value && D == 3 && MODEL == kNeoHooke && !WRITE_R && !DU;
-    const bool exact_local = gtol == T(0) && !(ctrl->local_fraction > 0.0);
+    // CF: the float neo-Hookean law in 3D with exact local steps (no member of the launch
+    // takes approximate ones) solves Step 1 in closed form (nh3_closed_form)
+    constexpr bool kClosedForm = CF;
+    static_assert(!CF || (std::is_same<T, float>::value && D == 3 && MODEL == kNeoHooke && !WRITE_R && !DU),
+                  "closed-form local step: float neo-Hookean law in 3D only");
     // G_{k+1} - G_k = (<F>_{k+1} - <F>_k) + D(u~_{k+1} - u~_k); the uniform first
     // term (nonzero only under mixed control) enters the voxel sums of r_d in closed
     // form in the last block (D u~ sums to zero over the cell), except in the
@@ -1546,18 +1567,11 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             const Law m = load_law<Law, T>(phase, mat, nparam, v);
             T gn2 = T(0);
             if constexpr (kClosedForm) {
-                if (exact_local && nh3_closed_form(m.mu, m.lam, rho, B, det<T, 3>(F), F)) {
+                if (nh3_closed_form(m.mu, m.lam, rho, B, det<T, 3>(F), F)) {
                     it = 1;
                     conv = true;
                 } else {
-                    const float2 r = nh3f_newton_out_of_line(Fcur + v, Fnext + v, V, B[0], B[1], B[2], B[3], B[4],
-                                                             B[5], B[6], B[7], B[8], m.mu, m.lam, rho, cap, ntol, gtol);
-                    gn2 = r.x;
-                    const int bits = __float_as_int(r.y);
-                    it = bits & 0xffff;
-                    conv = (bits >> 16) != 0;
-#pragma unroll
-                    for (int p = 0; p < NN; ++p) F[p] = Fnext[p * V + v];
+                    it = steepest_descent<T, 3>(m, F, B, rho, cap, ntol, conv);
                 }
             } else {
                 it = newton<T, D>(m, F, B, rho, cap, ntol, conv, gtol, &gn2);
@@ -1744,20 +1758,22 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
 
 // Resident blocks per SM the register budget is cut for: the float elastic laws
 // are latency-bound at fewer.
-template <typename T, int MODEL, bool WRITE_R, bool DU>
+constexpr int kCfMinBlocks = 6;  // 80 registers: two whole waves of the 1824-block grid
+template <typename T, int MODEL, bool WRITE_R, bool DU, bool CF>
 constexpr int local_min_blocks() {
     if (is_lce(MODEL)) return 1;
+    if (CF) return kCfMinBlocks;
     if (sizeof(T) == 4) return 4;
     return (WRITE_R && DU) ? 4 : 1;  // the double-word polish: FP32 work, latency-bound
 }
 
-template <typename T, int D, int MODEL, bool WRITE_R, bool DU>
-__global__ void __launch_bounds__(kLocalThreads, local_min_blocks<T, MODEL, WRITE_R, DU>())
+template <typename T, int D, int MODEL, bool WRITE_R, bool DU, bool CF = false>
+__global__ void __launch_bounds__(kLocalThreads, local_min_blocks<T, MODEL, WRITE_R, DU, CF>())
 k_local(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles, int first,
         int only_if_rho_changed) {
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tl = tiles[t];
-        local_tile<T, D, MODEL, WRITE_R, DU>(rds[tl.x], tl.y, first != 0, only_if_rho_changed);
+        local_tile<T, D, MODEL, WRITE_R, DU, CF>(rds[tl.x], tl.y, first != 0, only_if_rho_changed);
         __syncthreads();
     }
 }
@@ -1972,6 +1988,12 @@ cudaError_t run_local(const Exec& E, bool first, bool only_if, int mode) {
         const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, nt);
         kern<<<grid, kLocalThreads, 0, E.stream>>>(E.rds, tl, nt, is_first, flag);
     };
+    if constexpr (std::is_same<T, float>::value && D == 3 && MODEL == kNeoHooke) {
+        if (E.exact_local) {
+            go(k_local<T, D, MODEL, false, false, true>, first ? 1 : 0, first && only_if ? 1 : 0);
+            return cudaGetLastError();
+        }
+    }
     if (first) {
         go(k_local<T, D, MODEL, false, false>, 1, only_if ? 1 : 0);
         return cudaGetLastError();
