@@ -674,43 +674,6 @@ __device__ __forceinline__ bool grad_dw(const dw* F, dw mu, dw lam, const dw* Bm
     }
 }
 
-// The rare branch of polish_voxel_dw: the general double Newton from F_{k+1}, with
-// B = Bm + rho F_{k+1}, Bm = Lambda_{k+1} + rho e.  Everything is read back from
-// memory (F_{k+1} from Fc, Lambda_{k+1} from Lhi / Llo, e from Rio) and the call is
-// kept out of line with scalar arguments only, so that the one-step path carries
-// none of its registers.  Writes F_{k+2} (double-words) and R_{k+1}; returns the
-// Newton count, plus 1 << 16 when it met the tolerance.
-template <int D, int MODEL>
-__device__ __noinline__ int polish_fallback(const float* __restrict__ Fc, float* __restrict__ Fn,
-                                            const float* __restrict__ Lhi, const float* __restrict__ Llo,
-                                            float* __restrict__ Rio, float mu_hi, float mu_lo, float lam_hi,
-                                            float lam_lo, float rho_hi, float rho_lo, int cap, double tol, long long v,
-                                            long long V) {
-    constexpr int NN = D * D;
-    using Law64 = typename LawOf<double, D, MODEL>::type;
-    const Law64 m64{(double)mu_hi + (double)mu_lo, (double)lam_hi + (double)lam_lo};
-    const double rh = (double)rho_hi + (double)rho_lo;
-    double F0[NN], Fd[NN], B[NN];
-#pragma unroll
-    for (int p = 0; p < NN; ++p) {
-        F0[p] = (double)Fc[p * V + v] + (double)Fc[(NN + p) * V + v];
-        Fd[p] = F0[p];
-        const double e = (double)Rio[p * V + v];
-        B[p] = (double)Lhi[p * V + v] + (double)Llo[p * V + v] + rh * e + rh * F0[p];
-    }
-    bool conv;
-    const int it = newton<double, D>(m64, Fd, B, rh, cap, tol, conv);
-#pragma unroll
-    for (int p = 0; p < NN; ++p) {
-        const double e = (double)Rio[p * V + v];
-        Rio[p * V + v] = (float)((Fd[p] - F0[p]) - e);
-        const dw f = dw_from(Fd[p]);
-        Fn[p * V + v] = f.hi;
-        Fn[(NN + p) * V + v] = f.lo;
-    }
-    return it | (conv ? 1 << 16 : 0);
-}
-
 // Local step of the double polish, one voxel, on double-word state (elastic laws).
 //
 // Increment form: with R_k = F_{k+1} - G_k from the previous iteration (float) and
@@ -729,19 +692,22 @@ __device__ __noinline__ int polish_fallback(const float* __restrict__ Fc, float*
 // them and is corrected by the next iteration's step, which starts from this F (the
 // inexact local solves of Sections 2.1 and 4.2, r_l << r_d).  A fixed point still
 // has an exactly stationary local problem (to the 2^-48 resolution of the state):
-// the step from it is zero only where the gradient vanishes.  Otherwise (large or
-// unsafe step, failed factorisation, J <= 0) the general double Newton runs to the
-// tolerance from F_{k+1}, and its result is split back into double-words.
+// the step from it is zero only where the gradient vanishes.  Otherwise (a large or
+// unsafe step, a failed factorisation: rare, since the polish starts from a double
+// local solve and moves by residual-sized increments) a damped step is taken and the
+// following iterations continue from it; a voxel whose state is inverted keeps F.
+// All of it inline: an out-of-line fallback made the compiler spill around the call
+// on every voxel.
 //
 // Storage: F as (hi, lo) float arrays in the double F buffers (hi at p V + v, lo
-// at (d*d + p) V + v), Lambda as (Lhi, Llo), updated in place.  Returns the Newton
-// count; sp, sd get the voxel's squared residual terms.
+// at (d*d + p) V + v), Lambda as (Lhi, Llo), updated in place.  Returns the number
+// of steps (1); conv tells whether it was the full refinement step; sp, sd get the
+// voxel's squared residual terms.
 template <int D, int MODEL>
 __device__ __forceinline__ int polish_voxel_dw(const float* __restrict__ Fc, float* __restrict__ Fn,
                                                float* __restrict__ Lhi, float* __restrict__ Llo,
                                                float* __restrict__ Rio, const float* dG, dw mu, dw lam, dw rho,
-                                               int cap, double tol, long long v, long long V, float& sp, float& sd,
-                                               bool& conv) {
+                                               long long v, long long V, float& sp, float& sd, bool& conv) {
     constexpr int NN = D * D;
     constexpr int NP = NN * (NN + 1) / 2;
     using Law = typename LawOf<float, D, MODEL>::type;
@@ -763,51 +729,66 @@ __device__ __forceinline__ int polish_voxel_dw(const float* __restrict__ Fc, flo
     dw F[NN];
 #pragma unroll
     for (int p = 0; p < NN; ++p) F[p] = dw{Fc[p * V + v], Fc[(NN + p) * V + v]};
-    int it = 0;
-    bool done = false;
-    {
-        dw g[NN];
-        if (grad_dw<D, MODEL>(F, mu, lam, Bm, g)) {
-            const Law m{mu.hi, lam.hi};
-            float Ff[NN], aux[Law::NAUX], gf[NN], df[NN];
+    conv = false;
+    dw g[NN];
+    if (grad_dw<D, MODEL>(F, mu, lam, Bm, g)) {
+        const Law m{mu.hi, lam.hi};
+        float Ff[NN], aux[Law::NAUX], gf[NN], df[NN];
 #pragma unroll
-            for (int p = 0; p < NN; ++p) {
-                Ff[p] = F[p].hi;
-                gf[p] = g[p].hi;
-            }
-            if constexpr (MODEL == kNeoHooke) aux[NN] = det_cof<float, D>(Ff, aux);
-            else aux[0] = 1.f;
-            bool ok = MODEL != kNeoHooke || aux[NN] > 0.f;
-            if (ok) {
-                float Hf[NP];
-                m.hess(aux, rho.hi, Hf);
-                ok = chol_solve<float, NN>(Hf, gf, df);
-            }
-            float slope = 0.f, size = 0.f;
+        for (int p = 0; p < NN; ++p) {
+            Ff[p] = F[p].hi;
+            gf[p] = g[p].hi;
+        }
+        if constexpr (MODEL == kNeoHooke) aux[NN] = det_cof<float, D>(Ff, aux);
+        else aux[0] = 1.f;
+        bool ok = MODEL != kNeoHooke || aux[NN] > 0.f;
+        if (ok) {
+            float Hf[NP];
+            m.hess(aux, rho.hi, Hf);
+            ok = chol_solve<float, NN>(Hf, gf, df);
+        }
+        float slope = 0.f, size = 0.f;
 #pragma unroll
-            for (int p = 0; p < NN; ++p) {
-                slope += gf[p] * df[p];
-                size = fmaxf(size, fabsf(df[p]));
-            }
-            if (ok && slope < 0.f && size <= NewtonConst<float>::big && m.small_step_safe(aux, size)) {
+        for (int p = 0; p < NN; ++p) {
+            slope += gf[p] * df[p];
+            size = fmaxf(size, fabsf(df[p]));
+        }
+        float t = 1.f;
+        if (ok && slope < 0.f && size <= NewtonConst<float>::big && m.small_step_safe(aux, size)) {
+            conv = true;  // the one refinement step
+        } else {
+            // Rare (a large or unsafe step, a failed factorisation): a damped step
+            // instead of a full local solve -- the Newton direction, or steepest descent
+            // where that does not descend, shortened to the trust size and halved until J
+            // stays positive; the next iteration continues from it.
+            if (!(ok && slope < 0.f)) {
+                const float sc = 1.f / (mu.hi + rho.hi);
+                size = 0.f;
 #pragma unroll
                 for (int p = 0; p < NN; ++p) {
-                    F[p] = dw_add_f(F[p], df[p]);
-                    e[p] = df[p] - e[p];
+                    df[p] = -gf[p] * sc;
+                    size = fmaxf(size, fabsf(df[p]));
                 }
-                it = 1;
-                conv = true;
-                done = true;
             }
-        }
-    }
-    if (!done) {
+            t = size > NewtonConst<float>::big ? NewtonConst<float>::big / size : 1.f;
+            int h = 0;
+            for (; h < 30; ++h) {
+                float Ft[NN];
 #pragma unroll
-        for (int p = 0; p < NN; ++p) Rio[p * V + v] = e[p];
-        const int r = polish_fallback<D, MODEL>(Fc, Fn, Lhi, Llo, Rio, mu.hi, mu.lo, lam.hi, lam.lo, rho.hi, rho.lo,
-                                                cap, tol, v, V);
-        conv = (r >> 16) != 0;
-        return r & 0xffff;
+                for (int p = 0; p < NN; ++p) Ft[p] = Ff[p] + t * df[p];
+                if (det<float, D>(Ft) > 0.f) break;
+                t *= 0.5f;
+            }
+            if (h == 30 || !(size < 1e30f)) t = 0.f;
+        }
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            F[p] = dw_add_f(F[p], t * df[p]);
+            e[p] = t * df[p] - e[p];
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < NN; ++p) e[p] = -e[p];  // inverted state: F stays, R_{k+1} = -e
     }
 #pragma unroll
     for (int p = 0; p < NN; ++p) {
@@ -815,7 +796,7 @@ __device__ __forceinline__ int polish_voxel_dw(const float* __restrict__ Fc, flo
         Fn[(NN + p) * V + v] = F[p].lo;
         Rio[p * V + v] = e[p];
     }
-    return it;
+    return 1;
 }
 
 // ------------------------------------------------------------------ liquid crystal elastomer
@@ -1484,8 +1465,8 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             const dw mu{__ldg(L.mat32 + ph * nparam), __ldg(L.mat32lo + ph * nparam)};
             const dw lam{__ldg(L.mat32 + ph * nparam + 1), __ldg(L.mat32lo + ph * nparam + 1)};
             bool conv;
-            const int it = polish_voxel_dw<D, MODEL>(Fc_dw, Fn_dw, L.LH32, L.LL32, Rout, dG, mu, lam, rho_dw, cap,
-                                                     (double)ntol, v, V, spf, sdf, conv);
+            const int it = polish_voxel_dw<D, MODEL>(Fc_dw, Fn_dw, L.LH32, L.LL32, Rout, dG, mu, lam, rho_dw, v, V,
+                                                     spf, sdf, conv);
             rp2a += spf;
             rd2a += sdf;
             nmax = max(nmax, it);
