@@ -628,9 +628,17 @@ def bench_lce256(torch, rve, synth, iters=40):
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     s.close()
+    # the same 40 iterations in plain FP64: the mixed result's stress error (untimed)
+    s64 = rve.Rve(3, n, "lce", "fp64", max_iter=iters)
+    s64.set_material(ph, par, n0)
+    s64.solve(Fb, RHO, -1.0)
+    S64 = s64.stress()
+    s64.close()
+    err = float(np.max(np.abs(S - S64)) / np.max(np.abs(S64)))
     return {"workload": "lce256", "value": ph.size * info.iterations / (ms / 1e3), "unit": UNIT,
             "ms": ms, "iterations": info.iterations, "fp64_iterations": info.fp64_iterations,
-            "r_p": info.r_p, "r_d": info.r_d, "stress_xx": float(S[0, 0]), "precision": "mixed"}
+            "r_p": info.r_p, "r_d": info.r_d, "stress_xx": float(S[0, 0]), "precision": "mixed",
+            "stress_rel_err_vs_fp64": err}
 
 
 def bench_lce_path128(torch, rve, synth, incompressible=False, steps=5, iters=30, precision="fp64"):
@@ -789,11 +797,12 @@ def bench_batch64(torch, rve, synth, count=64):
             "precision": "mixed"}
 
 
-# LCE serving requests are one implicit time step (Section 5.1's dissipation, R27) with the
-# network's viscosity over the step, nu_F / (mu dt) = 5.6 (Section 5.3's values), and the same
-# value for the director, so that every request reaches the tolerance (with Section 5.3's
-# director viscosity, 0.0106, the director field keeps relaxing for hundreds of iterations)
-SERVE_LCE_VISC = 5.6
+# LCE serving requests are one implicit time step (Section 5.1's dissipation, R27):
+# nu_F / (mu dt) = 20, i.e. Section 5.3's network viscosity with a step of 0.0056 s (a
+# quarter of its 0.02 s), and the same value for the director.  At Section 5.3's own values
+# (5.6 and 0.0106) the director field of the larger polydomain cells keeps relaxing for
+# more than 1000 iterations; at 20 every request reaches the tolerance in 45-75 iterations.
+SERVE_LCE_VISC = 20.0
 
 
 def serving_inputs(synth, stream):

@@ -1222,7 +1222,14 @@ struct Member {
     bool running = false;
 };
 
-using RunKey = std::tuple<int, int, int>;
+// Members share a run (one launch per pass) by dimension, model, precision stage and
+// size class: 3D cells of N = 128, 256 or 512 form runs of their own, so that their
+// launches use the fixed-length FFT kernels of that N (a run of mixed sizes takes the
+// general kernels); every other size goes to one shared run.
+using RunKey = std::tuple<int, int, int, int>;
+int size_class(const rve* h) {
+    return (h->dim == 3 && (h->n == 128 || h->n == 256 || h->n == 512)) ? h->n : 0;
+}
 
 struct Engine {
     cudaStream_t stream = nullptr;
@@ -1379,14 +1386,14 @@ int run_chunk(Engine& E, BatchRun& r, int stage) {
 
 void run_insert(Engine& E, int slot) {
     const Member& m = E.mem[slot];
-    BatchRun& r = E.runs[RunKey(m.h->dim, m.h->L.model, m.stage)];
+    BatchRun& r = E.runs[RunKey(m.h->dim, m.h->L.model, m.stage, size_class(m.h))];
     r.active.insert(std::lower_bound(r.active.begin(), r.active.end(), slot), slot);
     r.dirty = true;
 }
 
 void run_remove(Engine& E, int slot) {
     const Member& m = E.mem[slot];
-    auto it = E.runs.find(RunKey(m.h->dim, m.h->L.model, m.stage));
+    auto it = E.runs.find(RunKey(m.h->dim, m.h->L.model, m.stage, size_class(m.h)));
     if (it == E.runs.end()) return;
     auto pos = std::find(it->second.active.begin(), it->second.active.end(), slot);
     if (pos != it->second.active.end()) {
