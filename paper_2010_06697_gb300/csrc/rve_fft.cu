@@ -274,7 +274,99 @@ __device__ __forceinline__ void xfwd_tile(const Launch& L, int bid) {
         const T* F_c1 = F + (long long)(c * D + 1) * Vn;
         const T* L_c0 = INCR ? nullptr : Lam + (long long)(c * D + 0) * Vn;
         const T* L_c1 = INCR ? nullptr : Lam + (long long)(c * D + 1) * Vn;
-        for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) {
+        bool vectorised = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if ((n & 3) == 0) {
+                vectorised = true;
+                // four consecutive x per thread (n a multiple of 4): float4 loads of the
+                // centre row and of the y and z neighbour rows (fields 256-byte aligned); the
+                // x neighbours of the end elements come from the adjacent lanes, or from memory
+                // at a line's ends (periodic wrap) and at a warp's ends.  Every lane of a warp
+                // runs every pass of the loop, so the shuffles see full warps.  The same
+                // arithmetic per element, in the same order, as the scalar form below.
+                const int lane = threadIdx.x & 31;
+                const int total = lpb * n / 4;
+                for (int base = 0; base < total; base += blockDim.x) {
+                    const int qd = base + threadIdx.x;
+                    const int e = 4 * qd;
+                    const int l = (int)fdiv(e, plan.div_n);
+                    const int x = e - l * n;
+                    const int line = line0 + l;
+                    const bool act = qd < total && line < nlines;
+                    const long long v = (long long)line * n + x;
+                    long long yp = v, ym = v, zp = v, zm = v;
+                    if (act) {
+                        const int zq = (int)fdiv(line, plan.div_n);
+                        const int y = line - zq * n;
+                        yp = v + (y + 1 == n ? (1 - n) * sn : sn);
+                        ym = v + (y == 0 ? (n - 1) * sn : -sn);
+                        if constexpr (D == 3) {
+                            zp = v + (zq + 1 == n ? (1 - n) * s2 : s2);
+                            zm = v + (zq == 0 ? (n - 1) * s2 : -s2);
+                        }
+                    }
+                    auto diffs = [&](const float* a0, const float* a1, float* dx, float* dy) {
+                        const float4 ctr = act ? *reinterpret_cast<const float4*>(a0 + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        float left = __shfl_sync(0xffffffffu, ctr.w, (lane + 31) & 31);
+                        float right = __shfl_sync(0xffffffffu, ctr.x, (lane + 1) & 31);
+                        if (act) {
+                            if (x == 0)
+                                left = a0[v + n - 1];
+                            else if (lane == 0)
+                                left = a0[v - 1];
+                            if (x + 4 == n)
+                                right = a0[v + 4 - n];
+                            else if (lane == 31)
+                                right = a0[v + 4];
+                            const float4 p = *reinterpret_cast<const float4*>(a1 + yp);
+                            const float4 m = *reinterpret_cast<const float4*>(a1 + ym);
+                            dy[0] = p.x - m.x;
+                            dy[1] = p.y - m.y;
+                            dy[2] = p.z - m.z;
+                            dy[3] = p.w - m.w;
+                        }
+                        dx[0] = ctr.y - left;
+                        dx[1] = ctr.z - ctr.x;
+                        dx[2] = ctr.w - ctr.y;
+                        dx[3] = right - ctr.z;
+                    };
+                    auto zdiff = [&](const float* a2, float* dz) {
+                        const float4 u = *reinterpret_cast<const float4*>(a2 + zp);
+                        const float4 d = *reinterpret_cast<const float4*>(a2 + zm);
+                        dz[0] = u.x - d.x;
+                        dz[1] = u.y - d.y;
+                        dz[2] = u.z - d.z;
+                        dz[3] = u.w - d.w;
+                    };
+                    float fx[4], fy[4] = {}, fz[4] = {}, lx[4], ly[4] = {}, lz[4] = {};
+                    diffs(F_c0, F_c1, fx, fy);
+                    if (!INCR) diffs(L_c0, L_c1, lx, ly);
+                    if constexpr (D == 3) {
+                        if (act) {
+                            zdiff(F + (long long)(c * D + 2) * Vn, fz);
+                            if (!INCR) zdiff(Lam + (long long)(c * D + 2) * Vn, lz);
+                        }
+                    }
+                    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (act) {
+                        float r[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            T q = fx[k] + fy[k];
+                            if (!INCR) q -= (lx[k] + ly[k]) * inv_rho;
+                            if constexpr (D == 3) {
+                                q += fz[k];
+                                if (!INCR) q -= lz[k] * inv_rho;
+                            }
+                            r[k] = -q * half_n;
+                        }
+                        o = make_float4(r[0], r[1], r[2], r[3]);
+                    }
+                    if (qd < total) *reinterpret_cast<float4*>(Ar + e) = o;
+                }
+            }
+        }
+        for (int idx = threadIdx.x; !vectorised && idx < lpb * n; idx += blockDim.x) {
             const int l = (int)fdiv(idx, plan.div_n);
             const int x = idx - l * n;
             const int line = line0 + l;
@@ -385,7 +477,21 @@ __device__ __forceinline__ void xinv_tile(const Launch& L, int bid) {
         const T* Xr = reinterpret_cast<const T*>(X);
         TO* O_c = Out + (long long)c * Vn;
         const TO* I_c = In + (long long)c * Vn;
-        for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) {
+        bool vectorised = false;
+        if constexpr (std::is_same<T, float>::value && std::is_same<TO, float>::value && !INCR) {
+            if ((n & 3) == 0) {  // float4 stores of four consecutive x (lines start on 16 bytes)
+                vectorised = true;
+                for (int qd = threadIdx.x; qd < lpb * n / 4; qd += blockDim.x) {
+                    const int e = 4 * qd;
+                    const int l = (int)fdiv(e, plan.div_n);
+                    const int line = line0 + l;
+                    if (line < nlines)
+                        *reinterpret_cast<float4*>(O_c + (long long)line * n + (e - l * n)) =
+                            *reinterpret_cast<const float4*>(Xr + e);
+                }
+            }
+        }
+        for (int idx = threadIdx.x; !vectorised && idx < lpb * n; idx += blockDim.x) {
             const int l = (int)fdiv(idx, plan.div_n);
             const int line = line0 + l;
             if (line < nlines) {
