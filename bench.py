@@ -58,12 +58,11 @@ def bytes_per_voxel(cls: str, s: int, d: int = 3) -> float:
 # DRAM bytes (read + write) per launch measured with ncu on the 128^3 inclusion cell
 # (profiles/), keyed by (kernel class, precision); absent = not captured since the
 # kernel last changed
-TRAFFIC = {("local", "fp32"): 220703232 + 120778240, ("local_r", "fp64"): 421989120 + 358003456,
+TRAFFIC = {("local", "fp32"): 221321216 + 133230080, ("local_r", "fp64"): 418162944 + 338556928,
            ("xfwd", "fp32"): 151019264 + 9842176, ("xinv", "fp32"): 25181952, ("solve", "fp32"): 25196800}
-# FP32 flops (fadd + fmul + 2 ffma, ncu instruction counters) per launch of the float local
-# step, averaged over all 97 of its launches in one solve of the 128^3 inclusion cell,
-# including the launches that exit at once after the stop flag (profiles/)
-FLOPS = {("local", "fp32"): 2.776e9}
+# FP32 flops per launch by kernel class, where counted with ncu for the current kernel
+# (none since the float local step became the closed form: no ALU view is reported)
+FLOPS = {}
 # FP32 peak from unit counts and clock: 128 lanes x 2 flops x 152 SMs x 2.07 GHz
 FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
 
