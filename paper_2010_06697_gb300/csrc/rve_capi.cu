@@ -206,6 +206,7 @@ int begin_solve(rve* h, const double Fbar[9], double rho, double tol, cudaStream
     for (int i = 0; i < 9; ++i) c.Fbar[i] = c.Fbar_prev[i] = Fbar[i];
     c.free_mask = h->free_mask;
     c.dw_state = 0;
+    c.div_given = 0;
     c.rho = rho;
     c.inv_rho = 1.0 / rho;
     c.mu_ref = o.mu_ref > 0 ? o.mu_ref : h->mu_ref;
@@ -258,12 +259,19 @@ int begin_solve(rve* h, const double Fbar[9], double rho, double tol, cudaStream
     return RVE_OK;
 }
 
+// The polish can start straight from the float state (admm::launch_switch_direct) for
+// the elastic laws without free <F> components; the others begin it with a double local
+// step, a double projection and a double fused pass from the state converted to double.
+bool switch_direct_ok(const rve* h) {
+    return (h->model == admm::kNeoHooke || h->model == admm::kLinear) && h->free_mask == 0;
+}
+
 // The switch of RVE_MIXED from the float phase to the double polish, on stream st.
-int switch_to_double(rve* h, cudaStream_t st) {
+int switch_to_double(rve* h, cudaStream_t st, bool direct) {
     Launch Ls = h->L;
     Ls.stream = st;
     h->launches += 1;
-    if (admm::launch_convert(Ls, true) != cudaSuccess) return RVE_E_CUDA;
+    if (!direct && admm::launch_convert(Ls, true) != cudaSuccess) return RVE_E_CUDA;
     h->state_fp64 = 1;
     h->hctrl->done = admm::kRunning;
     h->hctrl->phase_fp32 = 0;
@@ -275,7 +283,16 @@ int switch_to_double(rve* h, cudaStream_t st) {
     // needs a constant rho, so it keeps the value reached here
     h->hctrl->adaptive = 0;
     h->hctrl->rho_changed = 0;  // a pending redo is subsumed by the polish's first local step
-    return write_ctrl_on(h, st);
+    if (direct) {  // the state becomes double-words and the first x-forward pass takes r
+        h->hctrl->dw_state = 1;
+        h->hctrl->div_given = 1;
+    }
+    if (write_ctrl_on(h, st)) return RVE_E_CUDA;
+    if (direct) {
+        h->launches += 1;
+        if (admm::launch_switch_direct(Ls, st) != cudaSuccess) return RVE_E_CUDA;
+    }
+    return RVE_OK;
 }
 
 int status_of(int done) {
@@ -412,14 +429,14 @@ int capture_chunk(rve* h, bool fp64, bool incr, int slot) {
     return e3 == cudaSuccess ? RVE_OK : RVE_E_CUDA;
 }
 
-int run_phase_body(rve* h, bool fp64, bool polish);
+int run_phase_body(rve* h, bool fp64, bool polish, bool direct);
 
 // Run iterations in one precision until the device sets the stop flag.  polish
 // (RVE_MIXED; rho constant from the switch on): after the first step, one full double projection,
 // then increment projections in float (see admm::launch_fft_incr) with the state
 // of the elastic laws held as double-words; it returns to double on every exit.
-int run_phase(rve* h, bool fp64, bool polish = false) {
-    const int rc = run_phase_body(h, fp64, polish);
+int run_phase(rve* h, bool fp64, bool polish = false, bool direct = false) {
+    const int rc = run_phase_body(h, fp64, polish, direct);
     if (!polish) return rc;
     if (admm::launch_polish_state(h->L, false, h->stream) != cudaSuccess) return RVE_E_CUDA;
     h->launches += 2;
@@ -427,8 +444,10 @@ int run_phase(rve* h, bool fp64, bool polish = false) {
     return read_ctrl(h);
 }
 
-int run_phase_body(rve* h, bool fp64, bool polish) {
-    if (h->prof) {
+int run_phase_body(rve* h, bool fp64, bool polish, bool direct) {
+    // direct: the polish's state is already in place (switch_to_double), no first steps
+    if (direct) {
+    } else if (h->prof) {
         if (ensure_prof_events(h)) return RVE_E_CUDA;
         const size_t last = h->pev.size() - 2;
         CK(cudaEventRecord(h->pev[last], h->stream));
@@ -440,8 +459,8 @@ int run_phase_body(rve* h, bool fp64, bool polish) {
     } else if (admm::launch_local(h->E, fp64, true, false) != cudaSuccess) {
         return RVE_E_CUDA;
     }
-    h->launches += 1;
-    if (polish) {
+    if (!direct) h->launches += 1;
+    if (polish && !direct) {
         if (macro_step(h, true) != cudaSuccess) return RVE_E_CUDA;
         if (admm::launch_fft(h->E, true) != cudaSuccess) return RVE_E_CUDA;
         if (admm::launch_local(h->E, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
@@ -678,8 +697,9 @@ int solve_body(rve* h, const double Fbar[9], double rho, double tol, rve_solve_i
         if (rc) return rc;
         if (o.precision == RVE_MIXED && h->hctrl->done == admm::kSwitch) {
             const long long ksw = h->hctrl->k;
-            if (switch_to_double(h, h->stream)) return RVE_E_CUDA;
-            rc = run_phase(h, true, true);
+            const bool direct = switch_direct_ok(h);
+            if (switch_to_double(h, h->stream, direct)) return RVE_E_CUDA;
+            rc = run_phase(h, true, true, direct);
             if (rc) return rc;
             fp64_iters = (int)(h->hctrl->k - ksw);
         } else if (o.precision == RVE_FP64) {
@@ -1476,16 +1496,19 @@ int engine_tick(Engine& E, std::vector<int>& finished) {
         if (read_ctrl_on(h, E.stream)) return RVE_E_CUDA;
         if (h->opt.precision == RVE_MIXED && m.stage == kStageF32 && h->hctrl->done == admm::kSwitch) {
             m.ksw = h->hctrl->k;
-            if (switch_to_double(h, E.stream)) return RVE_E_CUDA;
-            // the member's first double iterations (local step, one full double projection,
-            // local step writing R) run on its own tile tables
-            admm::Exec Ei = h->E;
-            Ei.stream = E.stream;
-            if (admm::launch_local(Ei, true, true, false) != cudaSuccess) return RVE_E_CUDA;
-            if (admm::launch_fft(Ei, true) != cudaSuccess) return RVE_E_CUDA;
-            if (admm::launch_local(Ei, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
-            if (admm::launch_polish_state(h->L, true, E.stream) != cudaSuccess) return RVE_E_CUDA;
-            h->launches += admm::fft_stages(h->dim) + 4;
+            const bool direct = switch_direct_ok(h);
+            if (switch_to_double(h, E.stream, direct)) return RVE_E_CUDA;
+            if (!direct) {
+                // the member's first double iterations (local step, one full double
+                // projection, local step writing R) run on its own tile tables
+                admm::Exec Ei = h->E;
+                Ei.stream = E.stream;
+                if (admm::launch_local(Ei, true, true, false) != cudaSuccess) return RVE_E_CUDA;
+                if (admm::launch_fft(Ei, true) != cudaSuccess) return RVE_E_CUDA;
+                if (admm::launch_local(Ei, true, false, false, 1) != cudaSuccess) return RVE_E_CUDA;
+                if (admm::launch_polish_state(h->L, true, E.stream) != cudaSuccess) return RVE_E_CUDA;
+                h->launches += admm::fft_stages(h->dim) + 4;
+            }
             m.stage = kStagePolish;
             run_insert(E, slot);
         } else {

@@ -275,7 +275,15 @@ __device__ __forceinline__ void xfwd_tile(const Launch& L, int bid) {
         const T* L_c0 = INCR ? nullptr : Lam + (long long)(c * D + 0) * Vn;
         const T* L_c1 = INCR ? nullptr : Lam + (long long)(c * D + 1) * Vn;
         bool vectorised = false;
-        if constexpr (std::is_same<T, float>::value) {
+        if (INCR && ctrl->div_given) {  // the switch to the polish handed in D^T W itself (D32)
+            vectorised = true;
+            const T* Dg = (const T*)L.D32 + (long long)c * Vn;
+            for (int idx = threadIdx.x; idx < lpb * n; idx += blockDim.x) {
+                const int l = (int)fdiv(idx, plan.div_n);
+                const int line = line0 + l;
+                Ar[idx] = line < nlines ? Dg[(long long)line * n + (idx - l * n)] : T(0);
+            }
+        } else if constexpr (std::is_same<T, float>::value) {
             if ((n & 3) == 0) {
                 vectorised = true;
                 // four consecutive x per thread (n a multiple of 4): float4 loads of the
@@ -704,6 +712,7 @@ __device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid) {
     using Idx = typename std::conditional<INCR, int, long long>::type;
     const int z = line0 >> X::LOGN, y0 = line0 & (N - 1);
     constexpr Idx sn = N, s2 = (Idx)N * N;
+    const bool divg = INCR && ctrl->div_given;
     const Idx zp = (z + 1 == N ? (1 - N) * s2 : s2), zm = (z == 0 ? (N - 1) * s2 : -s2);
     for (int c = 0; c < D; ++c) {
         const T* F_c0 = F + (long long)(c * D + 0) * Vn;
@@ -754,17 +763,25 @@ __device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid) {
                     dz[2] = zu.z - zd.z;
                     dz[3] = zu.w - zd.w;
                 };
-                T fx[4], fy[4], fz[4], lx[4], ly[4], lz[4];
-                diffs(F_c0, F_c1, F_c2, fx, fy, fz);
-                if (!INCR) diffs(L_c0, L_c1, L_c2, lx, ly, lz);
                 T o[4];
+                if (INCR && divg) {  // the switch to the polish handed in D^T W itself (D32)
+                    const float4 g = *reinterpret_cast<const float4*>((const T*)L.D32 + (long long)c * Vn + v);
+                    o[0] = g.x;
+                    o[1] = g.y;
+                    o[2] = g.z;
+                    o[3] = g.w;
+                } else {
+                    T fx[4], fy[4], fz[4], lx[4], ly[4], lz[4];
+                    diffs(F_c0, F_c1, F_c2, fx, fy, fz);
+                    if (!INCR) diffs(L_c0, L_c1, L_c2, lx, ly, lz);
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    T q = fx[r] + fy[r];
-                    if (!INCR) q -= (lx[r] + ly[r]) * inv_rho;
-                    q += fz[r];
-                    if (!INCR) q -= lz[r] * inv_rho;
-                    o[r] = -q * half_n;
+                    for (int r = 0; r < 4; ++r) {
+                        T q = fx[r] + fy[r];
+                        if (!INCR) q -= (lx[r] + ly[r]) * inv_rho;
+                        q += fz[r];
+                        if (!INCR) q -= lz[r] * inv_rho;
+                        o[r] = -q * half_n;
+                    }
                 }
                 stage[(x >> 1) * S + l] = V{o[0], o[1]};  // z_m = r_{2m} + i r_{2m+1}
                 stage[((x >> 1) + 1) * S + l] = V{o[2], o[3]};

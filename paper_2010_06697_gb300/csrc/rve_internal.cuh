@@ -50,6 +50,8 @@ struct Ctrl {
     double Fbar_prev[9]; // <F> of the previous iteration (r_d under mixed control)
     unsigned free_mask;  // mixed control: bit 3i+j set = <F_ij> free, <S_ij> -> 0
     int dw_state;        // 1 while F and Lambda are held as double-words (polish)
+    int div_given;       // 1: the next increment x-forward pass transforms the divergence
+                         // already in D32 (the switch's residual) instead of D^T R
     double stress[9];    // <W_F(F)> of the current state (written by the stress kernel)
     double lam_mean[9];  // <Lambda>
     long long k;         // iterations completed over the handle's life: F_k, u~_k live in buffer k & 1
@@ -223,6 +225,9 @@ cudaError_t launch_save_prev(const Launch& L, bool from_fp64, cudaStream_t st);
 cudaError_t launch_macro(const Launch& L, bool fp64, cudaStream_t st, bool dws = false);
 // double <-> double-word state at the ends of the polish of the elastic laws
 cudaError_t launch_polish_state(const Launch& L, bool enter, cudaStream_t st);
+// RVE_MIXED, elastic laws without free <F> components: enter the double-word polish
+// straight from the float state (F_{k+1}, Lambda_k, u~_k at ctrl->k = k), see rve_local.cu
+cudaError_t launch_switch_direct(const Launch& L, cudaStream_t st);
 cudaError_t launch_convert(const Launch& L, bool to_fp64);
 // rve_fft.cu
 cudaError_t launch_fft(const Exec& E, bool fp64, int stage = -1);

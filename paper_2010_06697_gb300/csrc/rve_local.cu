@@ -1720,6 +1720,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
         }
     }
     c->rho_changed = 0;
+    c->div_given = 0;  // the switch's divergence has been transformed by now
     if (done == kRunning && c->adaptive) {  // eq. rho-update (He, Yang & Wang)
         double nr = rhod;
         if (r_d > 0.0 && r_p / r_d > c->rho_tau)
@@ -2081,6 +2082,96 @@ __global__ void k_polish_flag(Ctrl* __restrict__ ctrl, int enter) {
     if (enter ? (ctrl->done == kRunning && !ctrl->dw_state) : ctrl->dw_state) ctrl->dw_state = enter;
 }
 
+// ------------------------------------------------------------------ direct switch to the polish
+// RVE_MIXED, elastic laws, no free <F> components.  When the float phase stops (ctrl->k =
+// k) the state is Lambda_k, u~_k and the last fused pass's local result F_{k+1}, all float.
+// The polish's increment form needs u~_{k+1} = P(Q_{k+1}), Q_{k+1} = F_{k+1} - Lambda_k/rho,
+// to double precision (every later projection adds to it).  With the float u~_k as a first
+// approximation, u~_{k+1} = u~_k + delta where delta solves D^T D delta = r,
+//   r = D^T (Q_{k+1} - D u~_k)
+//     = -sum_j [ (F_ij(x+e_j) - F_ij(x-e_j)) - (Lambda_ij(x+e_j) - Lambda_ij(x-e_j)) / rho
+//                - (u_i(x+2e_j) - 2 u_i(x) + u_i(x-2e_j)) n/2 ] n/2,
+// of the order of the ADMM residuals and formed here in double from the float values
+// (exact in double), so that the float spectral solve of it (the increment passes, with r
+// handed in as the divergence: ctrl->div_given) leaves an error far below the polish
+// tolerance.  This replaces a double local step, a double projection and a double fused
+// pass.  The kernel also forms R_k = F_{k+1} - G_k (G_k = Fbar + D u~_k) and the polish's
+// state: F_{k+1} as double-words (float, 0) in the double F buffer k & 1 and u~_k in double
+// in the double u buffer k & 1.  R_k and r go to the idle double F buffer (k + 1) & 1: their
+// final places are float buffers that still hold inputs (k_switch_move copies them there).
+template <int D>
+__global__ void k_switch_resid(const Ctrl* __restrict__ ctrl, const float* F32_0, const float* F32_1,
+                               const float* __restrict__ L32, const float* U32_0, const float* U32_1, double* F64_0,
+                               double* F64_1, double* U64_0, double* U64_1, long long V, int n, FastDiv dn) {
+    constexpr int NN = D * D;
+    const int par = (int)(ctrl->k & 1);
+    const float* __restrict__ Fn = par ? F32_0 : F32_1;  // F_{k+1}: buffer (k + 1) & 1
+    const float* __restrict__ U = par ? U32_1 : U32_0;   // u~_k: buffer k & 1
+    float* __restrict__ Fdw = reinterpret_cast<float*>(par ? F64_1 : F64_0);
+    float* __restrict__ scr = reinterpret_cast<float*>(par ? F64_0 : F64_1);
+    double* __restrict__ Ud = par ? U64_1 : U64_0;
+    const double rho = ctrl->rho;
+    const double hn = 0.5 * (double)n;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        const unsigned q = fdiv((unsigned)v, dn);
+        const int c[3] = {(int)(v - (long long)q * n), D == 3 ? (int)(q - fdiv(q, dn) * (unsigned)n) : (int)q,
+                          D == 3 ? (int)fdiv(q, dn) : 0};
+        // voxel index of the neighbour s steps along axis j (periodic)
+        auto at = [&](int j, int st) -> long long {
+            int cc[3] = {c[0], c[1], c[2]};
+            cc[j] = (cc[j] + st + 2 * n) % n;
+            return ((long long)cc[2] * n + cc[1]) * n + cc[0];
+        };
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const float* u = U + (long long)i * V;
+            const double uc = (double)u[v];
+            double r = 0.0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const long long p1 = at(j, 1), m1 = at(j, -1);
+                const float* Fc = Fn + (long long)(i * D + j) * V;
+                const float* Lc = L32 + (long long)(i * D + j) * V;
+                const double lap = ((double)u[at(j, 2)] - 2.0 * uc + (double)u[at(j, -2)]) * hn;
+                r -= (((double)Fc[p1] - (double)Fc[m1]) - ((double)Lc[p1] - (double)Lc[m1]) / rho - lap) * hn;
+                const double G = ctrl->Fbar[i * 3 + j] + ((double)u[p1] - (double)u[m1]) * hn;
+                scr[(long long)(i * D + j) * V + v] = (float)((double)Fc[v] - G);
+            }
+            scr[(long long)(NN + i) * V + v] = (float)r;
+            Ud[(long long)i * V + v] = uc;
+        }
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            Fdw[(long long)p * V + v] = Fn[(long long)p * V + v];
+            Fdw[(long long)(NN + p) * V + v] = 0.f;
+        }
+    }
+}
+
+// Second half of the direct switch (pointwise): R_k to R32, r to D32, Lambda's low words
+// to zero (its high words are the float Lambda_k already in place); flags the double-word
+// state and the divergence for the next increment x-forward pass.
+template <int D>
+__global__ void k_switch_move(Ctrl* __restrict__ ctrl, const double* F64_0, const double* F64_1,
+                              float* __restrict__ R32, float* __restrict__ D32, float* __restrict__ LL32, long long V) {
+    constexpr int NN = D * D;
+    const int par = (int)(ctrl->k & 1);
+    const float* __restrict__ scr = reinterpret_cast<const float*>(par ? F64_0 : F64_1);
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            R32[(long long)p * V + v] = scr[(long long)p * V + v];
+            LL32[(long long)p * V + v] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) D32[(long long)i * V + v] = scr[(long long)(NN + i) * V + v];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->div_given = 1;
+        ctrl->dw_state = 1;
+    }
+}
+
 cudaError_t launch_polish_state(const Launch& L, bool enter, cudaStream_t st) {
     if (is_lce(L.model)) return cudaSuccess;  // the LCE polish stays in double
     const int blocks = L.local_blocks;
@@ -2091,6 +2182,20 @@ cudaError_t launch_polish_state(const Launch& L, bool enter, cudaStream_t st) {
         k_polish_state<2><<<blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.L64, L.LH32, L.LL32, L.V,
                                                    enter ? 1 : 0);
     k_polish_flag<<<1, 1, 0, st>>>(L.ctrl, enter ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_switch_direct(const Launch& L, cudaStream_t st) {
+    const int blocks = 152 * 8;
+    if (L.dim == 3) {
+        k_switch_resid<3><<<blocks, 256, 0, st>>>(L.ctrl, L.F32[0], L.F32[1], L.L32, L.U32[0], L.U32[1], L.F64[0],
+                                                  L.F64[1], L.U64[0], L.U64[1], L.V, L.n, L.plan.div_n);
+        k_switch_move<3><<<blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.R32, L.D32, L.LL32, L.V);
+    } else {
+        k_switch_resid<2><<<blocks, 256, 0, st>>>(L.ctrl, L.F32[0], L.F32[1], L.L32, L.U32[0], L.U32[1], L.F64[0],
+                                                  L.F64[1], L.U64[0], L.U64[1], L.V, L.n, L.plan.div_n);
+        k_switch_move<2><<<blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.R32, L.D32, L.LL32, L.V);
+    }
     return cudaGetLastError();
 }
 
