@@ -39,6 +39,55 @@ def test_two_gloo_ranks_combine_max_time_and_total_work():
         assert out[0] == out[1] == (150.0, 3e6)
 
 
+def _rank_solve(rank, world, port, out):
+    """Each rank drives its own solve (the FP64 oracle on a small cell stands in for the
+    GPU solve, which needs a device): replicas with different loads, no data-path
+    collective; only the timing and work aggregation crosses ranks."""
+    import time
+    import numpy as np
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_2010_06697_gb300 import synth
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ph = synth.inclusion_phase(8, 3, 10 + rank, radius=2)
+    par = synth.two_phase_params(1.0, 10.0)
+    Fbar = np.diag([0.95 - 0.01 * rank, 1.0, 1.0])
+    dist.barrier()
+    t0 = time.perf_counter()
+    r = oracle.admm_solve(ph, par, Fbar, 10.0, 1e-8, 300)
+    ms = 1e3 * (time.perf_counter() - t0)
+    dist.barrier()
+    tot_ms, tot_vox = bench.combine_ranks(ms, ph.size * r["iters"], dist, "cpu")
+    out[rank] = (ms, ph.size * r["iters"], tot_ms, tot_vox, r["stress"].tolist(), r["converged"])
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_each_drive_a_solve():
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        mp.start_processes(_rank_solve, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+        r0, r1 = out[0], out[1]
+    assert r0[5] and r1[5]
+    # whole-job figures: the slowest rank's time, the sum of the work, the same on both ranks
+    assert r0[2] == r1[2] == max(r0[0], r1[0])
+    assert r0[3] == r1[3] == r0[1] + r1[1]
+    # replicas are independent: each rank's result is its solve alone
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import oracle
+    from paper_2010_06697_gb300 import synth
+    for rank, r in ((0, r0), (1, r1)):
+        ph = synth.inclusion_phase(8, 3, 10 + rank, radius=2)
+        ref = oracle.admm_solve(ph, synth.two_phase_params(1.0, 10.0), np.diag([0.95 - 0.01 * rank, 1.0, 1.0]),
+                                10.0, 1e-8, 300)
+        assert np.array_equal(np.array(r[4]), ref["stress"])
+
+
 def test_single_rank_is_identity():
     sys.path.insert(0, ROOT)
     import bench
