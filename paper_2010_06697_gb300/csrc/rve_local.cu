@@ -2091,16 +2091,22 @@ __global__ void k_polish_flag(Ctrl* __restrict__ ctrl, int enter) {
 //   r = D^T (Q_{k+1} - D u~_k)
 //     = -sum_j [ (F_ij(x+e_j) - F_ij(x-e_j)) - (Lambda_ij(x+e_j) - Lambda_ij(x-e_j)) / rho
 //                - (u_i(x+2e_j) - 2 u_i(x) + u_i(x-2e_j)) n/2 ] n/2,
-// of the order of the ADMM residuals and formed here in double from the float values
-// (exact in double), so that the float spectral solve of it (the increment passes, with r
-// handed in as the divergence: ctrl->div_given) leaves an error far below the polish
-// tolerance.  This replaces a double local step, a double projection and a double fused
-// pass.  The kernel also forms R_k = F_{k+1} - G_k (G_k = Fbar + D u~_k) and the polish's
-// state: F_{k+1} as double-words (float, 0) in the double F buffer k & 1 and u~_k in double
-// in the double u buffer k & 1.  R_k and r go to the idle double F buffer (k + 1) & 1: their
-// final places are float buffers that still hold inputs (k_switch_move copies them there).
+// of the order of the ADMM residuals.  It is formed from the float values in double-word
+// arithmetic: the differences of two floats are exact pairs (two_sum), 1/rho is a float
+// pair, and the sum carries about 44 bits, so the rounding left in r is that of its final
+// float store, and the float spectral solve of it (the increment passes, with r handed in
+// as the divergence: ctrl->div_given) leaves an error far below the polish tolerance.
+// (Plain double arithmetic gives the same values but runs on the FP64 pipe: 1.07 ms per
+// 128^3 switch against the float pipe's few tens of us.)  This replaces a double local
+// step, a double projection and a double fused pass.  The kernel also forms
+// R_k = F_{k+1} - G_k (G_k = Fbar + D u~_k, again as a pair, stored rounded to float) and
+// the polish's state: F_{k+1} as double-words (float, 0) in the double F buffer k & 1 and
+// u~_k in double in the double u buffer k & 1.  R_k and r go to the idle double F buffer
+// (k + 1) & 1: their final places are float buffers that still hold inputs
+// (k_switch_move copies them there).  n >= 4, so one conditional wrap finds every
+// neighbour up to two voxels away.
 template <int D>
-__global__ void k_switch_resid(const Ctrl* __restrict__ ctrl, const float* F32_0, const float* F32_1,
+__global__ void __launch_bounds__(256, 2) k_switch_resid(const Ctrl* __restrict__ ctrl, const float* F32_0, const float* F32_1,
                                const float* __restrict__ L32, const float* U32_0, const float* U32_1, double* F64_0,
                                double* F64_1, double* U64_0, double* U64_1, long long V, int n, FastDiv dn) {
     constexpr int NN = D * D;
@@ -2110,35 +2116,50 @@ __global__ void k_switch_resid(const Ctrl* __restrict__ ctrl, const float* F32_0
     float* __restrict__ Fdw = reinterpret_cast<float*>(par ? F64_1 : F64_0);
     float* __restrict__ scr = reinterpret_cast<float*>(par ? F64_0 : F64_1);
     double* __restrict__ Ud = par ? U64_1 : U64_0;
-    const double rho = ctrl->rho;
-    const double hn = 0.5 * (double)n;
+    __shared__ dw Fb[NN + 1];  // Fbar as double-words, then 1/rho
+    if (threadIdx.x <= NN)
+        Fb[threadIdx.x] = dw_from(threadIdx.x < NN ? ctrl->Fbar[(threadIdx.x / D) * 3 + threadIdx.x % D] : 1.0 / ctrl->rho);
+    __syncthreads();
+    const dw irho = Fb[NN];
+    const float hn = 0.5f * (float)n;  // exact: n <= 512
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
         const unsigned q = fdiv((unsigned)v, dn);
         const int c[3] = {(int)(v - (long long)q * n), D == 3 ? (int)(q - fdiv(q, dn) * (unsigned)n) : (int)q,
                           D == 3 ? (int)fdiv(q, dn) : 0};
-        // voxel index of the neighbour s steps along axis j (periodic)
-        auto at = [&](int j, int st) -> long long {
-            int cc[3] = {c[0], c[1], c[2]};
-            cc[j] = (cc[j] + st + 2 * n) % n;
-            return ((long long)cc[2] * n + cc[1]) * n + cc[0];
-        };
+        // offsets of the neighbours 1 and 2 voxels away along each axis (periodic)
+        int o1p[D], o1m[D], o2p[D], o2m[D];  // |offset| < n^2 <= 2^18
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const int sj = j == 0 ? 1 : (j == 1 ? n : n * n);
+            auto off = [&](int s) {
+                int t = c[j] + s;
+                t += t < 0 ? n : 0;
+                t -= t >= n ? n : 0;
+                return (t - c[j]) * sj;
+            };
+            o1p[j] = off(1);
+            o1m[j] = off(-1);
+            o2p[j] = off(2);
+            o2m[j] = off(-2);
+        }
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const float* u = U + (long long)i * V;
-            const double uc = (double)u[v];
-            double r = 0.0;
+            const float* u = U + (long long)i * V + v;
+            const float uc = u[0];
+            dw acc{0.f, 0.f};
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const long long p1 = at(j, 1), m1 = at(j, -1);
-                const float* Fc = Fn + (long long)(i * D + j) * V;
-                const float* Lc = L32 + (long long)(i * D + j) * V;
-                const double lap = ((double)u[at(j, 2)] - 2.0 * uc + (double)u[at(j, -2)]) * hn;
-                r -= (((double)Fc[p1] - (double)Fc[m1]) - ((double)Lc[p1] - (double)Lc[m1]) / rho - lap) * hn;
-                const double G = ctrl->Fbar[i * 3 + j] + ((double)u[p1] - (double)u[m1]) * hn;
-                scr[(long long)(i * D + j) * V + v] = (float)((double)Fc[v] - G);
+                const float* Fc = Fn + (long long)(i * D + j) * V + v;
+                const float* Lc = L32 + (long long)(i * D + j) * V + v;
+                const dw dF = two_sum(Fc[o1p[j]], -Fc[o1m[j]]);
+                const dw dL = two_sum(Lc[o1p[j]], -Lc[o1m[j]]);
+                const dw lap = dw_add_f(two_sum(u[o2p[j]], u[o2m[j]]), -2.f * uc);
+                acc = dw_add(acc, dw_sub(dw_sub(dF, dw_mul(dL, irho)), dw_mul_f(lap, hn)));
+                const dw G = dw_add(Fb[i * D + j], dw_mul_f(two_sum(u[o1p[j]], -u[o1m[j]]), hn));
+                scr[(long long)(i * D + j) * V + v] = dw_add_f(dw_neg(G), Fc[0]).hi;
             }
-            scr[(long long)(NN + i) * V + v] = (float)r;
-            Ud[(long long)i * V + v] = uc;
+            scr[(long long)(NN + i) * V + v] = dw_mul_f(acc, -hn).hi;
+            Ud[(long long)i * V + v] = (double)uc;
         }
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
