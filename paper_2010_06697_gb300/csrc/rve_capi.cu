@@ -207,6 +207,7 @@ int begin_solve(rve* h, const double Fbar[9], double rho, double tol, cudaStream
     c.free_mask = h->free_mask;
     c.dw_state = 0;
     c.div_given = 0;
+    c.z_valid = 0;
     c.rho = rho;
     c.inv_rho = 1.0 / rho;
     c.mu_ref = o.mu_ref > 0 ? o.mu_ref : h->mu_ref;
@@ -283,6 +284,7 @@ int switch_to_double(rve* h, cudaStream_t st, bool direct) {
     // needs a constant rho, so it keeps the value reached here
     h->hctrl->adaptive = 0;
     h->hctrl->rho_changed = 0;  // a pending redo is subsumed by the polish's first local step
+    h->hctrl->z_valid = 0;
     if (direct) {  // the state becomes double-words and the first x-forward pass takes r
         h->hctrl->dw_state = 1;
         h->hctrl->div_given = 1;

@@ -52,6 +52,7 @@ struct Ctrl {
     int dw_state;        // 1 while F and Lambda are held as double-words (polish)
     int div_given;       // 1: the next increment x-forward pass transforms the divergence
                          // already in D32 (the switch's residual) instead of D^T R
+    int z_valid;         // polish: 1 once the linearisation offsets Z (double Lambda buffer) are formed
     double stress[9];    // <W_F(F)> of the current state (written by the stress kernel)
     double lam_mean[9];  // <Lambda>
     long long k;         // iterations completed over the handle's life: F_k, u~_k live in buffer k & 1

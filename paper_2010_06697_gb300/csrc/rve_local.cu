@@ -63,9 +63,10 @@ __device__ __forceinline__ double log_t(double x) { return log(x); }
 // ------------------------------------------------------------------ double-word arithmetic
 // A double-word number is the unevaluated sum hi + lo of two floats with |lo| <=
 // ulp(hi) / 2: about 48 significant bits, from FP32 instructions only.  GB300
-// executes FP32 at 64 times its FP64 rate, so the double polish keeps its state and
-// its gradient in this form (polish_voxel_dw).  Error-free transformations: two_sum
-// (Knuth), fast_two_sum (Dekker, needs |a| >= |b| or a = 0), two_prod with an FMA.
+// executes FP32 at 64 times its FP64 rate, so the double polish keeps its state as
+// pairs of floats and forms its linearisation offsets in this arithmetic
+// (polish_voxel_dev).  Error-free transformations: two_sum (Knuth), fast_two_sum
+// (Dekker, needs |a| >= |b| or a = 0), two_prod with an FMA.
 // The sum, product and quotient are the double-word algorithms analysed by Joldes,
 // Muller and Popescu, "Tight and rigorous error bounds for basic building blocks of
 // double-word arithmetic", ACM TOMS 44(2), 2017 (relative errors of a few u^2,
@@ -674,7 +675,7 @@ __device__ __forceinline__ bool grad_dw(const dw* F, dw mu, dw lam, const dw* Bm
     }
 }
 
-// Local step of the double polish, one voxel, on double-word state (elastic laws).
+// Local step of the double polish, one voxel, in deviation form (elastic laws).
 //
 // Increment form: with R_k = F_{k+1} - G_k from the previous iteration (float) and
 // dG = G_{k+1} - G_k = <F> change + D(u~_{k+1} - u~_k) (float), e = G_{k+1} - F_{k+1}
@@ -683,70 +684,112 @@ __device__ __forceinline__ bool grad_dw(const dw* F, dw mu, dw lam, const dw* Bm
 // phi at F_{k+1} is W_F(F) - Bm, Bm = Lambda_{k+1} + rho e: neither G nor
 // B = Lambda + rho G is needed.
 //
-// The step is ONE refinement Newton step per iteration, dF = -H_f^{-1} g with the
-// double-word gradient g and the float Hessian H_f, whenever that is a safe full
-// step (no line search, J stays positive): F_{k+2} = F_{k+1} + dF and R_{k+1} =
-// F_{k+2} - G_{k+1} = dF - e.  The local problem is then solved inexactly, with a
-// gradient left of about eps_float cond(H) |g| + c |dF|^2; in the polish |g| and
-// |dF| are of the order of the ADMM residuals, so that error is many orders below
-// them and is corrected by the next iteration's step, which starts from this F (the
-// inexact local solves of Sections 2.1 and 4.2, r_l << r_d).  A fixed point still
-// has an exactly stationary local problem (to the 2^-48 resolution of the state):
-// the step from it is zero only where the gradient vanishes.  Otherwise (a large or
-// unsafe step, a failed factorisation: rare, since the polish starts from a double
-// local solve and moves by residual-sized increments) a damped step is taken and the
-// following iterations continue from it; a voxel whose state is inverted keeps F.
-// All of it inline: an out-of-line fallback made the compiler spill around the call
-// on every voxel.
+// State: F = Fh + Fl and Lambda = Lh + Ll, pairs of floats whose high parts are held
+// fixed while the low parts (the deviations, of the order of the distance the polish
+// moves, far below 1) accumulate the updates.  Each pair carries about 48 significant
+// bits, like a double-word, without being renormalised after every update.  About Fh
+// the gradient is linear to second order:
+//   W_F(F) - Bm = Z + W_FF(Fh) Fl - Ll' - rho e + O(|Fl|^2),
+//   Z = W_F(Fh) - Lh (formed once in double-word arithmetic and stored as a float),
+//   Ll' = Ll + rho e (the new Lambda's low part),
+// where every term is small, so float arithmetic gives it to about 1e-7 of its own
+// size.  The neglected term is at most |W_FFF| |Fl|^2 / 2; the pair is renormalised
+// (two_sum, exact) and Z re-formed whenever max |Fl| exceeds kDevF = 4e-6 (term below
+// about 1e-10 |W_FFF| / 100), likewise when max |Ll| exceeds kDevL = 1e-4 (float
+// accumulation of Lambda's updates within 1e-11), and on the first step of a polish
+// (ctrl->z_valid = 0).  So no double-word arithmetic runs in the common step: the
+// earlier form of this step evaluated W_F(F) itself in double-word arithmetic, about
+// two thirds of its instructions.
 //
-// Storage: F as (hi, lo) float arrays in the double F buffers (hi at p V + v, lo
-// at (d*d + p) V + v), Lambda as (Lhi, Llo), updated in place.  Returns the number
-// of steps (1); conv tells whether it was the full refinement step; sp, sd get the
-// voxel's squared residual terms.
+// The step is ONE refinement Newton step per iteration, dF = -H_f^{-1} g with the
+// float Hessian H_f at Fh, whenever that is a safe full step (no line search, J stays
+// positive): F_{k+2} = F_{k+1} + dF and R_{k+1} = F_{k+2} - G_{k+1} = dF - e.  The
+// local problem is then solved inexactly, with a gradient left of about
+// eps_float cond(H) |g| + c |dF|^2 plus the linearisation term above; in the polish
+// |g| and |dF| are of the order of the ADMM residuals, so that error is many orders
+// below them and is corrected by the next iteration's step, which starts from this F
+// (the inexact local solves of Sections 2.1 and 4.2, r_l << r_d).  A fixed point has
+// a local problem stationary to that linearisation error.  Otherwise (a large or
+// unsafe step, a failed factorisation: rare, since the polish starts from a converged
+// local solve and moves by residual-sized increments) a damped step is taken and the
+// following iterations continue from it; a voxel whose Fh is inverted keeps F.
+//
+// Storage: F as (hi, lo) float arrays in the double F buffers (hi at p V + v, lo at
+// (d*d + p) V + v: the same layout as the double-words of the polish's ends), Lambda
+// as (Lhi, Llo) updated in place, Z in the idle double Lambda buffer.  conv tells
+// whether the step was the full refinement step; sp, sd get the voxel's squared
+// residual terms.
+constexpr float kDevF = 4e-6f;
+constexpr float kDevL = 1e-4f;
+
 template <int D, int MODEL>
-__device__ __forceinline__ int polish_voxel_dw(const float* __restrict__ Fc, float* __restrict__ Fn,
-                                               float* __restrict__ Lhi, float* __restrict__ Llo,
-                                               float* __restrict__ Rio, const float* dG, dw mu, dw lam, dw rho,
-                                               long long v, long long V, float& sp, float& sd, bool& conv) {
+__device__ __forceinline__ void polish_voxel_dev(const float* __restrict__ Fc, float* __restrict__ Fn,
+                                                 float* __restrict__ Lhi, float* __restrict__ Llo,
+                                                 float* __restrict__ Zb, float* __restrict__ Rio, const float* dG,
+                                                 dw mu, dw lam, float rho, bool fresh, long long v, long long V,
+                                                 float& sp, float& sd, bool& conv) {
     constexpr int NN = D * D;
     constexpr int NP = NN * (NN + 1) / 2;
     using Law = typename LawOf<float, D, MODEL>::type;
-    float e[NN];
-    dw Bm[NN];
+    float e[NN], hi[NN], lo[NN], ll[NN], z[NN];
     sp = 0.f;
     sd = 0.f;
+    bool ren = fresh;
 #pragma unroll
     for (int p = 0; p < NN; ++p) {
         e[p] = dG[p] - Rio[p * V + v];
         sp += e[p] * e[p];
         sd += dG[p] * dG[p];
-        const dw re = dw_mul_f(rho, e[p]);
-        const dw lam_new = dw_add(dw{Lhi[p * V + v], Llo[p * V + v]}, re);
-        Lhi[p * V + v] = lam_new.hi;
-        Llo[p * V + v] = lam_new.lo;
-        Bm[p] = dw_add(lam_new, re);
+        hi[p] = Fc[p * V + v];
+        lo[p] = Fc[(NN + p) * V + v];
+        ll[p] = Llo[p * V + v];
+        ren |= fabsf(lo[p]) > kDevF || fabsf(ll[p]) > kDevL;
     }
-    dw F[NN];
-#pragma unroll
-    for (int p = 0; p < NN; ++p) F[p] = dw{Fc[p * V + v], Fc[(NN + p) * V + v]};
-    conv = false;
-    dw g[NN];
-    if (grad_dw<D, MODEL>(F, mu, lam, Bm, g)) {
-        const Law m{mu.hi, lam.hi};
-        float Ff[NN], aux[Law::NAUX], gf[NN], df[NN];
+    if (ren) {  // rare: renormalise both pairs, Z from the new high parts
+        dw F[NN], Bm[NN], g[NN];
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
-            Ff[p] = F[p].hi;
-            gf[p] = g[p].hi;
+            const dw f = two_sum(hi[p], lo[p]);
+            const dw l = two_sum(Lhi[p * V + v], ll[p]);
+            hi[p] = f.hi;
+            lo[p] = f.lo;
+            ll[p] = l.lo;
+            Lhi[p * V + v] = l.hi;
+            F[p] = dw{f.hi, 0.f};
+            Bm[p] = dw{l.hi, 0.f};
         }
-        if constexpr (MODEL == kNeoHooke) aux[NN] = det_cof<float, D>(Ff, aux);
-        else aux[0] = 1.f;
-        bool ok = MODEL != kNeoHooke || aux[NN] > 0.f;
-        if (ok) {
-            float Hf[NP];
-            m.hess(aux, rho.hi, Hf);
-            ok = chol_solve<float, NN>(Hf, gf, df);
+        const bool ok = grad_dw<D, MODEL>(F, mu, lam, Bm, g);
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            z[p] = ok ? g[p].hi : 0.f;
+            Zb[p * V + v] = z[p];
         }
+    } else {
+#pragma unroll
+        for (int p = 0; p < NN; ++p) z[p] = Zb[p * V + v];
+    }
+#pragma unroll
+    for (int p = 0; p < NN; ++p) {
+        ll[p] += rho * e[p];  // Lambda_{k+1} - Lh
+        Llo[p * V + v] = ll[p];
+    }
+    const Law m{mu.hi, lam.hi};
+    float aux[Law::NAUX];
+    if constexpr (MODEL == kNeoHooke) aux[NN] = det_cof<float, D>(hi, aux);
+    else aux[0] = 1.f;
+    conv = false;
+    if (MODEL != kNeoHooke || aux[NN] > 0.f) {
+        float Hf[NP], gf[NN], df[NN];
+        m.hess(aux, rho, Hf);
+        // g = Z + (H_f - rho I) Fl - Ll' - rho e, H_f packed lower
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            float w = -rho * lo[p];
+#pragma unroll
+            for (int q = 0; q < NN; ++q) w += Hf[p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p] * lo[q];
+            gf[p] = (z[p] + w) - (ll[p] + rho * e[p]);
+        }
+        const bool ok = chol_solve<float, NN>(Hf, gf, df);
         float slope = 0.f, size = 0.f;
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
@@ -762,7 +805,7 @@ __device__ __forceinline__ int polish_voxel_dw(const float* __restrict__ Fc, flo
             // where that does not descend, shortened to the trust size and halved until J
             // stays positive; the next iteration continues from it.
             if (!(ok && slope < 0.f)) {
-                const float sc = 1.f / (mu.hi + rho.hi);
+                const float sc = 1.f / (mu.hi + rho);
                 size = 0.f;
 #pragma unroll
                 for (int p = 0; p < NN; ++p) {
@@ -775,7 +818,7 @@ __device__ __forceinline__ int polish_voxel_dw(const float* __restrict__ Fc, flo
             for (; h < 30; ++h) {
                 float Ft[NN];
 #pragma unroll
-                for (int p = 0; p < NN; ++p) Ft[p] = Ff[p] + t * df[p];
+                for (int p = 0; p < NN; ++p) Ft[p] = hi[p] + (lo[p] + t * df[p]);
                 if (det<float, D>(Ft) > 0.f) break;
                 t *= 0.5f;
             }
@@ -783,7 +826,7 @@ __device__ __forceinline__ int polish_voxel_dw(const float* __restrict__ Fc, flo
         }
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
-            F[p] = dw_add_f(F[p], t * df[p]);
+            lo[p] += t * df[p];
             e[p] = t * df[p] - e[p];
         }
     } else {
@@ -792,11 +835,10 @@ __device__ __forceinline__ int polish_voxel_dw(const float* __restrict__ Fc, flo
     }
 #pragma unroll
     for (int p = 0; p < NN; ++p) {
-        Fn[p * V + v] = F[p].hi;
-        Fn[(NN + p) * V + v] = F[p].lo;
+        Fn[p * V + v] = hi[p];
+        Fn[(NN + p) * V + v] = lo[p];
         Rio[p * V + v] = e[p];
     }
-    return 1;
 }
 
 // ------------------------------------------------------------------ liquid crystal elastomer
@@ -1352,8 +1394,8 @@ k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const 
 // DU (same polish, after its first iteration): the float increment
 // u~_{k+1} - u~_k written by the increment projection is read instead of u~_k,
 // and G_{k+1} - G_k = D(u~_{k+1} - u~_k) for r_d is formed in float.  For the
-// elastic laws this iteration runs in increment form on double-word state (INC,
-// polish_voxel_dw): F and Lambda are float pairs, and at ctrl->k = k the state
+// elastic laws this iteration runs in increment form on pairs of floats (INC,
+// polish_voxel_dev): F and Lambda are float pairs, and at ctrl->k = k the state
 // F_{k+1} sits in F buffer k & 1 (one parity off the double convention) so that
 // the conversions at the polish's ends read and write different buffers.
 // One tile = block `bid` of the RVE's local grid (L.local_blocks blocks).  FIRST
@@ -1414,6 +1456,10 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     const float* Fc_dw = reinterpret_cast<const float*>(par ? F1 : F0);
     float* Fn_dw = reinterpret_cast<float*>(par ? F0 : F1);
     const dw rho_dw = INC ? dw_from(ctrl->rho) : dw{0.f, 0.f};
+    // deviation form of the polish: Z = W_F(F_hi) - Lambda_hi per voxel in the idle double
+    // Lambda buffer, formed on the polish's first step
+    float* Zlin = reinterpret_cast<float*>(L.L64);
+    const bool z_fresh = INC && !ctrl->z_valid;
     const int cap = ctrl->newton_cap;
     const T ntol = (T)ctrl->newton_tol;
     // inexact local steps (Section 2.1): |grad phi| <= f mu_ref r_d, with r_d of the
@@ -1465,11 +1511,11 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
             const dw mu{__ldg(L.mat32 + ph * nparam), __ldg(L.mat32lo + ph * nparam)};
             const dw lam{__ldg(L.mat32 + ph * nparam + 1), __ldg(L.mat32lo + ph * nparam + 1)};
             bool conv;
-            const int it = polish_voxel_dw<D, MODEL>(Fc_dw, Fn_dw, L.LH32, L.LL32, Rout, dG, mu, lam, rho_dw, v, V,
-                                                     spf, sdf, conv);
+            polish_voxel_dev<D, MODEL>(Fc_dw, Fn_dw, L.LH32, L.LL32, Zlin, Rout, dG, mu, lam, rho_dw.hi, z_fresh, v,
+                                       V, spf, sdf, conv);
             rp2a += spf;
             rd2a += sdf;
-            nmax = max(nmax, it);
+            nmax = max(nmax, 1);
             nfail += conv ? 0 : 1;
             continue;
         }
@@ -1721,6 +1767,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     }
     c->rho_changed = 0;
     c->div_given = 0;  // the switch's divergence has been transformed by now
+    if (INC) c->z_valid = 1;  // the polish's first step has formed Z at every voxel
     if (done == kRunning && c->adaptive) {  // eq. rho-update (He, Yang & Wang)
         double nr = rhod;
         if (r_d > 0.0 && r_p / r_d > c->rho_tau)
@@ -2079,7 +2126,10 @@ __global__ void k_polish_state(Ctrl* __restrict__ ctrl, double* F0, double* F1, 
 // Flips ctrl->dw_state after the conversion (a separate launch: every block of
 // k_polish_state reads the flag first).
 __global__ void k_polish_flag(Ctrl* __restrict__ ctrl, int enter) {
-    if (enter ? (ctrl->done == kRunning && !ctrl->dw_state) : ctrl->dw_state) ctrl->dw_state = enter;
+    if (enter ? (ctrl->done == kRunning && !ctrl->dw_state) : ctrl->dw_state) {
+        ctrl->dw_state = enter;
+        ctrl->z_valid = 0;
+    }
 }
 
 // ------------------------------------------------------------------ direct switch to the polish
@@ -2190,6 +2240,7 @@ __global__ void k_switch_move(Ctrl* __restrict__ ctrl, const double* F64_0, cons
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctrl->div_given = 1;
         ctrl->dw_state = 1;
+        ctrl->z_valid = 0;
     }
 }
 
