@@ -734,7 +734,7 @@ void rve_default_options(rve_options* o) {
     o->rho_tau = 10.0;
     o->rho_min = 0.0;
     o->mu_ref = 0.0;
-    o->mixed_switch = 3e-7;
+    o->mixed_switch = 4e-7;
     o->check_every = 16;
     o->use_graph = 1;
     o->local_ratio = 0.0;
