@@ -41,6 +41,9 @@ struct rve {
     bool own_ws = false;
     Launch L{};
     admm::Exec E{};         // tile-table execution of this RVE alone
+    const Launch* self_mem[1] = {nullptr};   // E's member list: this RVE
+    unsigned char self_exact[1] = {0};
+    int self_tile0[1] = {0};
     Launch* d_L = nullptr;  // device copy of L (the descriptor the tile kernels read)
     Ctrl* hctrl = nullptr;  // pinned host mirror of the control block
     bool material_set = false;
@@ -672,6 +675,12 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
         }
         E.uniform_n = n;
         E.exact_local = (o.local_ratio == 0.0 && o.local_fraction == 0.0) ? 1 : 0;
+        h->self_mem[0] = &h->L;
+        h->self_exact[0] = (unsigned char)E.exact_local;
+        E.nmem = 1;
+        E.mem = h->self_mem;
+        E.mem_exact = h->self_exact;
+        E.mem_tile0 = h->self_tile0;
     }
     h->state_fp64 = o.precision == RVE_FP64 ? 1 : 0;
     h->hctrl->hist_cap = o.max_iter + 1;
@@ -1231,6 +1240,9 @@ enum Stage : int { kStageF32 = 0, kStageF64 = 1, kStagePolish = 2 };
 struct BatchRun {  // members of one (dim, model, stage) still iterating
     std::vector<int> active;  // slots
     admm::Exec E{};
+    std::vector<const Launch*> mem;     // E's member list, in the order of active
+    std::vector<unsigned char> mem_exact;
+    std::vector<int> mem_tile0;
     int2* d_tiles[admm::kTileClasses] = {};
     int cap[admm::kTileClasses] = {};
     cudaGraphExec_t graph = nullptr;
@@ -1355,10 +1367,22 @@ int run_upload(Engine& E, BatchRun& r) {
     r.E.rep = &E.mem[r.active.front()].h->L;
     r.E.uniform_n = E.mem[r.active.front()].h->n;
     r.E.exact_local = 1;
+    r.mem.clear();
+    r.mem_exact.clear();
+    r.mem_tile0.clear();
+    int tile0 = 0;
     for (int slot : r.active) {
         if (E.mem[slot].h->n != r.E.uniform_n) r.E.uniform_n = 0;
         if (!E.mem[slot].h->E.exact_local) r.E.exact_local = 0;
+        r.mem.push_back(&E.mem[slot].h->L);
+        r.mem_exact.push_back((unsigned char)E.mem[slot].h->E.exact_local);
+        r.mem_tile0.push_back(tile0);
+        tile0 += admm::tiles_local(E.mem[slot].h->L);
     }
+    r.E.nmem = (int)r.mem.size();
+    r.E.mem = r.mem.data();
+    r.E.mem_exact = r.mem_exact.data();
+    r.E.mem_tile0 = r.mem_tile0.data();
     for (int f = 0; f < 2; ++f) {
         r.E.smem_x[f] = 0;
         r.E.smem_a[f] = 0;

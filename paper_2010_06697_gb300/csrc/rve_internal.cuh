@@ -185,6 +185,15 @@ struct Exec {
     int exact_local;              // 1: no member takes approximate local steps (local_ratio,
                                   // local_fraction both 0): the float neo-Hookean law in 3D
                                   // then runs its closed-form local step
+    // the members in tile-table order: host copies of their descriptors, whether each takes
+    // exact local steps, and the index of each one's first tile in tiles[kTilesLocal].  In
+    // launches of one grid size N = 128, 256 or 512 the fused local pass of the float
+    // neo-Hookean law in 3D runs per member (k_local_cf for exact local steps), so that a
+    // member's kernel does not depend on the others
+    int nmem;
+    const Launch* const* mem;
+    const unsigned char* mem_exact;
+    const int* mem_tile0;
 };
 
 // FFT geometry of one grid shape: x-pass lines per block and half-length radices,

@@ -1280,6 +1280,11 @@ __device__ __forceinline__ void grad_u(const T* __restrict__ U, long long V, con
     }
 }
 
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -1378,6 +1383,185 @@ k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const 
     }
 }
 
+// End of one tile of the fused pass (not the local-step-only pass): block sums of the
+// thread partials r_p^2, r_d^2, r_l^2 (warp sums in the threads' accumulator type, float
+// in the float kernels, whose FP64 pipe is 1/64 of the FP32 rate; sums across warps and
+// tiles in double), the largest Newton count and the failures go to the tile's slot of
+// the partial buffer; the last tile of the RVE to
+// finish (atomic counter) sums all slots in a fixed order, so the result does not
+// depend on block scheduling, and runs the control step: residuals of iteration k,
+// stop flag, precision switch, adaptive rho.  INC: the increment form of the polish.
+template <int D, bool INC, typename Acc>
+__device__ __forceinline__ void finish_pass(Ctrl* __restrict__ ctrl, double* __restrict__ hist,
+                                            double* __restrict__ partials, int bid, int nblk, long long V,
+                                            long long k, Acc rp2a, Acc rd2a, Acc rl2a, int nmax, int nfail,
+                                            bool frac_on, const int* s_hist) {
+    __shared__ double s_sum[kLocalThreads / 32][3];
+    __shared__ int s_int[kLocalThreads / 32][2];
+    __shared__ int s_last;
+
+    // block partials: r_p^2, r_d^2 sums (double), Newton max / failures
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double rp2 = (double)warp_sum(rp2a);
+    const double rd2 = (double)warp_sum(rd2a);
+    const double rl2 = (double)warp_sum(rl2a);
+    nmax = warp_max(nmax);
+    for (int o = 16; o > 0; o >>= 1) nfail += __shfl_down_sync(0xffffffffu, nfail, o);
+    if (lane == 0) {
+        s_sum[warp][0] = rp2;
+        s_sum[warp][1] = rd2;
+        s_sum[warp][2] = rl2;
+        s_int[warp][0] = nmax;
+        s_int[warp][1] = nfail;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, cl = 0;
+        int mx = 0, nf = 0;
+        for (int w = 0; w < kLocalThreads / 32; ++w) {
+            a += s_sum[w][0];
+            b += s_sum[w][1];
+            cl += s_sum[w][2];
+            mx = max(mx, s_int[w][0]);
+            nf += s_int[w][1];
+        }
+        double* pp = partials + (size_t)bid * kPartialStride;
+        pp[0] = a;
+        pp[1] = b;
+        pp[2] = (double)mx;
+        pp[3] = (double)nf;
+        pp[4] = cl;
+        if (frac_on)
+            for (int b = 0; b < kNewtonBins; ++b)
+                if (s_hist[b]) atomicAdd(&ctrl->newton_hist[b], (unsigned)s_hist[b]);
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctrl->counter, 1u);
+        s_last = (prev == nblk - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+
+    // last block: fixed-order sum over all block partials
+    double a = 0, b = 0, cl = 0;
+    int mx = 0;
+    double nf = 0;
+    for (int i = threadIdx.x; i < (int)nblk; i += blockDim.x) {
+        const double* pp = partials + (size_t)i * kPartialStride;
+        a += __ldcg(pp + 0);
+        b += __ldcg(pp + 1);
+        mx = max(mx, (int)__ldcg(pp + 2));
+        nf += __ldcg(pp + 3);
+        cl += __ldcg(pp + 4);
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    cl = warp_sum(cl);
+    nf = warp_sum(nf);
+    mx = warp_max(mx);
+    if (lane == 0) {
+        s_sum[warp][0] = a;
+        s_sum[warp][1] = b;
+        s_sum[warp][2] = cl;
+        s_int[warp][0] = mx;
+        s_int[warp][1] = (int)nf;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    a = 0;
+    b = 0;
+    cl = 0;
+    mx = 0;
+    long long nft = 0;
+    for (int w = 0; w < kLocalThreads / 32; ++w) {
+        a += s_sum[w][0];
+        b += s_sum[w][1];
+        cl += s_sum[w][2];
+        mx = max(mx, s_int[w][0]);
+        nft += s_int[w][1];
+    }
+    Ctrl* c = ctrl;
+    const double rhod = c->rho;
+    if (!INC) {
+        double dm = 0.0;  // |<F>_{k+1} - <F>_k|^2 (mixed control)
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) {
+                const double x = c->Fbar[i * 3 + j] - c->Fbar_prev[i * 3 + j];
+                dm += x * x;
+            }
+        b += dm * (double)V;
+    }
+    const double r_p = sqrt(a / (double)V);
+    const double r_d = rhod / c->mu_ref * sqrt(b / (double)V);
+    const long long idx = k - c->k_start;
+    const double r_l = sqrt(cl / (double)V) / c->mu_ref;
+    if (idx >= 0 && idx < c->hist_cap) {
+        hist[kHistStride * idx + 0] = r_p;
+        hist[kHistStride * idx + 1] = r_d;
+        hist[kHistStride * idx + 2] = rhod;
+        hist[kHistStride * idx + 3] = r_l;
+    }
+    c->r_p = r_p;
+    c->rd_local = c->r_d;
+    c->r_d = r_d;
+    c->r_l = r_l;
+    c->k = k + 1;
+    c->newton_max = mx;
+    c->newton_fail = (unsigned long long)nft;
+    if (frac_on) {
+        // the smallest even count by which a fraction p of the voxels converged; if
+        // fewer converged within the cap, raise the cap by 2 (up to the configured one)
+        const double need = c->local_fraction * (double)V;
+        int cap_next = min(c->newton_cap + 2, c->newton_cap_max);
+        double cum = 0.0;
+        bool found = false;
+        for (int bin = 0; bin < kNewtonBins; ++bin) {
+            cum += (double)__ldcg(&c->newton_hist[bin]);
+            if (!found && cum >= need) {
+                cap_next = min(2 * (bin + 1), c->newton_cap_max);
+                found = true;
+            }
+            c->newton_hist[bin] = 0u;
+        }
+        c->newton_cap = cap_next;
+    }
+    int done = kRunning;
+    if (!(isfinite(r_p) && isfinite(r_d))) {
+        done = kNumerical;
+    } else if (r_p <= c->tol && r_d <= c->tol) {
+        done = kConverged;
+    } else if (k + 1 >= c->k_cap) {
+        done = kCapped;
+    } else if (c->phase_fp32) {
+        const double mres = fmax(r_p, r_d);
+        if (mres <= c->switch_tol) {
+            done = kSwitch;
+        } else if (mres < 0.9 * c->best) {
+            c->best = mres;
+            c->stall = 0;
+        } else if (++c->stall >= 10) {
+            done = kSwitch;
+        }
+    }
+    c->rho_changed = 0;
+    c->div_given = 0;  // the switch's divergence has been transformed by now
+    if (INC) c->z_valid = 1;  // the polish's first step has formed Z at every voxel
+    if (done == kRunning && c->adaptive) {  // eq. rho-update (He, Yang & Wang)
+        double nr = rhod;
+        if (r_d > 0.0 && r_p / r_d > c->rho_tau)
+            nr = c->rho_kappa * rhod;
+        else if (r_p > 0.0 && r_d / r_p > c->rho_tau)
+            nr = fmax(rhod / c->rho_kappa, c->rho_min);
+        if (nr != rhod) {
+            c->rho = nr;
+            c->inv_rho = 1.0 / nr;
+            c->rho_changed = 1;
+        }
+    }
+    c->done = done;
+    c->counter = 0u;
+}
+
 // The fused per-iteration kernel.  With FIRST = false, at iteration index k
 // (k iterations done): reads u~_{k+1}, u~_k, F_{k+1}, Lambda_k; writes
 // Lambda_{k+1} (Step 3), accumulates r_p, r_d of iteration k (Step 4) and runs
@@ -1422,9 +1606,6 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     const float* __restrict__ DUin = L.D32;
     const Dirs<T> dir = Set<T>::dirs(L);
     const int nblk = L.local_blocks;
-    __shared__ double s_sum[kLocalThreads / 32][3];
-    __shared__ int s_int[kLocalThreads / 32][2];
-    __shared__ int s_last;
     __shared__ int s_hist[kNewtonBins];       // fraction-converged local steps
 
     // the increment form needs the previous iteration's R: never the first step of a run
@@ -1620,168 +1801,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
         }
     }
     if (FIRST) return;
-
-    // block partials: r_p^2, r_d^2 sums (double), Newton max / failures
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double rp2 = (double)rp2a, rd2 = (double)rd2a, rl2 = (double)rl2a;
-    rp2 = warp_sum(rp2);
-    rd2 = warp_sum(rd2);
-    rl2 = warp_sum(rl2);
-    nmax = warp_max(nmax);
-    for (int o = 16; o > 0; o >>= 1) nfail += __shfl_down_sync(0xffffffffu, nfail, o);
-    if (lane == 0) {
-        s_sum[warp][0] = rp2;
-        s_sum[warp][1] = rd2;
-        s_sum[warp][2] = rl2;
-        s_int[warp][0] = nmax;
-        s_int[warp][1] = nfail;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0, b = 0, cl = 0;
-        int mx = 0, nf = 0;
-        for (int w = 0; w < kLocalThreads / 32; ++w) {
-            a += s_sum[w][0];
-            b += s_sum[w][1];
-            cl += s_sum[w][2];
-            mx = max(mx, s_int[w][0]);
-            nf += s_int[w][1];
-        }
-        double* pp = partials + (size_t)bid * kPartialStride;
-        pp[0] = a;
-        pp[1] = b;
-        pp[2] = (double)mx;
-        pp[3] = (double)nf;
-        pp[4] = cl;
-        if (frac_on)
-            for (int b = 0; b < kNewtonBins; ++b)
-                if (s_hist[b]) atomicAdd(&ctrl->newton_hist[b], (unsigned)s_hist[b]);
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctrl->counter, 1u);
-        s_last = (prev == nblk - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-
-    // last block: fixed-order sum over all block partials
-    double a = 0, b = 0, cl = 0;
-    int mx = 0;
-    double nf = 0;
-    for (int i = threadIdx.x; i < (int)nblk; i += blockDim.x) {
-        const double* pp = partials + (size_t)i * kPartialStride;
-        a += __ldcg(pp + 0);
-        b += __ldcg(pp + 1);
-        mx = max(mx, (int)__ldcg(pp + 2));
-        nf += __ldcg(pp + 3);
-        cl += __ldcg(pp + 4);
-    }
-    a = warp_sum(a);
-    b = warp_sum(b);
-    cl = warp_sum(cl);
-    nf = warp_sum(nf);
-    mx = warp_max(mx);
-    if (lane == 0) {
-        s_sum[warp][0] = a;
-        s_sum[warp][1] = b;
-        s_sum[warp][2] = cl;
-        s_int[warp][0] = mx;
-        s_int[warp][1] = (int)nf;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    a = 0;
-    b = 0;
-    cl = 0;
-    mx = 0;
-    long long nft = 0;
-    for (int w = 0; w < kLocalThreads / 32; ++w) {
-        a += s_sum[w][0];
-        b += s_sum[w][1];
-        cl += s_sum[w][2];
-        mx = max(mx, s_int[w][0]);
-        nft += s_int[w][1];
-    }
-    Ctrl* c = ctrl;
-    const double rhod = c->rho;
-    if (!INC) {
-        double dm = 0.0;  // |<F>_{k+1} - <F>_k|^2 (mixed control)
-        for (int i = 0; i < D; ++i)
-            for (int j = 0; j < D; ++j) {
-                const double x = c->Fbar[i * 3 + j] - c->Fbar_prev[i * 3 + j];
-                dm += x * x;
-            }
-        b += dm * (double)V;
-    }
-    const double r_p = sqrt(a / (double)V);
-    const double r_d = rhod / c->mu_ref * sqrt(b / (double)V);
-    const long long idx = k - c->k_start;
-    const double r_l = sqrt(cl / (double)V) / c->mu_ref;
-    if (idx >= 0 && idx < c->hist_cap) {
-        hist[kHistStride * idx + 0] = r_p;
-        hist[kHistStride * idx + 1] = r_d;
-        hist[kHistStride * idx + 2] = rhod;
-        hist[kHistStride * idx + 3] = r_l;
-    }
-    c->r_p = r_p;
-    c->rd_local = c->r_d;
-    c->r_d = r_d;
-    c->r_l = r_l;
-    c->k = k + 1;
-    c->newton_max = mx;
-    c->newton_fail = (unsigned long long)nft;
-    if (frac_on) {
-        // the smallest even count by which a fraction p of the voxels converged; if
-        // fewer converged within the cap, raise the cap by 2 (up to the configured one)
-        const double need = c->local_fraction * (double)V;
-        int cap_next = min(c->newton_cap + 2, c->newton_cap_max);
-        double cum = 0.0;
-        bool found = false;
-        for (int bin = 0; bin < kNewtonBins; ++bin) {
-            cum += (double)__ldcg(&c->newton_hist[bin]);
-            if (!found && cum >= need) {
-                cap_next = min(2 * (bin + 1), c->newton_cap_max);
-                found = true;
-            }
-            c->newton_hist[bin] = 0u;
-        }
-        c->newton_cap = cap_next;
-    }
-    int done = kRunning;
-    if (!(isfinite(r_p) && isfinite(r_d))) {
-        done = kNumerical;
-    } else if (r_p <= c->tol && r_d <= c->tol) {
-        done = kConverged;
-    } else if (k + 1 >= c->k_cap) {
-        done = kCapped;
-    } else if (c->phase_fp32) {
-        const double mres = fmax(r_p, r_d);
-        if (mres <= c->switch_tol) {
-            done = kSwitch;
-        } else if (mres < 0.9 * c->best) {
-            c->best = mres;
-            c->stall = 0;
-        } else if (++c->stall >= 10) {
-            done = kSwitch;
-        }
-    }
-    c->rho_changed = 0;
-    c->div_given = 0;  // the switch's divergence has been transformed by now
-    if (INC) c->z_valid = 1;  // the polish's first step has formed Z at every voxel
-    if (done == kRunning && c->adaptive) {  // eq. rho-update (He, Yang & Wang)
-        double nr = rhod;
-        if (r_d > 0.0 && r_p / r_d > c->rho_tau)
-            nr = c->rho_kappa * rhod;
-        else if (r_p > 0.0 && r_d / r_p > c->rho_tau)
-            nr = fmax(rhod / c->rho_kappa, c->rho_min);
-        if (nr != rhod) {
-            c->rho = nr;
-            c->inv_rho = 1.0 / nr;
-            c->rho_changed = 1;
-        }
-    }
-    c->done = done;
-    c->counter = 0u;
+    finish_pass<D, INC, Acc>(ctrl, hist, partials, bid, nblk, V, k, rp2a, rd2a, rl2a, nmax, nfail, frac_on, s_hist);
 }
 
 
@@ -1803,6 +1823,132 @@ k_local(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntil
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tl = tiles[t];
         local_tile<T, D, MODEL, WRITE_R, DU, CF>(rds[tl.x], tl.y, first != 0, only_if_rho_changed);
+        __syncthreads();
+    }
+}
+
+// The fused pass of one RVE for the float neo-Hookean law in 3D with exact local steps
+// (closed-form Step 1) on an N^3 grid, N = 128, 256 or 512: the same steps, sums and
+// tile partials as local_tile's closed-form instance, arranged so that the voxel loop
+// keeps few values in registers.  The RVE's buffers and constants are kernel parameters
+// (read from the constant bank where they are used), the grid size is a compile-time
+// constant (neighbours by shifts and masks, 32-bit offsets: 9 N^3 < 2^31), Fbar is read
+// from shared memory, and the previous iterate F_{k+1} is not held through the local
+// solve (its rare fallback reloads it).  local_tile's instance keeps the RVE descriptor
+// of each tile in registers and spills at the register cap of 6 blocks per SM (at 128^3:
+// 133 us per launch there, 108 us here).  F and Lambda are read and written with
+// evict-first hints (each value is touched once per pass), which leaves L1 and L2 to the
+// u~ stencils.
+struct CfArgs {
+    Ctrl* ctrl;
+    double* hist;
+    double* partials;
+    float* F[2];
+    float* Lam;
+    const float* U[2];
+    const uint8_t* phase;
+    const float* mat;
+    int nparam;
+    int nblk;    // tiles of the RVE's local grid
+    int chunk;   // voxels of a tile per sweep
+    float half_n;
+};
+
+template <int N>
+__global__ void __launch_bounds__(kLocalThreads, kCfMinBlocks)
+k_local_cf(const __grid_constant__ CfArgs a, int first, int only_if_rho_changed) {
+    static_assert(N == 128 || N == 256 || N == 512, "fixed grid sizes");
+    constexpr int LOG = N == 128 ? 7 : (N == 256 ? 8 : 9);
+    constexpr int V = N * N * N;
+    constexpr int NN = 9;
+    __shared__ float s_fb[NN];
+    Ctrl* __restrict__ ctrl = a.ctrl;
+    const bool FIRST = first != 0;
+    if (ctrl->done) return;
+    if (FIRST && only_if_rho_changed && !ctrl->rho_changed) return;
+    const long long k = ctrl->k;
+    // buffers as in local_tile: F_{k+1}, u~_{k+1} in buffer (k + 1) & 1 for the fused
+    // pass, F_k, u~_k in buffer k & 1 for the local step alone
+    const bool q = FIRST ? !(k & 1) : (k & 1);
+    const float* __restrict__ Fcur = q ? a.F[0] : a.F[1];
+    float* __restrict__ Fnext = q ? a.F[1] : a.F[0];
+    const float* __restrict__ Unew = q ? a.U[0] : a.U[1];
+    const float* __restrict__ Uold = q ? a.U[1] : a.U[0];
+    const float rho = (float)ctrl->rho;
+    const int cap = ctrl->newton_cap;
+    const float ntol = (float)ctrl->newton_tol;
+    if (threadIdx.x < NN) s_fb[threadIdx.x] = (float)ctrl->Fbar[(threadIdx.x / 3) * 3 + threadIdx.x % 3];
+    __syncthreads();
+    const volatile float* Fb = s_fb;
+    const float hn = a.half_n;
+    for (int t = blockIdx.x; t < a.nblk; t += gridDim.x) {
+        float rp2a = 0.f, rd2a = 0.f;
+        int nmax = 0, nfail = 0;
+        for (int v = t * a.chunk + threadIdx.x; threadIdx.x < a.chunk && v < V; v += a.nblk * a.chunk) {
+            const int x = v & (N - 1), y = (v >> LOG) & (N - 1), z = v >> (2 * LOG);
+            const int xp = v + (x == N - 1 ? 1 - N : 1), xm = v + (x == 0 ? N - 1 : -1);
+            const int yp = v + (y == N - 1 ? (1 - N) * N : N), ym = v + (y == 0 ? (N - 1) * N : -N);
+            const int zp = v + (z == N - 1 ? (1 - N) * N * N : N * N), zm = v + (z == 0 ? (N - 1) * N * N : -N * N);
+            float G[NN], L[NN], F[NN];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float* u = Unew + i * V;
+                G[3 * i + 0] = Fb[3 * i + 0] + (__ldg(u + xp) - __ldg(u + xm)) * hn;
+                G[3 * i + 1] = Fb[3 * i + 1] + (__ldg(u + yp) - __ldg(u + ym)) * hn;
+                G[3 * i + 2] = Fb[3 * i + 2] + (__ldg(u + zp) - __ldg(u + zm)) * hn;
+            }
+#pragma unroll
+            for (int p = 0; p < NN; ++p) {
+                L[p] = __ldcs(a.Lam + p * V + v);
+                F[p] = __ldcs(Fcur + p * V + v);
+            }
+            const float J0 = det<float, 3>(F);
+            if (!FIRST) {
+                // Steps 3-4 of iteration k (voxel sums in float, tile sums in double)
+                float sp = 0.f, sd = 0.f;
+#pragma unroll
+                for (int p = 0; p < NN; ++p) {
+                    const float df = G[p] - F[p];
+                    L[p] += rho * df;
+                    sp += df * df;
+                    __stcs(a.Lam + p * V + v, L[p]);
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float* u = Uold + i * V;
+                    const float g0 = Fb[3 * i + 0] + (__ldg(u + xp) - __ldg(u + xm)) * hn;
+                    const float g1 = Fb[3 * i + 1] + (__ldg(u + yp) - __ldg(u + ym)) * hn;
+                    const float g2 = Fb[3 * i + 2] + (__ldg(u + zp) - __ldg(u + zm)) * hn;
+                    const float d0 = G[3 * i + 0] - g0, d1 = G[3 * i + 1] - g1, d2 = G[3 * i + 2] - g2;
+                    sd += d0 * d0;
+                    sd += d1 * d1;
+                    sd += d2 * d2;
+                }
+                rp2a += sp;
+                rd2a += sd;
+            }
+            float B[NN];
+#pragma unroll
+            for (int p = 0; p < NN; ++p) B[p] = L[p] + rho * G[p];
+            const NeoHooke<float, 3> m = load_law<NeoHooke<float, 3>, float>(a.phase, a.mat, a.nparam, v);
+            float Fo[NN];
+            int it = 1;
+            bool conv = true;
+            if (!nh3_closed_form(m.mu, m.lam, rho, B, J0, Fo)) {
+#pragma unroll
+                for (int p = 0; p < NN; ++p) Fo[p] = __ldg(Fcur + p * V + v);
+                it = steepest_descent<float, 3>(m, Fo, B, rho, cap, ntol, conv);
+            }
+            nmax = max(nmax, it);
+            nfail += conv ? 0 : 1;
+            // as in local_tile: J <= 0 after the local step means an inverted start
+            if (!conv && !(det<float, 3>(Fo) > 0.f)) rp2a = NAN;
+#pragma unroll
+            for (int p = 0; p < NN; ++p) __stcs(Fnext + p * V + v, Fo[p]);
+        }
+        if (!FIRST)
+            finish_pass<3, false, float>(ctrl, a.hist, a.partials, t, a.nblk, (long long)V, k, rp2a, rd2a, 0.f, nmax,
+                                         nfail, false, nullptr);
         __syncthreads();
     }
 }
@@ -2018,6 +2164,32 @@ cudaError_t run_local(const Exec& E, bool first, bool only_if, int mode) {
         kern<<<grid, kLocalThreads, 0, E.stream>>>(E.rds, tl, nt, is_first, flag);
     };
     if constexpr (std::is_same<T, float>::value && D == 3 && MODEL == kNeoHooke) {
+        const int un = E.uniform_n;
+        if ((un == 128 || un == 256 || un == 512) && E.nmem > 0) {
+            // one launch per member: the lean closed-form kernel, or the Newton instance on
+            // the member's own tiles when it takes approximate local steps
+            for (int i = 0; i < E.nmem; ++i) {
+                const Launch& M = *E.mem[i];
+                if (E.mem_exact[i]) {
+                    const CfArgs a{M.ctrl, M.hist, M.partials, {M.F32[0], M.F32[1]}, M.L32, {M.U32[0], M.U32[1]},
+                                   M.phase, M.mat32, M.nparam, M.local_blocks, M.local_chunk, M.half_n32};
+                    auto lean = [&](auto kern) {
+                        const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, M.local_blocks);
+                        kern<<<grid, kLocalThreads, 0, E.stream>>>(a, first ? 1 : 0, first && only_if ? 1 : 0);
+                    };
+                    if (un == 128) lean(k_local_cf<128>);
+                    else if (un == 256) lean(k_local_cf<256>);
+                    else lean(k_local_cf<512>);
+                } else {
+                    auto kern = k_local<T, D, MODEL, false, false>;
+                    const int ntm = tiles_local(M);
+                    const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, ntm);
+                    kern<<<grid, kLocalThreads, 0, E.stream>>>(E.rds, tl + E.mem_tile0[i], ntm, first ? 1 : 0,
+                                                               first && only_if ? 1 : 0);
+                }
+            }
+            return cudaGetLastError();
+        }
         if (E.exact_local) {
             go(k_local<T, D, MODEL, false, false, true>, first ? 1 : 0, first && only_if ? 1 : 0);
             return cudaGetLastError();
