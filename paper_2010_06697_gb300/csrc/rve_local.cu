@@ -716,17 +716,20 @@ __device__ __forceinline__ bool grad_dw(const dw* F, dw mu, dw lam, const dw* Bm
 //
 // Storage: F as (hi, lo) float arrays in the double F buffers (hi at p V + v, lo at
 // (d*d + p) V + v: the same layout as the double-words of the polish's ends), Lambda
-// as (Lhi, Llo) updated in place, Z in the idle double Lambda buffer.  conv tells
-// whether the step was the full refinement step; sp, sd get the voxel's squared
-// residual terms.
+// as (Lhi, Llo) updated in place, Z in the idle double Lambda buffer.  The high parts
+// change only when renormalised, and then go to both F buffers (the current one is read
+// at this voxel by this thread alone): every voxel renormalises on the polish's first
+// step, so both buffers hold the same high parts from then on and a common step writes
+// only the low parts.  conv tells whether the step was the full refinement step; sp, sd
+// get the voxel's squared residual terms.
 constexpr float kDevF = 4e-6f;
 constexpr float kDevL = 1e-4f;
 
-template <int D, int MODEL>
-__device__ __forceinline__ void polish_voxel_dev(const float* __restrict__ Fc, float* __restrict__ Fn,
+template <int D, int MODEL, typename I>
+__device__ __forceinline__ void polish_voxel_dev(float* __restrict__ Fc, float* __restrict__ Fn,
                                                  float* __restrict__ Lhi, float* __restrict__ Llo,
                                                  float* __restrict__ Zb, float* __restrict__ Rio, const float* dG,
-                                                 dw mu, dw lam, float rho, bool fresh, long long v, long long V,
+                                                 dw mu, dw lam, float rho, bool fresh, I v, I V,
                                                  float& sp, float& sd, bool& conv) {
     constexpr int NN = D * D;
     constexpr int NP = NN * (NN + 1) / 2;
@@ -755,6 +758,8 @@ __device__ __forceinline__ void polish_voxel_dev(const float* __restrict__ Fc, f
             lo[p] = f.lo;
             ll[p] = l.lo;
             Lhi[p * V + v] = l.hi;
+            Fc[p * V + v] = f.hi;
+            Fn[p * V + v] = f.hi;
             F[p] = dw{f.hi, 0.f};
             Bm[p] = dw{l.hi, 0.f};
         }
@@ -835,7 +840,6 @@ __device__ __forceinline__ void polish_voxel_dev(const float* __restrict__ Fc, f
     }
 #pragma unroll
     for (int p = 0; p < NN; ++p) {
-        Fn[p * V + v] = hi[p];
         Fn[(NN + p) * V + v] = lo[p];
         Rio[p * V + v] = e[p];
     }
@@ -1634,7 +1638,7 @@ __device__ __forceinline__ void local_tile(const Launch& L, int bid, const bool 
     const T two_nsq = Set<T>::two_nsq(L);
     const float half_n32 = L.half_n32;
     // double-word polish: F_{k+1} in buffer k & 1 (see above), rho split once
-    const float* Fc_dw = reinterpret_cast<const float*>(par ? F1 : F0);
+    float* Fc_dw = reinterpret_cast<float*>(par ? F1 : F0);
     float* Fn_dw = reinterpret_cast<float*>(par ? F0 : F1);
     const dw rho_dw = INC ? dw_from(ctrl->rho) : dw{0.f, 0.f};
     // deviation form of the polish: Z = W_F(F_hi) - Lambda_hi per voxel in the idle double
@@ -1953,6 +1957,84 @@ k_local_cf(const __grid_constant__ CfArgs a, int first, int only_if_rho_changed)
     }
 }
 
+// The double-word polish step (local_tile's increment form, polish_voxel_dev) of one RVE
+// of an elastic law in 3D on an N^3 grid, N = 128, 256 or 512, laid out like
+// k_local_cf: buffers and constants as kernel parameters, N fixed at compile time,
+// 32-bit offsets.  Same arithmetic and tile partials as the tile-table instance.
+struct PolishArgs {
+    Ctrl* ctrl;
+    double* hist;
+    double* partials;
+    float* F[2];       // the double F buffers holding (hi, lo) float pairs
+    float* Lhi;
+    float* Llo;
+    float* Z;          // the idle double Lambda buffer
+    float* R;          // R = F_{k+2} - G_{k+1}, read and rewritten
+    const float* DU;   // float u~ increment of the last increment projection
+    const uint8_t* phase;
+    const float* mat;
+    const float* mat_lo;
+    int nparam;
+    int nblk;
+    int chunk;
+    float half_n;
+};
+
+template <int N, int MODEL>
+__global__ void __launch_bounds__(kLocalThreads, 4) k_polish_fixed(const __grid_constant__ PolishArgs a) {
+    static_assert(N == 128 || N == 256 || N == 512, "fixed grid sizes");
+    constexpr int LOG = N == 128 ? 7 : (N == 256 ? 8 : 9);
+    constexpr int V = N * N * N;
+    constexpr int NN = 9;
+    __shared__ float s_dfb[NN];
+    Ctrl* __restrict__ ctrl = a.ctrl;
+    if (ctrl->done) return;
+    const long long k = ctrl->k;
+    // F_{k+1} in buffer k & 1 (see local_tile)
+    float* Fc = (k & 1) ? a.F[1] : a.F[0];
+    float* Fn = (k & 1) ? a.F[0] : a.F[1];
+    const float rho = dw_from(ctrl->rho).hi;
+    const bool z_fresh = !ctrl->z_valid;
+    if (threadIdx.x < NN) {
+        const int i = threadIdx.x / 3, j = threadIdx.x % 3;
+        s_dfb[threadIdx.x] = (float)(ctrl->Fbar[i * 3 + j] - ctrl->Fbar_prev[i * 3 + j]);
+    }
+    __syncthreads();
+    const volatile float* dFb = s_dfb;
+    const float hn = a.half_n;
+    for (int t = blockIdx.x; t < a.nblk; t += gridDim.x) {
+        float rp2a = 0.f, rd2a = 0.f;
+        int nmax = 0, nfail = 0;
+        for (int v = t * a.chunk + threadIdx.x; threadIdx.x < a.chunk && v < V; v += a.nblk * a.chunk) {
+            const int x = v & (N - 1), y = (v >> LOG) & (N - 1), z = v >> (2 * LOG);
+            const int xp = v + (x == N - 1 ? 1 - N : 1), xm = v + (x == 0 ? N - 1 : -1);
+            const int yp = v + (y == N - 1 ? (1 - N) * N : N), ym = v + (y == 0 ? (N - 1) * N : -N);
+            const int zp = v + (z == N - 1 ? (1 - N) * N * N : N * N), zm = v + (z == 0 ? (N - 1) * N * N : -N * N);
+            float dG[NN], spf, sdf;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float* u = a.DU + i * V;
+                dG[3 * i + 0] = dFb[3 * i + 0] + (__ldg(u + xp) - __ldg(u + xm)) * hn;
+                dG[3 * i + 1] = dFb[3 * i + 1] + (__ldg(u + yp) - __ldg(u + ym)) * hn;
+                dG[3 * i + 2] = dFb[3 * i + 2] + (__ldg(u + zp) - __ldg(u + zm)) * hn;
+            }
+            const int ph = a.phase[v];
+            const dw mu{__ldg(a.mat + ph * a.nparam), __ldg(a.mat_lo + ph * a.nparam)};
+            const dw lam{__ldg(a.mat + ph * a.nparam + 1), __ldg(a.mat_lo + ph * a.nparam + 1)};
+            bool conv;
+            polish_voxel_dev<3, MODEL, int>(Fc, Fn, a.Lhi, a.Llo, a.Z, a.R, dG, mu, lam, rho, z_fresh, v, V, spf, sdf,
+                                            conv);
+            rp2a += spf;
+            rd2a += sdf;
+            nmax = 1;
+            nfail += conv ? 0 : 1;
+        }
+        finish_pass<3, true, float>(ctrl, a.hist, a.partials, t, a.nblk, (long long)V, k, rp2a, rd2a, 0.f, nmax,
+                                    nfail, false, nullptr);
+        __syncthreads();
+    }
+}
+
 // Mixed macroscopic control (Section 2.3; the UNI, PE and EB protocols of Section
 // 5.3).  The free components of <F> join Step 2's minimisation of
 // |<F> + D u~ - Q|^2, Q = F_{k+1} - Lambda_k / rho; D u~ has zero mean, so their
@@ -2198,6 +2280,27 @@ cudaError_t run_local(const Exec& E, bool first, bool only_if, int mode) {
     if (first) {
         go(k_local<T, D, MODEL, false, false>, 1, only_if ? 1 : 0);
         return cudaGetLastError();
+    }
+    if constexpr (std::is_same<T, double>::value && D == 3 && (MODEL == kNeoHooke || MODEL == kLinear)) {
+        const int un = E.uniform_n;
+        if (mode == 2 && (un == 128 || un == 256 || un == 512) && E.nmem > 0) {
+            // the double-word polish step, one lean launch per member
+            for (int i = 0; i < E.nmem; ++i) {
+                const Launch& M = *E.mem[i];
+                const PolishArgs a{M.ctrl, M.hist, M.partials,
+                                   {reinterpret_cast<float*>(M.F64[0]), reinterpret_cast<float*>(M.F64[1])},
+                                   M.LH32, M.LL32, reinterpret_cast<float*>(M.L64), M.R32, M.D32, M.phase, M.mat32,
+                                   M.mat32lo, M.nparam, M.local_blocks, M.local_chunk, M.half_n32};
+                auto lean = [&](auto kern) {
+                    const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, M.local_blocks);
+                    kern<<<grid, kLocalThreads, 0, E.stream>>>(a);
+                };
+                if (un == 128) lean(k_polish_fixed<128, MODEL>);
+                else if (un == 256) lean(k_polish_fixed<256, MODEL>);
+                else lean(k_polish_fixed<512, MODEL>);
+            }
+            return cudaGetLastError();
+        }
     }
     if constexpr (std::is_same<T, double>::value) {
         if (mode == 1) {
