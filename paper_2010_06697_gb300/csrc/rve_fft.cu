@@ -617,8 +617,10 @@ __device__ __forceinline__ V twiddled(V a, V w) {
 // thread's elements j + T r of column cl, on entry and on exit.  buf: two shared
 // buffers of N * S values (element e of column cl at e S + cl; S >= TK, padded for
 // the x passes); tw: the table exp(-2 pi i m / (N TWS)) (TWS = 2: the half-length
-// transforms of the x passes use every other entry of the grid's table).
-template <int N, bool INV, int TWS = 1, int S = ColPlan<N>::TK, typename V>
+// transforms of the x passes use every other entry of the grid's table).  ONE: a single
+// buffer of N * S values, read and rewritten in place with a barrier in between (the y/z
+// passes: half the shared memory, 1 us less per 128^3 pass).
+template <int N, bool INV, int TWS = 1, int S = ColPlan<N>::TK, bool ONE = false, typename V>
 __device__ __forceinline__ void col_fft(V (&x)[8], V* __restrict__ buf, const V* __restrict__ tw, int j, int cl) {
     using P = ColPlan<N>;
     constexpr int T = P::T, TK = S;
@@ -626,8 +628,8 @@ __device__ __forceinline__ void col_fft(V (&x)[8], V* __restrict__ buf, const V*
 #pragma unroll
     for (int p = 0; p < P::P8; ++p) {
         const int Ns = 1 << (3 * p);
-        V* in = buf + ((p + 1) & 1) * (N * TK);
-        V* out = buf + (p & 1) * (N * TK);
+        V* in = ONE ? buf : buf + ((p + 1) & 1) * (N * TK);
+        V* out = ONE ? buf : buf + (p & 1) * (N * TK);
         const int k = j & (Ns - 1);
         if (p > 0) {
 #pragma unroll
@@ -638,6 +640,7 @@ __device__ __forceinline__ void col_fft(V (&x)[8], V* __restrict__ buf, const V*
         dft8<INV>(x);
         const bool last = (p == P::P8 - 1) && P::RL == 1;
         if (!last) {
+            if (ONE && p > 0) __syncthreads();  // one buffer: this pass's reads are done
 #pragma unroll
             for (int r = 0; r < 8; ++r) out[((j - k) * 8 + r * Ns + k) * TK + cl] = x[r];
             __syncthreads();
@@ -645,7 +648,7 @@ __device__ __forceinline__ void col_fft(V (&x)[8], V* __restrict__ buf, const V*
     }
     if constexpr (P::RL > 1) {
         constexpr int RL = P::RL, Q = 8 / RL, Ns = N / RL;
-        const V* in = buf + ((P::P8 - 1) & 1) * (N * TK);
+        const V* in = ONE ? buf : buf + ((P::P8 - 1) & 1) * (N * TK);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int b = j + T * q;  // butterfly index (< Ns): twiddle exponent b r
@@ -978,9 +981,9 @@ __device__ __forceinline__ void faxis_fixed_tile(const Launch& L, int bid) {
 #pragma unroll
     for (int r = 0; r < 8; ++r) x[r] = S[base + (j + TT * r) * es_g + cl];
     if (MODE == 1) {
-        col_fft<N, true>(x, buf, s_tw, j, cl);
+        col_fft<N, true, 1, TK, true>(x, buf, s_tw, j, cl);
     } else {
-        col_fft<N, false>(x, buf, s_tw, j, cl);
+        col_fft<N, false, 1, TK, true>(x, buf, s_tw, j, cl);
         if (MODE == 2) {
             const T kout = (D == 3) ? __ldg(ksq + outer) : T(0);
             const T kcol = __ldg(ksq + min(col0 + cl, H - 1)) + kout;
@@ -989,7 +992,7 @@ __device__ __forceinline__ void faxis_fixed_tile(const Launch& L, int bid) {
                 const T den = __ldg(ksq + j + TT * r) + kcol;
                 x[r] = cscale(x[r], den > T(0) ? scale / den : T(0));
             }
-            col_fft<N, true>(x, buf, s_tw, j, cl);
+            col_fft<N, true, 1, TK, true>(x, buf, s_tw, j, cl);
         }
     }
 #pragma unroll
@@ -1072,7 +1075,7 @@ constexpr size_t xfixed_smem() {
 
 template <typename T, int N>
 constexpr size_t fixed_smem() {
-    return (size_t)(N + 2 * N * ColPlan<N>::TK) * sizeof(typename Cx<T>::t);
+    return (size_t)(N + N * ColPlan<N>::TK) * sizeof(typename Cx<T>::t);
 }
 
 template <typename K>
