@@ -80,9 +80,9 @@ typedef struct rve_options {
     double mu_ref;      /* modulus in r_d (eq. check); 0 selects the volume average
                            of the per-voxel shear modulus                          */
     double mixed_switch;/* RVE_MIXED: promote to double once max(r_p, r_d) <= this
-                           or float stagnates; default 4e-7 (float r_p levels off
+                           or float stagnates; default 3e-7 (float r_p levels off
                            near 1.3e-7 on O(1) deformation gradients, and float
-                           iterations below about 4e-7 no longer track the
+                           iterations below about 3e-7 no longer track the
                            double iteration)                                       */
     int check_every;    /* host reads the device status every this many iterations */
     int use_graph;      /* 1: replay iteration chunks as a CUDA graph (default 1)  */

@@ -211,6 +211,9 @@ int begin_solve(rve* h, const double Fbar[9], double rho, double tol, cudaStream
     c.dw_state = 0;
     c.div_given = 0;
     c.z_valid = 0;
+    c.spec_have = 0;  // the spectrum kept for r_d is that of an earlier state
+    c.spec_next = 0;
+    c.spec_sum = 0;
     c.rho = rho;
     c.inv_rho = 1.0 / rho;
     c.mu_ref = o.mu_ref > 0 ? o.mu_ref : h->mu_ref;
@@ -645,6 +648,15 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
         L.D32 = L.U32[1];
         L.LH32 = L.L32;
         L.LL32 = L.F32[1];
+        // the float phase's solved spectrum (3 V/2 complex = 12 V bytes) and the z pass's
+        // tile sums for r_d live in the double u~ buffer 0 (24 V bytes), idle until the polish
+        if (dim == 3 && (n == 128 || n == 256 || n == 512) && L.model == admm::kNeoHooke && o.local_ratio == 0.0 &&
+            o.local_fraction == 0.0) {
+            unsigned char* u0 = reinterpret_cast<unsigned char*>(L.U64[0]);
+            L.Sprev = reinterpret_cast<float*>(u0);
+            L.nz = admm::tiles_ax(L, false);
+            L.zpart = reinterpret_cast<double*>(u0 + align_up(sizeof(float) * 3 * (size_t)L.V));
+        }
     }
     if (L.plan.np_half < 0 || L.plan.np_full < 0) return fail(RVE_E_INVALID_ARG);
     if (admm::prepare_fft_kernels(n) != cudaSuccess) return fail(RVE_E_CUDA);
@@ -743,7 +755,7 @@ void rve_default_options(rve_options* o) {
     o->rho_tau = 10.0;
     o->rho_min = 0.0;
     o->mu_ref = 0.0;
-    o->mixed_switch = 4e-7;
+    o->mixed_switch = 3e-7;
     o->check_every = 16;
     o->use_graph = 1;
     o->local_ratio = 0.0;

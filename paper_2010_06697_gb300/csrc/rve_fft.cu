@@ -608,6 +608,15 @@ struct ColPlan {
     static constexpr int RL = N == 128 ? 2 : (N == 256 ? 4 : 1);   // last radix (1: none)
 };
 
+// Asynchronous 8-byte global-to-shared copies (cp.async, cached in L1), their commit and
+// the wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <bool INV, typename V>
 __device__ __forceinline__ V twiddled(V a, V w) {
     return cmul(a, INV ? cconj(w) : w);
@@ -977,6 +986,23 @@ __device__ __forceinline__ void faxis_fixed_tile(const Launch& L, int bid) {
         base = (long long)c * (Vn / 2) + col0;
     const int cl = threadIdx.x % TK;
     const int j = threadIdx.x / TK;
+    // the change of the solved spectrum for r_d (float phase, see Launch::Sprev): the kept
+    // u^_k is kept in tile order (the same tile and thread hold a mode every iteration:
+    // rows of 256 values, not the spectrum's column stride) and copied asynchronously
+    // into the block's second shared buffer while the forward transform runs
+    constexpr bool kSpec = MODE == 2 && !INCR && D == 3 && AXIS == 2 && std::is_same<T, float>::value;
+    float2* __restrict__ Sp = kSpec ? reinterpret_cast<float2*>(L.Sprev) : nullptr;
+    const bool have = kSpec && Sp && ctrl->spec_have;
+    float2* pre = reinterpret_cast<float2*>(buf + N * TK);
+    if constexpr (kSpec) {
+        if (have) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                cp_async8(pre + r * kFftThreads + threadIdx.x, Sp + ((long long)bid * 8 + r) * kFftThreads + threadIdx.x);
+            cp_async_commit();
+        }
+    }
+    float acc = 0.f;
     V x[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) x[r] = S[base + (j + TT * r) * es_g + cl];
@@ -987,16 +1013,53 @@ __device__ __forceinline__ void faxis_fixed_tile(const Launch& L, int bid) {
         if (MODE == 2) {
             const T kout = (D == 3) ? __ldg(ksq + outer) : T(0);
             const T kcol = __ldg(ksq + min(col0 + cl, H - 1)) + kout;
+            if constexpr (kSpec) {
+                if (have) cp_async_wait_all();  // this thread's own copies
+            }
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 const T den = __ldg(ksq + j + TT * r) + kcol;
                 x[r] = cscale(x[r], den > T(0) ? scale / den : T(0));
+                if constexpr (kSpec) {
+                    if (Sp) {
+                        const long long at = ((long long)bid * 8 + r) * kFftThreads + threadIdx.x;
+                        if (have) {
+                            const float2 o = pre[r * kFftThreads + threadIdx.x];
+                            const float dx = x[r].x - o.x, dy = x[r].y - o.y;
+                            acc += den * (dx * dx + dy * dy);
+                        }
+                        Sp[at] = x[r];
+                    }
+                }
             }
             col_fft<N, true, 1, TK, true>(x, buf, s_tw, j, cl);
         }
     }
 #pragma unroll
     for (int r = 0; r < 8; ++r) S[base + (j + TT * r) * es_g + cl] = x[r];
+    if constexpr (kSpec) {
+        if (Sp) {
+            // the spectrum holds x-frequencies 0 .. N/2-1, the first packed with N/2: the
+            // others stand for their conjugate partners too (weight 2); the tile's sum goes
+            // to its own slot (summed in a fixed order by the local pass)
+            __shared__ float s_red[kFftThreads / 32];
+            acc *= (col0 + cl == 0) ? 1.f : 2.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = 0.0;
+                for (int w = 0; w < kFftThreads / 32; ++w) t += (double)s_red[w];
+                L.zpart[bid] = t;
+                if (bid == 0) {
+                    Ctrl* c = const_cast<Ctrl*>(ctrl);
+                    c->spec_sum = ctrl->spec_have;
+                    c->spec_next = 1;
+                }
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------ launch
@@ -1038,8 +1101,10 @@ k_faxis(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntil
     }
 }
 
+// The z solves are held to 64 registers (4 blocks per SM): the float one, which also keeps
+// the spectrum for r_d, would take 73 and 3 blocks (2 us slower per 128^3 pass).
 template <typename T, int N, int D, int AXIS, int MODE, bool INCR>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kFftThreads, (MODE == 2 && !INCR) ? 4 : 1)
 k_faxis_fixed(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tl = tiles[t];
@@ -1073,9 +1138,11 @@ constexpr size_t xfixed_smem() {
     return (size_t)(N + 2 * XPlan<N>::H * XPlan<N>::S) * sizeof(typename Cx<T>::t);
 }
 
-template <typename T, int N>
+template <typename T, int N, int D = 3, int AXIS = 1, int MODE = 0, bool INCR = false>
 constexpr size_t fixed_smem() {
-    return (size_t)(N + N * ColPlan<N>::TK) * sizeof(typename Cx<T>::t);
+    // one transform buffer; the float z solve adds the buffer of the kept spectrum's copies
+    constexpr bool spec = MODE == 2 && !INCR && D == 3 && AXIS == 2 && std::is_same<T, float>::value;
+    return (size_t)(N + (spec ? 2 : 1) * N * ColPlan<N>::TK) * sizeof(typename Cx<T>::t);
 }
 
 template <typename K>
@@ -1094,15 +1161,18 @@ void go_axis(const Exec& E, int cls, size_t sma) {
         switch (E.uniform_n) {
             case 128:
                 if (tk == ColPlan<128>::TK)
-                    return go(k_faxis_fixed<T, 128, D, AXIS, MODE, INCR>, E, cls, fixed_smem<T, 128>());
+                    return go(k_faxis_fixed<T, 128, D, AXIS, MODE, INCR>, E, cls,
+                              fixed_smem<T, 128, D, AXIS, MODE, INCR>());
                 break;
             case 256:
                 if (tk == ColPlan<256>::TK)
-                    return go(k_faxis_fixed<T, 256, D, AXIS, MODE, INCR>, E, cls, fixed_smem<T, 256>());
+                    return go(k_faxis_fixed<T, 256, D, AXIS, MODE, INCR>, E, cls,
+                              fixed_smem<T, 256, D, AXIS, MODE, INCR>());
                 break;
             case 512:
                 if (tk == ColPlan<512>::TK)
-                    return go(k_faxis_fixed<T, 512, D, AXIS, MODE, INCR>, E, cls, fixed_smem<T, 512>());
+                    return go(k_faxis_fixed<T, 512, D, AXIS, MODE, INCR>, E, cls,
+                              fixed_smem<T, 512, D, AXIS, MODE, INCR>());
                 break;
             default:
                 break;

@@ -53,6 +53,10 @@ struct Ctrl {
     int div_given;       // 1: the next increment x-forward pass transforms the divergence
                          // already in D32 (the switch's residual) instead of D^T R
     int z_valid;         // polish: 1 once the linearisation offsets Z (double Lambda buffer) are formed
+    // r_d from the spectral solve (Launch::Sprev): spec_have = Sprev holds u^_k when the
+    // z pass of iteration k starts; spec_next = that pass stored u^_{k+1}; spec_sum = that
+    // pass wrote its tiles' sums of |k|^2 |u^_{k+1} - u^_k|^2 (read by the local pass)
+    int spec_have, spec_next, spec_sum;
     double stress[9];    // <W_F(F)> of the current state (written by the stress kernel)
     double lam_mean[9];  // <Lambda>
     long long k;         // iterations completed over the handle's life: F_k, u~_k live in buffer k & 1
@@ -163,6 +167,14 @@ struct Launch {
     float* R32;
     float* S32;
     float* D32;  // float u~ increment of the last increment projection (d*V)
+    // float phase of RVE_MIXED, 3D neo-Hookean with exact local steps on N = 128, 256, 512:
+    // the z pass keeps the solved spectrum u^ (d * V/2 complex, in the idle double u~
+    // buffer) and the squared norm of its change, so that the local pass takes r_d from
+    // it (Parseval) instead of a second u~ stencil; zpart: one double per z-pass tile
+    // (nz of them).  Null otherwise.
+    float* Sprev;
+    double* zpart;
+    int nz;
     float *LH32, *LL32;  // Lambda as double-word (hi, lo) during the polish (idle float buffers)
     FftPlan plan;
 };

@@ -1395,11 +1395,14 @@ k_init(const Ctrl* __restrict__ ctrl, T* F0, T* F1, T* Lam, T* U0, T* U1, const 
 // finish (atomic counter) sums all slots in a fixed order, so the result does not
 // depend on block scheduling, and runs the control step: residuals of iteration k,
 // stop flag, precision switch, adaptive rho.  INC: the increment form of the polish.
+// spec: the voxel sums of |G_{k+1} - G_k|^2 come from the z pass's tile sums zpart (nz of
+// them; see Launch::Sprev) instead of the threads' r_d partials.
 template <int D, bool INC, typename Acc>
 __device__ __forceinline__ void finish_pass(Ctrl* __restrict__ ctrl, double* __restrict__ hist,
                                             double* __restrict__ partials, int bid, int nblk, long long V,
                                             long long k, Acc rp2a, Acc rd2a, Acc rl2a, int nmax, int nfail,
-                                            bool frac_on, const int* s_hist) {
+                                            bool frac_on, const int* s_hist, bool spec = false,
+                                            const double* zpart = nullptr, int nz = 0) {
     __shared__ double s_sum[kLocalThreads / 32][3];
     __shared__ int s_int[kLocalThreads / 32][2];
     __shared__ int s_last;
@@ -1457,6 +1460,13 @@ __device__ __forceinline__ void finish_pass(Ctrl* __restrict__ ctrl, double* __r
         mx = max(mx, (int)__ldcg(pp + 2));
         nf += __ldcg(pp + 3);
         cl += __ldcg(pp + 4);
+    }
+    if (spec) {
+        // Parseval: sum_x |D w|^2 = (1/V) sum_m |k_m|^2 |w^(m)|^2 for the true DFT w^, and the
+        // z pass holds u^ scaled by 2/V, so the voxel sum is V/4 times its tile sums
+        double zb = 0.0;
+        for (int i = threadIdx.x; i < nz; i += blockDim.x) zb += __ldcg(zpart + i);
+        b += 0.25 * (double)V * zb;
     }
     a = warp_sum(a);
     b = warp_sum(b);
@@ -1549,6 +1559,9 @@ __device__ __forceinline__ void finish_pass(Ctrl* __restrict__ ctrl, double* __r
     }
     c->rho_changed = 0;
     c->div_given = 0;  // the switch's divergence has been transformed by now
+    c->spec_have = c->spec_next;  // the z pass of this iteration stored u^_{k+1}
+    c->spec_next = 0;
+    c->spec_sum = 0;
     if (INC) c->z_valid = 1;  // the polish's first step has formed Z at every voxel
     if (done == kRunning && c->adaptive) {  // eq. rho-update (He, Yang & Wang)
         double nr = rhod;
@@ -1856,6 +1869,8 @@ struct CfArgs {
     int nblk;    // tiles of the RVE's local grid
     int chunk;   // voxels of a tile per sweep
     float half_n;
+    const double* zpart;  // the z pass's tile sums for r_d (Launch::Sprev), or null
+    int nz;
 };
 
 template <int N>
@@ -1881,6 +1896,9 @@ k_local_cf(const __grid_constant__ CfArgs a, int first, int only_if_rho_changed)
     const float rho = (float)ctrl->rho;
     const int cap = ctrl->newton_cap;
     const float ntol = (float)ctrl->newton_tol;
+    // r_d from the z pass of this iteration when it summed the spectral change, else from
+    // the u~_k stencil here
+    const bool spec = !FIRST && a.zpart && ctrl->spec_sum;
     if (threadIdx.x < NN) s_fb[threadIdx.x] = (float)ctrl->Fbar[(threadIdx.x / 3) * 3 + threadIdx.x % 3];
     __syncthreads();
     const volatile float* Fb = s_fb;
@@ -1917,16 +1935,18 @@ k_local_cf(const __grid_constant__ CfArgs a, int first, int only_if_rho_changed)
                     sp += df * df;
                     __stcs(a.Lam + p * V + v, L[p]);
                 }
+                if (!spec) {
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const float* u = Uold + i * V;
-                    const float g0 = Fb[3 * i + 0] + (__ldg(u + xp) - __ldg(u + xm)) * hn;
-                    const float g1 = Fb[3 * i + 1] + (__ldg(u + yp) - __ldg(u + ym)) * hn;
-                    const float g2 = Fb[3 * i + 2] + (__ldg(u + zp) - __ldg(u + zm)) * hn;
-                    const float d0 = G[3 * i + 0] - g0, d1 = G[3 * i + 1] - g1, d2 = G[3 * i + 2] - g2;
-                    sd += d0 * d0;
-                    sd += d1 * d1;
-                    sd += d2 * d2;
+                    for (int i = 0; i < 3; ++i) {
+                        const float* u = Uold + i * V;
+                        const float g0 = Fb[3 * i + 0] + (__ldg(u + xp) - __ldg(u + xm)) * hn;
+                        const float g1 = Fb[3 * i + 1] + (__ldg(u + yp) - __ldg(u + ym)) * hn;
+                        const float g2 = Fb[3 * i + 2] + (__ldg(u + zp) - __ldg(u + zm)) * hn;
+                        const float d0 = G[3 * i + 0] - g0, d1 = G[3 * i + 1] - g1, d2 = G[3 * i + 2] - g2;
+                        sd += d0 * d0;
+                        sd += d1 * d1;
+                        sd += d2 * d2;
+                    }
                 }
                 rp2a += sp;
                 rd2a += sd;
@@ -1952,7 +1972,7 @@ k_local_cf(const __grid_constant__ CfArgs a, int first, int only_if_rho_changed)
         }
         if (!FIRST)
             finish_pass<3, false, float>(ctrl, a.hist, a.partials, t, a.nblk, (long long)V, k, rp2a, rd2a, 0.f, nmax,
-                                         nfail, false, nullptr);
+                                         nfail, false, nullptr, spec, a.zpart, a.nz);
         __syncthreads();
     }
 }
@@ -2253,8 +2273,10 @@ cudaError_t run_local(const Exec& E, bool first, bool only_if, int mode) {
             for (int i = 0; i < E.nmem; ++i) {
                 const Launch& M = *E.mem[i];
                 if (E.mem_exact[i]) {
-                    const CfArgs a{M.ctrl, M.hist, M.partials, {M.F32[0], M.F32[1]}, M.L32, {M.U32[0], M.U32[1]},
-                                   M.phase, M.mat32, M.nparam, M.local_blocks, M.local_chunk, M.half_n32};
+                    const CfArgs a{M.ctrl,     M.hist,           M.partials,       {M.F32[0], M.F32[1]},
+                                   M.L32,      {M.U32[0], M.U32[1]}, M.phase,      M.mat32,
+                                   M.nparam,   M.local_blocks,   M.local_chunk,    M.half_n32,
+                                   M.zpart,    M.nz};
                     auto lean = [&](auto kern) {
                         const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, M.local_blocks);
                         kern<<<grid, kLocalThreads, 0, E.stream>>>(a, first ? 1 : 0, first && only_if ? 1 : 0);

@@ -43,7 +43,7 @@ def test_default_options(lib):
     assert o.check_every >= 1 and o.use_graph == 1
     # the rest of the header's stated defaults
     assert o.lambda0 == rve.RVE_LAMBDA0_STRESS and o.newton_max == 30 and o.newton_tol == 0.0
-    assert o.rho_min == 0.0 and o.mu_ref == 0.0 and o.mixed_switch == 4e-7
+    assert o.rho_min == 0.0 and o.mu_ref == 0.0 and o.mixed_switch == 3e-7
     assert o.local_ratio == 0.0 and o.local_fraction == 0.0
 
 
