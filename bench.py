@@ -42,24 +42,28 @@ MU = (1.0, 10.0)
 NU = 0.3
 L2_BYTES = 129e6
 
-# algorithmic bytes per voxel and launch, per kernel class (s = bytes per scalar)
-#   local: read u~_{k+1}, u~_k (d each), F, Lambda (d^2 each); write F, Lambda; phase id (1 B)
-#   xfwd: read F, Lambda; write the spectrum (d scalars);  fwd_y / solve / inv_y / xinv: read + write d scalars
-#   local_r: local in double + write the float increment R (d^2 floats)
-#   xfwd_incr: read R (d^2 floats), write the float spectrum;  xinv_incr: read the float spectrum and
-#   u~_k (double), write u~_{k+1} (double)
+# algorithmic bytes per voxel and launch, per kernel class (s = bytes per scalar), for the
+# headline's kernels (3D float neo-Hookean on a fixed grid size, RVE_MIXED)
+#   local: read u~_{k+1} (d), F, Lambda (d^2 each); write F, Lambda; phase id (1 B).  The float
+#     pass takes r_d from the spectral solve; the double one also reads u~_k (d)
+#   xfwd: read F, Lambda; write the spectrum (d scalars);  fwd_y / inv_y / xinv: read + write d
+#   scalars;  solve: the same, and in the float phase also read + write the kept spectrum for r_d
+#   local_r (double-word polish): read the float u~ increment (d), R, F hi, F lo, Lambda lo, Z
+#   (d^2 floats each); write F lo, Lambda lo, R (d^2 floats each); phase id
+#   xfwd_incr: read R (d^2 floats), write the float spectrum;  xinv_incr: read the float spectrum
+#   and u~_k (double), write u~_{k+1} (double) and the float increment
 def bytes_per_voxel(cls: str, s: int, d: int = 3) -> float:
-    return {"local": (2 * d + 4 * d * d) * s + 1, "local_first": (d + 3 * d * d) * s + 1,
-            "xfwd": (2 * d * d + d) * s, "fwd_y": 2 * d * s, "solve": 2 * d * s, "inv_y": 2 * d * s,
-            "xinv": 2 * d * s, "local_r": (2 * d + 4 * d * d) * 8 + 1 + d * d * 4,
-            "xfwd_incr": (d * d + d) * 4, "xinv_incr": d * 4 + 2 * d * 8}[cls]
+    return {"local": (d + 4 * d * d) * s + 1 + (d * s if s == 8 else 0), "local_first": (d + 3 * d * d) * s + 1,
+            "xfwd": (2 * d * d + d) * s, "fwd_y": 2 * d * s, "solve": (4 if s == 4 else 2) * d * s,
+            "inv_y": 2 * d * s, "xinv": 2 * d * s, "local_r": d * 4 + 8 * d * d * 4 + 1,
+            "xfwd_incr": (d * d + d) * 4, "xinv_incr": d * 4 + 2 * d * 8 + d * 4}[cls]
 
 
 # DRAM bytes (read + write) per launch measured with ncu on the 128^3 inclusion cell
 # (profiles/), keyed by (kernel class, precision); absent = not captured since the
 # kernel last changed
-TRAFFIC = {("local", "fp32"): 221321216 + 133230080, ("local_r", "fp64"): 418162944 + 338556928,
-           ("xfwd", "fp32"): 151019264 + 9842176, ("xinv", "fp32"): 25181952, ("solve", "fp32"): 25196800}
+TRAFFIC = {("local", "fp32"): 178665984 + 91949056, ("local_r", "fp64"): 415438336 + 184841472,
+           ("xfwd", "fp32"): 151019264 + 9842176, ("xinv", "fp32"): 25181952, ("solve", "fp32"): 50366976 + 333056}
 # FP32 flops per launch by kernel class, where counted with ncu for the current kernel
 # (none since the float local step became the closed form: no ALU view is reported)
 FLOPS = {}

@@ -1101,10 +1101,10 @@ k_faxis(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntil
     }
 }
 
-// The z solves are held to 64 registers (4 blocks per SM): the float one, which also keeps
-// the spectrum for r_d, would take 73 and 3 blocks (2 us slower per 128^3 pass).
+// The float z solve, which also keeps the spectrum for r_d, is held to 64 registers (4
+// blocks per SM): with 73 registers and 3 blocks it runs 2 us slower per 128^3 pass.
 template <typename T, int N, int D, int AXIS, int MODE, bool INCR>
-__global__ void __launch_bounds__(kFftThreads, (MODE == 2 && !INCR) ? 4 : 1)
+__global__ void __launch_bounds__(kFftThreads, (MODE == 2 && !INCR && std::is_same<T, float>::value) ? 4 : 1)
 k_faxis_fixed(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tl = tiles[t];

@@ -96,16 +96,20 @@ def test_single_rank_is_identity():
 
 def test_byte_model_matches_the_documented_per_voxel_figures():
     """bench.py's algorithmic bytes per voxel and launch (the roofline numerators): one
-    iteration of the 3D path is 87 s + 1 bytes (s = 4 or 8: local 42 s + 1, x-forward 21 s,
-    four FFT passes 6 s each), the double-word polish local step 373 B, its increment x
-    passes 48 and 60 B."""
+    iteration of the 3D path in double is 87 s + 1 bytes (s = 8: local 42 s + 1, x-forward
+    21 s, four FFT passes 6 s each); the float iteration of the headline takes r_d from the
+    spectral solve, so its local pass reads 3 scalars less (39 s + 1) and its z solve also
+    reads and writes the kept spectrum (12 s): 90 s + 1 with s = 4.  The double-word polish
+    local step moves 301 B, its increment x passes 48 and 72 B."""
     sys.path.insert(0, ROOT)
     import bench
-    for s in (4, 8):
-        it = sum(bench.bytes_per_voxel(c, s) for c in ("local", "xfwd", "fwd_y", "solve", "inv_y", "xinv"))
-        assert it == 87 * s + 1
-        assert bench.bytes_per_voxel("local", s) == 42 * s + 1 and bench.bytes_per_voxel("xfwd", s) == 21 * s
-    assert bench.bytes_per_voxel("local_r", 0) == 373
-    assert bench.bytes_per_voxel("xfwd_incr", 0) == 48 and bench.bytes_per_voxel("xinv_incr", 0) == 60
+    it = sum(bench.bytes_per_voxel(c, 8) for c in ("local", "xfwd", "fwd_y", "solve", "inv_y", "xinv"))
+    assert it == 87 * 8 + 1
+    assert bench.bytes_per_voxel("local", 8) == 42 * 8 + 1 and bench.bytes_per_voxel("xfwd", 8) == 21 * 8
+    it = sum(bench.bytes_per_voxel(c, 4) for c in ("local", "xfwd", "fwd_y", "solve", "inv_y", "xinv"))
+    assert it == 90 * 4 + 1
+    assert bench.bytes_per_voxel("local", 4) == 39 * 4 + 1 and bench.bytes_per_voxel("solve", 4) == 12 * 4
+    assert bench.bytes_per_voxel("local_r", 0) == 301
+    assert bench.bytes_per_voxel("xfwd_incr", 0) == 48 and bench.bytes_per_voxel("xinv_incr", 0) == 72
     # 2D: d = 2 in the same formulas
     assert bench.bytes_per_voxel("local", 8, d=2) == (4 + 16) * 8 + 1
