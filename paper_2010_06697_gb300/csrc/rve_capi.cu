@@ -686,6 +686,7 @@ int create_common(rve_t* out, int dim, int n, int model, const rve_options* opt,
             E.smem_a[f] = admm::smem_a_bytes(L, f == 1);
         }
         E.uniform_n = n;
+        E.uniform_geom = 1;
         E.exact_local = (o.local_ratio == 0.0 && o.local_fraction == 0.0) ? 1 : 0;
         h->self_mem[0] = &h->L;
         h->self_exact[0] = (unsigned char)E.exact_local;
@@ -1378,6 +1379,7 @@ int run_upload(Engine& E, BatchRun& r) {
     r.E.rds = E.d_rds;
     r.E.rep = &E.mem[r.active.front()].h->L;
     r.E.uniform_n = E.mem[r.active.front()].h->n;
+    r.E.uniform_geom = 1;
     r.E.exact_local = 1;
     r.mem.clear();
     r.mem_exact.clear();
@@ -1385,6 +1387,9 @@ int run_upload(Engine& E, BatchRun& r) {
     int tile0 = 0;
     for (int slot : r.active) {
         if (E.mem[slot].h->n != r.E.uniform_n) r.E.uniform_n = 0;
+        const Launch& M = E.mem[slot].h->L;
+        const Launch& R0 = E.mem[r.active.front()].h->L;
+        if (M.lpb != R0.lpb || M.tk32 != R0.tk32 || M.tk64 != R0.tk64) r.E.uniform_geom = 0;
         if (!E.mem[slot].h->E.exact_local) r.E.exact_local = 0;
         r.mem.push_back(&E.mem[slot].h->L);
         r.mem_exact.push_back((unsigned char)E.mem[slot].h->E.exact_local);

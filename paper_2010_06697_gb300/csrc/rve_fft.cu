@@ -266,6 +266,7 @@ __device__ __forceinline__ void xfwd_tile(const Launch& L, int bid) {
     T* Ar = reinterpret_cast<T*>(A);
     load_twiddles(s_tw, g_tw, n);
     const int line0 = bid * lpb;
+    if (line0 >= nlines) return;  // tiles counted for the fixed kernels' one component each
     const FastDiv nl{(unsigned)lpb, 0u, 0u};  // transforms per block (only the count is used)
     const long long sn = n, s2 = sn * sn;
 
@@ -459,6 +460,7 @@ __device__ __forceinline__ void xinv_tile(const Launch& L, int bid) {
     load_twiddles(s_tw, g_tw, n);
     __syncthreads();
     const int line0 = bid * lpb;
+    if (line0 >= nlines) return;  // tiles counted for the fixed kernels' one component each
     const FastDiv nl{(unsigned)lpb, 0u, 0u};  // transforms per block (only the count is used)
     for (int c = 0; c < D; ++c) {
         V* S_c = S + (long long)c * (Vn / 2);
@@ -715,7 +717,11 @@ __device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid) {
     V* stage = buf + H * S;     // the second one stages the input lines
     T* stage_r = reinterpret_cast<T*>(stage);
     load_twiddles(s_tw, Args::tw(L), N);
-    const int line0 = bid * LPB;
+    // one component per tile (tiles_x): three times the blocks of a loop over components,
+    // whose load latency then overlaps across blocks instead of adding up within one
+    constexpr int NB = nlines / LPB;
+    const int c0 = bid / NB;
+    const int line0 = (bid % NB) * LPB;
     const int lt = threadIdx.x % LPB, jt = threadIdx.x / LPB;
     // a tile's LPB lines are consecutive y of one z plane (LPB divides N): the z
     // neighbours are fixed offsets.  Voxel indices fit 32 bits (N^3 < 2^31); the
@@ -726,7 +732,7 @@ __device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid) {
     constexpr Idx sn = N, s2 = (Idx)N * N;
     const bool divg = INCR && ctrl->div_given;
     const Idx zp = (z + 1 == N ? (1 - N) * s2 : s2), zm = (z == 0 ? (N - 1) * s2 : -s2);
-    for (int c = 0; c < D; ++c) {
+    for (int c = c0; c < c0 + 1; ++c) {
         const T* F_c0 = F + (long long)(c * D + 0) * Vn;
         const T* F_c1 = F + (long long)(c * D + 1) * Vn;
         const T* F_c2 = F + (long long)(c * D + 2) * Vn;
@@ -867,9 +873,11 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
     V* buf = s_tw + N;
     V* stage = buf + H * S;
     load_twiddles(s_tw, Args::tw(L), N);
-    const int line0 = bid * LPB;
+    constexpr int NB = nlines / LPB;  // one component per tile, as in xfwd_fixed_tile
+    const int c0 = bid / NB;
+    const int line0 = (bid % NB) * LPB;
     const int lt = threadIdx.x % LPB, jt = threadIdx.x / LPB;
-    for (int c = 0; c < D; ++c) {
+    for (int c = c0; c < c0 + 1; ++c) {
         V* S_c = Sp + (long long)c * (Vn / 2);
         __syncthreads();
         for (int idx = threadIdx.x; idx < LPB * H; idx += blockDim.x) {
@@ -1158,7 +1166,7 @@ template <typename T, int D, int AXIS, int MODE, bool INCR>
 void go_axis(const Exec& E, int cls, size_t sma) {
     const int tk = std::is_same<T, double>::value ? E.rep->tk64 : E.rep->tk32;
     if constexpr (D == 3) {
-        switch (E.uniform_n) {
+        switch (E.uniform_geom ? E.uniform_n : 0) {
             case 128:
                 if (tk == ColPlan<128>::TK)
                     return go(k_faxis_fixed<T, 128, D, AXIS, MODE, INCR>, E, cls,
@@ -1187,7 +1195,7 @@ template <typename T, int D, bool INCR>
 void go_xfwd(const Exec& E, size_t smx) {
     if constexpr (D == 3) {
         const int lpb = E.rep->lpb;
-        switch (E.uniform_n) {
+        switch (E.uniform_geom ? E.uniform_n : 0) {
             case 128:
                 if (lpb == XPlan<128>::LPB) return go(k_xfwd_fixed<T, 128, D, INCR>, E, kTilesX, xfixed_smem<T, 128>());
                 break;
@@ -1208,7 +1216,7 @@ template <typename T, typename TO, int D, bool INCR>
 void go_xinv(const Exec& E, size_t smx) {
     if constexpr (D == 3) {
         const int lpb = E.rep->lpb;
-        switch (E.uniform_n) {
+        switch (E.uniform_geom ? E.uniform_n : 0) {
             case 128:
                 if (lpb == XPlan<128>::LPB)
                     return go(k_xinv_fixed<T, TO, 128, D, INCR>, E, kTilesX, xfixed_smem<T, 128>());
@@ -1421,7 +1429,14 @@ void set_geometry(Launch& L) {
 }
 
 int tiles_local(const Launch& L) { return L.local_blocks; }
-int tiles_x(const Launch& L) { return L.xblocks; }
+// the fixed-length x kernels (3D, N = 128, 256, 512 with their lines per block) take one
+// component per tile
+int tiles_x(const Launch& L) {
+    const bool fixed = L.dim == 3 && ((L.n == 128 && L.lpb == XPlan<128>::LPB) ||
+                                      (L.n == 256 && L.lpb == XPlan<256>::LPB) ||
+                                      (L.n == 512 && L.lpb == XPlan<512>::LPB));
+    return L.xblocks * (fixed ? L.dim : 1);
+}
 int tiles_ax(const Launch& L, bool fp64) {
     const int H = L.n / 2;
     const int tk = fp64 ? L.tk64 : L.tk32;

@@ -194,6 +194,7 @@ struct Exec {
     size_t smem_x[2];             // dynamic shared memory of the x passes [fp64], max over members
     size_t smem_a[2];             // and of the y/z passes
     int uniform_n;                // N shared by every member (0 if sizes differ)
+    int uniform_geom;             // 1: every member has the first one's FFT geometry (lpb, tk)
     int exact_local;              // 1: no member takes approximate local steps (local_ratio,
                                   // local_fraction both 0): the float neo-Hookean law in 3D
                                   // then runs its closed-form local step
