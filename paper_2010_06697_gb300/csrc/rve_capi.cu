@@ -1253,8 +1253,9 @@ enum Stage : int { kStageF32 = 0, kStageF64 = 1, kStagePolish = 2 };
 struct BatchRun {  // members of one (dim, model, stage) still iterating
     std::vector<int> active;  // slots
     admm::Exec E{};
-    std::vector<const Launch*> mem;     // E's member list, in the order of active
-    std::vector<unsigned char> mem_exact;
+    int stage = 0;                      // precision stage of the run (enum Stage)
+    std::vector<const Launch*> mem;     // E's member list in local-tile order: the members
+    std::vector<unsigned char> mem_exact;  // without a lean local kernel first (lean_local)
     std::vector<int> mem_tile0;
     int2* d_tiles[admm::kTileClasses] = {};
     int cap[admm::kTileClasses] = {};
@@ -1350,11 +1351,23 @@ int engine_reserve(Engine& E, int need) {
     return RVE_OK;
 }
 
+// Whether a member takes the lean local kernel in this run's stage (no lean kernel in the
+// plain double stage).
+bool member_lean(const rve* h, int stage) {
+    if (stage == kStageF64) return false;
+    return admm::lean_local(h->L, h->E.exact_local != 0, stage == kStagePolish);
+}
+
 int run_upload(Engine& E, BatchRun& r) {
     std::vector<int2> t;
+    // local tiles: the members without a lean kernel first (they share one tile launch)
+    std::vector<int> local_order;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int slot : r.active)
+            if (member_lean(E.mem[slot].h, r.stage) == (pass == 1)) local_order.push_back(slot);
     for (int c = 0; c < admm::kTileClasses; ++c) {
         t.clear();
-        for (int slot : r.active) {
+        for (int slot : (c == admm::kTilesLocal ? local_order : r.active)) {
             const Launch& L = E.mem[slot].h->L;
             const int cnt = c == admm::kTilesLocal ? admm::tiles_local(L)
                           : c == admm::kTilesX     ? admm::tiles_x(L)
@@ -1385,7 +1398,7 @@ int run_upload(Engine& E, BatchRun& r) {
     r.mem_exact.clear();
     r.mem_tile0.clear();
     int tile0 = 0;
-    for (int slot : r.active) {
+    for (int slot : local_order) {
         if (E.mem[slot].h->n != r.E.uniform_n) r.E.uniform_n = 0;
         const Launch& M = E.mem[slot].h->L;
         const Launch& R0 = E.mem[r.active.front()].h->L;
@@ -1450,6 +1463,7 @@ int run_chunk(Engine& E, BatchRun& r, int stage) {
 void run_insert(Engine& E, int slot) {
     const Member& m = E.mem[slot];
     BatchRun& r = E.runs[RunKey(m.h->dim, m.h->L.model, m.stage, size_class(m.h))];
+    r.stage = m.stage;
     r.active.insert(std::lower_bound(r.active.begin(), r.active.end(), slot), slot);
     r.dirty = true;
 }

@@ -1421,7 +1421,7 @@ void set_geometry(Launch& L) {
     while (chunk > 32 && (L.V + chunk - 1) / chunk < 2 * 152) chunk /= 2;
     L.local_chunk = chunk;
     const long long want = (L.V + chunk - 1) / chunk;
-    const long long cap = 152 * 12;  // whole waves at 2, 3, 4 or 6 resident blocks per SM
+    const long long cap = kLocalTileCap;
     L.local_blocks = (int)(want < cap ? want : cap);
     Geometry g;
     if (!lookup_geometry(L.dim, L.n, &g)) g = default_geometry(L.dim, L.n);

@@ -8,6 +8,8 @@ namespace admm {
 
 constexpr int kMaxPasses = 16;
 constexpr int kLocalThreads = 128;    // threads per block of the local-step kernels
+constexpr int kLocalTileCap = 152 * 12;  // local tiles of one RVE at most (whole waves at 2, 3, 4 or 6
+                                         // resident blocks per SM)
 constexpr int kFftThreads = 256;      // threads per block of the FFT kernels
 // per-phase material constants: the law's own (mu, lam first); the LCE adds r, alpha,
 // kappa_F (2-4), the derived a, c1, c2 (5-7), the dissipation weights nu_F/dt, nu_n/dt
@@ -240,6 +242,9 @@ cudaError_t launch_init(const Launch& L, bool fp64, bool lambda_zero);
 // polish_mode (double only): 0 plain; 1 also write R; 2 also write R and take
 // r_d from the float u~ increment D32 (see local_tile).
 cudaError_t launch_local(const Exec& E, bool fp64, bool first, bool only_if_rho_changed, int polish_mode = 0);
+// whether a member's fused local pass takes the lean per-RVE kernel (float phase, or the
+// double-word polish with polish = true); the engine puts the other members' local tiles first
+bool lean_local(const Launch& L, bool exact, bool polish);
 cudaError_t launch_stress(const Launch& L, bool fp64);
 // LCE: save the current state (F_k, n_k) as the previous time step, in every precision held
 cudaError_t launch_save_prev(const Launch& L, bool from_fp64, cudaStream_t st);

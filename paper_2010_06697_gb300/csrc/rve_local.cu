@@ -1844,8 +1844,30 @@ k_local(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntil
     }
 }
 
+// Periodic neighbours of voxel v on an N^3 grid: by shifts and masks for a compile-time
+// N (a power of two), by the multiply-high divisor of the run-time n for N = 0.
+template <int N>
+__device__ __forceinline__ Nbr<3> nbr3(int v, const FastDiv& dn) {
+    if constexpr (N == 0) {
+        return neighbours<3>(v, dn);
+    } else {
+        constexpr int LOG = N == 128 ? 7 : (N == 256 ? 8 : 9);
+        static_assert(N == (1 << LOG), "power-of-two grids");
+        const int x = v & (N - 1), y = (v >> LOG) & (N - 1), z = v >> (2 * LOG);
+        Nbr<3> o;
+        o.xp = v + (x == N - 1 ? 1 - N : 1);
+        o.xm = v + (x == 0 ? N - 1 : -1);
+        o.yp = v + (y == N - 1 ? (1 - N) * N : N);
+        o.ym = v + (y == 0 ? (N - 1) * N : -N);
+        o.zp = v + (z == N - 1 ? (1 - N) * N * N : N * N);
+        o.zm = v + (z == 0 ? (N - 1) * N * N : -N * N);
+        return o;
+    }
+}
+
 // The fused pass of one RVE for the float neo-Hookean law in 3D with exact local steps
-// (closed-form Step 1) on an N^3 grid, N = 128, 256 or 512: the same steps, sums and
+// (closed-form Step 1) on an N^3 grid, N = 128, 256 or 512, or N = 0: any other grid of
+// at least 1824 x 128 voxels (a full local grid; the run-time n and V come in the args): the same steps, sums and
 // tile partials as local_tile's closed-form instance, arranged so that the voxel loop
 // keeps few values in registers.  The RVE's buffers and constants are kernel parameters
 // (read from the constant bank where they are used), the grid size is a compile-time
@@ -1871,14 +1893,15 @@ struct CfArgs {
     float half_n;
     const double* zpart;  // the z pass's tile sums for r_d (Launch::Sprev), or null
     int nz;
+    int V;                // voxels and the multiply-high divisor of n (N = 0 only)
+    FastDiv dn;
 };
 
 template <int N>
 __global__ void __launch_bounds__(kLocalThreads, kCfMinBlocks)
 k_local_cf(const __grid_constant__ CfArgs a, int first, int only_if_rho_changed) {
-    static_assert(N == 128 || N == 256 || N == 512, "fixed grid sizes");
-    constexpr int LOG = N == 128 ? 7 : (N == 256 ? 8 : 9);
-    constexpr int V = N * N * N;
+    static_assert(N == 0 || N == 128 || N == 256 || N == 512, "fixed grid sizes or run-time (0)");
+    const int V = N ? N * N * N : a.V;
     constexpr int NN = 9;
     __shared__ float s_fb[NN];
     Ctrl* __restrict__ ctrl = a.ctrl;
@@ -1907,10 +1930,8 @@ k_local_cf(const __grid_constant__ CfArgs a, int first, int only_if_rho_changed)
         float rp2a = 0.f, rd2a = 0.f;
         int nmax = 0, nfail = 0;
         for (int v = t * a.chunk + threadIdx.x; threadIdx.x < a.chunk && v < V; v += a.nblk * a.chunk) {
-            const int x = v & (N - 1), y = (v >> LOG) & (N - 1), z = v >> (2 * LOG);
-            const int xp = v + (x == N - 1 ? 1 - N : 1), xm = v + (x == 0 ? N - 1 : -1);
-            const int yp = v + (y == N - 1 ? (1 - N) * N : N), ym = v + (y == 0 ? (N - 1) * N : -N);
-            const int zp = v + (z == N - 1 ? (1 - N) * N * N : N * N), zm = v + (z == 0 ? (N - 1) * N * N : -N * N);
+            const Nbr<3> nb = nbr3<N>(v, a.dn);
+            const int xp = nb.xp, xm = nb.xm, yp = nb.yp, ym = nb.ym, zp = nb.zp, zm = nb.zm;
             float G[NN], L[NN], F[NN];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -1978,8 +1999,8 @@ k_local_cf(const __grid_constant__ CfArgs a, int first, int only_if_rho_changed)
 }
 
 // The double-word polish step (local_tile's increment form, polish_voxel_dev) of one RVE
-// of an elastic law in 3D on an N^3 grid, N = 128, 256 or 512, laid out like
-// k_local_cf: buffers and constants as kernel parameters, N fixed at compile time,
+// of an elastic law in 3D on an N^3 grid, N = 128, 256 or 512 or run-time (0), laid out
+// like k_local_cf: buffers and constants as kernel parameters, N fixed at compile time,
 // 32-bit offsets.  Same arithmetic and tile partials as the tile-table instance.
 struct PolishArgs {
     Ctrl* ctrl;
@@ -1998,13 +2019,14 @@ struct PolishArgs {
     int nblk;
     int chunk;
     float half_n;
+    int V;             // voxels and the multiply-high divisor of n (N = 0 only)
+    FastDiv dn;
 };
 
 template <int N, int MODEL>
 __global__ void __launch_bounds__(kLocalThreads, 4) k_polish_fixed(const __grid_constant__ PolishArgs a) {
-    static_assert(N == 128 || N == 256 || N == 512, "fixed grid sizes");
-    constexpr int LOG = N == 128 ? 7 : (N == 256 ? 8 : 9);
-    constexpr int V = N * N * N;
+    static_assert(N == 0 || N == 128 || N == 256 || N == 512, "fixed grid sizes or run-time (0)");
+    const int V = N ? N * N * N : a.V;
     constexpr int NN = 9;
     __shared__ float s_dfb[NN];
     Ctrl* __restrict__ ctrl = a.ctrl;
@@ -2026,10 +2048,8 @@ __global__ void __launch_bounds__(kLocalThreads, 4) k_polish_fixed(const __grid_
         float rp2a = 0.f, rd2a = 0.f;
         int nmax = 0, nfail = 0;
         for (int v = t * a.chunk + threadIdx.x; threadIdx.x < a.chunk && v < V; v += a.nblk * a.chunk) {
-            const int x = v & (N - 1), y = (v >> LOG) & (N - 1), z = v >> (2 * LOG);
-            const int xp = v + (x == N - 1 ? 1 - N : 1), xm = v + (x == 0 ? N - 1 : -1);
-            const int yp = v + (y == N - 1 ? (1 - N) * N : N), ym = v + (y == 0 ? (N - 1) * N : -N);
-            const int zp = v + (z == N - 1 ? (1 - N) * N * N : N * N), zm = v + (z == 0 ? (N - 1) * N * N : -N * N);
+            const Nbr<3> nb = nbr3<N>(v, a.dn);
+            const int xp = nb.xp, xm = nb.xm, yp = nb.yp, ym = nb.ym, zp = nb.zp, zm = nb.zm;
             float dG[NN], spf, sdf;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -2256,6 +2276,22 @@ cudaError_t run_init(const Launch& L, bool lambda_zero) {
     return cudaGetLastError();
 }
 
+}  // namespace
+
+// Whether a member's fused local pass runs the lean per-RVE kernel (k_local_cf in the
+// float phase, k_polish_fixed in the double-word polish): 3D, the neo-Hookean law with
+// exact local steps (float phase) or an elastic law (polish), and a grid of N = 128, 256,
+// 512 or a full local grid (every tile a whole block of voxels), so that a launch of its
+// own fills the GPU.  A function of the member alone: its results are the same in any batch.
+bool lean_local(const Launch& L, bool exact, bool polish) {
+    if (L.dim != 3) return false;
+    if (polish ? !(L.model == kNeoHooke || L.model == kLinear) : !(L.model == kNeoHooke && exact)) return false;
+    if (L.n == 128 || L.n == 256 || L.n == 512) return true;
+    return L.local_blocks == kLocalTileCap && L.local_chunk == kLocalThreads;
+}
+
+namespace {
+
 // mode: 0 plain, 1 write R (first polish iteration), 2 write R and read the float u~ increment
 template <typename T, int D, int MODEL>
 cudaError_t run_local(const Exec& E, bool first, bool only_if, int mode) {
@@ -2265,35 +2301,65 @@ cudaError_t run_local(const Exec& E, bool first, bool only_if, int mode) {
         const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, nt);
         kern<<<grid, kLocalThreads, 0, E.stream>>>(E.rds, tl, nt, is_first, flag);
     };
-    if constexpr (std::is_same<T, float>::value && D == 3 && MODEL == kNeoHooke) {
-        const int un = E.uniform_n;
-        if ((un == 128 || un == 256 || un == 512) && E.nmem > 0) {
-            // one launch per member: the lean closed-form kernel, or the Newton instance on
-            // the member's own tiles when it takes approximate local steps
-            for (int i = 0; i < E.nmem; ++i) {
-                const Launch& M = *E.mem[i];
-                if (E.mem_exact[i]) {
-                    const CfArgs a{M.ctrl,     M.hist,           M.partials,       {M.F32[0], M.F32[1]},
-                                   M.L32,      {M.U32[0], M.U32[1]}, M.phase,      M.mat32,
-                                   M.nparam,   M.local_blocks,   M.local_chunk,    M.half_n32,
-                                   M.zpart,    M.nz};
-                    auto lean = [&](auto kern) {
-                        const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, M.local_blocks);
-                        kern<<<grid, kLocalThreads, 0, E.stream>>>(a, first ? 1 : 0, first && only_if ? 1 : 0);
-                    };
-                    if (un == 128) lean(k_local_cf<128>);
-                    else if (un == 256) lean(k_local_cf<256>);
-                    else lean(k_local_cf<512>);
-                } else {
-                    auto kern = k_local<T, D, MODEL, false, false>;
-                    const int ntm = tiles_local(M);
-                    const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, ntm);
-                    kern<<<grid, kLocalThreads, 0, E.stream>>>(E.rds, tl + E.mem_tile0[i], ntm, first ? 1 : 0,
-                                                               first && only_if ? 1 : 0);
-                }
+    // Members with a lean kernel (lean_local) run one launch each; the others' tiles come
+    // first in the local tile table (the engine orders them so) and share one tile launch.
+    // Returns false when no member has a lean kernel.
+    auto lean_split = [&](bool polish, auto&& lean_launch, auto&& tile_launch) {
+        if (E.nmem <= 0) return false;
+        int prefix = 0;
+        bool any = false, exact_pre = true;
+        for (int i = 0; i < E.nmem; ++i) {
+            if (lean_local(*E.mem[i], E.mem_exact[i] != 0, polish)) {
+                any = true;
+            } else {
+                prefix += tiles_local(*E.mem[i]);
+                exact_pre = exact_pre && E.mem_exact[i];
             }
-            return cudaGetLastError();
         }
+        if (!any) return false;
+        bool ordered = true;  // the non-lean members' tiles form the prefix
+        for (int i = 0; i < E.nmem; ++i)
+            if (!lean_local(*E.mem[i], E.mem_exact[i] != 0, polish) &&
+                E.mem_tile0[i] + tiles_local(*E.mem[i]) > prefix)
+                ordered = false;
+        if (ordered) {
+            if (prefix > 0) tile_launch(0, prefix, exact_pre);
+        } else {
+            for (int i = 0; i < E.nmem; ++i)
+                if (!lean_local(*E.mem[i], E.mem_exact[i] != 0, polish))
+                    tile_launch(E.mem_tile0[i], tiles_local(*E.mem[i]), E.mem_exact[i] != 0);
+        }
+        for (int i = 0; i < E.nmem; ++i)
+            if (lean_local(*E.mem[i], E.mem_exact[i] != 0, polish)) lean_launch(*E.mem[i]);
+        return true;
+    };
+    auto tile_range = [&](auto kern, int t0, int cnt, int is_first, int flag) {
+        const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, cnt);
+        kern<<<grid, kLocalThreads, 0, E.stream>>>(E.rds, tl + t0, cnt, is_first, flag);
+    };
+    if constexpr (std::is_same<T, float>::value && D == 3 && MODEL == kNeoHooke) {
+        const int f = first ? 1 : 0, fo = first && only_if ? 1 : 0;
+        const bool split = lean_split(
+            false,
+            [&](const Launch& M) {
+                CfArgs a{M.ctrl,     M.hist,           M.partials,       {M.F32[0], M.F32[1]},
+                         M.L32,      {M.U32[0], M.U32[1]}, M.phase,      M.mat32,
+                         M.nparam,   M.local_blocks,   M.local_chunk,    M.half_n32,
+                         M.zpart,    M.nz,             (int)M.V,         M.plan.div_n};
+                auto lean = [&](auto kern) {
+                    const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, M.local_blocks);
+                    kern<<<grid, kLocalThreads, 0, E.stream>>>(a, f, fo);
+                };
+                if (M.n == 128) lean(k_local_cf<128>);
+                else if (M.n == 256) lean(k_local_cf<256>);
+                else if (M.n == 512) lean(k_local_cf<512>);
+                else lean(k_local_cf<0>);
+            },
+            [&](int t0, int cnt, bool exact) {
+                if (exact) tile_range(k_local<T, D, MODEL, false, false, true>, t0, cnt, f, fo);
+                else tile_range(k_local<T, D, MODEL, false, false>, t0, cnt, f, fo);
+            });
+        if (split) return cudaGetLastError();
         if (E.exact_local) {
             go(k_local<T, D, MODEL, false, false, true>, first ? 1 : 0, first && only_if ? 1 : 0);
             return cudaGetLastError();
@@ -2304,24 +2370,26 @@ cudaError_t run_local(const Exec& E, bool first, bool only_if, int mode) {
         return cudaGetLastError();
     }
     if constexpr (std::is_same<T, double>::value && D == 3 && (MODEL == kNeoHooke || MODEL == kLinear)) {
-        const int un = E.uniform_n;
-        if (mode == 2 && (un == 128 || un == 256 || un == 512) && E.nmem > 0) {
-            // the double-word polish step, one lean launch per member
-            for (int i = 0; i < E.nmem; ++i) {
-                const Launch& M = *E.mem[i];
-                const PolishArgs a{M.ctrl, M.hist, M.partials,
-                                   {reinterpret_cast<float*>(M.F64[0]), reinterpret_cast<float*>(M.F64[1])},
-                                   M.LH32, M.LL32, reinterpret_cast<float*>(M.L64), M.R32, M.D32, M.phase, M.mat32,
-                                   M.mat32lo, M.nparam, M.local_blocks, M.local_chunk, M.half_n32};
-                auto lean = [&](auto kern) {
-                    const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, M.local_blocks);
-                    kern<<<grid, kLocalThreads, 0, E.stream>>>(a);
-                };
-                if (un == 128) lean(k_polish_fixed<128, MODEL>);
-                else if (un == 256) lean(k_polish_fixed<256, MODEL>);
-                else lean(k_polish_fixed<512, MODEL>);
-            }
-            return cudaGetLastError();
+        if (mode == 2) {
+            const bool split = lean_split(
+                true,
+                [&](const Launch& M) {
+                    PolishArgs a{M.ctrl, M.hist, M.partials,
+                                 {reinterpret_cast<float*>(M.F64[0]), reinterpret_cast<float*>(M.F64[1])},
+                                 M.LH32, M.LL32, reinterpret_cast<float*>(M.L64), M.R32, M.D32, M.phase, M.mat32,
+                                 M.mat32lo, M.nparam, M.local_blocks, M.local_chunk, M.half_n32, (int)M.V,
+                                 M.plan.div_n};
+                    auto lean = [&](auto kern) {
+                        const int grid = persistent_grid((const void*)kern, kLocalThreads, 0, M.local_blocks);
+                        kern<<<grid, kLocalThreads, 0, E.stream>>>(a);
+                    };
+                    if (M.n == 128) lean(k_polish_fixed<128, MODEL>);
+                    else if (M.n == 256) lean(k_polish_fixed<256, MODEL>);
+                    else if (M.n == 512) lean(k_polish_fixed<512, MODEL>);
+                    else lean(k_polish_fixed<0, MODEL>);
+                },
+                [&](int t0, int cnt, bool) { tile_range(k_local<T, D, MODEL, true, true>, t0, cnt, 0, 0); });
+            if (split) return cudaGetLastError();
         }
     }
     if constexpr (std::is_same<T, double>::value) {

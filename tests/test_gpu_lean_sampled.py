@@ -1,5 +1,7 @@
-"""The float phase's per-RVE kernels on the largest grids (256^3 and 512^3, 134M voxels)
-against the FP64 oracle's local solve (Section 2.1, Step 1) at sampled voxels.
+"""The lean per-RVE local kernels (fixed grids of 256^3 and 512^3, 134M voxels, and a
+run-time grid, 96^3) against the FP64 oracle's local solve (Section 2.1, Step 1) at
+sampled voxels, a whole mixed-precision solve on a run-time grid against the FP64 path,
+and a batch mixing lean and tile-table members against the members solved alone.
 
 RVE_MIXED on these grids runs the closed-form local step in the lean per-RVE kernel,
 for the first local step of a solve (F_1 from Fbar) and fused with Steps 3-4 (F_2 from
@@ -15,6 +17,8 @@ import pytest
 
 import oracle
 from paper_2010_06697_gb300 import build, rve, synth
+
+from .test_gpu_batch import fbars, members
 
 pytestmark = pytest.mark.gpu
 TOL = 2e-5
@@ -39,7 +43,7 @@ def solve(ph, Fbar, rho, iters):
     return s
 
 
-@pytest.mark.parametrize("n", [256, 512])
+@pytest.mark.parametrize("n", [96, 256, 512])
 def test_lean_local_steps_match_oracle_sampled(n):
     ph = synth.inclusion_phase(n, 3, 2)
     Fbar = np.diag([0.9, 1.0, 1.0])
@@ -79,3 +83,44 @@ def test_lean_local_steps_match_oracle_sampled(n):
     s.close()
     F2_ref, _ = oracle.local_newton(mat_s, F1, L1, G1, rho)
     assert rel(F2, F2_ref) < TOL
+
+
+def test_runtime_grid_mixed_solve_matches_fp64():
+    """96^3 (a run-time grid: the float phase and the double-word polish both in the lean
+    kernels) solved to tol 1e-8 in RVE_MIXED and in FP64 (the tile-table double kernels):
+    both converge and their homogenised stresses agree to 1e-6."""
+    n = 96
+    ph = synth.inclusion_phase(n, 3, 4)
+    Fbar = np.diag([0.92, 1.0, 1.01])
+    out = {}
+    for prec in ("mixed", "fp64"):
+        s = rve.Rve(3, n, "neohookean", prec, max_iter=2000)
+        s.set_material(ph, PAR)
+        info = s.solve(Fbar, 10.0, 1e-8)
+        assert info.converged, (prec, info.as_dict())
+        out[prec] = (info, s.stress())
+        s.close()
+    assert out["mixed"][0].fp64_iterations > 0
+    assert rel(out["mixed"][1], out["fp64"][1]) < 1e-6
+
+
+def test_batch_with_lean_and_tile_members_bitwise():
+    """A batch run of mixed sizes with lean members (64^3, 72^3: full local grids) and a
+    tile-table member (12^3), mixed precision to tol 1e-8: every member's iterations and
+    stress equal its alone solve bit for bit (the lean launch and the shared tile launch
+    depend on each member alone)."""
+    specs = [(3, 64, "inclusion", 21), (3, 12, "inclusion", 22), (3, 72, "laminate", 23)]
+    Fb = fbars(len(specs), 70)
+    alone = members(specs, "mixed")
+    ref = []
+    for s, F in zip(alone, Fb):
+        info = s.solve(F, 10.0, 1e-8)
+        assert info.converged
+        ref.append((info.iterations, info.fp64_iterations, s.stress()))
+        s.close()
+    mix = members(specs, "mixed")
+    infos = rve.Batch(mix).solve(Fb, np.full(len(specs), 10.0), 1e-8)
+    for s, info, (it, it64, S) in zip(mix, infos, ref):
+        assert info.iterations == it and info.fp64_iterations == it64
+        assert np.array_equal(s.stress(), S)
+        s.close()
