@@ -211,6 +211,7 @@ int begin_solve(rve* h, const double Fbar[9], double rho, double tol, cudaStream
     c.dw_state = 0;
     c.div_given = 0;
     c.z_valid = 0;
+    c.u_pair = 0;
     c.spec_have = 0;  // the spectrum kept for r_d is that of an earlier state
     c.spec_next = 0;
     c.spec_sum = 0;

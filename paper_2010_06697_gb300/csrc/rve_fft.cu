@@ -452,6 +452,11 @@ __device__ __forceinline__ void xinv_tile(const Launch& L, int bid) {
     const int nlines = (D == 3) ? n * n : n;
     const int par = (int)(ctrl->k & 1);
     V* S = reinterpret_cast<V*>(INCR ? S0 : (par ? S0 : S1));
+    // u~ as float pairs (Ctrl::u_pair): the low parts of u~_k (pair buffer (k + 1) & 1) and
+    // of u~_{k+1} (buffer k & 1); the high parts stay as written at the switch
+    const bool upair = INCR && ctrl->u_pair;
+    const float* Plo_in = INCR ? reinterpret_cast<const float*>(par ? L.U64[0] : L.U64[1]) + D * Vn : nullptr;
+    float* Plo_out = INCR ? reinterpret_cast<float*>(par ? L.U64[1] : L.U64[0]) + D * Vn : nullptr;
     TO* Out = par ? O0 : O1;
     const TO* In = par ? O1 : O0;
     V* s_tw = reinterpret_cast<V*>(smem_raw);
@@ -507,7 +512,10 @@ __device__ __forceinline__ void xinv_tile(const Launch& L, int bid) {
             if (line < nlines) {
                 const long long o = (long long)line * n + (idx - l * n);
                 if (INCR) {
-                    O_c[o] = I_c[o] + (TO)Xr[idx];
+                    if (upair)
+                        Plo_out[(long long)c * Vn + o] = Plo_in[(long long)c * Vn + o] + (float)Xr[idx];
+                    else
+                        O_c[o] = I_c[o] + (TO)Xr[idx];
                     DUout[(long long)c * Vn + o] = Xr[idx];
                 } else
                     O_c[o] = (TO)Xr[idx];
@@ -869,6 +877,10 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
     V* Sp = reinterpret_cast<V*>(INCR ? S0 : (par ? S0 : S1));
     TO* Out = par ? O0 : O1;
     const TO* In = par ? O1 : O0;
+    // u~ as float pairs (Ctrl::u_pair), as in xinv_tile
+    const bool upair = INCR && ctrl->u_pair;
+    const float* Plo_in = INCR ? reinterpret_cast<const float*>(par ? L.U64[0] : L.U64[1]) + D * Vn : nullptr;
+    float* Plo_out = INCR ? reinterpret_cast<float*>(par ? L.U64[1] : L.U64[0]) + D * Vn : nullptr;
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* buf = s_tw + N;
     V* stage = buf + H * S;
@@ -879,6 +891,21 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
     const int lt = threadIdx.x % LPB, jt = threadIdx.x / LPB;
     for (int c = c0; c < c0 + 1; ++c) {
         V* S_c = Sp + (long long)c * (Vn / 2);
+        // the low parts of u~_k this thread updates at the end, loaded now so that their
+        // latency overlaps the transform (LPB * N = 4096: four groups of four x per thread)
+        float4 lo_k[4];
+        if constexpr (INCR && std::is_same<T, float>::value) {
+            if (upair) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = (threadIdx.x + q * kFftThreads) * 4;
+                    const int line = line0 + (e >> X::LOGN);
+                    lo_k[q] = line < nlines ? *reinterpret_cast<const float4*>(
+                                                  Plo_in + (long long)c * Vn + (long long)line * N + (e & (N - 1)))
+                                            : float4{0.f, 0.f, 0.f, 0.f};
+                }
+            }
+        }
         __syncthreads();
         for (int idx = threadIdx.x; idx < LPB * H; idx += blockDim.x) {
             const int l = idx >> (X::LOGN - 1);
@@ -914,7 +941,10 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
             // four consecutive x per thread (two staged complex values): one float4 store,
             // or for the increment two double2 read-modify-writes and a float4 store of the
             // increment (fields are 256-byte aligned, x and N multiples of 4)
-            for (int idx = threadIdx.x; idx < LPB * N / 4; idx += blockDim.x) {
+            static_assert(LPB * N / 4 == 4 * kFftThreads, "four groups of four x per thread");
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int idx = threadIdx.x + q * kFftThreads;
                 const int e = idx * 4;
                 const int l = e >> X::LOGN;
                 const int xi = e & (N - 1);
@@ -925,10 +955,16 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
                     const long long o = (long long)line * N + xi;
                     if constexpr (INCR) {
                         static_assert(std::is_same<TO, double>::value, "increment accumulates in double");
-                        const double2 i0 = *reinterpret_cast<const double2*>(I_c + o);
-                        const double2 i1 = *reinterpret_cast<const double2*>(I_c + o + 2);
-                        *reinterpret_cast<double2*>(O_c + o) = double2{i0.x + (TO)a.x, i0.y + (TO)a.y};
-                        *reinterpret_cast<double2*>(O_c + o + 2) = double2{i1.x + (TO)b.x, i1.y + (TO)b.y};
+                        if (upair) {
+                            const float4 p = lo_k[q];
+                            *reinterpret_cast<float4*>(Plo_out + (long long)c * Vn + o) =
+                                float4{p.x + a.x, p.y + a.y, p.z + b.x, p.w + b.y};
+                        } else {
+                            const double2 i0 = *reinterpret_cast<const double2*>(I_c + o);
+                            const double2 i1 = *reinterpret_cast<const double2*>(I_c + o + 2);
+                            *reinterpret_cast<double2*>(O_c + o) = double2{i0.x + (TO)a.x, i0.y + (TO)a.y};
+                            *reinterpret_cast<double2*>(O_c + o + 2) = double2{i1.x + (TO)b.x, i1.y + (TO)b.y};
+                        }
                         *reinterpret_cast<float4*>(DUout + (long long)c * Vn + o) = float4{a.x, a.y, b.x, b.y};
                     } else if constexpr (std::is_same<TO, float>::value) {
                         *reinterpret_cast<float4*>(O_c + o) = float4{a.x, a.y, b.x, b.y};
@@ -948,7 +984,10 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
                 const T v = stage_r[((xi >> 1) * S + l) * 2 + (xi & 1)];
                 const long long o = (long long)line * N + xi;
                 if (INCR) {
-                    O_c[o] = I_c[o] + (TO)v;
+                    if (upair)
+                        Plo_out[(long long)c * Vn + o] = Plo_in[(long long)c * Vn + o] + (float)v;
+                    else
+                        O_c[o] = I_c[o] + (TO)v;
                     DUout[(long long)c * Vn + o] = v;
                 } else {
                     O_c[o] = (TO)v;

@@ -59,6 +59,10 @@ struct Ctrl {
     // z pass of iteration k starts; spec_next = that pass stored u^_{k+1}; spec_sum = that
     // pass wrote its tiles' sums of |k|^2 |u^_{k+1} - u^_k|^2 (read by the local pass)
     int spec_have, spec_next, spec_sum;
+    // polish entered by the direct switch: u~ as float pairs (high parts fixed at the
+    // switch, in both double u~ buffers; low parts accumulate the increments), u~_k's pair
+    // in buffer (k + 1) & 1, converted back to double at the polish's end
+    int u_pair;
     double stress[9];    // <W_F(F)> of the current state (written by the stress kernel)
     double lam_mean[9];  // <Lambda>
     long long k;         // iterations completed over the handle's life: F_k, u~_k live in buffer k & 1

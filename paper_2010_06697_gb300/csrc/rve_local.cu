@@ -2464,13 +2464,23 @@ cudaError_t launch_macro(const Launch& L, bool fp64, cudaStream_t st, bool dws) 
 // speculative next iterate is dropped: every solve begins by recomputing it.
 template <int D>
 __global__ void k_polish_state(Ctrl* __restrict__ ctrl, double* F0, double* F1, double* __restrict__ Lam,
-                               float* __restrict__ Lh, float* __restrict__ Ll, long long V, int enter) {
+                               float* __restrict__ Lh, float* __restrict__ Ll, double* U0, double* U1, long long V,
+                               int enter) {
     constexpr int NN = D * D;
     if (enter ? (ctrl->done != kRunning || ctrl->dw_state) : !ctrl->dw_state) return;
     const long long k = ctrl->k;
     double* Fa = ((k + 1) & 1) ? F1 : F0;  // buffer (k + 1) & 1
     double* Fb = (k & 1) ? F1 : F0;        // buffer k & 1
     const long long n = (long long)NN * V;
+    if (!enter && ctrl->u_pair) {
+        // u~_k from its float pair (buffer (k + 1) & 1) to double in buffer k & 1
+        const float* Ua = reinterpret_cast<const float*>(((k + 1) & 1) ? U1 : U0);
+        double* Ub = (k & 1) ? U1 : U0;
+        const long long nu = (long long)D * V;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nu;
+             i += (long long)gridDim.x * blockDim.x)
+            Ub[i] = (double)Ua[i] + (double)Ua[nu + i];
+    }
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         if (enter) {
             const dw f = dw_from(Fa[i]);
@@ -2494,6 +2504,7 @@ __global__ void k_polish_flag(Ctrl* __restrict__ ctrl, int enter) {
     if (enter ? (ctrl->done == kRunning && !ctrl->dw_state) : ctrl->dw_state) {
         ctrl->dw_state = enter;
         ctrl->z_valid = 0;
+        ctrl->u_pair = 0;  // entered from double: u~ stays double; left: u~ is double again
     }
 }
 
@@ -2516,7 +2527,7 @@ __global__ void k_polish_flag(Ctrl* __restrict__ ctrl, int enter) {
 // step, a double projection and a double fused pass.  The kernel also forms
 // R_k = F_{k+1} - G_k (G_k = Fbar + D u~_k, again as a pair, stored rounded to float) and
 // the polish's state: F_{k+1} as double-words (float, 0) in the double F buffer k & 1 and
-// u~_k in double in the double u buffer k & 1.  R_k and r go to the idle double F buffer
+// u~_k as the float pair (u~_k, 0) in the double u buffer (k + 1) & 1 (Ctrl::u_pair).  R_k and r go to the idle double F buffer
 // (k + 1) & 1: their final places are float buffers that still hold inputs
 // (k_switch_move copies them there).  n >= 4, so one conditional wrap finds every
 // neighbour up to two voxels away.
@@ -2530,7 +2541,10 @@ __global__ void __launch_bounds__(256, 2) k_switch_resid(const Ctrl* __restrict_
     const float* __restrict__ U = par ? U32_1 : U32_0;   // u~_k: buffer k & 1
     float* __restrict__ Fdw = reinterpret_cast<float*>(par ? F64_1 : F64_0);
     float* __restrict__ scr = reinterpret_cast<float*>(par ? F64_0 : F64_1);
-    double* __restrict__ Ud = par ? U64_1 : U64_0;
+    // u~_k as a float pair (Ctrl::u_pair): (u~_k, 0) in buffer (k + 1) & 1, the high part
+    // also in buffer k & 1
+    float* __restrict__ Up = reinterpret_cast<float*>(par ? U64_0 : U64_1);
+    float* __restrict__ Uq = reinterpret_cast<float*>(par ? U64_1 : U64_0);
     __shared__ dw Fb[NN + 1];  // Fbar as double-words, then 1/rho
     if (threadIdx.x <= NN)
         Fb[threadIdx.x] = dw_from(threadIdx.x < NN ? ctrl->Fbar[(threadIdx.x / D) * 3 + threadIdx.x % D] : 1.0 / ctrl->rho);
@@ -2574,7 +2588,9 @@ __global__ void __launch_bounds__(256, 2) k_switch_resid(const Ctrl* __restrict_
                 scr[(long long)(i * D + j) * V + v] = dw_add_f(dw_neg(G), Fc[0]).hi;
             }
             scr[(long long)(NN + i) * V + v] = dw_mul_f(acc, -hn).hi;
-            Ud[(long long)i * V + v] = (double)uc;
+            Up[(long long)i * V + v] = uc;
+            Up[(long long)(D + i) * V + v] = 0.f;
+            Uq[(long long)i * V + v] = uc;
         }
 #pragma unroll
         for (int p = 0; p < NN; ++p) {
@@ -2606,6 +2622,7 @@ __global__ void k_switch_move(Ctrl* __restrict__ ctrl, const double* F64_0, cons
         ctrl->div_given = 1;
         ctrl->dw_state = 1;
         ctrl->z_valid = 0;
+        ctrl->u_pair = 1;
     }
 }
 
@@ -2613,11 +2630,11 @@ cudaError_t launch_polish_state(const Launch& L, bool enter, cudaStream_t st) {
     if (is_lce(L.model)) return cudaSuccess;  // the LCE polish stays in double
     const int blocks = L.local_blocks;
     if (L.dim == 3)
-        k_polish_state<3><<<blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.L64, L.LH32, L.LL32, L.V,
-                                                   enter ? 1 : 0);
+        k_polish_state<3><<<blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.L64, L.LH32, L.LL32, L.U64[0],
+                                                   L.U64[1], L.V, enter ? 1 : 0);
     else
-        k_polish_state<2><<<blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.L64, L.LH32, L.LL32, L.V,
-                                                   enter ? 1 : 0);
+        k_polish_state<2><<<blocks, 256, 0, st>>>(L.ctrl, L.F64[0], L.F64[1], L.L64, L.LH32, L.LL32, L.U64[0],
+                                                   L.U64[1], L.V, enter ? 1 : 0);
     k_polish_flag<<<1, 1, 0, st>>>(L.ctrl, enter ? 1 : 0);
     return cudaGetLastError();
 }

@@ -88,7 +88,8 @@ def test_lean_local_steps_match_oracle_sampled(n):
 def test_runtime_grid_mixed_solve_matches_fp64():
     """96^3 (a run-time grid: the float phase and the double-word polish both in the lean
     kernels) solved to tol 1e-8 in RVE_MIXED and in FP64 (the tile-table double kernels):
-    both converge and their homogenised stresses agree to 1e-6."""
+    both converge, their homogenised stresses agree to 1e-6, and so do the returned states
+    F, Lambda and u~ (the mixed polish keeps u~ as float pairs and returns it in double)."""
     n = 96
     ph = synth.inclusion_phase(n, 3, 4)
     Fbar = np.diag([0.92, 1.0, 1.01])
@@ -98,10 +99,13 @@ def test_runtime_grid_mixed_solve_matches_fp64():
         s.set_material(ph, PAR)
         info = s.solve(Fbar, 10.0, 1e-8)
         assert info.converged, (prec, info.as_dict())
-        out[prec] = (info, s.stress())
+        out[prec] = (info, s.stress(), {w: s.get_field(w) for w in (rve.RVE_FIELD_F, rve.RVE_FIELD_LAMBDA,
+                                                                       rve.RVE_FIELD_U)})
         s.close()
     assert out["mixed"][0].fp64_iterations > 0
     assert rel(out["mixed"][1], out["fp64"][1]) < 1e-6
+    for w, fm in out["mixed"][2].items():
+        assert rel(fm, out["fp64"][2][w]) < 1e-6, w
 
 
 def test_batch_with_lean_and_tile_members_bitwise():
