@@ -51,12 +51,13 @@ L2_BYTES = 129e6
 #   local_r (double-word polish): read the float u~ increment (d), R, F hi, F lo, Lambda lo, Z
 #   (d^2 floats each); write F lo, Lambda lo, R (d^2 floats each); phase id
 #   xfwd_incr: read R (d^2 floats), write the float spectrum;  xinv_incr: read the float spectrum
-#   and u~_k (double), write u~_{k+1} (double) and the float increment
+#   and the low parts of u~_k (float pairs after the direct switch), write the low parts of
+#   u~_{k+1} and the float increment
 def bytes_per_voxel(cls: str, s: int, d: int = 3) -> float:
     return {"local": (d + 4 * d * d) * s + 1 + (d * s if s == 8 else 0), "local_first": (d + 3 * d * d) * s + 1,
             "xfwd": (2 * d * d + d) * s, "fwd_y": 2 * d * s, "solve": (4 if s == 4 else 2) * d * s,
             "inv_y": 2 * d * s, "xinv": 2 * d * s, "local_r": d * 4 + 8 * d * d * 4 + 1,
-            "xfwd_incr": (d * d + d) * 4, "xinv_incr": d * 4 + 2 * d * 8 + d * 4}[cls]
+            "xfwd_incr": (d * d + d) * 4, "xinv_incr": 4 * d * 4}[cls]
 
 
 # DRAM bytes (read + write) per launch measured with ncu on the 128^3 inclusion cell

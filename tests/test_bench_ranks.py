@@ -100,7 +100,7 @@ def test_byte_model_matches_the_documented_per_voxel_figures():
     21 s, four FFT passes 6 s each); the float iteration of the headline takes r_d from the
     spectral solve, so its local pass reads 3 scalars less (39 s + 1) and its z solve also
     reads and writes the kept spectrum (12 s): 90 s + 1 with s = 4.  The double-word polish
-    local step moves 301 B, its increment x passes 48 and 72 B."""
+    local step moves 301 B, its increment x passes 48 and 48 B (u~ as float pairs)."""
     sys.path.insert(0, ROOT)
     import bench
     it = sum(bench.bytes_per_voxel(c, 8) for c in ("local", "xfwd", "fwd_y", "solve", "inv_y", "xinv"))
@@ -110,6 +110,6 @@ def test_byte_model_matches_the_documented_per_voxel_figures():
     assert it == 90 * 4 + 1
     assert bench.bytes_per_voxel("local", 4) == 39 * 4 + 1 and bench.bytes_per_voxel("solve", 4) == 12 * 4
     assert bench.bytes_per_voxel("local_r", 0) == 301
-    assert bench.bytes_per_voxel("xfwd_incr", 0) == 48 and bench.bytes_per_voxel("xinv_incr", 0) == 72
+    assert bench.bytes_per_voxel("xfwd_incr", 0) == 48 and bench.bytes_per_voxel("xinv_incr", 0) == 48
     # 2D: d = 2 in the same formulas
     assert bench.bytes_per_voxel("local", 8, d=2) == (4 + 16) * 8 + 1
