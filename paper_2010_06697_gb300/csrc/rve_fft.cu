@@ -942,8 +942,7 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
             // or for the increment two double2 read-modify-writes and a float4 store of the
             // increment (fields are 256-byte aligned, x and N multiples of 4)
             static_assert(LPB * N / 4 == 4 * kFftThreads, "four groups of four x per thread");
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            auto store = [&](int q) {
                 const int idx = threadIdx.x + q * kFftThreads;
                 const int e = idx * 4;
                 const int l = e >> X::LOGN;
@@ -973,6 +972,15 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
                         *reinterpret_cast<double2*>(O_c + o + 2) = double2{(TO)b.x, (TO)b.y};
                     }
                 }
+            };
+            // unrolled where the prefetched low parts of u~ live in registers; the plain
+            // float pass runs faster rolled
+            if constexpr (INCR) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) store(q);
+            } else {
+#pragma unroll 1
+                for (int q = 0; q < 4; ++q) store(q);
             }
             continue;
         }
