@@ -63,8 +63,9 @@ def bytes_per_voxel(cls: str, s: int, d: int = 3) -> float:
 # DRAM bytes (read + write) per launch measured with ncu on the 128^3 inclusion cell
 # (profiles/), keyed by (kernel class, precision); absent = not captured since the
 # kernel last changed
-TRAFFIC = {("local", "fp32"): 178665984 + 91949056, ("local_r", "fp64"): 415438336 + 184841472,
-           ("xfwd", "fp32"): 151019264 + 9842176, ("xinv", "fp32"): 25181952, ("solve", "fp32"): 50366976 + 333056}
+TRAFFIC = {("local", "fp32"): 178640128 + 91970304, ("local_r", "fp64"): 415352064 + 184859904,
+           ("xfwd", "fp32"): 151019264 + 9842176, ("solve", "fp32"): 50366976 + 333056,
+           ("xinv_incr", "fp32"): 50375680 + 3794688}
 # FP32 flops per launch by kernel class, where counted with ncu for the current kernel
 # (none since the float local step became the closed form: no ALU view is reported)
 FLOPS = {}
