@@ -402,6 +402,7 @@ int run_chunk_profiled(rve* h, bool fp64, bool incr) {
     for (long long i = 0; i < ran && i < h->opt.check_every; ++i) {
         cudaEvent_t* e = &h->pev[(size_t)i * per];
         for (int st = 0; st < S; ++st) {
+            if (admm::fft_stage_empty(h->E, fp64 && !incr, st)) continue;  // folded into a fused pass
             int cls = fft_class(h->dim, st), fb = f;
             if (incr) {
                 fb = 0;

@@ -1005,6 +1005,154 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
     }
 }
 
+// ------------------------------------------------------------------ fused inverse y + x passes (3D float, N = 128)
+// The inverse y and x transforms of one z-plane of one component in one block: the plane's
+// 64 columns take faxis_fixed_tile's inverse y transform (AXIS 1, MODE 1) in four rounds
+// of 16, into a shared plane (128 y rows of 64 x-frequencies, pitch 66) instead of back to
+// the spectrum in L2; then xinv_fixed_tile's four groups of 32 lines take their
+// complex-to-real transforms from it.  Same arithmetic in the same order as the two
+// separate passes (the same bits), with one L2 round trip of the spectrum and one launch
+// less per iteration.  While a group's x transform runs, that group's plane rows (32 x 66
+// values) hold its buffer (64 frequencies x 33 lines, XPlan's padded stride).  68.6 KB of
+// shared memory: 3 blocks per SM, one wave for the 384 planes of a 128^3 cell.  Tiles are
+// those of the x passes (tiles_x, 1536 per RVE); tiles 384 and up have nothing to do.
+// (The forward counterpart, the x transforms of a plane's lines followed by the y
+// transforms of its columns, ran slower than the two separate passes and is not used.)
+struct PlaneFused {
+    static constexpr int N = 128, H = 64, P = 66, LPB = 32, S = 33, G = N / LPB;
+};
+
+template <typename TO, bool INCR>
+__device__ __forceinline__ void yxinv_tile(const Launch& L, int bid) {
+    using T = float;
+    using V = float2;
+    using Args = FftArgs<T>;
+    using X = XPlan<128>;
+    using PF = PlaneFused;
+    constexpr int N = PF::N, H = PF::H, P = PF::P, LPB = PF::LPB, S = PF::S, TT = ColPlan<H>::T;
+    if (bid >= 3 * N) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Ctrl* __restrict__ ctrl = L.ctrl;
+    if (ctrl->done) return;
+    T* S0 = INCR ? (T*)L.S32 : Args::U(L, 0);
+    T* S1 = INCR ? (T*)L.S32 : Args::U(L, 1);
+    TO* O0 = INCR ? (TO*)L.U64[0] : (TO*)Args::U(L, 0);
+    TO* O1 = INCR ? (TO*)L.U64[1] : (TO*)Args::U(L, 1);
+    T* __restrict__ DUout = (T*)L.D32;
+    constexpr long long Vn = (long long)N * N * N;
+    const int par = (int)(ctrl->k & 1);
+    V* Sp = reinterpret_cast<V*>(INCR ? S0 : (par ? S0 : S1));
+    TO* Out = par ? O0 : O1;
+    const TO* In = par ? O1 : O0;
+    const bool upair = INCR && ctrl->u_pair;  // u~ as float pairs (Ctrl::u_pair)
+    const float* Plo_in = INCR ? reinterpret_cast<const float*>(par ? L.U64[0] : L.U64[1]) + 3 * Vn : nullptr;
+    float* Plo_out = INCR ? reinterpret_cast<float*>(par ? L.U64[1] : L.U64[0]) + 3 * Vn : nullptr;
+    V* s_tw = reinterpret_cast<V*>(smem_raw);
+    V* plane = s_tw + N;
+    load_twiddles(s_tw, Args::tw(L), N);
+    const int c = bid / N, z = bid % N;
+    // inverse y transforms of the plane's columns, 16 at a time (faxis_fixed_tile, AXIS 1,
+    // MODE 1), into the shared plane
+    using CP = ColPlan<N>;
+    {
+        const int cl = threadIdx.x % CP::TK, j = threadIdx.x / CP::TK;
+        const V* S_c = Sp + (long long)c * (Vn / 2) + (long long)z * N * H;
+        for (int k0 = 0; k0 < H; k0 += CP::TK) {
+            V x[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) x[r] = S_c[(long long)(j + CP::T * r) * H + k0 + cl];
+            col_fft<N, true, 1, P, true>(x, plane + k0, s_tw, j, cl);
+            __syncthreads();  // the transform's last readers of these columns are done
+#pragma unroll
+            for (int r = 0; r < 8; ++r) plane[(j + CP::T * r) * P + k0 + cl] = x[r];
+        }
+    }
+    const int lt = threadIdx.x % LPB, jt = threadIdx.x / LPB;
+    TO* O_c = Out + (long long)c * Vn;
+    const TO* I_c = In + (long long)c * Vn;
+    for (int g = 0; g < PF::G; ++g) {
+        V* gr = plane + g * LPB * P;
+        const int line0 = z * N + g * LPB;
+        float4 lo_k[4];  // low parts of u~_k for the final update (see xinv_fixed_tile)
+        if constexpr (INCR) {
+            if (upair) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = (threadIdx.x + q * kFftThreads) * 4;
+                    lo_k[q] = *reinterpret_cast<const float4*>(Plo_in + (long long)c * Vn +
+                                                               (long long)(line0 + (e >> X::LOGN)) * N + (e & (N - 1)));
+                }
+            }
+        }
+        __syncthreads();  // the plane is complete / the previous group's readers are done
+        // complex-to-real split of the group's rows into registers, then into its x buffer
+        V zz[LPB * H / kFftThreads];
+#pragma unroll
+        for (int i = 0; i < LPB * H / kFftThreads; ++i) {
+            const int idx = threadIdx.x + i * kFftThreads;
+            const int l = idx >> (X::LOGN - 1);
+            const int kk = idx & (H - 1);
+            const V Xk = gr[l * P + kk];
+            if (kk == 0) {
+                zz[i] = V{T(0.5) * (Xk.x + Xk.y), T(0.5) * (Xk.x - Xk.y)};
+            } else {
+                const V Xc = cconj(gr[l * P + (H - kk)]);
+                const V E = cscale(cadd(Xk, Xc), T(0.5));
+                const V O = cmul(cscale(csub(Xk, Xc), T(0.5)), cconj(s_tw[kk]));
+                zz[i] = cadd(E, mul_i(O));
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < LPB * H / kFftThreads; ++i) {
+            const int idx = threadIdx.x + i * kFftThreads;
+            gr[(idx & (H - 1)) * S + (idx >> (X::LOGN - 1))] = zz[i];
+        }
+        __syncthreads();
+        V xr[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) xr[r] = gr[(jt + TT * r) * S + lt];
+        col_fft<H, true, 2, S, true>(xr, gr, s_tw, jt, lt);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 8; ++r) gr[(jt + TT * r) * S + lt] = xr[r];
+        __syncthreads();
+        // four consecutive x per thread (xinv_fixed_tile's float stores)
+        auto store = [&](int q) {
+            const int idx = threadIdx.x + q * kFftThreads;
+            const int e = idx * 4;
+            const int l = e >> X::LOGN;
+            const int xi = e & (N - 1);
+            const int line = line0 + l;
+            const V a = gr[(xi >> 1) * S + l];
+            const V b = gr[((xi >> 1) + 1) * S + l];
+            const long long o = (long long)line * N + xi;
+            if constexpr (INCR) {
+                if (upair) {
+                    const float4 p = lo_k[q];
+                    *reinterpret_cast<float4*>(Plo_out + (long long)c * Vn + o) =
+                        float4{p.x + a.x, p.y + a.y, p.z + b.x, p.w + b.y};
+                } else {
+                    const double2 i0 = *reinterpret_cast<const double2*>(I_c + o);
+                    const double2 i1 = *reinterpret_cast<const double2*>(I_c + o + 2);
+                    *reinterpret_cast<double2*>(O_c + o) = double2{i0.x + (TO)a.x, i0.y + (TO)a.y};
+                    *reinterpret_cast<double2*>(O_c + o + 2) = double2{i1.x + (TO)b.x, i1.y + (TO)b.y};
+                }
+                *reinterpret_cast<float4*>(DUout + (long long)c * Vn + o) = float4{a.x, a.y, b.x, b.y};
+            } else {
+                *reinterpret_cast<float4*>(O_c + o) = float4{a.x, a.y, b.x, b.y};
+            }
+        };
+        if constexpr (INCR) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) store(q);
+        } else {
+#pragma unroll 1
+            for (int q = 0; q < 4; ++q) store(q);
+        }
+    }
+}
+
 // faxis_tile with a fixed column length N (see ColPlan); same tiles and modes.
 template <typename T, int N, int D, int AXIS, int MODE, bool INCR>
 __device__ __forceinline__ void faxis_fixed_tile(const Launch& L, int bid) {
@@ -1156,6 +1304,19 @@ k_faxis(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntil
     }
 }
 
+// 3 blocks of 68.6 KB per SM (one wave of a 128^3 cell's 384 planes): at most 85 registers
+template <typename TO, bool INCR>
+__global__ void __launch_bounds__(kFftThreads, 3) k_yxinv128(const Launch* __restrict__ rds,
+                                                          const int2* __restrict__ tiles, int ntiles) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        yxinv_tile<TO, INCR>(rds[tl.x], tl.y);
+        __syncthreads();
+    }
+}
+
+constexpr size_t kPlaneSmem = (size_t)(PlaneFused::N + PlaneFused::N * PlaneFused::P) * sizeof(float2);
+
 // The float z solve, which also keeps the spectrum for r_d, is held to 64 registers (4
 // blocks per SM): with 73 registers and 3 blocks it runs 2 us slower per 128^3 pass.
 template <typename T, int N, int D, int AXIS, int MODE, bool INCR>
@@ -1287,6 +1448,13 @@ void go_xinv(const Exec& E, size_t smx) {
 // (3D: 0 x-forward, 1 y-forward, 2 z solve, 3 y-inverse, 4 x-inverse;
 //  2D: 0 x-forward, 1 y solve, 2 x-inverse).  INCR: the float increment
 // projection of the double polish (see launch_fft_incr).
+// the float passes of 3D grids of N = 128 with the fixed kernels' geometry fuse the inverse
+// y and x transforms of each z-plane (yxinv_tile)
+bool fused_xy(const Exec& E) {
+    return E.rep->dim == 3 && E.uniform_geom && E.uniform_n == 128 && E.rep->lpb == XPlan<128>::LPB &&
+           E.rep->tk32 == ColPlan<128>::TK;
+}
+
 template <typename T, int D, bool INCR>
 cudaError_t run_fft(const Exec& E, int stage) {
     const int f = std::is_same<T, double>::value ? 1 : 0;
@@ -1295,15 +1463,24 @@ cudaError_t run_fft(const Exec& E, int stage) {
     const int last = D == 3 ? 4 : 2;
     auto want = [&](int s) { return stage < 0 || stage == s; };
     static_assert(!INCR || std::is_same<T, float>::value, "increment projection runs in float");
+    bool finv = false;  // inverse y and x passes of a z-plane fused in one block
+    if constexpr (D == 3 && std::is_same<T, float>::value) finv = fused_xy(E);
     if (want(0)) go_xfwd<T, D, INCR>(E, smx);
     if constexpr (D == 3) {
         if (want(1)) go_axis<T, D, 1, 0, INCR>(E, ax, sma);
         if (want(2)) go_axis<T, D, 2, 2, INCR>(E, ax, sma);
-        if (want(3)) go_axis<T, D, 1, 1, INCR>(E, ax, sma);
+        if (!finv && want(3)) go_axis<T, D, 1, 1, INCR>(E, ax, sma);
     } else if (want(1)) {
         go_axis<T, D, 1, 2, INCR>(E, ax, sma);
     }
-    if (want(last)) {
+    if (finv && want(last)) {
+        if constexpr (D == 3 && std::is_same<T, float>::value) {
+            if constexpr (INCR)
+                go(k_yxinv128<double, true>, E, kTilesX, kPlaneSmem);
+            else
+                go(k_yxinv128<float, false>, E, kTilesX, kPlaneSmem);
+        }
+    } else if (want(last)) {
         if constexpr (INCR)
             go_xinv<float, double, D, true>(E, smx);
         else
@@ -1321,6 +1498,10 @@ cudaError_t set_smem_attrs(int bytes) {
     };
     set((const void*)k_xfwd<T, D, false>);
     set((const void*)k_xinv<T, T, D, false>);
+    if constexpr (std::is_same<T, float>::value && D == 3) {
+        set((const void*)k_yxinv128<float, false>);
+        set((const void*)k_yxinv128<double, true>);
+    }
     set((const void*)k_faxis<T, D, 1, 0, false>);
     set((const void*)k_faxis<T, D, 1, 1, false>);
     set((const void*)k_faxis<T, D, 1, 2, false>);
@@ -1364,6 +1545,10 @@ cudaError_t launch_fft(const Exec& E, bool fp64, int stage) {
     const int dim = E.rep->dim;
     if (fp64) return dim == 3 ? run_fft<double, 3, false>(E, stage) : run_fft<double, 2, false>(E, stage);
     return dim == 3 ? run_fft<float, 3, false>(E, stage) : run_fft<float, 2, false>(E, stage);
+}
+
+bool fft_stage_empty(const Exec& E, bool fp64, int stage) {
+    return !fp64 && fused_xy(E) && stage == 3;
 }
 
 cudaError_t launch_fft_incr(const Exec& E, int stage) {

@@ -263,6 +263,8 @@ cudaError_t launch_switch_direct(const Launch& L, cudaStream_t st);
 cudaError_t launch_convert(const Launch& L, bool to_fp64);
 // rve_fft.cu
 cudaError_t launch_fft(const Exec& E, bool fp64, int stage = -1);
+// whether FFT stage `stage` issues no kernel (folded into a fused neighbour)
+bool fft_stage_empty(const Exec& E, bool fp64, int stage);
 // Projection of the float increment R into the double u~: u~_{k+1} = u~_k + P(R).
 cudaError_t launch_fft_incr(const Exec& E, int stage = -1);
 inline int fft_stages(int dim) { return dim == 3 ? 5 : 3; }
