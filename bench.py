@@ -52,7 +52,9 @@ L2_BYTES = 129e6
 #   (d^2 floats each); write F lo, Lambda lo, R (d^2 floats each); phase id
 #   xfwd_incr: read R (d^2 floats), write the float spectrum;  xinv_incr: read the float spectrum
 #   and the low parts of u~_k (float pairs after the direct switch), write the low parts of
-#   u~_{k+1} and the float increment
+#   u~_{k+1} and the float increment.  On the 128^3 float grid the inverse y and x transforms
+#   run fused per z-plane: xinv and xinv_incr then time both (the same bytes: the spectrum
+#   plane stays in shared memory) and inv_y has no launches
 def bytes_per_voxel(cls: str, s: int, d: int = 3) -> float:
     return {"local": (d + 4 * d * d) * s + 1 + (d * s if s == 8 else 0), "local_first": (d + 3 * d * d) * s + 1,
             "xfwd": (2 * d * d + d) * s, "fwd_y": 2 * d * s, "solve": (4 if s == 4 else 2) * d * s,
@@ -65,7 +67,7 @@ def bytes_per_voxel(cls: str, s: int, d: int = 3) -> float:
 # kernel last changed
 TRAFFIC = {("local", "fp32"): 178640128 + 91970304, ("local_r", "fp64"): 415352064 + 184859904,
            ("xfwd", "fp32"): 151019264 + 9842176, ("solve", "fp32"): 50366976 + 333056,
-           ("xinv_incr", "fp32"): 50375680 + 3794688}
+           ("xinv", "fp32"): 25195776 + 0, ("xinv_incr", "fp32"): 50370560 + 3523328}
 # FP32 flops per launch by kernel class, where counted with ncu for the current kernel
 # (none since the float local step became the closed form: no ALU view is reported)
 FLOPS = {}
