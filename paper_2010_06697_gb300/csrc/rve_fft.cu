@@ -314,48 +314,63 @@ __device__ __forceinline__ void xfwd_tile(const Launch& L, int bid) {
                             zm = v + (zq == 0 ? (n - 1) * s2 : -s2);
                         }
                     }
-                    auto diffs = [&](const float* a0, const float* a1, float* dx, float* dy) {
-                        const float4 ctr = act ? *reinterpret_cast<const float4*>(a0 + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    // all loads of the element group issued before the first use (as in
+                    // xfwd_fixed_tile), the line- and warp-end x neighbours among them
+                    auto ld4 = [](const float* p) { return *reinterpret_cast<const float4*>(p); };
+                    const float* A0[2] = {F_c0, L_c0};
+                    const float* A1[2] = {F_c1, L_c1};
+                    const float* A2[2] = {F + (long long)(c * D + 2) * Vn,
+                                          INCR ? nullptr : Lam + (long long)(c * D + 2) * Vn};
+                    constexpr int NA = INCR ? 1 : 2;
+                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const bool wl = act && (x == 0 || lane == 0), wr = act && (x + 4 == n || lane == 31);
+                    float4 ac[2], ap[2], am[2], au[2] = {z4, z4}, ad[2] = {z4, z4};
+                    float el[2] = {}, er[2] = {};
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) {
+                        ac[a] = act ? ld4(A0[a] + v) : z4;
+                        ap[a] = act ? ld4(A1[a] + yp) : z4;
+                        am[a] = act ? ld4(A1[a] + ym) : z4;
+                        if constexpr (D == 3) {
+                            if (act) {
+                                au[a] = ld4(A2[a] + zp);
+                                ad[a] = ld4(A2[a] + zm);
+                            }
+                        }
+                        if (wl) el[a] = A0[a][v + (x == 0 ? n - 1 : -1)];
+                        if (wr) er[a] = A0[a][v + (x + 4 == n ? 4 - n : 4)];
+                    }
+                    float dx[2][4], dy[2][4] = {}, dz[2][4] = {};
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) {
+                        const float4 ctr = ac[a];
                         float left = __shfl_sync(0xffffffffu, ctr.w, (lane + 31) & 31);
                         float right = __shfl_sync(0xffffffffu, ctr.x, (lane + 1) & 31);
+                        if (wl) left = el[a];
+                        if (wr) right = er[a];
                         if (act) {
-                            if (x == 0)
-                                left = a0[v + n - 1];
-                            else if (lane == 0)
-                                left = a0[v - 1];
-                            if (x + 4 == n)
-                                right = a0[v + 4 - n];
-                            else if (lane == 31)
-                                right = a0[v + 4];
-                            const float4 p = *reinterpret_cast<const float4*>(a1 + yp);
-                            const float4 m = *reinterpret_cast<const float4*>(a1 + ym);
-                            dy[0] = p.x - m.x;
-                            dy[1] = p.y - m.y;
-                            dy[2] = p.z - m.z;
-                            dy[3] = p.w - m.w;
+                            dy[a][0] = ap[a].x - am[a].x;
+                            dy[a][1] = ap[a].y - am[a].y;
+                            dy[a][2] = ap[a].z - am[a].z;
+                            dy[a][3] = ap[a].w - am[a].w;
+                            if constexpr (D == 3) {
+                                dz[a][0] = au[a].x - ad[a].x;
+                                dz[a][1] = au[a].y - ad[a].y;
+                                dz[a][2] = au[a].z - ad[a].z;
+                                dz[a][3] = au[a].w - ad[a].w;
+                            }
                         }
-                        dx[0] = ctr.y - left;
-                        dx[1] = ctr.z - ctr.x;
-                        dx[2] = ctr.w - ctr.y;
-                        dx[3] = right - ctr.z;
-                    };
-                    auto zdiff = [&](const float* a2, float* dz) {
-                        const float4 u = *reinterpret_cast<const float4*>(a2 + zp);
-                        const float4 d = *reinterpret_cast<const float4*>(a2 + zm);
-                        dz[0] = u.x - d.x;
-                        dz[1] = u.y - d.y;
-                        dz[2] = u.z - d.z;
-                        dz[3] = u.w - d.w;
-                    };
-                    float fx[4], fy[4] = {}, fz[4] = {}, lx[4], ly[4] = {}, lz[4] = {};
-                    diffs(F_c0, F_c1, fx, fy);
-                    if (!INCR) diffs(L_c0, L_c1, lx, ly);
-                    if constexpr (D == 3) {
-                        if (act) {
-                            zdiff(F + (long long)(c * D + 2) * Vn, fz);
-                            if (!INCR) zdiff(Lam + (long long)(c * D + 2) * Vn, lz);
-                        }
+                        dx[a][0] = ctr.y - left;
+                        dx[a][1] = ctr.z - ctr.x;
+                        dx[a][2] = ctr.w - ctr.y;
+                        dx[a][3] = right - ctr.z;
                     }
+                    const float* fx = dx[0];
+                    const float* fy = dy[0];
+                    const float* fz = dz[0];
+                    const float* lx = dx[1];
+                    const float* ly = dy[1];
+                    const float* lz = dz[1];
                     float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (act) {
                         float r[4];
@@ -764,48 +779,65 @@ __device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid) {
                 const int y = y0 + l;
                 const Idx v = (Idx)line0 * N + e;
                 const Idx yp = v + (y + 1 == N ? (1 - N) * sn : sn), ym = v + (y == 0 ? (N - 1) * sn : -sn);
-                auto diffs = [&](const T* a0, const T* a1, const T* a2, T* dx, T* dy, T* dz) {
-                    const float4 c = *reinterpret_cast<const float4*>(a0 + v);
-                    T left = __shfl_sync(0xffffffffu, c.w, (lane + 31) & 31);
-                    T right = __shfl_sync(0xffffffffu, c.x, (lane + 1) & 31);
-                    if constexpr (N > 128) {
-                        if (lane == 0) left = a0[v + (x == 0 ? N - 1 : -1)];
-                        if (lane == 31) right = a0[v + (x + 4 == N ? 4 - N : 4)];
-                    }
-                    dx[0] = c.y - left;
-                    dx[1] = c.z - c.x;
-                    dx[2] = c.w - c.y;
-                    dx[3] = right - c.z;
-                    const float4 p = *reinterpret_cast<const float4*>(a1 + yp);
-                    const float4 m = *reinterpret_cast<const float4*>(a1 + ym);
-                    dy[0] = p.x - m.x;
-                    dy[1] = p.y - m.y;
-                    dy[2] = p.z - m.z;
-                    dy[3] = p.w - m.w;
-                    const float4 zu = *reinterpret_cast<const float4*>(a2 + v + zp);
-                    const float4 zd = *reinterpret_cast<const float4*>(a2 + v + zm);
-                    dz[0] = zu.x - zd.x;
-                    dz[1] = zu.y - zd.y;
-                    dz[2] = zu.z - zd.z;
-                    dz[3] = zu.w - zd.w;
-                };
+                // all ten (increment: five) loads of the four elements are issued before the
+                // first use: with the loads of the F and the Lambda stencils interleaved
+                // with the lane shuffles, the pass took 48.6 us at 128^3 instead of 41.9
+                auto ld4 = [](const T* a) { return *reinterpret_cast<const float4*>(a); };
                 T o[4];
                 if (INCR && divg) {  // the switch to the polish handed in D^T W itself (D32)
-                    const float4 g = *reinterpret_cast<const float4*>((const T*)L.D32 + (long long)c * Vn + v);
+                    const float4 g = ld4((const T*)L.D32 + (long long)c * Vn + v);
                     o[0] = g.x;
                     o[1] = g.y;
                     o[2] = g.z;
                     o[3] = g.w;
                 } else {
-                    T fx[4], fy[4], fz[4], lx[4], ly[4], lz[4];
-                    diffs(F_c0, F_c1, F_c2, fx, fy, fz);
-                    if (!INCR) diffs(L_c0, L_c1, L_c2, lx, ly, lz);
+                    float4 ac[2], ap[2], am[2], au[2], ad[2];
+                    T el[2] = {}, er[2] = {};  // warp-end x neighbours (N > 128)
+                    const T* A0[2] = {F_c0, L_c0};
+                    const T* A1[2] = {F_c1, L_c1};
+                    const T* A2[2] = {F_c2, L_c2};
+                    constexpr int NA = INCR ? 1 : 2;
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) {
+                        ac[a] = ld4(A0[a] + v);
+                        ap[a] = ld4(A1[a] + yp);
+                        am[a] = ld4(A1[a] + ym);
+                        au[a] = ld4(A2[a] + v + zp);
+                        ad[a] = ld4(A2[a] + v + zm);
+                        if constexpr (N > 128) {
+                            if (lane == 0) el[a] = A0[a][v + (x == 0 ? N - 1 : -1)];
+                            if (lane == 31) er[a] = A0[a][v + (x + 4 == N ? 4 - N : 4)];
+                        }
+                    }
+                    T dx[2][4], dy[2][4], dz[2][4];
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) {
+                        const float4 c = ac[a];
+                        T left = __shfl_sync(0xffffffffu, c.w, (lane + 31) & 31);
+                        T right = __shfl_sync(0xffffffffu, c.x, (lane + 1) & 31);
+                        if constexpr (N > 128) {
+                            if (lane == 0) left = el[a];
+                            if (lane == 31) right = er[a];
+                        }
+                        dx[a][0] = c.y - left;
+                        dx[a][1] = c.z - c.x;
+                        dx[a][2] = c.w - c.y;
+                        dx[a][3] = right - c.z;
+                        dy[a][0] = ap[a].x - am[a].x;
+                        dy[a][1] = ap[a].y - am[a].y;
+                        dy[a][2] = ap[a].z - am[a].z;
+                        dy[a][3] = ap[a].w - am[a].w;
+                        dz[a][0] = au[a].x - ad[a].x;
+                        dz[a][1] = au[a].y - ad[a].y;
+                        dz[a][2] = au[a].z - ad[a].z;
+                        dz[a][3] = au[a].w - ad[a].w;
+                    }
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
-                        T q = fx[r] + fy[r];
-                        if (!INCR) q -= (lx[r] + ly[r]) * inv_rho;
-                        q += fz[r];
-                        if (!INCR) q -= lz[r] * inv_rho;
+                        T q = dx[0][r] + dy[0][r];
+                        if (!INCR) q -= (dx[1][r] + dy[1][r]) * inv_rho;
+                        q += dz[0][r];
+                        if (!INCR) q -= dz[1][r] * inv_rho;
                         o[r] = -q * half_n;
                     }
                 }
