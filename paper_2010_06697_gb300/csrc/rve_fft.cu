@@ -237,7 +237,7 @@ struct FftArgs<float> {
 // INCR: Q is the increment R given in F0 (= F1), Lambda is not read, and the
 // spectrum goes to U0 (= U1).
 template <typename T, int D, bool INCR>
-__device__ __forceinline__ void xfwd_tile(const Launch& L, int bid) {
+__device__ __forceinline__ void xfwd_tile(const Launch& L, int bid, const void*& twp) {
     using V = typename Cx<T>::t;
     using Args = FftArgs<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -264,7 +264,10 @@ __device__ __forceinline__ void xfwd_tile(const Launch& L, int bid) {
     V* A = s_tw + n;
     V* B = A + lpb * H;
     T* Ar = reinterpret_cast<T*>(A);
-    load_twiddles(s_tw, g_tw, n);
+    if (twp != (const void*)g_tw) {  // the RVE's table, loaded when the block's RVE changes
+        load_twiddles(s_tw, g_tw, n);
+        twp = g_tw;
+    }
     const int line0 = bid * lpb;
     if (line0 >= nlines) return;  // tiles counted for the fixed kernels' one component each
     const FastDiv nl{(unsigned)lpb, 0u, 0u};  // transforms per block (only the count is used)
@@ -448,7 +451,7 @@ __device__ __forceinline__ void xfwd_tile(const Launch& L, int bid) {
 // the precision TO of the state buffers O0/O1.
 // INCR also stores the float increment itself in DUout (read by the next local step for r_d).
 template <typename T, typename TO, int D, bool INCR>
-__device__ __forceinline__ void xinv_tile(const Launch& L, int bid) {
+__device__ __forceinline__ void xinv_tile(const Launch& L, int bid, const void*& twp) {
     using V = typename Cx<T>::t;
     using Args = FftArgs<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -477,7 +480,10 @@ __device__ __forceinline__ void xinv_tile(const Launch& L, int bid) {
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* A = s_tw + n;
     V* B = A + lpb * H;
-    load_twiddles(s_tw, g_tw, n);
+    if (twp != (const void*)g_tw) {  // the RVE's table, loaded when the block's RVE changes
+        load_twiddles(s_tw, g_tw, n);
+        twp = g_tw;
+    }
     __syncthreads();
     const int line0 = bid * lpb;
     if (line0 >= nlines) return;  // tiles counted for the fixed kernels' one component each
@@ -545,7 +551,7 @@ __device__ __forceinline__ void xinv_tile(const Launch& L, int bid) {
 // FFT along AXIS (1 = y, 2 = z) of tiles of `tk` adjacent x-frequency columns.
 // MODE 0: forward; 1: inverse; 2: forward, multiply by scale/|k|^2, inverse.
 template <typename T, int D, int AXIS, int MODE, bool INCR>
-__device__ __forceinline__ void faxis_tile(const Launch& L, int bid) {
+__device__ __forceinline__ void faxis_tile(const Launch& L, int bid, const void*& twp) {
     using V = typename Cx<T>::t;
     using Args = FftArgs<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -566,7 +572,10 @@ __device__ __forceinline__ void faxis_tile(const Launch& L, int bid) {
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* X = s_tw + n;
     V* Y = X + n * tk;
-    load_twiddles(s_tw, g_tw, n);
+    if (twp != (const void*)g_tw) {  // the RVE's table, loaded when the block's RVE changes
+        load_twiddles(s_tw, g_tw, n);
+        twp = g_tw;
+    }
 
     const int gxa = (H + tk - 1) / tk;
     const int gya = (D == 3) ? n : 1;
@@ -715,7 +724,7 @@ struct XPlan {
 };
 
 template <typename T, int N, int D, bool INCR>
-__device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid) {
+__device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid, bool& twl) {
     using V = typename Cx<T>::t;
     using Args = FftArgs<T>;
     using X = XPlan<N>;
@@ -739,7 +748,10 @@ __device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid) {
     V* buf = s_tw + N;          // two buffers of H * S values
     V* stage = buf + H * S;     // the second one stages the input lines
     T* stage_r = reinterpret_cast<T*>(stage);
-    load_twiddles(s_tw, Args::tw(L), N);
+    if (!twl) {  // the table of this length, once per block
+        load_twiddles(s_tw, Args::tw(L), N);
+        twl = true;
+    }
     // one component per tile (tiles_x): three times the blocks of a loop over components,
     // whose load latency then overlaps across blocks instead of adding up within one
     constexpr int NB = nlines / LPB;
@@ -890,7 +902,7 @@ __device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid) {
 }
 
 template <typename T, typename TO, int N, int D, bool INCR>
-__device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
+__device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid, bool& twl) {
     using V = typename Cx<T>::t;
     using Args = FftArgs<T>;
     using X = XPlan<N>;
@@ -916,7 +928,10 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid) {
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* buf = s_tw + N;
     V* stage = buf + H * S;
-    load_twiddles(s_tw, Args::tw(L), N);
+    if (!twl) {  // the table of this length, once per block
+        load_twiddles(s_tw, Args::tw(L), N);
+        twl = true;
+    }
     constexpr int NB = nlines / LPB;  // one component per tile, as in xfwd_fixed_tile
     const int c0 = bid / NB;
     const int line0 = (bid % NB) * LPB;
@@ -1055,7 +1070,7 @@ struct PlaneFused {
 };
 
 template <typename TO, bool INCR>
-__device__ __forceinline__ void yxinv_tile(const Launch& L, int bid) {
+__device__ __forceinline__ void yxinv_tile(const Launch& L, int bid, bool& twl) {
     using T = float;
     using V = float2;
     using Args = FftArgs<T>;
@@ -1081,7 +1096,10 @@ __device__ __forceinline__ void yxinv_tile(const Launch& L, int bid) {
     float* Plo_out = INCR ? reinterpret_cast<float*>(par ? L.U64[1] : L.U64[0]) + 3 * Vn : nullptr;
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* plane = s_tw + N;
-    load_twiddles(s_tw, Args::tw(L), N);
+    if (!twl) {  // the table of this length, once per block
+        load_twiddles(s_tw, Args::tw(L), N);
+        twl = true;
+    }
     const int c = bid / N, z = bid % N;
     // inverse y transforms of the plane's columns, 16 at a time (faxis_fixed_tile, AXIS 1,
     // MODE 1), into the shared plane
@@ -1187,7 +1205,7 @@ __device__ __forceinline__ void yxinv_tile(const Launch& L, int bid) {
 
 // faxis_tile with a fixed column length N (see ColPlan); same tiles and modes.
 template <typename T, int N, int D, int AXIS, int MODE, bool INCR>
-__device__ __forceinline__ void faxis_fixed_tile(const Launch& L, int bid) {
+__device__ __forceinline__ void faxis_fixed_tile(const Launch& L, int bid, bool& twl) {
     using V = typename Cx<T>::t;
     using Args = FftArgs<T>;
     using P = ColPlan<N>;
@@ -1205,7 +1223,10 @@ __device__ __forceinline__ void faxis_fixed_tile(const Launch& L, int bid) {
     V* S = reinterpret_cast<V*>(par ? U0 : U1);
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* buf = s_tw + N;
-    load_twiddles(s_tw, g_tw, N);
+    if (!twl) {  // the table of this length, once per block
+        load_twiddles(s_tw, g_tw, N);
+        twl = true;
+    }
     constexpr int gxa = H / TK;
     constexpr int gya = (D == 3) ? N : 1;
     const int col0 = (bid % gxa) * TK;
@@ -1309,9 +1330,10 @@ inline int lines_per_block(int n, int nlines) {
 template <typename T, int D, bool INCR>
 __global__ void __launch_bounds__(kFftThreads)
 k_xfwd(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
+    const void* twp = nullptr;  // the twiddle table in shared memory
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tl = tiles[t];
-        xfwd_tile<T, D, INCR>(rds[tl.x], tl.y);
+        xfwd_tile<T, D, INCR>(rds[tl.x], tl.y, twp);
         __syncthreads();
     }
 }
@@ -1319,9 +1341,10 @@ k_xfwd(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntile
 template <typename T, typename TO, int D, bool INCR>
 __global__ void __launch_bounds__(kFftThreads)
 k_xinv(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
+    const void* twp = nullptr;  // the twiddle table in shared memory
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tl = tiles[t];
-        xinv_tile<T, TO, D, INCR>(rds[tl.x], tl.y);
+        xinv_tile<T, TO, D, INCR>(rds[tl.x], tl.y, twp);
         __syncthreads();
     }
 }
@@ -1329,9 +1352,10 @@ k_xinv(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntile
 template <typename T, int D, int AXIS, int MODE, bool INCR>
 __global__ void __launch_bounds__(kFftThreads)
 k_faxis(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
+    const void* twp = nullptr;  // the twiddle table in shared memory
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tl = tiles[t];
-        faxis_tile<T, D, AXIS, MODE, INCR>(rds[tl.x], tl.y);
+        faxis_tile<T, D, AXIS, MODE, INCR>(rds[tl.x], tl.y, twp);
         __syncthreads();
     }
 }
@@ -1340,9 +1364,10 @@ k_faxis(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntil
 template <typename TO, bool INCR>
 __global__ void __launch_bounds__(kFftThreads, 3) k_yxinv128(const Launch* __restrict__ rds,
                                                           const int2* __restrict__ tiles, int ntiles) {
+    bool twl = false;  // the twiddle table is in shared memory
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tl = tiles[t];
-        yxinv_tile<TO, INCR>(rds[tl.x], tl.y);
+        yxinv_tile<TO, INCR>(rds[tl.x], tl.y, twl);
         __syncthreads();
     }
 }
@@ -1354,9 +1379,10 @@ constexpr size_t kPlaneSmem = (size_t)(PlaneFused::N + PlaneFused::N * PlaneFuse
 template <typename T, int N, int D, int AXIS, int MODE, bool INCR>
 __global__ void __launch_bounds__(kFftThreads, (MODE == 2 && !INCR && std::is_same<T, float>::value) ? 4 : 1)
 k_faxis_fixed(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
+    bool twl = false;  // the twiddle table is in shared memory
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tl = tiles[t];
-        faxis_fixed_tile<T, N, D, AXIS, MODE, INCR>(rds[tl.x], tl.y);
+        faxis_fixed_tile<T, N, D, AXIS, MODE, INCR>(rds[tl.x], tl.y, twl);
         __syncthreads();
     }
 }
@@ -1364,9 +1390,10 @@ k_faxis_fixed(const Launch* __restrict__ rds, const int2* __restrict__ tiles, in
 template <typename T, int N, int D, bool INCR>
 __global__ void __launch_bounds__(kFftThreads)
 k_xfwd_fixed(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
+    bool twl = false;  // the twiddle table is in shared memory
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tl = tiles[t];
-        xfwd_fixed_tile<T, N, D, INCR>(rds[tl.x], tl.y);
+        xfwd_fixed_tile<T, N, D, INCR>(rds[tl.x], tl.y, twl);
         __syncthreads();
     }
 }
@@ -1374,9 +1401,10 @@ k_xfwd_fixed(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int
 template <typename T, typename TO, int N, int D, bool INCR>
 __global__ void __launch_bounds__(kFftThreads)
 k_xinv_fixed(const Launch* __restrict__ rds, const int2* __restrict__ tiles, int ntiles) {
+    bool twl = false;  // the twiddle table is in shared memory
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tl = tiles[t];
-        xinv_fixed_tile<T, TO, N, D, INCR>(rds[tl.x], tl.y);
+        xinv_fixed_tile<T, TO, N, D, INCR>(rds[tl.x], tl.y, twl);
         __syncthreads();
     }
 }
