@@ -63,11 +63,12 @@ def bytes_per_voxel(cls: str, s: int, d: int = 3) -> float:
 
 
 # DRAM bytes (read + write) per launch measured with ncu on the 128^3 inclusion cell
-# (profiles/), keyed by (kernel class, precision); absent = not captured since the
-# kernel last changed
-TRAFFIC = {("local", "fp32"): 178640128 + 91970304, ("local_r", "fp64"): 415352064 + 184859904,
-           ("xfwd", "fp32"): 151019264 + 9842176, ("solve", "fp32"): 50366976 + 333056,
-           ("xinv", "fp32"): 25195776 + 0, ("xinv_incr", "fp32"): 50370560 + 3523328}
+# (profiles/), keyed by (kernel class, precision; solve: the float phase's z solve, which
+# also reads and writes the kept spectrum); absent = not captured since the kernel last changed
+TRAFFIC = {("local", "fp32"): 178659584 + 89560832, ("local_r", "fp64"): 415213312 + 181827840,
+           ("xfwd", "fp32"): 151093248 + 9586432, ("fwd_y", "fp32"): 25188096 + 0,
+           ("solve", "fp32"): 50367488 + 5888, ("xinv", "fp32"): 25196544 + 0,
+           ("xfwd_incr", "fp32"): 75529216 + 134144, ("xinv_incr", "fp32"): 50368768 + 327680}
 # FP32 flops per launch by kernel class, where counted with ncu for the current kernel
 # (none since the float local step became the closed form: no ALU view is reported)
 FLOPS = {}
