@@ -1029,23 +1029,23 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid, bool& 
 #pragma unroll 1
                 for (int q = 0; q < 4; ++q) store(q);
             }
-            continue;
-        }
-        for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
-            const int l = idx >> X::LOGN;
-            const int xi = idx & (N - 1);
-            const int line = line0 + l;
-            if (line < nlines) {
-                const T v = stage_r[((xi >> 1) * S + l) * 2 + (xi & 1)];
-                const long long o = (long long)line * N + xi;
-                if (INCR) {
-                    if (upair)
-                        Plo_out[(long long)c * Vn + o] = Plo_in[(long long)c * Vn + o] + (float)v;
-                    else
-                        O_c[o] = I_c[o] + (TO)v;
-                    DUout[(long long)c * Vn + o] = v;
-                } else {
-                    O_c[o] = (TO)v;
+        } else {
+            for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
+                const int l = idx >> X::LOGN;
+                const int xi = idx & (N - 1);
+                const int line = line0 + l;
+                if (line < nlines) {
+                    const T v = stage_r[((xi >> 1) * S + l) * 2 + (xi & 1)];
+                    const long long o = (long long)line * N + xi;
+                    if (INCR) {
+                        if (upair)
+                            Plo_out[(long long)c * Vn + o] = Plo_in[(long long)c * Vn + o] + (float)v;
+                        else
+                            O_c[o] = I_c[o] + (TO)v;
+                        DUout[(long long)c * Vn + o] = v;
+                    } else {
+                        O_c[o] = (TO)v;
+                    }
                 }
             }
         }
