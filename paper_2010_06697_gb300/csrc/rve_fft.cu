@@ -748,7 +748,7 @@ __device__ __forceinline__ void xfwd_fixed_tile(const Launch& L, int bid, bool& 
     V* buf = s_tw + N;          // two buffers of H * S values
     V* stage = buf + H * S;     // the second one stages the input lines
     T* stage_r = reinterpret_cast<T*>(stage);
-    if (!twl) {  // the table of this length, once per block
+    if (!twl) {  // exp(-2 pi i m / N) depends on N only: loaded on the block's first tile
         load_twiddles(s_tw, Args::tw(L), N);
         twl = true;
     }
@@ -928,7 +928,7 @@ __device__ __forceinline__ void xinv_fixed_tile(const Launch& L, int bid, bool& 
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* buf = s_tw + N;
     V* stage = buf + H * S;
-    if (!twl) {  // the table of this length, once per block
+    if (!twl) {  // exp(-2 pi i m / N) depends on N only: loaded on the block's first tile
         load_twiddles(s_tw, Args::tw(L), N);
         twl = true;
     }
@@ -1096,7 +1096,7 @@ __device__ __forceinline__ void yxinv_tile(const Launch& L, int bid, bool& twl) 
     float* Plo_out = INCR ? reinterpret_cast<float*>(par ? L.U64[1] : L.U64[0]) + 3 * Vn : nullptr;
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* plane = s_tw + N;
-    if (!twl) {  // the table of this length, once per block
+    if (!twl) {  // exp(-2 pi i m / N) depends on N only: loaded on the block's first tile
         load_twiddles(s_tw, Args::tw(L), N);
         twl = true;
     }
@@ -1223,7 +1223,7 @@ __device__ __forceinline__ void faxis_fixed_tile(const Launch& L, int bid, bool&
     V* S = reinterpret_cast<V*>(par ? U0 : U1);
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* buf = s_tw + N;
-    if (!twl) {  // the table of this length, once per block
+    if (!twl) {  // exp(-2 pi i m / N) depends on N only: loaded on the block's first tile
         load_twiddles(s_tw, g_tw, N);
         twl = true;
     }
